@@ -1,0 +1,332 @@
+"""Benchmark: 2D FMM potentials/sec at relative error <= 1e-6, mixed precision vs the FP64 GPU path.
+
+Workload (default): N = 2^20 points, half uniform in [0,1]^2 and half from 8 Gaussian clusters
+(sigma 0.01), strengths N(0,1), 8 levels (16 points per leaf), theta = 1/2, p = 20.
+
+One step = one pass of the whole method on one input resident in HBM: build the tree, build the
+interaction lists, evaluate (P2M, M2M, M2L, L2L, L2P + near field), potentials in input order.
+The L2 cache (129 MB) is flushed between steps by writing a 256 MB buffer outside the timed
+events.  Per-stage device times come from CUDA events recorded by the library on its stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (the method has no exchange step on one
+instance here); value = points of all ranks / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D FMM potentials/sec at rel err <=1e-6, mixed-prec vs FP64 GPU path"
+UNIT = "potentials/s"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---- clocks sampled during the timed region ------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- the reference arm: the FP64 CPU oracle as it stands ----------------------------------------
+
+def run_reference(args, rank):
+    import oracle
+    from paper_1006_2269_gb300 import workloads as W
+    if rank != 0:
+        return None
+    oracle.build()
+    w = W.MIXED_1M
+    ns, Ls = 1 << 16, 6  # bounded sample of the workload: same distribution, 16 points per leaf
+    c = W.mixed_1m_cloud(ns)
+    for _ in range(args.warmup):
+        oracle.fmm(c.x, c.y, c.q, Ls, w.p, w.theta)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fmm(c.x, c.y, c.q, Ls, w.p, w.theta)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = ns / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"clusters N={ns}, L={Ls}, theta=1/2, p={w.p} (bounded sample of {w.name})",
+                   "sample_of": w.name},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle FMM on N={ns} points of the same distribution, L={Ls}, p={w.p}"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# ---- our arm -----------------------------------------------------------------------------------
+
+def pair_counts(f):
+    """Algorithmic units of the current tree/lists: weak pairs per level and near-field pair
+    evaluations (sum over leaves of n_t * sum of strong n_s)."""
+    from paper_1006_2269_gb300 import fmm
+    _, L, nbox = fmm.fmm_tree_info(f.tree)
+    woff, widx, soff, sidx = (a.cpu().numpy().astype(np.int64) for a in f.export_lists())
+    _, _, lb = f.export_tree()
+    lb = lb.cpu().numpy().astype(np.int64)
+    nweak = int(woff[-1])
+    base = (4 ** L - 1) // 3
+    sizes = np.diff(lb)
+    so = soff[base:base + 4 ** L + 1] - soff[base]
+    s_idx = sidx[soff[base]:soff[base + 4 ** L]]
+    src = np.add.reduceat(sizes[s_idx], so[:-1]) if s_idx.size else np.zeros(4 ** L)
+    pairs = int(np.sum(sizes * src))
+    return nweak, pairs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1006_2269_gb300 import build, fmm, workloads as W
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    fmm.load_library()
+
+    w = W.MIXED_1M
+    c = W.mixed_1m_cloud()
+    n = w.n
+    xh, yh, qh = (torch.from_numpy(a).pin_memory() for a in (c.x, c.y, c.q))
+    x, y, q = (a.to(dev) for a in (xh, yh, qh))
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    f = fmm.FMM(x, y, w.levels, w.theta)
+
+    def step(mode):
+        fmm.fmm_build_tree(f.tree, x, y)
+        fmm.fmm_interaction_lists(f.tree, f.lists, w.theta)
+        fmm.fmm_evaluate(f.tree, f.lists, q, w.p, mode, phi)
+
+    # warm-up, then the accuracy check against the binary64 direct sum at sampled targets
+    for _ in range(args.warmup):
+        step(fmm.FMM_MODE_MIXED)
+    fmm.fmm_sync_status(f.tree, f.lists)
+    fmm.fmm_lists_sync(f.lists)
+    tg = torch.as_tensor(W.sample_targets(n, w.n_check, W.SEED_BASE + 101), device=dev)
+    ref = torch.empty(tg.numel(), dtype=torch.float64, device=dev)
+    fmm.fmm_direct(x, y, q, tg, ref)
+    step(fmm.FMM_MODE_MIXED)
+    torch.cuda.synchronize()
+    scale = ref.abs().max().item()
+    err_mixed = (phi[tg] - ref).abs().max().item() / scale
+    step(fmm.FMM_MODE_FP64)
+    torch.cuda.synchronize()
+    err_fp64 = (phi[tg] - ref).abs().max().item() / scale
+    nweak, npairs = pair_counts(f)
+
+    def timed(mode, steps, e2e=False, profile=False):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        fmm.fmm_profile_read()
+        fmm.fmm_profile_enable(profile)
+        l0 = fmm.fmm_launch_count()
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record(stream)
+            if e2e:
+                x.copy_(xh, non_blocking=True)
+                y.copy_(yh, non_blocking=True)
+                q.copy_(qh, non_blocking=True)
+            step(mode)
+            if e2e:
+                phi_h.copy_(phi, non_blocking=True)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        launches = fmm.fmm_launch_count() - l0
+        fmm.fmm_profile_enable(False)
+        prof = fmm.fmm_profile_read()
+        if world > 1:
+            dist.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+        t = torch.tensor([ms], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item(), launches, prof
+
+    with ClockSampler(local) as clk:
+        ms_mixed, launches, prof = timed(fmm.FMM_MODE_MIXED, args.steps, profile=True)
+    ms_mixed_plain, _, _ = timed(fmm.FMM_MODE_MIXED, args.steps)
+    ms_e2e, _, _ = timed(fmm.FMM_MODE_MIXED, args.steps, e2e=True)
+    ms_fp64, _, prof64 = timed(fmm.FMM_MODE_FP64, args.fp64_steps, profile=True)
+    fmm.fmm_sync_status(f.tree, f.lists)
+
+    K = args.steps
+    per_step = ms_mixed_plain / K
+    value = world * n / (per_step * 1e-3)
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]}
+    stage_ms64 = {k: v[0] / max(v[1], 1) for k, v in prof64.items() if v[1]}
+    top = max(stage_ms, key=stage_ms.get)
+
+    # roofline of the dominant kernel (per launch): algorithmic work / measured duration
+    P = w.p + 1
+    hbm, hbm_kind = peaks()
+    mufu_peak = 16 * SM_COUNT * SM_MAX_MHZ * 1e6  # log2 evaluations / s
+    fp32_peak = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6  # flop / s
+    t_top = stage_ms[top] * 1e-3
+    if top == "leaf":
+        roof = {"bound": "alu", "achieved": npairs / t_top / 1e12, "peak": mufu_peak / 1e12,
+                "unit": "Tlog2/s (MUFU)", "traffic": None}
+    elif top == "m2l":
+        roof = {"bound": "alu", "achieved": nweak * 4 * P * P / t_top / 1e12, "peak": fp32_peak / 1e12,
+                "unit": "TFLOP/s (FP32 FMA pipe)", "traffic": None}
+    elif top == "tree_sort":
+        byts = n * (32 + 16 * 24)
+        roof = {"bound": "hbm", "achieved": byts / t_top / 1e9, "peak": hbm, "unit": "GB/s",
+                "traffic": None}
+    else:
+        byts = n * 30 * w.levels
+        roof = {"bound": "hbm", "achieved": byts / t_top / 1e9, "peak": hbm, "unit": "GB/s",
+                "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = top
+    roof["peak_kind"] = hbm_kind if roof["bound"] == "hbm" else "derived: units x 152 SMs x 2070 MHz"
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "levels": w.levels, "theta": w.theta, "p": w.p,
+                   "mode": "mixed", "l2": "flushed between steps (256 MB write outside the events)",
+                   "replicas": world},
+        "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,
+        "fp64_path": {"value": world * n / (ms_fp64 / args.fp64_steps * 1e-3),
+                      "ms_per_step": ms_fp64 / args.fp64_steps, "stages_ms": stage_ms64},
+        "speedup_vs_fp64": (ms_fp64 / args.fp64_steps) / per_step,
+        "stages_ms": stage_ms, "weak_pairs": nweak, "near_pair_evals": npairs,
+        "e2e": {"value": world * n / (ms_e2e / K * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ns, Ls = 1 << 16, 6
+        cs = W.mixed_1m_cloud(ns)
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            oracle.fmm(cs.x, cs.y, cs.q, Ls, w.p, w.theta)
+            reps += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        dt = (time.perf_counter() - t0) / reps
+        out["cpu_baseline"] = {"value": ns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"oracle FMM, N={ns} points of the same distribution, L={Ls}, "
+                                         f"p={w.p}, {reps} runs"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    f.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

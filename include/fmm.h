@@ -1,0 +1,191 @@
+/*
+ * fmm.h -- C ABI of libfmm_gb300.so, a GB300-native (sm_103a) implementation of the
+ * asymmetric adaptive 2D fast multipole method of S. Engblom, "On well-separated sets and fast
+ * multipole methods".
+ *
+ * The library evaluates, for N points z_i = (x_i, y_i) with strengths q_i,
+ *
+ *     phi_i = sum_{j != i} q_j log|z_i - z_j|            (Eq. (1.1), 2D harmonic kernel)
+ *
+ * with the paper's method (Section 4): a balanced tree obtained by splitting every box at the
+ * median along x and then along y (Fig. 1.1, Fig. 4.1), strong/weak interaction lists from the
+ * one-parameter theta-criterion (Criterion 2.1), order-p complex expansions pushed through
+ * P2M -> M2M -> M2L -> L2L -> L2P, and a direct near-field sum along the finest strong lists.
+ *
+ * Conventions shared by every entry point
+ *   - Array arguments are DEVICE pointers (cudaMalloc'd or equivalent, on the device that is
+ *     current when the call is made) unless the argument name ends in _host.  They are owned by
+ *     the caller and are not retained after the call returns.
+ *   - Handles (fmm_tree, fmm_lists) are owned by the library; release them with the matching
+ *     *_destroy function.  A handle is bound to the device that was current at creation.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute calls only enqueue
+ *     work on it and return; they never synchronise with the host.  Conditions that can only
+ *     be seen on the device (non-finite input, list capacity overflow) set a device-side status
+ *     word that fmm_sync_status() reads.
+ *   - Every int-returning function returns FMM_OK (0) or a negative fmm_status; the message of
+ *     the last error on the calling thread is available from fmm_last_error().
+ *   - There is no CPU fallback: every step runs in the library's CUDA kernels.
+ *   - Point indices are 32-bit (N < 2^31).
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_ARG = -1,        /* bad argument (null pointer, size, p, theta, ...)            */
+    FMM_ERR_NONFINITE = -2,  /* a coordinate or strength is NaN or infinite                 */
+    FMM_ERR_LEVELS = -3,     /* N < 4^levels: some leaf would be empty                      */
+    FMM_ERR_OOM = -4,        /* device allocation failed                                    */
+    FMM_ERR_CUDA = -5,       /* a CUDA runtime call failed                                  */
+    FMM_ERR_CAPACITY = -6,   /* interaction lists exceeded the capacity of the fmm_lists   */
+    FMM_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up                          */
+    FMM_ERR_STATE = -8       /* handle used out of order (e.g. lists of another tree)       */
+} fmm_status;
+
+typedef enum {
+    FMM_MODE_FP64 = 0,   /* every stage in binary64                                         */
+    FMM_MODE_MIXED = 1   /* binary32 expansions, near field and accumulation (see below)    */
+} fmm_mode;
+
+typedef struct fmm_tree_s* fmm_tree;
+typedef struct fmm_lists_s* fmm_lists;
+
+/*
+ * Parameters of one evaluation.
+ *   p      expansion order: coefficients k = 0..p (a_0 is the logarithmic term), 0 <= p <= 40.
+ *          The relative error behaves like theta^(p+1)/(1-theta)^2 (Section 3).
+ *   mode   FMM_MODE_FP64 or FMM_MODE_MIXED.
+ *   tol    requested relative tolerance; in FMM_MODE_MIXED a tol below 1e-7 makes the final
+ *          L2P + near-field accumulation run in binary64.  Ignored in FMM_MODE_FP64.
+ */
+typedef struct {
+    int p;
+    int mode;
+    double tol;
+} fmm_params;
+
+/* ---------------------------------------------------------------------------------------------
+ * Tree: Section 4 (median splits), Fig. 1.1, Fig. 4.1.
+ * Box i of level l (0 <= l <= levels) has global id (4^l - 1)/3 + i; its children are boxes
+ * 4i+k of level l+1 with k = 0:(x-low,y-low) 1:(x-low,y-high) 2:(x-high,y-low) 3:(x-high,y-high).
+ * A set of n points is split along x into the floor(n/2) smallest in (x, input index) order and
+ * the rest; each half is then split the same way along y.  The split coordinate is 0.5*(a+b)
+ * of the two straddling coordinates.  The root is the tight bounding box of the points.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Allocate a tree for n points and `levels` levels below the root (n >= 4^levels, levels <= 13,
+ * n < 2^31).  Allocates device memory (synchronous); no kernel runs. */
+int fmm_tree_create(int64_t n, int levels, fmm_tree* out);
+
+/* Build the tree of points (x[n], y[n]) (binary64, device).  The tree keeps its own copy of
+ * everything it needs; x and y may be reused after the work on `stream` completes.  Non-finite
+ * coordinates set FMM_ERR_NONFINITE in the device status. */
+int fmm_build_tree(fmm_tree t, const double* x, const double* y, void* stream);
+
+/* Copy the tree out (device pointers, any may be NULL):
+ *   perm[n]            canonical point order: leaves in id order, inside a leaf ascending input
+ *                      index; perm[k] is the input index of the k-th point.
+ *   rects[4*nbox]      (x0, x1, y0, y1) per box in global id order, nbox = (4^(levels+1)-1)/3.
+ *   leaf_begin[4^levels + 1]  leaf i holds perm[leaf_begin[i] .. leaf_begin[i+1]).        */
+int fmm_tree_export(fmm_tree t, int32_t* perm, double* rects, int32_t* leaf_begin, void* stream);
+
+/* Number of points, levels and boxes of a tree (host values). */
+int fmm_tree_info(fmm_tree t, int64_t* n, int* levels, int64_t* nbox);
+
+void fmm_tree_destroy(fmm_tree t);
+
+/* ---------------------------------------------------------------------------------------------
+ * Interaction lists: Section 4 with Criterion 2.1.
+ * S(root) = {root}, W(root) = {}.  For a box b of level l >= 1 the candidates are the children
+ * of every box of S(parent(b)) in ascending id; a candidate c joins W(b) when
+ *     R + theta*r <= theta*d   and   R + r < d
+ * (d = distance of the centres, R/r = larger/smaller radius; centre = rectangle midpoint,
+ * radius = half diagonal), otherwise S(b).  Lists are CSR over global box ids whose entries are
+ * within-level box indices in ascending order.  M2L runs along W on every level, the direct
+ * near-field sum along S of the finest level.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Allocate list storage for tree t with room for weak_capacity weak and strong_capacity strong
+ * entries in total (0 = a default of 64 and 32 per box). */
+int fmm_lists_create(fmm_tree t, int64_t weak_capacity, int64_t strong_capacity, fmm_lists* out);
+
+/* Build the lists of tree t (which must have been built on the same stream or be complete)
+ * for 0 < theta < 1.  Overflow of the capacity sets FMM_ERR_CAPACITY in the device status;
+ * later kernels then read only within the capacity. */
+int fmm_interaction_lists(fmm_tree t, fmm_lists l, double theta, void* stream);
+
+/* Wait for `stream`, then report the list totals (host values, may be NULL) and the status. */
+int fmm_lists_sync(fmm_lists l, void* stream, int64_t* n_weak, int64_t* n_strong);
+
+/* Copy the lists out (device pointers): woff/soff[nbox+1], widx[n_weak], sidx[n_strong]. */
+int fmm_lists_export(fmm_lists l, int32_t* woff, int32_t* widx, int32_t* soff, int32_t* sidx,
+                     void* stream);
+
+void fmm_lists_destroy(fmm_lists l);
+
+/* ---------------------------------------------------------------------------------------------
+ * Evaluation: the upward pass (P2M on the leaves, M2M towards the root), M2L along the weak
+ * lists of every level, the downward pass (L2L), L2P and the direct sum along the strong lists
+ * of the finest level (Section 4).  Expansions are the classical complex ones of Section 5:
+ * multipole a_0 log(z - c) + sum_k a_k (z - c)^-k, local sum_l b_l (z - c)^l, stored scaled by
+ * the box radius.  phi[n] (binary64, device) receives the potentials in INPUT order.
+ * q[n]: strengths (binary64, device).  The first call with a given p allocates the expansion
+ * workspace of the tree (synchronous); later calls with the same or a smaller p allocate
+ * nothing.
+ * ------------------------------------------------------------------------------------------- */
+int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi,
+                 void* stream);
+
+/* Eq. (1.1) by direct summation in binary64 at m target input indices targets[m] (int64,
+ * device) over all n sources; phi[m] (device).  Coincident distinct points contribute 0. */
+int fmm_direct(const double* x, const double* y, const double* q, int64_t n,
+               const int64_t* targets, int64_t m, double* phi, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Instrumentation (no paper counterpart): per-stage device times and a kernel launch counter,
+ * used by the benchmark to report per-kernel rooflines.
+ * ------------------------------------------------------------------------------------------- */
+typedef enum {
+    FMM_STAGE_TREE_SORT = 0,   /* keys, bounding box, the x and y radix sorts                 */
+    FMM_STAGE_TREE_SPLIT = 1,  /* per-level stable partitions, split coordinates, rectangles  */
+    FMM_STAGE_TREE_FINISH = 2, /* canonical order, box geometry, gathered coordinates         */
+    FMM_STAGE_LISTS = 3,       /* strong/weak lists of all levels                              */
+    FMM_STAGE_GATHER = 4,      /* strengths into canonical order                               */
+    FMM_STAGE_P2M = 5,
+    FMM_STAGE_M2M = 6,
+    FMM_STAGE_M2L = 7,
+    FMM_STAGE_L2L = 8,
+    FMM_STAGE_LEAF = 9,        /* L2P + near-field direct sum, potentials written in input order */
+    FMM_STAGE_COUNT = 10
+} fmm_stage;
+
+/* Enable (on != 0) or disable recording of a CUDA event pair around every stage, on the stream
+ * of the call that runs the stage.  Process-wide; meant for one device at a time. */
+int fmm_profile_enable(int on);
+
+/* Wait for the recorded events and add, per stage, the elapsed milliseconds to ms[stage] and
+ * the number of recorded stage executions to count[stage] (host arrays of nstages entries, either
+ * may be NULL); then forget the records.  Returns the number of records read or an error. */
+int fmm_profile_read(double* ms_host, int64_t* count_host, int nstages);
+
+/* Number of kernels the library has launched in this process so far. */
+int64_t fmm_launch_count(void);
+
+/* Wait for `stream` and return the first error recorded in the device status of the tree and
+ * (if not NULL) the lists, then clear it. */
+int fmm_sync_status(fmm_tree t, fmm_lists l, void* stream);
+
+/* Message of the last error returned on the calling thread ("" if none). */
+const char* fmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_GB300_H */

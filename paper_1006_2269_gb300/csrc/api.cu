@@ -1,0 +1,350 @@
+// The C ABI of libfmm_gb300.so (declared in include/fmm.h): argument checks, handle lifetime,
+// device selection and the device status word.  All computation is in the kernels of tree.cu,
+// lists.cu, scan.cu and expand.cu.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fmm {
+
+static thread_local char g_msg[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(FMM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+static std::atomic<int64_t> g_launches{0};
+static std::mutex g_prof_mutex;
+static bool g_prof_on = false;
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+static std::vector<ProfRec> g_prof_recs;
+static std::vector<cudaEvent_t> g_prof_pool;
+static cudaEvent_t g_prof_open[FMM_STAGE_COUNT] = {};
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void prof_mark(int stage, bool begin, cudaStream_t s)
+{
+    if (!g_prof_on || stage < 0 || stage >= FMM_STAGE_COUNT) return;
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    cudaEvent_t e;
+    if (!g_prof_pool.empty()) {
+        e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return;
+    }
+    cudaEventRecord(e, s);
+    if (begin) {
+        if (g_prof_open[stage]) g_prof_pool.push_back(g_prof_open[stage]);
+        g_prof_open[stage] = e;
+    } else if (g_prof_open[stage]) {
+        g_prof_recs.push_back({stage, g_prof_open[stage], e});
+        g_prof_open[stage] = nullptr;
+    } else {
+        g_prof_pool.push_back(e);
+    }
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define GUARD(dev)                                                               \
+    DeviceGuard guard_(dev);                                                     \
+    if (!guard_.ok) return fail(FMM_ERR_CUDA, "cannot select device %d", (dev));
+
+void free_tree(fmm_tree t)
+{
+    if (!t) return;
+    void* ptrs[] = {t->rects, t->centers, t->radii, t->cen_hi, t->cen_lo, t->perm, t->leaf_begin,
+                    t->leaf_of, t->xs, t->ys, t->dxf, t->dyf, t->keys, t->vals, t->rs_counts,
+                    t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->status,
+                    t->Me, t->Le, t->Mf, t->Lf, t->qs, t->qf};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete t;
+}
+
+void free_lists(fmm_lists l)
+{
+    if (!l) return;
+    void* ptrs[] = {l->woff, l->soff, l->widx, l->sidx, l->wcnt, l->scnt, l->scan_tmp, l->status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete l;
+}
+
+int status_to_code(int32_t st)
+{
+    if (st & ST_NONFINITE) return fail(FMM_ERR_NONFINITE, "non-finite coordinate or strength");
+    if (st & ST_CAPACITY) return fail(FMM_ERR_CAPACITY, "interaction lists exceed the capacity");
+    if (st & ST_TIMEOUT) return fail(FMM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & ST_ARG) return fail(FMM_ERR_STATE, "inconsistent internal state detected on the device");
+    return FMM_OK;
+}
+
+}  // namespace
+}  // namespace fmm
+
+using namespace fmm;
+
+extern "C" {
+
+const char* fmm_last_error(void) { return g_msg; }
+
+int fmm_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    g_prof_on = on != 0;
+    return FMM_OK;
+}
+
+int fmm_profile_read(double* ms, int64_t* count, int nstages)
+{
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    int nread = 0;
+    for (const ProfRec& r : g_prof_recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+            return fail(FMM_ERR_CUDA, "profile events");
+        if (r.stage < nstages) {
+            if (ms) ms[r.stage] += t;
+            if (count) count[r.stage] += 1;
+        }
+        g_prof_pool.push_back(r.a);
+        g_prof_pool.push_back(r.b);
+        nread++;
+    }
+    g_prof_recs.clear();
+    return nread;
+}
+
+int64_t fmm_launch_count(void) { return g_launches.load(); }
+
+int fmm_tree_create(int64_t n, int levels, fmm_tree* out)
+{
+    if (!out) return fail(FMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (levels < 0 || levels > 13) return fail(FMM_ERR_ARG, "levels = %d outside [0, 13]", levels);
+    if (n < 1 || n >= ((int64_t)1 << 31) - 1) return fail(FMM_ERR_ARG, "n = %lld outside [1, 2^31)", (long long)n);
+    if (n < level_size(levels))
+        return fail(FMM_ERR_LEVELS, "n = %lld < 4^%d: some leaf would be empty", (long long)n, levels);
+    fmm_tree t = new (std::nothrow) fmm_tree_s();
+    if (!t) return fail(FMM_ERR_OOM, "host allocation");
+    t->n = n;
+    t->L = levels;
+    if (cudaGetDevice(&t->dev) != cudaSuccess) {
+        delete t;
+        return fail(FMM_ERR_CUDA, "no CUDA device");
+    }
+    int rc;
+    try {
+        rc = tree_alloc(t);
+    } catch (...) {
+        rc = fail(FMM_ERR_OOM, "host allocation");
+    }
+    if (rc) {
+        free_tree(t);
+        return rc;
+    }
+    *out = t;
+    return FMM_OK;
+}
+
+int fmm_build_tree(fmm_tree t, const double* x, const double* y, void* stream)
+{
+    if (!t || !x || !y) return fail(FMM_ERR_ARG, "NULL argument");
+    GUARD(t->dev);
+    return tree_build(t, x, y, (cudaStream_t)stream);
+}
+
+int fmm_tree_export(fmm_tree t, int32_t* perm, double* rects, int32_t* leaf_begin, void* stream)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (!t->built) return fail(FMM_ERR_STATE, "tree not built");
+    GUARD(t->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (perm) FMM_CUDA(cudaMemcpyAsync(perm, t->perm, 4 * t->n, cudaMemcpyDeviceToDevice, s));
+    if (rects) FMM_CUDA(cudaMemcpyAsync(rects, t->rects, 32 * t->nbox, cudaMemcpyDeviceToDevice, s));
+    if (leaf_begin)
+        FMM_CUDA(cudaMemcpyAsync(leaf_begin, t->leaf_begin, 4 * (t->nleaf + 1), cudaMemcpyDeviceToDevice, s));
+    return FMM_OK;
+}
+
+int fmm_tree_info(fmm_tree t, int64_t* n, int* levels, int64_t* nbox)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (n) *n = t->n;
+    if (levels) *levels = t->L;
+    if (nbox) *nbox = t->nbox;
+    return FMM_OK;
+}
+
+void fmm_tree_destroy(fmm_tree t)
+{
+    if (!t) return;
+    DeviceGuard g(t->dev);
+    free_tree(t);
+}
+
+int fmm_lists_create(fmm_tree t, int64_t weak_capacity, int64_t strong_capacity, fmm_lists* out)
+{
+    if (!t || !out) return fail(FMM_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    GUARD(t->dev);
+    if (weak_capacity <= 0) weak_capacity = 64 * t->nbox;
+    if (strong_capacity <= 0) strong_capacity = 32 * t->nbox;
+    if (weak_capacity >= INT32_MAX || strong_capacity >= INT32_MAX)
+        return fail(FMM_ERR_ARG, "capacity must be below 2^31 - 1");
+    fmm_lists l = new (std::nothrow) fmm_lists_s();
+    if (!l) return fail(FMM_ERR_OOM, "host allocation");
+    l->tree = t;
+    l->wcap = weak_capacity;
+    l->scap = strong_capacity;
+    const int64_t maxlev = level_size(t->L);
+    bool ok = cudaMalloc((void**)&l->woff, 4 * (t->nbox + 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->soff, 4 * (t->nbox + 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->widx, 4 * std::max<int64_t>(l->wcap, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->sidx, 4 * std::max<int64_t>(l->scap, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->wcnt, 4 * maxlev) == cudaSuccess &&
+              cudaMalloc((void**)&l->scnt, 4 * maxlev) == cudaSuccess &&
+              cudaMalloc((void**)&l->scan_tmp, 4 * scan_tmp_words(maxlev)) == cudaSuccess &&
+              cudaMalloc((void**)&l->status, 4) == cudaSuccess;
+    if (!ok) {
+        free_lists(l);
+        return fail(FMM_ERR_OOM, "list storage");
+    }
+    if (cudaMemset(l->status, 0, 4) != cudaSuccess) {
+        free_lists(l);
+        return fail(FMM_ERR_CUDA, "memset");
+    }
+    *out = l;
+    return FMM_OK;
+}
+
+int fmm_interaction_lists(fmm_tree t, fmm_lists l, double theta, void* stream)
+{
+    if (!t || !l) return fail(FMM_ERR_ARG, "NULL handle");
+    if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
+    if (!t->built) return fail(FMM_ERR_STATE, "tree not built");
+    if (!(theta > 0.0 && theta < 1.0)) return fail(FMM_ERR_ARG, "theta = %g outside (0, 1)", theta);
+    GUARD(t->dev);
+    return lists_build(t, l, theta, (cudaStream_t)stream);
+}
+
+int fmm_lists_sync(fmm_lists l, void* stream, int64_t* n_weak, int64_t* n_strong)
+{
+    if (!l) return fail(FMM_ERR_ARG, "NULL lists");
+    if (!l->built) return fail(FMM_ERR_STATE, "lists not built");
+    GUARD(l->tree->dev);
+    FMM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int32_t w = 0, s = 0, st = 0;
+    FMM_CUDA(cudaMemcpy(&w, l->woff + l->tree->nbox, 4, cudaMemcpyDeviceToHost));
+    FMM_CUDA(cudaMemcpy(&s, l->soff + l->tree->nbox, 4, cudaMemcpyDeviceToHost));
+    FMM_CUDA(cudaMemcpy(&st, l->status, 4, cudaMemcpyDeviceToHost));
+    if (n_weak) *n_weak = w;
+    if (n_strong) *n_strong = s;
+    if (st & ST_CAPACITY) return fail(FMM_ERR_CAPACITY, "lists need %d weak / %d strong entries, capacity %lld / %lld",
+                                      w, s, (long long)l->wcap, (long long)l->scap);
+    return FMM_OK;
+}
+
+int fmm_lists_export(fmm_lists l, int32_t* woff, int32_t* widx, int32_t* soff, int32_t* sidx, void* stream)
+{
+    if (!l) return fail(FMM_ERR_ARG, "NULL lists");
+    if (!l->built) return fail(FMM_ERR_STATE, "lists not built");
+    GUARD(l->tree->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    FMM_CUDA(cudaStreamSynchronize(s));
+    int32_t w = 0, st = 0;
+    FMM_CUDA(cudaMemcpy(&w, l->woff + l->tree->nbox, 4, cudaMemcpyDeviceToHost));
+    FMM_CUDA(cudaMemcpy(&st, l->soff + l->tree->nbox, 4, cudaMemcpyDeviceToHost));
+    const int64_t nb = l->tree->nbox + 1;
+    if (woff) FMM_CUDA(cudaMemcpyAsync(woff, l->woff, 4 * nb, cudaMemcpyDeviceToDevice, s));
+    if (soff) FMM_CUDA(cudaMemcpyAsync(soff, l->soff, 4 * nb, cudaMemcpyDeviceToDevice, s));
+    if (widx && w > 0)
+        FMM_CUDA(cudaMemcpyAsync(widx, l->widx, 4 * std::min<int64_t>(w, l->wcap), cudaMemcpyDeviceToDevice, s));
+    if (sidx && st > 0)
+        FMM_CUDA(cudaMemcpyAsync(sidx, l->sidx, 4 * std::min<int64_t>(st, l->scap), cudaMemcpyDeviceToDevice, s));
+    return FMM_OK;
+}
+
+void fmm_lists_destroy(fmm_lists l)
+{
+    if (!l) return;
+    DeviceGuard g(l->tree->dev);
+    free_lists(l);
+}
+
+int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi, void* stream)
+{
+    if (!t || !l || !q || !prm || !phi) return fail(FMM_ERR_ARG, "NULL argument");
+    if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
+    if (!t->built || !l->built) return fail(FMM_ERR_STATE, "tree or lists not built");
+    if (prm->p < 0 || prm->p > 40) return fail(FMM_ERR_ARG, "p = %d outside [0, 40]", prm->p);
+    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED)
+        return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
+    GUARD(t->dev);
+    return evaluate(t, l, q, *prm, phi, (cudaStream_t)stream);
+}
+
+int fmm_direct(const double* x, const double* y, const double* q, int64_t n, const int64_t* targets,
+               int64_t m, double* phi, void* stream)
+{
+    if (!x || !y || !q || (m > 0 && (!targets || !phi))) return fail(FMM_ERR_ARG, "NULL argument");
+    if (n < 1 || m < 0) return fail(FMM_ERR_ARG, "bad sizes n = %lld, m = %lld", (long long)n, (long long)m);
+    return direct(x, y, q, n, targets, m, phi, (cudaStream_t)stream);
+}
+
+int fmm_sync_status(fmm_tree t, fmm_lists l, void* stream)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    GUARD(t->dev);
+    FMM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int32_t st = 0, sl = 0;
+    FMM_CUDA(cudaMemcpy(&st, t->status, 4, cudaMemcpyDeviceToHost));
+    FMM_CUDA(cudaMemset(t->status, 0, 4));
+    if (l) {
+        FMM_CUDA(cudaMemcpy(&sl, l->status, 4, cudaMemcpyDeviceToHost));
+        FMM_CUDA(cudaMemset(l->status, 0, 4));
+    }
+    return status_to_code(st | sl);
+}
+
+}  // extern "C"

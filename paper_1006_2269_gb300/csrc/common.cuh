@@ -1,0 +1,174 @@
+// Internal declarations shared by the translation units of libfmm_gb300.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/fmm.h"
+
+namespace fmm {
+
+// ---- device status word bits (set by kernels with atomicOr, read by fmm_sync_status) ----
+enum : int32_t { ST_NONFINITE = 1, ST_CAPACITY = 2, ST_TIMEOUT = 4, ST_ARG = 8 };
+
+// ---- error reporting (thread-local message) ----
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define FMM_CUDA(call)                                             \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::fmm::cuda_fail(e_, #call); \
+    } while (0)
+
+#define FMM_LAUNCH_CHECK(what)                                     \
+    do {                                                           \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return ::fmm::cuda_fail(e_, what);  \
+    } while (0)
+
+// ---- instrumentation ----
+void note_launch(int n = 1);                          // count kernels launched by the library
+void prof_mark(int stage, bool begin, cudaStream_t s);  // CUDA event around a stage (if enabled)
+
+struct StageScope {
+    int stage;
+    cudaStream_t s;
+    StageScope(int st, cudaStream_t str) : stage(st), s(str) { prof_mark(stage, true, s); }
+    ~StageScope() { prof_mark(stage, false, s); }
+};
+
+// ---- level-order box numbering ----
+__host__ __device__ inline int64_t level_base(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
+__host__ __device__ inline int64_t level_size(int l) { return int64_t(1) << (2 * l); }
+
+// Descend the floor-left binary split tree of n positions by `depth` steps towards position
+// `pos`; returns the index j of the node at that depth and its offset o and size m.  A node of
+// size m has children of sizes floor(m/2) (left) and m - floor(m/2) (right); two steps make one
+// quadtree level (x-halves, then y-halves), so the node index at depth 2l is the box index of
+// level l.
+__device__ __forceinline__ int64_t descend_pos(int64_t n, int depth, int64_t pos, int64_t& o,
+                                               int64_t& m)
+{
+    int64_t j = 0;
+    o = 0;
+    m = n;
+    for (int d = 0; d < depth; d++) {
+        int64_t h = m >> 1;
+        if (pos < o + h) {
+            m = h;
+            j = 2 * j;
+        } else {
+            o += h;
+            m -= h;
+            j = 2 * j + 1;
+        }
+    }
+    return j;
+}
+
+// Offset and size of node j at `depth` (follow the bits of j from the most significant).
+__device__ __forceinline__ void descend_node(int64_t n, int depth, int64_t j, int64_t& o, int64_t& m)
+{
+    o = 0;
+    m = n;
+    for (int d = depth - 1; d >= 0; d--) {
+        int64_t h = m >> 1;
+        if ((j >> d) & 1) {
+            o += h;
+            m -= h;
+        } else {
+            m = h;
+        }
+    }
+}
+
+}  // namespace fmm
+
+// ---------------------------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------------------------
+struct fmm_tree_s {
+    int dev = 0;
+    int64_t n = 0;
+    int L = 0;
+    int64_t nbox = 0, nleaf = 0;
+    int64_t ntiles = 0;  // tiles of the sort / partition kernels
+
+    // products of the build (device)
+    double* rects = nullptr;     // [nbox][4] (x0, x1, y0, y1)
+    double* centers = nullptr;   // [nbox][2]
+    double* radii = nullptr;     // [nbox]
+    float* cen_hi = nullptr;     // [nbox][2] float part of the centre
+    float* cen_lo = nullptr;     // [nbox][2] float remainder (centre - hi)
+    int32_t* perm = nullptr;     // [n] canonical order -> input index
+    int32_t* leaf_begin = nullptr;  // [nleaf + 1]
+    int32_t* leaf_of = nullptr;  // [n] leaf of each input index
+    double* xs = nullptr;        // [n] x in canonical order
+    double* ys = nullptr;        // [n]
+    float* dxf = nullptr;        // [n] x - leaf centre, binary32, canonical order
+    float* dyf = nullptr;        // [n]
+
+    // build scratch (device)
+    uint64_t* keys = nullptr;    // [4][n] ping-pong keys for the x and y sorts
+    int32_t* vals = nullptr;     // [4][n] ping-pong values
+    uint32_t* rs_counts = nullptr;  // [2][256][ntiles]
+    uint32_t* rs_totals = nullptr;  // [2][256]
+    uint32_t* tilecnt = nullptr;    // [ntiles]
+    uint8_t* hflag = nullptr;       // [2][n] per input index: x-half / y-half bit
+    uint64_t* bbox_keys = nullptr;  // [4] ordered keys of xmin, xmax, ymin, ymax
+    int32_t* ones_before = nullptr;  // concatenated per depth 0 .. 2L-1: [2^depth]
+    std::vector<int64_t> ob_off;     // host: offset of each depth's table
+    int32_t* status = nullptr;       // device status word
+
+    // expansion workspace (allocated by the first evaluate that needs it; PS = padded P)
+    int ws_ps64 = 0, ws_ps32 = 0;
+    void* Me = nullptr;   // binary64 multipoles [nbox][PS] (double2: re, im)
+    void* Le = nullptr;   // binary64 locals     [nbox][PS]
+    void* Mf = nullptr;   // binary32 multipoles [nbox][PS] (float2)
+    void* Lf = nullptr;   // binary32 locals     [nbox][PS]
+    double* qs = nullptr;  // [n] strengths in canonical order
+    float* qf = nullptr;   // [n]
+    bool built = false;
+};
+
+struct fmm_lists_s {
+    fmm_tree tree = nullptr;
+    int64_t wcap = 0, scap = 0;
+    int32_t* woff = nullptr;  // [nbox + 1]
+    int32_t* soff = nullptr;  // [nbox + 1]
+    int32_t* widx = nullptr;  // [wcap]
+    int32_t* sidx = nullptr;  // [scap]
+    int32_t* wcnt = nullptr;  // [max level size] per-box counts of the level being built
+    int32_t* scnt = nullptr;
+    uint32_t* scan_tmp = nullptr;
+    int32_t* status = nullptr;
+    double theta = 0.0;
+    bool built = false;
+};
+
+namespace fmm {
+
+// tree.cu
+int tree_alloc(fmm_tree t);
+int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s);
+
+// lists.cu
+int lists_build(fmm_tree t, fmm_lists l, double theta, cudaStream_t s);
+
+// expand.cu
+int evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,
+             cudaStream_t s);
+int direct(const double* x, const double* y, const double* q, int64_t n, const int64_t* tgt,
+           int64_t m, double* phi, cudaStream_t s);
+
+// scan.cu: exclusive scan of int32 counts with a base value read from device memory:
+// out[i] = base[0] + sum_{j < i} in[j] for i = 0..m (out has m + 1 entries; out may alias
+// nothing).  tmp needs scan_tmp_words(m) words.
+int64_t scan_tmp_words(int64_t m);
+int scan_with_base(const int32_t* in, int64_t m, const int32_t* base, int32_t* out, uint32_t* tmp,
+                   cudaStream_t s);
+
+}  // namespace fmm

@@ -1,0 +1,316 @@
+"""Thin ctypes binding of libfmm_gb300.so (C ABI in include/fmm.h).
+
+Every function has the name of the C entry point it wraps and only marshals arguments: torch
+CUDA tensors become device pointers, the current torch stream becomes the cudaStream_t, and a
+negative status becomes :class:`FMMError`.  All arithmetic runs in the library's kernels; if the
+library is missing this module raises instead of computing anything on the CPU.
+
+:class:`FMM` bundles a tree, its lists and the evaluation for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "fmm.h")
+
+FMM_OK = 0
+FMM_ERR_ARG = -1
+FMM_ERR_NONFINITE = -2
+FMM_ERR_LEVELS = -3
+FMM_ERR_OOM = -4
+FMM_ERR_CUDA = -5
+FMM_ERR_CAPACITY = -6
+FMM_ERR_TIMEOUT = -7
+FMM_ERR_STATE = -8
+
+FMM_MODE_FP64 = 0
+FMM_MODE_MIXED = 1
+
+
+class FMMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class fmm_params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("mode", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load (once) and return the ctypes handle of libfmm_gb300.so."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_1006_2269_gb300.build`"
+                               " (there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        sig = {
+            "fmm_tree_create": (i32, [i64, i32, ctypes.POINTER(vp)]),
+            "fmm_build_tree": (i32, [vp, vp, vp, vp]),
+            "fmm_tree_export": (i32, [vp, vp, vp, vp, vp]),
+            "fmm_tree_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)]),
+            "fmm_tree_destroy": (None, [vp]),
+            "fmm_lists_create": (i32, [vp, i64, i64, ctypes.POINTER(vp)]),
+            "fmm_interaction_lists": (i32, [vp, vp, dbl, vp]),
+            "fmm_lists_sync": (i32, [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+            "fmm_lists_export": (i32, [vp, vp, vp, vp, vp, vp]),
+            "fmm_lists_destroy": (None, [vp]),
+            "fmm_evaluate": (i32, [vp, vp, vp, ctypes.POINTER(fmm_params), vp, vp]),
+            "fmm_direct": (i32, [vp, vp, vp, i64, vp, i64, vp, vp]),
+            "fmm_sync_status": (i32, [vp, vp, vp]),
+            "fmm_profile_enable": (i32, [i32]),
+            "fmm_profile_read": (i32, [vp, vp, i32]),
+            "fmm_launch_count": (i64, []),
+            "fmm_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def fmm_last_error() -> str:
+    return load_library().fmm_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != FMM_OK:
+        raise FMMError(rc, fmm_last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t: torch.Tensor | None, dtype, n=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise FMMError(FMM_ERR_ARG, f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise FMMError(FMM_ERR_ARG, f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise FMMError(FMM_ERR_ARG, f"{name} must be contiguous")
+    if n is not None and t.numel() < n:
+        raise FMMError(FMM_ERR_ARG, f"{name} has {t.numel()} elements, needs {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---- entry points, same names as the C ABI ----------------------------------------------------
+
+def fmm_tree_create(n: int, levels: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().fmm_tree_create(int(n), int(levels), ctypes.byref(h)))
+    return h
+
+
+def fmm_build_tree(tree, x: torch.Tensor, y: torch.Tensor, stream=None):
+    n = fmm_tree_info(tree)[0]
+    _check(load_library().fmm_build_tree(tree, _dev(x, torch.float64, n, "x"),
+                                         _dev(y, torch.float64, n, "y"), _stream(stream)))
+
+
+def fmm_tree_export(tree, perm=None, rects=None, leaf_begin=None, stream=None):
+    _check(load_library().fmm_tree_export(tree, _dev(perm, torch.int32, None, "perm"),
+                                          _dev(rects, torch.float64, None, "rects"),
+                                          _dev(leaf_begin, torch.int32, None, "leaf_begin"),
+                                          _stream(stream)))
+
+
+def fmm_tree_info(tree):
+    n, L, nb = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+    _check(load_library().fmm_tree_info(tree, ctypes.byref(n), ctypes.byref(L), ctypes.byref(nb)))
+    return n.value, L.value, nb.value
+
+
+def fmm_tree_destroy(tree):
+    if tree:
+        load_library().fmm_tree_destroy(tree)
+
+
+def fmm_lists_create(tree, weak_capacity: int = 0, strong_capacity: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().fmm_lists_create(tree, int(weak_capacity), int(strong_capacity), ctypes.byref(h)))
+    return h
+
+
+def fmm_interaction_lists(tree, lists, theta: float, stream=None):
+    _check(load_library().fmm_interaction_lists(tree, lists, float(theta), _stream(stream)))
+
+
+def fmm_lists_sync(lists, stream=None):
+    w, s = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().fmm_lists_sync(lists, _stream(stream), ctypes.byref(w), ctypes.byref(s)))
+    return w.value, s.value
+
+
+def fmm_lists_export(lists, woff, widx, soff, sidx, stream=None):
+    _check(load_library().fmm_lists_export(lists, _dev(woff, torch.int32, None, "woff"),
+                                           _dev(widx, torch.int32, None, "widx"),
+                                           _dev(soff, torch.int32, None, "soff"),
+                                           _dev(sidx, torch.int32, None, "sidx"), _stream(stream)))
+
+
+def fmm_lists_destroy(lists):
+    if lists:
+        load_library().fmm_lists_destroy(lists)
+
+
+def fmm_evaluate(tree, lists, q: torch.Tensor, p: int, mode: int, phi: torch.Tensor, tol: float = 1e-6,
+                 stream=None):
+    n = fmm_tree_info(tree)[0]
+    prm = fmm_params(int(p), int(mode), float(tol))
+    _check(load_library().fmm_evaluate(tree, lists, _dev(q, torch.float64, n, "q"), ctypes.byref(prm),
+                                       _dev(phi, torch.float64, n, "phi"), _stream(stream)))
+
+
+def fmm_direct(x, y, q, targets, phi, stream=None):
+    n = x.numel()
+    m = targets.numel()
+    _check(load_library().fmm_direct(_dev(x, torch.float64, n, "x"), _dev(y, torch.float64, n, "y"),
+                                     _dev(q, torch.float64, n, "q"), n,
+                                     _dev(targets, torch.int64, m, "targets"), m,
+                                     _dev(phi, torch.float64, m, "phi"), _stream(stream)))
+
+
+def fmm_sync_status(tree, lists=None, stream=None):
+    _check(load_library().fmm_sync_status(tree, lists, _stream(stream)))
+
+
+STAGES = ("tree_sort", "tree_split", "tree_finish", "lists", "gather", "p2m", "m2m", "m2l", "l2l",
+          "leaf")
+
+
+def fmm_profile_enable(on: bool = True):
+    _check(load_library().fmm_profile_enable(1 if on else 0))
+
+
+def fmm_profile_read():
+    """Per-stage (milliseconds, count) recorded since the last read."""
+    import numpy as np
+    ms = np.zeros(len(STAGES), np.float64)
+    cnt = np.zeros(len(STAGES), np.int64)
+    rc = load_library().fmm_profile_read(ms.ctypes.data_as(ctypes.c_void_p),
+                                         cnt.ctypes.data_as(ctypes.c_void_p), len(STAGES))
+    if rc < 0:
+        _check(rc)
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(STAGES)}
+
+
+def fmm_launch_count() -> int:
+    return int(load_library().fmm_launch_count())
+
+
+# ---- convenience ---------------------------------------------------------------------------
+
+class FMM:
+    """One point set: its tree, its interaction lists and any number of evaluations.
+
+    >>> f = FMM(x, y, levels=8, theta=0.5)          # x, y: CUDA float64
+    >>> phi = f.evaluate(q, p=20, mode="mixed")      # potentials in input order
+    """
+
+    def __init__(self, x: torch.Tensor, y: torch.Tensor, levels: int, theta: float = 0.5,
+                 weak_capacity: int = 0, strong_capacity: int = 0, check: bool = True):
+        self.n = x.numel()
+        self.levels = levels
+        self.theta = theta
+        self.device = x.device
+        self.tree = fmm_tree_create(self.n, levels)
+        self.lists = None
+        try:
+            self.lists = fmm_lists_create(self.tree, weak_capacity, strong_capacity)
+            self.rebuild(x, y, check=check)
+        except Exception:
+            self.close()
+            raise
+
+    def rebuild(self, x, y, theta=None, check: bool = True):
+        """Rebuild tree and lists for new coordinates (same n and levels); grows the list
+        capacity and retries when the lists overflow."""
+        if theta is not None:
+            self.theta = theta
+        fmm_build_tree(self.tree, x, y)
+        fmm_interaction_lists(self.tree, self.lists, self.theta)
+        if check:
+            try:
+                self.counts = fmm_lists_sync(self.lists)
+            except FMMError as e:
+                if e.code != FMM_ERR_CAPACITY:
+                    raise
+                w, s = self._needed()
+                fmm_lists_destroy(self.lists)
+                self.lists = None
+                self.lists = fmm_lists_create(self.tree, 2 * w + 1024, 2 * s + 1024)
+                return self.rebuild(x, y, check=check)
+            fmm_sync_status(self.tree, self.lists)
+
+    def _needed(self):
+        nbox = fmm_tree_info(self.tree)[2]
+        woff = torch.empty(nbox + 1, dtype=torch.int32, device=self.device)
+        soff = torch.empty(nbox + 1, dtype=torch.int32, device=self.device)
+        fmm_lists_export(self.lists, woff, None, soff, None)
+        torch.cuda.synchronize(self.device)
+        return int(woff[-1]), int(soff[-1])
+
+    def evaluate(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6, out=None,
+                 check: bool = True):
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        phi = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
+        fmm_evaluate(self.tree, self.lists, q, p, m, phi, tol)
+        if check:
+            fmm_sync_status(self.tree, self.lists)
+        return phi
+
+    def export_tree(self):
+        n, L, nbox = fmm_tree_info(self.tree)
+        perm = torch.empty(n, dtype=torch.int32, device=self.device)
+        rects = torch.empty((nbox, 4), dtype=torch.float64, device=self.device)
+        lb = torch.empty(4 ** L + 1, dtype=torch.int32, device=self.device)
+        fmm_tree_export(self.tree, perm, rects, lb)
+        return perm, rects, lb
+
+    def export_lists(self):
+        nbox = fmm_tree_info(self.tree)[2]
+        w, s = fmm_lists_sync(self.lists)
+        woff = torch.empty(nbox + 1, dtype=torch.int32, device=self.device)
+        soff = torch.empty(nbox + 1, dtype=torch.int32, device=self.device)
+        widx = torch.empty(max(w, 1), dtype=torch.int32, device=self.device)
+        sidx = torch.empty(max(s, 1), dtype=torch.int32, device=self.device)
+        fmm_lists_export(self.lists, woff, widx, soff, sidx)
+        torch.cuda.synchronize(self.device)
+        return woff, widx[:w], soff, sidx[:s]
+
+    def close(self):
+        if self.lists is not None:
+            fmm_lists_destroy(self.lists)
+            self.lists = None
+        if self.tree is not None:
+            fmm_tree_destroy(self.tree)
+            self.tree = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

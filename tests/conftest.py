@@ -18,3 +18,20 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def fmmlib():
+    """The CUDA library (built in-tree if stale) and its binding."""
+    from paper_1006_2269_gb300 import build, fmm
+    build.build()
+    fmm.load_library()
+    return fmm
+
+
+@pytest.fixture(scope="session")
+def cuda(fmmlib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")

@@ -1,0 +1,221 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tree permutation, box rectangles, leaf offsets and interaction lists must match bit for bit;
+binary64 potentials within 1e-12 (max-norm relative to max |phi|); the mixed-precision path
+within its declared tolerance 1e-6 of the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1006_2269_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+TOL_MIXED = 1e-6
+
+
+def _t(a, dev):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), device=dev)
+
+
+def relerr(a, ref):
+    return float(np.max(np.abs(a - ref)) / np.max(np.abs(ref)))
+
+
+def _dupes(n=4000, seed=8):
+    c = W.uniform(n, seed)
+    return W.Cloud(np.round(c.x * 16) / 16, np.round(c.y * 16) / 16, c.q, "dupes")
+
+
+def _collinear(n=3000, seed=9):
+    c = W.uniform(n, seed)
+    return W.Cloud(c.x, np.full(n, 0.25), c.q, "collinear")
+
+
+CASES = [
+    ("tiny_L0", lambda: W.uniform(37, 1), 0),
+    ("L1", lambda: W.uniform(101, 2), 1),
+    ("ragged", lambda: W.uniform(4 ** 3 + 13, 3), 3),
+    ("exact_4L", lambda: W.uniform(4 ** 5, 4), 5),
+    ("plain_fp64", lambda: W.plain_fp64_cloud(), 4),
+    ("clusters", lambda: W.clusters(30011, 5), 5),
+    ("circle", lambda: W.circle(20000, 6), 5),
+    ("normal", lambda: W.normal(12345, 7), 4),
+    ("rings", lambda: W.rings_plummer(40000, 8), 6),
+    ("dupes", _dupes, 3),
+    ("collinear", _collinear, 4),
+    ("multi_tile", lambda: W.uniform(3 * 4096 + 77, 10), 3),
+]
+
+
+@pytest.fixture(scope="module")
+def built(fmmlib, cuda, orc):
+    """GPU tree + lists and oracle tree + lists for every case (theta = 1/2)."""
+    out = {}
+    for name, make, L in CASES:
+        c = make()
+        f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), L, 0.5)
+        out[name] = (c, L, f)
+    return out
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_tree_bit_exact(built, orc, name):
+    c, L, f = built[name]
+    perm, rects, lb = f.export_tree()
+    operm, orects, olb = orc.tree(c.x, c.y, L)
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    assert np.array_equal(lb.cpu().numpy().astype(np.int64), olb)
+    g = rects.cpu().numpy()
+    assert np.array_equal(g.view(np.uint64), orects.view(np.uint64)) or np.array_equal(g, orects)
+
+
+@pytest.mark.parametrize("theta", [0.25, 0.5, math.sqrt(0.5)])
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_lists_bit_exact(built, orc, fmmlib, name, theta):
+    c, L, f = built[name]
+    if theta != 0.5:
+        f.rebuild(_t(c.x, f.device), _t(c.y, f.device), theta=theta)
+    try:
+        woff, widx, soff, sidx = (a.cpu().numpy().astype(np.int64) for a in f.export_lists())
+        _, orects, _ = orc.tree(c.x, c.y, L)
+        owoff, owidx, osoff, osidx = orc.lists(orects, L, theta)
+        assert np.array_equal(woff, owoff)
+        assert np.array_equal(soff, osoff)
+        assert np.array_equal(widx, owidx)
+        assert np.array_equal(sidx, osidx)
+    finally:
+        if theta != 0.5:
+            f.rebuild(_t(c.x, f.device), _t(c.y, f.device), theta=0.5)
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("p", [5, 17])
+def test_fp64_potentials(built, orc, cuda, name, p):
+    c, L, f = built[name]
+    phi = f.evaluate(_t(c.q, cuda), p, "fp64").cpu().numpy()
+    ref = orc.fmm(c.x, c.y, c.q, L, p, 0.5)
+    assert relerr(phi, ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("p", [16, 17, 20, 30, 9])
+def test_mixed_potentials(built, orc, cuda, name, p):
+    c, L, f = built[name]
+    phi = f.evaluate(_t(c.q, cuda), p, "mixed").cpu().numpy()
+    ref = orc.fmm(c.x, c.y, c.q, L, p, 0.5)
+    assert relerr(phi, ref) <= TOL_MIXED
+
+
+def test_plain_fp64_workload_vs_direct(built, orc, cuda):
+    # uniform N = 10240, L = 4, theta = 1/2, p = 17, checked against the direct sum on all targets
+    c, L, f = built["plain_fp64"]
+    phi = f.evaluate(_t(c.q, cuda), 17, "fp64").cpu().numpy()
+    ref = orc.direct(c.x, c.y, c.q, nthreads=0)
+    e = relerr(phi, ref)
+    assert e <= 1e-8  # theta^(p+1)-type truncation error, far below the paper's 1e-6 at p = 20
+    assert abs(e - relerr(orc.fmm(c.x, c.y, c.q, L, 17, 0.5), ref)) <= 1e-12
+
+
+def test_direct_kernel(fmmlib, orc, cuda):
+    import torch
+    c = W.clusters(20000, 11)
+    tg = W.sample_targets(c.x.shape[0], 300, 12)
+    phi = torch.empty(tg.shape[0], dtype=torch.float64, device=cuda)
+    fmmlib.fmm_direct(_t(c.x, cuda), _t(c.y, cuda), _t(c.q, cuda), _t(tg, cuda), phi)
+    ref = orc.direct(c.x, c.y, c.q, tg)
+    assert relerr(phi.cpu().numpy(), ref) <= 1e-13
+
+
+def test_reuse_and_repeat(built, cuda, orc):
+    # one tree serves many strength vectors; repeated calls give identical results
+    c, L, f = built["clusters"]
+    g = np.random.default_rng(3)
+    for _ in range(2):
+        q = g.standard_normal(c.x.shape[0])
+        a = f.evaluate(_t(q, cuda), 12, "fp64").cpu().numpy()
+        b = f.evaluate(_t(q, cuda), 12, "fp64").cpu().numpy()
+        assert np.array_equal(a, b)
+        assert relerr(a, orc.fmm(c.x, c.y, q, L, 12, 0.5)) <= TOL_FP64
+
+
+# ---- the large mixed-precision workload at full size, in the configuration the benchmark times --
+
+@pytest.fixture(scope="module")
+def big(fmmlib, cuda):
+    c = W.mixed_1m_cloud()
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), W.MIXED_1M.levels, W.MIXED_1M.theta)
+    return c, f
+
+
+def test_full_size_tree_and_lists_bit_exact(big, orc):
+    c, f = big
+    L = W.MIXED_1M.levels
+    perm, rects, lb = f.export_tree()
+    operm, orects, olb = orc.tree(c.x, c.y, L)
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    assert np.array_equal(rects.cpu().numpy(), orects)
+    assert np.array_equal(lb.cpu().numpy().astype(np.int64), olb)
+    woff, widx, soff, sidx = (a.cpu().numpy().astype(np.int64) for a in f.export_lists())
+    owoff, owidx, osoff, osidx = orc.lists(orects, L, W.MIXED_1M.theta)
+    assert np.array_equal(woff, owoff) and np.array_equal(widx, owidx)
+    assert np.array_equal(soff, osoff) and np.array_equal(sidx, osidx)
+
+
+def test_full_size_mixed_error_vs_direct(big, orc, cuda):
+    c, f = big
+    w = W.MIXED_1M
+    tg = W.sample_targets(w.n, w.n_check, 10061 + 100)
+    ref = orc.direct(c.x, c.y, c.q, tg, nthreads=0)
+    mixed = f.evaluate(_t(c.q, cuda), w.p, "mixed").cpu().numpy()[tg]
+    fp64 = f.evaluate(_t(c.q, cuda), w.p, "fp64").cpu().numpy()[tg]
+    assert relerr(mixed, ref) <= TOL_MIXED
+    assert relerr(fp64, ref) <= 1e-8
+
+
+# ---- error handling ---------------------------------------------------------------------------
+
+def test_nonfinite_input_is_reported(fmmlib, cuda):
+    c = W.uniform(1000, 13)
+    x = c.x.copy()
+    x[17] = np.nan
+    with pytest.raises(fmmlib.FMMError) as e:
+        fmmlib.FMM(_t(x, cuda), _t(c.y, cuda), 2, 0.5)
+    assert e.value.code == fmmlib.FMM_ERR_NONFINITE
+
+
+def test_capacity_overflow_is_reported_and_recovered(fmmlib, cuda, orc):
+    c = W.uniform(5000, 14)
+    x, y = _t(c.x, cuda), _t(c.y, cuda)
+    t = fmmlib.fmm_tree_create(c.x.shape[0], 4)
+    lists = fmmlib.fmm_lists_create(t, 10, 10)
+    try:
+        fmmlib.fmm_build_tree(t, x, y)
+        fmmlib.fmm_interaction_lists(t, lists, 0.5)
+        with pytest.raises(fmmlib.FMMError) as e:
+            fmmlib.fmm_lists_sync(lists)
+        assert e.value.code == fmmlib.FMM_ERR_CAPACITY
+    finally:
+        fmmlib.fmm_lists_destroy(lists)
+        fmmlib.fmm_tree_destroy(t)
+    # the convenience wrapper grows the capacity and retries
+    f = fmmlib.FMM(x, y, 4, 0.5, weak_capacity=10, strong_capacity=10)
+    phi = f.evaluate(_t(c.q, cuda), 8, "fp64").cpu().numpy()
+    assert relerr(phi, orc.fmm(c.x, c.y, c.q, 4, 8, 0.5)) <= TOL_FP64
+
+
+def test_bad_arguments(fmmlib, cuda):
+    c = W.uniform(300, 15)
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), 2, 0.5)
+    with pytest.raises(fmmlib.FMMError) as e:
+        fmmlib.fmm_interaction_lists(f.tree, f.lists, 1.0)
+    assert e.value.code == fmmlib.FMM_ERR_ARG
+    with pytest.raises(fmmlib.FMMError) as e:
+        f.evaluate(_t(c.q, cuda), 41, "fp64")
+    assert e.value.code == fmmlib.FMM_ERR_ARG
+    with pytest.raises(fmmlib.FMMError):
+        f.evaluate(_t(c.q.astype(np.float32), cuda), 5, "fp64")
