@@ -92,10 +92,10 @@ struct DeviceGuard {
 void free_tree(fmm_tree t)
 {
     if (!t) return;
-    void* ptrs[] = {t->rects, t->centers, t->radii, t->cen_hi, t->cen_lo, t->perm, t->leaf_begin,
+    void* ptrs[] = {t->rects, t->centers, t->radii, t->rad32, t->cen_hi, t->cen_lo, t->perm, t->leaf_begin,
                     t->leaf_of, t->xs, t->ys, t->dxf, t->dyf, t->keys, t->vals, t->rs_counts,
                     t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->status,
-                    t->Me, t->Le, t->Mf, t->Lf, t->qs, t->qf};
+                    t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->cleaf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -104,7 +104,7 @@ void free_tree(fmm_tree t)
 void free_lists(fmm_lists l)
 {
     if (!l) return;
-    void* ptrs[] = {l->woff, l->soff, l->widx, l->sidx, l->wcnt, l->scnt, l->scan_tmp, l->status};
+    void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete l;
@@ -237,14 +237,14 @@ int fmm_lists_create(fmm_tree t, int64_t weak_capacity, int64_t strong_capacity,
     l->tree = t;
     l->wcap = weak_capacity;
     l->scap = strong_capacity;
-    const int64_t maxlev = level_size(t->L);
     bool ok = cudaMalloc((void**)&l->woff, 4 * (t->nbox + 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->soff, 4 * (t->nbox + 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->widx, 4 * std::max<int64_t>(l->wcap, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->wtgt, 4 * std::max<int64_t>(l->wcap, 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->sidx, 4 * std::max<int64_t>(l->scap, 1)) == cudaSuccess &&
-              cudaMalloc((void**)&l->wcnt, 4 * maxlev) == cudaSuccess &&
-              cudaMalloc((void**)&l->scnt, 4 * maxlev) == cudaSuccess &&
-              cudaMalloc((void**)&l->scan_tmp, 4 * scan_tmp_words(maxlev)) == cudaSuccess &&
+              cudaMalloc((void**)&l->stgt, 4 * std::max<int64_t>(l->scap, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->flags, lists_flag_bytes(l->scap)) == cudaSuccess &&
+              cudaMalloc((void**)&l->tilecnt, 4 * lists_tile_words(l->scap)) == cudaSuccess &&
               cudaMalloc((void**)&l->status, 4) == cudaSuccess;
     if (!ok) {
         free_lists(l);

@@ -101,11 +101,13 @@ struct fmm_tree_s {
     double* rects = nullptr;     // [nbox][4] (x0, x1, y0, y1)
     double* centers = nullptr;   // [nbox][2]
     double* radii = nullptr;     // [nbox]
+    float* rad32 = nullptr;      // [nbox] radii rounded to binary32
     float* cen_hi = nullptr;     // [nbox][2] float part of the centre
     float* cen_lo = nullptr;     // [nbox][2] float remainder (centre - hi)
     int32_t* perm = nullptr;     // [n] canonical order -> input index
     int32_t* leaf_begin = nullptr;  // [nleaf + 1]
     int32_t* leaf_of = nullptr;  // [n] leaf of each input index
+    int32_t* cleaf = nullptr;    // [n] leaf of each canonical position
     double* xs = nullptr;        // [n] x in canonical order
     double* ys = nullptr;        // [n]
     float* dxf = nullptr;        // [n] x - leaf centre, binary32, canonical order
@@ -129,8 +131,9 @@ struct fmm_tree_s {
     void* Le = nullptr;   // binary64 locals     [nbox][PS]
     void* Mf = nullptr;   // binary32 multipoles [nbox][PS] (float2)
     void* Lf = nullptr;   // binary32 locals     [nbox][PS]
-    double* qs = nullptr;  // [n] strengths in canonical order
-    float* qf = nullptr;   // [n]
+    void* pk64 = nullptr;   // [n] double4 (x, y, q, 0) in canonical order (binary64 path)
+    void* pk32 = nullptr;   // [n] float4 (x - c_leaf, y - c_leaf, q, 0) (binary32 path)
+    double* acc = nullptr;  // [n] potential accumulator in canonical order
     bool built = false;
 };
 
@@ -139,11 +142,12 @@ struct fmm_lists_s {
     int64_t wcap = 0, scap = 0;
     int32_t* woff = nullptr;  // [nbox + 1]
     int32_t* soff = nullptr;  // [nbox + 1]
-    int32_t* widx = nullptr;  // [wcap]
+    int32_t* widx = nullptr;  // [wcap] within-level index of the source box
+    int32_t* wtgt = nullptr;  // [wcap] global id of the target box of each weak entry
     int32_t* sidx = nullptr;  // [scap]
-    int32_t* wcnt = nullptr;  // [max level size] per-box counts of the level being built
-    int32_t* scnt = nullptr;
-    uint32_t* scan_tmp = nullptr;
+    int32_t* stgt = nullptr;  // [scap]
+    uint8_t* flags = nullptr;     // [16 * scap] weak flag per candidate of the level being built
+    uint32_t* tilecnt = nullptr;  // per-tile weak counts of the level being built
     int32_t* status = nullptr;
     double theta = 0.0;
     bool built = false;
@@ -157,6 +161,8 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s);
 
 // lists.cu
 int lists_build(fmm_tree t, fmm_lists l, double theta, cudaStream_t s);
+int64_t lists_flag_bytes(int64_t scap);
+int64_t lists_tile_words(int64_t scap);
 
 // expand.cu
 int evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,

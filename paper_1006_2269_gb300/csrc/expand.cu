@@ -2,19 +2,26 @@
 //
 // Storage is radius-scaled: a box of centre c and radius rho keeps a~_k = a_k / rho^k (multipole)
 // and b~_l = b_l * rho^l (local), and points enter through xi = (z - c) / rho (taken as 0 when
-// rho = 0).  In scaled form every shift is a combination of quantities of modulus <= 1:
+// rho = 0).  In scaled form every shift combines quantities of modulus <= 1:
 //   P2M  a~_0 = sum q_j,  a~_k = -sum q_j xi_j^k / k
 //   M2M  b~_l = -a_0 w^l / l + sum_{k=1..l} a~_k C(l-1,k-1) s^k w^(l-k),
 //        w = (c_child - c_parent)/rho_p, s = rho_c/rho_p
-//   M2L  with z0 = c_src - c_tgt, u = -rho_s/z0, v = rho_t/z0 (|u| + |v| <= theta):
+//   M2L  with z0 = c_src - c_tgt, u = -rho_s/z0, v = rho_t/z0 (|u| + |v| <= theta < 1):
 //        b~_0 = a_0 log|z0| + sum_k a~_k u^k,
 //        b~_l = v^l [ -a_0/l + sum_k C(l+k-1,k-1) a~_k u^k ]
 //        evaluated as (2v)^l * sum_k M'[l][k] * (a~_k (2u)^k) with the fixed matrix
-//        M'[l][k] = C(l+k-1,k-1) / 2^(l+k) (k >= 1), M'[l][0] = -1/(l 2^l), whose entries are <= 1/2
-//        (the "diagonal scaling x constant Pascal matrix x diagonal scaling" form of Section 4)
+//        M'[l][k] = C(l+k-1,k-1) / 2^(l+k) (k >= 1), M'[l][0] = -1/(l 2^l) (entries <= 1/2):
+//        a pre-scaling, one constant Pascal-type matrix and a post-scaling (Section 4)
 //   L2L  b~'_l = s^l sum_{k>=l} b~_k C(k,l) w^(k-l)
 //   L2P  phi += Re sum_l b~_l xi^l
 // Only the real part of the potential is needed, so the imaginary part of log(-z0) is dropped.
+//
+// Work decomposition.  Interaction lists of balanced trees over clustered points range from a
+// few entries to thousands per box, so M2L and the near field run over the flat pair arrays of
+// the lists: every warp takes a fixed chunk of consecutive pairs (sorted by target), each lane a
+// contiguous sub-chunk; partial sums of equal targets are combined by a warp-segmented reduction
+// and added to the target with atomics.  The near-field sums of the binary32 path are flushed in
+// binary64, which keeps the accumulation error at the level of a few hundred binary32 terms.
 #include <math.h>
 
 #include <algorithm>
@@ -31,6 +38,9 @@ __constant__ float c_mf[PMAXC][PMAXC];      // M'[l][k] rounded to binary32
 __constant__ double c_binom[PMAXC][PMAXC];  // C(n, k), n < PMAXC
 
 namespace {
+
+constexpr int M2L_CH = 8;   // consecutive weak pairs per lane
+constexpr int P2P_CH = 16;  // consecutive leaf pairs per warp
 
 template <typename T>
 struct alignas(2 * sizeof(T)) cx {
@@ -72,11 +82,10 @@ __device__ __forceinline__ T ipow(T x, int e)
     return r;
 }
 
+// Level of a global box id: 4^l <= 3g + 1 < 4^(l+1).
 __device__ __forceinline__ int level_of(int64_t g)
 {
-    int l = 0;
-    while (level_base(l + 1) <= g) l++;
-    return l;
+    return (63 - __clzll((unsigned long long)(3 * g + 1))) >> 1;
 }
 
 // z0 = c_src - c_tgt: in binary64 directly, in binary32 from the float-float centres so that
@@ -106,26 +115,47 @@ struct Geo<float> {
 __device__ __forceinline__ double log_d(double x) { return log(x); }
 __device__ __forceinline__ float log_d(float x) { return logf(x); }
 
-// ---- strengths in canonical order ----
 template <typename T>
-__global__ void k_gather_q(const int32_t* __restrict__ perm, const double* __restrict__ q, int64_t n,
-                           T* __restrict__ qs, int32_t* status)
+struct Pk;  // packed point
+template <>
+struct alignas(32) Pk<double> {
+    double x, y, q, pad;
+};
+template <>
+struct alignas(16) Pk<float> {
+    float x, y, q, pad;
+};
+
+// ---- strengths into canonical order, packed with the coordinates ----
+template <typename T>
+__global__ void k_pack(const int32_t* __restrict__ perm, const double* __restrict__ q,
+                       const double* __restrict__ xs, const double* __restrict__ ys,
+                       const float* __restrict__ dxf, const float* __restrict__ dyf, int64_t n,
+                       Pk<T>* __restrict__ pk, int32_t* status)
 {
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double v = q[perm[i]];
         bad |= !isfinite(v);
-        qs[i] = (T)v;
+        Pk<T> p;
+        if (sizeof(T) == 8) {
+            p.x = (T)xs[i];
+            p.y = (T)ys[i];
+        } else {
+            p.x = (T)dxf[i];
+            p.y = (T)dyf[i];
+        }
+        p.q = (T)v;
+        p.pad = 0;
+        pk[i] = p;
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
 }
 
 // ---- P2M: one warp per leaf, one lane per point; column sums through shared memory ----
 template <typename T>
-__global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, const T* __restrict__ qs,
-                      const double* __restrict__ xs, const double* __restrict__ ys,
-                      const float* __restrict__ dxf, const float* __restrict__ dyf,
+__global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, const Pk<T>* __restrict__ pk,
                       const double* __restrict__ cen, const double* __restrict__ rad,
                       cx<T>* __restrict__ Me)
 {
@@ -142,15 +172,16 @@ __global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, cons
         const int32_t t = tb + lane;
         T xr = 0, xi = 0, qq = 0;
         if (t < t1) {
-            qq = qs[t];
+            const Pk<T> p = pk[t];
+            qq = p.q;
             if (rho > 0) {
                 if (sizeof(T) == 8) {
-                    xr = (T)((xs[t] - cen[2 * g]) / rho);
-                    xi = (T)((ys[t] - cen[2 * g + 1]) / rho);
+                    xr = (T)(((double)p.x - cen[2 * g]) / rho);
+                    xi = (T)(((double)p.y - cen[2 * g + 1]) / rho);
                 } else {
                     const T inv = (T)(1.0 / rho);
-                    xr = (T)dxf[t] * inv;
-                    xi = (T)dyf[t] * inv;
+                    xr = p.x * inv;
+                    xi = p.y * inv;
                 }
             }
         }
@@ -172,6 +203,14 @@ __global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, cons
         Me[g * PS + k] = k == 0 ? acc[s] : cscale(acc[s], (T)(-1.0 / k));
 }
 
+// Binomial table C(n, k), n, k < P, copied to shared memory by the whole block.
+template <typename T>
+__device__ __forceinline__ void load_binom(T* B, int P)
+{
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) B[i] = (T)c_binom[i / P][i % P];
+    __syncthreads();
+}
+
 // ---- M2M: one warp per parent, one lane per output coefficient ----
 template <typename T>
 __global__ void k_m2m(int l, int P, int PS, const double* __restrict__ cen,
@@ -179,9 +218,11 @@ __global__ void k_m2m(int l, int P, int PS, const double* __restrict__ cen,
 {
     extern __shared__ unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    T* B = (T*)smem;
+    cx<T>* D = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
+    load_binom(B, P);
     const int64_t b = (int64_t)blockIdx.x * wpb + w;
     if (b >= level_size(l)) return;
-    cx<T>* D = (cx<T>*)smem + (size_t)w * P;
     const int64_t g = level_base(l) + b;
     const double rp = rad[g];
     cx<T> acc[2] = {{0, 0}, {0, 0}};
@@ -201,7 +242,7 @@ __global__ void k_m2m(int l, int P, int PS, const double* __restrict__ cen,
                 h = D[0];
             } else {
                 h = cscale(D[0], (T)(-1.0 / o));
-                for (int j = 1; j <= o; j++) h = cfma(h, wv, cscale(D[j], (T)c_binom[o - 1][j - 1]));
+                for (int j = 1; j <= o; j++) h = cfma(h, wv, cscale(D[j], B[(o - 1) * P + (j - 1)]));
             }
             acc[si] = cadd(acc[si], h);
         }
@@ -210,108 +251,187 @@ __global__ void k_m2m(int l, int P, int PS, const double* __restrict__ cen,
     for (int o = lane, si = 0; o < P; o += 32, si++) Me[g * PS + o] = acc[si];
 }
 
-// ---- M2L, one thread per target box of levels 1..L (runtime P; operands in shared memory) ----
-template <typename T>
-__global__ void k_m2l_generic(int64_t g0, int64_t g1, int P, int PS, const int32_t* __restrict__ woff,
-                              const int32_t* __restrict__ widx, int64_t wcap, Geo<T> geo,
-                              const double* __restrict__ rad, const cx<T>* __restrict__ Me,
-                              cx<T>* __restrict__ Le)
+// ---- M2L over the flat weak-pair array of all levels ----
+// binary32, PI = compile-time bound on P (runtime P <= PI; coefficients beyond P are zero): the
+// scaled source coefficients and the partial sums live in registers, the constant matrix is read
+// from the constant bank by the unrolled contraction.
+template <typename T, int PI>
+__global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t* __restrict__ woff,
+                                                   const int32_t* __restrict__ widx,
+                                                   const int32_t* __restrict__ wtgt, int64_t wcap,
+                                                   int64_t nbox, Geo<T> geo, const double* __restrict__ rad,
+                                                   const cx<T>* __restrict__ Me, cx<T>* __restrict__ Le)
 {
-    extern __shared__ unsigned char smem[];
-    const int nt = blockDim.x, tid = threadIdx.x;
-    cx<T>* X = (cx<T>*)smem;            // X[k * nt + tid]
-    cx<T>* A = X + (size_t)P * nt;      // A[l * nt + tid]
-    const int64_t g = g0 + (int64_t)blockIdx.x * nt + tid;
-    if (g >= g1) return;
-    const int l = level_of(g);
-    const int64_t base = level_base(l);
-    for (int j = 0; j < P; j++) A[j * nt + tid] = {0, 0};
-    const T rt = (T)rad[g];
-    const int64_t e0 = min((int64_t)woff[g], wcap), e1 = min((int64_t)woff[g + 1], wcap);
-    for (int64_t e = e0; e < e1; e++) {
-        const int64_t sg = base + widx[e];
-        const cx<T> z0 = geo.diff(sg, g);
-        const T r2 = z0.re * z0.re + z0.im * z0.im;
-        const T ir2 = (T)1 / r2;
-        const cx<T> inv = {z0.re * ir2, -z0.im * ir2};
-        const T rs = (T)rad[sg];
-        const cx<T> u2 = cscale(inv, (T)(-2) * rs), v2 = cscale(inv, (T)2 * rt);
-        const T a0 = Me[sg * PS].re;
-        X[tid] = {a0, 0};
-        cx<T> up = u2;
-        for (int k = 1; k < P; k++) {
-            X[k * nt + tid] = cmul(Me[sg * PS + k], up);
-            up = cmul(up, u2);
-        }
-        cx<T> vp = {1, 0};
-        for (int o = 0; o < P; o++) {
-            cx<T> y = {0, 0};
-            for (int k = 0; k < P; k++) {
-                const T m = mtab<T>(o, k);
-                const cx<T> x = X[k * nt + tid];
-                y.re += m * x.re;
-                y.im += m * x.im;
+    const int lane = threadIdx.x & 31;
+    const int64_t e_begin = woff[1];
+    const int64_t e_end = min((int64_t)woff[nbox], wcap);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wb = e_begin + warp * 32 * M2L_CH; wb < e_end; wb += nwarps * 32 * M2L_CH) {
+        const int64_t e0 = wb + (int64_t)lane * M2L_CH;
+        const int64_t e1 = min(e0 + M2L_CH, e_end);
+        cx<T> acc[PI];
+#pragma unroll
+        for (int j = 0; j < PI; j++) acc[j] = {0, 0};
+        int64_t cur = -1;
+        for (int64_t e = e0; e < e1; e++) {
+            const int64_t g = wtgt[e];
+            if (g != cur) {
+                if (cur >= 0) {
+#pragma unroll
+                    for (int j = 0; j < PI; j++)
+                        if (j < P) {
+                            atomicAdd(&Le[cur * PS + j].re, acc[j].re);
+                            atomicAdd(&Le[cur * PS + j].im, acc[j].im);
+                        }
+                }
+#pragma unroll
+                for (int j = 0; j < PI; j++) acc[j] = {0, 0};
+                cur = g;
             }
-            if (o == 0) y.re += a0 * (T)0.5 * log_d(r2);
-            A[o * nt + tid] = cfma(vp, y, A[o * nt + tid]);
-            vp = cmul(vp, v2);
+            const int64_t sg = level_base(level_of(g)) + widx[e];
+            const cx<T> z0 = geo.diff(sg, g);
+            const T r2 = z0.re * z0.re + z0.im * z0.im;
+            const T ir2 = (T)1 / r2;
+            const cx<T> inv = {z0.re * ir2, -z0.im * ir2};
+            const cx<T> u2 = cscale(inv, (T)(-2.0 * rad[sg])), v2 = cscale(inv, (T)(2.0 * rad[g]));
+            const cx<T>* src = Me + sg * PS;
+            const T a0 = src[0].re;
+            cx<T> x[PI];
+            x[0] = {a0, 0};
+            cx<T> up = u2;
+#pragma unroll
+            for (int k = 1; k < PI; k++) {
+                cx<T> v = {0, 0};
+                if (k < P) v = cmul(src[k], up);
+                x[k] = v;
+                up = cmul(up, u2);
+            }
+            cx<T> vp = {1, 0};
+#pragma unroll
+            for (int o = 0; o < PI; o++) {
+                cx<T> y = {0, 0};
+#pragma unroll
+                for (int k = 0; k < PI; k++) {
+                    const T m = mtab<T>(o, k);
+                    const cx<T> xv = x[k];
+                    y.re += m * xv.re;
+                    y.im += m * xv.im;
+                }
+                if (o == 0) y.re += a0 * (T)0.5 * log_d(r2);
+                acc[o] = cfma(vp, y, acc[o]);
+                vp = cmul(vp, v2);
+            }
+        }
+        // warp-segmented reduction of the last partial sums (targets are non-decreasing across
+        // lanes; lanes without pairs carry -1 and sit at the end)
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t pkey = __shfl_down_sync(0xffffffffu, cur, off);
+            const bool take = (lane + off < 32) && pkey == cur;
+#pragma unroll
+            for (int j = 0; j < PI; j++) {
+                const T pr = __shfl_down_sync(0xffffffffu, acc[j].re, off);
+                const T pi = __shfl_down_sync(0xffffffffu, acc[j].im, off);
+                if (take) {
+                    acc[j].re += pr;
+                    acc[j].im += pi;
+                }
+            }
+        }
+        const int64_t prev = __shfl_up_sync(0xffffffffu, cur, 1);
+        if (cur >= 0 && (lane == 0 || prev != cur)) {
+#pragma unroll
+            for (int j = 0; j < PI; j++)
+                if (j < P) {
+                    atomicAdd(&Le[cur * PS + j].re, acc[j].re);
+                    atomicAdd(&Le[cur * PS + j].im, acc[j].im);
+                }
         }
     }
-    for (int o = 0; o < P; o++) Le[g * PS + o] = A[o * nt + tid];
 }
 
-// ---- M2L, binary32, compile-time P: the scaled source coefficients and the accumulators live
-// in registers and the constant matrix is read from the constant bank by the unrolled loop ----
-template <int P>
-__global__ void __launch_bounds__(128) k_m2l_f32(int64_t g0, int64_t g1, int PS,
-                                                 const int32_t* __restrict__ woff,
-                                                 const int32_t* __restrict__ widx, int64_t wcap,
-                                                 Geo<float> geo, const double* __restrict__ rad,
-                                                 const cx<float>* __restrict__ Me,
-                                                 cx<float>* __restrict__ Le)
+// ---- M2L, binary64: same decomposition, runtime P, operands and partial sums in shared memory
+// (one thread's column of X and A; the binary64 pipe bounds this kernel) ----
+__global__ void __launch_bounds__(64) k_m2l_pairs_f64(int P, int PS, const int32_t* __restrict__ woff,
+                                                      const int32_t* __restrict__ widx,
+                                                      const int32_t* __restrict__ wtgt, int64_t wcap,
+                                                      int64_t nbox, Geo<double> geo,
+                                                      const double* __restrict__ rad,
+                                                      const cx<double>* __restrict__ Me,
+                                                      cx<double>* __restrict__ Le)
 {
-    const int64_t g = g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= g1) return;
-    const int l = level_of(g);
-    const int64_t base = level_base(l);
-    cx<float> acc[P];
-#pragma unroll
-    for (int j = 0; j < P; j++) acc[j] = {0.f, 0.f};
-    const float rt = (float)rad[g];
-    const int64_t e0 = min((int64_t)woff[g], wcap), e1 = min((int64_t)woff[g + 1], wcap);
-    for (int64_t e = e0; e < e1; e++) {
-        const int64_t sg = base + widx[e];
-        const cx<float> z0 = geo.diff(sg, g);
-        const float r2 = z0.re * z0.re + z0.im * z0.im;
-        const float ir2 = 1.f / r2;
-        const cx<float> inv = {z0.re * ir2, -z0.im * ir2};
-        const float rs = (float)rad[sg];
-        const cx<float> u2 = cscale(inv, -2.f * rs), v2 = cscale(inv, 2.f * rt);
-        const cx<float>* src = Me + sg * PS;
-        cx<float> x[P];
-        x[0] = {src[0].re, 0.f};
-        cx<float> up = u2;
-#pragma unroll
-        for (int k = 1; k < P; k++) {
-            x[k] = cmul(src[k], up);
-            up = cmul(up, u2);
-        }
-        cx<float> vp = {1.f, 0.f};
-#pragma unroll
-        for (int o = 0; o < P; o++) {
-            cx<float> y = {0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < P; k++) {
-                y.re = fmaf(c_mf[o][k], x[k].re, y.re);
-                y.im = fmaf(c_mf[o][k], x[k].im, y.im);
+    extern __shared__ unsigned char smem[];
+    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    cx<double>* X = (cx<double>*)smem;  // X[k * nt + tid]
+    cx<double>* A = X + (size_t)P * nt;  // A[o * nt + tid]
+    const int64_t e_begin = woff[1];
+    const int64_t e_end = min((int64_t)woff[nbox], wcap);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wb = e_begin + warp * 32 * M2L_CH; wb < e_end; wb += nwarps * 32 * M2L_CH) {
+        const int64_t e0 = wb + (int64_t)lane * M2L_CH;
+        const int64_t e1 = min(e0 + M2L_CH, e_end);
+        for (int j = 0; j < P; j++) A[j * nt + tid] = {0, 0};
+        int64_t cur = -1;
+        for (int64_t e = e0; e < e1; e++) {
+            const int64_t g = wtgt[e];
+            if (g != cur) {
+                if (cur >= 0)
+                    for (int j = 0; j < P; j++) {
+                        atomicAdd(&Le[cur * PS + j].re, A[j * nt + tid].re);
+                        atomicAdd(&Le[cur * PS + j].im, A[j * nt + tid].im);
+                        A[j * nt + tid] = {0, 0};
+                    }
+                cur = g;
             }
-            if (o == 0) y.re = fmaf(x[0].re * 0.5f, logf(r2), y.re);
-            acc[o] = cfma(vp, y, acc[o]);
-            vp = cmul(vp, v2);
+            const int64_t sg = level_base(level_of(g)) + widx[e];
+            const cx<double> z0 = geo.diff(sg, g);
+            const double r2 = z0.re * z0.re + z0.im * z0.im;
+            const double ir2 = 1.0 / r2;
+            const cx<double> inv = {z0.re * ir2, -z0.im * ir2};
+            const cx<double> u2 = cscale(inv, -2.0 * rad[sg]), v2 = cscale(inv, 2.0 * rad[g]);
+            const cx<double>* src = Me + sg * PS;
+            const double a0 = src[0].re;
+            X[tid] = {a0, 0};
+            cx<double> up = u2;
+            for (int k = 1; k < P; k++) {
+                X[k * nt + tid] = cmul(src[k], up);
+                up = cmul(up, u2);
+            }
+            cx<double> vp = {1, 0};
+            for (int o = 0; o < P; o++) {
+                cx<double> y = {0, 0};
+                for (int k = 0; k < P; k++) {
+                    const double m = c_md[o][k];
+                    const cx<double> xv = X[k * nt + tid];
+                    y.re += m * xv.re;
+                    y.im += m * xv.im;
+                }
+                if (o == 0) y.re += a0 * 0.5 * log(r2);
+                A[o * nt + tid] = cfma(vp, y, A[o * nt + tid]);
+                vp = cmul(vp, v2);
+            }
+        }
+        const int64_t prev = __shfl_up_sync(0xffffffffu, cur, 1);
+        const bool head = cur >= 0 && (lane == 0 || prev != cur);
+        for (int j = 0; j < P; j++) {
+            cx<double> v = A[j * nt + tid];
+            for (int off = 1; off < 32; off <<= 1) {
+                const int64_t pkey = __shfl_down_sync(0xffffffffu, cur, off);
+                const double pr = __shfl_down_sync(0xffffffffu, v.re, off);
+                const double pi = __shfl_down_sync(0xffffffffu, v.im, off);
+                if ((lane + off < 32) && pkey == cur) {
+                    v.re += pr;
+                    v.im += pi;
+                }
+            }
+            if (head) {
+                atomicAdd(&Le[cur * PS + j].re, v.re);
+                atomicAdd(&Le[cur * PS + j].im, v.im);
+            }
         }
     }
-#pragma unroll
-    for (int o = 0; o < P; o++) Le[g * PS + o] = acc[o];
 }
 
 // ---- L2L: one warp per child box of level l+1 ----
@@ -321,9 +441,11 @@ __global__ void k_l2l(int l, int P, int PS, const double* __restrict__ cen, cons
 {
     extern __shared__ unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    T* Bn = (T*)smem;
+    cx<T>* B = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
+    load_binom(Bn, P);
     const int64_t c = (int64_t)blockIdx.x * wpb + w;
     if (c >= level_size(l + 1)) return;
-    cx<T>* B = (cx<T>*)smem + (size_t)w * P;
     const int64_t cg = level_base(l + 1) + c, pg = level_base(l) + (c >> 2);
     const double rp = rad[pg];
     cx<T> wv = {0, 0};
@@ -335,93 +457,228 @@ __global__ void k_l2l(int l, int P, int PS, const double* __restrict__ cen, cons
     for (int j = lane; j < P; j += 32) B[j] = Le[pg * PS + j];
     __syncwarp();
     for (int o = lane; o < P; o += 32) {
-        cx<T> h = cscale(B[P - 1], (T)c_binom[P - 1][o]);
-        for (int k = P - 2; k >= o; k--) h = cfma(h, wv, cscale(B[k], (T)c_binom[k][o]));
+        cx<T> h = cscale(B[P - 1], Bn[(P - 1) * P + o]);
+        for (int k = P - 2; k >= o; k--) h = cfma(h, wv, cscale(B[k], Bn[k * P + o]));
         const cx<T> r = cscale(h, ipow(s, o));
         Le[cg * PS + o] = cadd(Le[cg * PS + o], r);
     }
 }
 
-// ---- L2P + near field: one warp per leaf, one lane per target; source tiles of 32 points are
-// staged in shared memory and read by every lane.  Potentials are written in input order. ----
+// ---- L2P: one thread per point (canonical order); initialises the accumulator ----
 template <typename T>
-__global__ void k_leaf_eval(int L, int P, int PS, const int32_t* __restrict__ lb,
-                            const int32_t* __restrict__ perm, const int32_t* __restrict__ soff,
-                            const int32_t* __restrict__ sidx, int64_t scap, const double* __restrict__ xs,
-                            const double* __restrict__ ys, const float* __restrict__ dxf,
-                            const float* __restrict__ dyf, const T* __restrict__ qs,
-                            const double* __restrict__ cen, const float* __restrict__ chi,
-                            const float* __restrict__ clo, const double* __restrict__ rad,
-                            const cx<T>* __restrict__ Le, double* __restrict__ phi)
+__global__ void k_l2p(int L, int P, int PS, int64_t n, const int32_t* __restrict__ cleaf,
+                      const Pk<T>* __restrict__ pk, const double* __restrict__ cen,
+                      const double* __restrict__ rad, const cx<T>* __restrict__ Le,
+                      double* __restrict__ acc)
 {
-    extern __shared__ unsigned char smem[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    const int64_t b = (int64_t)blockIdx.x * wpb + w;
-    if (b >= level_size(L)) return;
-    cx<T>* B = (cx<T>*)smem + (size_t)w * (P + 48);
-    T* sx = (T*)(B + P);
-    T* sy = sx + 32;
-    T* sq = sy + 32;
-    const int64_t g = level_base(L) + b;
-    for (int j = lane; j < P; j += 32) B[j] = Le[g * PS + j];
-    const double rho = rad[g];
-    const int32_t t0 = lb[b], t1 = lb[b + 1];
-    const int64_t e0 = min((int64_t)soff[g], scap), e1 = min((int64_t)soff[g + 1], scap);
-    const bool f32 = sizeof(T) == 4;
-    __syncwarp();
-    for (int32_t tb = t0; tb < t1; tb += 32) {
-        const int32_t t = tb + lane;
-        const bool valid = t < t1;
-        T xi = 0, yi = 0;  // target: absolute (binary64) or offset from the leaf centre (binary32)
-        T far = 0;
-        if (valid) {
-            xi = f32 ? (T)dxf[t] : (T)xs[t];
-            yi = f32 ? (T)dyf[t] : (T)ys[t];
-            cx<T> z = {0, 0};
-            if (rho > 0) {
-                if (f32) {
-                    const T inv = (T)(1.0 / rho);
-                    z = {xi * inv, yi * inv};
-                } else {
-                    z = {(T)((xs[t] - cen[2 * g]) / rho), (T)((ys[t] - cen[2 * g + 1]) / rho)};
-                }
-            }
-            cx<T> h = B[P - 1];
-            for (int k = P - 2; k >= 0; k--) h = cfma(h, z, B[k]);
-            far = h.re;
-        }
-        T near = 0;
-        for (int64_t e = e0; e < e1; e++) {
-            const int64_t sb = sidx[e];
-            T ox = 0, oy = 0;  // binary32: centre of the source leaf relative to the target leaf
-            if (f32) {
-                const int64_t sg = level_base(L) + sb;
-                ox = (T)((chi[2 * sg] - chi[2 * g]) + (clo[2 * sg] - clo[2 * g]));
-                oy = (T)((chi[2 * sg + 1] - chi[2 * g + 1]) + (clo[2 * sg + 1] - clo[2 * g + 1]));
-            }
-            const int32_t s0 = lb[sb], s1 = lb[sb + 1];
-            for (int32_t sc = s0; sc < s1; sc += 32) {
-                const int32_t s = sc + lane;
-                if (s < s1) {
-                    sx[lane] = f32 ? (T)dxf[s] + ox : (T)xs[s];
-                    sy[lane] = f32 ? (T)dyf[s] + oy : (T)ys[s];
-                    sq[lane] = qs[s];
-                }
-                __syncwarp();
-                const int cnt = min(32, s1 - sc);
-                for (int j = 0; j < cnt; j++) {
-                    const T dx = xi - sx[j], dy = yi - sy[j];
-                    const T r2 = dx * dx + dy * dy;
-                    if (r2 > (T)0) near += sq[j] * (f32 ? (T)__log2f((float)r2) : (T)log((double)r2));
-                }
-                __syncwarp();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = level_base(L) + cleaf[i];
+        const double rho = rad[g];
+        const Pk<T> p = pk[i];
+        cx<T> z = {0, 0};
+        if (rho > 0) {
+            if (sizeof(T) == 8) {
+                z = {(T)(((double)p.x - cen[2 * g]) / rho), (T)(((double)p.y - cen[2 * g + 1]) / rho)};
+            } else {
+                const T inv = (T)(1.0 / rho);
+                z = {p.x * inv, p.y * inv};
             }
         }
-        if (valid) {
-            const T scale = f32 ? (T)(0.5 * 0.69314718055994530942) : (T)0.5;
-            phi[perm[t]] = (double)far + (double)(near * scale);
+        const cx<T>* B = Le + g * PS;
+        cx<T> h = B[P - 1];
+        for (int k = P - 2; k >= 0; k--) h = cfma(h, z, B[k]);
+        acc[i] = (double)h.re;
+    }
+}
+
+// ---- near field over the flat strong-pair array of the finest level ----
+//
+// Pair (target leaf, source leaf) e of the finest strong lists contributes
+//     phi_i += sum_{j in source leaf, z_j != z_i} q_j log|z_i - z_j|,  i in target leaf.
+// binary32 path: coordinates are offsets from the leaf centres, the target is moved into the
+// source frame through the float-float centre difference once per leaf pair, and
+// q_j * log2(r^2) is summed in binary32 over one source leaf, then into a float-float lane
+// accumulator.  A binary32 offset carries an absolute error of 2^-24 of the leaf scale M, so a
+// pair closer than M/64 (which includes j = i and coincident points) is redone from the binary64
+// coordinates; every other term then has |error| < 2^-17 in log2 units.  binary64 path: absolute
+// coordinates, binary64 log.  Flushes add binary64 partial sums to the accumulator atomically.
+
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float v)
+{
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
+// Leaves of at most 32 points: groups of gs = pow2ceil(max leaf size) lanes, one lane per target;
+// the G = 32/gs groups of a warp walk the warp's P2P_CH consecutive pairs round robin, each group
+// one whole source leaf at a time.
+template <typename T>
+__global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t* __restrict__ soff,
+                                                   const int32_t* __restrict__ sidx,
+                                                   const int32_t* __restrict__ stgt, int64_t scap,
+                                                   const int32_t* __restrict__ lb,
+                                                   const Pk<T>* __restrict__ pk,
+                                                   const double* __restrict__ xs,
+                                                   const double* __restrict__ ys,
+                                                   const float* __restrict__ chi,
+                                                   const float* __restrict__ clo,
+                                                   const double* __restrict__ rad,
+                                                   double* __restrict__ acc)
+{
+    constexpr bool F32 = sizeof(T) == 4;
+    const int lane = threadIdx.x & 31, G = 32 / gs, grp = lane / gs, ti = lane & (gs - 1);
+    const int64_t base = level_base(L);
+    const int64_t e_begin = min((int64_t)soff[base], scap);
+    const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double scale = F32 ? 0.5 * 0.69314718055994530942 : 0.5;
+    for (int64_t e0 = e_begin + warp * P2P_CH; e0 < e_end; e0 += nwarps * P2P_CH) {
+        const int64_t e1 = min(e0 + P2P_CH, e_end);
+        int64_t cur = -1;
+        int32_t it = 0;  // canonical index of this lane's target
+        bool active = false;
+        T tx = 0, ty = 0;
+        float hi = 0.f, lo = 0.f;  // binary32 path accumulator
+        double sum64 = 0.0;        // binary64 path accumulator
+        for (int64_t e = e0 + grp; e < e1; e += G) {
+            const int64_t tl = stgt[e] - base;
+            if (tl != cur) {
+                if (active) atomicAdd(&acc[it], F32 ? ((double)hi + (double)lo) * scale : sum64 * scale);
+                cur = tl;
+                const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0;
+                active = ti < nt;
+                it = t0 + ti;
+                hi = lo = 0.f;
+                sum64 = 0.0;
+                if (active) {
+                    const Pk<T> p = pk[it];
+                    tx = p.x;
+                    ty = p.y;
+                }
+            }
+            if (!active) continue;
+            const int64_t sl = sidx[e];
+            const int32_t s0 = lb[sl], ns = lb[sl + 1] - s0;
+            if constexpr (F32) {
+                const int64_t sg = base + sl, tg = base + tl;
+                const float ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
+                const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
+                const float xt = tx - ox, yt = ty - oy;
+                const float M = (float)rad[sg] + (float)rad[tg] + fabsf(ox) + fabsf(oy);
+                const float tau2 = (M * (1.f / 64.f)) * (M * (1.f / 64.f));
+                float part = 0.f;
+#pragma unroll 4
+                for (int j = 0; j < ns; j++) {
+                    const Pk<float> sp = pk[s0 + j];
+                    const float dx = xt - sp.x, dy = yt - sp.y;
+                    const float r2 = dx * dx + dy * dy;
+                    if (r2 >= tau2) {
+                        part += sp.q * __log2f(r2);
+                    } else {
+                        const double ddx = xs[it] - xs[s0 + j], ddy = ys[it] - ys[s0 + j];
+                        const double r2d = ddx * ddx + ddy * ddy;
+                        if (r2d > 0.0) part += sp.q * (float)log2(r2d);
+                    }
+                }
+                two_sum(hi, lo, part);
+            } else {
+                double part = 0.0;
+                for (int j = 0; j < ns; j++) {
+                    const Pk<double> sp = pk[s0 + j];
+                    const double dx = tx - sp.x, dy = ty - sp.y;
+                    const double r2 = dx * dx + dy * dy;
+                    if (r2 > 0.0) part += sp.q * log(r2);
+                }
+                sum64 += part;
+            }
+        }
+        if (active) atomicAdd(&acc[it], F32 ? ((double)hi + (double)lo) * scale : sum64 * scale);
+    }
+}
+
+// Leaves of more than 32 points: one lane per target, 32 targets at a time, every source of the
+// pair; one flush per (pair, block of 32 targets).
+template <typename T>
+__global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restrict__ soff,
+                                                   const int32_t* __restrict__ sidx,
+                                                   const int32_t* __restrict__ stgt, int64_t scap,
+                                                   const int32_t* __restrict__ lb,
+                                                   const Pk<T>* __restrict__ pk,
+                                                   const double* __restrict__ xs,
+                                                   const double* __restrict__ ys,
+                                                   const float* __restrict__ chi,
+                                                   const float* __restrict__ clo,
+                                                   const double* __restrict__ rad,
+                                                   double* __restrict__ acc)
+{
+    constexpr bool F32 = sizeof(T) == 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t base = level_base(L);
+    const int64_t e_begin = min((int64_t)soff[base], scap);
+    const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double scale = F32 ? 0.5 * 0.69314718055994530942 : 0.5;
+    for (int64_t e = e_begin + warp; e < e_end; e += nwarps) {
+        const int64_t tl = stgt[e] - base, sl = sidx[e];
+        const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0, s0 = lb[sl], ns = lb[sl + 1] - s0;
+        float ox = 0.f, oy = 0.f, tau2 = 0.f;
+        if constexpr (F32) {
+            const int64_t sg = base + sl, tg = base + tl;
+            ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
+            oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
+            const float M = (float)rad[sg] + (float)rad[tg] + fabsf(ox) + fabsf(oy);
+            tau2 = (M * (1.f / 64.f)) * (M * (1.f / 64.f));
+        }
+        for (int tc = 0; tc < nt; tc += 32) {
+            const int32_t it = t0 + tc + lane;
+            if (tc + lane >= nt) continue;
+            const Pk<T> p = pk[it];
+            if constexpr (F32) {
+                const float xt = p.x - ox, yt = p.y - oy;
+                float hi = 0.f, lo = 0.f;
+                for (int jb = 0; jb < ns; jb += 32) {
+                    float part = 0.f;
+                    const int je = min(ns, jb + 32);
+                    for (int j = jb; j < je; j++) {
+                        const Pk<float> sp = pk[s0 + j];
+                        const float dx = xt - sp.x, dy = yt - sp.y;
+                        const float r2 = dx * dx + dy * dy;
+                        if (r2 >= tau2) {
+                            part += sp.q * __log2f(r2);
+                        } else {
+                            const double ddx = xs[it] - xs[s0 + j], ddy = ys[it] - ys[s0 + j];
+                            const double r2d = ddx * ddx + ddy * ddy;
+                            if (r2d > 0.0) part += sp.q * (float)log2(r2d);
+                        }
+                    }
+                    two_sum(hi, lo, part);
+                }
+                atomicAdd(&acc[it], ((double)hi + (double)lo) * scale);
+            } else {
+                double part = 0.0;
+                for (int j = 0; j < ns; j++) {
+                    const Pk<double> sp = pk[s0 + j];
+                    const double dx = p.x - sp.x, dy = p.y - sp.y;
+                    const double r2 = dx * dx + dy * dy;
+                    if (r2 > 0.0) part += sp.q * log(r2);
+                }
+                atomicAdd(&acc[it], part * scale);
+            }
         }
     }
+}
+
+__global__ void k_unpermute(const int32_t* __restrict__ perm, const double* __restrict__ acc, int64_t n,
+                            double* __restrict__ phi)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        phi[perm[i]] = acc[i];
 }
 
 // ---- direct sum at sampled targets (binary64), one block per target ----
@@ -488,6 +745,11 @@ int ensure_tables()
 
 int alloc_ws(fmm_tree t, int PS, bool f64)
 {
+    if (!t->acc && cudaMalloc((void**)&t->acc, 8 * (size_t)t->n) != cudaSuccess)
+        return fail(FMM_ERR_OOM, "accumulator");
+    void** pk = f64 ? &t->pk64 : &t->pk32;
+    if (!*pk && cudaMalloc(pk, (f64 ? 32 : 16) * (size_t)t->n) != cudaSuccess)
+        return fail(FMM_ERR_OOM, "packed points");
     int& have = f64 ? t->ws_ps64 : t->ws_ps32;
     if (have >= PS) return 0;
     void** M = f64 ? &t->Me : &t->Mf;
@@ -500,10 +762,6 @@ int alloc_ws(fmm_tree t, int PS, bool f64)
     const size_t bytes = (size_t)t->nbox * PS * csz;
     if (cudaMalloc(M, bytes) != cudaSuccess || cudaMalloc(Lc, bytes) != cudaSuccess)
         return fail(FMM_ERR_OOM, "expansion workspace of %zu bytes", 2 * bytes);
-    if (f64 && !t->qs && cudaMalloc((void**)&t->qs, 8 * (size_t)t->n) != cudaSuccess)
-        return fail(FMM_ERR_OOM, "strength workspace");
-    if (!f64 && !t->qf && cudaMalloc((void**)&t->qf, 4 * (size_t)t->n) != cudaSuccess)
-        return fail(FMM_ERR_OOM, "strength workspace");
     have = PS;
     return 0;
 }
@@ -512,6 +770,42 @@ int grid_for(int64_t n, int threads)
 {
     int64_t g = (n + threads - 1) / threads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+}
+
+template <int PI>
+int launch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<float> geo, const cx<float>* Me,
+               cx<float>* Le, cudaStream_t s)
+{
+    k_m2l_pairs<float, PI><<<152 * 16, 128, 0, s>>>(P, PS, li->woff, li->widx, li->wtgt, li->wcap,
+                                                     t->nbox, geo, t->radii, Me, Le); note_launch();
+    FMM_LAUNCH_CHECK("evaluate: M2L");
+    return 0;
+}
+
+int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<float> geo, const cx<float>* Me,
+                 cx<float>* Le, cudaStream_t s)
+{
+    if (P <= 9) return launch_m2l<9>(t, li, P, PS, geo, Me, Le, s);
+    if (P <= 13) return launch_m2l<13>(t, li, P, PS, geo, Me, Le, s);
+    if (P <= 17) return launch_m2l<17>(t, li, P, PS, geo, Me, Le, s);
+    if (P == 18) return launch_m2l<18>(t, li, P, PS, geo, Me, Le, s);
+    if (P <= 21) return launch_m2l<21>(t, li, P, PS, geo, Me, Le, s);
+    if (P <= 25) return launch_m2l<25>(t, li, P, PS, geo, Me, Le, s);
+    if (P <= 31) return launch_m2l<31>(t, li, P, PS, geo, Me, Le, s);
+    if (P <= 33) return launch_m2l<33>(t, li, P, PS, geo, Me, Le, s);
+    return launch_m2l<41>(t, li, P, PS, geo, Me, Le, s);
+}
+
+int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<double> geo, const cx<double>* Me,
+                 cx<double>* Le, cudaStream_t s)
+{
+    const int NT = 64;
+    const size_t sm = (size_t)2 * P * NT * sizeof(cx<double>);
+    FMM_CUDA(cudaFuncSetAttribute(k_m2l_pairs_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_m2l_pairs_f64<<<152 * 16, NT, sm, s>>>(P, PS, li->woff, li->widx, li->wtgt, li->wcap, t->nbox,
+                                              geo, t->radii, Me, Le); note_launch();
+    FMM_LAUNCH_CHECK("evaluate: M2L");
+    return 0;
 }
 
 template <typename T>
@@ -523,88 +817,73 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     if (rc) return rc;
     cx<T>* Me = (cx<T>*)(f64 ? t->Me : t->Mf);
     cx<T>* Le = (cx<T>*)(f64 ? t->Le : t->Lf);
-    T* qs = f64 ? (T*)t->qs : (T*)t->qf;
+    Pk<T>* pk = (Pk<T>*)(f64 ? t->pk64 : t->pk32);
     const int L = t->L;
     const int64_t n = t->n;
+    const int WPB = 4;
+    const size_t bsm = ((P * P * sizeof(T) + 15) & ~15);
 
     {
         StageScope scope(FMM_STAGE_GATHER, s);
-        k_gather_q<T><<<grid_for(n, 256), 256, 0, s>>>(t->perm, q, n, qs, t->status); note_launch();
+        k_pack<T><<<grid_for(n, 256), 256, 0, s>>>(t->perm, q, t->xs, t->ys, t->dxf, t->dyf, n, pk,
+                                                   t->status); note_launch();
+        FMM_CUDA(cudaMemsetAsync(Le, 0, (size_t)t->nbox * PS * sizeof(cx<T>), s));
         FMM_LAUNCH_CHECK("evaluate: gather");
     }
-
-    const int WPB = 4;
     if (L >= 1) {
-        // upward pass
-        const int64_t nleaf = level_size(L);
-        size_t sm = (size_t)WPB * 33 * P * sizeof(cx<T>);
-        FMM_CUDA(cudaFuncSetAttribute(k_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         {
             StageScope scope(FMM_STAGE_P2M, s);
+            const int64_t nleaf = level_size(L);
+            const size_t sm = (size_t)WPB * 33 * P * sizeof(cx<T>);
+            FMM_CUDA(cudaFuncSetAttribute(k_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             k_p2m<T><<<(unsigned)((nleaf + WPB - 1) / WPB), 32 * WPB, sm, s>>>(
-                L, P, PS, t->leaf_begin, qs, t->xs, t->ys, t->dxf, t->dyf, t->centers, t->radii, Me); note_launch();
+                L, P, PS, t->leaf_begin, pk, t->centers, t->radii, Me); note_launch();
+            FMM_LAUNCH_CHECK("evaluate: P2M");
         }
-        StageScope m2m_scope(FMM_STAGE_M2M, s);
-        for (int l = L - 1; l >= 1; l--) {
-            const int64_t nb = level_size(l);
-            k_m2m<T><<<(unsigned)((nb + WPB - 1) / WPB), 32 * WPB, WPB * P * sizeof(cx<T>), s>>>(
-                l, P, PS, t->centers, t->radii, Me); note_launch();
-        }
-        FMM_LAUNCH_CHECK("evaluate: upward pass");
-        prof_mark(FMM_STAGE_M2M, false, s);
-        m2m_scope.stage = -1;
-
-        // M2L on the weak lists of every level (one launch over levels 1..L)
-        const int64_t g0 = 1, g1 = t->nbox;
-        bool done = false;
-        prof_mark(FMM_STAGE_M2L, true, s);
-        if (!f64) {
-            Geo<float> geo{t->cen_hi, t->cen_lo};
-            const unsigned blocks = (unsigned)((g1 - g0 + 127) / 128);
-            const cx<float>* Mf = (const cx<float>*)Me;
-            cx<float>* Lf = (cx<float>*)Le;
-            done = true;
-            switch (P) {
-                case 17: k_m2l_f32<17><<<blocks, 128, 0, s>>>(g0, g1, PS, li->woff, li->widx, li->wcap, geo, t->radii, Mf, Lf); note_launch(); break;
-                case 18: k_m2l_f32<18><<<blocks, 128, 0, s>>>(g0, g1, PS, li->woff, li->widx, li->wcap, geo, t->radii, Mf, Lf); note_launch(); break;
-                case 21: k_m2l_f32<21><<<blocks, 128, 0, s>>>(g0, g1, PS, li->woff, li->widx, li->wcap, geo, t->radii, Mf, Lf); note_launch(); break;
-                case 31: k_m2l_f32<31><<<blocks, 128, 0, s>>>(g0, g1, PS, li->woff, li->widx, li->wcap, geo, t->radii, Mf, Lf); note_launch(); break;
-                default: done = false;
+        {
+            StageScope scope(FMM_STAGE_M2M, s);
+            for (int l = L - 1; l >= 1; l--) {
+                const int64_t nb = level_size(l);
+                k_m2m<T><<<(unsigned)((nb + WPB - 1) / WPB), 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
+                    l, P, PS, t->centers, t->radii, Me); note_launch();
             }
+            FMM_LAUNCH_CHECK("evaluate: M2M");
         }
-        if (!done) {
-            const int NT = 64;
-            size_t sm2 = (size_t)2 * P * NT * sizeof(cx<T>);
-            FMM_CUDA(cudaFuncSetAttribute(k_m2l_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+        {
+            StageScope scope(FMM_STAGE_M2L, s);
             Geo<T> geo;
             if constexpr (sizeof(T) == 8) geo = Geo<T>{t->centers};
             else geo = Geo<T>{t->cen_hi, t->cen_lo};
-            k_m2l_generic<T><<<(unsigned)((g1 - g0 + NT - 1) / NT), NT, sm2, s>>>(
-                g0, g1, P, PS, li->woff, li->widx, li->wcap, geo, t->radii, Me, Le); note_launch();
+            rc = dispatch_m2l(t, li, P, PS, geo, Me, Le, s);
+            if (rc) return rc;
         }
-        prof_mark(FMM_STAGE_M2L, false, s);
-        FMM_LAUNCH_CHECK("evaluate: M2L");
-
-        // downward pass
-        StageScope l2l_scope(FMM_STAGE_L2L, s);
-        for (int l = 1; l < L; l++) {
-            const int64_t nc = level_size(l + 1);
-            k_l2l<T><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, WPB * P * sizeof(cx<T>), s>>>(
-                l, P, PS, t->centers, t->radii, Le); note_launch();
+        {
+            StageScope scope(FMM_STAGE_L2L, s);
+            for (int l = 1; l < L; l++) {
+                const int64_t nc = level_size(l + 1);
+                k_l2l<T><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
+                    l, P, PS, t->centers, t->radii, Le); note_launch();
+            }
+            FMM_LAUNCH_CHECK("evaluate: L2L");
         }
-        FMM_LAUNCH_CHECK("evaluate: L2L");
-    } else {
-        FMM_CUDA(cudaMemsetAsync(Le, 0, PS * sizeof(cx<T>), s));
     }
-
-    // L2P + near field on the leaves
     {
         StageScope scope(FMM_STAGE_LEAF, s);
-        const int64_t nleaf = level_size(L);
-        size_t sm = (size_t)WPB * ((P + 48) * sizeof(cx<T>));
-        k_leaf_eval<T><<<(unsigned)((nleaf + WPB - 1) / WPB), 32 * WPB, sm, s>>>(
-            L, P, PS, t->leaf_begin, t->perm, li->soff, li->sidx, li->scap, t->xs, t->ys, t->dxf,
-            t->dyf, qs, t->centers, t->cen_hi, t->cen_lo, t->radii, Le, phi); note_launch();
+        k_l2p<T><<<grid_for(n, 256), 256, 0, s>>>(L, P, PS, n, t->cleaf, pk, t->centers, t->radii, Le,
+                                                  t->acc); note_launch();
+        const int64_t maxleaf = (n + level_size(L) - 1) / level_size(L);
+        if (maxleaf <= 32) {
+            int gs = 1;
+            while (gs < maxleaf) gs <<= 1;
+            k_p2p_small<T><<<152 * 8, 256, 0, s>>>(L, gs, li->soff, li->sidx, li->stgt, li->scap,
+                                                   t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
+                                                   t->cen_lo, t->radii, t->acc); note_launch();
+        } else {
+            k_p2p_large<T><<<152 * 8, 256, 0, s>>>(L, li->soff, li->sidx, li->stgt, li->scap,
+                                                   t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
+                                                   t->cen_lo, t->radii, t->acc); note_launch();
+        }
+        k_unpermute<<<grid_for(n, 256), 256, 0, s>>>(t->perm, t->acc, n, phi); note_launch();
         FMM_LAUNCH_CHECK("evaluate: leaf evaluation");
     }
     return 0;

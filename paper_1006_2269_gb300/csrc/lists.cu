@@ -1,16 +1,26 @@
 // Interaction lists on the GPU: the connectivity rule of Section 4 with the theta-criterion
-// (Criterion 2.1).  Level by level, one warp per box tests the children of its parent's strong
-// list (one lane per candidate) and compacts the outcome with ballots, so every list comes out in
-// ascending candidate order.  A count pass, a device-wide scan and a fill pass turn the counts
-// into CSR offsets; the running total of each level is read from device memory, so the whole
-// build is asynchronous.  Storage is preallocated: entries beyond the capacity are dropped and
-// reported through the status word, and later levels never read past the capacity.
+// (Criterion 2.1).
+//
+// Level by level, every candidate pair (box b, child c of a box of S(parent(b))) is one thread.
+// Candidates are enumerated parent by parent, box by box (b = 4 parent + k), then in the order
+// of the parent's strong list and the child index, so each box owns a contiguous, ascending run
+// of candidates.  One global scan of the weak flags then gives every entry its CSR position and
+// every box its offsets, whatever the spread of list lengths (balanced trees of clustered points
+// have lists from a handful to thousands of entries).  The number of candidates of a level lives
+// in device memory, so the kernels use grid-stride loops over a fixed grid and the whole build is
+// asynchronous.  Entries beyond the preallocated capacity are dropped and flagged in the status
+// word; later levels never read past the capacity.
 #include <algorithm>
 
 #include "common.cuh"
 
 namespace fmm {
 namespace {
+
+constexpr int LT = 256;          // threads per block
+constexpr int LI = 8;            // candidates per thread per tile
+constexpr int LTILE = LT * LI;   // candidates per tile
+constexpr int LGRID = 152 * 8;   // blocks of the grid-stride kernels
 
 __device__ __forceinline__ unsigned lanemask_lt()
 {
@@ -31,7 +41,29 @@ __device__ __forceinline__ bool theta_weak(double ax, double ay, double ra, doub
     return (__dadd_rn(R, __dmul_rn(theta, r)) <= __dmul_rn(theta, d)) && (__dadd_rn(R, r) < d);
 }
 
-__global__ void k_lists_root(int32_t* woff, int32_t* soff, int32_t* sidx)
+// The same decision taken in binary32 first (float-float centres, binary32 radii).  Every
+// binary32 quantity below is within 2^-20 (relative to theta*d + R + theta*r, resp. d + R + r) of
+// its binary64 counterpart, so a margin larger than 2^-16 of that scale has the sign the binary64
+// test would find; only candidates closer to the boundary take the binary64 test.
+__device__ __forceinline__ bool theta_weak_fast(int64_t a, int64_t b, const float* __restrict__ chi,
+                                                const float* __restrict__ clo,
+                                                const float* __restrict__ rad32, const double* __restrict__ cen,
+                                                const double* __restrict__ rad, float th32, double theta)
+{
+    const float2 ha = *(const float2*)(chi + 2 * a), hb = *(const float2*)(chi + 2 * b);
+    const float2 la = *(const float2*)(clo + 2 * a), lb = *(const float2*)(clo + 2 * b);
+    const float dx = (ha.x - hb.x) + (la.x - lb.x), dy = (ha.y - hb.y) + (la.y - lb.y);
+    const float d = sqrtf(dx * dx + dy * dy);
+    const float ra = rad32[a], rb = rad32[b];
+    const float R = fmaxf(ra, rb), r = fminf(ra, rb);
+    const float m1 = th32 * d - (R + th32 * r), s1 = th32 * d + R + th32 * r;
+    const float m2 = d - (R + r), s2 = d + R + r;
+    const float eps = 1.0f / 65536.0f;
+    if (fabsf(m1) > eps * s1 && fabsf(m2) > eps * s2) return m1 >= 0.f && m2 > 0.f;
+    return theta_weak(cen[2 * a], cen[2 * a + 1], rad[a], cen[2 * b], cen[2 * b + 1], rad[b], theta);
+}
+
+__global__ void k_lists_root(int32_t* woff, int32_t* soff, int32_t* sidx, int32_t* stgt)
 {
     if (threadIdx.x == 0) {
         woff[0] = 0;
@@ -39,55 +71,200 @@ __global__ void k_lists_root(int32_t* woff, int32_t* soff, int32_t* sidx)
         soff[0] = 0;
         soff[1] = 1;
         sidx[0] = 0;
+        stgt[0] = 0;
     }
 }
 
-template <bool FILL>
-__global__ void __launch_bounds__(256) k_lists(int l, const double* __restrict__ cen,
-                                               const double* __restrict__ rad, double theta,
-                                               const int32_t* __restrict__ woff, int32_t* __restrict__ widx,
-                                               int64_t wcap, const int32_t* __restrict__ soff,
-                                               int32_t* __restrict__ sidx, int64_t scap,
-                                               int32_t* __restrict__ wcnt, int32_t* __restrict__ scnt)
+// Parent-level strong entries of level l-1 that lie within the capacity: [S0, S1).
+struct LevelCands {
+    int64_t S0, S1;
+    __device__ __forceinline__ int64_t count() const { return 16 * (S1 - S0); }
+};
+
+__device__ __forceinline__ LevelCands level_cands(const int32_t* soff, int l, int64_t scap)
 {
-    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b >= level_size(l)) return;
-    const int64_t base = level_base(l), g = base + b;
-    const int64_t pg = level_base(l - 1) + (b >> 2);
-    const int64_t s0 = min((int64_t)soff[pg], scap), s1 = min((int64_t)soff[pg + 1], scap);
-    const int64_t ncand = s1 > s0 ? 4 * (s1 - s0) : 0;
-    const double cx = cen[2 * g], cy = cen[2 * g + 1], r = rad[g];
-    const unsigned lt = lanemask_lt();
-    int64_t wpos = FILL ? woff[g] : 0, spos = FILL ? soff[g] : 0;
-    int nw = 0, ns = 0;
-    for (int64_t c0 = 0; c0 < ncand; c0 += 32) {
-        int64_t c = c0 + lane;
-        bool valid = c < ncand;
-        int32_t cand = 0;
-        bool weak = false;
-        if (valid) {
-            cand = 4 * sidx[s0 + (c >> 2)] + (int32_t)(c & 3);
-            int64_t cg = base + cand;
-            weak = theta_weak(cx, cy, r, cen[2 * cg], cen[2 * cg + 1], rad[cg], theta);
-        }
-        unsigned bw = __ballot_sync(0xffffffffu, valid && weak);
-        unsigned bs = __ballot_sync(0xffffffffu, valid && !weak);
-        if (FILL && valid) {
-            if (weak) {
-                int64_t p = wpos + nw + __popc(bw & lt);
-                if (p < wcap) widx[p] = cand;
-            } else {
-                int64_t p = spos + ns + __popc(bs & lt);
-                if (p < scap) sidx[p] = cand;
+    const int64_t pb0 = level_base(l - 1), np = level_size(l - 1);
+    LevelCands c;
+    c.S0 = min((int64_t)soff[pb0], scap);
+    c.S1 = min((int64_t)soff[pb0 + np], scap);
+    if (c.S1 < c.S0) c.S1 = c.S0;
+    return c;
+}
+
+// Decode candidate t of level l: box b (within-level), candidate c (within-level), and whether t
+// is the first candidate of its box.
+__device__ __forceinline__ void decode(const int32_t* __restrict__ soff, const int32_t* __restrict__ sidx,
+                                       int l, int64_t scap, const LevelCands& lc, int64_t t, int64_t& b,
+                                       int64_t& c, bool& first)
+{
+    const int64_t pb0 = level_base(l - 1), np = level_size(l - 1);
+    // parent p: largest p with 16 * (soff[pb0 + p] - S0) <= t
+    int64_t lo = 0, hi = np - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        int64_t off = min((int64_t)soff[pb0 + mid], scap);
+        if (16 * (off - lc.S0) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t p = lo;
+    const int64_t s0 = min((int64_t)soff[pb0 + p], scap), s1 = min((int64_t)soff[pb0 + p + 1], scap);
+    const int64_t m = s1 - s0;  // >= 1 whenever t falls inside this parent's block
+    const int64_t tp = t - 16 * (s0 - lc.S0);
+    const int64_t k = tp / (4 * m), r = tp - k * 4 * m;
+    b = 4 * p + k;
+    c = 4 * (int64_t)sidx[s0 + (r >> 2)] + (r & 3);
+    first = (r == 0);
+}
+
+__global__ void __launch_bounds__(LT) k_lists_flags(int l, const double* __restrict__ cen,
+                                                    const double* __restrict__ rad,
+                                                    const float* __restrict__ chi,
+                                                    const float* __restrict__ clo,
+                                                    const float* __restrict__ rad32, double theta,
+                                                    const int32_t* __restrict__ soff,
+                                                    const int32_t* __restrict__ sidx, int64_t scap,
+                                                    uint8_t* __restrict__ flags,
+                                                    uint32_t* __restrict__ tilecnt)
+{
+    __shared__ uint32_t wsum[LT / 32];
+    const LevelCands lc = level_cands(soff, l, scap);
+    const int64_t nc = lc.count();
+    const int64_t ntiles = (nc + LTILE - 1) / LTILE;
+    const int64_t base = level_base(l);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint32_t cnt = 0;
+        for (int j = 0; j < LI; j++) {
+            const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
+            if (t < nc) {
+                int64_t b, c;
+                bool first;
+                decode(soff, sidx, l, scap, lc, t, b, c, first);
+                const bool w = theta_weak_fast(base + b, base + c, chi, clo, rad32, cen, rad,
+                                               (float)theta, theta);
+                flags[t] = w ? 1 : 0;
+                cnt += w;
             }
         }
-        nw += __popc(bw);
-        ns += __popc(bs);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t s = 0;
+            for (int w = 0; w < LT / 32; w++) s += wsum[w];
+            tilecnt[tile] = s;
+        }
+        __syncthreads();
     }
-    if (!FILL && lane == 0) {
-        wcnt[b] = nw;
-        scnt[b] = ns;
+}
+
+// Exclusive scan of the weak counts per tile; writes the level totals into the offsets.
+__global__ void __launch_bounds__(1024) k_lists_scan(int l, int64_t scap, uint32_t* tilecnt,
+                                                     int32_t* woff, int32_t* soff)
+{
+    __shared__ int64_t wt[32];
+    const LevelCands lc = level_cands(soff, l, scap);
+    const int64_t nc = lc.count();
+    const int64_t ntiles = (nc + LTILE - 1) / LTILE;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < ntiles; b0 += blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        int64_t v = i < ntiles ? tilecnt[i] : 0, x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wt[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int64_t s = lane < nw ? wt[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            if (lane < nw) wt[lane] = s;
+        }
+        __syncthreads();
+        const int64_t before = w ? wt[w - 1] : 0, tot = wt[nw - 1];
+        if (i < ntiles) tilecnt[i] = (uint32_t)(carry + before + x - v);
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int64_t base = level_base(l), nb = level_size(l);
+        const int64_t W0 = woff[base], S0 = soff[base];
+        woff[base + nb] = (int32_t)min(W0 + carry, (int64_t)INT32_MAX);
+        soff[base + nb] = (int32_t)min(S0 + (nc - carry), (int64_t)INT32_MAX);
+    }
+}
+
+// Scatter the candidates into the weak and strong lists and write the box offsets.  The tile
+// prefix of weak flags is tilecnt[tile]; the strong prefix is its complement.
+__global__ void __launch_bounds__(LT) k_lists_fill(int l, const uint8_t* __restrict__ flags,
+                                                   const uint32_t* __restrict__ tilecnt, int64_t scap,
+                                                   int64_t wcap, int32_t* woff, int32_t* widx,
+                                                   int32_t* wtgt, int32_t* soff, int32_t* sidx,
+                                                   int32_t* stgt)
+{
+    __shared__ uint32_t wsum[LI][LT / 32];
+    const LevelCands lc = level_cands(soff, l, scap);
+    const int64_t nc = lc.count();
+    const int64_t ntiles = (nc + LTILE - 1) / LTILE;
+    const int64_t base = level_base(l);
+    const int64_t W0 = woff[base], S0 = soff[base];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint8_t f[LI];
+        uint32_t pre[LI];
+#pragma unroll
+        for (int j = 0; j < LI; j++) {
+            const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
+            f[j] = t < nc ? flags[t] : 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, f[j]);
+            pre[j] = __popc(bal & lt);
+            if (lane == 0) wsum[j][w] = __popc(bal);
+        }
+        __syncthreads();
+        // exclusive prefix in (row j, warp) order = candidate order inside the tile
+        uint32_t run = tilecnt[tile];
+#pragma unroll
+        for (int j = 0; j < LI; j++) {
+            uint32_t before = 0;
+            for (int ww = 0; ww < LT / 32; ww++) {
+                if (ww == w) before = run;
+                run += wsum[j][ww];
+            }
+            const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
+            if (t < nc) {
+                int64_t b, c;
+                bool first;
+                decode(soff, sidx, l, scap, lc, t, b, c, first);
+                const int64_t wpre = (int64_t)before + pre[j];  // weak candidates before t
+                const int64_t spre = t - wpre;                   // strong candidates before t
+                if (first) {
+                    woff[base + b] = (int32_t)min(W0 + wpre, (int64_t)INT32_MAX);
+                    soff[base + b] = (int32_t)min(S0 + spre, (int64_t)INT32_MAX);
+                }
+                if (f[j]) {
+                    const int64_t pos = W0 + wpre;
+                    if (pos < wcap) {
+                        widx[pos] = (int32_t)c;
+                        wtgt[pos] = (int32_t)(base + b);
+                    }
+                } else {
+                    const int64_t pos = S0 + spre;
+                    if (pos < scap) {
+                        sidx[pos] = (int32_t)c;
+                        stgt[pos] = (int32_t)(base + b);
+                    }
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -101,25 +278,21 @@ __global__ void k_lists_check(const int32_t* woff, const int32_t* soff, int64_t 
 
 }  // namespace
 
+int64_t lists_flag_bytes(int64_t scap) { return 16 * scap + LTILE; }
+int64_t lists_tile_words(int64_t scap) { return (16 * scap + LTILE - 1) / LTILE + 1; }
+
 int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s)
 {
     const int L = t->L;
     StageScope scope(FMM_STAGE_LISTS, s);
-    k_lists_root<<<1, 32, 0, s>>>(li->woff, li->soff, li->sidx); note_launch();
+    k_lists_root<<<1, 32, 0, s>>>(li->woff, li->soff, li->sidx, li->stgt); note_launch();
     for (int l = 1; l <= L; l++) {
-        int64_t nb = level_size(l);
-        unsigned blocks = (unsigned)((nb * 32 + 255) / 256);
-        k_lists<false><<<blocks, 256, 0, s>>>(l, t->centers, t->radii, theta, li->woff, li->widx,
-                                              li->wcap, li->soff, li->sidx, li->scap, li->wcnt,
-                                              li->scnt); note_launch();
-        int64_t base = level_base(l);
-        int rc = scan_with_base(li->wcnt, nb, li->woff + base, li->woff + base, li->scan_tmp, s);
-        if (rc) return rc;
-        rc = scan_with_base(li->scnt, nb, li->soff + base, li->soff + base, li->scan_tmp, s);
-        if (rc) return rc;
-        k_lists<true><<<blocks, 256, 0, s>>>(l, t->centers, t->radii, theta, li->woff, li->widx,
-                                             li->wcap, li->soff, li->sidx, li->scap, li->wcnt,
-                                             li->scnt); note_launch();
+        k_lists_flags<<<LGRID, LT, 0, s>>>(l, t->centers, t->radii, t->cen_hi, t->cen_lo, t->rad32,
+                                           theta, li->soff, li->sidx,
+                                           li->scap, li->flags, li->tilecnt); note_launch();
+        k_lists_scan<<<1, 1024, 0, s>>>(l, li->scap, li->tilecnt, li->woff, li->soff); note_launch();
+        k_lists_fill<<<LGRID, LT, 0, s>>>(l, li->flags, li->tilecnt, li->scap, li->wcap, li->woff,
+                                          li->widx, li->wtgt, li->soff, li->sidx, li->stgt); note_launch();
         FMM_LAUNCH_CHECK("lists");
     }
     k_lists_check<<<1, 32, 0, s>>>(li->woff, li->soff, t->nbox, li->wcap, li->scap, li->status); note_launch();

@@ -408,7 +408,8 @@ __global__ void k_leaf_of(const int32_t* __restrict__ X, int64_t n, int L, uint3
 // correctly rounded binary64 operations as the criterion's reference; plus a float-float copy
 // of the centre for the binary32 path.
 __global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, double* __restrict__ cen,
-                           double* __restrict__ rad, float* __restrict__ chi, float* __restrict__ clo)
+                           double* __restrict__ rad, float* __restrict__ rad32, float* __restrict__ chi,
+                           float* __restrict__ clo)
 {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nbox) return;
@@ -417,7 +418,9 @@ __global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, doubl
     double cx = midpoint(r[0], r[1]), cy = midpoint(r[2], r[3]);
     cen[2 * g] = cx;
     cen[2 * g + 1] = cy;
-    rad[g] = __dmul_rn(0.5, __dsqrt_rn(__dadd_rn(__dmul_rn(w, w), __dmul_rn(h, h))));
+    const double rg = __dmul_rn(0.5, __dsqrt_rn(__dadd_rn(__dmul_rn(w, w), __dmul_rn(h, h))));
+    rad[g] = rg;
+    rad32[g] = __double2float_rn(rg);
     float hx = __double2float_rn(cx), hy = __double2float_rn(cy);
     chi[2 * g] = hx;
     chi[2 * g + 1] = hy;
@@ -429,11 +432,13 @@ __global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, doubl
 __global__ void k_gather_points(const int32_t* __restrict__ perm, const uint32_t* __restrict__ leaf_of,
                                 const double* __restrict__ x, const double* __restrict__ y, int64_t n,
                                 int L, const double* __restrict__ cen, double* __restrict__ xs,
-                                double* __restrict__ ys, float* __restrict__ dxf, float* __restrict__ dyf)
+                                double* __restrict__ ys, float* __restrict__ dxf, float* __restrict__ dyf,
+                                int32_t* __restrict__ cleaf)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t id = perm[i];
+        cleaf[i] = (int32_t)leaf_of[id];
         int64_t g = level_base(L) + leaf_of[id];
         double a = x[id], b = y[id];
         xs[i] = a;
@@ -492,11 +497,13 @@ int tree_alloc(fmm_tree t)
     if ((rc = A((void**)&t->rects, 32 * nb))) return rc;
     if ((rc = A((void**)&t->centers, 16 * nb))) return rc;
     if ((rc = A((void**)&t->radii, 8 * nb))) return rc;
+    if ((rc = A((void**)&t->rad32, 4 * nb))) return rc;
     if ((rc = A((void**)&t->cen_hi, 8 * nb))) return rc;
     if ((rc = A((void**)&t->cen_lo, 8 * nb))) return rc;
     if ((rc = A((void**)&t->perm, 4 * nn))) return rc;
     if ((rc = A((void**)&t->leaf_begin, 4 * lb.size()))) return rc;
     if ((rc = A((void**)&t->leaf_of, 4 * nn))) return rc;
+    if ((rc = A((void**)&t->cleaf, 4 * nn))) return rc;
     if ((rc = A((void**)&t->xs, 8 * nn))) return rc;
     if ((rc = A((void**)&t->ys, 8 * nn))) return rc;
     if ((rc = A((void**)&t->dxf, 4 * nn))) return rc;
@@ -582,9 +589,9 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
 
         int64_t nb = t->nbox;
         k_geometry<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(t->rects, nb, t->centers, t->radii,
-                                                                t->cen_hi, t->cen_lo); note_launch();
+                                                                t->rad32, t->cen_hi, t->cen_lo); note_launch();
         k_gather_points<<<grid_for(n, 256), 256, 0, s>>>(t->perm, leaf_of, x, y, n, L, t->centers,
-                                                         t->xs, t->ys, t->dxf, t->dyf); note_launch();
+                                                         t->xs, t->ys, t->dxf, t->dyf, t->cleaf); note_launch();
         FMM_LAUNCH_CHECK("tree: canonical order");
     }
     t->built = true;

@@ -132,14 +132,15 @@ def test_direct_kernel(fmmlib, orc, cuda):
 
 
 def test_reuse_and_repeat(built, cuda, orc):
-    # one tree serves many strength vectors; repeated calls give identical results
+    # one tree serves many strength vectors; repeated calls agree to rounding (partial sums are
+    # combined with atomics, so their order, and the last bits, may differ between calls)
     c, L, f = built["clusters"]
     g = np.random.default_rng(3)
     for _ in range(2):
         q = g.standard_normal(c.x.shape[0])
         a = f.evaluate(_t(q, cuda), 12, "fp64").cpu().numpy()
         b = f.evaluate(_t(q, cuda), 12, "fp64").cpu().numpy()
-        assert np.array_equal(a, b)
+        assert relerr(a, b) <= 1e-14
         assert relerr(a, orc.fmm(c.x, c.y, q, L, 12, 0.5)) <= TOL_FP64
 
 
