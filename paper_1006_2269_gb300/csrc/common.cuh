@@ -4,8 +4,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <vector>
-
 #include "../../include/fmm.h"
 
 namespace fmm {
@@ -43,6 +41,9 @@ struct StageScope {
 // ---- level-order box numbering ----
 __host__ __device__ inline int64_t level_base(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 __host__ __device__ inline int64_t level_size(int l) { return int64_t(1) << (2 * l); }
+
+// The per-depth tables of ones_before are concatenated: depth d starts at 2^d - 1.
+__host__ __device__ inline int64_t ones_before_offset(int depth) { return (int64_t(1) << depth) - 1; }
 
 // Descend the floor-left binary split tree of n positions by `depth` steps towards position
 // `pos`; returns the index j of the node at that depth and its offset o and size m.  A node of
@@ -122,7 +123,6 @@ struct fmm_tree_s {
     uint8_t* hflag = nullptr;       // [2][n] per input index: x-half / y-half bit
     uint64_t* bbox_keys = nullptr;  // [4] ordered keys of xmin, xmax, ymin, ymax
     int32_t* ones_before = nullptr;  // concatenated per depth 0 .. 2L-1: [2^depth]
-    std::vector<int64_t> ob_off;     // host: offset of each depth's table
     int32_t* status = nullptr;       // device status word
 
     // expansion workspace (allocated by the first evaluate that needs it; PS = padded P)

@@ -12,6 +12,7 @@
 // segment by integer arithmetic, and the stable partitions are one global scan of the flag bits
 // plus a per-segment correction taken from a host-computed table.
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -468,9 +469,7 @@ int tree_alloc(fmm_tree t)
     // floor-left split sizes per depth; ones-before tables for depths 0 .. 2L-1; leaf offsets
     std::vector<int64_t> sizes{n}, next;
     std::vector<int32_t> ob_all;
-    t->ob_off.clear();
     for (int d = 0; d < 2 * L; d++) {
-        t->ob_off.push_back((int64_t)ob_all.size());
         int64_t acc = 0;
         for (int64_t m : sizes) {
             ob_all.push_back((int32_t)acc);
@@ -558,7 +557,7 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
             k_part_count<<<(unsigned)nt, TPB, 0, s>>>(Y, hx, n, t->tilecnt); note_launch();
             k_scan_tiles<<<1, 1024, 0, s>>>(t->tilecnt, nt); note_launch();
             k_part_scatter<<<(unsigned)nt, TPB, 0, s>>>(Y, Yo, hx, hy, n, 2 * l,
-                                                        t->ones_before + t->ob_off[2 * l], t->tilecnt,
+                                                        t->ones_before + ones_before_offset(2 * l), t->tilecnt,
                                                         t->status); note_launch();
             std::swap(Y, Yo);
             // split coordinates and child rectangles of level l
@@ -568,7 +567,7 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
             k_part_count<<<(unsigned)nt, TPB, 0, s>>>(X, hy, n, t->tilecnt); note_launch();
             k_scan_tiles<<<1, 1024, 0, s>>>(t->tilecnt, nt); note_launch();
             k_part_scatter<<<(unsigned)nt, TPB, 0, s>>>(X, Xo, hy, hx, n, 2 * l + 1,
-                                                        t->ones_before + t->ob_off[2 * l + 1], t->tilecnt,
+                                                        t->ones_before + ones_before_offset(2 * l + 1), t->tilecnt,
                                                         t->status); note_launch();
             std::swap(X, Xo);
             FMM_LAUNCH_CHECK("tree: level split");
