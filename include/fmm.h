@@ -101,6 +101,37 @@ int fmm_tree_info(fmm_tree t, int64_t* n, int* levels, int64_t* nbox);
 void fmm_tree_destroy(fmm_tree t);
 
 /* ---------------------------------------------------------------------------------------------
+ * Tree construction that allocates nothing.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running while its stream is
+ * captured into a CUDA graph (an allocation cannot be captured), code inside an application
+ * whose own memory manager owns the device, or latency-critical loops that cannot take the
+ * synchronisation a cudaMalloc/cudaFree may cause.  It computes exactly what fmm_build_tree
+ * followed by fmm_tree_export computes, but every intermediate buffer lives in one fixed device
+ * array compiled into the library (about 6.4 MB, held on every GPU that loads the library until
+ * the process exits), so inputs are limited to n <= FMM_NOALLOC_MAX_POINTS points and
+ * levels <= FMM_NOALLOC_MAX_LEVELS.
+ *
+ *   x[n], y[n]         point coordinates (binary64, device)
+ *   perm[n]            output, as fmm_tree_export
+ *   rects[4*nbox]      output, nbox = (4^(levels+1)-1)/3, as fmm_tree_export
+ *   leaf_begin[4^levels + 1]  output, as fmm_tree_export
+ *   status             optional (NULL or one device int32): receives the device status word of
+ *                      the build (0, or FMM_ERR_NONFINITE's bit 1 for non-finite coordinates)
+ *
+ * Returns FMM_ERR_ARG for sizes beyond the limits (nothing is launched) and FMM_ERR_LEVELS when
+ * n < 4^levels.  It calls no cudaMalloc, cudaFree or other allocating routine.  All calls share
+ * the one array, so calls on the same device must not overlap in time (two streams or two host
+ * threads running it at once corrupt each other's results).  The first call on a device looks
+ * up the array's address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * ------------------------------------------------------------------------------------------- */
+#define FMM_NOALLOC_MAX_POINTS 65536
+#define FMM_NOALLOC_MAX_LEVELS 7
+
+int fmm_build_tree_noalloc(const double* x, const double* y, int64_t n, int levels,
+                           int32_t* perm, double* rects, int32_t* leaf_begin, int32_t* status,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Interaction lists: Section 4 with Criterion 2.1.
  * S(root) = {root}, W(root) = {}.  For a box b of level l >= 1 the candidates are the children
  * of every box of S(parent(b)) in ascending id; a candidate c joins W(b) when

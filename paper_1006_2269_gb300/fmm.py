@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH):
             "fmm_evaluate": (i32, [vp, vp, vp, ctypes.POINTER(fmm_params), vp, vp]),
             "fmm_direct": (i32, [vp, vp, vp, i64, vp, i64, vp, vp]),
             "fmm_sync_status": (i32, [vp, vp, vp]),
+            "fmm_build_tree_noalloc": (i32, [vp, vp, i64, i32, vp, vp, vp, vp, vp]),
             "fmm_profile_enable": (i32, [i32]),
             "fmm_profile_read": (i32, [vp, vp, i32]),
             "fmm_launch_count": (i64, []),
@@ -128,6 +129,24 @@ def fmm_build_tree(tree, x: torch.Tensor, y: torch.Tensor, stream=None):
     n = fmm_tree_info(tree)[0]
     _check(load_library().fmm_build_tree(tree, _dev(x, torch.float64, n, "x"),
                                          _dev(y, torch.float64, n, "y"), _stream(stream)))
+
+
+FMM_NOALLOC_MAX_POINTS = 65536
+FMM_NOALLOC_MAX_LEVELS = 7
+
+
+def fmm_build_tree_noalloc(x, y, levels: int, perm, rects, leaf_begin, status=None, stream=None):
+    """Tree build for callers that cannot allocate device memory: the outputs are the caller's
+    tensors, every intermediate lives in the library's fixed device array (n <= 65536,
+    levels <= 7).  Calls on one device must not overlap in time."""
+    n = x.numel()
+    _check(load_library().fmm_build_tree_noalloc(_dev(x, torch.float64, n, "x"),
+                                                 _dev(y, torch.float64, n, "y"), n, int(levels),
+                                                 _dev(perm, torch.int32, n, "perm"),
+                                                 _dev(rects, torch.float64, None, "rects"),
+                                                 _dev(leaf_begin, torch.int32, None, "leaf_begin"),
+                                                 _dev(status, torch.int32, 1, "status"),
+                                                 _stream(stream)))
 
 
 def fmm_tree_export(tree, perm=None, rects=None, leaf_begin=None, stream=None):
