@@ -158,6 +158,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one instead of replaying a CUDA graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -200,6 +201,19 @@ def main():
         fmm.fmm_interaction_lists(f.tree, f.lists, w.theta)
         fmm.fmm_evaluate(f.tree, f.lists, q, w.p, mode, phi)
 
+    def capture(mode):
+        """The whole step (tree, lists, evaluation: ~140 kernels) as one CUDA graph."""
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            step(mode)
+        torch.cuda.current_stream().wait_stream(side)
+        with torch.cuda.graph(g):
+            step(mode)
+        torch.cuda.synchronize()
+        return g
+
     # warm-up, then the accuracy check against the binary64 direct sum at sampled targets
     for _ in range(args.warmup):
         step(fmm.FMM_MODE_MIXED)
@@ -217,6 +231,14 @@ def main():
     err_fp64 = (phi[tg] - ref).abs().max().item() / scale
     nweak, npairs = pair_counts(f)
 
+    graphs = {}
+    if not args.no_graph:
+        try:
+            graphs = {m: capture(m) for m in (fmm.FMM_MODE_MIXED, fmm.FMM_MODE_FP64)}
+        except Exception as exc:  # report and time plain launches instead
+            print(f"graph capture failed: {exc}", file=sys.stderr)
+            graphs = {}
+
     def timed(mode, steps, e2e=False, profile=False):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -233,12 +255,17 @@ def main():
                 x.copy_(xh, non_blocking=True)
                 y.copy_(yh, non_blocking=True)
                 q.copy_(qh, non_blocking=True)
-            step(mode)
+            if mode in graphs and not profile:
+                graphs[mode].replay()
+            else:
+                step(mode)
             if e2e:
                 phi_h.copy_(phi, non_blocking=True)
             ends[i].record(stream)
         torch.cuda.synchronize()
         launches = fmm.fmm_launch_count() - l0
+        if mode in graphs and not profile:
+            launches = per_step_launches * steps
         fmm.fmm_profile_enable(False)
         prof = fmm.fmm_profile_read()
         if world > 1:
@@ -249,9 +276,12 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return t.item(), launches, prof
 
+    l0 = fmm.fmm_launch_count()
+    step(fmm.FMM_MODE_MIXED)
+    per_step_launches = fmm.fmm_launch_count() - l0
+    _, _, prof = timed(fmm.FMM_MODE_MIXED, args.steps, profile=True)
     with ClockSampler(local) as clk:
-        ms_mixed, launches, prof = timed(fmm.FMM_MODE_MIXED, args.steps, profile=True)
-    ms_mixed_plain, _, _ = timed(fmm.FMM_MODE_MIXED, args.steps)
+        ms_mixed_plain, launches, _ = timed(fmm.FMM_MODE_MIXED, args.steps)
     ms_e2e, _, _ = timed(fmm.FMM_MODE_MIXED, args.steps, e2e=True)
     ms_fp64, _, prof64 = timed(fmm.FMM_MODE_FP64, args.fp64_steps, profile=True)
     fmm.fmm_sync_status(f.tree, f.lists)
@@ -293,7 +323,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "n": n, "levels": w.levels, "theta": w.theta, "p": w.p,
                    "mode": "mixed", "l2": "flushed between steps (256 MB write outside the events)",
-                   "replicas": world},
+                   "replicas": world, "cuda_graph": bool(graphs)},
         "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,
         "fp64_path": {"value": world * n / (ms_fp64 / args.fp64_steps * 1e-3),
                       "ms_per_step": ms_fp64 / args.fp64_steps, "stages_ms": stage_ms64},

@@ -107,7 +107,7 @@ void fmm_tree_destroy(fmm_tree t);
  * whose own memory manager owns the device, or latency-critical loops that cannot take the
  * synchronisation a cudaMalloc/cudaFree may cause.  It computes exactly what fmm_build_tree
  * followed by fmm_tree_export computes, but every intermediate buffer lives in one fixed device
- * array compiled into the library (about 6.4 MB, held on every GPU that loads the library until
+ * array compiled into the library (about 7.7 MB, held on every GPU that loads the library until
  * the process exits), so inputs are limited to n <= FMM_NOALLOC_MAX_POINTS points and
  * levels <= FMM_NOALLOC_MAX_LEVELS.
  *

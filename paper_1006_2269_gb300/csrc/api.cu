@@ -94,8 +94,8 @@ void free_tree(fmm_tree t)
     if (!t) return;
     void* ptrs[] = {t->rects, t->centers, t->radii, t->rad32, t->cen_hi, t->cen_lo, t->perm, t->leaf_begin,
                     t->leaf_of, t->xs, t->ys, t->dxf, t->dyf, t->keys, t->vals, t->rs_counts,
-                    t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->status,
-                    t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->cleaf};
+                    t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->node_off, t->segs, t->status,
+                    t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete t;

@@ -38,12 +38,20 @@ struct StageScope {
     ~StageScope() { prof_mark(stage, false, s); }
 };
 
+// Items per tile of the tree-build kernels (sorts and partitions): TREE_TPB threads x TREE_ITEMS.
+constexpr int TREE_TPB = 256;
+constexpr int TREE_ITEMS = 4;
+constexpr int TREE_TILE = TREE_TPB * TREE_ITEMS;
+
 // ---- level-order box numbering ----
 __host__ __device__ inline int64_t level_base(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 __host__ __device__ inline int64_t level_size(int l) { return int64_t(1) << (2 * l); }
 
 // The per-depth tables of ones_before are concatenated: depth d starts at 2^d - 1.
 __host__ __device__ inline int64_t ones_before_offset(int depth) { return (int64_t(1) << depth) - 1; }
+
+// Node offsets of depth d (2^d + 1 entries each) start at 2^d - 1 + d.
+__host__ __device__ inline int64_t node_offset_base(int depth) { return (int64_t(1) << depth) - 1 + depth; }
 
 // Descend the floor-left binary split tree of n positions by `depth` steps towards position
 // `pos`; returns the index j of the node at that depth and its offset o and size m.  A node of
@@ -123,6 +131,8 @@ struct fmm_tree_s {
     uint8_t* hflag = nullptr;       // [2][n] per input index: x-half / y-half bit
     uint64_t* bbox_keys = nullptr;  // [4] ordered keys of xmin, xmax, ymin, ymax
     int32_t* ones_before = nullptr;  // concatenated per depth 0 .. 2L-1: [2^depth]
+    int32_t* node_off = nullptr;     // node offsets per depth 0 .. 2L: [2^depth + 1]
+    int32_t* segs = nullptr;         // [4][n] box index carried by the items of X and Y
     int32_t* status = nullptr;       // device status word
 
     // expansion workspace (allocated by the first evaluate that needs it; PS = padded P)
@@ -133,7 +143,8 @@ struct fmm_tree_s {
     void* Lf = nullptr;   // binary32 locals     [nbox][PS]
     void* pk64 = nullptr;   // [n] double4 (x, y, q, 0) in canonical order (binary64 path)
     void* pk32 = nullptr;   // [n] float4 (x - c_leaf, y - c_leaf, q, 0) (binary32 path)
-    double* acc = nullptr;  // [n] potential accumulator in canonical order
+    double* acc = nullptr;  // [n] binary64 potential accumulator in canonical order
+    float* acc32 = nullptr; // [3n] binary32 far field, near-field hi and lo (canonical order)
     bool built = false;
 };
 

@@ -88,27 +88,48 @@ __device__ __forceinline__ int level_of(int64_t g)
     return (63 - __clzll((unsigned long long)(3 * g + 1))) >> 1;
 }
 
-// z0 = c_src - c_tgt: in binary64 directly, in binary32 from the float-float centres so that
-// the difference of two nearby centres keeps its relative accuracy.
+// Box geometry in the working precision.  z0 = c_a - c_b: in binary64 directly, in binary32 from
+// the float-float centres so that the difference of two nearby centres keeps its relative
+// accuracy.  The binary32 path never touches binary64 arithmetic (slow on this GPU): radii come
+// from a binary32 copy and point coordinates are binary32 offsets from their leaf centre.
 template <typename T>
 struct Geo;
 template <>
 struct Geo<double> {
     const double* cen;
+    const double* rad;
     __device__ __forceinline__ cx<double> diff(int64_t a, int64_t b) const
     {
         return {cen[2 * a] - cen[2 * b], cen[2 * a + 1] - cen[2 * b + 1]};
+    }
+    __device__ __forceinline__ double radius(int64_t g) const { return rad[g]; }
+    // (z - c_g) / rho_g for a point stored with absolute coordinates (0 when rho_g = 0)
+    __device__ __forceinline__ cx<double> local(int64_t g, double x, double y) const
+    {
+        const double rho = rad[g];
+        if (!(rho > 0.0)) return {0.0, 0.0};
+        return {(x - cen[2 * g]) / rho, (y - cen[2 * g + 1]) / rho};
     }
 };
 template <>
 struct Geo<float> {
     const float* hi;
     const float* lo;
+    const float* rad;
     __device__ __forceinline__ cx<float> diff(int64_t a, int64_t b) const
     {
         float2 ha = *(const float2*)(hi + 2 * a), hb = *(const float2*)(hi + 2 * b);
         float2 la = *(const float2*)(lo + 2 * a), lb = *(const float2*)(lo + 2 * b);
         return {(ha.x - hb.x) + (la.x - lb.x), (ha.y - hb.y) + (la.y - lb.y)};
+    }
+    __device__ __forceinline__ float radius(int64_t g) const { return rad[g]; }
+    // the point is stored as its offset from the centre of leaf g
+    __device__ __forceinline__ cx<float> local(int64_t g, float x, float y) const
+    {
+        const float rho = rad[g];
+        if (!(rho > 0.f)) return {0.f, 0.f};
+        const float inv = 1.f / rho;
+        return {x * inv, y * inv};
     }
 };
 
@@ -156,8 +177,7 @@ __global__ void k_pack(const int32_t* __restrict__ perm, const double* __restric
 // ---- P2M: one warp per leaf, one lane per point; column sums through shared memory ----
 template <typename T>
 __global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, const Pk<T>* __restrict__ pk,
-                      const double* __restrict__ cen, const double* __restrict__ rad,
-                      cx<T>* __restrict__ Me)
+                      Geo<T> geo, cx<T>* __restrict__ Me)
 {
     extern __shared__ unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -165,28 +185,18 @@ __global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, cons
     if (b >= level_size(L)) return;
     cx<T>* S = (cx<T>*)smem + (size_t)w * 33 * P;
     const int64_t g = level_base(L) + b;
-    const double rho = rad[g];
     const int32_t t0 = lb[b], t1 = lb[b + 1];
     cx<T> acc[2] = {{0, 0}, {0, 0}};
     for (int32_t tb = t0; tb < t1; tb += 32) {
         const int32_t t = tb + lane;
-        T xr = 0, xi = 0, qq = 0;
+        T qq = 0;
+        cx<T> xi_c = {0, 0};
         if (t < t1) {
             const Pk<T> p = pk[t];
             qq = p.q;
-            if (rho > 0) {
-                if (sizeof(T) == 8) {
-                    xr = (T)(((double)p.x - cen[2 * g]) / rho);
-                    xi = (T)(((double)p.y - cen[2 * g + 1]) / rho);
-                } else {
-                    const T inv = (T)(1.0 / rho);
-                    xr = p.x * inv;
-                    xi = p.y * inv;
-                }
-            }
+            xi_c = geo.local(g, p.x, p.y);
         }
         cx<T> pw = {qq, 0};
-        const cx<T> xi_c = {xr, xi};
         for (int k = 0; k < P; k++) {
             S[k * 33 + lane] = pw;
             pw = cmul(pw, xi_c);
@@ -200,7 +210,7 @@ __global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, cons
         __syncwarp();
     }
     for (int k = lane, s = 0; k < P; k += 32, s++)
-        Me[g * PS + k] = k == 0 ? acc[s] : cscale(acc[s], (T)(-1.0 / k));
+        Me[g * PS + k] = k == 0 ? acc[s] : cscale(acc[s], (T)-1 / (T)k);
 }
 
 // Binomial table C(n, k), n, k < P, copied to shared memory by the whole block.
@@ -213,8 +223,7 @@ __device__ __forceinline__ void load_binom(T* B, int P)
 
 // ---- M2M: one warp per parent, one lane per output coefficient ----
 template <typename T>
-__global__ void k_m2m(int l, int P, int PS, const double* __restrict__ cen,
-                      const double* __restrict__ rad, cx<T>* __restrict__ Me)
+__global__ void k_m2m(int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Me)
 {
     extern __shared__ unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -224,15 +233,16 @@ __global__ void k_m2m(int l, int P, int PS, const double* __restrict__ cen,
     const int64_t b = (int64_t)blockIdx.x * wpb + w;
     if (b >= level_size(l)) return;
     const int64_t g = level_base(l) + b;
-    const double rp = rad[g];
+    const T rp = geo.radius(g);
     cx<T> acc[2] = {{0, 0}, {0, 0}};
     for (int k = 0; k < 4; k++) {
         const int64_t cg = level_base(l + 1) + 4 * b + k;
         cx<T> wv = {0, 0};
         T s = 0;
         if (rp > 0) {
-            wv = {(T)((cen[2 * cg] - cen[2 * g]) / rp), (T)((cen[2 * cg + 1] - cen[2 * g + 1]) / rp)};
-            s = (T)(rad[cg] / rp);
+            const T ir = (T)1 / rp;
+            wv = cscale(geo.diff(cg, g), ir);
+            s = geo.radius(cg) * ir;
         }
         for (int j = lane; j < P; j += 32) D[j] = cscale(Me[cg * PS + j], ipow(s, j));
         __syncwarp();
@@ -241,7 +251,7 @@ __global__ void k_m2m(int l, int P, int PS, const double* __restrict__ cen,
             if (o == 0) {
                 h = D[0];
             } else {
-                h = cscale(D[0], (T)(-1.0 / o));
+                h = cscale(D[0], (T)-1 / (T)o);
                 for (int j = 1; j <= o; j++) h = cfma(h, wv, cscale(D[j], B[(o - 1) * P + (j - 1)]));
             }
             acc[si] = cadd(acc[si], h);
@@ -259,7 +269,7 @@ template <typename T, int PI>
 __global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t* __restrict__ woff,
                                                    const int32_t* __restrict__ widx,
                                                    const int32_t* __restrict__ wtgt, int64_t wcap,
-                                                   int64_t nbox, Geo<T> geo, const double* __restrict__ rad,
+                                                   int64_t nbox, Geo<T> geo,
                                                    const cx<T>* __restrict__ Me, cx<T>* __restrict__ Le)
 {
     const int lane = threadIdx.x & 31;
@@ -294,7 +304,7 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t*
             const T r2 = z0.re * z0.re + z0.im * z0.im;
             const T ir2 = (T)1 / r2;
             const cx<T> inv = {z0.re * ir2, -z0.im * ir2};
-            const cx<T> u2 = cscale(inv, (T)(-2.0 * rad[sg])), v2 = cscale(inv, (T)(2.0 * rad[g]));
+            const cx<T> u2 = cscale(inv, (T)-2 * geo.radius(sg)), v2 = cscale(inv, (T)2 * geo.radius(g));
             const cx<T>* src = Me + sg * PS;
             const T a0 = src[0].re;
             cx<T> x[PI];
@@ -357,7 +367,6 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(int P, int PS, const int32
                                                       const int32_t* __restrict__ widx,
                                                       const int32_t* __restrict__ wtgt, int64_t wcap,
                                                       int64_t nbox, Geo<double> geo,
-                                                      const double* __restrict__ rad,
                                                       const cx<double>* __restrict__ Me,
                                                       cx<double>* __restrict__ Le)
 {
@@ -390,7 +399,7 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(int P, int PS, const int32
             const double r2 = z0.re * z0.re + z0.im * z0.im;
             const double ir2 = 1.0 / r2;
             const cx<double> inv = {z0.re * ir2, -z0.im * ir2};
-            const cx<double> u2 = cscale(inv, -2.0 * rad[sg]), v2 = cscale(inv, 2.0 * rad[g]);
+            const cx<double> u2 = cscale(inv, -2.0 * geo.radius(sg)), v2 = cscale(inv, 2.0 * geo.radius(g));
             const cx<double>* src = Me + sg * PS;
             const double a0 = src[0].re;
             X[tid] = {a0, 0};
@@ -436,8 +445,7 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(int P, int PS, const int32
 
 // ---- L2L: one warp per child box of level l+1 ----
 template <typename T>
-__global__ void k_l2l(int l, int P, int PS, const double* __restrict__ cen, const double* __restrict__ rad,
-                      cx<T>* __restrict__ Le)
+__global__ void k_l2l(int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Le)
 {
     extern __shared__ unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -447,12 +455,13 @@ __global__ void k_l2l(int l, int P, int PS, const double* __restrict__ cen, cons
     const int64_t c = (int64_t)blockIdx.x * wpb + w;
     if (c >= level_size(l + 1)) return;
     const int64_t cg = level_base(l + 1) + c, pg = level_base(l) + (c >> 2);
-    const double rp = rad[pg];
+    const T rp = geo.radius(pg);
     cx<T> wv = {0, 0};
     T s = 0;
     if (rp > 0) {
-        wv = {(T)((cen[2 * cg] - cen[2 * pg]) / rp), (T)((cen[2 * cg + 1] - cen[2 * pg + 1]) / rp)};
-        s = (T)(rad[cg] / rp);
+        const T ir = (T)1 / rp;
+        wv = cscale(geo.diff(cg, pg), ir);
+        s = geo.radius(cg) * ir;
     }
     for (int j = lane; j < P; j += 32) B[j] = Le[pg * PS + j];
     __syncwarp();
@@ -465,30 +474,22 @@ __global__ void k_l2l(int l, int P, int PS, const double* __restrict__ cen, cons
 }
 
 // ---- L2P: one thread per point (canonical order); initialises the accumulator ----
+// binary64 path: writes the binary64 accumulator.  binary32 path: writes the binary32 far field;
+// the near-field accumulators are combined with it at the end.
 template <typename T>
 __global__ void k_l2p(int L, int P, int PS, int64_t n, const int32_t* __restrict__ cleaf,
-                      const Pk<T>* __restrict__ pk, const double* __restrict__ cen,
-                      const double* __restrict__ rad, const cx<T>* __restrict__ Le,
-                      double* __restrict__ acc)
+                      const Pk<T>* __restrict__ pk, Geo<T> geo, const cx<T>* __restrict__ Le,
+                      T* __restrict__ far)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = level_base(L) + cleaf[i];
-        const double rho = rad[g];
         const Pk<T> p = pk[i];
-        cx<T> z = {0, 0};
-        if (rho > 0) {
-            if (sizeof(T) == 8) {
-                z = {(T)(((double)p.x - cen[2 * g]) / rho), (T)(((double)p.y - cen[2 * g + 1]) / rho)};
-            } else {
-                const T inv = (T)(1.0 / rho);
-                z = {p.x * inv, p.y * inv};
-            }
-        }
+        const cx<T> z = geo.local(g, p.x, p.y);
         const cx<T>* B = Le + g * PS;
         cx<T> h = B[P - 1];
         for (int k = P - 2; k >= 0; k--) h = cfma(h, z, B[k]);
-        acc[i] = (double)h.re;
+        far[i] = h.re;
     }
 }
 
@@ -515,6 +516,8 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float v)
 // Leaves of at most 32 points: groups of gs = pow2ceil(max leaf size) lanes, one lane per target;
 // the G = 32/gs groups of a warp walk the warp's P2P_CH consecutive pairs round robin, each group
 // one whole source leaf at a time.
+// Accumulators: binary64 path acc64 (holds the far field already); binary32 path nhi/nlo, the
+// float-float near-field sums in log2 units (flushed with binary32 atomics).
 template <typename T>
 __global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t* __restrict__ soff,
                                                    const int32_t* __restrict__ sidx,
@@ -525,8 +528,9 @@ __global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t*
                                                    const double* __restrict__ ys,
                                                    const float* __restrict__ chi,
                                                    const float* __restrict__ clo,
-                                                   const double* __restrict__ rad,
-                                                   double* __restrict__ acc)
+                                                   const float* __restrict__ rad32,
+                                                   double* __restrict__ acc64, float* __restrict__ nhi,
+                                                   float* __restrict__ nlo)
 {
     constexpr bool F32 = sizeof(T) == 4;
     const int lane = threadIdx.x & 31, G = 32 / gs, grp = lane / gs, ti = lane & (gs - 1);
@@ -535,7 +539,6 @@ __global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t*
     const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double scale = F32 ? 0.5 * 0.69314718055994530942 : 0.5;
     for (int64_t e0 = e_begin + warp * P2P_CH; e0 < e_end; e0 += nwarps * P2P_CH) {
         const int64_t e1 = min(e0 + P2P_CH, e_end);
         int64_t cur = -1;
@@ -547,7 +550,14 @@ __global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t*
         for (int64_t e = e0 + grp; e < e1; e += G) {
             const int64_t tl = stgt[e] - base;
             if (tl != cur) {
-                if (active) atomicAdd(&acc[it], F32 ? ((double)hi + (double)lo) * scale : sum64 * scale);
+                if (active) {
+                    if (F32) {
+                        atomicAdd(&nhi[it], hi);
+                        atomicAdd(&nlo[it], lo);
+                    } else {
+                        atomicAdd(&acc64[it], 0.5 * sum64);
+                    }
+                }
                 cur = tl;
                 const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0;
                 active = ti < nt;
@@ -568,7 +578,7 @@ __global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t*
                 const float ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
                 const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
                 const float xt = tx - ox, yt = ty - oy;
-                const float M = (float)rad[sg] + (float)rad[tg] + fabsf(ox) + fabsf(oy);
+                const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
                 const float tau2 = (M * (1.f / 64.f)) * (M * (1.f / 64.f));
                 float part = 0.f;
 #pragma unroll 4
@@ -596,7 +606,14 @@ __global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t*
                 sum64 += part;
             }
         }
-        if (active) atomicAdd(&acc[it], F32 ? ((double)hi + (double)lo) * scale : sum64 * scale);
+        if (active) {
+            if (F32) {
+                atomicAdd(&nhi[it], hi);
+                atomicAdd(&nlo[it], lo);
+            } else {
+                atomicAdd(&acc64[it], 0.5 * sum64);
+            }
+        }
     }
 }
 
@@ -612,8 +629,9 @@ __global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restr
                                                    const double* __restrict__ ys,
                                                    const float* __restrict__ chi,
                                                    const float* __restrict__ clo,
-                                                   const double* __restrict__ rad,
-                                                   double* __restrict__ acc)
+                                                   const float* __restrict__ rad32,
+                                                   double* __restrict__ acc64, float* __restrict__ nhi,
+                                                   float* __restrict__ nlo)
 {
     constexpr bool F32 = sizeof(T) == 4;
     const int lane = threadIdx.x & 31;
@@ -622,7 +640,6 @@ __global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restr
     const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double scale = F32 ? 0.5 * 0.69314718055994530942 : 0.5;
     for (int64_t e = e_begin + warp; e < e_end; e += nwarps) {
         const int64_t tl = stgt[e] - base, sl = sidx[e];
         const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0, s0 = lb[sl], ns = lb[sl + 1] - s0;
@@ -631,7 +648,7 @@ __global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restr
             const int64_t sg = base + sl, tg = base + tl;
             ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
             oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
-            const float M = (float)rad[sg] + (float)rad[tg] + fabsf(ox) + fabsf(oy);
+            const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
             tau2 = (M * (1.f / 64.f)) * (M * (1.f / 64.f));
         }
         for (int tc = 0; tc < nt; tc += 32) {
@@ -658,7 +675,8 @@ __global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restr
                     }
                     two_sum(hi, lo, part);
                 }
-                atomicAdd(&acc[it], ((double)hi + (double)lo) * scale);
+                atomicAdd(&nhi[it], hi);
+                atomicAdd(&nlo[it], lo);
             } else {
                 double part = 0.0;
                 for (int j = 0; j < ns; j++) {
@@ -667,7 +685,7 @@ __global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restr
                     const double r2 = dx * dx + dy * dy;
                     if (r2 > 0.0) part += sp.q * log(r2);
                 }
-                atomicAdd(&acc[it], part * scale);
+                atomicAdd(&acc64[it], 0.5 * part);
             }
         }
     }
@@ -679,6 +697,18 @@ __global__ void k_unpermute(const int32_t* __restrict__ perm, const double* __re
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         phi[perm[i]] = acc[i];
+}
+
+// binary32 path: phi = far + (ln 2 / 2) * near, combined in binary32 (the mixed path targets
+// tolerances >= 1e-7), written in input order.
+__global__ void k_combine32(const int32_t* __restrict__ perm, const float* __restrict__ far,
+                            const float* __restrict__ nhi, const float* __restrict__ nlo, int64_t n,
+                            double* __restrict__ phi)
+{
+    const float scale = 0.34657359027997264f;  // ln(2) / 2
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        phi[perm[i]] = (double)(far[i] + scale * (nhi[i] + nlo[i]));
 }
 
 // ---- direct sum at sampled targets (binary64), one block per target ----
@@ -745,7 +775,9 @@ int ensure_tables()
 
 int alloc_ws(fmm_tree t, int PS, bool f64)
 {
-    if (!t->acc && cudaMalloc((void**)&t->acc, 8 * (size_t)t->n) != cudaSuccess)
+    if (f64 && !t->acc && cudaMalloc((void**)&t->acc, 8 * (size_t)t->n) != cudaSuccess)
+        return fail(FMM_ERR_OOM, "accumulator");
+    if (!f64 && !t->acc32 && cudaMalloc((void**)&t->acc32, 3 * 4 * (size_t)t->n) != cudaSuccess)
         return fail(FMM_ERR_OOM, "accumulator");
     void** pk = f64 ? &t->pk64 : &t->pk32;
     if (!*pk && cudaMalloc(pk, (f64 ? 32 : 16) * (size_t)t->n) != cudaSuccess)
@@ -777,7 +809,7 @@ int launch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<float> geo, const cx
                cx<float>* Le, cudaStream_t s)
 {
     k_m2l_pairs<float, PI><<<152 * 16, 128, 0, s>>>(P, PS, li->woff, li->widx, li->wtgt, li->wcap,
-                                                     t->nbox, geo, t->radii, Me, Le); note_launch();
+                                                     t->nbox, geo, Me, Le); note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L");
     return 0;
 }
@@ -803,7 +835,7 @@ int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<double> geo, const
     const size_t sm = (size_t)2 * P * NT * sizeof(cx<double>);
     FMM_CUDA(cudaFuncSetAttribute(k_m2l_pairs_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_m2l_pairs_f64<<<152 * 16, NT, sm, s>>>(P, PS, li->woff, li->widx, li->wtgt, li->wcap, t->nbox,
-                                              geo, t->radii, Me, Le); note_launch();
+                                              geo, Me, Le); note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L");
     return 0;
 }
@@ -822,6 +854,12 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     const int64_t n = t->n;
     const int WPB = 4;
     const size_t bsm = ((P * P * sizeof(T) + 15) & ~15);
+    Geo<T> geo;
+    if constexpr (sizeof(T) == 8) geo = Geo<T>{t->centers, t->radii};
+    else geo = Geo<T>{t->cen_hi, t->cen_lo, t->rad32};
+    float* far32 = t->acc32;
+    float* nhi = t->acc32 + n;
+    float* nlo = t->acc32 + 2 * n;
 
     {
         StageScope scope(FMM_STAGE_GATHER, s);
@@ -837,7 +875,7 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             const size_t sm = (size_t)WPB * 33 * P * sizeof(cx<T>);
             FMM_CUDA(cudaFuncSetAttribute(k_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             k_p2m<T><<<(unsigned)((nleaf + WPB - 1) / WPB), 32 * WPB, sm, s>>>(
-                L, P, PS, t->leaf_begin, pk, t->centers, t->radii, Me); note_launch();
+                L, P, PS, t->leaf_begin, pk, geo, Me); note_launch();
             FMM_LAUNCH_CHECK("evaluate: P2M");
         }
         {
@@ -845,15 +883,12 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             for (int l = L - 1; l >= 1; l--) {
                 const int64_t nb = level_size(l);
                 k_m2m<T><<<(unsigned)((nb + WPB - 1) / WPB), 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
-                    l, P, PS, t->centers, t->radii, Me); note_launch();
+                    l, P, PS, geo, Me); note_launch();
             }
             FMM_LAUNCH_CHECK("evaluate: M2M");
         }
         {
             StageScope scope(FMM_STAGE_M2L, s);
-            Geo<T> geo;
-            if constexpr (sizeof(T) == 8) geo = Geo<T>{t->centers};
-            else geo = Geo<T>{t->cen_hi, t->cen_lo};
             rc = dispatch_m2l(t, li, P, PS, geo, Me, Le, s);
             if (rc) return rc;
         }
@@ -862,28 +897,33 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             for (int l = 1; l < L; l++) {
                 const int64_t nc = level_size(l + 1);
                 k_l2l<T><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
-                    l, P, PS, t->centers, t->radii, Le); note_launch();
+                    l, P, PS, geo, Le); note_launch();
             }
             FMM_LAUNCH_CHECK("evaluate: L2L");
         }
     }
     {
         StageScope scope(FMM_STAGE_LEAF, s);
-        k_l2p<T><<<grid_for(n, 256), 256, 0, s>>>(L, P, PS, n, t->cleaf, pk, t->centers, t->radii, Le,
-                                                  t->acc); note_launch();
+        if (!f64) FMM_CUDA(cudaMemsetAsync(nhi, 0, 2 * 4 * (size_t)n, s));
+        k_l2p<T><<<grid_for(n, 256), 256, 0, s>>>(L, P, PS, n, t->cleaf, pk, geo, Le,
+                                                  f64 ? (T*)t->acc : (T*)far32); note_launch();
         const int64_t maxleaf = (n + level_size(L) - 1) / level_size(L);
         if (maxleaf <= 32) {
             int gs = 1;
             while (gs < maxleaf) gs <<= 1;
             k_p2p_small<T><<<152 * 8, 256, 0, s>>>(L, gs, li->soff, li->sidx, li->stgt, li->scap,
                                                    t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
-                                                   t->cen_lo, t->radii, t->acc); note_launch();
+                                                   t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
         } else {
             k_p2p_large<T><<<152 * 8, 256, 0, s>>>(L, li->soff, li->sidx, li->stgt, li->scap,
                                                    t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
-                                                   t->cen_lo, t->radii, t->acc); note_launch();
+                                                   t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
         }
-        k_unpermute<<<grid_for(n, 256), 256, 0, s>>>(t->perm, t->acc, n, phi); note_launch();
+        if (f64)
+            k_unpermute<<<grid_for(n, 256), 256, 0, s>>>(t->perm, t->acc, n, phi);
+        else
+            k_combine32<<<grid_for(n, 256), 256, 0, s>>>(t->perm, far32, nhi, nlo, n, phi);
+        note_launch();
         FMM_LAUNCH_CHECK("evaluate: leaf evaluation");
     }
     return 0;

@@ -91,27 +91,63 @@ __device__ __forceinline__ LevelCands level_cands(const int32_t* soff, int l, in
     return c;
 }
 
-// Decode candidate t of level l: box b (within-level), candidate c (within-level), and whether t
-// is the first candidate of its box.
-__device__ __forceinline__ void decode(const int32_t* __restrict__ soff, const int32_t* __restrict__ sidx,
-                                       int l, int64_t scap, const LevelCands& lc, int64_t t, int64_t& b,
-                                       int64_t& c, bool& first)
+// Parent offsets of one tile.  Every parent owns 16 * |S(parent)| >= 16 consecutive candidates,
+// so a tile of LTILE candidates touches at most LTILE / 16 + 2 parents: their clamped strong-list
+// offsets are staged in shared memory once per tile and every candidate is decoded there.
+constexpr int TP_MAX = LTILE / 16 + 2;
+
+struct TileParents {
+    int64_t p0;               // first parent of the tile
+    int np;                   // parents staged
+    int64_t off[TP_MAX + 1];  // clamped soff of parents p0 .. p0 + np
+};
+
+__device__ __forceinline__ int64_t find_parent(const int32_t* __restrict__ soff, int64_t pb0, int64_t np,
+                                               int64_t scap, int64_t S0, int64_t t)
 {
-    const int64_t pb0 = level_base(l - 1), np = level_size(l - 1);
-    // parent p: largest p with 16 * (soff[pb0 + p] - S0) <= t
     int64_t lo = 0, hi = np - 1;
     while (lo < hi) {
-        int64_t mid = (lo + hi + 1) >> 1;
-        int64_t off = min((int64_t)soff[pb0 + mid], scap);
-        if (16 * (off - lc.S0) <= t) lo = mid;
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (16 * (min((int64_t)soff[pb0 + mid], scap) - S0) <= t) lo = mid;
         else hi = mid - 1;
     }
-    const int64_t p = lo;
-    const int64_t s0 = min((int64_t)soff[pb0 + p], scap), s1 = min((int64_t)soff[pb0 + p + 1], scap);
-    const int64_t m = s1 - s0;  // >= 1 whenever t falls inside this parent's block
-    const int64_t tp = t - 16 * (s0 - lc.S0);
-    const int64_t k = tp / (4 * m), r = tp - k * 4 * m;
-    b = 4 * p + k;
+    return lo;
+}
+
+// Called by the whole block: stage the parents of candidates [t0, t1).
+__device__ __forceinline__ void stage_parents(TileParents& tp, const int32_t* __restrict__ soff, int l,
+                                              int64_t scap, const LevelCands& lc, int64_t t0, int64_t t1)
+{
+    const int64_t pb0 = level_base(l - 1), np = level_size(l - 1);
+    __shared__ int64_t ends[2];
+    if (threadIdx.x < 2) ends[threadIdx.x] = find_parent(soff, pb0, np, scap, lc.S0, threadIdx.x ? t1 - 1 : t0);
+    __syncthreads();
+    const int64_t p0 = ends[0], p1 = ends[1];
+    const int cnt = (int)(p1 - p0 + 1);
+    for (int i = threadIdx.x; i <= cnt; i += blockDim.x) tp.off[i] = min((int64_t)soff[pb0 + p0 + i], scap);
+    if (threadIdx.x == 0) {
+        tp.p0 = p0;
+        tp.np = cnt;
+    }
+    __syncthreads();
+}
+
+// Decode candidate t of level l: box b (within-level), candidate c (within-level), and whether t
+// is the first candidate of its box.
+__device__ __forceinline__ void decode(const TileParents& tp, const int32_t* __restrict__ sidx,
+                                       const LevelCands& lc, int64_t t, int64_t& b, int64_t& c, bool& first)
+{
+    int lo = 0, hi = tp.np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (16 * (tp.off[mid] - lc.S0) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t s0 = tp.off[lo];
+    const uint32_t m = (uint32_t)(tp.off[lo + 1] - s0);  // >= 1 for the parent that owns t
+    const uint32_t tq = (uint32_t)(t - 16 * (s0 - lc.S0));
+    const uint32_t k = tq / (4 * m), r = tq - k * 4 * m;
+    b = 4 * (tp.p0 + lo) + k;
     c = 4 * (int64_t)sidx[s0 + (r >> 2)] + (r & 3);
     first = (r == 0);
 }
@@ -127,18 +163,20 @@ __global__ void __launch_bounds__(LT) k_lists_flags(int l, const double* __restr
                                                     uint32_t* __restrict__ tilecnt)
 {
     __shared__ uint32_t wsum[LT / 32];
+    __shared__ TileParents tp;
     const LevelCands lc = level_cands(soff, l, scap);
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
     const int64_t base = level_base(l);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        stage_parents(tp, soff, l, scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint32_t cnt = 0;
         for (int j = 0; j < LI; j++) {
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             if (t < nc) {
                 int64_t b, c;
                 bool first;
-                decode(soff, sidx, l, scap, lc, t, b, c, first);
+                decode(tp, sidx, lc, t, b, c, first);
                 const bool w = theta_weak_fast(base + b, base + c, chi, clo, rad32, cen, rad,
                                                (float)theta, theta);
                 flags[t] = w ? 1 : 0;
@@ -210,6 +248,7 @@ __global__ void __launch_bounds__(LT) k_lists_fill(int l, const uint8_t* __restr
                                                    int32_t* stgt)
 {
     __shared__ uint32_t wsum[LI][LT / 32];
+    __shared__ TileParents tp;
     const LevelCands lc = level_cands(soff, l, scap);
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
@@ -218,6 +257,7 @@ __global__ void __launch_bounds__(LT) k_lists_fill(int l, const uint8_t* __restr
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        stage_parents(tp, soff, l, scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint8_t f[LI];
         uint32_t pre[LI];
 #pragma unroll
@@ -242,7 +282,7 @@ __global__ void __launch_bounds__(LT) k_lists_fill(int l, const uint8_t* __restr
             if (t < nc) {
                 int64_t b, c;
                 bool first;
-                decode(soff, sidx, l, scap, lc, t, b, c, first);
+                decode(tp, sidx, lc, t, b, c, first);
                 const int64_t wpre = (int64_t)before + pre[j];  // weak candidates before t
                 const int64_t spre = t - wpre;                   // strong candidates before t
                 if (first) {

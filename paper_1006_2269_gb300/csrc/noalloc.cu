@@ -23,15 +23,15 @@ namespace {
 constexpr int64_t NA_MAX_N = FMM_NOALLOC_MAX_POINTS;
 constexpr int NA_MAX_L = FMM_NOALLOC_MAX_LEVELS;
 constexpr int64_t NA_MAX_NBOX = ((int64_t(1) << (2 * (NA_MAX_L + 1))) - 1) / 3;
-constexpr int64_t NA_TILE = 4096;  // items per tile of the build kernels
+constexpr int64_t NA_TILE = TREE_TILE;  // items per tile of the build kernels
 constexpr int64_t NA_TILES = (NA_MAX_N + NA_TILE - 1) / NA_TILE;
 
 constexpr int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
 
 // Byte layout of the scratch array (every region 256-byte aligned).
 struct Layout {
-    int64_t keys, vals, rs_counts, rs_totals, tilecnt, hflag, bbox, ones_before, status, centers,
-        radii, rad32, cen_hi, cen_lo, leaf_of, cleaf, xs, ys, dxf, dyf, total;
+    int64_t keys, vals, rs_counts, rs_totals, tilecnt, hflag, bbox, ones_before, node_off, segs,
+        status, centers, radii, rad32, cen_hi, cen_lo, leaf_of, cleaf, xs, ys, dxf, dyf, total;
 };
 
 constexpr Layout make_layout()
@@ -46,6 +46,8 @@ constexpr Layout make_layout()
     L.hflag = o;       o += align256(2 * NA_MAX_N);
     L.bbox = o;        o += align256(8 * 4);
     L.ones_before = o; o += align256(4 * (int64_t(1) << (2 * NA_MAX_L)));
+    L.node_off = o;    o += align256(4 * ((int64_t(1) << (2 * NA_MAX_L + 1)) + 2 * NA_MAX_L + 1));
+    L.segs = o;        o += align256(4 * 4 * NA_MAX_N);
     L.status = o;      o += align256(4);
     L.centers = o;     o += align256(16 * NA_MAX_NBOX);
     L.radii = o;       o += align256(8 * NA_MAX_NBOX);
@@ -88,11 +90,20 @@ int scratch_base(unsigned char** out)
     return 0;
 }
 
-// Per-depth "ones before" tables of the stable partitions and the leaf offsets; the same values
-// the allocating path computes on the host.  One block; depths are independent.
+// Per-depth "ones before" tables of the stable partitions, node offsets and leaf offsets; the
+// same values the allocating path computes on the host.  One block; depths are independent.
 __global__ void __launch_bounds__(1024) k_noalloc_tables(int64_t n, int L, int32_t* ones_before,
-                                                         int32_t* leaf_begin)
+                                                         int32_t* node_off, int32_t* leaf_begin)
 {
+    for (int d = 0; d <= 2 * L; d++) {
+        const int64_t nodes = int64_t(1) << d;
+        int32_t* off = node_off + node_offset_base(d);
+        for (int64_t j = threadIdx.x; j <= nodes; j += blockDim.x) {
+            int64_t o = n, m = 0;
+            if (j < nodes) descend_node(n, d, j, o, m);
+            off[j] = (int32_t)o;
+        }
+    }
     __shared__ int64_t wt[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int d = 0; d < 2 * L; d++) {
@@ -176,6 +187,8 @@ extern "C" int fmm_build_tree_noalloc(const double* x, const double* y, int64_t 
     t.hflag = (uint8_t*)(base + Lo.hflag);
     t.bbox_keys = (uint64_t*)(base + Lo.bbox);
     t.ones_before = (int32_t*)(base + Lo.ones_before);
+    t.node_off = (int32_t*)(base + Lo.node_off);
+    t.segs = (int32_t*)(base + Lo.segs);
     t.status = (int32_t*)(base + Lo.status);
     t.centers = (double*)(base + Lo.centers);
     t.radii = (double*)(base + Lo.radii);
@@ -195,7 +208,7 @@ extern "C" int fmm_build_tree_noalloc(const double* x, const double* y, int64_t 
     // the array keeps the previous call's contents: the status word must start at zero; every
     // other region is fully written before it is read
     FMM_CUDA(cudaMemsetAsync(t.status, 0, 4, s));
-    k_noalloc_tables<<<1, 1024, 0, s>>>(n, levels, t.ones_before, leaf_begin); note_launch();
+    k_noalloc_tables<<<1, 1024, 0, s>>>(n, levels, t.ones_before, t.node_off, leaf_begin); note_launch();
     FMM_LAUNCH_CHECK("fmm_build_tree_noalloc: tables");
     rc = tree_build(&t, x, y, s);
     if (rc) return rc;

@@ -19,9 +19,9 @@
 namespace fmm {
 namespace {
 
-constexpr int TPB = 256;             // threads per block of the tiled kernels
-constexpr int ITEMS = 16;            // items per thread
-constexpr int TILE = TPB * ITEMS;    // 4096 items per tile
+constexpr int TPB = TREE_TPB;        // threads per block of the tiled kernels
+constexpr int ITEMS = TREE_ITEMS;    // items per thread
+constexpr int TILE = TREE_TILE;      // items per tile
 constexpr int WARPS = TPB / 32;
 constexpr int WCHUNK = ITEMS * 32;   // contiguous items handled by one warp
 constexpr int BINS = 256;            // radix digit of 8 bits
@@ -299,34 +299,45 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* a, int64_t m)
     }
 }
 
-// Stable partition of every segment (node at `depth`) of `in` by flag[in[pos]]: zeros keep their
-// order and come first, ones follow.  Each segment of size m holds exactly m - floor(m/2) ones
-// (the flag marks the right child at depth+1), ob[j] counts the ones of all segments before
-// segment j, and tileoff[] is the exclusive scan of the ones per tile.  If flagout != null it
-// receives, per item, whether its new position lies in the right child at depth+2.
+// Stable partition inside segments.  Items carry the index of their level-l box (seg, a node at
+// depth 2l of the floor-left split tree whose offsets are tabulated in node_off).
+//   xmode = 0 (the y-ordered list): segments are the boxes themselves, flag = x-half bit; an item
+//       lands in its x-half (depth 2l+1), where the y order makes its y-half bit "position in the
+//       upper half"; out_seg receives the level-(l+1) box, flagout the y-half bit.
+//   xmode = 1 (the x-ordered list): segments are the x-halves (depth 2l+1, the half follows from
+//       the position), flag = y-half bit; out_seg receives the level-(l+1) box, flagout the
+//       x-half bit of the next level.
+// Zeros keep their order and come first.  A segment of size m holds m - floor(m/2) ones, ob[j]
+// counts the ones of all segments before segment j at that depth, tileoff[] is the exclusive scan
+// of the ones per tile.
 __global__ void __launch_bounds__(TPB) k_part_scatter(const int32_t* __restrict__ in,
+                                                      const int32_t* __restrict__ in_seg,
                                                       int32_t* __restrict__ out,
+                                                      int32_t* __restrict__ out_seg,
                                                       const uint8_t* __restrict__ flag,
-                                                      uint8_t* __restrict__ flagout, int64_t n,
-                                                      int depth, const int32_t* __restrict__ ob,
+                                                      uint8_t* __restrict__ flagout, int32_t n, int l,
+                                                      int xmode, const int32_t* __restrict__ node_off,
+                                                      const int32_t* __restrict__ ones_before,
                                                       const uint32_t* __restrict__ tileoff,
                                                       int32_t* status)
 {
     __shared__ uint32_t wtot[WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)w * WCHUNK;
+    const int32_t base = (int32_t)blockIdx.x * TILE + w * WCHUNK;
+    const int32_t* offD = node_off + node_offset_base(2 * l);
+    const int32_t* ob = ones_before + ones_before_offset(2 * l + xmode);
     int32_t id[ITEMS];
     uint32_t pre[ITEMS];
     uint32_t fl = 0, run = 0;
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
-        int64_t i = base + j * 32 + lane;
-        bool valid = i < n;
+        const int32_t i = base + j * 32 + lane;
+        const bool valid = i < n;
         id[j] = valid ? in[i] : 0;
-        uint32_t f = valid ? flag[id[j]] : 0;
+        const uint32_t f = valid ? flag[id[j]] : 0;
         fl |= f << j;
-        unsigned bal = __ballot_sync(0xffffffffu, f);
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
         pre[j] = run + __popc(bal & lt);
         run += __popc(bal);
     }
@@ -336,32 +347,44 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(const int32_t* __restrict_
     for (int ww = 0; ww < w; ww++) woff += wtot[ww];
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
-        int64_t i = base + j * 32 + lane;
+        const int32_t i = base + j * 32 + lane;
         if (i >= n) continue;
-        int64_t G = (int64_t)woff + pre[j];
-        int64_t o, m;
-        int64_t node = descend_pos(n, depth, i, o, m);
-        int64_t ones = G - ob[node];
-        int64_t h = m >> 1;
-        bool f = (fl >> j) & 1;
-        int64_t np = f ? (o + h + ones) : (i - ones);
+        const int32_t G = (int32_t)(woff + pre[j]);
+        const int32_t seg = in_seg[i];
+        int32_t o = offD[seg], m = offD[seg + 1] - o;
+        int32_t seg1 = seg;
+        if (xmode) {  // the x-half of the box
+            const int32_t h = m >> 1;
+            const int32_t bit = i >= o + h;
+            seg1 = 2 * seg + bit;
+            if (bit) {
+                o += h;
+                m -= h;
+            } else {
+                m = h;
+            }
+        }
+        const int32_t ones = G - ob[seg1];
+        const int32_t h = m >> 1;
+        const int32_t f = (fl >> j) & 1;
+        const int32_t np = f ? (o + h + ones) : (i - ones);
         if (np < o || np >= o + m) {  // cannot happen for consistent tables; never write out of range
             atomicOr(status, ST_ARG);
             continue;
         }
+        const int32_t o2 = f ? o + h : o, m2 = f ? m - h : h;
+        const int32_t seg2 = 2 * seg1 + f;
+        const int32_t bit2 = np >= o2 + (m2 >> 1);
         out[np] = id[j];
-        if (flagout) {
-            int64_t o2 = f ? o + h : o, m2 = f ? m - h : h;
-            flagout[id[j]] = (np >= o2 + (m2 >> 1)) ? 1 : 0;
-        }
+        out_seg[np] = xmode ? seg2 : 2 * seg2 + bit2;
+        flagout[id[j]] = (uint8_t)bit2;
     }
 }
 
 // Level-0 x-split: the upper half of the x order has the bit set.
-__global__ void k_init_hx(const int32_t* __restrict__ X, int64_t n, uint8_t* __restrict__ hx)
+__global__ void k_init_hx(const int32_t* __restrict__ X, int32_t n, uint8_t* __restrict__ hx)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         hx[X[i]] = (i >= (n >> 1)) ? 1 : 0;
 }
 
@@ -371,13 +394,13 @@ __device__ __forceinline__ double midpoint(double a, double b) { return __dmul_r
 // x-ordered list segmented by the boxes of level l, Yn the y-ordered list segmented by their
 // x-halves.
 __global__ void k_split_rects(const int32_t* __restrict__ X, const int32_t* __restrict__ Yn,
-                              const double* __restrict__ x, const double* __restrict__ y, int64_t n,
-                              int l, double* __restrict__ rects)
+                              const double* __restrict__ x, const double* __restrict__ y,
+                              const int32_t* __restrict__ node_off, int l, double* __restrict__ rects)
 {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= level_size(l)) return;
-    int64_t o, m;
-    descend_node(n, 2 * l, b, o, m);
+    const int32_t* offD = node_off + node_offset_base(2 * l);
+    const int64_t o = offD[b], m = offD[b + 1] - o;
     int64_t mx = m >> 1;
     double xs = midpoint(x[X[o + mx - 1]], x[X[o + mx]]);
     int64_t ho[2] = {o, o + mx}, hm[2] = {mx, m - mx};
@@ -396,13 +419,12 @@ __global__ void k_split_rects(const int32_t* __restrict__ X, const int32_t* __re
     cr[12] = xs; cr[13] = px1; cr[14] = ys[1]; cr[15] = py1;
 }
 
-__global__ void k_leaf_of(const int32_t* __restrict__ X, int64_t n, int L, uint32_t* __restrict__ leaf_of)
+// After the last level every item of X carries its leaf.
+__global__ void k_leaf_of(const int32_t* __restrict__ X, const int32_t* __restrict__ XS, int32_t n,
+                          uint32_t* __restrict__ leaf_of)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t o, m;
-        leaf_of[X[i]] = (uint32_t)descend_pos(n, 2 * L, i, o, m);
-    }
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        leaf_of[X[i]] = (uint32_t)XS[i];
 }
 
 // Centre (rectangle midpoint) and radius (half diagonal) of every box, with the same sequence of
@@ -466,10 +488,18 @@ int tree_alloc(fmm_tree t)
     t->nleaf = level_size(L);
     t->ntiles = (n + TILE - 1) / TILE;
 
-    // floor-left split sizes per depth; ones-before tables for depths 0 .. 2L-1; leaf offsets
+    // floor-left split sizes per depth; ones-before tables for depths 0 .. 2L-1; node offsets for
+    // depths 0 .. 2L; leaf offsets
     std::vector<int64_t> sizes{n}, next;
-    std::vector<int32_t> ob_all;
-    for (int d = 0; d < 2 * L; d++) {
+    std::vector<int32_t> ob_all, off_all;
+    for (int d = 0; d <= 2 * L; d++) {
+        int64_t o = 0;
+        for (int64_t m : sizes) {
+            off_all.push_back((int32_t)o);
+            o += m;
+        }
+        off_all.push_back((int32_t)o);
+        if (d == 2 * L) break;
         int64_t acc = 0;
         for (int64_t m : sizes) {
             ob_all.push_back((int32_t)acc);
@@ -515,10 +545,13 @@ int tree_alloc(fmm_tree t)
     if ((rc = A((void**)&t->hflag, 2 * nn))) return rc;
     if ((rc = A((void**)&t->bbox_keys, 32))) return rc;
     if ((rc = A((void**)&t->ones_before, 4 * ob_all.size()))) return rc;
+    if ((rc = A((void**)&t->node_off, 4 * off_all.size()))) return rc;
+    if ((rc = A((void**)&t->segs, 4 * 4 * nn))) return rc;
     if ((rc = A((void**)&t->status, 4))) return rc;
     FMM_CUDA(cudaMemcpy(t->leaf_begin, lb.data(), 4 * lb.size(), cudaMemcpyHostToDevice));
     if (!ob_all.empty())
         FMM_CUDA(cudaMemcpy(t->ones_before, ob_all.data(), 4 * ob_all.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemcpy(t->node_off, off_all.data(), 4 * off_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemset(t->status, 0, 4));
     return 0;
 }
@@ -533,6 +566,7 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
     uint8_t* hx = t->hflag;
     uint8_t* hy = t->hflag + n;
     int32_t *X, *Xo, *Y, *Yo;
+    int32_t* Xfinal_seg = nullptr;
 
     {
         StageScope scope(FMM_STAGE_TREE_SORT, s);
@@ -551,34 +585,40 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
 
     {
         StageScope scope(FMM_STAGE_TREE_SPLIT, s);
-        k_init_hx<<<grid_for(n, 256), 256, 0, s>>>(X, n, hx); note_launch();
+        // box index carried by every item of X and Y (all in the root at level 0)
+        int32_t *XS = t->segs, *XSo = t->segs + n, *YS = t->segs + 2 * n, *YSo = t->segs + 3 * n;
+        FMM_CUDA(cudaMemsetAsync(XS, 0, 4 * n, s));
+        FMM_CUDA(cudaMemsetAsync(YS, 0, 4 * n, s));
+        const int32_t n32 = (int32_t)n;
+        k_init_hx<<<grid_for(n, 256), 256, 0, s>>>(X, n32, hx); note_launch();
         for (int l = 0; l < L; l++) {
             // Y: stable partition of each box by its x-half bit; records the y-half bit
             k_part_count<<<(unsigned)nt, TPB, 0, s>>>(Y, hx, n, t->tilecnt); note_launch();
             k_scan_tiles<<<1, 1024, 0, s>>>(t->tilecnt, nt); note_launch();
-            k_part_scatter<<<(unsigned)nt, TPB, 0, s>>>(Y, Yo, hx, hy, n, 2 * l,
-                                                        t->ones_before + ones_before_offset(2 * l), t->tilecnt,
-                                                        t->status); note_launch();
+            k_part_scatter<<<(unsigned)nt, TPB, 0, s>>>(Y, YS, Yo, YSo, hx, hy, n32, l, 0, t->node_off,
+                                                        t->ones_before, t->tilecnt, t->status); note_launch();
             std::swap(Y, Yo);
+            std::swap(YS, YSo);
             // split coordinates and child rectangles of level l
             int64_t nb = level_size(l);
-            k_split_rects<<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(X, Y, x, y, n, l, t->rects); note_launch();
+            k_split_rects<<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(X, Y, x, y, t->node_off, l, t->rects); note_launch();
             // X: stable partition of each x-half by the y-half bit; records the next x-half bit
             k_part_count<<<(unsigned)nt, TPB, 0, s>>>(X, hy, n, t->tilecnt); note_launch();
             k_scan_tiles<<<1, 1024, 0, s>>>(t->tilecnt, nt); note_launch();
-            k_part_scatter<<<(unsigned)nt, TPB, 0, s>>>(X, Xo, hy, hx, n, 2 * l + 1,
-                                                        t->ones_before + ones_before_offset(2 * l + 1), t->tilecnt,
-                                                        t->status); note_launch();
+            k_part_scatter<<<(unsigned)nt, TPB, 0, s>>>(X, XS, Xo, XSo, hy, hx, n32, l, 1, t->node_off,
+                                                        t->ones_before, t->tilecnt, t->status); note_launch();
             std::swap(X, Xo);
+            std::swap(XS, XSo);
             FMM_LAUNCH_CHECK("tree: level split");
         }
+        Xfinal_seg = XS;
     }
 
     {
         StageScope scope(FMM_STAGE_TREE_FINISH, s);
         // canonical order: stable sort of the input indices by leaf (inside a leaf: input order)
         uint32_t* leaf_of = (uint32_t*)t->leaf_of;
-        k_leaf_of<<<grid_for(n, 256), 256, 0, s>>>(X, n, L, leaf_of); note_launch();
+        k_leaf_of<<<grid_for(n, 256), 256, 0, s>>>(X, Xfinal_seg, (int32_t)n, leaf_of); note_launch();
         uint32_t* k32 = (uint32_t*)t->keys;  // reuse the key buffers: [0, n) and [n, 2n)
         int32_t* v32 = t->vals + 2 * n;      // value buffers [2n, 4n)
         int bits = std::max(8, 2 * L);  // with L = 0 all keys are 0 and the order stays the input order
