@@ -617,6 +617,130 @@ __global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t*
     }
 }
 
+__device__ __forceinline__ float lg2_fast(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Exact-path sum of one target against one source leaf (binary32, pairs closer than sqrt(tau2)
+// redone in binary64; j = i and coincident points skipped).
+__device__ __forceinline__ float p2p_exact(float xt, float yt, int32_t it, const Pk<float>* __restrict__ pk,
+                                           int32_t s0, int32_t ns, float tau2, const double* __restrict__ xs,
+                                           const double* __restrict__ ys)
+{
+    float part = 0.f;
+    for (int32_t j = 0; j < ns; j++) {
+        if (s0 + j == it) continue;
+        const Pk<float> sp = pk[s0 + j];
+        const float dx = xt - sp.x, dy = yt - sp.y;
+        const float r2 = dx * dx + dy * dy;
+        if (r2 >= tau2) {
+            part += sp.q * lg2_fast(r2);
+        } else {
+            const double ddx = xs[it] - xs[s0 + j], ddy = ys[it] - ys[s0 + j];
+            const double r2d = ddx * ddx + ddy * ddy;
+            if (r2d > 0.0) part += sp.q * (float)log2(r2d);
+        }
+    }
+    return part;
+}
+
+// binary32 near field for leaves of at most 32 points.  Groups of gsl lanes work on one leaf pair,
+// each lane on two targets (t0 + li and t0 + li + gsl), so a warp holds 32 / gsl leaf pairs at
+// once and every source load serves two pair evaluations.  The main loop has no branch: it keeps
+// the smallest r^2 it met and, for the rare lane whose minimum falls below the exactness threshold
+// (and for the leaf's pair with itself), the leaf pair is redone by the exact path.
+__global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* __restrict__ soff,
+                                                 const int32_t* __restrict__ sidx,
+                                                 const int32_t* __restrict__ stgt, int64_t scap,
+                                                 const int32_t* __restrict__ lb,
+                                                 const Pk<float>* __restrict__ pk,
+                                                 const double* __restrict__ xs,
+                                                 const double* __restrict__ ys,
+                                                 const float* __restrict__ chi,
+                                                 const float* __restrict__ clo,
+                                                 const float* __restrict__ rad32,
+                                                 float* __restrict__ nhi, float* __restrict__ nlo)
+{
+    const int lane = threadIdx.x & 31, G = 32 / gsl, grp = lane / gsl, li = lane - grp * gsl;
+    const int32_t base = (int32_t)level_base(L);
+    const int64_t e_begin = min((int64_t)soff[base], scap);
+    const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e0 = e_begin + warp * P2P_CH; e0 < e_end; e0 += nwarps * P2P_CH) {
+        const int64_t e1 = min(e0 + P2P_CH, e_end);
+        int32_t cur = -1, it0 = 0, it1 = 0;
+        bool v0 = false, v1 = false;
+        float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f;
+        float hi0 = 0.f, lo0 = 0.f, hi1 = 0.f, lo1 = 0.f;
+        for (int64_t e = e0 + grp; e < e1; e += G) {
+            const int32_t tl = stgt[e] - base;
+            if (tl != cur) {
+                if (v0) { atomicAdd(&nhi[it0], hi0); atomicAdd(&nlo[it0], lo0); }
+                if (v1) { atomicAdd(&nhi[it1], hi1); atomicAdd(&nlo[it1], lo1); }
+                cur = tl;
+                const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0;
+                it0 = t0 + li;
+                it1 = t0 + li + gsl;
+                v0 = li < nt;
+                v1 = li + gsl < nt;
+                hi0 = lo0 = hi1 = lo1 = 0.f;
+                if (v0) { const Pk<float> p = pk[it0]; tx0 = p.x; ty0 = p.y; }
+                if (v1) { const Pk<float> p = pk[it1]; tx1 = p.x; ty1 = p.y; }
+            }
+            if (!v0) continue;  // v1 implies v0
+            const int32_t sl = sidx[e];
+            const int32_t s0 = lb[sl], ns = lb[sl + 1] - s0;
+            const int32_t sg = base + sl, tg = base + tl;
+            const float ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
+            const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
+            const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
+            const float tau2 = fmaxf((M * (1.f / 64.f)) * (M * (1.f / 64.f)), 1e-30f);
+            const float xa = tx0 - ox, ya = ty0 - oy, xb = tx1 - ox, yb = ty1 - oy;
+            float pa = 0.f, pb = 0.f, ma = 3.0e38f, mb = 3.0e38f;
+            const Pk<float>* src = pk + s0;
+            if (sl != tl) {
+#pragma unroll 4
+                for (int32_t j = 0; j < ns; j++) {
+                    const Pk<float> sp = src[j];
+                    const float dxa = xa - sp.x, dya = ya - sp.y;
+                    const float dxb = xb - sp.x, dyb = yb - sp.y;
+                    const float ra = dxa * dxa + dya * dya, rb = dxb * dxb + dyb * dyb;
+                    ma = fminf(ma, ra);
+                    mb = fminf(mb, rb);
+                    pa += sp.q * lg2_fast(ra);
+                    pb += sp.q * lg2_fast(rb);
+                }
+            } else {
+                // the leaf with itself: a point meets itself once; give that term r^2 = 1 (log 0)
+                const int32_t ia = it0 - s0, ib = it1 - s0;
+#pragma unroll 4
+                for (int32_t j = 0; j < ns; j++) {
+                    const Pk<float> sp = src[j];
+                    const float dxa = xa - sp.x, dya = ya - sp.y;
+                    const float dxb = xb - sp.x, dyb = yb - sp.y;
+                    float ra = dxa * dxa + dya * dya, rb = dxb * dxb + dyb * dyb;
+                    ra = j == ia ? 3.0e38f : ra;
+                    rb = j == ib ? 3.0e38f : rb;
+                    ma = fminf(ma, ra);
+                    mb = fminf(mb, rb);
+                    pa += j == ia ? 0.f : sp.q * lg2_fast(ra);
+                    pb += j == ib ? 0.f : sp.q * lg2_fast(rb);
+                }
+            }
+            if (ma < tau2) pa = p2p_exact(xa, ya, it0, pk, s0, ns, tau2, xs, ys);
+            if (v1 && mb < tau2) pb = p2p_exact(xb, yb, it1, pk, s0, ns, tau2, xs, ys);
+            two_sum(hi0, lo0, pa);
+            if (v1) two_sum(hi1, lo1, pb);
+        }
+        if (v0) { atomicAdd(&nhi[it0], hi0); atomicAdd(&nlo[it0], lo0); }
+        if (v1) { atomicAdd(&nhi[it1], hi1); atomicAdd(&nlo[it1], lo1); }
+    }
+}
+
 // Leaves of more than 32 points: one lane per target, 32 targets at a time, every source of the
 // pair; one flush per (pair, block of 32 targets).
 template <typename T>
@@ -911,9 +1035,15 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         if (maxleaf <= 32) {
             int gs = 1;
             while (gs < maxleaf) gs <<= 1;
-            k_p2p_small<T><<<152 * 8, 256, 0, s>>>(L, gs, li->soff, li->sidx, li->stgt, li->scap,
-                                                   t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
-                                                   t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
+            if constexpr (sizeof(T) == 4) {
+                k_p2p_f32<<<152 * 8, 256, 0, s>>>(L, gs > 1 ? gs / 2 : 1, li->soff, li->sidx, li->stgt,
+                                                  li->scap, t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
+                                                  t->cen_lo, t->rad32, nhi, nlo); note_launch();
+            } else {
+                k_p2p_small<T><<<152 * 8, 256, 0, s>>>(L, gs, li->soff, li->sidx, li->stgt, li->scap,
+                                                       t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
+                                                       t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
+            }
         } else {
             k_p2p_large<T><<<152 * 8, 256, 0, s>>>(L, li->soff, li->sidx, li->stgt, li->scap,
                                                    t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
