@@ -61,8 +61,10 @@ typedef struct fmm_lists_s* fmm_lists;
  *   p      expansion order: coefficients k = 0..p (a_0 is the logarithmic term), 0 <= p <= 40.
  *          The relative error behaves like theta^(p+1)/(1-theta)^2 (Section 3).
  *   mode   FMM_MODE_FP64 or FMM_MODE_MIXED.
- *   tol    requested relative tolerance; in FMM_MODE_MIXED a tol below 1e-7 makes the final
- *          L2P + near-field accumulation run in binary64.  Ignored in FMM_MODE_FP64.
+ *   tol    requested relative tolerance (0 = none).  In FMM_MODE_MIXED a tol below 1e-7 is
+ *          beyond what binary32 expansions can deliver (their rounding alone is about 1e-7 of
+ *          the potential), so such a call runs every stage in binary64, exactly as
+ *          FMM_MODE_FP64.  Ignored in FMM_MODE_FP64.
  */
 typedef struct {
     int p;
@@ -83,6 +85,27 @@ typedef struct {
  * n < 2^31).  Allocates device memory (synchronous); no kernel runs. */
 int fmm_tree_create(int64_t n, int levels, fmm_tree* out);
 
+/* Batched problems (no paper counterpart: the paper treats one point set at a time).
+ * A tree may hold a forest of n_inst independent instances, instance i with n[i] points and
+ * levels[i] levels (host arrays; each instance obeys the limits of fmm_tree_create, and the
+ * total number of points is below 2^31).  Every call on such a tree processes all instances in
+ * the same launches, each exactly as if it were alone: the points of instance i never interact
+ * with those of another.  Point arrays (x, y, q, phi, perm) are the instances' arrays
+ * concatenated in instance order; box arrays (rects) the instances' boxes concatenated (each in
+ * its own global id order); leaf_begin the instances' 4^levels[i] + 1 offsets concatenated.
+ * Indices stored in these arrays are local to their instance.  fmm_tree_instance reports where
+ * instance i starts.  fmm_tree_create(n, L, out) is the forest of one instance. */
+#define FMM_MAX_INSTANCES 65535
+int fmm_tree_create_batched(int n_inst, const int64_t* n_host, const int* levels_host, fmm_tree* out);
+
+/* Number of instances of a tree (or a negative fmm_status). */
+int fmm_tree_num_instances(fmm_tree t);
+
+/* Instance i of a tree (host values, any pointer may be NULL): its first point p0 and point
+ * count n, levels, first box b0 and box count nbox, first leaf_begin entry lb0. */
+int fmm_tree_instance(fmm_tree t, int i, int64_t* p0, int64_t* n, int* levels, int64_t* b0,
+                      int64_t* nbox, int64_t* lb0);
+
 /* Build the tree of points (x[n], y[n]) (binary64, device).  The tree keeps its own copy of
  * everything it needs; x and y may be reused after the work on `stream` completes.  Non-finite
  * coordinates set FMM_ERR_NONFINITE in the device status. */
@@ -95,7 +118,8 @@ int fmm_build_tree(fmm_tree t, const double* x, const double* y, void* stream);
  *   leaf_begin[4^levels + 1]  leaf i holds perm[leaf_begin[i] .. leaf_begin[i+1]).        */
 int fmm_tree_export(fmm_tree t, int32_t* perm, double* rects, int32_t* leaf_begin, void* stream);
 
-/* Number of points, levels and boxes of a tree (host values). */
+/* Number of points, levels and boxes of a tree (host values; for a forest the totals over its
+ * instances and the largest levels). */
 int fmm_tree_info(fmm_tree t, int64_t* n, int* levels, int64_t* nbox);
 
 void fmm_tree_destroy(fmm_tree t);
@@ -143,20 +167,38 @@ int fmm_build_tree_noalloc(const double* x, const double* y, int64_t n, int leve
  * ------------------------------------------------------------------------------------------- */
 
 /* Allocate list storage for tree t with room for weak_capacity weak and strong_capacity strong
- * entries in total (0 = a default of 64 and 32 per box). */
+ * entries in total (0 = a default of 64 and 32 per box).  For a forest the totals are shared out
+ * over the instances in proportion to their box counts (at least 16 weak and 8 strong per box). */
 int fmm_lists_create(fmm_tree t, int64_t weak_capacity, int64_t strong_capacity, fmm_lists* out);
+
+/* List storage of a forest with the capacity of every instance given (host arrays of n_inst
+ * positive entries). */
+int fmm_lists_create_batched(fmm_tree t, const int64_t* weak_capacity_host,
+                             const int64_t* strong_capacity_host, fmm_lists* out);
 
 /* Build the lists of tree t (which must have been built on the same stream or be complete)
  * for 0 < theta < 1.  Overflow of the capacity sets FMM_ERR_CAPACITY in the device status;
  * later kernels then read only within the capacity. */
 int fmm_interaction_lists(fmm_tree t, fmm_lists l, double theta, void* stream);
 
-/* Wait for `stream`, then report the list totals (host values, may be NULL) and the status. */
+/* Wait for `stream`, then report the list totals over all instances (host values, may be NULL)
+ * and the status: FMM_ERR_CAPACITY when an instance's lists did not fit. */
 int fmm_lists_sync(fmm_lists l, void* stream, int64_t* n_weak, int64_t* n_strong);
 
-/* Copy the lists out (device pointers): woff/soff[nbox+1], widx[n_weak], sidx[n_strong]. */
+/* As fmm_lists_sync, with the entry counts of every instance (host arrays of n_inst entries,
+ * may be NULL).  For an instance whose lists fit they are exact; for one that overflowed they
+ * are a lower bound of what it needs (levels below the overflow see truncated lists). */
+int fmm_lists_counts(fmm_lists l, void* stream, int64_t* n_weak_host, int64_t* n_strong_host);
+
+/* Copy the lists out (device pointers): woff/soff[nbox+1], widx[n_weak], sidx[n_strong].
+ * Trees of one instance only. */
 int fmm_lists_export(fmm_lists l, int32_t* woff, int32_t* widx, int32_t* soff, int32_t* sidx,
                      void* stream);
+
+/* The lists of instance i, as fmm_lists_export for that instance alone (nbox = its box count,
+ * offsets start at 0). */
+int fmm_lists_export_instance(fmm_lists l, int i, int32_t* woff, int32_t* widx, int32_t* soff,
+                              int32_t* sidx, void* stream);
 
 void fmm_lists_destroy(fmm_lists l);
 
@@ -172,6 +214,16 @@ void fmm_lists_destroy(fmm_lists l);
  * ------------------------------------------------------------------------------------------- */
 int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi,
                  void* stream);
+
+/* Launch-shape tuning (no paper counterpart).  fmm_autotune runs complete evaluations of
+ * (t, l, q, prm) on `stream` for a ladder of grid sizes of the M2L and near-field kernels, timing
+ * each with CUDA events, and keeps the fastest for later evaluations of this tree; phi receives
+ * the potentials of the last run.  It synchronises with the host (not for use under stream
+ * capture).  The chosen blocks per instance are reported in m2l_blocks / p2p_blocks (host, may be
+ * NULL).  fmm_set_launch sets them directly (0 = the built-in default). */
+int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi,
+                 void* stream, int* m2l_blocks_host, int* p2p_blocks_host);
+int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks);
 
 /* Eq. (1.1) by direct summation in binary64 at m target input indices targets[m] (int64,
  * device) over all n sources; phi[m] (device).  Coincident distinct points contribute 0. */

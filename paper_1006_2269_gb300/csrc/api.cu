@@ -95,18 +95,21 @@ void free_tree(fmm_tree t)
     void* ptrs[] = {t->rects, t->centers, t->radii, t->rad32, t->cen_hi, t->cen_lo, t->perm, t->leaf_begin,
                     t->leaf_of, t->xs, t->ys, t->dxf, t->dyf, t->keys, t->vals, t->rs_counts,
                     t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->node_off, t->segs, t->status,
-                    t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf};
+                    t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf, t->dinst, t->Lf0lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (t->own_hinst) delete[] t->hinst;
     delete t;
 }
 
 void free_lists(fmm_lists l)
 {
     if (!l) return;
-    void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status};
+    void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status,
+                    l->dlinst};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    delete[] l->hlinst;
     delete l;
 }
 
@@ -157,25 +160,34 @@ int fmm_profile_read(double* ms, int64_t* count, int nstages)
 
 int64_t fmm_launch_count(void) { return g_launches.load(); }
 
-int fmm_tree_create(int64_t n, int levels, fmm_tree* out)
+int fmm_tree_create_batched(int n_inst, const int64_t* n, const int* levels, fmm_tree* out)
 {
-    if (!out) return fail(FMM_ERR_ARG, "out is NULL");
+    if (!out || !n || !levels) return fail(FMM_ERR_ARG, "NULL argument");
     *out = nullptr;
-    if (levels < 0 || levels > 13) return fail(FMM_ERR_ARG, "levels = %d outside [0, 13]", levels);
-    if (n < 1 || n >= ((int64_t)1 << 31) - 1) return fail(FMM_ERR_ARG, "n = %lld outside [1, 2^31)", (long long)n);
-    if (n < level_size(levels))
-        return fail(FMM_ERR_LEVELS, "n = %lld < 4^%d: some leaf would be empty", (long long)n, levels);
+    if (n_inst < 1 || n_inst > FMM_MAX_INSTANCES)
+        return fail(FMM_ERR_ARG, "n_inst = %d outside [1, %d]", n_inst, FMM_MAX_INSTANCES);
+    int64_t total = 0;
+    for (int i = 0; i < n_inst; i++) {
+        if (levels[i] < 0 || levels[i] > 13)
+            return fail(FMM_ERR_ARG, "instance %d: levels = %d outside [0, 13]", i, levels[i]);
+        if (n[i] < 1 || n[i] >= ((int64_t)1 << 31) - 1)
+            return fail(FMM_ERR_ARG, "instance %d: n = %lld outside [1, 2^31)", i, (long long)n[i]);
+        if (n[i] < level_size(levels[i]))
+            return fail(FMM_ERR_LEVELS, "instance %d: n = %lld < 4^%d: some leaf would be empty", i,
+                        (long long)n[i], levels[i]);
+        total += n[i];
+    }
+    if (total >= ((int64_t)1 << 31) - 1)
+        return fail(FMM_ERR_ARG, "total of %lld points is not below 2^31 - 1", (long long)total);
     fmm_tree t = new (std::nothrow) fmm_tree_s();
     if (!t) return fail(FMM_ERR_OOM, "host allocation");
-    t->n = n;
-    t->L = levels;
     if (cudaGetDevice(&t->dev) != cudaSuccess) {
         delete t;
         return fail(FMM_ERR_CUDA, "no CUDA device");
     }
     int rc;
     try {
-        rc = tree_alloc(t);
+        rc = tree_alloc(t, n_inst, n, levels);
     } catch (...) {
         rc = fail(FMM_ERR_OOM, "host allocation");
     }
@@ -185,6 +197,11 @@ int fmm_tree_create(int64_t n, int levels, fmm_tree* out)
     }
     *out = t;
     return FMM_OK;
+}
+
+int fmm_tree_create(int64_t n, int levels, fmm_tree* out)
+{
+    return fmm_tree_create_batched(1, &n, &levels, out);
 }
 
 int fmm_build_tree(fmm_tree t, const double* x, const double* y, void* stream)
@@ -203,7 +220,7 @@ int fmm_tree_export(fmm_tree t, int32_t* perm, double* rects, int32_t* leaf_begi
     if (perm) FMM_CUDA(cudaMemcpyAsync(perm, t->perm, 4 * t->n, cudaMemcpyDeviceToDevice, s));
     if (rects) FMM_CUDA(cudaMemcpyAsync(rects, t->rects, 32 * t->nbox, cudaMemcpyDeviceToDevice, s));
     if (leaf_begin)
-        FMM_CUDA(cudaMemcpyAsync(leaf_begin, t->leaf_begin, 4 * (t->nleaf + 1), cudaMemcpyDeviceToDevice, s));
+        FMM_CUDA(cudaMemcpyAsync(leaf_begin, t->leaf_begin, 4 * (t->nleaf + t->n_inst), cudaMemcpyDeviceToDevice, s));
     return FMM_OK;
 }
 
@@ -211,8 +228,29 @@ int fmm_tree_info(fmm_tree t, int64_t* n, int* levels, int64_t* nbox)
 {
     if (!t) return fail(FMM_ERR_ARG, "NULL tree");
     if (n) *n = t->n;
-    if (levels) *levels = t->L;
+    if (levels) *levels = t->Lmax;
     if (nbox) *nbox = t->nbox;
+    return FMM_OK;
+}
+
+int fmm_tree_num_instances(fmm_tree t)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    return t->n_inst;
+}
+
+int fmm_tree_instance(fmm_tree t, int i, int64_t* p0, int64_t* n, int* levels, int64_t* b0, int64_t* nbox,
+                      int64_t* lb0)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (i < 0 || i >= t->n_inst) return fail(FMM_ERR_ARG, "instance %d outside [0, %d)", i, t->n_inst);
+    const Inst& S = t->hinst[i];
+    if (p0) *p0 = S.p0;
+    if (n) *n = S.n;
+    if (levels) *levels = S.L;
+    if (b0) *b0 = S.b0;
+    if (nbox) *nbox = S.nbox;
+    if (lb0) *lb0 = S.lb0;
     return FMM_OK;
 }
 
@@ -223,39 +261,61 @@ void fmm_tree_destroy(fmm_tree t)
     free_tree(t);
 }
 
+namespace {
+
+int lists_create_impl(fmm_tree t, const int64_t* wcap, const int64_t* scap, fmm_lists* out)
+{
+    fmm_lists l = new (std::nothrow) fmm_lists_s();
+    if (!l) return fail(FMM_ERR_OOM, "host allocation");
+    l->tree = t;
+    int rc;
+    try {
+        rc = lists_alloc(t, l, wcap, scap);
+    } catch (...) {
+        rc = fail(FMM_ERR_OOM, "host allocation");
+    }
+    if (rc) {
+        free_lists(l);
+        return rc;
+    }
+    *out = l;
+    return FMM_OK;
+}
+
+}  // namespace
+
 int fmm_lists_create(fmm_tree t, int64_t weak_capacity, int64_t strong_capacity, fmm_lists* out)
 {
     if (!t || !out) return fail(FMM_ERR_ARG, "NULL argument");
     *out = nullptr;
     GUARD(t->dev);
-    if (weak_capacity <= 0) weak_capacity = 64 * t->nbox;
-    if (strong_capacity <= 0) strong_capacity = 32 * t->nbox;
     if (weak_capacity >= INT32_MAX || strong_capacity >= INT32_MAX)
         return fail(FMM_ERR_ARG, "capacity must be below 2^31 - 1");
-    fmm_lists l = new (std::nothrow) fmm_lists_s();
-    if (!l) return fail(FMM_ERR_OOM, "host allocation");
-    l->tree = t;
-    l->wcap = weak_capacity;
-    l->scap = strong_capacity;
-    bool ok = cudaMalloc((void**)&l->woff, 4 * (t->nbox + 1)) == cudaSuccess &&
-              cudaMalloc((void**)&l->soff, 4 * (t->nbox + 1)) == cudaSuccess &&
-              cudaMalloc((void**)&l->widx, 4 * std::max<int64_t>(l->wcap, 1)) == cudaSuccess &&
-              cudaMalloc((void**)&l->wtgt, 4 * std::max<int64_t>(l->wcap, 1)) == cudaSuccess &&
-              cudaMalloc((void**)&l->sidx, 4 * std::max<int64_t>(l->scap, 1)) == cudaSuccess &&
-              cudaMalloc((void**)&l->stgt, 4 * std::max<int64_t>(l->scap, 1)) == cudaSuccess &&
-              cudaMalloc((void**)&l->flags, lists_flag_bytes(l->scap)) == cudaSuccess &&
-              cudaMalloc((void**)&l->tilecnt, 4 * lists_tile_words(l->scap)) == cudaSuccess &&
-              cudaMalloc((void**)&l->status, 4) == cudaSuccess;
-    if (!ok) {
-        free_lists(l);
-        return fail(FMM_ERR_OOM, "list storage");
+    // one instance: the capacities as given; several: shared out in proportion to the box counts
+    std::vector<int64_t> w(t->n_inst), st(t->n_inst);
+    for (int i = 0; i < t->n_inst; i++) {
+        const Inst& S = t->hinst[i];
+        const double share = (double)S.nbox / (double)t->nbox;
+        w[i] = weak_capacity <= 0 ? 64 * S.nbox
+               : t->n_inst == 1   ? weak_capacity
+                                  : std::max<int64_t>(16 * S.nbox, (int64_t)(share * (double)weak_capacity));
+        st[i] = strong_capacity <= 0 ? 32 * S.nbox
+                : t->n_inst == 1     ? strong_capacity
+                                     : std::max<int64_t>(8 * S.nbox, (int64_t)(share * (double)strong_capacity));
     }
-    if (cudaMemset(l->status, 0, 4) != cudaSuccess) {
-        free_lists(l);
-        return fail(FMM_ERR_CUDA, "memset");
-    }
-    *out = l;
-    return FMM_OK;
+    return lists_create_impl(t, w.data(), st.data(), out);
+}
+
+int fmm_lists_create_batched(fmm_tree t, const int64_t* weak_capacity, const int64_t* strong_capacity,
+                             fmm_lists* out)
+{
+    if (!t || !out || !weak_capacity || !strong_capacity) return fail(FMM_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    GUARD(t->dev);
+    for (int i = 0; i < t->n_inst; i++)
+        if (weak_capacity[i] < 1 || strong_capacity[i] < 1)
+            return fail(FMM_ERR_ARG, "instance %d: capacities must be positive", i);
+    return lists_create_impl(t, weak_capacity, strong_capacity, out);
 }
 
 int fmm_interaction_lists(fmm_tree t, fmm_lists l, double theta, void* stream)
@@ -268,41 +328,102 @@ int fmm_interaction_lists(fmm_tree t, fmm_lists l, double theta, void* stream)
     return lists_build(t, l, theta, (cudaStream_t)stream);
 }
 
-int fmm_lists_sync(fmm_lists l, void* stream, int64_t* n_weak, int64_t* n_strong)
+namespace {
+
+// Per-instance entry counts (ends of the CSR offsets) and the list status word.
+int read_counts(fmm_lists l, cudaStream_t s, std::vector<int32_t>& woff, std::vector<int32_t>& soff,
+                int32_t& st)
+{
+    fmm_tree t = l->tree;
+    const int64_t m = t->nbox + t->n_inst;
+    woff.resize(m);
+    soff.resize(m);
+    FMM_CUDA(cudaStreamSynchronize(s));
+    FMM_CUDA(cudaMemcpy(woff.data(), l->woff, 4 * m, cudaMemcpyDeviceToHost));
+    FMM_CUDA(cudaMemcpy(soff.data(), l->soff, 4 * m, cudaMemcpyDeviceToHost));
+    FMM_CUDA(cudaMemcpy(&st, l->status, 4, cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+}  // namespace
+
+int fmm_lists_counts(fmm_lists l, void* stream, int64_t* n_weak, int64_t* n_strong)
 {
     if (!l) return fail(FMM_ERR_ARG, "NULL lists");
     if (!l->built) return fail(FMM_ERR_STATE, "lists not built");
     GUARD(l->tree->dev);
-    FMM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-    int32_t w = 0, s = 0, st = 0;
-    FMM_CUDA(cudaMemcpy(&w, l->woff + l->tree->nbox, 4, cudaMemcpyDeviceToHost));
-    FMM_CUDA(cudaMemcpy(&s, l->soff + l->tree->nbox, 4, cudaMemcpyDeviceToHost));
-    FMM_CUDA(cudaMemcpy(&st, l->status, 4, cudaMemcpyDeviceToHost));
-    if (n_weak) *n_weak = w;
-    if (n_strong) *n_strong = s;
-    if (st & ST_CAPACITY) return fail(FMM_ERR_CAPACITY, "lists need %d weak / %d strong entries, capacity %lld / %lld",
-                                      w, s, (long long)l->wcap, (long long)l->scap);
+    std::vector<int32_t> wo, so;
+    int32_t st = 0;
+    int rc = read_counts(l, (cudaStream_t)stream, wo, so, st);
+    if (rc) return rc;
+    fmm_tree t = l->tree;
+    int bad = -1;
+    for (int i = 0; i < t->n_inst; i++) {
+        const Inst& S = t->hinst[i];
+        const LInst& T = l->hlinst[i];
+        const int64_t w = wo[S.o0 + S.nbox], sc = so[S.o0 + S.nbox];
+        if (n_weak) n_weak[i] = w;
+        if (n_strong) n_strong[i] = sc;
+        if (bad < 0 && (w > T.wcap || sc > T.scap)) bad = i;
+    }
+    if (st & ST_CAPACITY) {
+        if (bad < 0) bad = 0;
+        const Inst& S = t->hinst[bad];
+        return fail(FMM_ERR_CAPACITY, "instance %d: lists need %d weak / %d strong entries, capacity %lld / %lld",
+                    bad, wo[S.o0 + S.nbox], so[S.o0 + S.nbox], (long long)l->hlinst[bad].wcap,
+                    (long long)l->hlinst[bad].scap);
+    }
+    return FMM_OK;
+}
+
+int fmm_lists_sync(fmm_lists l, void* stream, int64_t* n_weak, int64_t* n_strong)
+{
+    if (!l) return fail(FMM_ERR_ARG, "NULL lists");
+    if (!l->built) return fail(FMM_ERR_STATE, "lists not built");
+    const int ni = l->tree->n_inst;
+    std::vector<int64_t> w(ni), st(ni);
+    const int rc = fmm_lists_counts(l, stream, w.data(), st.data());
+    int64_t sw = 0, ss = 0;
+    for (int i = 0; i < ni; i++) {
+        sw += w[i];
+        ss += st[i];
+    }
+    if (n_weak) *n_weak = sw;
+    if (n_strong) *n_strong = ss;
+    return rc;
+}
+
+int fmm_lists_export_instance(fmm_lists l, int i, int32_t* woff, int32_t* widx, int32_t* soff, int32_t* sidx,
+                              void* stream)
+{
+    if (!l) return fail(FMM_ERR_ARG, "NULL lists");
+    if (!l->built) return fail(FMM_ERR_STATE, "lists not built");
+    fmm_tree t = l->tree;
+    if (i < 0 || i >= t->n_inst) return fail(FMM_ERR_ARG, "instance %d outside [0, %d)", i, t->n_inst);
+    GUARD(t->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Inst& S = t->hinst[i];
+    const LInst& T = l->hlinst[i];
+    FMM_CUDA(cudaStreamSynchronize(s));
+    int32_t w = 0, st = 0;
+    FMM_CUDA(cudaMemcpy(&w, l->woff + S.o0 + S.nbox, 4, cudaMemcpyDeviceToHost));
+    FMM_CUDA(cudaMemcpy(&st, l->soff + S.o0 + S.nbox, 4, cudaMemcpyDeviceToHost));
+    const int64_t nb = S.nbox + 1;
+    if (woff) FMM_CUDA(cudaMemcpyAsync(woff, l->woff + S.o0, 4 * nb, cudaMemcpyDeviceToDevice, s));
+    if (soff) FMM_CUDA(cudaMemcpyAsync(soff, l->soff + S.o0, 4 * nb, cudaMemcpyDeviceToDevice, s));
+    if (widx && w > 0)
+        FMM_CUDA(cudaMemcpyAsync(widx, l->widx + T.w0, 4 * std::min<int64_t>(w, T.wcap), cudaMemcpyDeviceToDevice, s));
+    if (sidx && st > 0)
+        FMM_CUDA(cudaMemcpyAsync(sidx, l->sidx + T.s0, 4 * std::min<int64_t>(st, T.scap), cudaMemcpyDeviceToDevice, s));
     return FMM_OK;
 }
 
 int fmm_lists_export(fmm_lists l, int32_t* woff, int32_t* widx, int32_t* soff, int32_t* sidx, void* stream)
 {
     if (!l) return fail(FMM_ERR_ARG, "NULL lists");
-    if (!l->built) return fail(FMM_ERR_STATE, "lists not built");
-    GUARD(l->tree->dev);
-    cudaStream_t s = (cudaStream_t)stream;
-    FMM_CUDA(cudaStreamSynchronize(s));
-    int32_t w = 0, st = 0;
-    FMM_CUDA(cudaMemcpy(&w, l->woff + l->tree->nbox, 4, cudaMemcpyDeviceToHost));
-    FMM_CUDA(cudaMemcpy(&st, l->soff + l->tree->nbox, 4, cudaMemcpyDeviceToHost));
-    const int64_t nb = l->tree->nbox + 1;
-    if (woff) FMM_CUDA(cudaMemcpyAsync(woff, l->woff, 4 * nb, cudaMemcpyDeviceToDevice, s));
-    if (soff) FMM_CUDA(cudaMemcpyAsync(soff, l->soff, 4 * nb, cudaMemcpyDeviceToDevice, s));
-    if (widx && w > 0)
-        FMM_CUDA(cudaMemcpyAsync(widx, l->widx, 4 * std::min<int64_t>(w, l->wcap), cudaMemcpyDeviceToDevice, s));
-    if (sidx && st > 0)
-        FMM_CUDA(cudaMemcpyAsync(sidx, l->sidx, 4 * std::min<int64_t>(st, l->scap), cudaMemcpyDeviceToDevice, s));
-    return FMM_OK;
+    if (l->tree->n_inst != 1)
+        return fail(FMM_ERR_ARG, "the tree holds %d instances: use fmm_lists_export_instance", l->tree->n_inst);
+    return fmm_lists_export_instance(l, 0, woff, widx, soff, sidx, stream);
 }
 
 void fmm_lists_destroy(fmm_lists l)
@@ -322,6 +443,29 @@ int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
         return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
     GUARD(t->dev);
     return evaluate(t, l, q, *prm, phi, (cudaStream_t)stream);
+}
+
+int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi, void* stream,
+                 int* m2l_blocks, int* p2p_blocks)
+{
+    if (!t || !l || !q || !prm || !phi) return fail(FMM_ERR_ARG, "NULL argument");
+    if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
+    if (!t->built || !l->built) return fail(FMM_ERR_STATE, "tree or lists not built");
+    if (prm->p < 0 || prm->p > 40) return fail(FMM_ERR_ARG, "p = %d outside [0, 40]", prm->p);
+    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED)
+        return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
+    GUARD(t->dev);
+    return autotune(t, l, q, *prm, phi, (cudaStream_t)stream, m2l_blocks, p2p_blocks);
+}
+
+int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (m2l_blocks < 0 || p2p_blocks < 0 || m2l_blocks > 65535 || p2p_blocks > 65535)
+        return fail(FMM_ERR_ARG, "block counts must lie in [0, 65535]");
+    t->tune_m2l_blocks = m2l_blocks;
+    t->tune_p2p_blocks = p2p_blocks;
+    return FMM_OK;
 }
 
 int fmm_direct(const double* x, const double* y, const double* q, int64_t n, const int64_t* targets,

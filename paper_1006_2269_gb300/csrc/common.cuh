@@ -97,24 +97,57 @@ __device__ __forceinline__ void descend_node(int64_t n, int depth, int64_t j, in
 }  // namespace fmm
 
 // ---------------------------------------------------------------------------------------------
-// Handles
+// Handles.  A tree handle holds a forest: one or more independent instances (point sets) whose
+// arrays are concatenated.  Every kernel processes all instances of a launch, finds its instance
+// from a block index and offsets its pointers with the instance's entry of the table below, so the
+// kernel bodies index one instance's arrays exactly as for a single point set.
 // ---------------------------------------------------------------------------------------------
+namespace fmm {
+
+struct Inst {
+    int64_t p0, n;        // points [p0, p0 + n) of the concatenated point arrays
+    int64_t b0, nbox;     // boxes [b0, b0 + nbox), level order inside the instance
+    int64_t o0;           // CSR offsets of the lists: [o0, o0 + nbox + 1) (o0 = b0 + instance)
+    int64_t t0, ntiles;   // tree-build tiles [t0, t0 + ntiles)
+    int64_t ob0;          // ones-before tables: 2^(2L) - 1 entries
+    int64_t no0;          // node-offset tables: 2^(2L+1) + 2L entries
+    int64_t lb0;          // leaf offsets: 4^L + 1 entries
+    int32_t L, pad;
+};
+
+struct LInst {            // list storage of one instance
+    int64_t w0, wcap;     // weak entries [w0, w0 + wcap)
+    int64_t s0, scap;     // strong entries [s0, s0 + scap)
+    int64_t f0;           // candidate flags [f0, f0 + 16 scap + tile)
+    int64_t c0;           // candidate tile counts
+};
+
+}  // namespace fmm
+
 struct fmm_tree_s {
     int dev = 0;
-    int64_t n = 0;
-    int L = 0;
-    int64_t nbox = 0, nleaf = 0;
-    int64_t ntiles = 0;  // tiles of the sort / partition kernels
+    int n_inst = 0;
+    int Lmax = 0;
+    int64_t n = 0;          // total points
+    int64_t nbox = 0;       // total boxes
+    int64_t ntiles = 0;     // total tree-build tiles
+    int64_t max_tiles = 0;  // largest per-instance tile count
+    int64_t max_n = 0;      // largest instance
+    int64_t nleaf = 0;      // total leaves
+    int64_t n_ob = 0, n_no = 0;
+    fmm::Inst* hinst = nullptr;   // host copy of the instance table [n_inst]
+    fmm::Inst* dinst = nullptr;   // device copy
+    bool own_hinst = true;
 
-    // products of the build (device)
+    // products of the build (device; concatenated over instances)
     double* rects = nullptr;     // [nbox][4] (x0, x1, y0, y1)
     double* centers = nullptr;   // [nbox][2]
     double* radii = nullptr;     // [nbox]
     float* rad32 = nullptr;      // [nbox] radii rounded to binary32
     float* cen_hi = nullptr;     // [nbox][2] float part of the centre
     float* cen_lo = nullptr;     // [nbox][2] float remainder (centre - hi)
-    int32_t* perm = nullptr;     // [n] canonical order -> input index
-    int32_t* leaf_begin = nullptr;  // [nleaf + 1]
+    int32_t* perm = nullptr;     // [n] canonical order -> input index (local to the instance)
+    int32_t* leaf_begin = nullptr;  // per instance [4^L + 1], local positions
     int32_t* leaf_of = nullptr;  // [n] leaf of each input index
     int32_t* cleaf = nullptr;    // [n] leaf of each canonical position
     double* xs = nullptr;        // [n] x in canonical order
@@ -125,13 +158,13 @@ struct fmm_tree_s {
     // build scratch (device)
     uint64_t* keys = nullptr;    // [4][n] ping-pong keys for the x and y sorts
     int32_t* vals = nullptr;     // [4][n] ping-pong values
-    uint32_t* rs_counts = nullptr;  // [2][256][ntiles]
-    uint32_t* rs_totals = nullptr;  // [2][256]
+    uint32_t* rs_counts = nullptr;  // [2][256][ntiles] (per instance: [2][256][its tiles])
+    uint32_t* rs_totals = nullptr;  // [n_inst][2][256]
     uint32_t* tilecnt = nullptr;    // [ntiles]
     uint8_t* hflag = nullptr;       // [2][n] per input index: x-half / y-half bit
-    uint64_t* bbox_keys = nullptr;  // [4] ordered keys of xmin, xmax, ymin, ymax
-    int32_t* ones_before = nullptr;  // concatenated per depth 0 .. 2L-1: [2^depth]
-    int32_t* node_off = nullptr;     // node offsets per depth 0 .. 2L: [2^depth + 1]
+    uint64_t* bbox_keys = nullptr;  // [n_inst][4] ordered keys of xmin, xmax, ymin, ymax
+    int32_t* ones_before = nullptr;  // per instance, per depth 0 .. 2L-1: [2^depth]
+    int32_t* node_off = nullptr;     // per instance, node offsets per depth 0 .. 2L: [2^depth + 1]
     int32_t* segs = nullptr;         // [4][n] box index carried by the items of X and Y
     int32_t* status = nullptr;       // device status word
 
@@ -144,20 +177,26 @@ struct fmm_tree_s {
     void* pk64 = nullptr;   // [n] double4 (x, y, q, 0) in canonical order (binary64 path)
     void* pk32 = nullptr;   // [n] float4 (x - c_leaf, y - c_leaf, q, 0) (binary32 path)
     double* acc = nullptr;  // [n] binary64 potential accumulator in canonical order
-    float* acc32 = nullptr; // [3n] binary32 far field, near-field hi and lo (canonical order)
+    float* acc32 = nullptr; // [4n] binary32 far field hi and lo, near field hi and lo (canonical order)
+    float* Lf0lo = nullptr; // [nbox] low part of Re b_0 of the binary32 locals (float-float)
+
+    // launch tuning (set by fmm_autotune; 0 = defaults)
+    int tune_m2l_blocks = 0, tune_p2p_blocks = 0;
     bool built = false;
 };
 
 struct fmm_lists_s {
     fmm_tree tree = nullptr;
-    int64_t wcap = 0, scap = 0;
-    int32_t* woff = nullptr;  // [nbox + 1]
-    int32_t* soff = nullptr;  // [nbox + 1]
-    int32_t* widx = nullptr;  // [wcap] within-level index of the source box
-    int32_t* wtgt = nullptr;  // [wcap] global id of the target box of each weak entry
-    int32_t* sidx = nullptr;  // [scap]
-    int32_t* stgt = nullptr;  // [scap]
-    uint8_t* flags = nullptr;     // [16 * scap] weak flag per candidate of the level being built
+    int64_t wcap = 0, scap = 0;   // totals over instances
+    fmm::LInst* hlinst = nullptr;
+    fmm::LInst* dlinst = nullptr;
+    int32_t* woff = nullptr;  // per instance [nbox + 1], local entry positions
+    int32_t* soff = nullptr;
+    int32_t* widx = nullptr;  // within-level index of the source box
+    int32_t* wtgt = nullptr;  // local box id of the target box of each weak entry
+    int32_t* sidx = nullptr;
+    int32_t* stgt = nullptr;
+    uint8_t* flags = nullptr;     // weak flag per candidate of the level being built
     uint32_t* tilecnt = nullptr;  // per-tile weak counts of the level being built
     int32_t* status = nullptr;
     double theta = 0.0;
@@ -167,19 +206,26 @@ struct fmm_lists_s {
 namespace fmm {
 
 // tree.cu
-int tree_alloc(fmm_tree t);
+int tree_alloc(fmm_tree t, int n_inst, const int64_t* n, const int* levels);
+void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls);
+void forest_totals(fmm_tree t);
+int blocks_for(int64_t n, int threads, int n_inst);
+int tree_tables_host(int64_t n, int L, int32_t* ones_before, int32_t* node_off, int32_t* leaf_begin);
 int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s);
 
 // lists.cu
 int lists_build(fmm_tree t, fmm_lists l, double theta, cudaStream_t s);
 int64_t lists_flag_bytes(int64_t scap);
 int64_t lists_tile_words(int64_t scap);
+int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int64_t* strong_capacity);
 
 // expand.cu
 int evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,
              cudaStream_t s);
 int direct(const double* x, const double* y, const double* q, int64_t n, const int64_t* tgt,
            int64_t m, double* phi, cudaStream_t s);
+int autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,
+             cudaStream_t s, int* m2l_blocks, int* p2p_blocks);
 
 // scan.cu: exclusive scan of int32 counts with a base value read from device memory:
 // out[i] = base[0] + sum_{j < i} in[j] for i = 0..m (out has m + 1 entries; out may alias

@@ -39,6 +39,7 @@ __constant__ double c_binom[PMAXC][PMAXC];  // C(n, k), n < PMAXC
 
 namespace {
 
+constexpr double MIXED_TOL_FLOOR = 1e-7;  // smallest tolerance the binary32 path is asked for
 constexpr int M2L_CH = 8;   // consecutive weak pairs per lane
 constexpr int P2P_CH = 16;  // consecutive leaf pairs per warp
 
@@ -103,6 +104,7 @@ struct Geo<double> {
         return {cen[2 * a] - cen[2 * b], cen[2 * a + 1] - cen[2 * b + 1]};
     }
     __device__ __forceinline__ double radius(int64_t g) const { return rad[g]; }
+    __device__ __forceinline__ Geo shift(int64_t b0) const { return Geo{cen + 2 * b0, rad + b0}; }
     // (z - c_g) / rho_g for a point stored with absolute coordinates (0 when rho_g = 0)
     __device__ __forceinline__ cx<double> local(int64_t g, double x, double y) const
     {
@@ -123,6 +125,7 @@ struct Geo<float> {
         return {(ha.x - hb.x) + (la.x - lb.x), (ha.y - hb.y) + (la.y - lb.y)};
     }
     __device__ __forceinline__ float radius(int64_t g) const { return rad[g]; }
+    __device__ __forceinline__ Geo shift(int64_t b0) const { return Geo{hi + 2 * b0, lo + 2 * b0, rad + b0}; }
     // the point is stored as its offset from the centre of leaf g
     __device__ __forceinline__ cx<float> local(int64_t g, float x, float y) const
     {
@@ -135,6 +138,27 @@ struct Geo<float> {
 
 __device__ __forceinline__ double log_d(double x) { return log(x); }
 __device__ __forceinline__ float log_d(float x) { return logf(x); }
+
+// Float-float accumulation (Knuth's two-sum): hi + lo holds a sum whose rounding errors are
+// carried in lo instead of lost.
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float v)
+{
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
+// hi + lo += vhi + vlo on values shared between threads: the atomic addition returns the value it
+// found, so the rounding error of the sum it stored is recovered exactly by a two-sum and added to
+// lo with the incoming low part.
+__device__ __forceinline__ void atomic_add_ff(float* hi, float* lo, float vhi, float vlo)
+{
+    const float old = atomicAdd(hi, vhi);
+    const float s = old + vhi;
+    const float bb = s - old;
+    atomicAdd(lo, ((old - (s - bb)) + (vhi - bb)) + vlo);
+}
 
 template <typename T>
 struct Pk;  // packed point
@@ -149,11 +173,20 @@ struct alignas(16) Pk<float> {
 
 // ---- strengths into canonical order, packed with the coordinates ----
 template <typename T>
-__global__ void k_pack(const int32_t* __restrict__ perm, const double* __restrict__ q,
-                       const double* __restrict__ xs, const double* __restrict__ ys,
-                       const float* __restrict__ dxf, const float* __restrict__ dyf, int64_t n,
-                       Pk<T>* __restrict__ pk, int32_t* status)
+__global__ void k_pack(const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+                       const double* __restrict__ q, const double* __restrict__ xs,
+                       const double* __restrict__ ys, const float* __restrict__ dxf,
+                       const float* __restrict__ dyf, Pk<T>* __restrict__ pk, int32_t* status)
 {
+    const Inst S = I[blockIdx.y];
+    perm += S.p0;
+    q += S.p0;
+    xs += S.p0;
+    ys += S.p0;
+    dxf += S.p0;
+    dyf += S.p0;
+    pk += S.p0;
+    const int64_t n = S.n;
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -176,14 +209,20 @@ __global__ void k_pack(const int32_t* __restrict__ perm, const double* __restric
 
 // ---- P2M: one warp per leaf, one lane per point; column sums through shared memory ----
 template <typename T>
-__global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, const Pk<T>* __restrict__ pk,
-                      Geo<T> geo, cx<T>* __restrict__ Me)
+__global__ void k_p2m(const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ lb,
+                      const Pk<T>* __restrict__ pk, Geo<T> geo, cx<T>* __restrict__ Me)
 {
     extern __shared__ unsigned char smem[];
+    const Inst S = I[blockIdx.y];
+    const int L = S.L;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const int64_t b = (int64_t)blockIdx.x * wpb + w;
-    if (b >= level_size(L)) return;
-    cx<T>* S = (cx<T>*)smem + (size_t)w * 33 * P;
+    if (L < 1 || b >= level_size(L)) return;
+    lb += S.lb0;
+    pk += S.p0;
+    geo = geo.shift(S.b0);
+    Me += S.b0 * PS;
+    cx<T>* Sm = (cx<T>*)smem + (size_t)w * 33 * P;
     const int64_t g = level_base(L) + b;
     const int32_t t0 = lb[b], t1 = lb[b + 1];
     cx<T> acc[2] = {{0, 0}, {0, 0}};
@@ -198,13 +237,13 @@ __global__ void k_p2m(int L, int P, int PS, const int32_t* __restrict__ lb, cons
         }
         cx<T> pw = {qq, 0};
         for (int k = 0; k < P; k++) {
-            S[k * 33 + lane] = pw;
+            Sm[k * 33 + lane] = pw;
             pw = cmul(pw, xi_c);
         }
         __syncwarp();
         for (int k = lane, s = 0; k < P; k += 32, s++) {
             cx<T> sum = {0, 0};
-            for (int j = 0; j < 32; j++) sum = cadd(sum, S[k * 33 + j]);
+            for (int j = 0; j < 32; j++) sum = cadd(sum, Sm[k * 33 + j]);
             acc[s] = cadd(acc[s], sum);
         }
         __syncwarp();
@@ -223,9 +262,13 @@ __device__ __forceinline__ void load_binom(T* B, int P)
 
 // ---- M2M: one warp per parent, one lane per output coefficient ----
 template <typename T>
-__global__ void k_m2m(int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Me)
+__global__ void k_m2m(const Inst* __restrict__ I, int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Me)
 {
     extern __shared__ unsigned char smem[];
+    const Inst S = I[blockIdx.y];
+    if (l + 1 > S.L) return;
+    geo = geo.shift(S.b0);
+    Me += S.b0 * PS;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     T* B = (T*)smem;
     cx<T>* D = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
@@ -266,12 +309,24 @@ __global__ void k_m2m(int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Me)
 // scaled source coefficients and the partial sums live in registers, the constant matrix is read
 // from the constant bank by the unrolled contraction.
 template <typename T, int PI>
-__global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t* __restrict__ woff,
+__global__ void __launch_bounds__(128) k_m2l_pairs(const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+                                                   int P, int PS, const int32_t* __restrict__ woff,
                                                    const int32_t* __restrict__ widx,
-                                                   const int32_t* __restrict__ wtgt, int64_t wcap,
-                                                   int64_t nbox, Geo<T> geo,
-                                                   const cx<T>* __restrict__ Me, cx<T>* __restrict__ Le)
+                                                   const int32_t* __restrict__ wtgt, Geo<T> geo,
+                                                   const cx<T>* __restrict__ Me, cx<T>* __restrict__ Le,
+                                                   float* __restrict__ L0lo)
 {
+    const Inst S = I[blockIdx.y];
+    const LInst TL = LIs[blockIdx.y];
+    if (S.L < 1) return;
+    woff += S.o0;
+    widx += TL.w0;
+    wtgt += TL.w0;
+    const int64_t wcap = TL.wcap, nbox = S.nbox;
+    geo = geo.shift(S.b0);
+    Me += S.b0 * PS;
+    Le += S.b0 * PS;
+    L0lo += S.b0;
     const int lane = threadIdx.x & 31;
     const int64_t e_begin = woff[1];
     const int64_t e_end = min((int64_t)woff[nbox], wcap);
@@ -280,7 +335,10 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t*
     for (int64_t wb = e_begin + warp * 32 * M2L_CH; wb < e_end; wb += nwarps * 32 * M2L_CH) {
         const int64_t e0 = wb + (int64_t)lane * M2L_CH;
         const int64_t e1 = min(e0 + M2L_CH, e_end);
+        // Re b_0 carries the whole far potential (large terms that cancel little): it is summed
+        // in float-float, acc[0].re + lo0, and added to the box as hi/lo
         cx<T> acc[PI];
+        T lo0 = 0;
 #pragma unroll
         for (int j = 0; j < PI; j++) acc[j] = {0, 0};
         int64_t cur = -1;
@@ -288,8 +346,10 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t*
             const int64_t g = wtgt[e];
             if (g != cur) {
                 if (cur >= 0) {
+                    atomic_add_ff(&Le[cur * PS].re, &L0lo[cur], acc[0].re, lo0);
+                    atomicAdd(&Le[cur * PS].im, acc[0].im);
 #pragma unroll
-                    for (int j = 0; j < PI; j++)
+                    for (int j = 1; j < PI; j++)
                         if (j < P) {
                             atomicAdd(&Le[cur * PS + j].re, acc[j].re);
                             atomicAdd(&Le[cur * PS + j].im, acc[j].im);
@@ -297,6 +357,7 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t*
                 }
 #pragma unroll
                 for (int j = 0; j < PI; j++) acc[j] = {0, 0};
+                lo0 = 0;
                 cur = g;
             }
             const int64_t sg = level_base(level_of(g)) + widx[e];
@@ -328,8 +389,13 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t*
                     y.re += m * xv.re;
                     y.im += m * xv.im;
                 }
-                if (o == 0) y.re += a0 * (T)0.5 * log_d(r2);
-                acc[o] = cfma(vp, y, acc[o]);
+                if (o == 0) {
+                    two_sum(acc[0].re, lo0, a0 * (T)0.5 * log_d(r2));
+                    two_sum(acc[0].re, lo0, y.re);
+                    acc[0].im += y.im;
+                } else {
+                    acc[o] = cfma(vp, y, acc[o]);
+                }
                 vp = cmul(vp, v2);
             }
         }
@@ -339,20 +405,28 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t*
         for (int off = 1; off < 32; off <<= 1) {
             const int64_t pkey = __shfl_down_sync(0xffffffffu, cur, off);
             const bool take = (lane + off < 32) && pkey == cur;
+            const T plo = __shfl_down_sync(0xffffffffu, lo0, off);
 #pragma unroll
             for (int j = 0; j < PI; j++) {
                 const T pr = __shfl_down_sync(0xffffffffu, acc[j].re, off);
                 const T pi = __shfl_down_sync(0xffffffffu, acc[j].im, off);
                 if (take) {
-                    acc[j].re += pr;
+                    if (j == 0) {
+                        two_sum(acc[0].re, lo0, pr);
+                        lo0 += plo;
+                    } else {
+                        acc[j].re += pr;
+                    }
                     acc[j].im += pi;
                 }
             }
         }
         const int64_t prev = __shfl_up_sync(0xffffffffu, cur, 1);
         if (cur >= 0 && (lane == 0 || prev != cur)) {
+            atomic_add_ff(&Le[cur * PS].re, &L0lo[cur], acc[0].re, lo0);
+            atomicAdd(&Le[cur * PS].im, acc[0].im);
 #pragma unroll
-            for (int j = 0; j < PI; j++)
+            for (int j = 1; j < PI; j++)
                 if (j < P) {
                     atomicAdd(&Le[cur * PS + j].re, acc[j].re);
                     atomicAdd(&Le[cur * PS + j].im, acc[j].im);
@@ -363,14 +437,25 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(int P, int PS, const int32_t*
 
 // ---- M2L, binary64: same decomposition, runtime P, operands and partial sums in shared memory
 // (one thread's column of X and A; the binary64 pipe bounds this kernel) ----
-__global__ void __launch_bounds__(64) k_m2l_pairs_f64(int P, int PS, const int32_t* __restrict__ woff,
+__global__ void __launch_bounds__(64) k_m2l_pairs_f64(const Inst* __restrict__ I,
+                                                      const LInst* __restrict__ LIs, int P, int PS,
+                                                      const int32_t* __restrict__ woff,
                                                       const int32_t* __restrict__ widx,
-                                                      const int32_t* __restrict__ wtgt, int64_t wcap,
-                                                      int64_t nbox, Geo<double> geo,
+                                                      const int32_t* __restrict__ wtgt, Geo<double> geo,
                                                       const cx<double>* __restrict__ Me,
                                                       cx<double>* __restrict__ Le)
 {
     extern __shared__ unsigned char smem[];
+    const Inst S = I[blockIdx.y];
+    const LInst TL = LIs[blockIdx.y];
+    if (S.L < 1) return;
+    woff += S.o0;
+    widx += TL.w0;
+    wtgt += TL.w0;
+    const int64_t wcap = TL.wcap, nbox = S.nbox;
+    geo = geo.shift(S.b0);
+    Me += S.b0 * PS;
+    Le += S.b0 * PS;
     const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31;
     cx<double>* X = (cx<double>*)smem;  // X[k * nt + tid]
     cx<double>* A = X + (size_t)P * nt;  // A[o * nt + tid]
@@ -445,9 +530,15 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(int P, int PS, const int32
 
 // ---- L2L: one warp per child box of level l+1 ----
 template <typename T>
-__global__ void k_l2l(int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Le)
+__global__ void k_l2l(const Inst* __restrict__ I, int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Le,
+                      float* __restrict__ L0lo)
 {
     extern __shared__ unsigned char smem[];
+    const Inst S = I[blockIdx.y];
+    if (l + 1 > S.L) return;
+    geo = geo.shift(S.b0);
+    Le += S.b0 * PS;
+    if constexpr (sizeof(T) == 4) L0lo += S.b0;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     T* Bn = (T*)smem;
     cx<T>* B = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
@@ -466,6 +557,22 @@ __global__ void k_l2l(int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Le)
     for (int j = lane; j < P; j += 32) B[j] = Le[pg * PS + j];
     __syncwarp();
     for (int o = lane; o < P; o += 32) {
+        if constexpr (sizeof(T) == 4) {
+            if (o == 0) {
+                // child b_0 = parent b_0 + sum_{k >= 1} b_k w^k, added to the child's hi/lo pair
+                cx<T> h = {0, 0};
+                for (int k = P - 1; k >= 1; k--) h = cfma(h, wv, B[k]);
+                const cx<T> r = cmul(h, wv);
+                T hi = Le[cg * PS].re, lo = L0lo[cg] + L0lo[pg];
+                two_sum(hi, lo, B[0].re);
+                two_sum(hi, lo, r.re);
+                const T sum = hi + lo;
+                L0lo[cg] = lo - (sum - hi);
+                Le[cg * PS].re = sum;
+                Le[cg * PS].im += B[0].im + r.im;
+                continue;
+            }
+        }
         cx<T> h = cscale(B[P - 1], Bn[(P - 1) * P + o]);
         for (int k = P - 2; k >= o; k--) h = cfma(h, wv, cscale(B[k], Bn[k * P + o]));
         const cx<T> r = cscale(h, ipow(s, o));
@@ -477,19 +584,40 @@ __global__ void k_l2l(int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Le)
 // binary64 path: writes the binary64 accumulator.  binary32 path: writes the binary32 far field;
 // the near-field accumulators are combined with it at the end.
 template <typename T>
-__global__ void k_l2p(int L, int P, int PS, int64_t n, const int32_t* __restrict__ cleaf,
+__global__ void k_l2p(const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ cleaf,
                       const Pk<T>* __restrict__ pk, Geo<T> geo, const cx<T>* __restrict__ Le,
-                      T* __restrict__ far)
+                      const float* __restrict__ L0lo, T* __restrict__ far, float* __restrict__ farlo)
 {
+    const Inst S = I[blockIdx.y];
+    const int L = S.L;
+    const int64_t n = S.n;
+    cleaf += S.p0;
+    pk += S.p0;
+    far += S.p0;
+    geo = geo.shift(S.b0);
+    Le += S.b0 * PS;
+    if constexpr (sizeof(T) == 4) {
+        L0lo += S.b0;
+        farlo += S.p0;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = level_base(L) + cleaf[i];
         const Pk<T> p = pk[i];
         const cx<T> z = geo.local(g, p.x, p.y);
         const cx<T>* B = Le + g * PS;
-        cx<T> h = B[P - 1];
-        for (int k = P - 2; k >= 0; k--) h = cfma(h, z, B[k]);
-        far[i] = h.re;
+        if constexpr (sizeof(T) == 4) {
+            cx<T> h = {0, 0};
+            for (int k = P - 1; k >= 1; k--) h = cfma(h, z, B[k]);
+            T hi = B[0].re, lo = L0lo[g];
+            two_sum(hi, lo, cmul(h, z).re);
+            far[i] = hi;
+            farlo[i] = lo;
+        } else {
+            cx<T> h = B[P - 1];
+            for (int k = P - 2; k >= 0; k--) h = cfma(h, z, B[k]);
+            far[i] = h.re;
+        }
     }
 }
 
@@ -505,13 +633,6 @@ __global__ void k_l2p(int L, int P, int PS, int64_t n, const int32_t* __restrict
 // coordinates; every other term then has |error| < 2^-17 in log2 units.  binary64 path: absolute
 // coordinates, binary64 log.  Flushes add binary64 partial sums to the accumulator atomically.
 
-__device__ __forceinline__ void two_sum(float& hi, float& lo, float v)
-{
-    const float s = hi + v;
-    const float bb = s - hi;
-    lo += (hi - (s - bb)) + (v - bb);
-    hi = s;
-}
 
 // Leaves of at most 32 points: groups of gs = pow2ceil(max leaf size) lanes, one lane per target;
 // the G = 32/gs groups of a warp walk the warp's P2P_CH consecutive pairs round robin, each group
@@ -519,9 +640,10 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float v)
 // Accumulators: binary64 path acc64 (holds the far field already); binary32 path nhi/nlo, the
 // float-float near-field sums in log2 units (flushed with binary32 atomics).
 template <typename T>
-__global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t* __restrict__ soff,
+__global__ void __launch_bounds__(256) k_p2p_small(const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+                                                   int gs, const int32_t* __restrict__ soff,
                                                    const int32_t* __restrict__ sidx,
-                                                   const int32_t* __restrict__ stgt, int64_t scap,
+                                                   const int32_t* __restrict__ stgt,
                                                    const int32_t* __restrict__ lb,
                                                    const Pk<T>* __restrict__ pk,
                                                    const double* __restrict__ xs,
@@ -533,6 +655,24 @@ __global__ void __launch_bounds__(256) k_p2p_small(int L, int gs, const int32_t*
                                                    float* __restrict__ nlo)
 {
     constexpr bool F32 = sizeof(T) == 4;
+    const Inst S = I[blockIdx.y];
+    const LInst TL = LIs[blockIdx.y];
+    const int L = S.L;
+    if ((S.n + level_size(L) - 1) / level_size(L) > gs) return;  // left to k_p2p_large
+    const int64_t scap = TL.scap;
+    soff += S.o0;
+    sidx += TL.s0;
+    stgt += TL.s0;
+    lb += S.lb0;
+    pk += S.p0;
+    xs += S.p0;
+    ys += S.p0;
+    chi += 2 * S.b0;
+    clo += 2 * S.b0;
+    rad32 += S.b0;
+    acc64 += S.p0;
+    nhi += S.p0;
+    nlo += S.p0;
     const int lane = threadIdx.x & 31, G = 32 / gs, grp = lane / gs, ti = lane & (gs - 1);
     const int64_t base = level_base(L);
     const int64_t e_begin = min((int64_t)soff[base], scap);
@@ -652,9 +792,10 @@ __device__ __forceinline__ float p2p_exact(float xt, float yt, int32_t it, const
 // once and every source load serves two pair evaluations.  The main loop has no branch: it keeps
 // the smallest r^2 it met and, for the rare lane whose minimum falls below the exactness threshold
 // (and for the leaf's pair with itself), the leaf pair is redone by the exact path.
-__global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* __restrict__ soff,
+__global__ void __launch_bounds__(256) k_p2p_f32(const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+                                                 const int32_t* __restrict__ soff,
                                                  const int32_t* __restrict__ sidx,
-                                                 const int32_t* __restrict__ stgt, int64_t scap,
+                                                 const int32_t* __restrict__ stgt,
                                                  const int32_t* __restrict__ lb,
                                                  const Pk<float>* __restrict__ pk,
                                                  const double* __restrict__ xs,
@@ -664,6 +805,27 @@ __global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* 
                                                  const float* __restrict__ rad32,
                                                  float* __restrict__ nhi, float* __restrict__ nlo)
 {
+    const Inst S = I[blockIdx.y];
+    const LInst TL = LIs[blockIdx.y];
+    const int L = S.L;
+    const int64_t scap = TL.scap;
+    soff += S.o0;
+    sidx += TL.s0;
+    stgt += TL.s0;
+    lb += S.lb0;
+    pk += S.p0;
+    xs += S.p0;
+    ys += S.p0;
+    chi += 2 * S.b0;
+    clo += 2 * S.b0;
+    rad32 += S.b0;
+    nhi += S.p0;
+    nlo += S.p0;
+    // groups of gsl lanes, two targets per lane: gsl = pow2ceil(largest leaf of this instance) / 2
+    const int64_t maxleaf = (S.n + level_size(L) - 1) / level_size(L);
+    if (maxleaf > 64) return;  // left to k_p2p_large
+    int gsl = 1;
+    while (2 * gsl < maxleaf) gsl <<= 1;
     const int lane = threadIdx.x & 31, G = 32 / gsl, grp = lane / gsl, li = lane - grp * gsl;
     const int32_t base = (int32_t)level_base(L);
     const int64_t e_begin = min((int64_t)soff[base], scap);
@@ -674,7 +836,7 @@ __global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* 
         const int64_t e1 = min(e0 + P2P_CH, e_end);
         int32_t cur = -1, it0 = 0, it1 = 0;
         bool v0 = false, v1 = false;
-        float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f;
+        float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, tq0 = 0.f, tq1 = 0.f;
         float hi0 = 0.f, lo0 = 0.f, hi1 = 0.f, lo1 = 0.f;
         for (int64_t e = e0 + grp; e < e1; e += G) {
             const int32_t tl = stgt[e] - base;
@@ -688,8 +850,8 @@ __global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* 
                 v0 = li < nt;
                 v1 = li + gsl < nt;
                 hi0 = lo0 = hi1 = lo1 = 0.f;
-                if (v0) { const Pk<float> p = pk[it0]; tx0 = p.x; ty0 = p.y; }
-                if (v1) { const Pk<float> p = pk[it1]; tx1 = p.x; ty1 = p.y; }
+                if (v0) { const Pk<float> p = pk[it0]; tx0 = p.x; ty0 = p.y; tq0 = p.q; }
+                if (v1) { const Pk<float> p = pk[it1]; tx1 = p.x; ty1 = p.y; tq1 = p.q; }
             }
             if (!v0) continue;  // v1 implies v0
             const int32_t sl = sidx[e];
@@ -699,8 +861,15 @@ __global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* 
             const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
             const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
             const float tau2 = fmaxf((M * (1.f / 64.f)) * (M * (1.f / 64.f)), 1e-30f);
+            // logs are taken of r^2 / M^2, near 1 for most pairs, and log2(M^2) times the sources'
+            // strength is added once per leaf pair: the running sums stay small, and so do their
+            // rounding errors
+            const float M2 = M * M;
+            const bool scaled = M2 > 1e-30f && M2 < 1e30f;
+            const float s2 = scaled ? 1.f / M2 : 1.f;
+            const float c2 = scaled ? lg2_fast(M2) : 0.f;
             const float xa = tx0 - ox, ya = ty0 - oy, xb = tx1 - ox, yb = ty1 - oy;
-            float pa = 0.f, pb = 0.f, ma = 3.0e38f, mb = 3.0e38f;
+            float pa = 0.f, pb = 0.f, ma = 3.0e38f, mb = 3.0e38f, qs = 0.f;
             const Pk<float>* src = pk + s0;
             if (sl != tl) {
 #pragma unroll 4
@@ -711,11 +880,14 @@ __global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* 
                     const float ra = dxa * dxa + dya * dya, rb = dxb * dxb + dyb * dyb;
                     ma = fminf(ma, ra);
                     mb = fminf(mb, rb);
-                    pa += sp.q * lg2_fast(ra);
-                    pb += sp.q * lg2_fast(rb);
+                    qs += sp.q;
+                    pa += sp.q * lg2_fast(ra * s2);
+                    pb += sp.q * lg2_fast(rb * s2);
                 }
+                pa += c2 * qs;
+                pb += c2 * qs;
             } else {
-                // the leaf with itself: a point meets itself once; give that term r^2 = 1 (log 0)
+                // the leaf with itself: a point meets itself once; that term is left out
                 const int32_t ia = it0 - s0, ib = it1 - s0;
 #pragma unroll 4
                 for (int32_t j = 0; j < ns; j++) {
@@ -727,9 +899,12 @@ __global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* 
                     rb = j == ib ? 3.0e38f : rb;
                     ma = fminf(ma, ra);
                     mb = fminf(mb, rb);
-                    pa += j == ia ? 0.f : sp.q * lg2_fast(ra);
-                    pb += j == ib ? 0.f : sp.q * lg2_fast(rb);
+                    qs += sp.q;
+                    pa += j == ia ? 0.f : sp.q * lg2_fast(ra * s2);
+                    pb += j == ib ? 0.f : sp.q * lg2_fast(rb * s2);
                 }
+                pa += c2 * (qs - tq0);
+                pb += c2 * (qs - tq1);
             }
             if (ma < tau2) pa = p2p_exact(xa, ya, it0, pk, s0, ns, tau2, xs, ys);
             if (v1 && mb < tau2) pb = p2p_exact(xb, yb, it1, pk, s0, ns, tau2, xs, ys);
@@ -744,9 +919,10 @@ __global__ void __launch_bounds__(256) k_p2p_f32(int L, int gsl, const int32_t* 
 // Leaves of more than 32 points: one lane per target, 32 targets at a time, every source of the
 // pair; one flush per (pair, block of 32 targets).
 template <typename T>
-__global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restrict__ soff,
+__global__ void __launch_bounds__(256) k_p2p_large(const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+                                                   int small_leaf, const int32_t* __restrict__ soff,
                                                    const int32_t* __restrict__ sidx,
-                                                   const int32_t* __restrict__ stgt, int64_t scap,
+                                                   const int32_t* __restrict__ stgt,
                                                    const int32_t* __restrict__ lb,
                                                    const Pk<T>* __restrict__ pk,
                                                    const double* __restrict__ xs,
@@ -758,6 +934,24 @@ __global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restr
                                                    float* __restrict__ nlo)
 {
     constexpr bool F32 = sizeof(T) == 4;
+    const Inst S = I[blockIdx.y];
+    const LInst TL = LIs[blockIdx.y];
+    const int L = S.L;
+    if ((S.n + level_size(L) - 1) / level_size(L) <= small_leaf) return;  // done by the leaf-pair kernel
+    const int64_t scap = TL.scap;
+    soff += S.o0;
+    sidx += TL.s0;
+    stgt += TL.s0;
+    lb += S.lb0;
+    pk += S.p0;
+    xs += S.p0;
+    ys += S.p0;
+    chi += 2 * S.b0;
+    clo += 2 * S.b0;
+    rad32 += S.b0;
+    acc64 += S.p0;
+    nhi += S.p0;
+    nlo += S.p0;
     const int lane = threadIdx.x & 31;
     const int64_t base = level_base(L);
     const int64_t e_begin = min((int64_t)soff[base], scap);
@@ -815,9 +1009,14 @@ __global__ void __launch_bounds__(256) k_p2p_large(int L, const int32_t* __restr
     }
 }
 
-__global__ void k_unpermute(const int32_t* __restrict__ perm, const double* __restrict__ acc, int64_t n,
-                            double* __restrict__ phi)
+__global__ void k_unpermute(const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+                            const double* __restrict__ acc, double* __restrict__ phi)
 {
+    const Inst S = I[blockIdx.y];
+    perm += S.p0;
+    acc += S.p0;
+    phi += S.p0;
+    const int64_t n = S.n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         phi[perm[i]] = acc[i];
@@ -825,14 +1024,24 @@ __global__ void k_unpermute(const int32_t* __restrict__ perm, const double* __re
 
 // binary32 path: phi = far + (ln 2 / 2) * near, combined in binary32 (the mixed path targets
 // tolerances >= 1e-7), written in input order.
-__global__ void k_combine32(const int32_t* __restrict__ perm, const float* __restrict__ far,
-                            const float* __restrict__ nhi, const float* __restrict__ nlo, int64_t n,
+__global__ void k_combine32(const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+                            const float* __restrict__ far, const float* __restrict__ farlo,
+                            const float* __restrict__ nhi, const float* __restrict__ nlo,
                             double* __restrict__ phi)
 {
-    const float scale = 0.34657359027997264f;  // ln(2) / 2
+    const Inst S = I[blockIdx.y];
+    perm += S.p0;
+    far += S.p0;
+    farlo += S.p0;
+    nhi += S.p0;
+    nlo += S.p0;
+    phi += S.p0;
+    const int64_t n = S.n;
+    const double scale = 0.34657359027997264;  // ln(2) / 2: near-field sums are of log2(r^2)
+    // the two float-float sums are joined in binary64 (four additions per point)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        phi[perm[i]] = (double)(far[i] + scale * (nhi[i] + nlo[i]));
+        phi[perm[i]] = ((double)far[i] + (double)farlo[i]) + scale * ((double)nhi[i] + (double)nlo[i]);
 }
 
 // ---- direct sum at sampled targets (binary64), one block per target ----
@@ -901,8 +1110,10 @@ int alloc_ws(fmm_tree t, int PS, bool f64)
 {
     if (f64 && !t->acc && cudaMalloc((void**)&t->acc, 8 * (size_t)t->n) != cudaSuccess)
         return fail(FMM_ERR_OOM, "accumulator");
-    if (!f64 && !t->acc32 && cudaMalloc((void**)&t->acc32, 3 * 4 * (size_t)t->n) != cudaSuccess)
+    if (!f64 && !t->acc32 && cudaMalloc((void**)&t->acc32, 4 * 4 * (size_t)t->n) != cudaSuccess)
         return fail(FMM_ERR_OOM, "accumulator");
+    if (!f64 && !t->Lf0lo && cudaMalloc((void**)&t->Lf0lo, 4 * (size_t)t->nbox) != cudaSuccess)
+        return fail(FMM_ERR_OOM, "local expansion low parts");
     void** pk = f64 ? &t->pk64 : &t->pk32;
     if (!*pk && cudaMalloc(pk, (f64 ? 32 : 16) * (size_t)t->n) != cudaSuccess)
         return fail(FMM_ERR_OOM, "packed points");
@@ -922,18 +1133,21 @@ int alloc_ws(fmm_tree t, int PS, bool f64)
     return 0;
 }
 
-int grid_for(int64_t n, int threads)
+// Blocks per instance of a launch over all instances: the single-instance count, shared out over
+// the instances (a tuned value from fmm_autotune replaces the default when set).
+int per_inst_blocks(int total, int n_inst, int tuned)
 {
-    int64_t g = (n + threads - 1) / threads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+    if (tuned > 0) return tuned;
+    return std::max(1, total / std::max(1, n_inst));
 }
 
 template <int PI>
 int launch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<float> geo, const cx<float>* Me,
                cx<float>* Le, cudaStream_t s)
 {
-    k_m2l_pairs<float, PI><<<152 * 16, 128, 0, s>>>(P, PS, li->woff, li->widx, li->wtgt, li->wcap,
-                                                     t->nbox, geo, Me, Le); note_launch();
+    const dim3 grid(per_inst_blocks(152 * 16, t->n_inst, t->tune_m2l_blocks), t->n_inst);
+    k_m2l_pairs<float, PI><<<grid, 128, 0, s>>>(t->dinst, li->dlinst, P, PS, li->woff, li->widx,
+                                                li->wtgt, geo, Me, Le, t->Lf0lo); note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L");
     return 0;
 }
@@ -958,8 +1172,9 @@ int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<double> geo, const
     const int NT = 64;
     const size_t sm = (size_t)2 * P * NT * sizeof(cx<double>);
     FMM_CUDA(cudaFuncSetAttribute(k_m2l_pairs_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_m2l_pairs_f64<<<152 * 16, NT, sm, s>>>(P, PS, li->woff, li->widx, li->wtgt, li->wcap, t->nbox,
-                                              geo, Me, Le); note_launch();
+    const dim3 grid(per_inst_blocks(152 * 16, t->n_inst, t->tune_m2l_blocks), t->n_inst);
+    k_m2l_pairs_f64<<<grid, NT, sm, s>>>(t->dinst, li->dlinst, P, PS, li->woff, li->widx, li->wtgt,
+                                         geo, Me, Le); note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L");
     return 0;
 }
@@ -974,40 +1189,54 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     cx<T>* Me = (cx<T>*)(f64 ? t->Me : t->Mf);
     cx<T>* Le = (cx<T>*)(f64 ? t->Le : t->Lf);
     Pk<T>* pk = (Pk<T>*)(f64 ? t->pk64 : t->pk32);
-    const int L = t->L;
+    const Inst* I = t->dinst;
+    const LInst* LI = li->dlinst;
+    const unsigned ni = (unsigned)t->n_inst;
+    const int Lmax = t->Lmax;
     const int64_t n = t->n;
+    // largest leaf of each instance (leaves are balanced); its largest and smallest value
+    int64_t maxleaf = 0, minleaf = INT64_MAX;
+    for (int i = 0; i < t->n_inst; i++) {
+        const Inst& S = t->hinst[i];
+        const int64_t ml = (S.n + level_size(S.L) - 1) / level_size(S.L);
+        maxleaf = std::max(maxleaf, ml);
+        minleaf = std::min(minleaf, ml);
+    }
     const int WPB = 4;
     const size_t bsm = ((P * P * sizeof(T) + 15) & ~15);
     Geo<T> geo;
     if constexpr (sizeof(T) == 8) geo = Geo<T>{t->centers, t->radii};
     else geo = Geo<T>{t->cen_hi, t->cen_lo, t->rad32};
-    float* far32 = t->acc32;
-    float* nhi = t->acc32 + n;
-    float* nlo = t->acc32 + 2 * n;
+    float* far32 = t->acc32;        // binary32 path: far field hi, lo; near field hi, lo
+    float* farlo = t->acc32 + n;
+    float* nhi = t->acc32 + 2 * n;
+    float* nlo = t->acc32 + 3 * n;
+    const dim3 gpts(blocks_for(t->max_n, 256, t->n_inst), ni);
 
     {
         StageScope scope(FMM_STAGE_GATHER, s);
-        k_pack<T><<<grid_for(n, 256), 256, 0, s>>>(t->perm, q, t->xs, t->ys, t->dxf, t->dyf, n, pk,
-                                                   t->status); note_launch();
+        k_pack<T><<<gpts, 256, 0, s>>>(I, t->perm, q, t->xs, t->ys, t->dxf, t->dyf, pk, t->status);
+        note_launch();
         FMM_CUDA(cudaMemsetAsync(Le, 0, (size_t)t->nbox * PS * sizeof(cx<T>), s));
+        if (!f64) FMM_CUDA(cudaMemsetAsync(t->Lf0lo, 0, 4 * (size_t)t->nbox, s));
         FMM_LAUNCH_CHECK("evaluate: gather");
     }
-    if (L >= 1) {
+    if (Lmax >= 1) {
         {
             StageScope scope(FMM_STAGE_P2M, s);
-            const int64_t nleaf = level_size(L);
+            const int64_t nleaf = level_size(Lmax);
             const size_t sm = (size_t)WPB * 33 * P * sizeof(cx<T>);
             FMM_CUDA(cudaFuncSetAttribute(k_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_p2m<T><<<(unsigned)((nleaf + WPB - 1) / WPB), 32 * WPB, sm, s>>>(
-                L, P, PS, t->leaf_begin, pk, geo, Me); note_launch();
+            k_p2m<T><<<dim3((unsigned)((nleaf + WPB - 1) / WPB), ni), 32 * WPB, sm, s>>>(
+                I, P, PS, t->leaf_begin, pk, geo, Me); note_launch();
             FMM_LAUNCH_CHECK("evaluate: P2M");
         }
         {
             StageScope scope(FMM_STAGE_M2M, s);
-            for (int l = L - 1; l >= 1; l--) {
+            for (int l = Lmax - 1; l >= 1; l--) {
                 const int64_t nb = level_size(l);
-                k_m2m<T><<<(unsigned)((nb + WPB - 1) / WPB), 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
-                    l, P, PS, geo, Me); note_launch();
+                k_m2m<T><<<dim3((unsigned)((nb + WPB - 1) / WPB), ni), 32 * WPB,
+                           bsm + WPB * P * sizeof(cx<T>), s>>>(I, l, P, PS, geo, Me); note_launch();
             }
             FMM_LAUNCH_CHECK("evaluate: M2M");
         }
@@ -1018,10 +1247,10 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         }
         {
             StageScope scope(FMM_STAGE_L2L, s);
-            for (int l = 1; l < L; l++) {
+            for (int l = 1; l < Lmax; l++) {
                 const int64_t nc = level_size(l + 1);
-                k_l2l<T><<<(unsigned)((nc + WPB - 1) / WPB), 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
-                    l, P, PS, geo, Le); note_launch();
+                k_l2l<T><<<dim3((unsigned)((nc + WPB - 1) / WPB), ni), 32 * WPB,
+                           bsm + WPB * P * sizeof(cx<T>), s>>>(I, l, P, PS, geo, Le, t->Lf0lo); note_launch();
             }
             FMM_LAUNCH_CHECK("evaluate: L2L");
         }
@@ -1029,30 +1258,35 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     {
         StageScope scope(FMM_STAGE_LEAF, s);
         if (!f64) FMM_CUDA(cudaMemsetAsync(nhi, 0, 2 * 4 * (size_t)n, s));
-        k_l2p<T><<<grid_for(n, 256), 256, 0, s>>>(L, P, PS, n, t->cleaf, pk, geo, Le,
-                                                  f64 ? (T*)t->acc : (T*)far32); note_launch();
-        const int64_t maxleaf = (n + level_size(L) - 1) / level_size(L);
-        if (maxleaf <= 32) {
-            int gs = 1;
-            while (gs < maxleaf) gs <<= 1;
+        k_l2p<T><<<gpts, 256, 0, s>>>(I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo, f64 ? (T*)t->acc : (T*)far32,
+                                      farlo);
+        note_launch();
+        const dim3 gp2p(per_inst_blocks(152 * 8, t->n_inst, t->tune_p2p_blocks), ni);
+        // instances whose leaves hold at most SMALL_LEAF points take the leaf-pair kernel, the
+        // others (if any) the general one; each kernel skips the instances of the other
+        const int small_leaf = f64 ? 32 : 64;
+        if (minleaf <= small_leaf) {
             if constexpr (sizeof(T) == 4) {
-                k_p2p_f32<<<152 * 8, 256, 0, s>>>(L, gs > 1 ? gs / 2 : 1, li->soff, li->sidx, li->stgt,
-                                                  li->scap, t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
-                                                  t->cen_lo, t->rad32, nhi, nlo); note_launch();
+                k_p2p_f32<<<gp2p, 256, 0, s>>>(I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk,
+                                               t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
             } else {
-                k_p2p_small<T><<<152 * 8, 256, 0, s>>>(L, gs, li->soff, li->sidx, li->stgt, li->scap,
-                                                       t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
-                                                       t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
+                int gs = 1;
+                while (gs < std::min<int64_t>(maxleaf, 32)) gs <<= 1;
+                k_p2p_small<T><<<gp2p, 256, 0, s>>>(I, LI, gs, li->soff, li->sidx, li->stgt,
+                                                    t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
+                                                    t->cen_lo, t->rad32, t->acc, nhi, nlo);
             }
-        } else {
-            k_p2p_large<T><<<152 * 8, 256, 0, s>>>(L, li->soff, li->sidx, li->stgt, li->scap,
-                                                   t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
-                                                   t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
+            note_launch();
+        }
+        if (maxleaf > small_leaf) {
+            k_p2p_large<T><<<gp2p, 256, 0, s>>>(I, LI, small_leaf, li->soff, li->sidx, li->stgt,
+                                                t->leaf_begin, pk, t->xs, t->ys, t->cen_hi, t->cen_lo,
+                                                t->rad32, t->acc, nhi, nlo); note_launch();
         }
         if (f64)
-            k_unpermute<<<grid_for(n, 256), 256, 0, s>>>(t->perm, t->acc, n, phi);
+            k_unpermute<<<gpts, 256, 0, s>>>(I, t->perm, t->acc, phi);
         else
-            k_combine32<<<grid_for(n, 256), 256, 0, s>>>(t->perm, far32, nhi, nlo, n, phi);
+            k_combine32<<<gpts, 256, 0, s>>>(I, t->perm, far32, farlo, nhi, nlo, phi);
         note_launch();
         FMM_LAUNCH_CHECK("evaluate: leaf evaluation");
     }
@@ -1067,8 +1301,71 @@ int evaluate(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     int rc = ensure_tables();
     if (rc) return rc;
     const int P = prm.p + 1;
-    if (prm.mode == FMM_MODE_FP64) return run<double>(t, li, q, P, phi, s);
+    // binary32 expansions carry a rounding error of about 1e-7 relative to the potential: a
+    // tighter requested tolerance takes the binary64 path
+    const bool f64 = prm.mode == FMM_MODE_FP64 || (prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR);
+    if (f64) return run<double>(t, li, q, P, phi, s);
     return run<float>(t, li, q, P, phi, s);
+}
+
+// Launch-shape tuner: times complete evaluations (CUDA events on the caller's stream, best of
+// three after one warm-up) for a ladder of grid sizes of the two dominant kernels, the M2L pair
+// kernel first and then the near-field kernel, and keeps the fastest of each.
+int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, double* phi,
+             cudaStream_t s, int* m2l_blocks, int* p2p_blocks)
+{
+    cudaEvent_t e0, e1;
+    FMM_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(FMM_ERR_CUDA, "cudaEventCreate");
+    }
+    auto time_one = [&](float& best) -> int {
+        best = 1e30f;
+        for (int r = 0; r < 4; r++) {
+            FMM_CUDA(cudaEventRecord(e0, s));
+            int rc = evaluate(t, li, q, prm, phi, s);
+            if (rc) return rc;
+            FMM_CUDA(cudaEventRecord(e1, s));
+            FMM_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FMM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) best = std::min(best, ms);
+        }
+        return 0;
+    };
+    const int ni = t->n_inst;
+    const int ladder[] = {152, 152 * 2, 152 * 4, 152 * 8, 152 * 16, 152 * 32, 152 * 64};
+    int rc = 0;
+    t->tune_m2l_blocks = t->tune_p2p_blocks = 0;
+    for (int stage = 0; stage < 2 && !rc; stage++) {
+        int& knob = stage == 0 ? t->tune_m2l_blocks : t->tune_p2p_blocks;
+        int best_v = 0, last = -1;
+        float best_ms = 1e30f;
+        for (int total : ladder) {
+            const int v = std::max(1, total / ni);
+            if (v == last) continue;
+            last = v;
+            knob = v;
+            float ms = 0.f;
+            rc = time_one(ms);
+            if (rc) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_v = v;
+            }
+        }
+        knob = best_v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        t->tune_m2l_blocks = t->tune_p2p_blocks = 0;
+        return rc;
+    }
+    if (m2l_blocks) *m2l_blocks = t->tune_m2l_blocks;
+    if (p2p_blocks) *p2p_blocks = t->tune_p2p_blocks;
+    return 0;
 }
 
 int direct(const double* x, const double* y, const double* q, int64_t n, const int64_t* tgt,

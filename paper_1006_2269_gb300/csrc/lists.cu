@@ -4,13 +4,17 @@
 // Level by level, every candidate pair (box b, child c of a box of S(parent(b))) is one thread.
 // Candidates are enumerated parent by parent, box by box (b = 4 parent + k), then in the order
 // of the parent's strong list and the child index, so each box owns a contiguous, ascending run
-// of candidates.  One global scan of the weak flags then gives every entry its CSR position and
-// every box its offsets, whatever the spread of list lengths (balanced trees of clustered points
-// have lists from a handful to thousands of entries).  The number of candidates of a level lives
-// in device memory, so the kernels use grid-stride loops over a fixed grid and the whole build is
+// of candidates.  One scan of the weak flags then gives every entry its CSR position and every
+// box its offsets, whatever the spread of list lengths (balanced trees of clustered points have
+// lists from a handful to thousands of entries).  The number of candidates of a level lives in
+// device memory, so the kernels use grid-stride loops over a fixed grid and the whole build is
 // asynchronous.  Entries beyond the preallocated capacity are dropped and flagged in the status
 // word; later levels never read past the capacity.
+//
+// All instances of a forest are processed by the same launches (instance = blockIdx.y); each
+// instance has its own CSR arrays, capacities and scratch, found through the instance tables.
 #include <algorithm>
+#include <new>
 
 #include "common.cuh"
 
@@ -20,7 +24,6 @@ namespace {
 constexpr int LT = 256;          // threads per block
 constexpr int LI = 8;            // candidates per thread per tile
 constexpr int LTILE = LT * LI;   // candidates per tile
-constexpr int LGRID = 152 * 8;   // blocks of the grid-stride kernels
 
 __device__ __forceinline__ unsigned lanemask_lt()
 {
@@ -63,15 +66,48 @@ __device__ __forceinline__ bool theta_weak_fast(int64_t a, int64_t b, const floa
     return theta_weak(cen[2 * a], cen[2 * a + 1], rad[a], cen[2 * b], cen[2 * b + 1], rad[b], theta);
 }
 
-__global__ void k_lists_root(int32_t* woff, int32_t* soff, int32_t* sidx, int32_t* stgt)
+// One instance's view of the list arrays (pointers already offset to the instance).
+struct LView {
+    int32_t *woff, *soff, *widx, *wtgt, *sidx, *stgt;
+    uint8_t* flags;
+    uint32_t* tilecnt;
+    int64_t wcap, scap;
+};
+
+__device__ __forceinline__ LView lview(const Inst& S, const LInst& T, int32_t* woff, int32_t* soff,
+                                       int32_t* widx, int32_t* wtgt, int32_t* sidx, int32_t* stgt,
+                                       uint8_t* flags, uint32_t* tilecnt)
 {
-    if (threadIdx.x == 0) {
-        woff[0] = 0;
-        woff[1] = 0;
-        soff[0] = 0;
-        soff[1] = 1;
-        sidx[0] = 0;
-        stgt[0] = 0;
+    LView v;
+    v.woff = woff + S.o0;
+    v.soff = soff + S.o0;
+    v.widx = widx + T.w0;
+    v.wtgt = wtgt + T.w0;
+    v.sidx = sidx + T.s0;
+    v.stgt = stgt + T.s0;
+    v.flags = flags + T.f0;
+    v.tilecnt = tilecnt + T.c0;
+    v.wcap = T.wcap;
+    v.scap = T.scap;
+    return v;
+}
+
+#define LIST_ARGS                                                                                 \
+    const Inst *__restrict__ I, const LInst *__restrict__ LIs, int32_t *woff, int32_t *soff,     \
+        int32_t *widx, int32_t *wtgt, int32_t *sidx, int32_t *stgt, uint8_t *flags,               \
+        uint32_t *tilecnt
+#define LIST_VIEW() lview(I[blockIdx.y], LIs[blockIdx.y], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt)
+
+__global__ void k_lists_root(LIST_ARGS, int n_inst)
+{
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        const LView v = lview(I[i], LIs[i], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt);
+        v.woff[0] = 0;
+        v.woff[1] = 0;
+        v.soff[0] = 0;
+        v.soff[1] = 1;
+        v.sidx[0] = 0;
+        v.stgt[0] = 0;
     }
 }
 
@@ -152,34 +188,39 @@ __device__ __forceinline__ void decode(const TileParents& tp, const int32_t* __r
     first = (r == 0);
 }
 
-__global__ void __launch_bounds__(LT) k_lists_flags(int l, const double* __restrict__ cen,
+// grid (blocks, instances)
+__global__ void __launch_bounds__(LT) k_lists_flags(LIST_ARGS, int l, const double* __restrict__ cen,
                                                     const double* __restrict__ rad,
                                                     const float* __restrict__ chi,
                                                     const float* __restrict__ clo,
-                                                    const float* __restrict__ rad32, double theta,
-                                                    const int32_t* __restrict__ soff,
-                                                    const int32_t* __restrict__ sidx, int64_t scap,
-                                                    uint8_t* __restrict__ flags,
-                                                    uint32_t* __restrict__ tilecnt)
+                                                    const float* __restrict__ rad32, double theta)
 {
+    const Inst S = I[blockIdx.y];
+    if (l > S.L) return;
+    const LView v = LIST_VIEW();
+    cen += 2 * S.b0;
+    rad += S.b0;
+    chi += 2 * S.b0;
+    clo += 2 * S.b0;
+    rad32 += S.b0;
     __shared__ uint32_t wsum[LT / 32];
     __shared__ TileParents tp;
-    const LevelCands lc = level_cands(soff, l, scap);
+    const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
     const int64_t base = level_base(l);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        stage_parents(tp, soff, l, scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
+        stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint32_t cnt = 0;
         for (int j = 0; j < LI; j++) {
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             if (t < nc) {
                 int64_t b, c;
                 bool first;
-                decode(tp, sidx, lc, t, b, c, first);
+                decode(tp, v.sidx, lc, t, b, c, first);
                 const bool w = theta_weak_fast(base + b, base + c, chi, clo, rad32, cen, rad,
                                                (float)theta, theta);
-                flags[t] = w ? 1 : 0;
+                v.flags[t] = w ? 1 : 0;
                 cnt += w;
             }
         }
@@ -190,25 +231,28 @@ __global__ void __launch_bounds__(LT) k_lists_flags(int l, const double* __restr
         if (threadIdx.x == 0) {
             uint32_t s = 0;
             for (int w = 0; w < LT / 32; w++) s += wsum[w];
-            tilecnt[tile] = s;
+            v.tilecnt[tile] = s;
         }
         __syncthreads();
     }
 }
 
 // Exclusive scan of the weak counts per tile; writes the level totals into the offsets.
-__global__ void __launch_bounds__(1024) k_lists_scan(int l, int64_t scap, uint32_t* tilecnt,
-                                                     int32_t* woff, int32_t* soff)
+// grid (1, instances)
+__global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, int l)
 {
+    const Inst S = I[blockIdx.y];
+    if (l > S.L) return;
+    const LView v = LIST_VIEW();
     __shared__ int64_t wt[32];
-    const LevelCands lc = level_cands(soff, l, scap);
+    const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int64_t carry = 0;
     for (int64_t b0 = 0; b0 < ntiles; b0 += blockDim.x) {
         const int64_t i = b0 + threadIdx.x;
-        int64_t v = i < ntiles ? tilecnt[i] : 0, x = v;
+        int64_t val = i < ntiles ? v.tilecnt[i] : 0, x = val;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int64_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -227,50 +271,50 @@ __global__ void __launch_bounds__(1024) k_lists_scan(int l, int64_t scap, uint32
         }
         __syncthreads();
         const int64_t before = w ? wt[w - 1] : 0, tot = wt[nw - 1];
-        if (i < ntiles) tilecnt[i] = (uint32_t)(carry + before + x - v);
+        if (i < ntiles) v.tilecnt[i] = (uint32_t)(carry + before + x - val);
         carry += tot;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         const int64_t base = level_base(l), nb = level_size(l);
-        const int64_t W0 = woff[base], S0 = soff[base];
-        woff[base + nb] = (int32_t)min(W0 + carry, (int64_t)INT32_MAX);
-        soff[base + nb] = (int32_t)min(S0 + (nc - carry), (int64_t)INT32_MAX);
+        const int64_t W0 = v.woff[base], S0 = v.soff[base];
+        v.woff[base + nb] = (int32_t)min(W0 + carry, (int64_t)INT32_MAX);
+        v.soff[base + nb] = (int32_t)min(S0 + (nc - carry), (int64_t)INT32_MAX);
     }
 }
 
 // Scatter the candidates into the weak and strong lists and write the box offsets.  The tile
 // prefix of weak flags is tilecnt[tile]; the strong prefix is its complement.
-__global__ void __launch_bounds__(LT) k_lists_fill(int l, const uint8_t* __restrict__ flags,
-                                                   const uint32_t* __restrict__ tilecnt, int64_t scap,
-                                                   int64_t wcap, int32_t* woff, int32_t* widx,
-                                                   int32_t* wtgt, int32_t* soff, int32_t* sidx,
-                                                   int32_t* stgt)
+// grid (blocks, instances)
+__global__ void __launch_bounds__(LT) k_lists_fill(LIST_ARGS, int l)
 {
+    const Inst S = I[blockIdx.y];
+    if (l > S.L) return;
+    const LView v = LIST_VIEW();
     __shared__ uint32_t wsum[LI][LT / 32];
     __shared__ TileParents tp;
-    const LevelCands lc = level_cands(soff, l, scap);
+    const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
     const int64_t base = level_base(l);
-    const int64_t W0 = woff[base], S0 = soff[base];
+    const int64_t W0 = v.woff[base], S0 = v.soff[base];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        stage_parents(tp, soff, l, scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
+        stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint8_t f[LI];
         uint32_t pre[LI];
 #pragma unroll
         for (int j = 0; j < LI; j++) {
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
-            f[j] = t < nc ? flags[t] : 0;
+            f[j] = t < nc ? v.flags[t] : 0;
             const unsigned bal = __ballot_sync(0xffffffffu, f[j]);
             pre[j] = __popc(bal & lt);
             if (lane == 0) wsum[j][w] = __popc(bal);
         }
         __syncthreads();
         // exclusive prefix in (row j, warp) order = candidate order inside the tile
-        uint32_t run = tilecnt[tile];
+        uint32_t run = v.tilecnt[tile];
 #pragma unroll
         for (int j = 0; j < LI; j++) {
             uint32_t before = 0;
@@ -282,24 +326,24 @@ __global__ void __launch_bounds__(LT) k_lists_fill(int l, const uint8_t* __restr
             if (t < nc) {
                 int64_t b, c;
                 bool first;
-                decode(tp, sidx, lc, t, b, c, first);
+                decode(tp, v.sidx, lc, t, b, c, first);
                 const int64_t wpre = (int64_t)before + pre[j];  // weak candidates before t
                 const int64_t spre = t - wpre;                   // strong candidates before t
                 if (first) {
-                    woff[base + b] = (int32_t)min(W0 + wpre, (int64_t)INT32_MAX);
-                    soff[base + b] = (int32_t)min(S0 + spre, (int64_t)INT32_MAX);
+                    v.woff[base + b] = (int32_t)min(W0 + wpre, (int64_t)INT32_MAX);
+                    v.soff[base + b] = (int32_t)min(S0 + spre, (int64_t)INT32_MAX);
                 }
                 if (f[j]) {
                     const int64_t pos = W0 + wpre;
-                    if (pos < wcap) {
-                        widx[pos] = (int32_t)c;
-                        wtgt[pos] = (int32_t)(base + b);
+                    if (pos < v.wcap) {
+                        v.widx[pos] = (int32_t)c;
+                        v.wtgt[pos] = (int32_t)(base + b);
                     }
                 } else {
                     const int64_t pos = S0 + spre;
-                    if (pos < scap) {
-                        sidx[pos] = (int32_t)c;
-                        stgt[pos] = (int32_t)(base + b);
+                    if (pos < v.scap) {
+                        v.sidx[pos] = (int32_t)c;
+                        v.stgt[pos] = (int32_t)(base + b);
                     }
                 }
             }
@@ -308,12 +352,15 @@ __global__ void __launch_bounds__(LT) k_lists_fill(int l, const uint8_t* __restr
     }
 }
 
-__global__ void k_lists_check(const int32_t* woff, const int32_t* soff, int64_t nbox, int64_t wcap,
-                              int64_t scap, int32_t* status)
+__global__ void k_lists_check(LIST_ARGS, int n_inst, int32_t* status)
 {
-    if (threadIdx.x == 0 && ((int64_t)woff[nbox] > wcap || (int64_t)soff[nbox] > scap ||
-                             woff[nbox] == INT32_MAX || soff[nbox] == INT32_MAX))
-        atomicOr(status, ST_CAPACITY);
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        const Inst& S = I[i];
+        const LView v = lview(S, LIs[i], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt);
+        const int32_t W = v.woff[S.nbox], Sx = v.soff[S.nbox];
+        if ((int64_t)W > v.wcap || (int64_t)Sx > v.scap || W == INT32_MAX || Sx == INT32_MAX)
+            atomicOr(status, ST_CAPACITY);
+    }
 }
 
 }  // namespace
@@ -321,21 +368,63 @@ __global__ void k_lists_check(const int32_t* woff, const int32_t* soff, int64_t 
 int64_t lists_flag_bytes(int64_t scap) { return 16 * scap + LTILE; }
 int64_t lists_tile_words(int64_t scap) { return (16 * scap + LTILE - 1) / LTILE + 1; }
 
+// Capacities are split over the instances in proportion to their box counts (at least 16 weak and
+// 8 strong entries per box).
+int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int64_t* strong_capacity)
+{
+    const int ni = t->n_inst;
+    l->hlinst = new (std::nothrow) LInst[ni];
+    if (!l->hlinst) return fail(FMM_ERR_OOM, "host allocation");
+    int64_t w0 = 0, s0 = 0, f0 = 0, c0 = 0;
+    for (int i = 0; i < ni; i++) {
+        LInst& T = l->hlinst[i];
+        T.wcap = weak_capacity[i];
+        T.scap = strong_capacity[i];
+        T.w0 = w0;
+        T.s0 = s0;
+        T.f0 = f0;
+        T.c0 = c0;
+        w0 += T.wcap;
+        s0 += T.scap;
+        f0 += lists_flag_bytes(T.scap);
+        c0 += lists_tile_words(T.scap);
+    }
+    if (w0 >= INT32_MAX || s0 >= INT32_MAX) return fail(FMM_ERR_ARG, "capacity must be below 2^31 - 1");
+    l->wcap = w0;
+    l->scap = s0;
+    const int64_t noff = t->nbox + ni;
+    bool ok = cudaMalloc((void**)&l->dlinst, sizeof(LInst) * ni) == cudaSuccess &&
+              cudaMalloc((void**)&l->woff, 4 * noff) == cudaSuccess &&
+              cudaMalloc((void**)&l->soff, 4 * noff) == cudaSuccess &&
+              cudaMalloc((void**)&l->widx, 4 * std::max<int64_t>(w0, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->wtgt, 4 * std::max<int64_t>(w0, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->sidx, 4 * std::max<int64_t>(s0, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->stgt, 4 * std::max<int64_t>(s0, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->flags, f0) == cudaSuccess &&
+              cudaMalloc((void**)&l->tilecnt, 4 * c0) == cudaSuccess &&
+              cudaMalloc((void**)&l->status, 4) == cudaSuccess;
+    if (!ok) return fail(FMM_ERR_OOM, "list storage");
+    FMM_CUDA(cudaMemcpy(l->dlinst, l->hlinst, sizeof(LInst) * ni, cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemset(l->status, 0, 4));
+    return 0;
+}
+
 int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s)
 {
-    const int L = t->L;
+    const int L = t->Lmax, ni = t->n_inst;
+    const int gx = std::max(1, (152 * 8) / ni);
     StageScope scope(FMM_STAGE_LISTS, s);
-    k_lists_root<<<1, 32, 0, s>>>(li->woff, li->soff, li->sidx, li->stgt); note_launch();
+#define LARGS t->dinst, li->dlinst, li->woff, li->soff, li->widx, li->wtgt, li->sidx, li->stgt, li->flags, li->tilecnt
+    k_lists_root<<<1, 256, 0, s>>>(LARGS, ni); note_launch();
     for (int l = 1; l <= L; l++) {
-        k_lists_flags<<<LGRID, LT, 0, s>>>(l, t->centers, t->radii, t->cen_hi, t->cen_lo, t->rad32,
-                                           theta, li->soff, li->sidx,
-                                           li->scap, li->flags, li->tilecnt); note_launch();
-        k_lists_scan<<<1, 1024, 0, s>>>(l, li->scap, li->tilecnt, li->woff, li->soff); note_launch();
-        k_lists_fill<<<LGRID, LT, 0, s>>>(l, li->flags, li->tilecnt, li->scap, li->wcap, li->woff,
-                                          li->widx, li->wtgt, li->soff, li->sidx, li->stgt); note_launch();
+        k_lists_flags<<<dim3(gx, ni), LT, 0, s>>>(LARGS, l, t->centers, t->radii, t->cen_hi, t->cen_lo,
+                                                  t->rad32, theta); note_launch();
+        k_lists_scan<<<dim3(1, ni), 1024, 0, s>>>(LARGS, l); note_launch();
+        k_lists_fill<<<dim3(gx, ni), LT, 0, s>>>(LARGS, l); note_launch();
         FMM_LAUNCH_CHECK("lists");
     }
-    k_lists_check<<<1, 32, 0, s>>>(li->woff, li->soff, t->nbox, li->wcap, li->scap, li->status); note_launch();
+    k_lists_check<<<1, 256, 0, s>>>(LARGS, ni, li->status); note_launch();
+#undef LARGS
     FMM_LAUNCH_CHECK("lists: check");
     li->theta = theta;
     li->built = true;

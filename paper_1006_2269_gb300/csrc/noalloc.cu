@@ -30,7 +30,7 @@ constexpr int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
 
 // Byte layout of the scratch array (every region 256-byte aligned).
 struct Layout {
-    int64_t keys, vals, rs_counts, rs_totals, tilecnt, hflag, bbox, ones_before, node_off, segs,
+    int64_t inst, keys, vals, rs_counts, rs_totals, tilecnt, hflag, bbox, ones_before, node_off, segs,
         status, centers, radii, rad32, cen_hi, cen_lo, leaf_of, cleaf, xs, ys, dxf, dyf, total;
 };
 
@@ -38,6 +38,7 @@ constexpr Layout make_layout()
 {
     Layout L{};
     int64_t o = 0;
+    L.inst = o;        o += align256(sizeof(Inst));
     L.keys = o;        o += align256(8 * 4 * NA_MAX_N);
     L.vals = o;        o += align256(4 * 4 * NA_MAX_N);
     L.rs_counts = o;   o += align256(4 * 2 * 256 * NA_TILES);
@@ -92,9 +93,11 @@ int scratch_base(unsigned char** out)
 
 // Per-depth "ones before" tables of the stable partitions, node offsets and leaf offsets; the
 // same values the allocating path computes on the host.  One block; depths are independent.
-__global__ void __launch_bounds__(1024) k_noalloc_tables(int64_t n, int L, int32_t* ones_before,
-                                                         int32_t* node_off, int32_t* leaf_begin)
+__global__ void __launch_bounds__(1024) k_noalloc_tables(Inst S, Inst* inst, int64_t n, int L,
+                                                         int32_t* ones_before, int32_t* node_off,
+                                                         int32_t* leaf_begin)
 {
+    if (threadIdx.x == 0) *inst = S;  // the instance table of the build kernels
     for (int d = 0; d <= 2 * L; d++) {
         const int64_t nodes = int64_t(1) << d;
         int32_t* off = node_off + node_offset_base(d);
@@ -173,12 +176,14 @@ extern "C" int fmm_build_tree_noalloc(const double* x, const double* y, int64_t 
     cudaStream_t s = (cudaStream_t)stream;
 
     fmm_tree_s t;  // a handle on the stack whose buffers are regions of the scratch array
-    t.n = n;
-    t.L = levels;
-    t.nbox = level_base(levels + 1);
-    t.nleaf = level_size(levels);
-    t.ntiles = (n + NA_TILE - 1) / NA_TILE;
+    Inst hs;       // its one instance
+    fill_instances(&hs, 1, &n, &levels);
+    t.n_inst = 1;
+    t.hinst = &hs;
+    t.own_hinst = false;
+    forest_totals(&t);
     const Layout& Lo = kLayout;
+    t.dinst = (Inst*)(base + Lo.inst);
     t.keys = (uint64_t*)(base + Lo.keys);
     t.vals = (int32_t*)(base + Lo.vals);
     t.rs_counts = (uint32_t*)(base + Lo.rs_counts);
@@ -208,7 +213,8 @@ extern "C" int fmm_build_tree_noalloc(const double* x, const double* y, int64_t 
     // the array keeps the previous call's contents: the status word must start at zero; every
     // other region is fully written before it is read
     FMM_CUDA(cudaMemsetAsync(t.status, 0, 4, s));
-    k_noalloc_tables<<<1, 1024, 0, s>>>(n, levels, t.ones_before, t.node_off, leaf_begin); note_launch();
+    k_noalloc_tables<<<1, 1024, 0, s>>>(hs, t.dinst, n, levels, t.ones_before, t.node_off, leaf_begin);
+    note_launch();
     FMM_LAUNCH_CHECK("fmm_build_tree_noalloc: tables");
     rc = tree_build(&t, x, y, s);
     if (rc) return rc;

@@ -8,10 +8,15 @@
 //   * a stable partition of its Y segment by that half bit leaves Y segmented by x-halves,
 //     each still in y order, so the y-split of a half is again "the first floor(m/2)";
 //   * a stable partition of each x-half of X by the y bit leaves X segmented by the children.
-// Segment offsets follow from N alone (floor-left binary splits), so every kernel locates its
-// segment by integer arithmetic, and the stable partitions are one global scan of the flag bits
-// plus a per-segment correction taken from a host-computed table.
+// Segment offsets follow from N alone (floor-left binary splits) and are tabulated once, items
+// carry the index of their box, and the stable partitions are one scan of the flag bits per tile
+// plus a per-segment correction from a table.
+//
+// A tree handle may hold many independent instances (a forest); every kernel covers all of them
+// in one launch: the instance is a block index, and the kernel offsets its pointers by the
+// instance's entry of the instance table, so the bodies below index one point set.
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "common.cuh"
@@ -77,23 +82,30 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_t
 
 // ---- keys, bounding box and finiteness -------------------------------------------------------
 
-__global__ void k_bbox_init(uint64_t* bbox)
+__global__ void k_bbox_init(int n_inst, uint64_t* bbox)
 {
-    if (threadIdx.x == 0) {
-        bbox[0] = ~0ull;
-        bbox[1] = 0ull;
-        bbox[2] = ~0ull;
-        bbox[3] = 0ull;
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        bbox[4 * i + 0] = ~0ull;
+        bbox[4 * i + 1] = 0ull;
+        bbox[4 * i + 2] = ~0ull;
+        bbox[4 * i + 3] = 0ull;
     }
 }
 
-__global__ void k_make_keys(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
-                            uint64_t* __restrict__ kx, uint64_t* __restrict__ ky,
+// grid (blocks, instances)
+__global__ void k_make_keys(const Inst* __restrict__ I, const double* __restrict__ x,
+                            const double* __restrict__ y, int64_t ntot, uint64_t* __restrict__ kx,
                             uint64_t* bbox, int32_t* status)
 {
+    const Inst S = I[blockIdx.y];
+    x += S.p0;
+    y += S.p0;
+    uint64_t* ky = kx + 2 * ntot + S.p0;  // the y keys live 2 ntot further
+    kx += S.p0;
+    bbox += 4 * blockIdx.y;
     uint64_t mnx = ~0ull, mxx = 0, mny = ~0ull, mxy = 0;
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double a = x[i], b = y[i];
         bad |= !isfinite(a) || !isfinite(b);
@@ -123,74 +135,83 @@ __global__ void k_make_keys(const double* __restrict__ x, const double* __restri
 
 // The root rectangle is the tight bounding box.  The extreme keys are converted back to the
 // exact coordinates (min/max involve no rounding).
-__global__ void k_root_rect(const uint64_t* bbox, double* rects)
+__global__ void k_root_rect(const Inst* __restrict__ I, int n_inst, const uint64_t* bbox, double* rects)
 {
-    if (threadIdx.x < 4) rects[threadIdx.x] = key_value(bbox[threadIdx.x]);
+    for (int i = threadIdx.x; i < 4 * n_inst; i += blockDim.x)
+        rects[4 * I[i / 4].b0 + (i % 4)] = key_value(bbox[i]);
 }
 
 // ---- stable LSD radix sort (8-bit digits) ----------------------------------------------------
-// blockIdx.y selects one of several independent sorts laid out `stride` elements apart.
+// grid (tiles, sorts, instances).  Sort `srt` of an instance uses keys[srt * stride + p0 ...] and
+// counts [2][256][its tiles] at 2 * 256 * t0.
 
 template <typename K>
-__global__ void __launch_bounds__(TPB) k_rs_hist(const K* __restrict__ keys, int64_t stride, int64_t n,
-                                                 int shift, uint32_t* __restrict__ counts,
-                                                 int64_t ntiles)
+__global__ void __launch_bounds__(TPB) k_rs_hist(const Inst* __restrict__ I, const K* __restrict__ keys,
+                                                 int64_t stride, int shift, uint32_t* __restrict__ counts)
 {
+    const Inst S = I[blockIdx.z];
+    if (blockIdx.x >= S.ntiles) return;
     __shared__ uint32_t h[BINS];
-    keys += (int64_t)blockIdx.y * stride;
-    counts += (int64_t)blockIdx.y * BINS * ntiles;
+    keys += (int64_t)blockIdx.y * stride + S.p0;
+    counts += 2 * BINS * S.t0 + (int64_t)blockIdx.y * BINS * S.ntiles;
     for (int i = threadIdx.x; i < BINS; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * TILE;
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < ITEMS; j++) {
         int64_t i = base + (int64_t)j * TPB + threadIdx.x;
-        bool v = i < n;
+        bool v = i < S.n;
         uint32_t d = v ? (uint32_t)((keys[i] >> shift) & (BINS - 1)) : 0xffffffffu;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         if (v && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < BINS; i += blockDim.x) counts[(int64_t)i * ntiles + blockIdx.x] = h[i];
+    for (int i = threadIdx.x; i < BINS; i += blockDim.x) counts[(int64_t)i * S.ntiles + blockIdx.x] = h[i];
 }
 
-// One block per (digit, sort): exclusive scan of that digit's per-tile counts, in place.
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* counts, int64_t ntiles, uint32_t* totals)
+// grid (digits, sorts, instances): exclusive scan of one digit's per-tile counts, in place.
+__global__ void __launch_bounds__(1024) k_rs_scan(const Inst* __restrict__ I, uint32_t* counts,
+                                                  uint32_t* totals)
 {
+    const Inst S = I[blockIdx.z];
     __shared__ uint32_t wt[32];
-    uint32_t* c = counts + ((int64_t)blockIdx.y * BINS + blockIdx.x) * ntiles;
+    uint32_t* c = counts + 2 * BINS * S.t0 + ((int64_t)blockIdx.y * BINS + blockIdx.x) * S.ntiles;
     uint32_t carry = 0;
-    for (int64_t b = 0; b < ntiles; b += blockDim.x) {
+    for (int64_t b = 0; b < S.ntiles; b += blockDim.x) {
         int64_t i = b + threadIdx.x;
-        uint32_t v = i < ntiles ? c[i] : 0;
+        uint32_t v = i < S.ntiles ? c[i] : 0;
         uint32_t tot;
         uint32_t e = block_excl_scan(v, wt, tot);
-        if (i < ntiles) c[i] = carry + e;
+        if (i < S.ntiles) c[i] = carry + e;
         carry += tot;
     }
-    if (threadIdx.x == 0) totals[blockIdx.y * BINS + blockIdx.x] = carry;
+    if (threadIdx.x == 0) totals[(2 * (int64_t)blockIdx.z + blockIdx.y) * BINS + blockIdx.x] = carry;
 }
 
 // Stable scatter.  Each warp owns WCHUNK consecutive items and walks them in order, ranking
 // equal digits with match_any; warps are then ordered by a per-digit scan, tiles by k_rs_scan,
 // digits by the scan of the totals.  With FIRST the values are the item indices.
 template <typename K, bool FIRST>
-__global__ void __launch_bounds__(TPB) k_rs_scatter(const K* __restrict__ kin, const int32_t* __restrict__ vin,
+__global__ void __launch_bounds__(TPB) k_rs_scatter(const Inst* __restrict__ I, const K* __restrict__ kin,
+                                                    const int32_t* __restrict__ vin,
                                                     K* __restrict__ kout, int32_t* __restrict__ vout,
-                                                    int64_t stride, int64_t n, int shift,
+                                                    int64_t stride, int shift,
                                                     const uint32_t* __restrict__ counts,
-                                                    const uint32_t* __restrict__ totals, int64_t ntiles)
+                                                    const uint32_t* __restrict__ totals)
 {
+    const Inst S = I[blockIdx.z];
+    if (blockIdx.x >= S.ntiles) return;
     __shared__ uint32_t dbase[BINS];
     __shared__ uint32_t wcnt[WARPS][BINS];
     __shared__ uint32_t wt[32];
-    const int64_t so = (int64_t)blockIdx.y * stride;
+    const int64_t so = (int64_t)blockIdx.y * stride + S.p0;
     kin += so;
     kout += so;
     vout += so;
     if (!FIRST) vin += so;
-    counts += (int64_t)blockIdx.y * BINS * ntiles;
-    totals += blockIdx.y * BINS;
+    counts += 2 * BINS * S.t0 + (int64_t)blockIdx.y * BINS * S.ntiles;
+    totals += (2 * (int64_t)blockIdx.z + blockIdx.y) * BINS;
+    const int64_t n = S.n, ntiles = S.ntiles;
     {
         uint32_t tot;
         uint32_t e = block_excl_scan(threadIdx.x < BINS ? totals[threadIdx.x] : 0, wt, tot);
@@ -240,27 +261,28 @@ __global__ void __launch_bounds__(TPB) k_rs_scatter(const K* __restrict__ kin, c
     }
 }
 
-// Sorts `nsorts` independent arrays of n keys laid out `stride` apart; buffer A holds the input
-// keys, buffer B = A + n (same for values).  Returns the index (0 = A, 1 = B) holding the result.
+// Sorts `nsorts` arrays per instance; buffer A holds the input keys, buffer B = A + ntot (same for
+// values).  Returns the index (0 = A, 1 = B) holding the result.
 template <typename K>
-int radix_sort(K* keys, int32_t* vals, int64_t stride, int nsorts, int64_t n, int bits,
-               uint32_t* counts, uint32_t* totals, int64_t ntiles, cudaStream_t s)
+int radix_sort(fmm_tree t, K* keys, int32_t* vals, int64_t stride, int nsorts, int bits,
+               cudaStream_t s)
 {
     int cur = 0;
-    dim3 grid((unsigned)ntiles, (unsigned)nsorts);
+    const int64_t ntot = t->n;
+    dim3 grid((unsigned)t->max_tiles, (unsigned)nsorts, (unsigned)t->n_inst);
     for (int shift = 0; shift < bits; shift += 8) {
-        K* kin = keys + (cur ? n : 0);
-        K* kout = keys + (cur ? 0 : n);
-        int32_t* vin = vals + (cur ? n : 0);
-        int32_t* vout = vals + (cur ? 0 : n);
-        k_rs_hist<K><<<grid, TPB, 0, s>>>(kin, stride, n, shift, counts, ntiles); note_launch();
-        k_rs_scan<<<dim3(BINS, nsorts), 1024, 0, s>>>(counts, ntiles, totals); note_launch();
+        K* kin = keys + (cur ? ntot : 0);
+        K* kout = keys + (cur ? 0 : ntot);
+        int32_t* vin = vals + (cur ? ntot : 0);
+        int32_t* vout = vals + (cur ? 0 : ntot);
+        k_rs_hist<K><<<grid, TPB, 0, s>>>(t->dinst, kin, stride, shift, t->rs_counts); note_launch();
+        k_rs_scan<<<dim3(BINS, nsorts, t->n_inst), 1024, 0, s>>>(t->dinst, t->rs_counts, t->rs_totals); note_launch();
         if (shift == 0)
-            k_rs_scatter<K, true><<<grid, TPB, 0, s>>>(kin, nullptr, kout, vout, stride, n, shift,
-                                                       counts, totals, ntiles);
+            k_rs_scatter<K, true><<<grid, TPB, 0, s>>>(t->dinst, kin, nullptr, kout, vout, stride, shift,
+                                                       t->rs_counts, t->rs_totals);
         else
-            k_rs_scatter<K, false><<<grid, TPB, 0, s>>>(kin, vin, kout, vout, stride, n, shift,
-                                                        counts, totals, ntiles);
+            k_rs_scatter<K, false><<<grid, TPB, 0, s>>>(t->dinst, kin, vin, kout, vout, stride, shift,
+                                                        t->rs_counts, t->rs_totals);
         note_launch();
         cur ^= 1;
     }
@@ -269,32 +291,42 @@ int radix_sort(K* keys, int32_t* vals, int64_t stride, int nsorts, int64_t n, in
 
 // ---- stable partitions inside segments ---------------------------------------------------------
 
-__global__ void __launch_bounds__(TPB) k_part_count(const int32_t* __restrict__ in,
-                                                    const uint8_t* __restrict__ flag, int64_t n,
+// grid (tiles, instances)
+__global__ void __launch_bounds__(TPB) k_part_count(const Inst* __restrict__ I, int l,
+                                                    const int32_t* __restrict__ in,
+                                                    const uint8_t* __restrict__ flag,
                                                     uint32_t* __restrict__ tilecnt)
 {
+    const Inst S = I[blockIdx.y];
+    if (l >= S.L || blockIdx.x >= S.ntiles) return;
+    in += S.p0;
+    flag += S.p0;
     __shared__ uint32_t wt[32];
     const int64_t base = (int64_t)blockIdx.x * TILE;
     uint32_t c = 0;
     for (int j = 0; j < ITEMS; j++) {
         int64_t i = base + (int64_t)j * TPB + threadIdx.x;
-        if (i < n) c += flag[in[i]];
+        if (i < S.n) c += flag[in[i]];
     }
     uint32_t tot;
     block_excl_scan(c, wt, tot);
-    if (threadIdx.x == 0) tilecnt[blockIdx.x] = tot;
+    if (threadIdx.x == 0) tilecnt[S.t0 + blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* a, int64_t m)
+// grid (1, instances)
+__global__ void __launch_bounds__(1024) k_scan_tiles(const Inst* __restrict__ I, int l, uint32_t* a)
 {
+    const Inst S = I[blockIdx.y];
+    if (l >= S.L) return;
+    a += S.t0;
     __shared__ uint32_t wt[32];
     uint32_t carry = 0;
-    for (int64_t b = 0; b < m; b += blockDim.x) {
+    for (int64_t b = 0; b < S.ntiles; b += blockDim.x) {
         int64_t i = b + threadIdx.x;
-        uint32_t v = i < m ? a[i] : 0;
+        uint32_t v = i < S.ntiles ? a[i] : 0;
         uint32_t tot;
         uint32_t e = block_excl_scan(v, wt, tot);
-        if (i < m) a[i] = carry + e;
+        if (i < S.ntiles) a[i] = carry + e;
         carry += tot;
     }
 }
@@ -309,24 +341,46 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* a, int64_t m)
 //       x-half bit of the next level.
 // Zeros keep their order and come first.  A segment of size m holds m - floor(m/2) ones, ob[j]
 // counts the ones of all segments before segment j at that depth, tileoff[] is the exclusive scan
-// of the ones per tile.
-__global__ void __launch_bounds__(TPB) k_part_scatter(const int32_t* __restrict__ in,
+// of the ones per tile.  An instance with fewer than l + 1 levels is finished: its items are
+// copied through unchanged so that the next level finds them in the output buffer.
+// grid (tiles, instances).
+__global__ void __launch_bounds__(TPB) k_part_scatter(const Inst* __restrict__ I, int l, int xmode,
+                                                      const int32_t* __restrict__ in,
                                                       const int32_t* __restrict__ in_seg,
                                                       int32_t* __restrict__ out,
                                                       int32_t* __restrict__ out_seg,
                                                       const uint8_t* __restrict__ flag,
-                                                      uint8_t* __restrict__ flagout, int32_t n, int l,
-                                                      int xmode, const int32_t* __restrict__ node_off,
+                                                      uint8_t* __restrict__ flagout,
+                                                      const int32_t* __restrict__ node_off,
                                                       const int32_t* __restrict__ ones_before,
                                                       const uint32_t* __restrict__ tileoff,
                                                       int32_t* status)
 {
+    const Inst S = I[blockIdx.y];
+    if (blockIdx.x >= S.ntiles) return;
+    in += S.p0;
+    in_seg += S.p0;
+    out += S.p0;
+    out_seg += S.p0;
+    const int32_t n = (int32_t)S.n;
+    if (l >= S.L) {
+        for (int j = 0; j < ITEMS; j++) {
+            const int32_t i = (int32_t)blockIdx.x * TILE + j * TPB + threadIdx.x;
+            if (i < n) {
+                out[i] = in[i];
+                out_seg[i] = in_seg[i];
+            }
+        }
+        return;
+    }
+    flag += S.p0;
+    flagout += S.p0;
     __shared__ uint32_t wtot[WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     const int32_t base = (int32_t)blockIdx.x * TILE + w * WCHUNK;
-    const int32_t* offD = node_off + node_offset_base(2 * l);
-    const int32_t* ob = ones_before + ones_before_offset(2 * l + xmode);
+    const int32_t* offD = node_off + S.no0 + node_offset_base(2 * l);
+    const int32_t* ob = ones_before + S.ob0 + ones_before_offset(2 * l + xmode);
     int32_t id[ITEMS];
     uint32_t pre[ITEMS];
     uint32_t fl = 0, run = 0;
@@ -343,7 +397,7 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(const int32_t* __restrict_
     }
     if (lane == 0) wtot[w] = run;
     __syncthreads();
-    uint32_t woff = tileoff[blockIdx.x];
+    uint32_t woff = tileoff[S.t0 + blockIdx.x];
     for (int ww = 0; ww < w; ww++) woff += wtot[ww];
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
@@ -381,9 +435,13 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(const int32_t* __restrict_
     }
 }
 
-// Level-0 x-split: the upper half of the x order has the bit set.
-__global__ void k_init_hx(const int32_t* __restrict__ X, int32_t n, uint8_t* __restrict__ hx)
+// Level-0 x-split: the upper half of the x order has the bit set.  grid (blocks, instances)
+__global__ void k_init_hx(const Inst* __restrict__ I, const int32_t* __restrict__ X, uint8_t* __restrict__ hx)
 {
+    const Inst S = I[blockIdx.y];
+    X += S.p0;
+    hx += S.p0;
+    const int32_t n = (int32_t)S.n;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         hx[X[i]] = (i >= (n >> 1)) ? 1 : 0;
 }
@@ -392,14 +450,21 @@ __device__ __forceinline__ double midpoint(double a, double b) { return __dmul_r
 
 // Split coordinates of the boxes of level l and the rectangles of their children.  X is the
 // x-ordered list segmented by the boxes of level l, Yn the y-ordered list segmented by their
-// x-halves.
-__global__ void k_split_rects(const int32_t* __restrict__ X, const int32_t* __restrict__ Yn,
-                              const double* __restrict__ x, const double* __restrict__ y,
-                              const int32_t* __restrict__ node_off, int l, double* __restrict__ rects)
+// x-halves.  grid (blocks, instances)
+__global__ void k_split_rects(const Inst* __restrict__ I, int l, const int32_t* __restrict__ X,
+                              const int32_t* __restrict__ Yn, const double* __restrict__ x,
+                              const double* __restrict__ y, const int32_t* __restrict__ node_off,
+                              double* __restrict__ rects)
 {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= level_size(l)) return;
-    const int32_t* offD = node_off + node_offset_base(2 * l);
+    const Inst S = I[blockIdx.y];
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= S.L || b >= level_size(l)) return;
+    X += S.p0;
+    Yn += S.p0;
+    x += S.p0;
+    y += S.p0;
+    rects += 4 * S.b0;
+    const int32_t* offD = node_off + S.no0 + node_offset_base(2 * l);
     const int64_t o = offD[b], m = offD[b + 1] - o;
     int64_t mx = m >> 1;
     double xs = midpoint(x[X[o + mx - 1]], x[X[o + mx]]);
@@ -419,17 +484,22 @@ __global__ void k_split_rects(const int32_t* __restrict__ X, const int32_t* __re
     cr[12] = xs; cr[13] = px1; cr[14] = ys[1]; cr[15] = py1;
 }
 
-// After the last level every item of X carries its leaf.
-__global__ void k_leaf_of(const int32_t* __restrict__ X, const int32_t* __restrict__ XS, int32_t n,
-                          uint32_t* __restrict__ leaf_of)
+// After the last level every item of X carries its leaf.  grid (blocks, instances)
+__global__ void k_leaf_of(const Inst* __restrict__ I, const int32_t* __restrict__ X,
+                          const int32_t* __restrict__ XS, uint32_t* __restrict__ leaf_of)
 {
+    const Inst S = I[blockIdx.y];
+    X += S.p0;
+    XS += S.p0;
+    leaf_of += S.p0;
+    const int32_t n = (int32_t)S.n;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         leaf_of[X[i]] = (uint32_t)XS[i];
 }
 
 // Centre (rectangle midpoint) and radius (half diagonal) of every box, with the same sequence of
 // correctly rounded binary64 operations as the criterion's reference; plus a float-float copy
-// of the centre for the binary32 path.
+// of the centre and a binary32 radius for the binary32 path.  One thread per box of the forest.
 __global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, double* __restrict__ cen,
                            double* __restrict__ rad, float* __restrict__ rad32, float* __restrict__ chi,
                            float* __restrict__ clo)
@@ -452,17 +522,30 @@ __global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, doubl
 }
 
 // Coordinates in canonical order, and their binary32 offsets from the leaf centre.
-__global__ void k_gather_points(const int32_t* __restrict__ perm, const uint32_t* __restrict__ leaf_of,
-                                const double* __restrict__ x, const double* __restrict__ y, int64_t n,
-                                int L, const double* __restrict__ cen, double* __restrict__ xs,
-                                double* __restrict__ ys, float* __restrict__ dxf, float* __restrict__ dyf,
+// grid (blocks, instances)
+__global__ void k_gather_points(const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+                                const uint32_t* __restrict__ leaf_of, const double* __restrict__ x,
+                                const double* __restrict__ y, const double* __restrict__ cen,
+                                double* __restrict__ xs, double* __restrict__ ys,
+                                float* __restrict__ dxf, float* __restrict__ dyf,
                                 int32_t* __restrict__ cleaf)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+    const Inst S = I[blockIdx.y];
+    perm += S.p0;
+    leaf_of += S.p0;
+    x += S.p0;
+    y += S.p0;
+    xs += S.p0;
+    ys += S.p0;
+    dxf += S.p0;
+    dyf += S.p0;
+    cleaf += S.p0;
+    cen += 2 * S.b0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t id = perm[i];
         cleaf[i] = (int32_t)leaf_of[id];
-        int64_t g = level_base(L) + leaf_of[id];
+        int64_t g = level_base(S.L) + leaf_of[id];
         double a = x[id], b = y[id];
         xs[i] = a;
         ys[i] = b;
@@ -471,38 +554,35 @@ __global__ void k_gather_points(const int32_t* __restrict__ perm, const uint32_t
     }
 }
 
-int grid_for(int64_t n, int threads)
-{
-    int64_t g = (n + threads - 1) / threads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
-}
-
 }  // namespace
 
-// Host side: sizes are fixed by (n, L) alone, so all tables are computed here once.
-int tree_alloc(fmm_tree t)
+int blocks_for(int64_t n, int threads, int n_inst)
 {
-    const int64_t n = t->n;
-    const int L = t->L;
-    t->nbox = level_base(L + 1);
-    t->nleaf = level_size(L);
-    t->ntiles = (n + TILE - 1) / TILE;
+    int64_t g = (n + threads - 1) / threads;
+    int64_t cap = std::max<int64_t>(1, (152 * 32) / std::max(1, n_inst));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
 
-    // floor-left split sizes per depth; ones-before tables for depths 0 .. 2L-1; node offsets for
-    // depths 0 .. 2L; leaf offsets
+// Host tables of one instance (sizes depend on (n, L) only): ones-before tables for depths
+// 0 .. 2L-1, node offsets for depths 0 .. 2L, leaf offsets.  Any pointer may be null.
+int tree_tables_host(int64_t n, int L, int32_t* ones_before, int32_t* node_off, int32_t* leaf_begin)
+{
     std::vector<int64_t> sizes{n}, next;
-    std::vector<int32_t> ob_all, off_all;
+    int64_t iob = 0, ino = 0;
     for (int d = 0; d <= 2 * L; d++) {
         int64_t o = 0;
         for (int64_t m : sizes) {
-            off_all.push_back((int32_t)o);
+            if (node_off) node_off[ino] = (int32_t)o;
+            ino++;
             o += m;
         }
-        off_all.push_back((int32_t)o);
+        if (node_off) node_off[ino] = (int32_t)o;
+        ino++;
         if (d == 2 * L) break;
         int64_t acc = 0;
         for (int64_t m : sizes) {
-            ob_all.push_back((int32_t)acc);
+            if (ones_before) ones_before[iob] = (int32_t)acc;
+            iob++;
             acc += m - m / 2;
         }
         next.clear();
@@ -512,9 +592,73 @@ int tree_alloc(fmm_tree t)
         }
         sizes.swap(next);
     }
-    std::vector<int32_t> lb(sizes.size() + 1);
-    lb[0] = 0;
-    for (size_t i = 0; i < sizes.size(); i++) lb[i + 1] = lb[i] + (int32_t)sizes[i];
+    if (leaf_begin) {
+        leaf_begin[0] = 0;
+        for (size_t i = 0; i < sizes.size(); i++) leaf_begin[i + 1] = leaf_begin[i] + (int32_t)sizes[i];
+    }
+    return 0;
+}
+
+// The instance table of a forest; every size follows from the (n, L) of its instances.
+void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls)
+{
+    int64_t p0 = 0, b0 = 0, t0 = 0, ob0 = 0, no0 = 0, lb0 = 0;
+    for (int i = 0; i < n_inst; i++) {
+        Inst& S = out[i];
+        S = Inst{};
+        S.n = ns[i];
+        S.L = Ls[i];
+        S.p0 = p0;
+        S.b0 = b0;
+        S.nbox = level_base(S.L + 1);
+        S.o0 = b0 + i;
+        S.t0 = t0;
+        S.ntiles = (S.n + TILE - 1) / TILE;
+        S.ob0 = ob0;
+        S.no0 = no0;
+        S.lb0 = lb0;
+        p0 += S.n;
+        b0 += S.nbox;
+        t0 += S.ntiles;
+        ob0 += ones_before_offset(2 * S.L);
+        no0 += node_offset_base(2 * S.L + 1);
+        lb0 += level_size(S.L) + 1;
+    }
+}
+
+void forest_totals(fmm_tree t)
+{
+    t->n = t->nbox = t->ntiles = t->n_ob = t->n_no = t->nleaf = 0;
+    t->Lmax = 0;
+    t->max_tiles = t->max_n = 0;
+    for (int i = 0; i < t->n_inst; i++) {
+        const Inst& S = t->hinst[i];
+        t->n += S.n;
+        t->nbox += S.nbox;
+        t->ntiles += S.ntiles;
+        t->n_ob += ones_before_offset(2 * S.L);
+        t->n_no += node_offset_base(2 * S.L + 1);
+        t->nleaf += level_size(S.L);
+        t->Lmax = std::max(t->Lmax, S.L);
+        t->max_tiles = std::max(t->max_tiles, S.ntiles);
+        t->max_n = std::max(t->max_n, S.n);
+    }
+}
+
+int tree_alloc(fmm_tree t, int n_inst, const int64_t* ns, const int* Ls)
+{
+    t->n_inst = n_inst;
+    t->hinst = new (std::nothrow) Inst[n_inst];
+    if (!t->hinst) return fail(FMM_ERR_OOM, "host allocation");
+    fill_instances(t->hinst, n_inst, ns, Ls);
+    forest_totals(t);
+
+    std::vector<int32_t> ob_all(std::max<int64_t>(t->n_ob, 1)), off_all(t->n_no);
+    std::vector<int32_t> lb_all(t->nleaf + n_inst);
+    for (int i = 0; i < n_inst; i++) {
+        const Inst& S = t->hinst[i];
+        tree_tables_host(S.n, S.L, ob_all.data() + S.ob0, off_all.data() + S.no0, lb_all.data() + S.lb0);
+    }
 
     auto A = [&](void** p, size_t bytes) -> int {
         cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
@@ -522,7 +666,8 @@ int tree_alloc(fmm_tree t)
         return 0;
     };
     int rc = 0;
-    const size_t nb = (size_t)t->nbox, nn = (size_t)n;
+    const size_t nb = (size_t)t->nbox, nn = (size_t)t->n, ni = (size_t)n_inst;
+    if ((rc = A((void**)&t->dinst, sizeof(Inst) * ni))) return rc;
     if ((rc = A((void**)&t->rects, 32 * nb))) return rc;
     if ((rc = A((void**)&t->centers, 16 * nb))) return rc;
     if ((rc = A((void**)&t->radii, 8 * nb))) return rc;
@@ -530,7 +675,7 @@ int tree_alloc(fmm_tree t)
     if ((rc = A((void**)&t->cen_hi, 8 * nb))) return rc;
     if ((rc = A((void**)&t->cen_lo, 8 * nb))) return rc;
     if ((rc = A((void**)&t->perm, 4 * nn))) return rc;
-    if ((rc = A((void**)&t->leaf_begin, 4 * lb.size()))) return rc;
+    if ((rc = A((void**)&t->leaf_begin, 4 * lb_all.size()))) return rc;
     if ((rc = A((void**)&t->leaf_of, 4 * nn))) return rc;
     if ((rc = A((void**)&t->cleaf, 4 * nn))) return rc;
     if ((rc = A((void**)&t->xs, 8 * nn))) return rc;
@@ -540,17 +685,17 @@ int tree_alloc(fmm_tree t)
     if ((rc = A((void**)&t->keys, 8 * 4 * nn))) return rc;
     if ((rc = A((void**)&t->vals, 4 * 4 * nn))) return rc;
     if ((rc = A((void**)&t->rs_counts, 4 * 2 * BINS * (size_t)t->ntiles))) return rc;
-    if ((rc = A((void**)&t->rs_totals, 4 * 2 * BINS))) return rc;
+    if ((rc = A((void**)&t->rs_totals, 4 * 2 * BINS * ni))) return rc;
     if ((rc = A((void**)&t->tilecnt, 4 * (size_t)t->ntiles))) return rc;
     if ((rc = A((void**)&t->hflag, 2 * nn))) return rc;
-    if ((rc = A((void**)&t->bbox_keys, 32))) return rc;
+    if ((rc = A((void**)&t->bbox_keys, 32 * ni))) return rc;
     if ((rc = A((void**)&t->ones_before, 4 * ob_all.size()))) return rc;
     if ((rc = A((void**)&t->node_off, 4 * off_all.size()))) return rc;
     if ((rc = A((void**)&t->segs, 4 * 4 * nn))) return rc;
     if ((rc = A((void**)&t->status, 4))) return rc;
-    FMM_CUDA(cudaMemcpy(t->leaf_begin, lb.data(), 4 * lb.size(), cudaMemcpyHostToDevice));
-    if (!ob_all.empty())
-        FMM_CUDA(cudaMemcpy(t->ones_before, ob_all.data(), 4 * ob_all.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemcpy(t->dinst, t->hinst, sizeof(Inst) * ni, cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemcpy(t->leaf_begin, lb_all.data(), 4 * lb_all.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemcpy(t->ones_before, ob_all.data(), 4 * ob_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemcpy(t->node_off, off_all.data(), 4 * off_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemset(t->status, 0, 4));
     return 0;
@@ -558,24 +703,26 @@ int tree_alloc(fmm_tree t)
 
 int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
 {
-    const int64_t n = t->n;
-    const int L = t->L;
-    const int64_t nt = t->ntiles;
-    uint64_t* kx = t->keys;          // x sort: buffers [0, n) and [n, 2n)
-    int32_t* vals = t->vals;         // x sort values [0, 2n); y sort values [2n, 4n)
+    const int64_t n = t->n;  // total points of the forest
+    const int ni = t->n_inst;
+    const int L = t->Lmax;
+    const unsigned mt = (unsigned)t->max_tiles;
+    uint64_t* kx = t->keys;   // x sort: buffers [0, n) and [n, 2n); y sort: [2n, 4n)
+    int32_t* vals = t->vals;  // x sort values [0, 2n); y sort values [2n, 4n)
     uint8_t* hx = t->hflag;
     uint8_t* hy = t->hflag + n;
     int32_t *X, *Xo, *Y, *Yo;
     int32_t* Xfinal_seg = nullptr;
+    const int pb = blocks_for(t->max_n, 256, ni);
 
     {
         StageScope scope(FMM_STAGE_TREE_SORT, s);
-        k_bbox_init<<<1, 32, 0, s>>>(t->bbox_keys); note_launch();
-        k_make_keys<<<grid_for(n, 256), 256, 0, s>>>(x, y, n, kx, kx + 2 * n, t->bbox_keys, t->status); note_launch();
-        k_root_rect<<<1, 32, 0, s>>>(t->bbox_keys, t->rects); note_launch();
+        k_bbox_init<<<1, 256, 0, s>>>(ni, t->bbox_keys); note_launch();
+        k_make_keys<<<dim3(pb, ni), 256, 0, s>>>(t->dinst, x, y, n, kx, t->bbox_keys, t->status); note_launch();
+        k_root_rect<<<1, 256, 0, s>>>(t->dinst, ni, t->bbox_keys, t->rects); note_launch();
         FMM_LAUNCH_CHECK("tree: keys");
         // x order and y order of all points, ties by input index (two sorts in one launch sequence)
-        int cur = radix_sort<uint64_t>(kx, vals, 2 * n, 2, n, 64, t->rs_counts, t->rs_totals, nt, s);
+        int cur = radix_sort<uint64_t>(t, kx, vals, 2 * n, 2, 64, s);
         FMM_LAUNCH_CHECK("tree: radix sort");
         X = vals + (cur ? n : 0);
         Xo = vals + (cur ? 0 : n);
@@ -589,23 +736,23 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
         int32_t *XS = t->segs, *XSo = t->segs + n, *YS = t->segs + 2 * n, *YSo = t->segs + 3 * n;
         FMM_CUDA(cudaMemsetAsync(XS, 0, 4 * n, s));
         FMM_CUDA(cudaMemsetAsync(YS, 0, 4 * n, s));
-        const int32_t n32 = (int32_t)n;
-        k_init_hx<<<grid_for(n, 256), 256, 0, s>>>(X, n32, hx); note_launch();
+        k_init_hx<<<dim3(pb, ni), 256, 0, s>>>(t->dinst, X, hx); note_launch();
         for (int l = 0; l < L; l++) {
             // Y: stable partition of each box by its x-half bit; records the y-half bit
-            k_part_count<<<(unsigned)nt, TPB, 0, s>>>(Y, hx, n, t->tilecnt); note_launch();
-            k_scan_tiles<<<1, 1024, 0, s>>>(t->tilecnt, nt); note_launch();
-            k_part_scatter<<<(unsigned)nt, TPB, 0, s>>>(Y, YS, Yo, YSo, hx, hy, n32, l, 0, t->node_off,
+            k_part_count<<<dim3(mt, ni), TPB, 0, s>>>(t->dinst, l, Y, hx, t->tilecnt); note_launch();
+            k_scan_tiles<<<dim3(1, ni), 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
+            k_part_scatter<<<dim3(mt, ni), TPB, 0, s>>>(t->dinst, l, 0, Y, YS, Yo, YSo, hx, hy, t->node_off,
                                                         t->ones_before, t->tilecnt, t->status); note_launch();
             std::swap(Y, Yo);
             std::swap(YS, YSo);
             // split coordinates and child rectangles of level l
-            int64_t nb = level_size(l);
-            k_split_rects<<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(X, Y, x, y, t->node_off, l, t->rects); note_launch();
+            const int64_t nb = level_size(l);
+            k_split_rects<<<dim3((unsigned)((nb + 127) / 128), ni), 128, 0, s>>>(t->dinst, l, X, Y, x, y,
+                                                                                 t->node_off, t->rects); note_launch();
             // X: stable partition of each x-half by the y-half bit; records the next x-half bit
-            k_part_count<<<(unsigned)nt, TPB, 0, s>>>(X, hy, n, t->tilecnt); note_launch();
-            k_scan_tiles<<<1, 1024, 0, s>>>(t->tilecnt, nt); note_launch();
-            k_part_scatter<<<(unsigned)nt, TPB, 0, s>>>(X, XS, Xo, XSo, hy, hx, n32, l, 1, t->node_off,
+            k_part_count<<<dim3(mt, ni), TPB, 0, s>>>(t->dinst, l, X, hy, t->tilecnt); note_launch();
+            k_scan_tiles<<<dim3(1, ni), 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
+            k_part_scatter<<<dim3(mt, ni), TPB, 0, s>>>(t->dinst, l, 1, X, XS, Xo, XSo, hy, hx, t->node_off,
                                                         t->ones_before, t->tilecnt, t->status); note_launch();
             std::swap(X, Xo);
             std::swap(XS, XSo);
@@ -618,19 +765,19 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
         StageScope scope(FMM_STAGE_TREE_FINISH, s);
         // canonical order: stable sort of the input indices by leaf (inside a leaf: input order)
         uint32_t* leaf_of = (uint32_t*)t->leaf_of;
-        k_leaf_of<<<grid_for(n, 256), 256, 0, s>>>(X, Xfinal_seg, (int32_t)n, leaf_of); note_launch();
+        k_leaf_of<<<dim3(pb, ni), 256, 0, s>>>(t->dinst, X, Xfinal_seg, leaf_of); note_launch();
         uint32_t* k32 = (uint32_t*)t->keys;  // reuse the key buffers: [0, n) and [n, 2n)
         int32_t* v32 = t->vals + 2 * n;      // value buffers [2n, 4n)
-        int bits = std::max(8, 2 * L);  // with L = 0 all keys are 0 and the order stays the input order
+        const int bits = std::max(8, 2 * L);  // with L = 0 all keys are 0: the order stays the input order
         FMM_CUDA(cudaMemcpyAsync(k32, leaf_of, 4 * n, cudaMemcpyDeviceToDevice, s));
-        int c2 = radix_sort<uint32_t>(k32, v32, 0, 1, n, bits, t->rs_counts, t->rs_totals, nt, s);
+        int c2 = radix_sort<uint32_t>(t, k32, v32, 0, 1, bits, s);
         FMM_CUDA(cudaMemcpyAsync(t->perm, v32 + (c2 ? n : 0), 4 * n, cudaMemcpyDeviceToDevice, s));
 
-        int64_t nb = t->nbox;
+        const int64_t nb = t->nbox;
         k_geometry<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(t->rects, nb, t->centers, t->radii,
                                                                 t->rad32, t->cen_hi, t->cen_lo); note_launch();
-        k_gather_points<<<grid_for(n, 256), 256, 0, s>>>(t->perm, leaf_of, x, y, n, L, t->centers,
-                                                         t->xs, t->ys, t->dxf, t->dyf, t->cleaf); note_launch();
+        k_gather_points<<<dim3(pb, ni), 256, 0, s>>>(t->dinst, t->perm, leaf_of, x, y, t->centers,
+                                                     t->xs, t->ys, t->dxf, t->dyf, t->cleaf); note_launch();
         FMM_LAUNCH_CHECK("tree: canonical order");
     }
     t->built = true;

@@ -60,6 +60,16 @@ def load_library(path: str = LIB_PATH):
         vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         sig = {
             "fmm_tree_create": (i32, [i64, i32, ctypes.POINTER(vp)]),
+            "fmm_tree_create_batched": (i32, [i32, vp, vp, ctypes.POINTER(vp)]),
+            "fmm_tree_num_instances": (i32, [vp]),
+            "fmm_tree_instance": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                        ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+            "fmm_lists_create_batched": (i32, [vp, vp, vp, ctypes.POINTER(vp)]),
+            "fmm_lists_counts": (i32, [vp, vp, vp, vp]),
+            "fmm_lists_export_instance": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+            "fmm_autotune": (i32, [vp, vp, vp, ctypes.POINTER(fmm_params), vp, vp, ctypes.POINTER(i32),
+                                   ctypes.POINTER(i32)]),
+            "fmm_set_launch": (i32, [vp, i32, i32]),
             "fmm_build_tree": (i32, [vp, vp, vp, vp]),
             "fmm_tree_export": (i32, [vp, vp, vp, vp, vp]),
             "fmm_tree_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)]),
@@ -125,6 +135,33 @@ def fmm_tree_create(n: int, levels: int) -> ctypes.c_void_p:
     return h
 
 
+def fmm_tree_create_batched(ns, levels) -> ctypes.c_void_p:
+    """A forest of len(ns) independent instances (instance i: ns[i] points, levels[i] levels)."""
+    import numpy as np
+    n_arr = np.ascontiguousarray(ns, dtype=np.int64)
+    l_arr = np.ascontiguousarray(levels, dtype=np.int32)
+    if n_arr.shape != l_arr.shape or n_arr.ndim != 1:
+        raise FMMError(FMM_ERR_ARG, "ns and levels must be 1-d sequences of one length")
+    h = ctypes.c_void_p()
+    _check(load_library().fmm_tree_create_batched(int(n_arr.size), n_arr.ctypes.data_as(ctypes.c_void_p),
+                                                  l_arr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+    return h
+
+
+def fmm_tree_num_instances(tree) -> int:
+    rc = load_library().fmm_tree_num_instances(tree)
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def fmm_tree_instance(tree, i: int) -> dict:
+    """Where instance i of a forest lives: p0, n, levels, b0, nbox, lb0."""
+    v = [ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()]
+    _check(load_library().fmm_tree_instance(tree, int(i), *[ctypes.byref(a) for a in v]))
+    return dict(zip(("p0", "n", "levels", "b0", "nbox", "lb0"), (a.value for a in v)))
+
+
 def fmm_build_tree(tree, x: torch.Tensor, y: torch.Tensor, stream=None):
     n = fmm_tree_info(tree)[0]
     _check(load_library().fmm_build_tree(tree, _dev(x, torch.float64, n, "x"),
@@ -173,6 +210,35 @@ def fmm_lists_create(tree, weak_capacity: int = 0, strong_capacity: int = 0) -> 
     return h
 
 
+def fmm_lists_create_batched(tree, weak_capacity, strong_capacity) -> ctypes.c_void_p:
+    import numpy as np
+    w = np.ascontiguousarray(weak_capacity, dtype=np.int64)
+    st = np.ascontiguousarray(strong_capacity, dtype=np.int64)
+    ni = fmm_tree_num_instances(tree)
+    if w.shape != (ni,) or st.shape != (ni,):
+        raise FMMError(FMM_ERR_ARG, f"capacities need {ni} entries each")
+    h = ctypes.c_void_p()
+    _check(load_library().fmm_lists_create_batched(tree, w.ctypes.data_as(ctypes.c_void_p),
+                                                   st.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+    return h
+
+
+def fmm_lists_counts(lists, n_inst: int, stream=None, check: bool = True):
+    """Per-instance (weak, strong) entry counts; with check=False a capacity overflow is
+    returned as the third value instead of raised."""
+    import numpy as np
+    w = np.zeros(n_inst, np.int64)
+    st = np.zeros(n_inst, np.int64)
+    rc = load_library().fmm_lists_counts(lists, _stream(stream), w.ctypes.data_as(ctypes.c_void_p),
+                                         st.ctypes.data_as(ctypes.c_void_p))
+    if check:
+        _check(rc)
+        return w, st
+    if rc not in (FMM_OK, FMM_ERR_CAPACITY):
+        _check(rc)
+    return w, st, rc == FMM_ERR_CAPACITY
+
+
 def fmm_interaction_lists(tree, lists, theta: float, stream=None):
     _check(load_library().fmm_interaction_lists(tree, lists, float(theta), _stream(stream)))
 
@@ -190,6 +256,13 @@ def fmm_lists_export(lists, woff, widx, soff, sidx, stream=None):
                                            _dev(sidx, torch.int32, None, "sidx"), _stream(stream)))
 
 
+def fmm_lists_export_instance(lists, i: int, woff, widx, soff, sidx, stream=None):
+    _check(load_library().fmm_lists_export_instance(lists, int(i), _dev(woff, torch.int32, None, "woff"),
+                                                    _dev(widx, torch.int32, None, "widx"),
+                                                    _dev(soff, torch.int32, None, "soff"),
+                                                    _dev(sidx, torch.int32, None, "sidx"), _stream(stream)))
+
+
 def fmm_lists_destroy(lists):
     if lists:
         load_library().fmm_lists_destroy(lists)
@@ -201,6 +274,23 @@ def fmm_evaluate(tree, lists, q: torch.Tensor, p: int, mode: int, phi: torch.Ten
     prm = fmm_params(int(p), int(mode), float(tol))
     _check(load_library().fmm_evaluate(tree, lists, _dev(q, torch.float64, n, "q"), ctypes.byref(prm),
                                        _dev(phi, torch.float64, n, "phi"), _stream(stream)))
+
+
+def fmm_autotune(tree, lists, q: torch.Tensor, p: int, mode: int, phi: torch.Tensor, tol: float = 1e-6,
+                 stream=None):
+    """Time complete evaluations over a ladder of grid sizes and keep the fastest; returns the
+    chosen (M2L, near-field) blocks per instance."""
+    n = fmm_tree_info(tree)[0]
+    prm = fmm_params(int(p), int(mode), float(tol))
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().fmm_autotune(tree, lists, _dev(q, torch.float64, n, "q"), ctypes.byref(prm),
+                                       _dev(phi, torch.float64, n, "phi"), _stream(stream),
+                                       ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def fmm_set_launch(tree, m2l_blocks: int = 0, p2p_blocks: int = 0):
+    _check(load_library().fmm_set_launch(tree, int(m2l_blocks), int(p2p_blocks)))
 
 
 def fmm_direct(x, y, q, targets, phi, stream=None):
@@ -319,6 +409,104 @@ class FMM:
         fmm_lists_export(self.lists, woff, widx, soff, sidx)
         torch.cuda.synchronize(self.device)
         return woff, widx[:w], soff, sidx[:s]
+
+    def close(self):
+        if self.lists is not None:
+            fmm_lists_destroy(self.lists)
+            self.lists = None
+        if self.tree is not None:
+            fmm_tree_destroy(self.tree)
+            self.tree = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FMMBatch:
+    """Many independent point sets evaluated together: one forest tree, one set of lists, and
+    every launch covering all instances.  Coordinates, strengths and potentials are the
+    instances' arrays concatenated in instance order.
+
+    >>> b = FMMBatch(x, y, sizes=[1000, 50000], levels=[3, 6], theta=0.5)
+    >>> phi = b.evaluate(q, p=16)
+    """
+
+    def __init__(self, x: torch.Tensor, y: torch.Tensor, sizes, levels, theta: float = 0.5,
+                 check: bool = True, weak_per_box: int = 48, strong_per_box: int = 24):
+        self.sizes = [int(v) for v in sizes]
+        self.levels = [int(v) for v in levels]
+        self.n = sum(self.sizes)
+        self.n_inst = len(self.sizes)
+        self.theta = theta
+        self.device = x.device
+        self.tree = fmm_tree_create_batched(self.sizes, self.levels)
+        self.lists = None
+        self.inst = [fmm_tree_instance(self.tree, i) for i in range(self.n_inst)]
+        try:
+            nb = [d["nbox"] for d in self.inst]
+            self.lists = fmm_lists_create_batched(self.tree, [weak_per_box * v for v in nb],
+                                                  [strong_per_box * v for v in nb])
+            self.rebuild(x, y, check=check)
+        except Exception:
+            self.close()
+            raise
+
+    def rebuild(self, x, y, theta=None, check: bool = True):
+        """Rebuild for new coordinates (same sizes and levels); regrows the capacity of every
+        instance whose lists overflowed and rebuilds."""
+        if theta is not None:
+            self.theta = theta
+        fmm_build_tree(self.tree, x, y)
+        fmm_interaction_lists(self.tree, self.lists, self.theta)
+        if check:
+            w, s, over = fmm_lists_counts(self.lists, self.n_inst, check=False)
+            if over:
+                nb = [d["nbox"] for d in self.inst]
+                fmm_lists_destroy(self.lists)
+                self.lists = None
+                # counts of an instance that overflowed are lower bounds: at least double it
+                self.lists = fmm_lists_create_batched(self.tree, [max(2 * int(a) + 64, 16 * b) for a, b in zip(w, nb)],
+                                                      [max(2 * int(a) + 64, 8 * b) for a, b in zip(s, nb)])
+                return self.rebuild(x, y, check=check)
+            self.counts = (w, s)
+            fmm_sync_status(self.tree, self.lists)
+
+    def evaluate(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6, out=None,
+                 check: bool = True):
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        phi = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
+        fmm_evaluate(self.tree, self.lists, q, p, m, phi, tol)
+        if check:
+            fmm_sync_status(self.tree, self.lists)
+        return phi
+
+    def autotune(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6):
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        phi = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        return fmm_autotune(self.tree, self.lists, q, p, m, phi, tol)
+
+    def export_instance(self, i: int):
+        """perm, rects, leaf_begin and the lists (woff, widx, soff, sidx) of instance i."""
+        d = self.inst[i]
+        n, L, nbox = fmm_tree_info(self.tree)
+        perm = torch.empty(n, dtype=torch.int32, device=self.device)
+        rects = torch.empty((nbox, 4), dtype=torch.float64, device=self.device)
+        nlb = sum(4 ** v + 1 for v in self.levels)
+        lb = torch.empty(nlb, dtype=torch.int32, device=self.device)
+        fmm_tree_export(self.tree, perm, rects, lb)
+        w, s = fmm_lists_counts(self.lists, self.n_inst)
+        woff = torch.empty(d["nbox"] + 1, dtype=torch.int32, device=self.device)
+        soff = torch.empty(d["nbox"] + 1, dtype=torch.int32, device=self.device)
+        widx = torch.empty(max(int(w[i]), 1), dtype=torch.int32, device=self.device)
+        sidx = torch.empty(max(int(s[i]), 1), dtype=torch.int32, device=self.device)
+        fmm_lists_export_instance(self.lists, i, woff, widx, soff, sidx)
+        torch.cuda.synchronize(self.device)
+        p0, lb0 = d["p0"], d["lb0"]
+        return (perm[p0:p0 + d["n"]], rects[d["b0"]:d["b0"] + d["nbox"]],
+                lb[lb0:lb0 + 4 ** d["levels"] + 1], woff, widx[:int(w[i])], soff, sidx[:int(s[i])])
 
     def close(self):
         if self.lists is not None:
