@@ -150,6 +150,101 @@ def pair_counts(f):
     return nweak, pairs
 
 
+def bench_batched(dev, steps, warmup, sequential=True):
+    """The batched workload: 512 independent instances, N log-uniform in [1e3, 2e5] (uniform
+    square / 2D normal / jittered unit circle), theta = 1/2, p = 16, leaves of ~32 points.  One
+    step = tree, lists and evaluation of every instance, all instances in the same launches,
+    replayed as one CUDA graph with the launch shapes chosen by the library's autotuner.  For
+    comparison the same instances are also run one after another through single-instance
+    handles (one step, plain launches)."""
+    import torch
+    from paper_1006_2269_gb300 import fmm, workloads as W
+    inst = W.batched_instances()
+    sizes = [c.x.shape[0] for c, _ in inst]
+    levels = [L for _, L in inst]
+    x = torch.as_tensor(np.concatenate([c.x for c, _ in inst]), device=dev)
+    y = torch.as_tensor(np.concatenate([c.y for c, _ in inst]), device=dev)
+    q = torch.as_tensor(np.concatenate([c.q for c, _ in inst]), device=dev)
+    n = int(sum(sizes))
+    theta, p = 0.5, 16
+    b = fmm.FMMBatch(x, y, sizes, levels, theta)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    m2l_blocks, p2p_blocks = b.autotune(q, p)
+
+    def step():
+        fmm.fmm_build_tree(b.tree, x, y)
+        fmm.fmm_interaction_lists(b.tree, b.lists, theta)
+        fmm.fmm_evaluate(b.tree, b.lists, q, p, fmm.FMM_MODE_MIXED, phi)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    fmm.fmm_sync_status(b.tree, b.lists)
+    l0 = fmm.fmm_launch_count()
+    step()
+    launches = fmm.fmm_launch_count() - l0
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, e in ev:
+        flush.zero_()
+        a.record(stream)
+        g.replay()
+        e.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(e) for a, e in ev) / steps
+    fmm.fmm_sync_status(b.tree, b.lists)
+    # accuracy: 16 sampled targets of every instance against the binary64 direct sum
+    worst = 0.0
+    for i, d in enumerate(b.inst):
+        a0, m = d["p0"], d["n"]
+        tg = torch.as_tensor(W.sample_targets(m, 16, W.SEED_BASE + 500 + i), device=dev)
+        ref = torch.empty(tg.numel(), dtype=torch.float64, device=dev)
+        fmm.fmm_direct(x[a0:a0 + m], y[a0:a0 + m], q[a0:a0 + m], tg, ref)
+        err = ((phi[a0:a0 + m][tg] - ref).abs().max() / ref.abs().max()).item()
+        worst = max(worst, err)
+    out = {"workload": "512 instances, N log-uniform in [1e3, 2e5], uniform/normal/circle, "
+                       "theta=1/2, p=16, ~32 points per leaf",
+           "instances": len(sizes), "points": n, "value": n / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms, "gpu_launches_per_step": launches, "cuda_graph": True,
+           "autotuned_blocks_per_instance": {"m2l": m2l_blocks, "near_field": p2p_blocks},
+           "rel_err_max_sampled": worst, "n_check_per_instance": 16}
+    b.close()
+    if sequential:
+        # the same instances one by one through single-instance handles
+        fs = []
+        try:
+            for i, (c, L) in enumerate(inst):
+                a0 = int(sum(sizes[:i]))
+                fs.append((fmm.FMM(x[a0:a0 + sizes[i]], y[a0:a0 + sizes[i]], L, theta), a0, sizes[i]))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(stream)
+            for f, a0, m in fs:
+                fmm.fmm_build_tree(f.tree, x[a0:a0 + m], y[a0:a0 + m])
+                fmm.fmm_interaction_lists(f.tree, f.lists, theta)
+                fmm.fmm_evaluate(f.tree, f.lists, q[a0:a0 + m], p, fmm.FMM_MODE_MIXED, phi[a0:a0 + m])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            out["one_by_one"] = {"value": n / (t * 1e-3), "ms_per_step": t,
+                                 "note": "same instances through 512 single-instance handles, plain launches"}
+        finally:
+            for f, _, _ in fs:
+                f.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,6 +254,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one instead of replaying a CUDA graph")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -335,6 +431,8 @@ def main():
         "roofline": roof,
         "clocks": clk.summary(),
     }
+    if not args.no_batched:
+        out["batched"] = bench_batched(dev, max(3, min(K, 10)), args.warmup, sequential=(rank == 0))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -215,12 +215,14 @@ void fmm_lists_destroy(fmm_lists l);
 int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi,
                  void* stream);
 
-/* Launch-shape tuning (no paper counterpart).  fmm_autotune runs complete evaluations of
- * (t, l, q, prm) on `stream` for a ladder of grid sizes of the M2L and near-field kernels, timing
- * each with CUDA events, and keeps the fastest for later evaluations of this tree; phi receives
- * the potentials of the last run.  It synchronises with the host (not for use under stream
- * capture).  The chosen blocks per instance are reported in m2l_blocks / p2p_blocks (host, may be
- * NULL).  fmm_set_launch sets them directly (0 = the built-in default). */
+/* Launch-shape tuning (no paper counterpart).  The M2L and near-field launches of a tree use a
+ * total number of blocks that is shared out over its instances in proportion to their work.
+ * fmm_autotune runs complete evaluations of (t, l, q, prm) on `stream` for a ladder of such
+ * totals, timing each with CUDA events, and keeps the fastest for later evaluations of this tree;
+ * phi receives the potentials of the last run.  It synchronises with the host (not for use under
+ * stream capture).  The chosen totals are reported in m2l_blocks / p2p_blocks (host, may be
+ * NULL).  fmm_set_launch sets them directly (0 = the built-in default); it uploads small launch
+ * tables and so also synchronises. */
 int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi,
                  void* stream, int* m2l_blocks_host, int* p2p_blocks_host);
 int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks);

@@ -98,6 +98,7 @@ void free_tree(fmm_tree t)
                     t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf, t->dinst, t->Lf0lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    sched_free_all(t);
     if (t->own_hinst) delete[] t->hinst;
     delete t;
 }
@@ -463,9 +464,10 @@ int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks)
     if (!t) return fail(FMM_ERR_ARG, "NULL tree");
     if (m2l_blocks < 0 || p2p_blocks < 0 || m2l_blocks > 65535 || p2p_blocks > 65535)
         return fail(FMM_ERR_ARG, "block counts must lie in [0, 65535]");
+    GUARD(t->dev);
     t->tune_m2l_blocks = m2l_blocks;
     t->tune_p2p_blocks = p2p_blocks;
-    return FMM_OK;
+    return sched_tuned(t);
 }
 
 int fmm_direct(const double* x, const double* y, const double* q, int64_t n, const int64_t* targets,

@@ -115,6 +115,44 @@ struct Inst {
     int32_t L, pad;
 };
 
+// Launch schedule over the instances of a forest.  A launch is a 1-D grid; block b works for
+// instance inst[b] as the rank-th of the nb = span[inst].y blocks that instance received
+// (span[inst].x is its first block).  Blocks are shared out in proportion to each instance's
+// work, so small and large instances finish together.  A tree of one instance needs no tables:
+// inst == nullptr means instance 0 owns the whole grid.
+struct Sched {
+    const int32_t* inst = nullptr;  // [blocks]
+    const int2* span = nullptr;     // [n_inst]
+};
+
+struct Slot {
+    int i, rank, nb;
+};
+
+__device__ __forceinline__ Slot slot_of(const Sched& m)
+{
+    if (m.inst == nullptr) return Slot{0, (int)blockIdx.x, (int)gridDim.x};
+    const int i = __ldg(m.inst + blockIdx.x);
+    const int2 sp = __ldg(m.span + i);
+    return Slot{i, (int)blockIdx.x - sp.x, sp.y};
+}
+
+// Radix digit-count scans: digits handled by one block of an instance with `ntiles` tiles
+// (digits x tiles <= 1024, so one block-wide scan covers them), or 1 from 1024 tiles on.
+__host__ __device__ inline int rs_digits_per_block(int64_t ntiles)
+{
+    if (ntiles >= 1024) return 1;
+    const int64_t g = 1024 / (ntiles < 1 ? 1 : ntiles);
+    return (int)(g < 256 ? g : 256);
+}
+
+// Host side of a schedule: the device tables (owned by the tree) and the grid size.
+struct SchedH {
+    Sched d;
+    int blocks = 0;
+    void* mem = nullptr;
+};
+
 struct LInst {            // list storage of one instance
     int64_t w0, wcap;     // weak entries [w0, w0 + wcap)
     int64_t s0, scap;     // strong entries [s0, s0 + scap)
@@ -180,8 +218,20 @@ struct fmm_tree_s {
     float* acc32 = nullptr; // [4n] binary32 far field hi and lo, near field hi and lo (canonical order)
     float* Lf0lo = nullptr; // [nbox] low part of Re b_0 of the binary32 locals (float-float)
 
-    // launch tuning (set by fmm_autotune; 0 = defaults)
+    // launch tuning (set by fmm_autotune; 0 = defaults): total blocks of the M2L and near-field
+    // launches, shared out over the instances in proportion to their work
     int tune_m2l_blocks = 0, tune_p2p_blocks = 0;
+
+    // launch schedules (device tables only for forests of more than one instance)
+    fmm::SchedH s_tiles;   // one block per tree-build tile
+    fmm::SchedH s_pts;     // blocks in proportion to the points
+    fmm::SchedH s_rsscan;  // radix digit-count scans (groups of digits per block)
+    fmm::SchedH s_p2m;     // the leaves, 4 per block
+    fmm::SchedH s_m2l, s_p2p;
+    fmm::SchedH* s_split = nullptr;  // [Lmax] boxes of level l, 128 per block (levels l < L)
+    fmm::SchedH* s_m2m = nullptr;    // [Lmax] boxes of level l, 4 per block (l < L)
+    fmm::SchedH* s_l2l = nullptr;    // [Lmax] children of level l, 4 per block (l < L)
+    fmm::SchedH* s_lists = nullptr;  // [Lmax + 1] candidate tiles of level l (l <= L)
     bool built = false;
 };
 
@@ -205,11 +255,17 @@ struct fmm_lists_s {
 
 namespace fmm {
 
+// sched.cu: build / free schedules.  blocks[i] = blocks of instance i (0 = none).
+int sched_make(fmm_tree t, const int64_t* blocks, SchedH& out);
+void sched_free(SchedH& h);
+int sched_all(fmm_tree t);          // every schedule that depends on the instances only
+int sched_tuned(fmm_tree t);        // the M2L and near-field schedules (depend on the tuning)
+void sched_free_all(fmm_tree t);
+
 // tree.cu
 int tree_alloc(fmm_tree t, int n_inst, const int64_t* n, const int* levels);
 void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls);
 void forest_totals(fmm_tree t);
-int blocks_for(int64_t n, int threads, int n_inst);
 int tree_tables_host(int64_t n, int L, int32_t* ones_before, int32_t* node_off, int32_t* leaf_begin);
 int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s);
 

@@ -160,6 +160,13 @@ __device__ __forceinline__ void atomic_add_ff(float* hi, float* lo, float vhi, f
     atomicAdd(lo, ((old - (s - bb)) + (vhi - bb)) + vlo);
 }
 
+__device__ __forceinline__ float lg2_fast(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <typename T>
 struct Pk;  // packed point
 template <>
@@ -173,12 +180,13 @@ struct alignas(16) Pk<float> {
 
 // ---- strengths into canonical order, packed with the coordinates ----
 template <typename T>
-__global__ void k_pack(const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+__global__ void k_pack(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                        const double* __restrict__ q, const double* __restrict__ xs,
                        const double* __restrict__ ys, const float* __restrict__ dxf,
                        const float* __restrict__ dyf, Pk<T>* __restrict__ pk, int32_t* status)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     perm += S.p0;
     q += S.p0;
     xs += S.p0;
@@ -188,8 +196,8 @@ __global__ void k_pack(const Inst* __restrict__ I, const int32_t* __restrict__ p
     pk += S.p0;
     const int64_t n = S.n;
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)z.nb * blockDim.x) {
         double v = q[perm[i]];
         bad |= !isfinite(v);
         Pk<T> p;
@@ -209,47 +217,49 @@ __global__ void k_pack(const Inst* __restrict__ I, const int32_t* __restrict__ p
 
 // ---- P2M: one warp per leaf, one lane per point; column sums through shared memory ----
 template <typename T>
-__global__ void k_p2m(const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ lb,
+__global__ void k_p2m(Sched sc, const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ lb,
                       const Pk<T>* __restrict__ pk, Geo<T> geo, cx<T>* __restrict__ Me)
 {
     extern __shared__ unsigned char smem[];
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     const int L = S.L;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    const int64_t b = (int64_t)blockIdx.x * wpb + w;
-    if (L < 1 || b >= level_size(L)) return;
+    if (L < 1) return;
     lb += S.lb0;
     pk += S.p0;
     geo = geo.shift(S.b0);
     Me += S.b0 * PS;
     cx<T>* Sm = (cx<T>*)smem + (size_t)w * 33 * P;
-    const int64_t g = level_base(L) + b;
-    const int32_t t0 = lb[b], t1 = lb[b + 1];
-    cx<T> acc[2] = {{0, 0}, {0, 0}};
-    for (int32_t tb = t0; tb < t1; tb += 32) {
-        const int32_t t = tb + lane;
-        T qq = 0;
-        cx<T> xi_c = {0, 0};
-        if (t < t1) {
-            const Pk<T> p = pk[t];
-            qq = p.q;
-            xi_c = geo.local(g, p.x, p.y);
+    for (int64_t b = (int64_t)z.rank * wpb + w; b < level_size(L); b += (int64_t)z.nb * wpb) {
+        const int64_t g = level_base(L) + b;
+        const int32_t t0 = lb[b], t1 = lb[b + 1];
+        cx<T> acc[2] = {{0, 0}, {0, 0}};
+        for (int32_t tb = t0; tb < t1; tb += 32) {
+            const int32_t t = tb + lane;
+            T qq = 0;
+            cx<T> xi_c = {0, 0};
+            if (t < t1) {
+                const Pk<T> p = pk[t];
+                qq = p.q;
+                xi_c = geo.local(g, p.x, p.y);
+            }
+            cx<T> pw = {qq, 0};
+            for (int k = 0; k < P; k++) {
+                Sm[k * 33 + lane] = pw;
+                pw = cmul(pw, xi_c);
+            }
+            __syncwarp();
+            for (int k = lane, s = 0; k < P; k += 32, s++) {
+                cx<T> sum = {0, 0};
+                for (int j = 0; j < 32; j++) sum = cadd(sum, Sm[k * 33 + j]);
+                acc[s] = cadd(acc[s], sum);
+            }
+            __syncwarp();
         }
-        cx<T> pw = {qq, 0};
-        for (int k = 0; k < P; k++) {
-            Sm[k * 33 + lane] = pw;
-            pw = cmul(pw, xi_c);
-        }
-        __syncwarp();
-        for (int k = lane, s = 0; k < P; k += 32, s++) {
-            cx<T> sum = {0, 0};
-            for (int j = 0; j < 32; j++) sum = cadd(sum, Sm[k * 33 + j]);
-            acc[s] = cadd(acc[s], sum);
-        }
-        __syncwarp();
+        for (int k = lane, s = 0; k < P; k += 32, s++)
+            Me[g * PS + k] = k == 0 ? acc[s] : cscale(acc[s], (T)-1 / (T)k);
     }
-    for (int k = lane, s = 0; k < P; k += 32, s++)
-        Me[g * PS + k] = k == 0 ? acc[s] : cscale(acc[s], (T)-1 / (T)k);
 }
 
 // Binomial table C(n, k), n, k < P, copied to shared memory by the whole block.
@@ -262,10 +272,11 @@ __device__ __forceinline__ void load_binom(T* B, int P)
 
 // ---- M2M: one warp per parent, one lane per output coefficient ----
 template <typename T>
-__global__ void k_m2m(const Inst* __restrict__ I, int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Me)
+__global__ void k_m2m(Sched sc, const Inst* __restrict__ I, int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Me)
 {
     extern __shared__ unsigned char smem[];
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     if (l + 1 > S.L) return;
     geo = geo.shift(S.b0);
     Me += S.b0 * PS;
@@ -273,35 +284,35 @@ __global__ void k_m2m(const Inst* __restrict__ I, int l, int P, int PS, Geo<T> g
     T* B = (T*)smem;
     cx<T>* D = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
     load_binom(B, P);
-    const int64_t b = (int64_t)blockIdx.x * wpb + w;
-    if (b >= level_size(l)) return;
-    const int64_t g = level_base(l) + b;
-    const T rp = geo.radius(g);
-    cx<T> acc[2] = {{0, 0}, {0, 0}};
-    for (int k = 0; k < 4; k++) {
-        const int64_t cg = level_base(l + 1) + 4 * b + k;
-        cx<T> wv = {0, 0};
-        T s = 0;
-        if (rp > 0) {
-            const T ir = (T)1 / rp;
-            wv = cscale(geo.diff(cg, g), ir);
-            s = geo.radius(cg) * ir;
-        }
-        for (int j = lane; j < P; j += 32) D[j] = cscale(Me[cg * PS + j], ipow(s, j));
-        __syncwarp();
-        for (int o = lane, si = 0; o < P; o += 32, si++) {
-            cx<T> h;
-            if (o == 0) {
-                h = D[0];
-            } else {
-                h = cscale(D[0], (T)-1 / (T)o);
-                for (int j = 1; j <= o; j++) h = cfma(h, wv, cscale(D[j], B[(o - 1) * P + (j - 1)]));
+    for (int64_t b = (int64_t)z.rank * wpb + w; b < level_size(l); b += (int64_t)z.nb * wpb) {
+        const int64_t g = level_base(l) + b;
+        const T rp = geo.radius(g);
+        cx<T> acc[2] = {{0, 0}, {0, 0}};
+        for (int k = 0; k < 4; k++) {
+            const int64_t cg = level_base(l + 1) + 4 * b + k;
+            cx<T> wv = {0, 0};
+            T s = 0;
+            if (rp > 0) {
+                const T ir = (T)1 / rp;
+                wv = cscale(geo.diff(cg, g), ir);
+                s = geo.radius(cg) * ir;
             }
-            acc[si] = cadd(acc[si], h);
+            for (int j = lane; j < P; j += 32) D[j] = cscale(Me[cg * PS + j], ipow(s, j));
+            __syncwarp();
+            for (int o = lane, si = 0; o < P; o += 32, si++) {
+                cx<T> h;
+                if (o == 0) {
+                    h = D[0];
+                } else {
+                    h = cscale(D[0], (T)-1 / (T)o);
+                    for (int j = 1; j <= o; j++) h = cfma(h, wv, cscale(D[j], B[(o - 1) * P + (j - 1)]));
+                }
+                acc[si] = cadd(acc[si], h);
+            }
+            __syncwarp();
         }
-        __syncwarp();
+        for (int o = lane, si = 0; o < P; o += 32, si++) Me[g * PS + o] = acc[si];
     }
-    for (int o = lane, si = 0; o < P; o += 32, si++) Me[g * PS + o] = acc[si];
 }
 
 // ---- M2L over the flat weak-pair array of all levels ----
@@ -309,15 +320,16 @@ __global__ void k_m2m(const Inst* __restrict__ I, int l, int P, int PS, Geo<T> g
 // scaled source coefficients and the partial sums live in registers, the constant matrix is read
 // from the constant bank by the unrolled contraction.
 template <typename T, int PI>
-__global__ void __launch_bounds__(128) k_m2l_pairs(const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+__global__ void __launch_bounds__(128) k_m2l_pairs(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                    int P, int PS, const int32_t* __restrict__ woff,
                                                    const int32_t* __restrict__ widx,
                                                    const int32_t* __restrict__ wtgt, Geo<T> geo,
                                                    const cx<T>* __restrict__ Me, cx<T>* __restrict__ Le,
                                                    float* __restrict__ L0lo)
 {
-    const Inst S = I[blockIdx.y];
-    const LInst TL = LIs[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
     if (S.L < 1) return;
     woff += S.o0;
     widx += TL.w0;
@@ -330,8 +342,8 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(const Inst* __restrict__ I, c
     const int lane = threadIdx.x & 31;
     const int64_t e_begin = woff[1];
     const int64_t e_end = min((int64_t)woff[nbox], wcap);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
     for (int64_t wb = e_begin + warp * 32 * M2L_CH; wb < e_end; wb += nwarps * 32 * M2L_CH) {
         const int64_t e0 = wb + (int64_t)lane * M2L_CH;
         const int64_t e1 = min(e0 + M2L_CH, e_end);
@@ -437,7 +449,7 @@ __global__ void __launch_bounds__(128) k_m2l_pairs(const Inst* __restrict__ I, c
 
 // ---- M2L, binary64: same decomposition, runtime P, operands and partial sums in shared memory
 // (one thread's column of X and A; the binary64 pipe bounds this kernel) ----
-__global__ void __launch_bounds__(64) k_m2l_pairs_f64(const Inst* __restrict__ I,
+__global__ void __launch_bounds__(64) k_m2l_pairs_f64(Sched sc, const Inst* __restrict__ I,
                                                       const LInst* __restrict__ LIs, int P, int PS,
                                                       const int32_t* __restrict__ woff,
                                                       const int32_t* __restrict__ widx,
@@ -446,8 +458,9 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(const Inst* __restrict__ I
                                                       cx<double>* __restrict__ Le)
 {
     extern __shared__ unsigned char smem[];
-    const Inst S = I[blockIdx.y];
-    const LInst TL = LIs[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
     if (S.L < 1) return;
     woff += S.o0;
     widx += TL.w0;
@@ -461,8 +474,8 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(const Inst* __restrict__ I
     cx<double>* A = X + (size_t)P * nt;  // A[o * nt + tid]
     const int64_t e_begin = woff[1];
     const int64_t e_end = min((int64_t)woff[nbox], wcap);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
     for (int64_t wb = e_begin + warp * 32 * M2L_CH; wb < e_end; wb += nwarps * 32 * M2L_CH) {
         const int64_t e0 = wb + (int64_t)lane * M2L_CH;
         const int64_t e1 = min(e0 + M2L_CH, e_end);
@@ -530,11 +543,12 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(const Inst* __restrict__ I
 
 // ---- L2L: one warp per child box of level l+1 ----
 template <typename T>
-__global__ void k_l2l(const Inst* __restrict__ I, int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Le,
+__global__ void k_l2l(Sched sc, const Inst* __restrict__ I, int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Le,
                       float* __restrict__ L0lo)
 {
     extern __shared__ unsigned char smem[];
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     if (l + 1 > S.L) return;
     geo = geo.shift(S.b0);
     Le += S.b0 * PS;
@@ -543,40 +557,41 @@ __global__ void k_l2l(const Inst* __restrict__ I, int l, int P, int PS, Geo<T> g
     T* Bn = (T*)smem;
     cx<T>* B = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
     load_binom(Bn, P);
-    const int64_t c = (int64_t)blockIdx.x * wpb + w;
-    if (c >= level_size(l + 1)) return;
-    const int64_t cg = level_base(l + 1) + c, pg = level_base(l) + (c >> 2);
-    const T rp = geo.radius(pg);
-    cx<T> wv = {0, 0};
-    T s = 0;
-    if (rp > 0) {
-        const T ir = (T)1 / rp;
-        wv = cscale(geo.diff(cg, pg), ir);
-        s = geo.radius(cg) * ir;
-    }
-    for (int j = lane; j < P; j += 32) B[j] = Le[pg * PS + j];
-    __syncwarp();
-    for (int o = lane; o < P; o += 32) {
-        if constexpr (sizeof(T) == 4) {
-            if (o == 0) {
-                // child b_0 = parent b_0 + sum_{k >= 1} b_k w^k, added to the child's hi/lo pair
-                cx<T> h = {0, 0};
-                for (int k = P - 1; k >= 1; k--) h = cfma(h, wv, B[k]);
-                const cx<T> r = cmul(h, wv);
-                T hi = Le[cg * PS].re, lo = L0lo[cg] + L0lo[pg];
-                two_sum(hi, lo, B[0].re);
-                two_sum(hi, lo, r.re);
-                const T sum = hi + lo;
-                L0lo[cg] = lo - (sum - hi);
-                Le[cg * PS].re = sum;
-                Le[cg * PS].im += B[0].im + r.im;
-                continue;
-            }
+    for (int64_t c = (int64_t)z.rank * wpb + w; c < level_size(l + 1); c += (int64_t)z.nb * wpb) {
+        const int64_t cg = level_base(l + 1) + c, pg = level_base(l) + (c >> 2);
+        const T rp = geo.radius(pg);
+        cx<T> wv = {0, 0};
+        T s = 0;
+        if (rp > 0) {
+            const T ir = (T)1 / rp;
+            wv = cscale(geo.diff(cg, pg), ir);
+            s = geo.radius(cg) * ir;
         }
-        cx<T> h = cscale(B[P - 1], Bn[(P - 1) * P + o]);
-        for (int k = P - 2; k >= o; k--) h = cfma(h, wv, cscale(B[k], Bn[k * P + o]));
-        const cx<T> r = cscale(h, ipow(s, o));
-        Le[cg * PS + o] = cadd(Le[cg * PS + o], r);
+        for (int j = lane; j < P; j += 32) B[j] = Le[pg * PS + j];
+        __syncwarp();
+        for (int o = lane; o < P; o += 32) {
+            if constexpr (sizeof(T) == 4) {
+                if (o == 0) {
+                    // child b_0 = parent b_0 + sum_{k >= 1} b_k w^k, added to the child's hi/lo pair
+                    cx<T> h = {0, 0};
+                    for (int k = P - 1; k >= 1; k--) h = cfma(h, wv, B[k]);
+                    const cx<T> r = cmul(h, wv);
+                    T hi = Le[cg * PS].re, lo = L0lo[cg] + L0lo[pg];
+                    two_sum(hi, lo, B[0].re);
+                    two_sum(hi, lo, r.re);
+                    const T sum = hi + lo;
+                    L0lo[cg] = lo - (sum - hi);
+                    Le[cg * PS].re = sum;
+                    Le[cg * PS].im += B[0].im + r.im;
+                    continue;
+                }
+            }
+            cx<T> h = cscale(B[P - 1], Bn[(P - 1) * P + o]);
+            for (int k = P - 2; k >= o; k--) h = cfma(h, wv, cscale(B[k], Bn[k * P + o]));
+            const cx<T> r = cscale(h, ipow(s, o));
+            Le[cg * PS + o] = cadd(Le[cg * PS + o], r);
+        }
+        __syncwarp();  // B is rewritten by the next box
     }
 }
 
@@ -584,11 +599,12 @@ __global__ void k_l2l(const Inst* __restrict__ I, int l, int P, int PS, Geo<T> g
 // binary64 path: writes the binary64 accumulator.  binary32 path: writes the binary32 far field;
 // the near-field accumulators are combined with it at the end.
 template <typename T>
-__global__ void k_l2p(const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ cleaf,
+__global__ void k_l2p(Sched sc, const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ cleaf,
                       const Pk<T>* __restrict__ pk, Geo<T> geo, const cx<T>* __restrict__ Le,
                       const float* __restrict__ L0lo, T* __restrict__ far, float* __restrict__ farlo)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     const int L = S.L;
     const int64_t n = S.n;
     cleaf += S.p0;
@@ -600,8 +616,8 @@ __global__ void k_l2p(const Inst* __restrict__ I, int P, int PS, const int32_t* 
         L0lo += S.b0;
         farlo += S.p0;
     }
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)z.nb * blockDim.x) {
         const int64_t g = level_base(L) + cleaf[i];
         const Pk<T> p = pk[i];
         const cx<T> z = geo.local(g, p.x, p.y);
@@ -628,10 +644,11 @@ __global__ void k_l2p(const Inst* __restrict__ I, int P, int PS, const int32_t* 
 // binary32 path: coordinates are offsets from the leaf centres, the target is moved into the
 // source frame through the float-float centre difference once per leaf pair, and
 // q_j * log2(r^2) is summed in binary32 over one source leaf, then into a float-float lane
-// accumulator.  A binary32 offset carries an absolute error of 2^-24 of the leaf scale M, so a
-// pair closer than M/64 (which includes j = i and coincident points) is redone from the binary64
-// coordinates; every other term then has |error| < 2^-17 in log2 units.  binary64 path: absolute
-// coordinates, binary64 log.  Flushes add binary64 partial sums to the accumulator atomically.
+// accumulator.  A binary32 offset carries an absolute error of about 2^-25 of the leaf-pair scale
+// M, so a pair closer than M/256 (which includes j = i and coincident points) takes its squared
+// distance from the binary64 coordinates; every other term then has |error| < 2^-14 in log2
+// units.  binary64 path: absolute coordinates, binary64 log.  Flushes add binary64 partial sums
+// to the accumulator atomically.
 
 
 // Leaves of at most 32 points: groups of gs = pow2ceil(max leaf size) lanes, one lane per target;
@@ -640,7 +657,7 @@ __global__ void k_l2p(const Inst* __restrict__ I, int P, int PS, const int32_t* 
 // Accumulators: binary64 path acc64 (holds the far field already); binary32 path nhi/nlo, the
 // float-float near-field sums in log2 units (flushed with binary32 atomics).
 template <typename T>
-__global__ void __launch_bounds__(256) k_p2p_small(const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+__global__ void __launch_bounds__(256) k_p2p_small(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                    int gs, const int32_t* __restrict__ soff,
                                                    const int32_t* __restrict__ sidx,
                                                    const int32_t* __restrict__ stgt,
@@ -655,8 +672,9 @@ __global__ void __launch_bounds__(256) k_p2p_small(const Inst* __restrict__ I, c
                                                    float* __restrict__ nlo)
 {
     constexpr bool F32 = sizeof(T) == 4;
-    const Inst S = I[blockIdx.y];
-    const LInst TL = LIs[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
     const int L = S.L;
     if ((S.n + level_size(L) - 1) / level_size(L) > gs) return;  // left to k_p2p_large
     const int64_t scap = TL.scap;
@@ -677,8 +695,8 @@ __global__ void __launch_bounds__(256) k_p2p_small(const Inst* __restrict__ I, c
     const int64_t base = level_base(L);
     const int64_t e_begin = min((int64_t)soff[base], scap);
     const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
     for (int64_t e0 = e_begin + warp * P2P_CH; e0 < e_end; e0 += nwarps * P2P_CH) {
         const int64_t e1 = min(e0 + P2P_CH, e_end);
         int64_t cur = -1;
@@ -719,7 +737,7 @@ __global__ void __launch_bounds__(256) k_p2p_small(const Inst* __restrict__ I, c
                 const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
                 const float xt = tx - ox, yt = ty - oy;
                 const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
-                const float tau2 = (M * (1.f / 64.f)) * (M * (1.f / 64.f));
+                const float tau2 = (M * (1.f / 256.f)) * (M * (1.f / 256.f));
                 float part = 0.f;
 #pragma unroll 4
                 for (int j = 0; j < ns; j++) {
@@ -731,7 +749,8 @@ __global__ void __launch_bounds__(256) k_p2p_small(const Inst* __restrict__ I, c
                     } else {
                         const double ddx = xs[it] - xs[s0 + j], ddy = ys[it] - ys[s0 + j];
                         const double r2d = ddx * ddx + ddy * ddy;
-                        if (r2d > 0.0) part += sp.q * (float)log2(r2d);
+                        if (r2d >= 1e-36) part += sp.q * lg2_fast((float)r2d);
+                            else if (r2d > 0.0) part += sp.q * (float)log2(r2d);
                     }
                 }
                 two_sum(hi, lo, part);
@@ -757,15 +776,11 @@ __global__ void __launch_bounds__(256) k_p2p_small(const Inst* __restrict__ I, c
     }
 }
 
-__device__ __forceinline__ float lg2_fast(float x)
-{
-    float r;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
-// Exact-path sum of one target against one source leaf (binary32, pairs closer than sqrt(tau2)
-// redone in binary64; j = i and coincident points skipped).
+// Sum of one target against one source leaf when some pair is closer than sqrt(tau2): the binary32
+// offsets (rounded to about 2^-24 of the leaf-pair extent M) cannot resolve such a pair, so its
+// squared distance is taken from the binary64 coordinates; the logarithm stays binary32, whose
+// absolute error does not grow as r shrinks.  j = i and coincident points are skipped.
 __device__ __forceinline__ float p2p_exact(float xt, float yt, int32_t it, const Pk<float>* __restrict__ pk,
                                            int32_t s0, int32_t ns, float tau2, const double* __restrict__ xs,
                                            const double* __restrict__ ys)
@@ -781,7 +796,10 @@ __device__ __forceinline__ float p2p_exact(float xt, float yt, int32_t it, const
         } else {
             const double ddx = xs[it] - xs[s0 + j], ddy = ys[it] - ys[s0 + j];
             const double r2d = ddx * ddx + ddy * ddy;
-            if (r2d > 0.0) part += sp.q * (float)log2(r2d);
+            if (r2d >= 1e-36)
+                part += sp.q * lg2_fast((float)r2d);
+            else if (r2d > 0.0)  // below the binary32 normal range
+                part += sp.q * (float)log2(r2d);
         }
     }
     return part;
@@ -792,7 +810,7 @@ __device__ __forceinline__ float p2p_exact(float xt, float yt, int32_t it, const
 // once and every source load serves two pair evaluations.  The main loop has no branch: it keeps
 // the smallest r^2 it met and, for the rare lane whose minimum falls below the exactness threshold
 // (and for the leaf's pair with itself), the leaf pair is redone by the exact path.
-__global__ void __launch_bounds__(256) k_p2p_f32(const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+__global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                  const int32_t* __restrict__ soff,
                                                  const int32_t* __restrict__ sidx,
                                                  const int32_t* __restrict__ stgt,
@@ -805,8 +823,9 @@ __global__ void __launch_bounds__(256) k_p2p_f32(const Inst* __restrict__ I, con
                                                  const float* __restrict__ rad32,
                                                  float* __restrict__ nhi, float* __restrict__ nlo)
 {
-    const Inst S = I[blockIdx.y];
-    const LInst TL = LIs[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
     const int L = S.L;
     const int64_t scap = TL.scap;
     soff += S.o0;
@@ -830,8 +849,8 @@ __global__ void __launch_bounds__(256) k_p2p_f32(const Inst* __restrict__ I, con
     const int32_t base = (int32_t)level_base(L);
     const int64_t e_begin = min((int64_t)soff[base], scap);
     const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
     for (int64_t e0 = e_begin + warp * P2P_CH; e0 < e_end; e0 += nwarps * P2P_CH) {
         const int64_t e1 = min(e0 + P2P_CH, e_end);
         int32_t cur = -1, it0 = 0, it1 = 0;
@@ -860,7 +879,7 @@ __global__ void __launch_bounds__(256) k_p2p_f32(const Inst* __restrict__ I, con
             const float ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
             const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
             const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
-            const float tau2 = fmaxf((M * (1.f / 64.f)) * (M * (1.f / 64.f)), 1e-30f);
+            const float tau2 = fmaxf((M * (1.f / 256.f)) * (M * (1.f / 256.f)), 1e-30f);
             // logs are taken of r^2 / M^2, near 1 for most pairs, and log2(M^2) times the sources'
             // strength is added once per leaf pair: the running sums stay small, and so do their
             // rounding errors
@@ -919,7 +938,7 @@ __global__ void __launch_bounds__(256) k_p2p_f32(const Inst* __restrict__ I, con
 // Leaves of more than 32 points: one lane per target, 32 targets at a time, every source of the
 // pair; one flush per (pair, block of 32 targets).
 template <typename T>
-__global__ void __launch_bounds__(256) k_p2p_large(const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+__global__ void __launch_bounds__(256) k_p2p_large(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                    int small_leaf, const int32_t* __restrict__ soff,
                                                    const int32_t* __restrict__ sidx,
                                                    const int32_t* __restrict__ stgt,
@@ -934,8 +953,9 @@ __global__ void __launch_bounds__(256) k_p2p_large(const Inst* __restrict__ I, c
                                                    float* __restrict__ nlo)
 {
     constexpr bool F32 = sizeof(T) == 4;
-    const Inst S = I[blockIdx.y];
-    const LInst TL = LIs[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
     const int L = S.L;
     if ((S.n + level_size(L) - 1) / level_size(L) <= small_leaf) return;  // done by the leaf-pair kernel
     const int64_t scap = TL.scap;
@@ -956,8 +976,8 @@ __global__ void __launch_bounds__(256) k_p2p_large(const Inst* __restrict__ I, c
     const int64_t base = level_base(L);
     const int64_t e_begin = min((int64_t)soff[base], scap);
     const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
     for (int64_t e = e_begin + warp; e < e_end; e += nwarps) {
         const int64_t tl = stgt[e] - base, sl = sidx[e];
         const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0, s0 = lb[sl], ns = lb[sl + 1] - s0;
@@ -967,7 +987,7 @@ __global__ void __launch_bounds__(256) k_p2p_large(const Inst* __restrict__ I, c
             ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
             oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
             const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
-            tau2 = (M * (1.f / 64.f)) * (M * (1.f / 64.f));
+            tau2 = (M * (1.f / 256.f)) * (M * (1.f / 256.f));
         }
         for (int tc = 0; tc < nt; tc += 32) {
             const int32_t it = t0 + tc + lane;
@@ -988,7 +1008,8 @@ __global__ void __launch_bounds__(256) k_p2p_large(const Inst* __restrict__ I, c
                         } else {
                             const double ddx = xs[it] - xs[s0 + j], ddy = ys[it] - ys[s0 + j];
                             const double r2d = ddx * ddx + ddy * ddy;
-                            if (r2d > 0.0) part += sp.q * (float)log2(r2d);
+                            if (r2d >= 1e-36) part += sp.q * lg2_fast((float)r2d);
+                            else if (r2d > 0.0) part += sp.q * (float)log2(r2d);
                         }
                     }
                     two_sum(hi, lo, part);
@@ -1009,27 +1030,29 @@ __global__ void __launch_bounds__(256) k_p2p_large(const Inst* __restrict__ I, c
     }
 }
 
-__global__ void k_unpermute(const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+__global__ void k_unpermute(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                             const double* __restrict__ acc, double* __restrict__ phi)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     perm += S.p0;
     acc += S.p0;
     phi += S.p0;
     const int64_t n = S.n;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)z.nb * blockDim.x)
         phi[perm[i]] = acc[i];
 }
 
 // binary32 path: phi = far + (ln 2 / 2) * near, combined in binary32 (the mixed path targets
 // tolerances >= 1e-7), written in input order.
-__global__ void k_combine32(const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+__global__ void k_combine32(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                             const float* __restrict__ far, const float* __restrict__ farlo,
                             const float* __restrict__ nhi, const float* __restrict__ nlo,
                             double* __restrict__ phi)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     perm += S.p0;
     far += S.p0;
     farlo += S.p0;
@@ -1039,8 +1062,8 @@ __global__ void k_combine32(const Inst* __restrict__ I, const int32_t* __restric
     const int64_t n = S.n;
     const double scale = 0.34657359027997264;  // ln(2) / 2: near-field sums are of log2(r^2)
     // the two float-float sums are joined in binary64 (four additions per point)
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)z.nb * blockDim.x)
         phi[perm[i]] = ((double)far[i] + (double)farlo[i]) + scale * ((double)nhi[i] + (double)nlo[i]);
 }
 
@@ -1133,20 +1156,12 @@ int alloc_ws(fmm_tree t, int PS, bool f64)
     return 0;
 }
 
-// Blocks per instance of a launch over all instances: the single-instance count, shared out over
-// the instances (a tuned value from fmm_autotune replaces the default when set).
-int per_inst_blocks(int total, int n_inst, int tuned)
-{
-    if (tuned > 0) return tuned;
-    return std::max(1, total / std::max(1, n_inst));
-}
-
 template <int PI>
 int launch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<float> geo, const cx<float>* Me,
                cx<float>* Le, cudaStream_t s)
 {
-    const dim3 grid(per_inst_blocks(152 * 16, t->n_inst, t->tune_m2l_blocks), t->n_inst);
-    k_m2l_pairs<float, PI><<<grid, 128, 0, s>>>(t->dinst, li->dlinst, P, PS, li->woff, li->widx,
+    if (t->s_m2l.blocks == 0) return 0;
+    k_m2l_pairs<float, PI><<<t->s_m2l.blocks, 128, 0, s>>>(t->s_m2l.d, t->dinst, li->dlinst, P, PS, li->woff, li->widx,
                                                 li->wtgt, geo, Me, Le, t->Lf0lo); note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L");
     return 0;
@@ -1172,9 +1187,9 @@ int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<double> geo, const
     const int NT = 64;
     const size_t sm = (size_t)2 * P * NT * sizeof(cx<double>);
     FMM_CUDA(cudaFuncSetAttribute(k_m2l_pairs_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const dim3 grid(per_inst_blocks(152 * 16, t->n_inst, t->tune_m2l_blocks), t->n_inst);
-    k_m2l_pairs_f64<<<grid, NT, sm, s>>>(t->dinst, li->dlinst, P, PS, li->woff, li->widx, li->wtgt,
-                                         geo, Me, Le); note_launch();
+    if (t->s_m2l.blocks == 0) return 0;
+    k_m2l_pairs_f64<<<t->s_m2l.blocks, NT, sm, s>>>(t->s_m2l.d, t->dinst, li->dlinst, P, PS, li->woff, li->widx,
+                                                    li->wtgt, geo, Me, Le); note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L");
     return 0;
 }
@@ -1191,7 +1206,6 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     Pk<T>* pk = (Pk<T>*)(f64 ? t->pk64 : t->pk32);
     const Inst* I = t->dinst;
     const LInst* LI = li->dlinst;
-    const unsigned ni = (unsigned)t->n_inst;
     const int Lmax = t->Lmax;
     const int64_t n = t->n;
     // largest leaf of each instance (leaves are balanced); its largest and smallest value
@@ -1211,11 +1225,12 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     float* farlo = t->acc32 + n;
     float* nhi = t->acc32 + 2 * n;
     float* nlo = t->acc32 + 3 * n;
-    const dim3 gpts(blocks_for(t->max_n, 256, t->n_inst), ni);
+    const unsigned gpts = (unsigned)t->s_pts.blocks;
+    const Sched spts = t->s_pts.d;
 
     {
         StageScope scope(FMM_STAGE_GATHER, s);
-        k_pack<T><<<gpts, 256, 0, s>>>(I, t->perm, q, t->xs, t->ys, t->dxf, t->dyf, pk, t->status);
+        k_pack<T><<<gpts, 256, 0, s>>>(spts, I, t->perm, q, t->xs, t->ys, t->dxf, t->dyf, pk, t->status);
         note_launch();
         FMM_CUDA(cudaMemsetAsync(Le, 0, (size_t)t->nbox * PS * sizeof(cx<T>), s));
         if (!f64) FMM_CUDA(cudaMemsetAsync(t->Lf0lo, 0, 4 * (size_t)t->nbox, s));
@@ -1224,19 +1239,17 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     if (Lmax >= 1) {
         {
             StageScope scope(FMM_STAGE_P2M, s);
-            const int64_t nleaf = level_size(Lmax);
             const size_t sm = (size_t)WPB * 33 * P * sizeof(cx<T>);
             FMM_CUDA(cudaFuncSetAttribute(k_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_p2m<T><<<dim3((unsigned)((nleaf + WPB - 1) / WPB), ni), 32 * WPB, sm, s>>>(
-                I, P, PS, t->leaf_begin, pk, geo, Me); note_launch();
+            k_p2m<T><<<t->s_p2m.blocks, 32 * WPB, sm, s>>>(t->s_p2m.d, I, P, PS, t->leaf_begin, pk, geo, Me);
+            note_launch();
             FMM_LAUNCH_CHECK("evaluate: P2M");
         }
         {
             StageScope scope(FMM_STAGE_M2M, s);
             for (int l = Lmax - 1; l >= 1; l--) {
-                const int64_t nb = level_size(l);
-                k_m2m<T><<<dim3((unsigned)((nb + WPB - 1) / WPB), ni), 32 * WPB,
-                           bsm + WPB * P * sizeof(cx<T>), s>>>(I, l, P, PS, geo, Me); note_launch();
+                k_m2m<T><<<t->s_m2m[l].blocks, 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
+                    t->s_m2m[l].d, I, l, P, PS, geo, Me); note_launch();
             }
             FMM_LAUNCH_CHECK("evaluate: M2M");
         }
@@ -1248,9 +1261,8 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         {
             StageScope scope(FMM_STAGE_L2L, s);
             for (int l = 1; l < Lmax; l++) {
-                const int64_t nc = level_size(l + 1);
-                k_l2l<T><<<dim3((unsigned)((nc + WPB - 1) / WPB), ni), 32 * WPB,
-                           bsm + WPB * P * sizeof(cx<T>), s>>>(I, l, P, PS, geo, Le, t->Lf0lo); note_launch();
+                k_l2l<T><<<t->s_l2l[l].blocks, 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
+                    t->s_l2l[l].d, I, l, P, PS, geo, Le, t->Lf0lo); note_launch();
             }
             FMM_LAUNCH_CHECK("evaluate: L2L");
         }
@@ -1258,35 +1270,36 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     {
         StageScope scope(FMM_STAGE_LEAF, s);
         if (!f64) FMM_CUDA(cudaMemsetAsync(nhi, 0, 2 * 4 * (size_t)n, s));
-        k_l2p<T><<<gpts, 256, 0, s>>>(I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo, f64 ? (T*)t->acc : (T*)far32,
-                                      farlo);
+        k_l2p<T><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo,
+                                      f64 ? (T*)t->acc : (T*)far32, farlo);
         note_launch();
-        const dim3 gp2p(per_inst_blocks(152 * 8, t->n_inst, t->tune_p2p_blocks), ni);
+        const unsigned gp2p = (unsigned)t->s_p2p.blocks;
+        const Sched sp2p = t->s_p2p.d;
         // instances whose leaves hold at most SMALL_LEAF points take the leaf-pair kernel, the
         // others (if any) the general one; each kernel skips the instances of the other
         const int small_leaf = f64 ? 32 : 64;
         if (minleaf <= small_leaf) {
             if constexpr (sizeof(T) == 4) {
-                k_p2p_f32<<<gp2p, 256, 0, s>>>(I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk,
+                k_p2p_f32<<<gp2p, 256, 0, s>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk,
                                                t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
             } else {
                 int gs = 1;
                 while (gs < std::min<int64_t>(maxleaf, 32)) gs <<= 1;
-                k_p2p_small<T><<<gp2p, 256, 0, s>>>(I, LI, gs, li->soff, li->sidx, li->stgt,
+                k_p2p_small<T><<<gp2p, 256, 0, s>>>(sp2p, I, LI, gs, li->soff, li->sidx, li->stgt,
                                                     t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
                                                     t->cen_lo, t->rad32, t->acc, nhi, nlo);
             }
             note_launch();
         }
         if (maxleaf > small_leaf) {
-            k_p2p_large<T><<<gp2p, 256, 0, s>>>(I, LI, small_leaf, li->soff, li->sidx, li->stgt,
+            k_p2p_large<T><<<gp2p, 256, 0, s>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt,
                                                 t->leaf_begin, pk, t->xs, t->ys, t->cen_hi, t->cen_lo,
                                                 t->rad32, t->acc, nhi, nlo); note_launch();
         }
         if (f64)
-            k_unpermute<<<gpts, 256, 0, s>>>(I, t->perm, t->acc, phi);
+            k_unpermute<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->acc, phi);
         else
-            k_combine32<<<gpts, 256, 0, s>>>(I, t->perm, far32, farlo, nhi, nlo, phi);
+            k_combine32<<<gpts, 256, 0, s>>>(spts, I, t->perm, far32, farlo, nhi, nlo, phi);
         note_launch();
         FMM_LAUNCH_CHECK("evaluate: leaf evaluation");
     }
@@ -1334,19 +1347,17 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
         }
         return 0;
     };
-    const int ni = t->n_inst;
     const int ladder[] = {152, 152 * 2, 152 * 4, 152 * 8, 152 * 16, 152 * 32, 152 * 64};
     int rc = 0;
     t->tune_m2l_blocks = t->tune_p2p_blocks = 0;
+    if ((rc = sched_tuned(t))) return rc;
     for (int stage = 0; stage < 2 && !rc; stage++) {
         int& knob = stage == 0 ? t->tune_m2l_blocks : t->tune_p2p_blocks;
-        int best_v = 0, last = -1;
+        int best_v = 0;
         float best_ms = 1e30f;
-        for (int total : ladder) {
-            const int v = std::max(1, total / ni);
-            if (v == last) continue;
-            last = v;
+        for (int v : ladder) {
             knob = v;
+            if ((rc = sched_tuned(t))) break;
             float ms = 0.f;
             rc = time_one(ms);
             if (rc) break;
@@ -1359,8 +1370,10 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (!rc) rc = sched_tuned(t);
     if (rc) {
         t->tune_m2l_blocks = t->tune_p2p_blocks = 0;
+        sched_tuned(t);
         return rc;
     }
     if (m2l_blocks) *m2l_blocks = t->tune_m2l_blocks;

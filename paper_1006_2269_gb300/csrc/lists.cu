@@ -11,8 +11,9 @@
 // asynchronous.  Entries beyond the preallocated capacity are dropped and flagged in the status
 // word; later levels never read past the capacity.
 //
-// All instances of a forest are processed by the same launches (instance = blockIdx.y); each
-// instance has its own CSR arrays, capacities and scratch, found through the instance tables.
+// All instances of a forest are processed by the same launches (a schedule gives every block its
+// instance and its rank among that instance's blocks); each instance has its own CSR arrays,
+// capacities and scratch, found through the instance tables.
 #include <algorithm>
 #include <new>
 
@@ -96,7 +97,7 @@ __device__ __forceinline__ LView lview(const Inst& S, const LInst& T, int32_t* w
     const Inst *__restrict__ I, const LInst *__restrict__ LIs, int32_t *woff, int32_t *soff,     \
         int32_t *widx, int32_t *wtgt, int32_t *sidx, int32_t *stgt, uint8_t *flags,               \
         uint32_t *tilecnt
-#define LIST_VIEW() lview(I[blockIdx.y], LIs[blockIdx.y], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt)
+#define LIST_VIEW(i) lview(I[i], LIs[i], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt)
 
 __global__ void k_lists_root(LIST_ARGS, int n_inst)
 {
@@ -188,16 +189,17 @@ __device__ __forceinline__ void decode(const TileParents& tp, const int32_t* __r
     first = (r == 0);
 }
 
-// grid (blocks, instances)
-__global__ void __launch_bounds__(LT) k_lists_flags(LIST_ARGS, int l, const double* __restrict__ cen,
+// schedule: candidate tiles of level l
+__global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, int l, const double* __restrict__ cen,
                                                     const double* __restrict__ rad,
                                                     const float* __restrict__ chi,
                                                     const float* __restrict__ clo,
                                                     const float* __restrict__ rad32, double theta)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     if (l > S.L) return;
-    const LView v = LIST_VIEW();
+    const LView v = LIST_VIEW(z.i);
     cen += 2 * S.b0;
     rad += S.b0;
     chi += 2 * S.b0;
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(LT) k_lists_flags(LIST_ARGS, int l, const doub
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
     const int64_t base = level_base(l);
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint32_t cnt = 0;
         for (int j = 0; j < LI; j++) {
@@ -238,12 +240,12 @@ __global__ void __launch_bounds__(LT) k_lists_flags(LIST_ARGS, int l, const doub
 }
 
 // Exclusive scan of the weak counts per tile; writes the level totals into the offsets.
-// grid (1, instances)
+// One block per instance.
 __global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, int l)
 {
-    const Inst S = I[blockIdx.y];
+    const Inst S = I[blockIdx.x];
     if (l > S.L) return;
-    const LView v = LIST_VIEW();
+    const LView v = LIST_VIEW(blockIdx.x);
     __shared__ int64_t wt[32];
     const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
@@ -285,12 +287,13 @@ __global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, int l)
 
 // Scatter the candidates into the weak and strong lists and write the box offsets.  The tile
 // prefix of weak flags is tilecnt[tile]; the strong prefix is its complement.
-// grid (blocks, instances)
-__global__ void __launch_bounds__(LT) k_lists_fill(LIST_ARGS, int l)
+// schedule: candidate tiles of level l
+__global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, int l)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     if (l > S.L) return;
-    const LView v = LIST_VIEW();
+    const LView v = LIST_VIEW(z.i);
     __shared__ uint32_t wsum[LI][LT / 32];
     __shared__ TileParents tp;
     const LevelCands lc = level_cands(v.soff, l, v.scap);
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(LT) k_lists_fill(LIST_ARGS, int l)
     const int64_t W0 = v.woff[base], S0 = v.soff[base];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint8_t f[LI];
         uint32_t pre[LI];
@@ -412,15 +415,18 @@ int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int
 int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s)
 {
     const int L = t->Lmax, ni = t->n_inst;
-    const int gx = std::max(1, (152 * 8) / ni);
     StageScope scope(FMM_STAGE_LISTS, s);
 #define LARGS t->dinst, li->dlinst, li->woff, li->soff, li->widx, li->wtgt, li->sidx, li->stgt, li->flags, li->tilecnt
     k_lists_root<<<1, 256, 0, s>>>(LARGS, ni); note_launch();
     for (int l = 1; l <= L; l++) {
-        k_lists_flags<<<dim3(gx, ni), LT, 0, s>>>(LARGS, l, t->centers, t->radii, t->cen_hi, t->cen_lo,
-                                                  t->rad32, theta); note_launch();
-        k_lists_scan<<<dim3(1, ni), 1024, 0, s>>>(LARGS, l); note_launch();
-        k_lists_fill<<<dim3(gx, ni), LT, 0, s>>>(LARGS, l); note_launch();
+        // a single instance keeps the fixed grid of the grid-stride loops (its candidate count
+        // is only known on the device); a forest shares blocks in proportion to 4^l
+        const SchedH& sh = t->s_lists[l];
+        const unsigned g = ni == 1 ? 152 * 8 : (unsigned)sh.blocks;
+        k_lists_flags<<<g, LT, 0, s>>>(sh.d, LARGS, l, t->centers, t->radii, t->cen_hi, t->cen_lo,
+                                       t->rad32, theta); note_launch();
+        k_lists_scan<<<ni, 1024, 0, s>>>(LARGS, l); note_launch();
+        k_lists_fill<<<g, LT, 0, s>>>(sh.d, LARGS, l); note_launch();
         FMM_LAUNCH_CHECK("lists");
     }
     k_lists_check<<<1, 256, 0, s>>>(LARGS, ni, li->status); note_launch();

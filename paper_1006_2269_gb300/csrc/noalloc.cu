@@ -182,6 +182,12 @@ extern "C" int fmm_build_tree_noalloc(const double* x, const double* y, int64_t 
     t.hinst = &hs;
     t.own_hinst = false;
     forest_totals(&t);
+    // a single instance needs no schedule tables (only small host arrays of grid sizes)
+    rc = sched_all(&t);
+    if (rc) {
+        sched_free_all(&t);
+        return rc;
+    }
     const Layout& Lo = kLayout;
     t.dinst = (Inst*)(base + Lo.inst);
     t.keys = (uint64_t*)(base + Lo.keys);
@@ -217,6 +223,7 @@ extern "C" int fmm_build_tree_noalloc(const double* x, const double* y, int64_t 
     note_launch();
     FMM_LAUNCH_CHECK("fmm_build_tree_noalloc: tables");
     rc = tree_build(&t, x, y, s);
+    sched_free_all(&t);
     if (rc) return rc;
     if (status) FMM_CUDA(cudaMemcpyAsync(status, t.status, 4, cudaMemcpyDeviceToDevice, s));
     return FMM_OK;

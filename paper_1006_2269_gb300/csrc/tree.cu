@@ -13,8 +13,9 @@
 // plus a per-segment correction from a table.
 //
 // A tree handle may hold many independent instances (a forest); every kernel covers all of them
-// in one launch: the instance is a block index, and the kernel offsets its pointers by the
-// instance's entry of the instance table, so the bodies below index one point set.
+// in one launch: a schedule tells each block its instance (and its rank among that instance's
+// blocks), and the kernel offsets its pointers by the instance's entry of the instance table, so
+// the bodies below index one point set.
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -92,21 +93,21 @@ __global__ void k_bbox_init(int n_inst, uint64_t* bbox)
     }
 }
 
-// grid (blocks, instances)
-__global__ void k_make_keys(const Inst* __restrict__ I, const double* __restrict__ x,
+// schedule: points
+__global__ void k_make_keys(Sched sc, const Inst* __restrict__ I, const double* __restrict__ x,
                             const double* __restrict__ y, int64_t ntot, uint64_t* __restrict__ kx,
                             uint64_t* bbox, int32_t* status)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     x += S.p0;
     y += S.p0;
     uint64_t* ky = kx + 2 * ntot + S.p0;  // the y keys live 2 ntot further
     kx += S.p0;
-    bbox += 4 * blockIdx.y;
+    bbox += 4 * z.i;
     uint64_t mnx = ~0ull, mxx = 0, mny = ~0ull, mxy = 0;
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
         double a = x[i], b = y[i];
         bad |= !isfinite(a) || !isfinite(b);
         uint64_t ka = order_key(a), kb = order_key(b);
@@ -142,21 +143,22 @@ __global__ void k_root_rect(const Inst* __restrict__ I, int n_inst, const uint64
 }
 
 // ---- stable LSD radix sort (8-bit digits) ----------------------------------------------------
-// grid (tiles, sorts, instances).  Sort `srt` of an instance uses keys[srt * stride + p0 ...] and
-// counts [2][256][its tiles] at 2 * 256 * t0.
+// grid (tile schedule, sorts): one block per tile of an instance.  Sort `srt` of an instance uses
+// keys[srt * stride + p0 ...] and counts [2][256][its tiles] at 2 * 256 * t0.
 
 template <typename K>
-__global__ void __launch_bounds__(TPB) k_rs_hist(const Inst* __restrict__ I, const K* __restrict__ keys,
+__global__ void __launch_bounds__(TPB) k_rs_hist(Sched sc, const Inst* __restrict__ I, const K* __restrict__ keys,
                                                  int64_t stride, int shift, uint32_t* __restrict__ counts)
 {
-    const Inst S = I[blockIdx.z];
-    if (blockIdx.x >= S.ntiles) return;
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const int64_t tile = z.rank;
     __shared__ uint32_t h[BINS];
     keys += (int64_t)blockIdx.y * stride + S.p0;
     counts += 2 * BINS * S.t0 + (int64_t)blockIdx.y * BINS * S.ntiles;
     for (int i = threadIdx.x; i < BINS; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * TILE;
+    const int64_t base = tile * TILE;
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < ITEMS; j++) {
         int64_t i = base + (int64_t)j * TPB + threadIdx.x;
@@ -166,41 +168,69 @@ __global__ void __launch_bounds__(TPB) k_rs_hist(const Inst* __restrict__ I, con
         if (v && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < BINS; i += blockDim.x) counts[(int64_t)i * S.ntiles + blockIdx.x] = h[i];
+    for (int i = threadIdx.x; i < BINS; i += blockDim.x) counts[(int64_t)i * S.ntiles + tile] = h[i];
 }
 
-// grid (digits, sorts, instances): exclusive scan of one digit's per-tile counts, in place.
-__global__ void __launch_bounds__(1024) k_rs_scan(const Inst* __restrict__ I, uint32_t* counts,
+// grid (digit-group schedule, sorts): exclusive scans of the per-tile counts of every digit, in
+// place, and each digit's total.  A block takes G = rs_digits_per_block(ntiles) consecutive
+// digits of one instance: below 1024 tiles their counts (G x ntiles <= 1024 values) go through one
+// block-wide scan whose segments are the digits; from 1024 tiles on G = 1 and the digit is scanned
+// in chunks of 1024.
+__global__ void __launch_bounds__(1024) k_rs_scan(Sched sc, const Inst* __restrict__ I, uint32_t* counts,
                                                   uint32_t* totals)
 {
-    const Inst S = I[blockIdx.z];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     __shared__ uint32_t wt[32];
-    uint32_t* c = counts + 2 * BINS * S.t0 + ((int64_t)blockIdx.y * BINS + blockIdx.x) * S.ntiles;
-    uint32_t carry = 0;
-    for (int64_t b = 0; b < S.ntiles; b += blockDim.x) {
-        int64_t i = b + threadIdx.x;
-        uint32_t v = i < S.ntiles ? c[i] : 0;
-        uint32_t tot;
-        uint32_t e = block_excl_scan(v, wt, tot);
-        if (i < S.ntiles) c[i] = carry + e;
-        carry += tot;
+    __shared__ uint32_t ex[1024];
+    const int64_t nt = S.ntiles;
+    const int G = rs_digits_per_block(nt);
+    const int d0 = z.rank * G;
+    if (d0 >= BINS) return;
+    uint32_t* c = counts + 2 * BINS * S.t0 + (int64_t)blockIdx.y * BINS * nt + (int64_t)d0 * nt;
+    uint32_t* tot = totals + (2 * (int64_t)z.i + blockIdx.y) * BINS + d0;
+    if (nt >= 1024) {
+        uint32_t carry = 0;
+        for (int64_t b = 0; b < nt; b += blockDim.x) {
+            const int64_t i = b + threadIdx.x;
+            const uint32_t v = i < nt ? c[i] : 0;
+            uint32_t t;
+            const uint32_t e = block_excl_scan(v, wt, t);
+            if (i < nt) c[i] = carry + e;
+            carry += t;
+        }
+        if (threadIdx.x == 0) tot[0] = carry;
+        return;
     }
-    if (threadIdx.x == 0) totals[(2 * (int64_t)blockIdx.z + blockIdx.y) * BINS + blockIdx.x] = carry;
+    const int nd = min(G, BINS - d0);
+    const int64_t len = (int64_t)nd * nt;
+    const int k = threadIdx.x;
+    const uint32_t v = k < len ? c[k] : 0;
+    uint32_t t;
+    const uint32_t e = block_excl_scan(v, wt, t);
+    ex[k] = e;
+    __syncthreads();
+    if (k < len) {
+        const int k0 = k - (int)(k % nt);
+        c[k] = e - ex[k0];
+        if (k % nt == nt - 1) tot[k / nt] = e + v - ex[k0];
+    }
 }
 
 // Stable scatter.  Each warp owns WCHUNK consecutive items and walks them in order, ranking
 // equal digits with match_any; warps are then ordered by a per-digit scan, tiles by k_rs_scan,
 // digits by the scan of the totals.  With FIRST the values are the item indices.
 template <typename K, bool FIRST>
-__global__ void __launch_bounds__(TPB) k_rs_scatter(const Inst* __restrict__ I, const K* __restrict__ kin,
+__global__ void __launch_bounds__(TPB) k_rs_scatter(Sched sc, const Inst* __restrict__ I, const K* __restrict__ kin,
                                                     const int32_t* __restrict__ vin,
                                                     K* __restrict__ kout, int32_t* __restrict__ vout,
                                                     int64_t stride, int shift,
                                                     const uint32_t* __restrict__ counts,
                                                     const uint32_t* __restrict__ totals)
 {
-    const Inst S = I[blockIdx.z];
-    if (blockIdx.x >= S.ntiles) return;
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const int64_t tile = z.rank;
     __shared__ uint32_t dbase[BINS];
     __shared__ uint32_t wcnt[WARPS][BINS];
     __shared__ uint32_t wt[32];
@@ -210,7 +240,7 @@ __global__ void __launch_bounds__(TPB) k_rs_scatter(const Inst* __restrict__ I, 
     vout += so;
     if (!FIRST) vin += so;
     counts += 2 * BINS * S.t0 + (int64_t)blockIdx.y * BINS * S.ntiles;
-    totals += (2 * (int64_t)blockIdx.z + blockIdx.y) * BINS;
+    totals += (2 * (int64_t)z.i + blockIdx.y) * BINS;
     const int64_t n = S.n, ntiles = S.ntiles;
     {
         uint32_t tot;
@@ -221,7 +251,7 @@ __global__ void __launch_bounds__(TPB) k_rs_scatter(const Inst* __restrict__ I, 
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)w * WCHUNK;
+    const int64_t base = tile * TILE + (int64_t)w * WCHUNK;
     K k[ITEMS];
     int32_t val[ITEMS];
     uint32_t r[ITEMS];
@@ -254,7 +284,7 @@ __global__ void __launch_bounds__(TPB) k_rs_scatter(const Inst* __restrict__ I, 
         int64_t i = base + j * 32 + lane;
         if (i < n) {
             uint32_t d = (uint32_t)((k[j] >> shift) & (BINS - 1));
-            int64_t pos = (int64_t)dbase[d] + counts[(int64_t)d * ntiles + blockIdx.x] + wcnt[w][d] + r[j];
+            int64_t pos = (int64_t)dbase[d] + counts[(int64_t)d * ntiles + tile] + wcnt[w][d] + r[j];
             kout[pos] = k[j];
             vout[pos] = val[j];
         }
@@ -269,19 +299,21 @@ int radix_sort(fmm_tree t, K* keys, int32_t* vals, int64_t stride, int nsorts, i
 {
     int cur = 0;
     const int64_t ntot = t->n;
-    dim3 grid((unsigned)t->max_tiles, (unsigned)nsorts, (unsigned)t->n_inst);
+    const dim3 grid((unsigned)t->s_tiles.blocks, (unsigned)nsorts);
+    const dim3 gscan((unsigned)t->s_rsscan.blocks, (unsigned)nsorts);
+    const Sched st = t->s_tiles.d;
     for (int shift = 0; shift < bits; shift += 8) {
         K* kin = keys + (cur ? ntot : 0);
         K* kout = keys + (cur ? 0 : ntot);
         int32_t* vin = vals + (cur ? ntot : 0);
         int32_t* vout = vals + (cur ? 0 : ntot);
-        k_rs_hist<K><<<grid, TPB, 0, s>>>(t->dinst, kin, stride, shift, t->rs_counts); note_launch();
-        k_rs_scan<<<dim3(BINS, nsorts, t->n_inst), 1024, 0, s>>>(t->dinst, t->rs_counts, t->rs_totals); note_launch();
+        k_rs_hist<K><<<grid, TPB, 0, s>>>(st, t->dinst, kin, stride, shift, t->rs_counts); note_launch();
+        k_rs_scan<<<gscan, 1024, 0, s>>>(t->s_rsscan.d, t->dinst, t->rs_counts, t->rs_totals); note_launch();
         if (shift == 0)
-            k_rs_scatter<K, true><<<grid, TPB, 0, s>>>(t->dinst, kin, nullptr, kout, vout, stride, shift,
+            k_rs_scatter<K, true><<<grid, TPB, 0, s>>>(st, t->dinst, kin, nullptr, kout, vout, stride, shift,
                                                        t->rs_counts, t->rs_totals);
         else
-            k_rs_scatter<K, false><<<grid, TPB, 0, s>>>(t->dinst, kin, vin, kout, vout, stride, shift,
+            k_rs_scatter<K, false><<<grid, TPB, 0, s>>>(st, t->dinst, kin, vin, kout, vout, stride, shift,
                                                         t->rs_counts, t->rs_totals);
         note_launch();
         cur ^= 1;
@@ -291,18 +323,19 @@ int radix_sort(fmm_tree t, K* keys, int32_t* vals, int64_t stride, int nsorts, i
 
 // ---- stable partitions inside segments ---------------------------------------------------------
 
-// grid (tiles, instances)
-__global__ void __launch_bounds__(TPB) k_part_count(const Inst* __restrict__ I, int l,
+// tile schedule
+__global__ void __launch_bounds__(TPB) k_part_count(Sched sc, const Inst* __restrict__ I, int l,
                                                     const int32_t* __restrict__ in,
                                                     const uint8_t* __restrict__ flag,
                                                     uint32_t* __restrict__ tilecnt)
 {
-    const Inst S = I[blockIdx.y];
-    if (l >= S.L || blockIdx.x >= S.ntiles) return;
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    if (l >= S.L) return;
     in += S.p0;
     flag += S.p0;
     __shared__ uint32_t wt[32];
-    const int64_t base = (int64_t)blockIdx.x * TILE;
+    const int64_t base = (int64_t)z.rank * TILE;
     uint32_t c = 0;
     for (int j = 0; j < ITEMS; j++) {
         int64_t i = base + (int64_t)j * TPB + threadIdx.x;
@@ -310,13 +343,13 @@ __global__ void __launch_bounds__(TPB) k_part_count(const Inst* __restrict__ I, 
     }
     uint32_t tot;
     block_excl_scan(c, wt, tot);
-    if (threadIdx.x == 0) tilecnt[S.t0 + blockIdx.x] = tot;
+    if (threadIdx.x == 0) tilecnt[S.t0 + z.rank] = tot;
 }
 
-// grid (1, instances)
+// one block per instance
 __global__ void __launch_bounds__(1024) k_scan_tiles(const Inst* __restrict__ I, int l, uint32_t* a)
 {
-    const Inst S = I[blockIdx.y];
+    const Inst S = I[blockIdx.x];
     if (l >= S.L) return;
     a += S.t0;
     __shared__ uint32_t wt[32];
@@ -343,8 +376,8 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const Inst* __restrict__ I,
 // counts the ones of all segments before segment j at that depth, tileoff[] is the exclusive scan
 // of the ones per tile.  An instance with fewer than l + 1 levels is finished: its items are
 // copied through unchanged so that the next level finds them in the output buffer.
-// grid (tiles, instances).
-__global__ void __launch_bounds__(TPB) k_part_scatter(const Inst* __restrict__ I, int l, int xmode,
+// tile schedule
+__global__ void __launch_bounds__(TPB) k_part_scatter(Sched sc, const Inst* __restrict__ I, int l, int xmode,
                                                       const int32_t* __restrict__ in,
                                                       const int32_t* __restrict__ in_seg,
                                                       int32_t* __restrict__ out,
@@ -356,8 +389,9 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(const Inst* __restrict__ I
                                                       const uint32_t* __restrict__ tileoff,
                                                       int32_t* status)
 {
-    const Inst S = I[blockIdx.y];
-    if (blockIdx.x >= S.ntiles) return;
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const int32_t tile = z.rank;
     in += S.p0;
     in_seg += S.p0;
     out += S.p0;
@@ -365,7 +399,7 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(const Inst* __restrict__ I
     const int32_t n = (int32_t)S.n;
     if (l >= S.L) {
         for (int j = 0; j < ITEMS; j++) {
-            const int32_t i = (int32_t)blockIdx.x * TILE + j * TPB + threadIdx.x;
+            const int32_t i = tile * TILE + j * TPB + threadIdx.x;
             if (i < n) {
                 out[i] = in[i];
                 out_seg[i] = in_seg[i];
@@ -378,7 +412,7 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(const Inst* __restrict__ I
     __shared__ uint32_t wtot[WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    const int32_t base = (int32_t)blockIdx.x * TILE + w * WCHUNK;
+    const int32_t base = tile * TILE + w * WCHUNK;
     const int32_t* offD = node_off + S.no0 + node_offset_base(2 * l);
     const int32_t* ob = ones_before + S.ob0 + ones_before_offset(2 * l + xmode);
     int32_t id[ITEMS];
@@ -397,7 +431,7 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(const Inst* __restrict__ I
     }
     if (lane == 0) wtot[w] = run;
     __syncthreads();
-    uint32_t woff = tileoff[S.t0 + blockIdx.x];
+    uint32_t woff = tileoff[S.t0 + tile];
     for (int ww = 0; ww < w; ww++) woff += wtot[ww];
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
@@ -435,36 +469,25 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(const Inst* __restrict__ I
     }
 }
 
-// Level-0 x-split: the upper half of the x order has the bit set.  grid (blocks, instances)
-__global__ void k_init_hx(const Inst* __restrict__ I, const int32_t* __restrict__ X, uint8_t* __restrict__ hx)
+// Level-0 x-split: the upper half of the x order has the bit set.  schedule: points
+__global__ void k_init_hx(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ X, uint8_t* __restrict__ hx)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     X += S.p0;
     hx += S.p0;
     const int32_t n = (int32_t)S.n;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int32_t i = z.rank * blockDim.x + threadIdx.x; i < n; i += z.nb * blockDim.x)
         hx[X[i]] = (i >= (n >> 1)) ? 1 : 0;
 }
 
 __device__ __forceinline__ double midpoint(double a, double b) { return __dmul_rn(0.5, __dadd_rn(a, b)); }
 
-// Split coordinates of the boxes of level l and the rectangles of their children.  X is the
-// x-ordered list segmented by the boxes of level l, Yn the y-ordered list segmented by their
-// x-halves.  grid (blocks, instances)
-__global__ void k_split_rects(const Inst* __restrict__ I, int l, const int32_t* __restrict__ X,
-                              const int32_t* __restrict__ Yn, const double* __restrict__ x,
-                              const double* __restrict__ y, const int32_t* __restrict__ node_off,
-                              double* __restrict__ rects)
+__device__ __forceinline__ void split_one(int64_t b, int l, const int32_t* __restrict__ X,
+                                          const int32_t* __restrict__ Yn, const double* __restrict__ x,
+                                          const double* __restrict__ y, const int32_t* __restrict__ offD,
+                                          double* __restrict__ rects)
 {
-    const Inst S = I[blockIdx.y];
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= S.L || b >= level_size(l)) return;
-    X += S.p0;
-    Yn += S.p0;
-    x += S.p0;
-    y += S.p0;
-    rects += 4 * S.b0;
-    const int32_t* offD = node_off + S.no0 + node_offset_base(2 * l);
     const int64_t o = offD[b], m = offD[b + 1] - o;
     int64_t mx = m >> 1;
     double xs = midpoint(x[X[o + mx - 1]], x[X[o + mx]]);
@@ -484,16 +507,38 @@ __global__ void k_split_rects(const Inst* __restrict__ I, int l, const int32_t* 
     cr[12] = xs; cr[13] = px1; cr[14] = ys[1]; cr[15] = py1;
 }
 
-// After the last level every item of X carries its leaf.  grid (blocks, instances)
-__global__ void k_leaf_of(const Inst* __restrict__ I, const int32_t* __restrict__ X,
+// Split coordinates of the boxes of level l and the rectangles of their children.  X is the
+// x-ordered list segmented by the boxes of level l, Yn the y-ordered list segmented by their
+// x-halves.  schedule: boxes of level l, one thread each
+__global__ void k_split_rects(Sched sc, const Inst* __restrict__ I, int l, const int32_t* __restrict__ X,
+                              const int32_t* __restrict__ Yn, const double* __restrict__ x,
+                              const double* __restrict__ y, const int32_t* __restrict__ node_off,
+                              double* __restrict__ rects)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    if (l >= S.L) return;
+    X += S.p0;
+    Yn += S.p0;
+    x += S.p0;
+    y += S.p0;
+    rects += 4 * S.b0;
+    const int32_t* offD = node_off + S.no0 + node_offset_base(2 * l);
+    for (int64_t b = (int64_t)z.rank * blockDim.x + threadIdx.x; b < level_size(l); b += (int64_t)z.nb * blockDim.x)
+        split_one(b, l, X, Yn, x, y, offD, rects);
+}
+
+// After the last level every item of X carries its leaf.  schedule: points
+__global__ void k_leaf_of(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ X,
                           const int32_t* __restrict__ XS, uint32_t* __restrict__ leaf_of)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     X += S.p0;
     XS += S.p0;
     leaf_of += S.p0;
     const int32_t n = (int32_t)S.n;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int32_t i = z.rank * blockDim.x + threadIdx.x; i < n; i += z.nb * blockDim.x)
         leaf_of[X[i]] = (uint32_t)XS[i];
 }
 
@@ -522,15 +567,16 @@ __global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, doubl
 }
 
 // Coordinates in canonical order, and their binary32 offsets from the leaf centre.
-// grid (blocks, instances)
-__global__ void k_gather_points(const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+// schedule: points
+__global__ void k_gather_points(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                                 const uint32_t* __restrict__ leaf_of, const double* __restrict__ x,
                                 const double* __restrict__ y, const double* __restrict__ cen,
                                 double* __restrict__ xs, double* __restrict__ ys,
                                 float* __restrict__ dxf, float* __restrict__ dyf,
                                 int32_t* __restrict__ cleaf)
 {
-    const Inst S = I[blockIdx.y];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
     perm += S.p0;
     leaf_of += S.p0;
     x += S.p0;
@@ -541,8 +587,7 @@ __global__ void k_gather_points(const Inst* __restrict__ I, const int32_t* __res
     dyf += S.p0;
     cleaf += S.p0;
     cen += 2 * S.b0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
         int32_t id = perm[i];
         cleaf[i] = (int32_t)leaf_of[id];
         int64_t g = level_base(S.L) + leaf_of[id];
@@ -555,13 +600,6 @@ __global__ void k_gather_points(const Inst* __restrict__ I, const int32_t* __res
 }
 
 }  // namespace
-
-int blocks_for(int64_t n, int threads, int n_inst)
-{
-    int64_t g = (n + threads - 1) / threads;
-    int64_t cap = std::max<int64_t>(1, (152 * 32) / std::max(1, n_inst));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
-}
 
 // Host tables of one instance (sizes depend on (n, L) only): ones-before tables for depths
 // 0 .. 2L-1, node offsets for depths 0 .. 2L, leaf offsets.  Any pointer may be null.
@@ -698,7 +736,7 @@ int tree_alloc(fmm_tree t, int n_inst, const int64_t* ns, const int* Ls)
     FMM_CUDA(cudaMemcpy(t->ones_before, ob_all.data(), 4 * ob_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemcpy(t->node_off, off_all.data(), 4 * off_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemset(t->status, 0, 4));
-    return 0;
+    return sched_all(t);
 }
 
 int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
@@ -706,19 +744,19 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
     const int64_t n = t->n;  // total points of the forest
     const int ni = t->n_inst;
     const int L = t->Lmax;
-    const unsigned mt = (unsigned)t->max_tiles;
+    const unsigned gt = (unsigned)t->s_tiles.blocks, gp = (unsigned)t->s_pts.blocks;
+    const Sched st = t->s_tiles.d, sp = t->s_pts.d;
     uint64_t* kx = t->keys;   // x sort: buffers [0, n) and [n, 2n); y sort: [2n, 4n)
     int32_t* vals = t->vals;  // x sort values [0, 2n); y sort values [2n, 4n)
     uint8_t* hx = t->hflag;
     uint8_t* hy = t->hflag + n;
     int32_t *X, *Xo, *Y, *Yo;
     int32_t* Xfinal_seg = nullptr;
-    const int pb = blocks_for(t->max_n, 256, ni);
 
     {
         StageScope scope(FMM_STAGE_TREE_SORT, s);
         k_bbox_init<<<1, 256, 0, s>>>(ni, t->bbox_keys); note_launch();
-        k_make_keys<<<dim3(pb, ni), 256, 0, s>>>(t->dinst, x, y, n, kx, t->bbox_keys, t->status); note_launch();
+        k_make_keys<<<gp, 256, 0, s>>>(sp, t->dinst, x, y, n, kx, t->bbox_keys, t->status); note_launch();
         k_root_rect<<<1, 256, 0, s>>>(t->dinst, ni, t->bbox_keys, t->rects); note_launch();
         FMM_LAUNCH_CHECK("tree: keys");
         // x order and y order of all points, ties by input index (two sorts in one launch sequence)
@@ -736,24 +774,23 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
         int32_t *XS = t->segs, *XSo = t->segs + n, *YS = t->segs + 2 * n, *YSo = t->segs + 3 * n;
         FMM_CUDA(cudaMemsetAsync(XS, 0, 4 * n, s));
         FMM_CUDA(cudaMemsetAsync(YS, 0, 4 * n, s));
-        k_init_hx<<<dim3(pb, ni), 256, 0, s>>>(t->dinst, X, hx); note_launch();
+        k_init_hx<<<gp, 256, 0, s>>>(sp, t->dinst, X, hx); note_launch();
         for (int l = 0; l < L; l++) {
             // Y: stable partition of each box by its x-half bit; records the y-half bit
-            k_part_count<<<dim3(mt, ni), TPB, 0, s>>>(t->dinst, l, Y, hx, t->tilecnt); note_launch();
-            k_scan_tiles<<<dim3(1, ni), 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
-            k_part_scatter<<<dim3(mt, ni), TPB, 0, s>>>(t->dinst, l, 0, Y, YS, Yo, YSo, hx, hy, t->node_off,
-                                                        t->ones_before, t->tilecnt, t->status); note_launch();
+            k_part_count<<<gt, TPB, 0, s>>>(st, t->dinst, l, Y, hx, t->tilecnt); note_launch();
+            k_scan_tiles<<<ni, 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
+            k_part_scatter<<<gt, TPB, 0, s>>>(st, t->dinst, l, 0, Y, YS, Yo, YSo, hx, hy, t->node_off,
+                                              t->ones_before, t->tilecnt, t->status); note_launch();
             std::swap(Y, Yo);
             std::swap(YS, YSo);
             // split coordinates and child rectangles of level l
-            const int64_t nb = level_size(l);
-            k_split_rects<<<dim3((unsigned)((nb + 127) / 128), ni), 128, 0, s>>>(t->dinst, l, X, Y, x, y,
-                                                                                 t->node_off, t->rects); note_launch();
+            k_split_rects<<<t->s_split[l].blocks, 128, 0, s>>>(t->s_split[l].d, t->dinst, l, X, Y, x, y,
+                                                                t->node_off, t->rects); note_launch();
             // X: stable partition of each x-half by the y-half bit; records the next x-half bit
-            k_part_count<<<dim3(mt, ni), TPB, 0, s>>>(t->dinst, l, X, hy, t->tilecnt); note_launch();
-            k_scan_tiles<<<dim3(1, ni), 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
-            k_part_scatter<<<dim3(mt, ni), TPB, 0, s>>>(t->dinst, l, 1, X, XS, Xo, XSo, hy, hx, t->node_off,
-                                                        t->ones_before, t->tilecnt, t->status); note_launch();
+            k_part_count<<<gt, TPB, 0, s>>>(st, t->dinst, l, X, hy, t->tilecnt); note_launch();
+            k_scan_tiles<<<ni, 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
+            k_part_scatter<<<gt, TPB, 0, s>>>(st, t->dinst, l, 1, X, XS, Xo, XSo, hy, hx, t->node_off,
+                                              t->ones_before, t->tilecnt, t->status); note_launch();
             std::swap(X, Xo);
             std::swap(XS, XSo);
             FMM_LAUNCH_CHECK("tree: level split");
@@ -765,7 +802,7 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
         StageScope scope(FMM_STAGE_TREE_FINISH, s);
         // canonical order: stable sort of the input indices by leaf (inside a leaf: input order)
         uint32_t* leaf_of = (uint32_t*)t->leaf_of;
-        k_leaf_of<<<dim3(pb, ni), 256, 0, s>>>(t->dinst, X, Xfinal_seg, leaf_of); note_launch();
+        k_leaf_of<<<gp, 256, 0, s>>>(sp, t->dinst, X, Xfinal_seg, leaf_of); note_launch();
         uint32_t* k32 = (uint32_t*)t->keys;  // reuse the key buffers: [0, n) and [n, 2n)
         int32_t* v32 = t->vals + 2 * n;      // value buffers [2n, 4n)
         const int bits = std::max(8, 2 * L);  // with L = 0 all keys are 0: the order stays the input order
@@ -776,8 +813,8 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
         const int64_t nb = t->nbox;
         k_geometry<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(t->rects, nb, t->centers, t->radii,
                                                                 t->rad32, t->cen_hi, t->cen_lo); note_launch();
-        k_gather_points<<<dim3(pb, ni), 256, 0, s>>>(t->dinst, t->perm, leaf_of, x, y, t->centers,
-                                                     t->xs, t->ys, t->dxf, t->dyf, t->cleaf); note_launch();
+        k_gather_points<<<gp, 256, 0, s>>>(sp, t->dinst, t->perm, leaf_of, x, y, t->centers,
+                                           t->xs, t->ys, t->dxf, t->dyf, t->cleaf); note_launch();
         FMM_LAUNCH_CHECK("tree: canonical order");
     }
     t->built = true;
