@@ -27,17 +27,19 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fmm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "mlp_oracle.c")]
 _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``fmm_oracle.c`` into ``liboracle.so`` next to it (plain gcc, no GPU)."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+    """Compile ``fmm_oracle.c`` and ``mlp_oracle.c`` into ``liboracle.so`` next to them (plain
+    gcc, no GPU)."""
+    if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(f) for f in _SRCS):
         return _SO
     base = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fcx-fortran-rules",
-            "-fno-fast-math", "-o", _SO + ".tmp", _SRC, "-lm"]
+            "-fno-fast-math", "-o", _SO + ".tmp", *_SRCS, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -81,6 +83,14 @@ def _load():
         lib.orc_direct.argtypes = [i64, vp, vp, vp, i64, vp, vp, i32]
         lib.orc_fmm.restype = i32
         lib.orc_fmm.argtypes = [i64, vp, vp, vp, i32, i32, dbl, vp, vp, vp]
+        lib.orc_mlp_nparams.restype = ctypes.c_long
+        lib.orc_mlp_nparams.argtypes = []
+        lib.orc_mlp_forward.restype = None
+        lib.orc_mlp_forward.argtypes = [vp, vp, i32, vp]
+        lib.orc_mlp_loss_grad.restype = dbl
+        lib.orc_mlp_loss_grad.argtypes = [vp, vp, vp, i32, vp]
+        lib.orc_features.restype = None
+        lib.orc_features.argtypes = [vp, i32, i64, dbl, vp]
         _lib = lib
         return lib
 
