@@ -227,6 +227,68 @@ int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
                  void* stream, int* m2l_blocks_host, int* p2p_blocks_host);
 int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks);
 
+/* ---------------------------------------------------------------------------------------------
+ * Parameter selector (no paper counterpart).  The paper picks the parameters by rule: p from the
+ * tolerance through the error estimate of Section 3 (p ~ log TOL / log theta) and about 20 points
+ * per leaf (end of Section 4).  The selector instead predicts the (levels, p) that meets a
+ * tolerance fastest, with a small network trained on runs of the method itself:
+ *
+ *   features (64 binary32 per instance, fmm_selector_features): for levels l = 1..15 of a built
+ *     tree, four statistics over the boxes of level l -- mean of log2(long side / root long side),
+ *     standard deviation of log2(long side), mean and max of log2(long / short side) -- at
+ *     [4(l-1) .. 4(l-1)+3] (zeros for missing levels); [60] log10 N, [61] log10 tol,
+ *     [62] levels / 16, [63] 0.
+ *   network: 64 -> 128 (ReLU) -> 128 (ReLU) -> 225 logits, softmax; class c means
+ *     levels = 4 + c / 25, p = 8 + c % 25.  Parameters: one flat binary32 array of
+ *     FMM_MLP_PARAMS values, row-major W1[128][64], b1[128], W2[128][128], b2[128],
+ *     W3[225][128], b3[225] (y = W x + b).
+ *   training: softmax cross-entropy averaged over the batch, Adam (beta1 0.9, beta2 0.999,
+ *     eps 1e-8, bias-corrected), all on the GPU in binary32.
+ * ------------------------------------------------------------------------------------------- */
+#define FMM_MLP_IN 64
+#define FMM_MLP_HIDDEN 128
+#define FMM_MLP_OUT 225
+#define FMM_MLP_PARAMS 53857
+#define FMM_SEL_LMIN 4
+#define FMM_SEL_LMAX 12
+#define FMM_SEL_PMIN 8
+#define FMM_SEL_PMAX 32
+#define FMM_SEL_NP 25
+#define FMM_FEAT_LOG10N 60
+#define FMM_FEAT_LOG10TOL 61
+
+typedef struct fmm_mlp_s* fmm_mlp;
+
+/* Features of every instance of built tree t for tolerance 0 < tol < 1: features[n_inst][64]
+ * (device, binary32).  The tree's device must be current. */
+int fmm_selector_features(fmm_tree t, double tol, float* features, void* stream);
+
+/* A network with room for batches of up to batch_max samples; parameters start at zero. */
+int fmm_mlp_create(int batch_max, fmm_mlp* out);
+void fmm_mlp_destroy(fmm_mlp m);
+
+/* Copy parameters in (any memory cudaMemcpy can read; resets the Adam state) or out. */
+int fmm_mlp_set_params(fmm_mlp m, const float* params, void* stream);
+int fmm_mlp_get_params(fmm_mlp m, float* params, void* stream);
+
+/* Class probabilities prob[B][225] of inputs X[B][64] (device). */
+int fmm_mlp_forward(fmm_mlp m, const float* X, int B, float* prob, void* stream);
+
+/* Gradient of the mean cross-entropy of labels[B] (device int32 classes) with respect to the
+ * parameters, grad[FMM_MLP_PARAMS], and the mean loss loss[1] (device; either may be NULL).
+ * A label outside [0, 225) makes the loss NaN. */
+int fmm_mlp_gradients(fmm_mlp m, const float* X, const int32_t* labels, int B, float* grad, float* loss,
+                      void* stream);
+
+/* One Adam step with learning rate lr on the batch (X, labels); loss[1] (device, may be NULL)
+ * receives the batch's mean loss before the step. */
+int fmm_mlp_train_step(fmm_mlp m, const float* X, const int32_t* labels, int B, float lr, float* loss,
+                       void* stream);
+
+/* The selector's choice for B feature vectors (device): levels_p[B][2] = (levels, p) of the most
+ * probable class among those with 4^levels <= N (device int32). */
+int fmm_select_params(fmm_mlp m, const float* features, int B, int32_t* levels_p, void* stream);
+
 /* Eq. (1.1) by direct summation in binary64 at m target input indices targets[m] (int64,
  * device) over all n sources; phi[m] (device).  Coincident distinct points contribute 0. */
 int fmm_direct(const double* x, const double* y, const double* q, int64_t n,

@@ -70,6 +70,15 @@ def load_library(path: str = LIB_PATH):
             "fmm_autotune": (i32, [vp, vp, vp, ctypes.POINTER(fmm_params), vp, vp, ctypes.POINTER(i32),
                                    ctypes.POINTER(i32)]),
             "fmm_set_launch": (i32, [vp, i32, i32]),
+            "fmm_selector_features": (i32, [vp, dbl, vp, vp]),
+            "fmm_mlp_create": (i32, [i32, ctypes.POINTER(vp)]),
+            "fmm_mlp_destroy": (None, [vp]),
+            "fmm_mlp_set_params": (i32, [vp, vp, vp]),
+            "fmm_mlp_get_params": (i32, [vp, vp, vp]),
+            "fmm_mlp_forward": (i32, [vp, vp, i32, vp, vp]),
+            "fmm_mlp_gradients": (i32, [vp, vp, vp, i32, vp, vp, vp]),
+            "fmm_mlp_train_step": (i32, [vp, vp, vp, i32, ctypes.c_float, vp, vp]),
+            "fmm_select_params": (i32, [vp, vp, i32, vp, vp]),
             "fmm_build_tree": (i32, [vp, vp, vp, vp]),
             "fmm_tree_export": (i32, [vp, vp, vp, vp, vp]),
             "fmm_tree_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)]),
@@ -291,6 +300,66 @@ def fmm_autotune(tree, lists, q: torch.Tensor, p: int, mode: int, phi: torch.Ten
 
 def fmm_set_launch(tree, m2l_blocks: int = 0, p2p_blocks: int = 0):
     _check(load_library().fmm_set_launch(tree, int(m2l_blocks), int(p2p_blocks)))
+
+
+FMM_MLP_IN, FMM_MLP_HIDDEN, FMM_MLP_OUT, FMM_MLP_PARAMS = 64, 128, 225, 53857
+FMM_SEL_LMIN, FMM_SEL_LMAX, FMM_SEL_PMIN, FMM_SEL_PMAX, FMM_SEL_NP = 4, 12, 8, 32, 25
+
+
+def fmm_selector_features(tree, tol: float, out: torch.Tensor, stream=None):
+    """Selector inputs of every instance of a built tree: out[n_inst][64] (CUDA float32)."""
+    ni = fmm_tree_num_instances(tree)
+    _check(load_library().fmm_selector_features(tree, float(tol), _dev(out, torch.float32, 64 * ni, "features"),
+                                                _stream(stream)))
+
+
+def fmm_mlp_create(batch_max: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().fmm_mlp_create(int(batch_max), ctypes.byref(h)))
+    return h
+
+
+def fmm_mlp_destroy(m):
+    if m:
+        load_library().fmm_mlp_destroy(m)
+
+
+def fmm_mlp_set_params(m, params: torch.Tensor, stream=None):
+    _check(load_library().fmm_mlp_set_params(m, _dev(params, torch.float32, FMM_MLP_PARAMS, "params"),
+                                             _stream(stream)))
+
+
+def fmm_mlp_get_params(m, out: torch.Tensor, stream=None):
+    _check(load_library().fmm_mlp_get_params(m, _dev(out, torch.float32, FMM_MLP_PARAMS, "params"),
+                                             _stream(stream)))
+
+
+def fmm_mlp_forward(m, X: torch.Tensor, prob: torch.Tensor, stream=None):
+    B = X.shape[0]
+    _check(load_library().fmm_mlp_forward(m, _dev(X, torch.float32, 64 * B, "X"), B,
+                                          _dev(prob, torch.float32, 225 * B, "prob"), _stream(stream)))
+
+
+def fmm_mlp_gradients(m, X: torch.Tensor, labels: torch.Tensor, grad=None, loss=None, stream=None):
+    B = X.shape[0]
+    _check(load_library().fmm_mlp_gradients(m, _dev(X, torch.float32, 64 * B, "X"),
+                                            _dev(labels, torch.int32, B, "labels"), B,
+                                            _dev(grad, torch.float32, FMM_MLP_PARAMS, "grad"),
+                                            _dev(loss, torch.float32, 1, "loss"), _stream(stream)))
+
+
+def fmm_mlp_train_step(m, X: torch.Tensor, labels: torch.Tensor, lr: float, loss=None, stream=None):
+    B = X.shape[0]
+    _check(load_library().fmm_mlp_train_step(m, _dev(X, torch.float32, 64 * B, "X"),
+                                             _dev(labels, torch.int32, B, "labels"), B, float(lr),
+                                             _dev(loss, torch.float32, 1, "loss"), _stream(stream)))
+
+
+def fmm_select_params(m, features: torch.Tensor, out: torch.Tensor, stream=None):
+    """out[B][2] (CUDA int32) = (levels, p) chosen for each feature vector."""
+    B = features.shape[0]
+    _check(load_library().fmm_select_params(m, _dev(features, torch.float32, 64 * B, "features"), B,
+                                            _dev(out, torch.int32, 2 * B, "out"), _stream(stream)))
 
 
 def fmm_direct(x, y, q, targets, phi, stream=None):

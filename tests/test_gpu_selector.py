@@ -1,0 +1,210 @@
+"""The parameter selector on the GPU against the FP64 reference (oracle/mlp_oracle.c).
+
+Features: the library's kernel on GPU-built trees against the reference on the oracle's trees
+(the rectangles agree bit for bit, so only binary32 rounding of the outputs remains).  Network:
+forward probabilities and the gradient of the loss against the FP64 backward pass; one Adam step
+against its closed form; the masked arg-max against numpy.  Then the whole pipeline on a few
+small point sets (runs of the method -> labels -> training on the GPU -> selection), and the
+gain of the trained weights over the fixed-parameter rule.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1006_2269_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a, dev, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), device=dev, dtype=dtype)
+
+
+@pytest.fixture(scope="module")
+def mlp_ref():
+    import oracle
+    from oracle import mlp
+    oracle.build()
+    return mlp
+
+
+FEATURE_CASES = [
+    (lambda: W.uniform(5000, 301), 4, 1e-6),
+    (lambda: W.clusters(20000, 302), 5, 1e-3),
+    (lambda: W.circle(9000, 303), 4, 1e-9),
+    (lambda: W.normal(4 ** 3 + 7, 304), 3, 1e-6),
+    (lambda: W.rings_plummer(30000, 305), 6, 1e-4),
+    (lambda: W.uniform(50, 306), 0, 1e-2),
+]
+
+
+@pytest.mark.parametrize("k", range(len(FEATURE_CASES)))
+def test_features_match_reference(fmmlib, orc, mlp_ref, cuda, k):
+    import torch
+    make, L, tol = FEATURE_CASES[k]
+    c = make()
+    t = fmmlib.fmm_tree_create(c.x.shape[0], L)
+    try:
+        fmmlib.fmm_build_tree(t, _t(c.x, cuda), _t(c.y, cuda))
+        out = torch.empty(64, dtype=torch.float32, device=cuda)
+        fmmlib.fmm_selector_features(t, tol, out)
+        got = out.cpu().numpy().astype(np.float64)
+    finally:
+        fmmlib.fmm_tree_destroy(t)
+    _, rects, _ = orc.tree(c.x, c.y, L)
+    ref = mlp_ref.features(rects, L, c.x.shape[0], tol)
+    assert np.all(np.abs(got - ref) <= 2e-6 * np.maximum(1.0, np.abs(ref)))
+
+
+def test_features_of_a_forest(fmmlib, orc, mlp_ref, cuda):
+    import torch
+    clouds = [W.uniform(3000, 311), W.circle(7000, 312), W.clusters(12000, 313)]
+    levels = [3, 4, 5]
+    x = np.concatenate([c.x for c in clouds])
+    y = np.concatenate([c.y for c in clouds])
+    t = fmmlib.fmm_tree_create_batched([c.x.shape[0] for c in clouds], levels)
+    try:
+        fmmlib.fmm_build_tree(t, _t(x, cuda), _t(y, cuda))
+        out = torch.empty((3, 64), dtype=torch.float32, device=cuda)
+        fmmlib.fmm_selector_features(t, 1e-6, out)
+        got = out.cpu().numpy().astype(np.float64)
+    finally:
+        fmmlib.fmm_tree_destroy(t)
+    for i, (c, L) in enumerate(zip(clouds, levels)):
+        _, rects, _ = orc.tree(c.x, c.y, L)
+        ref = mlp_ref.features(rects, L, c.x.shape[0], 1e-6)
+        assert np.all(np.abs(got[i] - ref) <= 2e-6 * np.maximum(1.0, np.abs(ref)))
+
+
+def _net(fmmlib, cuda, params, bmax=64):
+    m = fmmlib.fmm_mlp_create(bmax)
+    fmmlib.fmm_mlp_set_params(m, _t(params.astype(np.float32), cuda))
+    return m
+
+
+def _random_params(mlp_ref, seed, scale=0.15):
+    return np.random.default_rng(seed).normal(0, scale, mlp_ref.nparams()).astype(np.float32)
+
+
+def test_forward_matches_reference(fmmlib, mlp_ref, cuda):
+    import torch
+    p = _random_params(mlp_ref, 5)
+    X = np.random.default_rng(6).normal(size=(37, 64)).astype(np.float32)
+    m = _net(fmmlib, cuda, p)
+    try:
+        prob = torch.empty((37, 225), dtype=torch.float32, device=cuda)
+        fmmlib.fmm_mlp_forward(m, _t(X, cuda), prob)
+        got = prob.cpu().numpy()
+    finally:
+        fmmlib.fmm_mlp_destroy(m)
+    ref = mlp_ref.forward(p.astype(np.float64), X.astype(np.float64))
+    assert np.max(np.abs(got - ref)) <= 2e-6
+    assert np.allclose(got.sum(axis=1), 1.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("B", [1, 13, 64])
+def test_gradients_match_reference(fmmlib, mlp_ref, cuda, B):
+    import torch
+    p = _random_params(mlp_ref, 7 + B)
+    g = np.random.default_rng(8 + B)
+    X = g.normal(size=(B, 64)).astype(np.float32)
+    y = g.integers(0, 225, B).astype(np.int32)
+    m = _net(fmmlib, cuda, p)
+    try:
+        grad = torch.empty(mlp_ref.nparams(), dtype=torch.float32, device=cuda)
+        loss = torch.empty(1, dtype=torch.float32, device=cuda)
+        fmmlib.fmm_mlp_gradients(m, _t(X, cuda), _t(y, cuda), grad, loss)
+        gg, ll = grad.cpu().numpy().astype(np.float64), float(loss.item())
+    finally:
+        fmmlib.fmm_mlp_destroy(m)
+    lref, gref = mlp_ref.loss_grad(p.astype(np.float64), X.astype(np.float64), y)
+    assert abs(ll - lref) <= 1e-5 * abs(lref)
+    assert np.max(np.abs(gg - gref)) <= 1e-4 * np.max(np.abs(gref))
+
+
+def test_adam_first_step_closed_form(fmmlib, mlp_ref, cuda):
+    # from zero moments the bias-corrected first step is -lr * g / (|g| + eps)
+    import torch
+    p = _random_params(mlp_ref, 9)
+    g = np.random.default_rng(10)
+    X = g.normal(size=(16, 64)).astype(np.float32)
+    y = g.integers(0, 225, 16).astype(np.int32)
+    lr = 1e-3
+    m = _net(fmmlib, cuda, p)
+    try:
+        fmmlib.fmm_mlp_train_step(m, _t(X, cuda), _t(y, cuda), lr)
+        out = torch.empty(mlp_ref.nparams(), dtype=torch.float32, device=cuda)
+        fmmlib.fmm_mlp_get_params(m, out)
+        p1 = out.cpu().numpy().astype(np.float64)
+    finally:
+        fmmlib.fmm_mlp_destroy(m)
+    _, gref = mlp_ref.loss_grad(p.astype(np.float64), X.astype(np.float64), y)
+    step = p1 - p.astype(np.float64)
+    big = np.abs(gref) > 1e-5 * np.abs(gref).max()  # where eps and binary32 noise cannot matter
+    assert np.allclose(step[big], -lr * np.sign(gref[big]), rtol=2e-3, atol=1e-7)
+    assert np.all(np.abs(step) <= lr * (1 + 1e-4))
+
+
+def test_masked_argmax(fmmlib, mlp_ref, cuda):
+    import torch
+    p = _random_params(mlp_ref, 11, scale=0.4)
+    g = np.random.default_rng(12)
+    X = g.normal(size=(50, 64)).astype(np.float32)
+    ns = np.array([10 ** v for v in g.uniform(2.5, 7.0, 50)])
+    X[:, 60] = np.log10(ns).astype(np.float32)
+    m = _net(fmmlib, cuda, p)
+    try:
+        out = torch.empty((50, 2), dtype=torch.int32, device=cuda)
+        fmmlib.fmm_select_params(m, _t(X, cuda), out)
+        got = out.cpu().numpy()
+    finally:
+        fmmlib.fmm_mlp_destroy(m)
+    prob = mlp_ref.forward(p.astype(np.float64), X.astype(np.float64))
+    for i in range(50):
+        n = 10.0 ** float(X[i, 60])
+        ok = np.array([4 ** (4 + c // 25) <= n * (1 + 1e-6) for c in range(225)])
+        c = int(np.argmax(np.where(ok, prob[i], -1.0)))
+        assert tuple(got[i]) == (4 + c // 25, 8 + c % 25)
+
+
+def test_pipeline_end_to_end(fmmlib, cuda):
+    # runs of the method -> labels -> GPU training -> selection, on a few small point sets
+    from paper_1006_2269_gb300 import selector as S
+    X, y, tables = S.generate(5, 77, cuda, nmin=1e4, nmax=2.5e4, tols=(1e-3, 1e-6))
+    assert X.shape == (10, 64) and y.shape == (10,)
+    for tab in tables:
+        for r in tab["tables"]["mixed"]:
+            L, p, ms, err = r
+            assert ms > 0 and err < 1.0
+    # the label is the fastest run meeting the tolerance
+    tab = tables[0]["tables"]["mixed"]
+    c = S.label(tab, 1e-6)
+    ok = [r for r in tab if r[3] <= 1e-6]
+    assert ok and S.class_of(*min(ok, key=lambda r: r[2])[:2]) == c
+    sel = S.Selector(S.init_params(3), cuda)
+    try:
+        hist = sel.train(X, y, epochs=150, batch=8, lr=3e-3)
+        assert hist[-1] < 0.5 * hist[0]
+        assert sel.accuracy(X, y) >= 0.8  # memorises its ten samples
+        L, p = sel.select(_t(W.uniform(20000, 5).x, cuda), _t(W.uniform(20000, 5).y, cuda), 1e-6)
+        assert S.LMIN <= L <= 7 and S.PMIN <= p <= S.PMAX
+    finally:
+        sel.close()
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                    "paper_1006_2269_gb300", "selector_weights.f32")),
+                    reason="no trained selector weights")
+def test_trained_selector_gain(fmmlib, cuda):
+    # fresh point sets (seeds unseen in training): the trained selector against the plain rule
+    from paper_1006_2269_gb300 import selector as S
+    sel = S.Selector.load(device=cuda)
+    try:
+        g = S.gain(sel, 10, 4242, cuda)
+    finally:
+        sel.close()
+    assert g["met_tol_selector"] >= 0.8
+    assert g["ms_selector"] <= g["ms_fallback"]

@@ -1,0 +1,42 @@
+"""Host-side logic of the parameter selector (no GPU): the plain rule, classes, labels."""
+import math
+
+import pytest
+
+from paper_1006_2269_gb300 import selector as S
+
+
+def test_fallback_rule():
+    # smallest p with 2^-(p+1) * 4 <= tol, about 20 points per leaf
+    assert S.fallback_params(10 ** 6, 1e-6) == (8, 21)
+    assert S.fallback_params(20000, 1e-3) == (5, 11)
+    assert S.fallback_params(300, 1e-9) == (4, 31)
+    for tol in (1e-3, 1e-6, 1e-9):
+        _, p = S.fallback_params(10 ** 5, tol)
+        assert 0.5 ** (p + 1) * 4 <= tol < 0.5 ** p * 4
+
+
+def test_classes_round_trip():
+    seen = set()
+    for L in range(S.LMIN, S.LMAX + 1):
+        for p in range(S.PMIN, S.PMAX + 1):
+            c = S.class_of(L, p)
+            assert 0 <= c < S.NCLASS and S.params_of(c) == (L, p)
+            seen.add(c)
+    assert len(seen) == S.NCLASS == 225
+
+
+def test_label_picks_fastest_feasible():
+    tab = [(5, 10, 1.0, 3e-4), (5, 12, 1.2, 2e-5), (6, 10, 0.8, 5e-3), (6, 14, 0.9, 1e-7)]
+    assert S.label(tab, 1e-3) == S.class_of(6, 14)
+    assert S.label(tab, 1e-2) == S.class_of(6, 10)
+    assert S.label(tab, 1e-9) == S.class_of(6, 14)  # nothing meets it: the most accurate
+
+
+@pytest.mark.parametrize("n", [10 ** 4, 37000, 2 * 10 ** 5, 10 ** 6])
+def test_candidates_are_feasible(n):
+    Ls = S.candidate_levels(n)
+    assert Ls and all(S.LMIN <= L <= S.LMAX and 4 ** L <= n for L in Ls)
+    assert S.probe_levels(n) <= S.max_levels(n)
+    for tol in S.TOLS:
+        assert all(S.PMIN <= p <= S.PMAX for p in S.candidate_ps(tol))
