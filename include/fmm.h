@@ -221,11 +221,18 @@ int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
  * totals, timing each with CUDA events, and keeps the fastest for later evaluations of this tree;
  * phi receives the potentials of the last run.  It synchronises with the host (not for use under
  * stream capture).  The chosen totals are reported in m2l_blocks / p2p_blocks (host, may be
- * NULL).  fmm_set_launch sets them directly (0 = the built-in default); it uploads small launch
- * tables and so also synchronises. */
+ * NULL).  For the mixed path it also times the two binary32 M2L kernels (fmm_set_m2l_kernel)
+ * and keeps the faster.  fmm_set_launch sets the totals directly (0 = the built-in default); it
+ * uploads small launch tables and so also synchronises. */
 int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi,
                  void* stream, int* m2l_blocks_host, int* p2p_blocks_host);
 int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks);
+
+/* Which kernel performs the binary32 M2L of tree t: 0 (default) the tensor cores (tcgen05,
+ * split-tf32 products: each operand as a tf32 high and low part, three products accumulated in
+ * binary32) whenever p <= 31, 1 the SIMT units in plain binary32.  The binary64 path always uses
+ * the SIMT units. */
+int fmm_set_m2l_kernel(fmm_tree t, int kind);
 
 /* ---------------------------------------------------------------------------------------------
  * Parameter selector (no paper counterpart).  The paper picks the parameters by rule: p from the

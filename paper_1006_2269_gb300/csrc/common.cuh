@@ -221,6 +221,7 @@ struct fmm_tree_s {
     // launch tuning (set by fmm_autotune; 0 = defaults): total blocks of the M2L and near-field
     // launches, shared out over the instances in proportion to their work
     int tune_m2l_blocks = 0, tune_p2p_blocks = 0;
+    int m2l_kind = 0;  // binary32 M2L: 0 = tensor cores (when p <= 31), 1 = SIMT units
 
     // launch schedules (device tables only for forests of more than one instance)
     fmm::SchedH s_tiles;   // one block per tree-build tile
@@ -282,6 +283,10 @@ int direct(const double* x, const double* y, const double* q, int64_t n, const i
            int64_t m, double* phi, cudaStream_t s);
 int autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,
              cudaStream_t s, int* m2l_blocks, int* p2p_blocks);
+
+// m2l_tc.cu: binary32 M2L on the tensor cores (Me, Le: [nbox][PS] float2)
+bool m2l_tc_supported(int P);
+int m2l_tc(fmm_tree t, fmm_lists l, int P, int PS, const void* Me, void* Le, cudaStream_t s);
 
 // scan.cu: exclusive scan of int32 counts with a base value read from device memory:
 // out[i] = base[0] + sum_{j < i} in[j] for i = 0..m (out has m + 1 entries; out may alias

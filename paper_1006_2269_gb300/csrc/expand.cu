@@ -1255,7 +1255,10 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         }
         {
             StageScope scope(FMM_STAGE_M2L, s);
-            rc = dispatch_m2l(t, li, P, PS, geo, Me, Le, s);
+            if (sizeof(T) == 4 && t->m2l_kind == 0 && m2l_tc_supported(P))
+                rc = m2l_tc(t, li, P, PS, Me, Le, s);
+            else
+                rc = dispatch_m2l(t, li, P, PS, geo, Me, Le, s);
             if (rc) return rc;
         }
         {
@@ -1367,6 +1370,16 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
             }
         }
         knob = best_v;
+    }
+    // binary32 M2L: tensor cores or SIMT units, whichever is faster here
+    if (!rc && prm.mode == FMM_MODE_MIXED && !(prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR) &&
+        m2l_tc_supported(prm.p + 1) && (rc = sched_tuned(t)) == 0) {
+        float ms_kind[2] = {0.f, 0.f};
+        for (int kind = 0; kind < 2 && !rc; kind++) {
+            t->m2l_kind = kind;
+            rc = time_one(ms_kind[kind]);
+        }
+        t->m2l_kind = ms_kind[1] < ms_kind[0] ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

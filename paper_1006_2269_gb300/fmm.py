@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
             "fmm_autotune": (i32, [vp, vp, vp, ctypes.POINTER(fmm_params), vp, vp, ctypes.POINTER(i32),
                                    ctypes.POINTER(i32)]),
             "fmm_set_launch": (i32, [vp, i32, i32]),
+            "fmm_set_m2l_kernel": (i32, [vp, i32]),
             "fmm_selector_features": (i32, [vp, dbl, vp, vp]),
             "fmm_mlp_create": (i32, [i32, ctypes.POINTER(vp)]),
             "fmm_mlp_destroy": (None, [vp]),
@@ -360,6 +361,14 @@ def fmm_select_params(m, features: torch.Tensor, out: torch.Tensor, stream=None)
     B = features.shape[0]
     _check(load_library().fmm_select_params(m, _dev(features, torch.float32, 64 * B, "features"), B,
                                             _dev(out, torch.int32, 2 * B, "out"), _stream(stream)))
+
+
+FMM_M2L_TENSOR, FMM_M2L_SIMT = 0, 1
+
+
+def fmm_set_m2l_kernel(tree, kind: int):
+    """Binary32 M2L on the tensor cores (0, default) or on the SIMT units (1)."""
+    _check(load_library().fmm_set_m2l_kernel(tree, int(kind)))
 
 
 def fmm_direct(x, y, q, targets, phi, stream=None):
