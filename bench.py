@@ -34,6 +34,14 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
+def measured_bf16_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -310,11 +318,19 @@ def main():
         torch.cuda.synchronize()
         return g
 
-    # warm-up, then the accuracy check against the binary64 direct sum at sampled targets
+    # warm-up, launch tuning of each path, then the accuracy check against the binary64 direct
+    # sum at sampled targets
     for _ in range(args.warmup):
         step(fmm.FMM_MODE_MIXED)
     fmm.fmm_sync_status(f.tree, f.lists)
     fmm.fmm_lists_sync(f.lists)
+    tuned = {fmm.FMM_MODE_FP64: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_FP64, phi),
+             fmm.FMM_MODE_MIXED: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_MIXED, phi)}
+
+    def use(mode):
+        fmm.fmm_set_launch(f.tree, *tuned[mode])
+
+    use(fmm.FMM_MODE_MIXED)
     tg = torch.as_tensor(W.sample_targets(n, w.n_check, W.SEED_BASE + 101), device=dev)
     ref = torch.empty(tg.numel(), dtype=torch.float64, device=dev)
     fmm.fmm_direct(x, y, q, tg, ref)
@@ -322,6 +338,7 @@ def main():
     torch.cuda.synchronize()
     scale = ref.abs().max().item()
     err_mixed = (phi[tg] - ref).abs().max().item() / scale
+    use(fmm.FMM_MODE_FP64)
     step(fmm.FMM_MODE_FP64)
     torch.cuda.synchronize()
     err_fp64 = (phi[tg] - ref).abs().max().item() / scale
@@ -330,12 +347,15 @@ def main():
     graphs = {}
     if not args.no_graph:
         try:
-            graphs = {m: capture(m) for m in (fmm.FMM_MODE_MIXED, fmm.FMM_MODE_FP64)}
+            for m in (fmm.FMM_MODE_MIXED, fmm.FMM_MODE_FP64):
+                use(m)
+                graphs[m] = capture(m)
         except Exception as exc:  # report and time plain launches instead
             print(f"graph capture failed: {exc}", file=sys.stderr)
             graphs = {}
 
     def timed(mode, steps, e2e=False, profile=False):
+        use(mode)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         if world > 1:
@@ -372,6 +392,7 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return t.item(), launches, prof
 
+    use(fmm.FMM_MODE_MIXED)
     l0 = fmm.fmm_launch_count()
     step(fmm.FMM_MODE_MIXED)
     per_step_launches = fmm.fmm_launch_count() - l0
@@ -395,9 +416,19 @@ def main():
     mufu_peak = 16 * SM_COUNT * SM_MAX_MHZ * 1e6  # log2 evaluations / s
     fp32_peak = 128 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6  # flop / s
     t_top = stage_ms[top] * 1e-3
+    m2l_kind = fmm.fmm_get_m2l_kernel(f.tree)
+    if m2l_kind == fmm.FMM_M2L_AUTO:
+        m2l_kind = fmm.FMM_M2L_TENSOR if 24 <= P <= 32 else fmm.FMM_M2L_SIMT
     if top == "leaf":
         roof = {"bound": "alu", "achieved": npairs / t_top / 1e12, "peak": mufu_peak / 1e12,
                 "unit": "Tlog2/s (MUFU)", "traffic": None}
+    elif top == "m2l" and m2l_kind == fmm.FMM_M2L_TENSOR:
+        # tcgen05 split-tf32: three tf32 products per element of the contraction (4 P^2 flop per
+        # weak pair each); peak = tf32 dense rate, the measured bf16 rate x the nominal tf32/bf16
+        # ratio 1/2
+        bf16 = measured_bf16_tflops()
+        roof = {"bound": "tensor", "achieved": 3 * nweak * 4 * P * P / t_top / 1e12, "peak": bf16 / 2,
+                "unit": "TFLOP/s (tf32 tensor)", "traffic": None}
     elif top == "m2l":
         roof = {"bound": "alu", "achieved": nweak * 4 * P * P / t_top / 1e12, "peak": fp32_peak / 1e12,
                 "unit": "TFLOP/s (FP32 FMA pipe)", "traffic": None}
@@ -419,7 +450,11 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "n": n, "levels": w.levels, "theta": w.theta, "p": w.p,
                    "mode": "mixed", "l2": "flushed between steps (256 MB write outside the events)",
-                   "replicas": world, "cuda_graph": bool(graphs)},
+                   "replicas": world, "cuda_graph": bool(graphs),
+                   "autotuned_blocks": {"m2l": tuned[fmm.FMM_MODE_MIXED][0],
+                                        "near_field": tuned[fmm.FMM_MODE_MIXED][1]},
+                   "m2l_kernel": "tensor cores (tcgen05, split tf32)" if m2l_kind == fmm.FMM_M2L_TENSOR
+                   else "SIMT binary32"},
         "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,
         "fp64_path": {"value": world * n / (ms_fp64 / args.fp64_steps * 1e-3),
                       "ms_per_step": ms_fp64 / args.fp64_steps, "stages_ms": stage_ms64},

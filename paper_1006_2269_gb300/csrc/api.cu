@@ -462,9 +462,15 @@ int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
 int fmm_set_m2l_kernel(fmm_tree t, int kind)
 {
     if (!t) return fail(FMM_ERR_ARG, "NULL tree");
-    if (kind != 0 && kind != 1) return fail(FMM_ERR_ARG, "unknown M2L kernel %d", kind);
+    if (kind < 0 || kind > 2) return fail(FMM_ERR_ARG, "unknown M2L kernel %d", kind);
     t->m2l_kind = kind;
     return FMM_OK;
+}
+
+int fmm_get_m2l_kernel(fmm_tree t)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    return t->m2l_kind;
 }
 
 int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks)

@@ -221,7 +221,7 @@ struct fmm_tree_s {
     // launch tuning (set by fmm_autotune; 0 = defaults): total blocks of the M2L and near-field
     // launches, shared out over the instances in proportion to their work
     int tune_m2l_blocks = 0, tune_p2p_blocks = 0;
-    int m2l_kind = 0;  // binary32 M2L: 0 = tensor cores (when p <= 31), 1 = SIMT units
+    int m2l_kind = 0;  // binary32 M2L: 0 = by order (tensor cores for 24 <= P <= 32), 1 = SIMT, 2 = tensor cores
 
     // launch schedules (device tables only for forests of more than one instance)
     fmm::SchedH s_tiles;   // one block per tree-build tile

@@ -1255,7 +1255,10 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         }
         {
             StageScope scope(FMM_STAGE_M2L, s);
-            if (sizeof(T) == 4 && t->m2l_kind == 0 && m2l_tc_supported(P))
+            // tensor cores where they measured faster than the SIMT kernel (P >= 24; below, the
+            // scaling work around the contraction dominates), unless chosen explicitly
+            const bool tc = m2l_tc_supported(P) && (t->m2l_kind == 2 || (t->m2l_kind == 0 && P >= 24));
+            if (sizeof(T) == 4 && tc)
                 rc = m2l_tc(t, li, P, PS, Me, Le, s);
             else
                 rc = dispatch_m2l(t, li, P, PS, geo, Me, Le, s);
@@ -1374,12 +1377,14 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     // binary32 M2L: tensor cores or SIMT units, whichever is faster here
     if (!rc && prm.mode == FMM_MODE_MIXED && !(prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR) &&
         m2l_tc_supported(prm.p + 1) && (rc = sched_tuned(t)) == 0) {
-        float ms_kind[2] = {0.f, 0.f};
-        for (int kind = 0; kind < 2 && !rc; kind++) {
-            t->m2l_kind = kind;
-            rc = time_one(ms_kind[kind]);
+        float ms_simt = 0.f, ms_tc = 0.f;
+        t->m2l_kind = 1;
+        rc = time_one(ms_simt);
+        if (!rc) {
+            t->m2l_kind = 2;
+            rc = time_one(ms_tc);
         }
-        t->m2l_kind = ms_kind[1] < ms_kind[0] ? 1 : 0;
+        t->m2l_kind = ms_tc < ms_simt ? 2 : 1;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

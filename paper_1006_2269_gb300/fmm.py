@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
                                    ctypes.POINTER(i32)]),
             "fmm_set_launch": (i32, [vp, i32, i32]),
             "fmm_set_m2l_kernel": (i32, [vp, i32]),
+            "fmm_get_m2l_kernel": (i32, [vp]),
             "fmm_selector_features": (i32, [vp, dbl, vp, vp]),
             "fmm_mlp_create": (i32, [i32, ctypes.POINTER(vp)]),
             "fmm_mlp_destroy": (None, [vp]),
@@ -363,12 +364,19 @@ def fmm_select_params(m, features: torch.Tensor, out: torch.Tensor, stream=None)
                                             _dev(out, torch.int32, 2 * B, "out"), _stream(stream)))
 
 
-FMM_M2L_TENSOR, FMM_M2L_SIMT = 0, 1
+FMM_M2L_AUTO, FMM_M2L_SIMT, FMM_M2L_TENSOR = 0, 1, 2
 
 
 def fmm_set_m2l_kernel(tree, kind: int):
-    """Binary32 M2L on the tensor cores (0, default) or on the SIMT units (1)."""
+    """Binary32 M2L by order (0, default), on the SIMT units (1) or on the tensor cores (2)."""
     _check(load_library().fmm_set_m2l_kernel(tree, int(kind)))
+
+
+def fmm_get_m2l_kernel(tree) -> int:
+    rc = load_library().fmm_get_m2l_kernel(tree)
+    if rc < 0:
+        _check(rc)
+    return rc
 
 
 def fmm_direct(x, y, q, targets, phi, stream=None):

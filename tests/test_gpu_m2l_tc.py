@@ -46,7 +46,7 @@ def test_tensor_core_m2l(fmmlib, orc, cuda, name, p):
         tc = f.evaluate(q, p, "mixed").cpu().numpy()
         fmmlib.fmm_set_m2l_kernel(f.tree, fmmlib.FMM_M2L_SIMT)
         simt = f.evaluate(q, p, "mixed").cpu().numpy()
-        fmmlib.fmm_set_m2l_kernel(f.tree, fmmlib.FMM_M2L_TENSOR)
+        fmmlib.fmm_set_m2l_kernel(f.tree, fmmlib.FMM_M2L_AUTO)
     finally:
         f.close()
     ref = orc.fmm(c.x, c.y, c.q, L, p, 0.5)
@@ -63,6 +63,7 @@ def test_tensor_core_m2l_forest(fmmlib, orc, cuda):
     q = np.concatenate([c.q for c in clouds])
     b = fmmlib.FMMBatch(_t(x, cuda), _t(y, cuda), [c.x.shape[0] for c in clouds], levels, 0.5)
     try:
+        fmmlib.fmm_set_m2l_kernel(b.tree, fmmlib.FMM_M2L_TENSOR)
         phi = b.evaluate(_t(q, cuda), 18, "mixed").cpu().numpy()
         for d, c, L in zip(b.inst, clouds, levels):
             ref = orc.fmm(c.x, c.y, c.q, L, 18, 0.5)
