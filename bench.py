@@ -66,10 +66,14 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:  # sampling has started
+                time.sleep(0.01)
+            self.lines.clear()
         except Exception:
             self.proc = None
         return self
@@ -256,7 +260,7 @@ def bench_batched(dev, steps, warmup, sequential=True):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -430,8 +434,11 @@ def main():
         roof = {"bound": "tensor", "achieved": 3 * nweak * 4 * P * P / t_top / 1e12, "peak": bf16 / 2,
                 "unit": "TFLOP/s (tf32 tensor)", "traffic": None}
     elif top == "m2l":
+        # dram__bytes_read.sum + dram__bytes_write.sum of k_m2l_pairs<float, 21> on this workload,
+        # from one ncu capture; valid while that kernel is unchanged
+        traffic = 193367296 if (P == 21 and n == 1 << 20) else None
         roof = {"bound": "alu", "achieved": nweak * 4 * P * P / t_top / 1e12, "peak": fp32_peak / 1e12,
-                "unit": "TFLOP/s (FP32 FMA pipe)", "traffic": None}
+                "unit": "TFLOP/s (FP32 FMA pipe)", "traffic": traffic}
     elif top == "tree_sort":
         byts = n * (32 + 16 * 24)
         roof = {"bound": "hbm", "achieved": byts / t_top / 1e9, "peak": hbm, "unit": "GB/s",
