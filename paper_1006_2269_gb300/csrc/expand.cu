@@ -42,6 +42,7 @@ namespace {
 constexpr double MIXED_TOL_FLOOR = 1e-7;  // smallest tolerance the binary32 path is asked for
 constexpr int M2L_CH = 8;   // consecutive weak pairs per lane
 constexpr int P2P_CH = 16;  // consecutive leaf pairs per warp
+constexpr int P2P_GROUP_CH = 8;  // consecutive leaf pairs per lane group (binary32 kernel)
 
 template <typename T>
 struct alignas(2 * sizeof(T)) cx {
@@ -805,11 +806,12 @@ __device__ __forceinline__ float p2p_exact(float xt, float yt, int32_t it, const
     return part;
 }
 
-// binary32 near field for leaves of at most 32 points.  Groups of gsl lanes work on one leaf pair,
+// binary32 near field for leaves of at most 64 points.  Groups of gsl lanes work on one leaf pair,
 // each lane on two targets (t0 + li and t0 + li + gsl), so a warp holds 32 / gsl leaf pairs at
-// once and every source load serves two pair evaluations.  The main loop has no branch: it keeps
-// the smallest r^2 it met and, for the rare lane whose minimum falls below the exactness threshold
-// (and for the leaf's pair with itself), the leaf pair is redone by the exact path.
+// once and every source load serves two pair evaluations; each group walks its own run of
+// consecutive leaf pairs and flushes its sums when the target leaf changes.  The main loop has no
+// branch: it keeps the smallest r^2 it met and, for the rare lane whose minimum falls below the
+// exactness threshold, the leaf pair is redone by the exact path.
 __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                  const int32_t* __restrict__ soff,
                                                  const int32_t* __restrict__ sidx,
@@ -851,13 +853,17 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
     const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
     const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
-    for (int64_t e0 = e_begin + warp * P2P_CH; e0 < e_end; e0 += nwarps * P2P_CH) {
-        const int64_t e1 = min(e0 + P2P_CH, e_end);
+    // each group takes P2P_GROUP_CH consecutive leaf pairs of the warp's chunk, so its target leaf
+    // changes (and its partial sums are flushed) only where the list moves to the next target
+    const int64_t wch = (int64_t)G * P2P_GROUP_CH;
+    for (int64_t w0 = e_begin + warp * wch; w0 < e_end; w0 += nwarps * wch) {
+        const int64_t e0 = w0 + (int64_t)grp * P2P_GROUP_CH;
+        const int64_t e1 = min(e0 + P2P_GROUP_CH, e_end);
         int32_t cur = -1, it0 = 0, it1 = 0;
         bool v0 = false, v1 = false;
         float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, tq0 = 0.f, tq1 = 0.f;
         float hi0 = 0.f, lo0 = 0.f, hi1 = 0.f, lo1 = 0.f;
-        for (int64_t e = e0 + grp; e < e1; e += G) {
+        for (int64_t e = e0; e < e1; e++) {
             const int32_t tl = stgt[e] - base;
             if (tl != cur) {
                 if (v0) { atomicAdd(&nhi[it0], hi0); atomicAdd(&nlo[it0], lo0); }
