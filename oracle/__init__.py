@@ -12,6 +12,8 @@ multiply-add is fused); this module only compiles it and marshals numpy arrays:
 * :func:`lists`      -- strong/weak connectivity with the theta-criterion (Section 4, Crit. 2.1)
 * :func:`fmm`        -- the whole method, P2M .. P2P, unscaled textbook expansions (Section 5)
 * :func:`direct`     -- the O(N^2) definition, Eq. (1.1)
+* :func:`fmm_field`, :func:`direct_field` -- the complex field -q_j / (z_i - z_j) of Section 5's
+  first experiment, by the method and by direct summation
 * :func:`p2m`, :func:`m2m`, :func:`m2l`, :func:`l2l`, :func:`l2p`, :func:`m2p` -- one operator
   at a time, for the pins.
 * :mod:`oracle.mlp`  -- FP64 reference of the parameter-selector network.
@@ -83,6 +85,10 @@ def _load():
         lib.orc_direct.argtypes = [i64, vp, vp, vp, i64, vp, vp, i32]
         lib.orc_fmm.restype = i32
         lib.orc_fmm.argtypes = [i64, vp, vp, vp, i32, i32, dbl, vp, vp, vp]
+        lib.orc_fmm_field.restype = i32
+        lib.orc_fmm_field.argtypes = [i64, vp, vp, vp, i32, i32, dbl, vp, vp]
+        lib.orc_direct_field.restype = None
+        lib.orc_direct_field.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp, i32]
         lib.orc_mlp_nparams.restype = ctypes.c_long
         lib.orc_mlp_nparams.argtypes = []
         lib.orc_mlp_forward.restype = None
@@ -192,6 +198,28 @@ def direct(x, y, q, targets=None, nthreads: int = 0):
     phi = np.empty(t.shape[0], np.float64)
     _load().orc_direct(n, _ptr(x), _ptr(y), _ptr(q), t.shape[0], _ptr(t), _ptr(phi), int(nthreads))
     return phi
+
+
+def fmm_field(x, y, q, L: int, p: int, theta: float):
+    """The complex field F_i = sum_{j != i} -q_j / (z_i - z_j) by the method (Section 5's first
+    experiment); returns a complex array in input order."""
+    x, y, q = _f64(x), _f64(y), _f64(q)
+    n = x.shape[0]
+    fre, fim = np.empty(n), np.empty(n)
+    rc = _load().orc_fmm_field(n, _ptr(x), _ptr(y), _ptr(q), int(L), int(p), float(theta), _ptr(fre), _ptr(fim))
+    if rc:
+        raise OracleError(f"orc_fmm_field returned {rc}")
+    return fre + 1j * fim
+
+
+def direct_field(x, y, q, targets=None, nthreads: int = 0):
+    """The same field by direct summation at the given input indices (all points by default)."""
+    x, y, q = _f64(x), _f64(y), _f64(q)
+    n = x.shape[0]
+    t = np.arange(n, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, np.int64)
+    fre, fim = np.empty(t.shape[0]), np.empty(t.shape[0])
+    _load().orc_direct_field(n, _ptr(x), _ptr(y), _ptr(q), t.shape[0], _ptr(t), _ptr(fre), _ptr(fim), int(nthreads))
+    return fre + 1j * fim
 
 
 def _cvec(a, p):

@@ -400,6 +400,14 @@ static double l2p(const cplx* b, cplx dz, int p)
     return creal(s);
 }
 
+/* Derivative of the local expansion: sum_{l >= 1} l b_l dz^(l-1), dz = z - c. */
+static cplx l2p_deriv(const cplx* b, cplx dz, int p)
+{
+    cplx s = 0, pw = 1.0;
+    for (int l = 1; l <= p; l++) { s += (double)l * b[l] * pw; pw *= dz; }
+    return s;
+}
+
 /* M2P (test helper only): Re[a_0 log(dz) + sum_k a_k dz^{-k}], dz = z - c. */
 static double m2p(const cplx* a, cplx dz, int p)
 {
@@ -495,6 +503,33 @@ void orc_direct(int64_t n, const double* x, const double* y, const double* q,
 }
 
 /* ------------------------------------------------------------------------------------------
+ * Direct summation of the complex field of Section 5's first experiment,
+ * G(z_i, z_j) = -q_j / (z_i - z_j):  F[t] = sum_{j != tgt[t]} -q_j / (z_tgt - z_j), skipping
+ * coincident points.  fre/fim receive the real and imaginary parts.
+ * ------------------------------------------------------------------------------------------ */
+void orc_direct_field(int64_t n, const double* x, const double* y, const double* q,
+                      int64_t m, const int64_t* tgt, double* fre, double* fim, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t t = 0; t < m; t++) {
+        int64_t i = tgt[t];
+        cplx s = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double dx = x[i] - x[j], dy = y[i] - y[j];
+            if (dx == 0.0 && dy == 0.0) continue;
+            s -= q[j] / (dx + I * dy);
+        }
+        fre[t] = creal(s);
+        fim[t] = cimag(s);
+    }
+    (void)nthreads;
+}
+
+/* ------------------------------------------------------------------------------------------
  * The full method (Section 4):  tree -> connectivity -> upward pass (P2M at the finest level,
  * M2M towards the root) -> M2L along the weak lists of every level -> downward pass (L2L) ->
  * L2P plus direct evaluation along the strong lists of the finest level.  phi is written in
@@ -503,8 +538,9 @@ void orc_direct(int64_t n, const double* x, const double* y, const double* q,
  * each box centre; a box's local expansion is complete, i.e. includes its ancestors' shifts).
  * Returns 0 or a negative code as orc_tree.
  * ------------------------------------------------------------------------------------------ */
-int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L, int p,
-            double theta, double* phi, double* mpole_out, double* local_out)
+static int fmm_core(int64_t n, const double* x, const double* y, const double* q, int L, int p,
+                    double theta, double* phi, double* fre, double* fim, double* mpole_out,
+                    double* local_out)
 {
     if (p < 0 || p > ORC_PMAX || !(theta > 0.0 && theta < 1.0)) return -1;
     int64_t nbox = orc_nbox(L), nleaf = ((int64_t)1) << (2 * L);
@@ -558,6 +594,23 @@ int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L,
         int64_t g = lbase + b;
         for (int64_t t = lb[b]; t < lb[b + 1]; t++) {
             int64_t i = perm[t];
+            if (fre) {
+                /* the field: minus the derivative of the local expansion, minus the near sum */
+                cplx f = -l2p_deriv(Lc + g * P, (x[i] + I * y[i]) - CEN(g), p);
+                for (int64_t e = li->soff[g]; e < li->soff[g + 1]; e++) {
+                    int64_t sb = li->sidx[e];
+                    for (int64_t u = lb[sb]; u < lb[sb + 1]; u++) {
+                        int64_t j = perm[u];
+                        if (j == i) continue;
+                        double dx = x[i] - x[j], dy = y[i] - y[j];
+                        if (dx == 0.0 && dy == 0.0) continue;
+                        f -= q[j] / (dx + I * dy);
+                    }
+                }
+                fre[i] = creal(f);
+                fim[i] = cimag(f);
+                continue;
+            }
             double s = l2p(Lc + g * P, (x[i] + I * y[i]) - CEN(g), p);
             for (int64_t e = li->soff[g]; e < li->soff[g + 1]; e++) {
                 int64_t sb = li->sidx[e];
@@ -580,4 +633,19 @@ int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L,
     free(M); free(Lc); free(cen); free(rad); free(perm); free(rects); free(lb);
     orc_lists_free(li);
     return 0;
+}
+
+int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L, int p,
+            double theta, double* phi, double* mpole_out, double* local_out)
+{
+    return fmm_core(n, x, y, q, L, p, theta, phi, NULL, NULL, mpole_out, local_out);
+}
+
+/* The method for the complex field G(z_i, z_j) = -q_j / (z_i - z_j) (Section 5): the same tree,
+ * lists and expansions; at the finest level minus the derivative of the local expansion plus the
+ * direct field along the strong lists.  fre/fim in input order. */
+int orc_fmm_field(int64_t n, const double* x, const double* y, const double* q, int L, int p,
+                  double theta, double* fre, double* fim)
+{
+    return fmm_core(n, x, y, q, L, p, theta, NULL, fre, fim, NULL, NULL);
 }
