@@ -45,7 +45,8 @@ typedef enum {
     FMM_ERR_CUDA = -5,       /* a CUDA runtime call failed                                  */
     FMM_ERR_CAPACITY = -6,   /* interaction lists exceeded the capacity of the fmm_lists   */
     FMM_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up                          */
-    FMM_ERR_STATE = -8       /* handle used out of order (e.g. lists of another tree)       */
+    FMM_ERR_STATE = -8,      /* handle used out of order (e.g. lists of another tree)       */
+    FMM_ERR_DEGENERATE = -9  /* field only: a leaf box of zero size (its points all coincide) */
 } fmm_status;
 
 typedef enum {
@@ -298,6 +299,23 @@ int fmm_mlp_train_step(fmm_mlp m, const float* X, const int32_t* labels, int B, 
 /* The selector's choice for B feature vectors (device): levels_p[B][2] = (levels, p) of the most
  * probable class among those with 4^levels <= N (device int32). */
 int fmm_select_params(fmm_mlp m, const float* features, int B, int32_t* levels_p, void* stream);
+
+/* The complex field of Section 5's first experiment, G(z_i, z_j) = -q_j / (z_i - z_j):
+ *     F_i = sum_{j != i} -q_j / (z_i - z_j)   (Re F = -dphi/dx, Im F = +dphi/dy of Eq. (1.1))
+ * with the same tree, lists and expansions as fmm_evaluate: the far part is minus the derivative
+ * of the local expansion, the near part the direct sum along the strong lists of the finest
+ * level; coincident points contribute nothing.  fre[n], fim[n] (binary64, device) in INPUT order.
+ * Modes and the tolerance rule as for fmm_evaluate; the binary32 near field keeps the
+ * coordinates as float-float offsets from the leaf centres and handles leaves of up to 64
+ * points (larger leaves take the binary64 path).  A leaf box of zero size (all its points
+ * coincide, with at least two levels) has no scaled derivative: the device status then reports
+ * FMM_ERR_DEGENERATE. */
+int fmm_evaluate_field(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* fre,
+                       double* fim, void* stream);
+
+/* The same field by direct summation in binary64 at m target input indices (int64, device). */
+int fmm_direct_field(const double* x, const double* y, const double* q, int64_t n,
+                     const int64_t* targets, int64_t m, double* fre, double* fim, void* stream);
 
 /* Eq. (1.1) by direct summation in binary64 at m target input indices targets[m] (int64,
  * device) over all n sources; phi[m] (device).  Coincident distinct points contribute 0. */

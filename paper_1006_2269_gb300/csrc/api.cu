@@ -95,7 +95,8 @@ void free_tree(fmm_tree t)
     void* ptrs[] = {t->rects, t->centers, t->radii, t->rad32, t->cen_hi, t->cen_lo, t->perm, t->leaf_begin,
                     t->leaf_of, t->xs, t->ys, t->dxf, t->dyf, t->keys, t->vals, t->rs_counts,
                     t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->node_off, t->segs, t->status,
-                    t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf, t->dinst, t->Lf0lo};
+                    t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf, t->dinst, t->Lf0lo,
+                    t->pkf, t->qf, t->accf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     sched_free_all(t);
@@ -119,6 +120,8 @@ int status_to_code(int32_t st)
     if (st & ST_NONFINITE) return fail(FMM_ERR_NONFINITE, "non-finite coordinate or strength");
     if (st & ST_CAPACITY) return fail(FMM_ERR_CAPACITY, "interaction lists exceed the capacity");
     if (st & ST_TIMEOUT) return fail(FMM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & ST_DEGENERATE)
+        return fail(FMM_ERR_DEGENERATE, "a leaf box of zero size: the far part of the field is undefined there");
     if (st & ST_ARG) return fail(FMM_ERR_STATE, "inconsistent internal state detected on the device");
     return FMM_OK;
 }
@@ -482,6 +485,27 @@ int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks)
     t->tune_m2l_blocks = m2l_blocks;
     t->tune_p2p_blocks = p2p_blocks;
     return sched_tuned(t);
+}
+
+int fmm_evaluate_field(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* fre,
+                       double* fim, void* stream)
+{
+    if (!t || !l || !q || !prm || !fre || !fim) return fail(FMM_ERR_ARG, "NULL argument");
+    if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
+    if (!t->built || !l->built) return fail(FMM_ERR_STATE, "tree or lists not built");
+    if (prm->p < 0 || prm->p > 40) return fail(FMM_ERR_ARG, "p = %d outside [0, 40]", prm->p);
+    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED)
+        return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
+    GUARD(t->dev);
+    return evaluate_field(t, l, q, *prm, fre, fim, (cudaStream_t)stream);
+}
+
+int fmm_direct_field(const double* x, const double* y, const double* q, int64_t n, const int64_t* targets,
+                     int64_t m, double* fre, double* fim, void* stream)
+{
+    if (!x || !y || !q || (m > 0 && (!targets || !fre || !fim))) return fail(FMM_ERR_ARG, "NULL argument");
+    if (n < 1 || m < 0) return fail(FMM_ERR_ARG, "bad sizes n = %lld, m = %lld", (long long)n, (long long)m);
+    return direct_field(x, y, q, n, targets, m, fre, fim, (cudaStream_t)stream);
 }
 
 int fmm_direct(const double* x, const double* y, const double* q, int64_t n, const int64_t* targets,

@@ -9,7 +9,7 @@
 namespace fmm {
 
 // ---- device status word bits (set by kernels with atomicOr, read by fmm_sync_status) ----
-enum : int32_t { ST_NONFINITE = 1, ST_CAPACITY = 2, ST_TIMEOUT = 4, ST_ARG = 8 };
+enum : int32_t { ST_NONFINITE = 1, ST_CAPACITY = 2, ST_TIMEOUT = 4, ST_ARG = 8, ST_DEGENERATE = 16 };
 
 // ---- error reporting (thread-local message) ----
 int fail(int code, const char* fmt, ...);
@@ -215,7 +215,11 @@ struct fmm_tree_s {
     void* pk64 = nullptr;   // [n] double4 (x, y, q, 0) in canonical order (binary64 path)
     void* pk32 = nullptr;   // [n] float4 (x - c_leaf, y - c_leaf, q, 0) (binary32 path)
     double* acc = nullptr;  // [n] binary64 potential accumulator in canonical order
-    float* acc32 = nullptr; // [4n] binary32 far field hi and lo, near field hi and lo (canonical order)
+    float* acc32 = nullptr; // [6n] binary32 accumulators: potential far hi, lo, near hi, lo; the field
+                            // far re, im, near re hi, lo, im hi, lo (canonical order)
+    void* pkf = nullptr;    // [n] float4 float-float offsets from the leaf centre (binary32 field)
+    float* qf = nullptr;    // [n] strengths in canonical order (binary32 field)
+    double* accf = nullptr; // [2n] binary64 field accumulator (re, im)
     float* Lf0lo = nullptr; // [nbox] low part of Re b_0 of the binary32 locals (float-float)
 
     // launch tuning (set by fmm_autotune; 0 = defaults): total blocks of the M2L and near-field
@@ -279,6 +283,10 @@ int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int
 // expand.cu
 int evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,
              cudaStream_t s);
+int evaluate_field(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* fre,
+                   double* fim, cudaStream_t s);
+int direct_field(const double* x, const double* y, const double* q, int64_t n, const int64_t* tgt,
+                 int64_t m, double* fre, double* fim, cudaStream_t s);
 int direct(const double* x, const double* y, const double* q, int64_t n, const int64_t* tgt,
            int64_t m, double* phi, cudaStream_t s);
 int autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,

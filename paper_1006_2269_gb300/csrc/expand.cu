@@ -1098,6 +1098,351 @@ __global__ void k_direct(const double* __restrict__ x, const double* __restrict_
     }
 }
 
+
+// ---- the complex field of Section 5's first experiment: F_i = sum_{j != i} -q_j / (z_i - z_j) ----
+// Far part: minus the derivative of the local expansion, -sum_{l >= 1} l b~_l w^(l-1) / rho with
+// w = (z - c) / rho.  Near part: the direct sum along the finest-level strong lists.
+
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// The binary32 near field works on float-float offsets from the leaf centre (x - c = hi + lo,
+// each binary32): a difference of two nearby points then keeps its relative accuracy, so no pair
+// needs binary64.  pkf = (x_hi, y_hi, x_lo, y_lo), qf = q, canonical order.
+__global__ void k_pack_field32(Sched sc, const Inst* __restrict__ I, const double* __restrict__ q,
+                               const int32_t* __restrict__ perm, const double* __restrict__ xs,
+                               const double* __restrict__ ys, const float* __restrict__ dxf,
+                               const float* __restrict__ dyf, const int32_t* __restrict__ cleaf,
+                               const double* __restrict__ cen, float4* __restrict__ pkf, float* __restrict__ qf)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    q += S.p0;
+    perm += S.p0;
+    xs += S.p0;
+    ys += S.p0;
+    dxf += S.p0;
+    dyf += S.p0;
+    cleaf += S.p0;
+    pkf += S.p0;
+    qf += S.p0;
+    cen += 2 * S.b0;
+    const int64_t base = level_base(S.L);
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
+        const int64_t g = base + cleaf[i];
+        const float hx = dxf[i], hy = dyf[i];
+        const float lx = __double2float_rn(__dsub_rn(__dsub_rn(xs[i], cen[2 * g]), (double)hx));
+        const float ly = __double2float_rn(__dsub_rn(__dsub_rn(ys[i], cen[2 * g + 1]), (double)hy));
+        pkf[i] = make_float4(hx, hy, lx, ly);
+        qf[i] = (float)q[perm[i]];
+    }
+}
+
+// far part of the field; a zero-size target leaf (all its points coincide) has no scaled
+// derivative: the status word records it (FMM_ERR_DEGENERATE)
+template <typename T>
+__global__ void k_l2p_field(Sched sc, const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ cleaf,
+                            const Pk<T>* __restrict__ pk, Geo<T> geo, const cx<T>* __restrict__ Le,
+                            T* __restrict__ fre, T* __restrict__ fim, int32_t* status)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const int L = S.L;
+    cleaf += S.p0;
+    pk += S.p0;
+    fre += S.p0;
+    fim += S.p0;
+    geo = geo.shift(S.b0);
+    Le += S.b0 * PS;
+    bool degenerate = false;
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
+        const int64_t g = level_base(L) + cleaf[i];
+        const Pk<T> p = pk[i];
+        const T rho = geo.radius(g);
+        cx<T> f = {0, 0};
+        if (rho > (T)0) {
+            const cx<T> w = geo.local(g, p.x, p.y);
+            const cx<T>* B = Le + g * PS;
+            cx<T> h = {0, 0};
+            for (int l = P - 1; l >= 1; l--) h = cfma(h, w, cscale(B[l], (T)l));
+            f = cscale(h, (T)-1 / rho);
+        } else if (L >= 2) {
+            degenerate = true;
+        }
+        fre[i] = f.re;
+        fim[i] = f.im;
+    }
+    if (__any_sync(0xffffffffu, degenerate) && (threadIdx.x & 31) == 0) atomicOr(status, ST_DEGENERATE);
+}
+
+// binary32 near field: the layout of k_p2p_f32 (lane groups on a leaf pair, two targets per lane,
+// a run of consecutive leaf pairs per group), with float-float offsets and a binary32 reciprocal;
+// coincident points (r = 0, including j = i) contribute nothing.  Accumulators: float-float per
+// component, fhr/fhl (real hi, lo) and fir/fil (imaginary hi, lo).
+__global__ void __launch_bounds__(256) k_p2p_field_f32(Sched sc, const Inst* __restrict__ I,
+                                                       const LInst* __restrict__ LIs,
+                                                       const int32_t* __restrict__ soff,
+                                                       const int32_t* __restrict__ sidx,
+                                                       const int32_t* __restrict__ stgt,
+                                                       const int32_t* __restrict__ lb,
+                                                       const float4* __restrict__ pkf, const float* __restrict__ qf,
+                                                       const float* __restrict__ chi, const float* __restrict__ clo,
+                                                       float* __restrict__ fhr, float* __restrict__ flr,
+                                                       float* __restrict__ fhi, float* __restrict__ fli)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
+    const int L = S.L;
+    const int64_t scap = TL.scap;
+    soff += S.o0;
+    sidx += TL.s0;
+    stgt += TL.s0;
+    lb += S.lb0;
+    pkf += S.p0;
+    qf += S.p0;
+    chi += 2 * S.b0;
+    clo += 2 * S.b0;
+    fhr += S.p0;
+    flr += S.p0;
+    fhi += S.p0;
+    fli += S.p0;
+    const int64_t maxleaf = (S.n + level_size(L) - 1) / level_size(L);
+    if (maxleaf > 64) return;  // left to the general kernel
+    int gsl = 1;
+    while (2 * gsl < maxleaf) gsl <<= 1;
+    const int lane = threadIdx.x & 31, G = 32 / gsl, grp = lane / gsl, li = lane - grp * gsl;
+    const int32_t base = (int32_t)level_base(L);
+    const int64_t e_begin = min((int64_t)soff[base], scap);
+    const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
+    const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
+    const int64_t wch = (int64_t)G * P2P_GROUP_CH;
+    for (int64_t w0 = e_begin + warp * wch; w0 < e_end; w0 += nwarps * wch) {
+        const int64_t e0 = w0 + (int64_t)grp * P2P_GROUP_CH;
+        const int64_t e1 = min(e0 + P2P_GROUP_CH, e_end);
+        int32_t cur = -1, it0 = 0, it1 = 0;
+        bool v0 = false, v1 = false;
+        float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
+        float ar = 0.f, arl = 0.f, ai = 0.f, ail = 0.f, br = 0.f, brl = 0.f, bi = 0.f, bil = 0.f;
+        auto flush = [&]() {
+            if (v0) {
+                atomicAdd(&fhr[it0], ar);
+                atomicAdd(&flr[it0], arl);
+                atomicAdd(&fhi[it0], ai);
+                atomicAdd(&fli[it0], ail);
+            }
+            if (v1) {
+                atomicAdd(&fhr[it1], br);
+                atomicAdd(&flr[it1], brl);
+                atomicAdd(&fhi[it1], bi);
+                atomicAdd(&fli[it1], bil);
+            }
+        };
+        for (int64_t e = e0; e < e1; e++) {
+            const int32_t tl = stgt[e] - base;
+            if (tl != cur) {
+                flush();
+                cur = tl;
+                const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0;
+                it0 = t0 + li;
+                it1 = t0 + li + gsl;
+                v0 = li < nt;
+                v1 = li + gsl < nt;
+                ar = arl = ai = ail = br = brl = bi = bil = 0.f;
+                if (v0) ta = pkf[it0];
+                if (v1) tb = pkf[it1];
+            }
+            if (!v0) continue;  // v1 implies v0
+            const int32_t sl = sidx[e];
+            const int32_t s0 = lb[sl], ns = lb[sl + 1] - s0;
+            const int32_t sg = base + sl, tg = base + tl;
+            // centre difference c_s - c_t as float-float (two-sum of the high parts)
+            float oxh, oxl, oyh, oyl;
+            {
+                const float a = chi[2 * sg], b = -chi[2 * tg];
+                oxh = a + b;
+                const float bb = oxh - a;
+                oxl = ((a - (oxh - bb)) + (b - bb)) + (clo[2 * sg] - clo[2 * tg]);
+                const float c = chi[2 * sg + 1], d = -chi[2 * tg + 1];
+                oyh = c + d;
+                const float dd = oyh - c;
+                oyl = ((c - (oyh - dd)) + (d - dd)) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
+            }
+            // targets in the source leaf's frame, float-float
+            auto to_frame = [](float h, float l, float oh, float ol, float& rh, float& rl) {
+                const float b = -oh;
+                rh = h + b;
+                const float bb = rh - h;
+                rl = ((h - (rh - bb)) + (b - bb)) + (l - ol);
+            };
+            float xah, xal, yah, yal, xbh, xbl, ybh, ybl;
+            to_frame(ta.x, ta.z, oxh, oxl, xah, xal);
+            to_frame(ta.y, ta.w, oyh, oyl, yah, yal);
+            to_frame(tb.x, tb.z, oxh, oxl, xbh, xbl);
+            to_frame(tb.y, tb.w, oyh, oyl, ybh, ybl);
+            float pra = 0.f, pia = 0.f, prb = 0.f, pib = 0.f;
+#pragma unroll 4
+            for (int32_t j = 0; j < ns; j++) {
+                const float4 sp = pkf[s0 + j];
+                const float q = qf[s0 + j];
+                const float dxa = (xah - sp.x) + (xal - sp.z), dya = (yah - sp.y) + (yal - sp.w);
+                const float dxb = (xbh - sp.x) + (xbl - sp.z), dyb = (ybh - sp.y) + (ybl - sp.w);
+                const float ra = dxa * dxa + dya * dya, rb = dxb * dxb + dyb * dyb;
+                const float sa = ra > 1e-36f ? q * rcp_fast(ra) : 0.f;
+                const float sb = rb > 1e-36f ? q * rcp_fast(rb) : 0.f;
+                pra -= sa * dxa;  // -q / dz = -q (dx - i dy) / r^2
+                pia += sa * dya;
+                prb -= sb * dxb;
+                pib += sb * dyb;
+            }
+            two_sum(ar, arl, pra);
+            two_sum(ai, ail, pia);
+            if (v1) {
+                two_sum(br, brl, prb);
+                two_sum(bi, bil, pib);
+            }
+        }
+        flush();
+    }
+}
+
+// binary64 near field: one warp per leaf pair, one lane per target
+__global__ void __launch_bounds__(256) k_p2p_field64(Sched sc, const Inst* __restrict__ I,
+                                                     const LInst* __restrict__ LIs,
+                                                     const int32_t* __restrict__ soff,
+                                                     const int32_t* __restrict__ sidx,
+                                                     const int32_t* __restrict__ stgt,
+                                                     const int32_t* __restrict__ lb,
+                                                     const Pk<double>* __restrict__ pk,
+                                                     double* __restrict__ fre, double* __restrict__ fim)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
+    const int L = S.L;
+    const int64_t scap = TL.scap;
+    soff += S.o0;
+    sidx += TL.s0;
+    stgt += TL.s0;
+    lb += S.lb0;
+    pk += S.p0;
+    fre += S.p0;
+    fim += S.p0;
+    const int lane = threadIdx.x & 31;
+    const int64_t base = level_base(L);
+    const int64_t e_begin = min((int64_t)soff[base], scap);
+    const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
+    const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
+    for (int64_t e = e_begin + warp; e < e_end; e += nwarps) {
+        const int64_t tl = stgt[e] - base, sl = sidx[e];
+        const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0, s0 = lb[sl], ns = lb[sl + 1] - s0;
+        for (int tc = lane; tc < nt; tc += 32) {
+            const Pk<double> p = pk[t0 + tc];
+            double sr = 0.0, si = 0.0;
+            for (int32_t j = 0; j < ns; j++) {
+                const Pk<double> sp = pk[s0 + j];
+                const double dx = p.x - sp.x, dy = p.y - sp.y;
+                const double r2 = dx * dx + dy * dy;
+                if (r2 > 0.0) {
+                    const double s_ = sp.q / r2;
+                    sr -= s_ * dx;
+                    si += s_ * dy;
+                }
+            }
+            atomicAdd(&fre[t0 + tc], sr);
+            atomicAdd(&fim[t0 + tc], si);
+        }
+    }
+}
+
+__global__ void k_unpermute_field(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+                                  const double* __restrict__ ar, const double* __restrict__ ai,
+                                  double* __restrict__ fre, double* __restrict__ fim)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    perm += S.p0;
+    ar += S.p0;
+    ai += S.p0;
+    fre += S.p0;
+    fim += S.p0;
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
+        fre[perm[i]] = ar[i];
+        fim[perm[i]] = ai[i];
+    }
+}
+
+__global__ void k_combine_field32(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+                                  const float* __restrict__ far_r, const float* __restrict__ far_i,
+                                  const float* __restrict__ fhr, const float* __restrict__ flr,
+                                  const float* __restrict__ fhi, const float* __restrict__ fli,
+                                  double* __restrict__ fre, double* __restrict__ fim)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    perm += S.p0;
+    far_r += S.p0;
+    far_i += S.p0;
+    fhr += S.p0;
+    flr += S.p0;
+    fhi += S.p0;
+    fli += S.p0;
+    fre += S.p0;
+    fim += S.p0;
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
+        fre[perm[i]] = (double)far_r[i] + ((double)fhr[i] + (double)flr[i]);
+        fim[perm[i]] = (double)far_i[i] + ((double)fhi[i] + (double)fli[i]);
+    }
+}
+
+// Direct field at sampled targets (binary64), the judge of the field's error.
+__global__ void k_direct_field(const double* __restrict__ x, const double* __restrict__ y,
+                               const double* __restrict__ q, int64_t n, const int64_t* __restrict__ tgt,
+                               double* __restrict__ fre, double* __restrict__ fim)
+{
+    __shared__ double red[2][32];
+    const int64_t i = tgt[blockIdx.x];
+    const double xi = x[i], yi = y[i];
+    double sr = 0, si = 0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double dx = xi - x[j], dy = yi - y[j];
+        const double r2 = dx * dx + dy * dy;
+        if (j != i && r2 > 0.0) {
+            sr -= q[j] * dx / r2;
+            si += q[j] * dy / r2;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = sr;
+        red[1][threadIdx.x >> 5] = si;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        sr = threadIdx.x < (blockDim.x >> 5) ? red[0][threadIdx.x] : 0.0;
+        si = threadIdx.x < (blockDim.x >> 5) ? red[1][threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (threadIdx.x == 0) {
+            fre[blockIdx.x] = sr;
+            fim[blockIdx.x] = si;
+        }
+    }
+}
+
 // ---- per-device constant tables ----
 std::mutex g_tab_mutex;
 bool g_tab_ready[128] = {};
@@ -1139,7 +1484,7 @@ int alloc_ws(fmm_tree t, int PS, bool f64)
 {
     if (f64 && !t->acc && cudaMalloc((void**)&t->acc, 8 * (size_t)t->n) != cudaSuccess)
         return fail(FMM_ERR_OOM, "accumulator");
-    if (!f64 && !t->acc32 && cudaMalloc((void**)&t->acc32, 4 * 4 * (size_t)t->n) != cudaSuccess)
+    if (!f64 && !t->acc32 && cudaMalloc((void**)&t->acc32, 6 * 4 * (size_t)t->n) != cudaSuccess)
         return fail(FMM_ERR_OOM, "accumulator");
     if (!f64 && !t->Lf0lo && cudaMalloc((void**)&t->Lf0lo, 4 * (size_t)t->nbox) != cudaSuccess)
         return fail(FMM_ERR_OOM, "local expansion low parts");
@@ -1200,13 +1545,23 @@ int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<double> geo, const
     return 0;
 }
 
+// The whole evaluation: the potential into phi, or (fim != nullptr) the complex field into
+// phi (real part) and fim (imaginary part).
 template <typename T>
-int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStream_t s)
+int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStream_t s, double* fim = nullptr)
 {
     const bool f64 = sizeof(T) == 8;
+    const bool field = fim != nullptr;
     const int PS = (P + 1) & ~1;
     int rc = alloc_ws(t, PS, f64);
     if (rc) return rc;
+    if (field) {
+        if (f64 && !t->accf && cudaMalloc((void**)&t->accf, 16 * (size_t)t->n) != cudaSuccess)
+            return fail(FMM_ERR_OOM, "field accumulator");
+        if (!f64 && !t->pkf && (cudaMalloc(&t->pkf, 16 * (size_t)t->n) != cudaSuccess ||
+                                cudaMalloc((void**)&t->qf, 4 * (size_t)t->n) != cudaSuccess))
+            return fail(FMM_ERR_OOM, "field workspace");
+    }
     cx<T>* Me = (cx<T>*)(f64 ? t->Me : t->Mf);
     cx<T>* Le = (cx<T>*)(f64 ? t->Le : t->Lf);
     Pk<T>* pk = (Pk<T>*)(f64 ? t->pk64 : t->pk32);
@@ -1279,7 +1634,37 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             FMM_LAUNCH_CHECK("evaluate: L2L");
         }
     }
-    {
+    if (field) {
+        StageScope scope(FMM_STAGE_LEAF, s);
+        const unsigned gp2p = (unsigned)t->s_p2p.blocks;
+        const Sched sp2p = t->s_p2p.d;
+        if constexpr (sizeof(T) == 4) {
+            float* fr = t->acc32 + 0 * n;
+            float* fi = t->acc32 + 1 * n;
+            float* hr = t->acc32 + 2 * n;
+            float* lr = t->acc32 + 3 * n;
+            float* hi = t->acc32 + 4 * n;
+            float* lo = t->acc32 + 5 * n;
+            FMM_CUDA(cudaMemsetAsync(hr, 0, 4 * 4 * (size_t)n, s));
+            k_pack_field32<<<gpts, 256, 0, s>>>(spts, I, q, t->perm, t->xs, t->ys, t->dxf, t->dyf, t->cleaf,
+                                                t->centers, (float4*)t->pkf, t->qf); note_launch();
+            k_l2p_field<float><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, fr, fi, t->status);
+            note_launch();
+            k_p2p_field_f32<<<gp2p, 256, 0, s>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin,
+                                                 (const float4*)t->pkf, t->qf, t->cen_hi, t->cen_lo, hr, lr,
+                                                 hi, lo); note_launch();
+            k_combine_field32<<<gpts, 256, 0, s>>>(spts, I, t->perm, fr, fi, hr, lr, hi, lo, phi, fim);
+            note_launch();
+        } else {
+            k_l2p_field<double><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->accf,
+                                                     t->accf + n, t->status); note_launch();
+            k_p2p_field64<<<gp2p, 256, 0, s>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin,
+                                               (const Pk<double>*)pk, t->accf, t->accf + n); note_launch();
+            k_unpermute_field<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->accf, t->accf + n, phi, fim);
+            note_launch();
+        }
+        FMM_LAUNCH_CHECK("evaluate: field");
+    } else {
         StageScope scope(FMM_STAGE_LEAF, s);
         if (!f64) FMM_CUDA(cudaMemsetAsync(nhi, 0, 2 * 4 * (size_t)n, s));
         k_l2p<T><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo,
@@ -1402,6 +1787,36 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     }
     if (m2l_blocks) *m2l_blocks = t->tune_m2l_blocks;
     if (p2p_blocks) *p2p_blocks = t->tune_p2p_blocks;
+    return 0;
+}
+
+int evaluate_field(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, double* fre,
+                   double* fim, cudaStream_t s)
+{
+    int rc = ensure_tables();
+    if (rc) return rc;
+    const int P = prm.p + 1;
+    int64_t maxleaf = 0;
+    for (int i = 0; i < t->n_inst; i++) {
+        const Inst& S = t->hinst[i];
+        maxleaf = std::max<int64_t>(maxleaf, (S.n + level_size(S.L) - 1) / level_size(S.L));
+    }
+    // the binary32 near-field kernel holds up to 64 targets per leaf; larger leaves, tolerances
+    // below the binary32 floor and binary64 mode take the binary64 path
+    const bool f64 = prm.mode == FMM_MODE_FP64 || (prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR) || maxleaf > 64;
+    if (f64) return run<double>(t, li, q, P, fre, s, fim);
+    return run<float>(t, li, q, P, fre, s, fim);
+}
+
+int direct_field(const double* x, const double* y, const double* q, int64_t n, const int64_t* tgt,
+                 int64_t m, double* fre, double* fim, cudaStream_t s)
+{
+    if (m <= 0) return 0;
+    for (int64_t off = 0; off < m; off += 65535) {
+        const int64_t c = std::min<int64_t>(65535, m - off);
+        k_direct_field<<<(unsigned)c, 256, 0, s>>>(x, y, q, n, tgt + off, fre + off, fim + off); note_launch();
+    }
+    FMM_LAUNCH_CHECK("direct field");
     return 0;
 }
 

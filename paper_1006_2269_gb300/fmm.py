@@ -28,6 +28,7 @@ FMM_ERR_CUDA = -5
 FMM_ERR_CAPACITY = -6
 FMM_ERR_TIMEOUT = -7
 FMM_ERR_STATE = -8
+FMM_ERR_DEGENERATE = -9
 
 FMM_MODE_FP64 = 0
 FMM_MODE_MIXED = 1
@@ -92,6 +93,8 @@ def load_library(path: str = LIB_PATH):
             "fmm_lists_destroy": (None, [vp]),
             "fmm_evaluate": (i32, [vp, vp, vp, ctypes.POINTER(fmm_params), vp, vp]),
             "fmm_direct": (i32, [vp, vp, vp, i64, vp, i64, vp, vp]),
+            "fmm_evaluate_field": (i32, [vp, vp, vp, ctypes.POINTER(fmm_params), vp, vp, vp]),
+            "fmm_direct_field": (i32, [vp, vp, vp, i64, vp, i64, vp, vp, vp]),
             "fmm_sync_status": (i32, [vp, vp, vp]),
             "fmm_build_tree_noalloc": (i32, [vp, vp, i64, i32, vp, vp, vp, vp, vp]),
             "fmm_profile_enable": (i32, [i32]),
@@ -379,6 +382,27 @@ def fmm_get_m2l_kernel(tree) -> int:
     return rc
 
 
+def fmm_evaluate_field(tree, lists, q: torch.Tensor, p: int, mode: int, fre: torch.Tensor, fim: torch.Tensor,
+                       tol: float = 1e-6, stream=None):
+    """The complex field F_i = sum_{j != i} -q_j / (z_i - z_j): real part into fre, imaginary
+    part into fim (CUDA float64, input order)."""
+    n = fmm_tree_info(tree)[0]
+    prm = fmm_params(int(p), int(mode), float(tol))
+    _check(load_library().fmm_evaluate_field(tree, lists, _dev(q, torch.float64, n, "q"), ctypes.byref(prm),
+                                             _dev(fre, torch.float64, n, "fre"), _dev(fim, torch.float64, n, "fim"),
+                                             _stream(stream)))
+
+
+def fmm_direct_field(x, y, q, targets, fre, fim, stream=None):
+    n = x.numel()
+    m = targets.numel()
+    _check(load_library().fmm_direct_field(_dev(x, torch.float64, n, "x"), _dev(y, torch.float64, n, "y"),
+                                           _dev(q, torch.float64, n, "q"), n,
+                                           _dev(targets, torch.int64, m, "targets"), m,
+                                           _dev(fre, torch.float64, m, "fre"), _dev(fim, torch.float64, m, "fim"),
+                                           _stream(stream)))
+
+
 def fmm_direct(x, y, q, targets, phi, stream=None):
     n = x.numel()
     m = targets.numel()
@@ -477,6 +501,16 @@ class FMM:
             fmm_sync_status(self.tree, self.lists)
         return phi
 
+    def evaluate_field(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6, check: bool = True):
+        """The complex field F_i = sum_{j != i} -q_j / (z_i - z_j) (complex128 CUDA tensor)."""
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        fre = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        fim = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        fmm_evaluate_field(self.tree, self.lists, q, p, m, fre, fim, tol)
+        if check:
+            fmm_sync_status(self.tree, self.lists)
+        return torch.complex(fre, fim)
+
     def export_tree(self):
         n, L, nbox = fmm_tree_info(self.tree)
         perm = torch.empty(n, dtype=torch.int32, device=self.device)
@@ -568,6 +602,15 @@ class FMMBatch:
         if check:
             fmm_sync_status(self.tree, self.lists)
         return phi
+
+    def evaluate_field(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6, check: bool = True):
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        fre = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        fim = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        fmm_evaluate_field(self.tree, self.lists, q, p, m, fre, fim, tol)
+        if check:
+            fmm_sync_status(self.tree, self.lists)
+        return torch.complex(fre, fim)
 
     def autotune(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6):
         m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)

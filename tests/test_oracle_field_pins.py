@@ -69,7 +69,7 @@ def test_method_converges_like_theta_power():
         f = oracle.fmm_field(c.x, c.y, c.q, 4, p, 0.5)
         errs.append(np.max(np.abs(f - d)) / np.max(np.abs(d)))
     errs = np.array(errs)
-    # four more orders gain at least theta^4 / 2 = 1/32 ... here: every step at least 8x
+    # every four more orders cut the error at least 8-fold (theta^4 = 1/16, with a margin of 2)
     assert np.all(errs[1:] <= errs[:-1] / 8)
     # and the level is that of the Section 3 estimate theta^(p+1) / (1 - theta)^2
     assert np.all(errs <= 0.5 ** (np.array([4, 8, 12, 16]) + 1) / 0.25)
