@@ -321,7 +321,7 @@ __global__ void k_m2m(Sched sc, const Inst* __restrict__ I, int l, int P, int PS
 // scaled source coefficients and the partial sums live in registers, the constant matrix is read
 // from the constant bank by the unrolled contraction.
 template <typename T, int PI>
-__global__ void __launch_bounds__(128) k_m2l_pairs(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+__global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pairs(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                    int P, int PS, const int32_t* __restrict__ woff,
                                                    const int32_t* __restrict__ widx,
                                                    const int32_t* __restrict__ wtgt, Geo<T> geo,
