@@ -422,7 +422,7 @@ def main():
     t_top = stage_ms[top] * 1e-3
     m2l_kind = fmm.fmm_get_m2l_kernel(f.tree)
     if m2l_kind == fmm.FMM_M2L_AUTO:
-        m2l_kind = fmm.FMM_M2L_TENSOR if 24 <= P <= 32 else fmm.FMM_M2L_SIMT
+        m2l_kind = fmm.FMM_M2L_TENSOR if 29 <= P <= 32 else fmm.FMM_M2L_SIMT
     if top == "leaf":
         roof = {"bound": "alu", "achieved": npairs / t_top / 1e12, "peak": mufu_peak / 1e12,
                 "unit": "Tlog2/s (MUFU)", "traffic": None}

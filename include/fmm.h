@@ -232,8 +232,8 @@ int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks);
 /* Which kernel performs the binary32 M2L of tree t: 2 the tensor cores (tcgen05, split-tf32
  * products: each operand as a tf32 high and low part, three products accumulated in binary32;
  * p <= 31 only), 1 the SIMT units in plain binary32, 0 (default) by the order: tensor cores for
- * 23 <= p <= 31, where they measured faster on GB300, SIMT units otherwise.  fmm_autotune sets 1
- * or 2 by timing both.  The binary64 path always uses the SIMT units. */
+ * 28 <= p <= 31, where they measured clearly faster on GB300, SIMT units otherwise.
+ * fmm_autotune sets 1 or 2 by timing both.  The binary64 path always uses the SIMT units. */
 int fmm_set_m2l_kernel(fmm_tree t, int kind);
 /* The current choice (0, 1 or 2), or a negative fmm_status. */
 int fmm_get_m2l_kernel(fmm_tree t);

@@ -1616,9 +1616,10 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         }
         {
             StageScope scope(FMM_STAGE_M2L, s);
-            // tensor cores where they measured faster than the SIMT kernel (P >= 24; below, the
-            // scaling work around the contraction dominates), unless chosen explicitly
-            const bool tc = m2l_tc_supported(P) && (t->m2l_kind == 2 || (t->m2l_kind == 0 && P >= 24));
+            // tensor cores where they measured clearly faster than the SIMT kernel (P >= 29, on
+            // 2^20 clustered points: 3.3 ms against 3.9-4.6 ms at p = 30; below, the scaling work
+            // around the contraction dominates), unless chosen explicitly
+            const bool tc = m2l_tc_supported(P) && (t->m2l_kind == 2 || (t->m2l_kind == 0 && P >= 29));
             if (sizeof(T) == 4 && tc)
                 rc = m2l_tc(t, li, P, PS, Me, Le, s);
             else
