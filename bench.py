@@ -436,7 +436,7 @@ def main():
     elif top == "m2l":
         # dram__bytes_read.sum + dram__bytes_write.sum of k_m2l_pairs<float, 21> on this workload,
         # from one ncu capture; valid while that kernel is unchanged
-        traffic = 193367296 if (P == 21 and n == 1 << 20) else None
+        traffic = 195066880 if (P == 21 and n == 1 << 20) else None
         roof = {"bound": "alu", "achieved": nweak * 4 * P * P / t_top / 1e12, "peak": fp32_peak / 1e12,
                 "unit": "TFLOP/s (FP32 FMA pipe)", "traffic": traffic}
     elif top == "tree_sort":
