@@ -85,6 +85,10 @@ def _load():
         lib.orc_direct.argtypes = [i64, vp, vp, vp, i64, vp, vp, i32]
         lib.orc_fmm.restype = i32
         lib.orc_fmm.argtypes = [i64, vp, vp, vp, i32, i32, dbl, vp, vp, vp]
+        lib.orc_fmm_ex.restype = i32
+        lib.orc_fmm_ex.argtypes = [i64, vp, vp, vp, i32, i32, dbl, i32, vp]
+        lib.orc_lists_merge_parents.restype = None
+        lib.orc_lists_merge_parents.argtypes = [vp, vp, dbl]
         lib.orc_fmm_field.restype = i32
         lib.orc_fmm_field.argtypes = [i64, vp, vp, vp, i32, i32, dbl, vp, vp]
         lib.orc_direct_field.restype = None
@@ -153,12 +157,19 @@ def theta_weak(c1, r1, c2, r2, theta) -> bool:
                                        float(c2[0]), float(c2[1]), float(r2), float(theta)))
 
 
-def lists(rects, L: int, theta: float):
+PARENT_FLAG = 0x40000000
+
+
+def lists(rects, L: int, theta: float, parents: bool = False):
     """Connectivity of Section 4.  Returns (woff, widx, soff, sidx): CSR over all boxes in
-    global id order; entries are within-level indices of the coupled boxes."""
+    global id order; entries are within-level indices of the coupled boxes.  With ``parents``
+    the optional optimisation of Section 4 is applied to the weak lists: four weak siblings whose
+    parent satisfies the criterion become one entry (parent index | PARENT_FLAG)."""
     rects = _f64(rects)
     lib = _load()
     h = lib.orc_lists_build(L, _ptr(rects), float(theta))
+    if parents:
+        lib.orc_lists_merge_parents(h, _ptr(rects), float(theta))
     try:
         out = []
         for weak in (1, 0):
@@ -172,12 +183,19 @@ def lists(rects, L: int, theta: float):
     return tuple(out)
 
 
-def fmm(x, y, q, L: int, p: int, theta: float, want_coeffs: bool = False):
+def fmm(x, y, q, L: int, p: int, theta: float, want_coeffs: bool = False, parents: bool = False):
     """The whole method in FP64 (Section 4).  Returns phi in input order, plus the unscaled
-    multipole and local coefficients (complex, [nbox, p+1]) when ``want_coeffs``."""
+    multipole and local coefficients (complex, [nbox, p+1]) when ``want_coeffs``.  ``parents``
+    applies the optional parent-level interactions (see :func:`lists`)."""
     x, y, q = _f64(x), _f64(y), _f64(q)
     n = x.shape[0]
     phi = np.empty(n, np.float64)
+    if parents:
+        assert not want_coeffs
+        rc = _load().orc_fmm_ex(n, _ptr(x), _ptr(y), _ptr(q), L, p, float(theta), 1, _ptr(phi))
+        if rc:
+            raise OracleError(f"orc_fmm_ex failed ({rc})")
+        return phi
     M = Lc = None
     mp = lp = None
     if want_coeffs:

@@ -261,6 +261,54 @@ void* orc_lists_build(int L, const double* rects, double theta)
     return h;
 }
 
+/* Optional structural optimisation of Section 4: a box weakly coupled to all four children of a
+ * box P interacts with P instead, whenever the theta-criterion between P and the box holds.  The
+ * four children appear as four consecutive weak entries 4k, 4k+1, 4k+2, 4k+3 (candidates are
+ * taken parent by parent, child by child); they are replaced, in place of the first, by one entry
+ * k | ORC_PARENT_FLAG naming the parent at the level above.  Applied once to every level's weak
+ * lists after they are complete (the strong lists, which generate the next level's candidates,
+ * are untouched). */
+#define ORC_PARENT_FLAG 0x40000000
+
+void orc_lists_merge_parents(void* hp, const double* rects, double theta)
+{
+    orc_lists_t* h = (orc_lists_t*)hp;
+    double* c = (double*)malloc(sizeof(double) * 2 * (size_t)h->nbox);
+    double* r = (double*)malloc(sizeof(double) * (size_t)h->nbox);
+    orc_geometry(h->nbox, rects, c, r);
+    int64_t* noff = (int64_t*)calloc((size_t)h->nbox + 1, sizeof(int64_t));
+    int32_t* nidx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(h->woff[h->nbox] + 1));
+    int64_t nw = 0;
+    for (int64_t g = 0; g < h->nbox; g++) {
+        noff[g] = nw;
+        int l = 0;
+        while (level_base(l + 1) <= g) l++;
+        const int64_t pbase = l >= 1 ? level_base(l - 1) : 0;
+        int64_t e = h->woff[g];
+        while (e < h->woff[g + 1]) {
+            const int32_t v = h->widx[e];
+            if (l >= 1 && e + 3 < h->woff[g + 1] && v % 4 == 0 && h->widx[e + 1] == v + 1 &&
+                h->widx[e + 2] == v + 2 && h->widx[e + 3] == v + 3) {
+                const int64_t P = pbase + v / 4;
+                if (orc_theta_weak(c[2 * g], c[2 * g + 1], r[g], c[2 * P], c[2 * P + 1], r[P], theta)) {
+                    nidx[nw++] = (v / 4) | ORC_PARENT_FLAG;
+                    e += 4;
+                    continue;
+                }
+            }
+            nidx[nw++] = v;
+            e++;
+        }
+    }
+    noff[h->nbox] = nw;
+    free(h->woff);
+    free(h->widx);
+    h->woff = noff;
+    h->widx = nidx;
+    h->wcap = h->woff[h->nbox] + 1;
+    free(c); free(r);
+}
+
 int64_t orc_lists_total(void* hp, int weak)
 {
     orc_lists_t* h = (orc_lists_t*)hp;
@@ -539,7 +587,7 @@ void orc_direct_field(int64_t n, const double* x, const double* y, const double*
  * Returns 0 or a negative code as orc_tree.
  * ------------------------------------------------------------------------------------------ */
 static int fmm_core(int64_t n, const double* x, const double* y, const double* q, int L, int p,
-                    double theta, double* phi, double* fre, double* fim, double* mpole_out,
+                    double theta, int flags, double* phi, double* fre, double* fim, double* mpole_out,
                     double* local_out)
 {
     if (p < 0 || p > ORC_PMAX || !(theta > 0.0 && theta < 1.0)) return -1;
@@ -553,6 +601,7 @@ static int fmm_core(int64_t n, const double* x, const double* y, const double* q
     double* rad = (double*)malloc(sizeof(double) * (size_t)nbox);
     orc_geometry(nbox, rects, cen, rad);
     orc_lists_t* li = (orc_lists_t*)orc_lists_build(L, rects, theta);
+    if (flags & 1) orc_lists_merge_parents(li, rects, theta);
     int P = p + 1;
     cplx* M = (cplx*)calloc((size_t)(nbox * P), sizeof(cplx));
     cplx* Lc = (cplx*)calloc((size_t)(nbox * P), sizeof(cplx));
@@ -576,7 +625,8 @@ static int fmm_core(int64_t n, const double* x, const double* y, const double* q
         for (int64_t b = 0; b < nb; b++) {
             int64_t g = base + b;
             for (int64_t e = li->woff[g]; e < li->woff[g + 1]; e++) {
-                int64_t sg = base + li->widx[e];
+                const int32_t v = li->widx[e];
+                int64_t sg = (v & ORC_PARENT_FLAG) ? level_base(l - 1) + (v & ~ORC_PARENT_FLAG) : base + v;
                 m2l(M + sg * P, CEN(sg) - CEN(g), p, Lc + g * P);
             }
         }
@@ -638,7 +688,14 @@ static int fmm_core(int64_t n, const double* x, const double* y, const double* q
 int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L, int p,
             double theta, double* phi, double* mpole_out, double* local_out)
 {
-    return fmm_core(n, x, y, q, L, p, theta, phi, NULL, NULL, mpole_out, local_out);
+    return fmm_core(n, x, y, q, L, p, theta, 0, phi, NULL, NULL, mpole_out, local_out);
+}
+
+/* The method with the optional parent-level interactions (flags & 1, see orc_lists_merge_parents). */
+int orc_fmm_ex(int64_t n, const double* x, const double* y, const double* q, int L, int p,
+               double theta, int flags, double* phi)
+{
+    return fmm_core(n, x, y, q, L, p, theta, flags, phi, NULL, NULL, NULL, NULL);
 }
 
 /* The method for the complex field G(z_i, z_j) = -q_j / (z_i - z_j) (Section 5): the same tree,
@@ -647,5 +704,5 @@ int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L,
 int orc_fmm_field(int64_t n, const double* x, const double* y, const double* q, int L, int p,
                   double theta, double* fre, double* fim)
 {
-    return fmm_core(n, x, y, q, L, p, theta, NULL, fre, fim, NULL, NULL);
+    return fmm_core(n, x, y, q, L, p, theta, 0, NULL, fre, fim, NULL, NULL);
 }
