@@ -177,6 +177,17 @@ int fmm_lists_create(fmm_tree t, int64_t weak_capacity, int64_t strong_capacity,
 int fmm_lists_create_batched(fmm_tree t, const int64_t* weak_capacity_host,
                              const int64_t* strong_capacity_host, fmm_lists* out);
 
+/* Optional structural optimisation of Section 4 (mode FMM_LISTS_PARENTS; FMM_LISTS_PLAIN is the
+ * default): a box whose weak list holds all four children of a box P of the level above, as four
+ * consecutive entries 4k .. 4k+3, interacts with P instead whenever the theta-criterion between P
+ * and the box holds.  Such an entry is k | FMM_PARENT_FLAG (a within-level index of the level
+ * above).  Strong lists are unchanged.  Setting the mode allocates (synchronous) and requires a
+ * rebuild of the lists. */
+#define FMM_LISTS_PLAIN 0
+#define FMM_LISTS_PARENTS 1
+#define FMM_PARENT_FLAG 0x40000000
+int fmm_lists_set_mode(fmm_lists l, int mode);
+
 /* Build the lists of tree t (which must have been built on the same stream or be complete)
  * for 0 < theta < 1.  Overflow of the capacity sets FMM_ERR_CAPACITY in the device status;
  * later kernels then read only within the capacity. */
@@ -224,7 +235,9 @@ int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
  * stream capture).  The chosen totals are reported in m2l_blocks / p2p_blocks (host, may be
  * NULL).  For the mixed path it also times the two binary32 M2L kernels (fmm_set_m2l_kernel)
  * and keeps the faster.  fmm_set_launch sets the totals directly (0 = the built-in default); it
- * uploads small launch tables and so also synchronises. */
+ * uploads small launch tables and so also synchronises.  Both replace the tree's launch tables
+ * and grid sizes: a CUDA graph captured before either call still names the old ones and must
+ * not be launched again; capture it anew. */
 int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi,
                  void* stream, int* m2l_blocks_host, int* p2p_blocks_host);
 int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks);
@@ -232,7 +245,8 @@ int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks);
 /* Which kernel performs the binary32 M2L of tree t: 2 the tensor cores (tcgen05, split-tf32
  * products: each operand as a tf32 high and low part, three products accumulated in binary32;
  * p <= 31 only), 1 the SIMT units in plain binary32, 0 (default) by the order: tensor cores for
- * 28 <= p <= 31, where they measured clearly faster on GB300, SIMT units otherwise.
+ * 28 <= p <= 31, where they measured clearly faster on GB300, SIMT units otherwise.  Changing
+ * the kind does not touch the launch tables, but a captured graph keeps the kernel it saw.
  * fmm_autotune sets 1 or 2 by timing both.  The binary64 path always uses the SIMT units. */
 int fmm_set_m2l_kernel(fmm_tree t, int kind);
 /* The current choice (0, 1 or 2), or a negative fmm_status. */

@@ -108,7 +108,7 @@ void free_lists(fmm_lists l)
 {
     if (!l) return;
     void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status,
-                    l->dlinst};
+                    l->dlinst, l->tiledrop};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] l->hlinst;
@@ -320,6 +320,21 @@ int fmm_lists_create_batched(fmm_tree t, const int64_t* weak_capacity, const int
         if (weak_capacity[i] < 1 || strong_capacity[i] < 1)
             return fail(FMM_ERR_ARG, "instance %d: capacities must be positive", i);
     return lists_create_impl(t, weak_capacity, strong_capacity, out);
+}
+
+int fmm_lists_set_mode(fmm_lists l, int mode)
+{
+    if (!l) return fail(FMM_ERR_ARG, "NULL lists");
+    if (mode != FMM_LISTS_PLAIN && mode != FMM_LISTS_PARENTS) return fail(FMM_ERR_ARG, "unknown lists mode %d", mode);
+    GUARD(l->tree->dev);
+    if (mode == FMM_LISTS_PARENTS && !l->tiledrop) {
+        int64_t words = 0;
+        for (int i = 0; i < l->tree->n_inst; i++) words += lists_tile_words(l->hlinst[i].scap);
+        if (cudaMalloc((void**)&l->tiledrop, 4 * words) != cudaSuccess) return fail(FMM_ERR_OOM, "list storage");
+    }
+    l->mode = mode;
+    l->built = false;  // the lists must be rebuilt in the new mode
+    return FMM_OK;
 }
 
 int fmm_interaction_lists(fmm_tree t, fmm_lists l, double theta, void* stream)

@@ -43,9 +43,20 @@ constexpr int TREE_TPB = 256;
 constexpr int TREE_ITEMS = 4;
 constexpr int TREE_TILE = TREE_TPB * TREE_ITEMS;
 
+// Weak-list entry naming the parent (level l - 1) of four weak siblings: index | PARENT_FLAG.
+constexpr int32_t PARENT_FLAG = FMM_PARENT_FLAG;
+
 // ---- level-order box numbering ----
 __host__ __device__ inline int64_t level_base(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 __host__ __device__ inline int64_t level_size(int l) { return int64_t(1) << (2 * l); }
+
+// Source box of a weak-list entry v of target box g (global ids within an instance): a box of
+// g's level, or with PARENT_FLAG a box of the level above.
+__device__ __forceinline__ int64_t weak_source(int64_t g, int32_t v)
+{
+    const int l = (63 - __clzll((unsigned long long)(3 * g + 1))) >> 1;
+    return (v & PARENT_FLAG) ? level_base(l - 1) + (v & ~PARENT_FLAG) : level_base(l) + v;
+}
 
 // The per-depth tables of ones_before are concatenated: depth d starts at 2^d - 1.
 __host__ __device__ inline int64_t ones_before_offset(int depth) { return (int64_t(1) << depth) - 1; }
@@ -256,6 +267,11 @@ struct fmm_lists_s {
     int32_t* status = nullptr;
     double theta = 0.0;
     bool built = false;
+    // parent-level interactions (Section 4's optional optimisation): FMM_LISTS_PARENTS lets
+    // four weak siblings become one entry naming their parent; tiledrop counts the siblings
+    // dropped per candidate tile
+    int mode = 0;
+    uint32_t* tiledrop = nullptr;
 };
 
 namespace fmm {

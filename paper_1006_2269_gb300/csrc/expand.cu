@@ -84,11 +84,6 @@ __device__ __forceinline__ T ipow(T x, int e)
     return r;
 }
 
-// Level of a global box id: 4^l <= 3g + 1 < 4^(l+1).
-__device__ __forceinline__ int level_of(int64_t g)
-{
-    return (63 - __clzll((unsigned long long)(3 * g + 1))) >> 1;
-}
 
 // Box geometry in the working precision.  z0 = c_a - c_b: in binary64 directly, in binary32 from
 // the float-float centres so that the difference of two nearby centres keeps its relative
@@ -373,7 +368,7 @@ __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pai
                 lo0 = 0;
                 cur = g;
             }
-            const int64_t sg = level_base(level_of(g)) + widx[e];
+            const int64_t sg = weak_source(g, widx[e]);
             const cx<T> z0 = geo.diff(sg, g);
             const T r2 = z0.re * z0.re + z0.im * z0.im;
             const T ir2 = (T)1 / r2;
@@ -493,7 +488,7 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(Sched sc, const Inst* __re
                     }
                 cur = g;
             }
-            const int64_t sg = level_base(level_of(g)) + widx[e];
+            const int64_t sg = weak_source(g, widx[e]);
             const cx<double> z0 = geo.diff(sg, g);
             const double r2 = z0.re * z0.re + z0.im * z0.im;
             const double ir2 = 1.0 / r2;

@@ -189,8 +189,16 @@ __device__ __forceinline__ void decode(const TileParents& tp, const int32_t* __r
     first = (r == 0);
 }
 
+// Candidate flags: 0 strong, 1 weak.  With parent-level interactions (PAR, Section 4's optional
+// step) four weak siblings c = 4k .. 4k+3 of one target box whose parent k also satisfies the
+// criterion with the target become one entry: 2 on the first (the entry names the parent), 3 on
+// the other three (no entry).  The four children of a source box are candidates 4q .. 4q+3,
+// which sit in lanes 4q' .. 4q'+3 of one warp (tiles, rows and boxes all start at multiples of
+// 4), so one ballot tells each lane about its quad.
 // schedule: candidate tiles of level l
-__global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, int l, const double* __restrict__ cen,
+template <bool PAR>
+__global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, uint32_t* tiledrop, int l,
+                                                    const double* __restrict__ cen,
                                                     const double* __restrict__ rad,
                                                     const float* __restrict__ chi,
                                                     const float* __restrict__ clo,
@@ -205,56 +213,69 @@ __global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, int l, 
     chi += 2 * S.b0;
     clo += 2 * S.b0;
     rad32 += S.b0;
-    __shared__ uint32_t wsum[LT / 32];
+    __shared__ uint32_t wsum[LT / 32], dsum[LT / 32];
     __shared__ TileParents tp;
     const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
-    const int64_t base = level_base(l);
+    const int64_t base = level_base(l), pbase = level_base(l - 1);
+    const int lane = threadIdx.x & 31;
     for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
-        uint32_t cnt = 0;
+        uint32_t cnt = 0, drop = 0;
         for (int j = 0; j < LI; j++) {
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
+            int64_t b = 0, c = 0;
+            bool w = false;
             if (t < nc) {
-                int64_t b, c;
                 bool first;
                 decode(tp, v.sidx, lc, t, b, c, first);
-                const bool w = theta_weak_fast(base + b, base + c, chi, clo, rad32, cen, rad,
-                                               (float)theta, theta);
-                v.flags[t] = w ? 1 : 0;
-                cnt += w;
+                w = theta_weak_fast(base + b, base + c, chi, clo, rad32, cen, rad, (float)theta, theta);
             }
+            uint8_t f = w ? 1 : 0;
+            if (PAR) {
+                const unsigned q = __ballot_sync(0xffffffffu, w) >> (lane & ~3) & 0xFu;
+                bool m = false;
+                if (q == 0xFu && (lane & 3) == 0)
+                    m = theta_weak_fast(base + b, pbase + (c >> 2), chi, clo, rad32, cen, rad, (float)theta, theta);
+                if (__ballot_sync(0xffffffffu, m) >> (lane & ~3) & 1u) f = (lane & 3) ? 3 : 2;
+                drop += f == 3;
+            }
+            if (t < nc) v.flags[t] = f;
+            cnt += f == 1 || f == 2;
         }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+        for (int o = 16; o; o >>= 1) {
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (PAR) drop += __shfl_xor_sync(0xffffffffu, drop, o);
+        }
+        if (lane == 0) {
+            wsum[threadIdx.x >> 5] = cnt;
+            dsum[threadIdx.x >> 5] = drop;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint32_t s = 0;
-            for (int w = 0; w < LT / 32; w++) s += wsum[w];
+            uint32_t s = 0, d = 0;
+            for (int w = 0; w < LT / 32; w++) {
+                s += wsum[w];
+                d += dsum[w];
+            }
             v.tilecnt[tile] = s;
+            if (PAR) tiledrop[LIs[z.i].c0 + tile] = d;
         }
         __syncthreads();
     }
 }
 
-// Exclusive scan of the weak counts per tile; writes the level totals into the offsets.
-// One block per instance.
-__global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, int l)
+// In-place exclusive scan of a[0 .. n) by the whole block; returns the total.
+__device__ int64_t block_exclusive_scan(uint32_t* a, int64_t n)
 {
-    const Inst S = I[blockIdx.x];
-    if (l > S.L) return;
-    const LView v = LIST_VIEW(blockIdx.x);
     __shared__ int64_t wt[32];
-    const LevelCands lc = level_cands(v.soff, l, v.scap);
-    const int64_t nc = lc.count();
-    const int64_t ntiles = (nc + LTILE - 1) / LTILE;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int64_t carry = 0;
-    for (int64_t b0 = 0; b0 < ntiles; b0 += blockDim.x) {
+    for (int64_t b0 = 0; b0 < n; b0 += blockDim.x) {
         const int64_t i = b0 + threadIdx.x;
-        int64_t val = i < ntiles ? v.tilecnt[i] : 0, x = val;
+        int64_t val = i < n ? a[i] : 0, x = val;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int64_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -273,28 +294,46 @@ __global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, int l)
         }
         __syncthreads();
         const int64_t before = w ? wt[w - 1] : 0, tot = wt[nw - 1];
-        if (i < ntiles) v.tilecnt[i] = (uint32_t)(carry + before + x - val);
+        if (i < n) a[i] = (uint32_t)(carry + before + x - val);
         carry += tot;
         __syncthreads();
     }
+    return carry;
+}
+
+// Exclusive scan of the weak counts per tile (and of the dropped siblings with PAR); writes the
+// level totals into the offsets.  One block per instance.
+template <bool PAR>
+__global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, uint32_t* tiledrop, int l)
+{
+    const Inst S = I[blockIdx.x];
+    if (l > S.L) return;
+    const LView v = LIST_VIEW(blockIdx.x);
+    const LevelCands lc = level_cands(v.soff, l, v.scap);
+    const int64_t nc = lc.count();
+    const int64_t ntiles = (nc + LTILE - 1) / LTILE;
+    const int64_t nweak = block_exclusive_scan(v.tilecnt, ntiles);
+    const int64_t ndrop = PAR ? block_exclusive_scan(tiledrop + LIs[blockIdx.x].c0, ntiles) : 0;
     if (threadIdx.x == 0) {
         const int64_t base = level_base(l), nb = level_size(l);
         const int64_t W0 = v.woff[base], S0 = v.soff[base];
-        v.woff[base + nb] = (int32_t)min(W0 + carry, (int64_t)INT32_MAX);
-        v.soff[base + nb] = (int32_t)min(S0 + (nc - carry), (int64_t)INT32_MAX);
+        v.woff[base + nb] = (int32_t)min(W0 + nweak, (int64_t)INT32_MAX);
+        v.soff[base + nb] = (int32_t)min(S0 + (nc - nweak - ndrop), (int64_t)INT32_MAX);
     }
 }
 
 // Scatter the candidates into the weak and strong lists and write the box offsets.  The tile
-// prefix of weak flags is tilecnt[tile]; the strong prefix is its complement.
+// prefix of weak flags is tilecnt[tile] (of dropped siblings, tiledrop[tile]); the strong prefix
+// is the rest.
 // schedule: candidate tiles of level l
-__global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, int l)
+template <bool PAR>
+__global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, const uint32_t* tiledrop, int l)
 {
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
     if (l > S.L) return;
     const LView v = LIST_VIEW(z.i);
-    __shared__ uint32_t wsum[LI][LT / 32];
+    __shared__ uint32_t wsum[LI][LT / 32], dsum[PAR ? LI : 1][LT / 32];
     __shared__ TileParents tp;
     const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
@@ -306,40 +345,52 @@ __global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, int l)
     for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint8_t f[LI];
-        uint32_t pre[LI];
+        uint32_t pre[LI], dpre[LI];
 #pragma unroll
         for (int j = 0; j < LI; j++) {
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             f[j] = t < nc ? v.flags[t] : 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, f[j]);
+            const unsigned bal = __ballot_sync(0xffffffffu, f[j] == 1 || f[j] == 2);
             pre[j] = __popc(bal & lt);
             if (lane == 0) wsum[j][w] = __popc(bal);
+            dpre[j] = 0;
+            if (PAR) {
+                const unsigned bd = __ballot_sync(0xffffffffu, f[j] == 3);
+                dpre[j] = __popc(bd & lt);
+                if (lane == 0) dsum[j][w] = __popc(bd);
+            }
         }
         __syncthreads();
         // exclusive prefix in (row j, warp) order = candidate order inside the tile
-        uint32_t run = v.tilecnt[tile];
+        uint32_t run = v.tilecnt[tile], drun = PAR ? tiledrop[LIs[z.i].c0 + tile] : 0;
 #pragma unroll
         for (int j = 0; j < LI; j++) {
-            uint32_t before = 0;
+            uint32_t before = 0, dbefore = 0;
             for (int ww = 0; ww < LT / 32; ww++) {
-                if (ww == w) before = run;
+                if (ww == w) {
+                    before = run;
+                    dbefore = drun;
+                }
                 run += wsum[j][ww];
+                if (PAR) drun += dsum[j][ww];
             }
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             if (t < nc) {
                 int64_t b, c;
                 bool first;
                 decode(tp, v.sidx, lc, t, b, c, first);
-                const int64_t wpre = (int64_t)before + pre[j];  // weak candidates before t
-                const int64_t spre = t - wpre;                   // strong candidates before t
+                const int64_t wpre = (int64_t)before + pre[j];              // weak entries before t
+                const int64_t spre = t - wpre - ((int64_t)dbefore + dpre[j]);  // strong entries before t
                 if (first) {
                     v.woff[base + b] = (int32_t)min(W0 + wpre, (int64_t)INT32_MAX);
                     v.soff[base + b] = (int32_t)min(S0 + spre, (int64_t)INT32_MAX);
                 }
-                if (f[j]) {
+                if (PAR && f[j] == 3) {
+                    // a sibling covered by its parent's entry
+                } else if (f[j]) {
                     const int64_t pos = W0 + wpre;
                     if (pos < v.wcap) {
-                        v.widx[pos] = (int32_t)c;
+                        v.widx[pos] = f[j] == 2 ? (int32_t)(c >> 2) | PARENT_FLAG : (int32_t)c;
                         v.wtgt[pos] = (int32_t)(base + b);
                     }
                 } else {
@@ -416,6 +467,7 @@ int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s)
 {
     const int L = t->Lmax, ni = t->n_inst;
     StageScope scope(FMM_STAGE_LISTS, s);
+    const bool par = li->mode == FMM_LISTS_PARENTS;
 #define LARGS t->dinst, li->dlinst, li->woff, li->soff, li->widx, li->wtgt, li->sidx, li->stgt, li->flags, li->tilecnt
     k_lists_root<<<1, 256, 0, s>>>(LARGS, ni); note_launch();
     for (int l = 1; l <= L; l++) {
@@ -423,10 +475,17 @@ int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s)
         // is only known on the device); a forest shares blocks in proportion to 4^l
         const SchedH& sh = t->s_lists[l];
         const unsigned g = ni == 1 ? 152 * 8 : (unsigned)sh.blocks;
-        k_lists_flags<<<g, LT, 0, s>>>(sh.d, LARGS, l, t->centers, t->radii, t->cen_hi, t->cen_lo,
-                                       t->rad32, theta); note_launch();
-        k_lists_scan<<<ni, 1024, 0, s>>>(LARGS, l); note_launch();
-        k_lists_fill<<<g, LT, 0, s>>>(sh.d, LARGS, l); note_launch();
+        if (par) {
+            k_lists_flags<true><<<g, LT, 0, s>>>(sh.d, LARGS, li->tiledrop, l, t->centers, t->radii, t->cen_hi,
+                                                 t->cen_lo, t->rad32, theta); note_launch();
+            k_lists_scan<true><<<ni, 1024, 0, s>>>(LARGS, li->tiledrop, l); note_launch();
+            k_lists_fill<true><<<g, LT, 0, s>>>(sh.d, LARGS, li->tiledrop, l); note_launch();
+        } else {
+            k_lists_flags<false><<<g, LT, 0, s>>>(sh.d, LARGS, nullptr, l, t->centers, t->radii, t->cen_hi,
+                                                  t->cen_lo, t->rad32, theta); note_launch();
+            k_lists_scan<false><<<ni, 1024, 0, s>>>(LARGS, nullptr, l); note_launch();
+            k_lists_fill<false><<<g, LT, 0, s>>>(sh.d, LARGS, nullptr, l); note_launch();
+        }
         FMM_LAUNCH_CHECK("lists");
     }
     k_lists_check<<<1, 256, 0, s>>>(LARGS, ni, li->status); note_launch();

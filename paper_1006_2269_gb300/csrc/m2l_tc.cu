@@ -140,7 +140,6 @@ __device__ __forceinline__ void two_sum_f(float& hi, float& lo, float v)
     hi = s;
 }
 
-__device__ __forceinline__ int level_of_box(int64_t g) { return (63 - __clzll((unsigned long long)(3 * g + 1))) >> 1; }
 
 __device__ __forceinline__ unsigned lanemask_lt_()
 {
@@ -227,7 +226,7 @@ __global__ void __launch_bounds__(TC_ROWS, (KC <= 24 ? 4 : 3)) k_m2l_tc(Sched sc
         cg = -1;
         if (tl < ntile && e < e_end) {
             cg = wtgt[e];
-            const int64_t sg = level_base(level_of_box(cg)) + widx[e];
+            const int64_t sg = weak_source(cg, widx[e]);
             ha = *(const float2*)(chi + 2 * sg);
             hb = *(const float2*)(chi + 2 * cg);
             la = *(const float2*)(clo + 2 * sg);

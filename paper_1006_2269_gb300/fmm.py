@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
             "fmm_tree_destroy": (None, [vp]),
             "fmm_lists_create": (i32, [vp, i64, i64, ctypes.POINTER(vp)]),
             "fmm_interaction_lists": (i32, [vp, vp, dbl, vp]),
+            "fmm_lists_set_mode": (i32, [vp, i32]),
             "fmm_lists_sync": (i32, [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
             "fmm_lists_export": (i32, [vp, vp, vp, vp, vp, vp]),
             "fmm_lists_destroy": (None, [vp]),
@@ -251,6 +252,14 @@ def fmm_lists_counts(lists, n_inst: int, stream=None, check: bool = True):
     if rc not in (FMM_OK, FMM_ERR_CAPACITY):
         _check(rc)
     return w, st, rc == FMM_ERR_CAPACITY
+
+
+FMM_LISTS_PLAIN, FMM_LISTS_PARENTS, FMM_PARENT_FLAG = 0, 1, 0x40000000
+
+
+def fmm_lists_set_mode(lists, mode: int):
+    """FMM_LISTS_PARENTS: four weak siblings become their parent where the criterion allows."""
+    _check(load_library().fmm_lists_set_mode(lists, int(mode)))
 
 
 def fmm_interaction_lists(tree, lists, theta: float, stream=None):
@@ -450,15 +459,18 @@ class FMM:
     """
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, levels: int, theta: float = 0.5,
-                 weak_capacity: int = 0, strong_capacity: int = 0, check: bool = True):
+                 weak_capacity: int = 0, strong_capacity: int = 0, check: bool = True, parents: bool = False):
         self.n = x.numel()
         self.levels = levels
         self.theta = theta
         self.device = x.device
+        self.parents = parents
         self.tree = fmm_tree_create(self.n, levels)
         self.lists = None
         try:
             self.lists = fmm_lists_create(self.tree, weak_capacity, strong_capacity)
+            if parents:
+                fmm_lists_set_mode(self.lists, FMM_LISTS_PARENTS)
             self.rebuild(x, y, check=check)
         except Exception:
             self.close()
@@ -481,6 +493,8 @@ class FMM:
                 fmm_lists_destroy(self.lists)
                 self.lists = None
                 self.lists = fmm_lists_create(self.tree, 2 * w + 1024, 2 * s + 1024)
+                if self.parents:
+                    fmm_lists_set_mode(self.lists, FMM_LISTS_PARENTS)
                 return self.rebuild(x, y, check=check)
             fmm_sync_status(self.tree, self.lists)
 
@@ -555,7 +569,7 @@ class FMMBatch:
     """
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, sizes, levels, theta: float = 0.5,
-                 check: bool = True, weak_per_box: int = 48, strong_per_box: int = 24):
+                 check: bool = True, weak_per_box: int = 48, strong_per_box: int = 24, parents: bool = False):
         self.sizes = [int(v) for v in sizes]
         self.levels = [int(v) for v in levels]
         self.n = sum(self.sizes)
@@ -567,8 +581,11 @@ class FMMBatch:
         self.inst = [fmm_tree_instance(self.tree, i) for i in range(self.n_inst)]
         try:
             nb = [d["nbox"] for d in self.inst]
+            self.parents = parents
             self.lists = fmm_lists_create_batched(self.tree, [weak_per_box * v for v in nb],
                                                   [strong_per_box * v for v in nb])
+            if parents:
+                fmm_lists_set_mode(self.lists, FMM_LISTS_PARENTS)
             self.rebuild(x, y, check=check)
         except Exception:
             self.close()
@@ -590,6 +607,8 @@ class FMMBatch:
                 # counts of an instance that overflowed are lower bounds: at least double it
                 self.lists = fmm_lists_create_batched(self.tree, [max(2 * int(a) + 64, 16 * b) for a, b in zip(w, nb)],
                                                       [max(2 * int(a) + 64, 8 * b) for a, b in zip(s, nb)])
+                if self.parents:
+                    fmm_lists_set_mode(self.lists, FMM_LISTS_PARENTS)
                 return self.rebuild(x, y, check=check)
             self.counts = (w, s)
             fmm_sync_status(self.tree, self.lists)
