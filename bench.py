@@ -144,6 +144,11 @@ def run_reference(args, rank):
 
 # ---- our arm -----------------------------------------------------------------------------------
 
+# dram__bytes_read.sum + dram__bytes_write.sum of the SIMT M2L kernel per launch on the 1M
+# clustered workload, from one ncu capture each; valid while that kernel is unchanged
+M2L_TRAFFIC = {(21, 1 << 20, "parents"): 136172544}
+
+
 def pair_counts(f):
     """Algorithmic units of the current tree/lists: weak pairs per level and near-field pair
     evaluations (sum over leaves of n_t * sum of strong n_s)."""
@@ -267,6 +272,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched workload")
+    ap.add_argument("--lists", default="auto", choices=["auto", "plain", "parents"],
+                    help="interaction lists: the plain rule, with parent-level interactions (Section 4), "
+                         "or the faster of the two on this workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -328,6 +336,31 @@ def main():
         step(fmm.FMM_MODE_MIXED)
     fmm.fmm_sync_status(f.tree, f.lists)
     fmm.fmm_lists_sync(f.lists)
+
+    # Section 4's optional parent-level interactions change the lists (fewer M2L shifts), not the
+    # accuracy class; "auto" keeps whichever variant runs the whole step faster here
+    def time_lists(mode_lists, k=20):
+        fmm.fmm_lists_set_mode(f.lists, mode_lists)
+        step(fmm.FMM_MODE_MIXED)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            step(fmm.FMM_MODE_MIXED)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    lists_ms = {}
+    if args.lists == "auto":
+        lists_ms = {name: time_lists(m) for name, m in (("plain", fmm.FMM_LISTS_PLAIN),
+                                                       ("parents", fmm.FMM_LISTS_PARENTS))}
+        lists_kind = min(lists_ms, key=lists_ms.get)
+    else:
+        lists_kind = args.lists
+    fmm.fmm_lists_set_mode(f.lists, fmm.FMM_LISTS_PARENTS if lists_kind == "parents" else fmm.FMM_LISTS_PLAIN)
+    step(fmm.FMM_MODE_MIXED)
+    fmm.fmm_sync_status(f.tree, f.lists)
     tuned = {fmm.FMM_MODE_FP64: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_FP64, phi),
              fmm.FMM_MODE_MIXED: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_MIXED, phi)}
 
@@ -436,7 +469,7 @@ def main():
     elif top == "m2l":
         # dram__bytes_read.sum + dram__bytes_write.sum of k_m2l_pairs<float, 21> on this workload,
         # from one ncu capture; valid while that kernel is unchanged
-        traffic = 195066880 if (P == 21 and n == 1 << 20) else None
+        traffic = M2L_TRAFFIC.get((P, n, lists_kind))
         roof = {"bound": "alu", "achieved": nweak * 4 * P * P / t_top / 1e12, "peak": fp32_peak / 1e12,
                 "unit": "TFLOP/s (FP32 FMA pipe)", "traffic": traffic}
     elif top == "tree_sort":
@@ -461,7 +494,10 @@ def main():
                    "autotuned_blocks": {"m2l": tuned[fmm.FMM_MODE_MIXED][0],
                                         "near_field": tuned[fmm.FMM_MODE_MIXED][1]},
                    "m2l_kernel": "tensor cores (tcgen05, split tf32)" if m2l_kind == fmm.FMM_M2L_TENSOR
-                   else "SIMT binary32"},
+                   else "SIMT binary32",
+                   "lists": lists_kind + (" (parent-level interactions, Section 4)" if lists_kind == "parents"
+                                          else ""),
+                   "lists_trial_ms_per_step": lists_ms or None},
         "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,
         "fp64_path": {"value": world * n / (ms_fp64 / args.fp64_steps * 1e-3),
                       "ms_per_step": ms_fp64 / args.fp64_steps, "stages_ms": stage_ms64},

@@ -14,8 +14,8 @@ multiply-add is fused); this module only compiles it and marshals numpy arrays:
 * :func:`direct`     -- the O(N^2) definition, Eq. (1.1)
 * :func:`fmm_field`, :func:`direct_field` -- the complex field -q_j / (z_i - z_j) of Section 5's
   first experiment, by the method and by direct summation
-* :func:`p2m`, :func:`m2m`, :func:`m2l`, :func:`l2l`, :func:`l2p`, :func:`m2p` -- one operator
-  at a time, for the pins.
+* :func:`p2m`, :func:`m2m`, :func:`m2l`, :func:`l2l`, :func:`l2p`, :func:`m2p`, :func:`p2l` -- one
+  operator at a time, for the pins.
 * :mod:`oracle.mlp`  -- FP64 reference of the parameter-selector network.
 """
 from __future__ import annotations
@@ -89,6 +89,14 @@ def _load():
         lib.orc_fmm_ex.argtypes = [i64, vp, vp, vp, i32, i32, dbl, i32, vp]
         lib.orc_lists_merge_parents.restype = None
         lib.orc_lists_merge_parents.argtypes = [vp, vp, dbl]
+        lib.orc_lists_swap_leaves.restype = None
+        lib.orc_lists_swap_leaves.argtypes = [vp, vp, dbl]
+        lib.orc_theta_swapped.restype = i32
+        lib.orc_theta_swapped.argtypes = [dbl] * 7
+        lib.orc_p2l.restype = None
+        lib.orc_p2l.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, vp]
+        lib.orc_fmm_field_ex.restype = i32
+        lib.orc_fmm_field_ex.argtypes = [i64, vp, vp, vp, i32, i32, dbl, i32, vp, vp]
         lib.orc_fmm_field.restype = i32
         lib.orc_fmm_field.argtypes = [i64, vp, vp, vp, i32, i32, dbl, vp, vp]
         lib.orc_direct_field.restype = None
@@ -158,41 +166,54 @@ def theta_weak(c1, r1, c2, r2, theta) -> bool:
 
 
 PARENT_FLAG = 0x40000000
+SWAP_M2P = 0x20000000
 
 
-def lists(rects, L: int, theta: float, parents: bool = False):
+def theta_swapped(c1, r1, c2, r2, theta) -> bool:
+    """Criterion 2.1 with the roles of the two radii exchanged (disjointness included)."""
+    return bool(_load().orc_theta_swapped(float(c1[0]), float(c1[1]), float(r1),
+                                          float(c2[0]), float(c2[1]), float(r2), float(theta)))
+
+
+def lists(rects, L: int, theta: float, parents: bool = False, swap: bool = False):
     """Connectivity of Section 4.  Returns (woff, widx, soff, sidx): CSR over all boxes in
     global id order; entries are within-level indices of the coupled boxes.  With ``parents``
     the optional optimisation of Section 4 is applied to the weak lists: four weak siblings whose
-    parent satisfies the criterion become one entry (parent index | PARENT_FLAG)."""
+    parent satisfies the criterion become one entry (parent index | PARENT_FLAG).  With ``swap``
+    the finest-level role exchange is applied too and (xoff, xidx) are appended: the leaf pairs
+    taken out of the strong lists, SWAP_M2P marking those where the target is the larger leaf."""
     rects = _f64(rects)
     lib = _load()
     h = lib.orc_lists_build(L, _ptr(rects), float(theta))
     if parents:
         lib.orc_lists_merge_parents(h, _ptr(rects), float(theta))
+    if swap:
+        lib.orc_lists_swap_leaves(h, _ptr(rects), float(theta))
     try:
         out = []
-        for weak in (1, 0):
-            tot = lib.orc_lists_total(h, weak)
+        for kind in ((1, 0, 2) if swap else (1, 0)):
+            tot = lib.orc_lists_total(h, kind)
             off = np.empty(nbox(L) + 1, np.int64)
             idx = np.empty(max(tot, 1), np.int32)
-            lib.orc_lists_copy(h, weak, _ptr(off), _ptr(idx))
+            lib.orc_lists_copy(h, kind, _ptr(off), _ptr(idx))
             out += [off, idx[:tot]]
     finally:
         lib.orc_lists_free(h)
     return tuple(out)
 
 
-def fmm(x, y, q, L: int, p: int, theta: float, want_coeffs: bool = False, parents: bool = False):
+def fmm(x, y, q, L: int, p: int, theta: float, want_coeffs: bool = False, parents: bool = False,
+        swap: bool = False):
     """The whole method in FP64 (Section 4).  Returns phi in input order, plus the unscaled
     multipole and local coefficients (complex, [nbox, p+1]) when ``want_coeffs``.  ``parents``
-    applies the optional parent-level interactions (see :func:`lists`)."""
+    and ``swap`` apply the optional optimisations (see :func:`lists`)."""
     x, y, q = _f64(x), _f64(y), _f64(q)
     n = x.shape[0]
     phi = np.empty(n, np.float64)
-    if parents:
+    if parents or swap:
         assert not want_coeffs
-        rc = _load().orc_fmm_ex(n, _ptr(x), _ptr(y), _ptr(q), L, p, float(theta), 1, _ptr(phi))
+        flags = (1 if parents else 0) | (2 if swap else 0)
+        rc = _load().orc_fmm_ex(n, _ptr(x), _ptr(y), _ptr(q), L, p, float(theta), flags, _ptr(phi))
         if rc:
             raise OracleError(f"orc_fmm_ex failed ({rc})")
         return phi
@@ -218,13 +239,15 @@ def direct(x, y, q, targets=None, nthreads: int = 0):
     return phi
 
 
-def fmm_field(x, y, q, L: int, p: int, theta: float):
+def fmm_field(x, y, q, L: int, p: int, theta: float, parents: bool = False, swap: bool = False):
     """The complex field F_i = sum_{j != i} -q_j / (z_i - z_j) by the method (Section 5's first
-    experiment); returns a complex array in input order."""
+    experiment); returns a complex array in input order.  ``parents`` / ``swap`` as :func:`fmm`."""
     x, y, q = _f64(x), _f64(y), _f64(q)
     n = x.shape[0]
     fre, fim = np.empty(n), np.empty(n)
-    rc = _load().orc_fmm_field(n, _ptr(x), _ptr(y), _ptr(q), int(L), int(p), float(theta), _ptr(fre), _ptr(fim))
+    flags = (1 if parents else 0) | (2 if swap else 0)
+    rc = _load().orc_fmm_field_ex(n, _ptr(x), _ptr(y), _ptr(q), int(L), int(p), float(theta), flags,
+                                  _ptr(fre), _ptr(fim))
     if rc:
         raise OracleError(f"orc_fmm_field returned {rc}")
     return fre + 1j * fim
@@ -280,6 +303,14 @@ def l2p(b, dz, p: int) -> float:
     """Re sum_l b_l dz^l."""
     b = _cvec(b, p)
     return float(_load().orc_l2p(_ptr(b), float(np.real(dz)), float(np.imag(dz)), p))
+
+
+def p2l(x, y, q, center, p: int):
+    """Local coefficients b_0..b_p about ``center`` of sources outside a disc about it (unscaled)."""
+    x, y, q = _f64(x), _f64(y), _f64(q)
+    b = np.empty(p + 1, np.complex128)
+    _load().orc_p2l(x.shape[0], _ptr(x), _ptr(y), _ptr(q), float(center[0]), float(center[1]), p, _ptr(b))
+    return b
 
 
 def m2p(a, dz, p: int) -> float:

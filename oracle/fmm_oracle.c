@@ -38,6 +38,12 @@
  *   R6  p is the order: coefficients k = 0..p (a_0 is the log term).
  *   R7  coincident points contribute nothing (log 0 is skipped, like j = i).
  *   R8  canonical point order: leaves in level order, inside a leaf ascending input index.
+ *   R19 parent-level interactions (optional, flags & 1): only four consecutive weak entries
+ *       4k .. 4k+3 (all children of one box, in candidate order) are replaced, by one entry for
+ *       their parent in the position of the first, when Criterion 2.1 holds for the parent.
+ *   R20 role exchange (optional, flags & 2): finest level only; a strong leaf pair passes when
+ *       r + theta*R <= theta*d and R + r < d; the smaller target takes P2L, the larger M2P; the
+ *       pair leaves the strong list.
  */
 #include <complex.h>
 #include <math.h>
@@ -195,6 +201,21 @@ int orc_theta_weak(double c1x, double c1y, double r1, double c2x, double c2y, do
     return (R + theta * r <= theta * d) && (R + r < d);
 }
 
+/*
+ * The same criterion with the roles of the two radii exchanged (Section 4, finest-level
+ * optimisation): r + theta*R <= theta*d, i.e. the smaller sphere seen from outside the larger one
+ * at ratio <= theta, for disjoint spheres.  Only differs from Criterion 2.1 when r < R.
+ */
+int orc_theta_swapped(double c1x, double c1y, double r1, double c2x, double c2y, double r2,
+                      double theta)
+{
+    double dx = c1x - c2x, dy = c1y - c2y;
+    double d = sqrt(dx * dx + dy * dy);
+    double R = r1 > r2 ? r1 : r2;
+    double r = r1 > r2 ? r2 : r1;
+    return (r + theta * R <= theta * d) && (R + r < d);
+}
+
 /* ------------------------------------------------------------------------------------------
  * Connectivity: Section 4.  S(root) = {root}, W(root) = {}.  For a box b on level l >= 1, the
  * candidates are the children of every box in S(parent(b)), taken in ascending id; a candidate
@@ -210,6 +231,8 @@ typedef struct {
     int32_t* widx;
     int32_t* sidx;
     int64_t wcap, scap;
+    int64_t* xoff;  /* role-exchange lists of the finest level (NULL unless built) */
+    int32_t* xidx;
 } orc_lists_t;
 
 static void push(int32_t** a, int64_t* cap, int64_t n, int32_t v)
@@ -309,17 +332,67 @@ void orc_lists_merge_parents(void* hp, const double* rects, double theta)
     free(c); free(r);
 }
 
-int64_t orc_lists_total(void* hp, int weak)
+/* The second optional optimisation of Section 4, at the finest level only: a strongly coupled
+ * pair of leaves of different radii whose criterion holds with the roles of r and R exchanged
+ * (orc_theta_swapped) is taken out of the strong list of the target leaf and put on its role
+ * exchange list X, in the same order.  If the target is the smaller leaf, the source's points
+ * become terms of the target's local expansion (P2L); if it is the larger one, the source's
+ * multipole expansion is evaluated at the target's points (M2P) and the entry carries
+ * ORC_SWAP_M2P.  Applied once, after the lists are complete. */
+#define ORC_SWAP_M2P 0x20000000
+
+void orc_lists_swap_leaves(void* hp, const double* rects, double theta)
 {
     orc_lists_t* h = (orc_lists_t*)hp;
-    return weak ? h->woff[h->nbox] : h->soff[h->nbox];
+    double* c = (double*)malloc(sizeof(double) * 2 * (size_t)h->nbox);
+    double* r = (double*)malloc(sizeof(double) * (size_t)h->nbox);
+    orc_geometry(h->nbox, rects, c, r);
+    const int64_t base = level_base(h->L);
+    int64_t* nsoff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(h->nbox + 1));
+    int32_t* nsidx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(h->soff[h->nbox] + 1));
+    h->xoff = (int64_t*)calloc((size_t)h->nbox + 1, sizeof(int64_t));
+    h->xidx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(h->soff[h->nbox] + 1));
+    int64_t ns = 0, nx = 0;
+    for (int64_t g = 0; g < h->nbox; g++) {
+        nsoff[g] = ns;
+        h->xoff[g] = nx;
+        for (int64_t e = h->soff[g]; e < h->soff[g + 1]; e++) {
+            const int32_t v = h->sidx[e];
+            const int64_t sg = base + v;
+            if (g >= base &&
+                orc_theta_swapped(c[2 * g], c[2 * g + 1], r[g], c[2 * sg], c[2 * sg + 1], r[sg], theta))
+                h->xidx[nx++] = r[g] > r[sg] ? (v | ORC_SWAP_M2P) : v;
+            else
+                nsidx[ns++] = v;
+        }
+    }
+    nsoff[h->nbox] = ns;
+    h->xoff[h->nbox] = nx;
+    free(h->soff);
+    free(h->sidx);
+    h->soff = nsoff;
+    h->sidx = nsidx;
+    h->scap = ns + 1;
+    free(c); free(r);
 }
 
-void orc_lists_copy(void* hp, int weak, int64_t* off, int32_t* idx)
+/* kind: 1 weak, 0 strong, 2 role exchange (empty unless orc_lists_swap_leaves ran) */
+int64_t orc_lists_total(void* hp, int kind)
 {
     orc_lists_t* h = (orc_lists_t*)hp;
-    const int64_t* o = weak ? h->woff : h->soff;
-    const int32_t* v = weak ? h->widx : h->sidx;
+    if (kind == 2) return h->xoff ? h->xoff[h->nbox] : 0;
+    return kind ? h->woff[h->nbox] : h->soff[h->nbox];
+}
+
+void orc_lists_copy(void* hp, int kind, int64_t* off, int32_t* idx)
+{
+    orc_lists_t* h = (orc_lists_t*)hp;
+    if (kind == 2 && !h->xoff) {
+        memset(off, 0, sizeof(int64_t) * (size_t)(h->nbox + 1));
+        return;
+    }
+    const int64_t* o = kind == 2 ? h->xoff : kind ? h->woff : h->soff;
+    const int32_t* v = kind == 2 ? h->xidx : kind ? h->widx : h->sidx;
     memcpy(off, o, sizeof(int64_t) * (size_t)(h->nbox + 1));
     if (o[h->nbox]) memcpy(idx, v, sizeof(int32_t) * (size_t)o[h->nbox]);
 }
@@ -328,7 +401,7 @@ void orc_lists_free(void* hp)
 {
     orc_lists_t* h = (orc_lists_t*)hp;
     if (!h) return;
-    free(h->woff); free(h->soff); free(h->widx); free(h->sidx); free(h);
+    free(h->woff); free(h->soff); free(h->widx); free(h->sidx); free(h->xoff); free(h->xidx); free(h);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -456,12 +529,42 @@ static cplx l2p_deriv(const cplx* b, cplx dz, int p)
     return s;
 }
 
-/* M2P (test helper only): Re[a_0 log(dz) + sum_k a_k dz^{-k}], dz = z - c. */
+/* M2P: Re[a_0 log(dz) + sum_k a_k dz^{-k}], dz = z - c (the multipole evaluated at a point;
+ * used by the role exchange of Section 4). */
 static double m2p(const cplx* a, cplx dz, int p)
 {
     cplx s = a[0] * clog(dz), pw = 1.0, inv = 1.0 / dz;
     for (int k = 1; k <= p; k++) { pw *= inv; s += a[k] * pw; }
     return creal(s);
+}
+
+/* Derivative of the multipole expansion in z: a_0 / dz - sum_k k a_k dz^{-k-1}. */
+static cplx m2p_deriv(const cplx* a, cplx dz, int p)
+{
+    cplx inv = 1.0 / dz, pw = inv, s = a[0] * inv;
+    for (int k = 1; k <= p; k++) { pw *= inv; s -= (double)k * a[k] * pw; }
+    return s;
+}
+
+/*
+ * P2L: the local expansion about c of sources z_j lying outside a disc about c that holds the
+ * evaluation points (the role exchange of Section 4).  With w = z - c,
+ *   log(z - z_j) = log(c - z_j) + log(1 - w / (z_j - c)) = log(c - z_j) - sum_{l>=1} (w/(z_j - c))^l / l,
+ * so b_0 += q_j log(c - z_j) and b_l += -q_j / (l (z_j - c)^l).  Accumulates into b.
+ */
+static void p2l(int64_t m, const int32_t* ids, const double* x, const double* y, const double* q,
+                cplx c, int p, cplx* b)
+{
+    for (int64_t t = 0; t < m; t++) {
+        int64_t j = ids ? ids[t] : t;
+        cplx dz = (x[j] + I * y[j]) - c;
+        cplx inv = 1.0 / dz, pw = 1.0;
+        b[0] += q[j] * clog(-dz);
+        for (int l = 1; l <= p; l++) {
+            pw *= inv;
+            b[l] -= q[j] * pw / (double)l;
+        }
+    }
 }
 
 /* ---- flat-array wrappers of the operators (complex numbers interleaved re, im) ---- */
@@ -472,6 +575,16 @@ void orc_p2m(int64_t m, const double* x, const double* y, const double* q, doubl
     cplx a[ORC_PMAX + 1];
     p2m(m, NULL, x, y, q, cx + I * cy, p, a);
     for (int k = 0; k <= p; k++) { a_out[2 * k] = creal(a[k]); a_out[2 * k + 1] = cimag(a[k]); }
+}
+
+/* P2L of m sources about (cx, cy); b_out receives the p+1 local coefficients. */
+void orc_p2l(int64_t m, const double* x, const double* y, const double* q, double cx, double cy,
+             int p, double* b_out)
+{
+    cplx b[ORC_PMAX + 1];
+    for (int l = 0; l <= p; l++) b[l] = 0;
+    p2l(m, NULL, x, y, q, cx + I * cy, p, b);
+    for (int l = 0; l <= p; l++) { b_out[2 * l] = creal(b[l]); b_out[2 * l + 1] = cimag(b[l]); }
 }
 
 static void load_c(const double* v, int p, cplx* c)
@@ -602,6 +715,7 @@ static int fmm_core(int64_t n, const double* x, const double* y, const double* q
     orc_geometry(nbox, rects, cen, rad);
     orc_lists_t* li = (orc_lists_t*)orc_lists_build(L, rects, theta);
     if (flags & 1) orc_lists_merge_parents(li, rects, theta);
+    if (flags & 2) orc_lists_swap_leaves(li, rects, theta);
     int P = p + 1;
     cplx* M = (cplx*)calloc((size_t)(nbox * P), sizeof(cplx));
     cplx* Lc = (cplx*)calloc((size_t)(nbox * P), sizeof(cplx));
@@ -639,14 +753,34 @@ static int fmm_core(int64_t n, const double* x, const double* y, const double* q
                 }
         }
     }
-    /* evaluation on the finest level: L2P plus direct sums over the strong lists */
+    /* role exchange (flags & 2): the sources of a larger leaf on a smaller target's X list join
+     * the target's local expansion (P2L) */
+    if (li->xoff)
+        for (int64_t b = 0; b < nleaf; b++) {
+            int64_t g = lbase + b;
+            for (int64_t e = li->xoff[g]; e < li->xoff[g + 1]; e++) {
+                const int32_t v = li->xidx[e];
+                if (v & ORC_SWAP_M2P) continue;
+                p2l(lb[v + 1] - lb[v], perm + lb[v], x, y, q, CEN(g), p, Lc + g * P);
+            }
+        }
+    /* evaluation on the finest level: L2P plus direct sums over the strong lists (and, with the
+     * role exchange, the multipoles of the smaller leaves on the X list evaluated directly) */
     for (int64_t b = 0; b < nleaf; b++) {
         int64_t g = lbase + b;
+        const int64_t x0 = li->xoff ? li->xoff[g] : 0, x1 = li->xoff ? li->xoff[g + 1] : 0;
         for (int64_t t = lb[b]; t < lb[b + 1]; t++) {
             int64_t i = perm[t];
+            const cplx zi = x[i] + I * y[i];
             if (fre) {
                 /* the field: minus the derivative of the local expansion, minus the near sum */
-                cplx f = -l2p_deriv(Lc + g * P, (x[i] + I * y[i]) - CEN(g), p);
+                cplx f = -l2p_deriv(Lc + g * P, zi - CEN(g), p);
+                for (int64_t e = x0; e < x1; e++) {
+                    const int32_t v = li->xidx[e];
+                    if (!(v & ORC_SWAP_M2P)) continue;
+                    const int64_t sg = lbase + (v & ~ORC_SWAP_M2P);
+                    f -= m2p_deriv(M + sg * P, zi - CEN(sg), p);
+                }
                 for (int64_t e = li->soff[g]; e < li->soff[g + 1]; e++) {
                     int64_t sb = li->sidx[e];
                     for (int64_t u = lb[sb]; u < lb[sb + 1]; u++) {
@@ -661,7 +795,13 @@ static int fmm_core(int64_t n, const double* x, const double* y, const double* q
                 fim[i] = cimag(f);
                 continue;
             }
-            double s = l2p(Lc + g * P, (x[i] + I * y[i]) - CEN(g), p);
+            double s = l2p(Lc + g * P, zi - CEN(g), p);
+            for (int64_t e = x0; e < x1; e++) {
+                const int32_t v = li->xidx[e];
+                if (!(v & ORC_SWAP_M2P)) continue;
+                const int64_t sg = lbase + (v & ~ORC_SWAP_M2P);
+                s += m2p(M + sg * P, zi - CEN(sg), p);
+            }
             for (int64_t e = li->soff[g]; e < li->soff[g + 1]; e++) {
                 int64_t sb = li->sidx[e];
                 for (int64_t u = lb[sb]; u < lb[sb + 1]; u++) {
@@ -691,7 +831,9 @@ int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L,
     return fmm_core(n, x, y, q, L, p, theta, 0, phi, NULL, NULL, mpole_out, local_out);
 }
 
-/* The method with the optional parent-level interactions (flags & 1, see orc_lists_merge_parents). */
+/* The method with the optional structural optimisations of Section 4: flags & 1 parent-level
+ * interactions (orc_lists_merge_parents), flags & 2 the finest-level role exchange
+ * (orc_lists_swap_leaves). */
 int orc_fmm_ex(int64_t n, const double* x, const double* y, const double* q, int L, int p,
                double theta, int flags, double* phi)
 {
@@ -705,4 +847,11 @@ int orc_fmm_field(int64_t n, const double* x, const double* y, const double* q, 
                   double theta, double* fre, double* fim)
 {
     return fmm_core(n, x, y, q, L, p, theta, 0, NULL, fre, fim, NULL, NULL);
+}
+
+/* The field with the optional optimisations (flags as orc_fmm_ex). */
+int orc_fmm_field_ex(int64_t n, const double* x, const double* y, const double* q, int L, int p,
+                     double theta, int flags, double* fre, double* fim)
+{
+    return fmm_core(n, x, y, q, L, p, theta, flags, NULL, fre, fim, NULL, NULL);
 }
