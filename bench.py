@@ -272,9 +272,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched workload")
-    ap.add_argument("--lists", default="auto", choices=["auto", "plain", "parents"],
-                    help="interaction lists: the plain rule, with parent-level interactions (Section 4), "
-                         "or the faster of the two on this workload")
+    ap.add_argument("--lists", default="auto", choices=["auto", "plain", "parents", "exchange", "parents+exchange"],
+                    help="interaction lists: the plain rule, with Section 4's parent-level interactions and/or "
+                         "finest-level role exchange, or the fastest variant on this workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -337,8 +337,9 @@ def main():
     fmm.fmm_sync_status(f.tree, f.lists)
     fmm.fmm_lists_sync(f.lists)
 
-    # Section 4's optional parent-level interactions change the lists (fewer M2L shifts), not the
-    # accuracy class; "auto" keeps whichever variant runs the whole step faster here
+    # Section 4's optional optimisations (parent-level interactions: fewer M2L shifts; role
+    # exchange: P2L / M2P instead of some near-field pairs) change the lists, not the accuracy
+    # class; "auto" keeps whichever variant runs the whole step fastest here
     def time_lists(mode_lists, k=20):
         fmm.fmm_lists_set_mode(f.lists, mode_lists)
         step(fmm.FMM_MODE_MIXED)
@@ -351,14 +352,16 @@ def main():
         torch.cuda.synchronize()
         return a.elapsed_time(b) / k
 
+    variants = {"plain": fmm.FMM_LISTS_PLAIN, "parents": fmm.FMM_LISTS_PARENTS,
+                "exchange": fmm.FMM_LISTS_EXCHANGE,
+                "parents+exchange": fmm.FMM_LISTS_PARENTS | fmm.FMM_LISTS_EXCHANGE}
     lists_ms = {}
     if args.lists == "auto":
-        lists_ms = {name: time_lists(m) for name, m in (("plain", fmm.FMM_LISTS_PLAIN),
-                                                       ("parents", fmm.FMM_LISTS_PARENTS))}
+        lists_ms = {name: time_lists(m) for name, m in variants.items()}
         lists_kind = min(lists_ms, key=lists_ms.get)
     else:
         lists_kind = args.lists
-    fmm.fmm_lists_set_mode(f.lists, fmm.FMM_LISTS_PARENTS if lists_kind == "parents" else fmm.FMM_LISTS_PLAIN)
+    fmm.fmm_lists_set_mode(f.lists, variants[lists_kind])
     step(fmm.FMM_MODE_MIXED)
     fmm.fmm_sync_status(f.tree, f.lists)
     tuned = {fmm.FMM_MODE_FP64: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_FP64, phi),
@@ -495,8 +498,7 @@ def main():
                                         "near_field": tuned[fmm.FMM_MODE_MIXED][1]},
                    "m2l_kernel": "tensor cores (tcgen05, split tf32)" if m2l_kind == fmm.FMM_M2L_TENSOR
                    else "SIMT binary32",
-                   "lists": lists_kind + (" (parent-level interactions, Section 4)" if lists_kind == "parents"
-                                          else ""),
+                   "lists": lists_kind + ("" if lists_kind == "plain" else " (Section 4's optional optimisations)"),
                    "lists_trial_ms_per_step": lists_ms or None},
         "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,
         "fp64_path": {"value": world * n / (ms_fp64 / args.fp64_steps * 1e-3),

@@ -177,16 +177,32 @@ int fmm_lists_create(fmm_tree t, int64_t weak_capacity, int64_t strong_capacity,
 int fmm_lists_create_batched(fmm_tree t, const int64_t* weak_capacity_host,
                              const int64_t* strong_capacity_host, fmm_lists* out);
 
-/* Optional structural optimisation of Section 4 (mode FMM_LISTS_PARENTS; FMM_LISTS_PLAIN is the
- * default): a box whose weak list holds all four children of a box P of the level above, as four
- * consecutive entries 4k .. 4k+3, interacts with P instead whenever the theta-criterion between P
- * and the box holds.  Such an entry is k | FMM_PARENT_FLAG (a within-level index of the level
- * above).  Strong lists are unchanged.  Setting the mode allocates (synchronous) and requires a
- * rebuild of the lists. */
+/* Optional structural optimisations of Section 4; mode is a combination of the bits below
+ * (FMM_LISTS_PLAIN = 0 is the default).
+ *  FMM_LISTS_PARENTS: a box whose weak list holds all four children of a box P of the level
+ *    above, as four consecutive entries 4k .. 4k+3, interacts with P instead whenever the
+ *    theta-criterion between P and the box holds.  Such an entry is k | FMM_PARENT_FLAG (a
+ *    within-level index of the level above).
+ *  FMM_LISTS_EXCHANGE: at the finest level, a strongly coupled pair of leaves of different radii
+ *    for which the criterion holds with the roles of r and R exchanged (r + theta*R <= theta*d,
+ *    disjoint circles) leaves the strong list of the target for its exchange list: if the target
+ *    is the smaller leaf the source's points are added to its local expansion (P2L), else the
+ *    source's multipole expansion is evaluated at its points (M2P; entry s | FMM_SWAP_M2P).
+ * Setting the mode allocates (synchronous) and requires a rebuild of the lists.  The exchange
+ * lists share the strong capacity (their count is checked against it). */
 #define FMM_LISTS_PLAIN 0
 #define FMM_LISTS_PARENTS 1
+#define FMM_LISTS_EXCHANGE 2
 #define FMM_PARENT_FLAG 0x40000000
+#define FMM_SWAP_M2P 0x20000000
 int fmm_lists_set_mode(fmm_lists l, int mode);
+
+/* Instance i's exchange lists (FMM_LISTS_EXCHANGE): xoff[nbox_i + 1] offsets over all its boxes
+ * in level order (empty below the finest level), xidx[xoff[nbox_i]] within-level leaf indices
+ * (| FMM_SWAP_M2P where the target is the larger leaf).  Device buffers; either may be NULL.
+ * Synchronises the stream; *count_host (may be NULL) receives the number of entries. */
+int fmm_lists_export_exchange(fmm_lists l, int i, int32_t* xoff, int32_t* xidx, int64_t* count_host,
+                              void* stream);
 
 /* Build the lists of tree t (which must have been built on the same stream or be complete)
  * for 0 < theta < 1.  Overflow of the capacity sets FMM_ERR_CAPACITY in the device status;

@@ -108,7 +108,7 @@ void free_lists(fmm_lists l)
 {
     if (!l) return;
     void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status,
-                    l->dlinst, l->tiledrop};
+                    l->dlinst, l->tiledrop, l->tileswap, l->xoff, l->xidx, l->xtgt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] l->hlinst;
@@ -325,15 +325,47 @@ int fmm_lists_create_batched(fmm_tree t, const int64_t* weak_capacity, const int
 int fmm_lists_set_mode(fmm_lists l, int mode)
 {
     if (!l) return fail(FMM_ERR_ARG, "NULL lists");
-    if (mode != FMM_LISTS_PLAIN && mode != FMM_LISTS_PARENTS) return fail(FMM_ERR_ARG, "unknown lists mode %d", mode);
+    if (mode & ~(FMM_LISTS_PARENTS | FMM_LISTS_EXCHANGE)) return fail(FMM_ERR_ARG, "unknown lists mode %d", mode);
     GUARD(l->tree->dev);
-    if (mode == FMM_LISTS_PARENTS && !l->tiledrop) {
-        int64_t words = 0;
-        for (int i = 0; i < l->tree->n_inst; i++) words += lists_tile_words(l->hlinst[i].scap);
-        if (cudaMalloc((void**)&l->tiledrop, 4 * words) != cudaSuccess) return fail(FMM_ERR_OOM, "list storage");
+    int64_t words = 0, scap = 0;
+    for (int i = 0; i < l->tree->n_inst; i++) {
+        words += lists_tile_words(l->hlinst[i].scap);
+        scap += l->hlinst[i].scap;
+    }
+    if ((mode & FMM_LISTS_PARENTS) && !l->tiledrop &&
+        cudaMalloc((void**)&l->tiledrop, 4 * words) != cudaSuccess)
+        return fail(FMM_ERR_OOM, "list storage");
+    if ((mode & FMM_LISTS_EXCHANGE) && !l->tileswap) {
+        if (cudaMalloc((void**)&l->tileswap, 4 * words) != cudaSuccess ||
+            cudaMalloc((void**)&l->xoff, 4 * (size_t)(l->tree->nbox + l->tree->n_inst)) != cudaSuccess ||
+            cudaMalloc((void**)&l->xidx, 4 * (size_t)std::max<int64_t>(scap, 1)) != cudaSuccess ||
+            cudaMalloc((void**)&l->xtgt, 4 * (size_t)std::max<int64_t>(scap, 1)) != cudaSuccess)
+            return fail(FMM_ERR_OOM, "list storage");
     }
     l->mode = mode;
     l->built = false;  // the lists must be rebuilt in the new mode
+    return FMM_OK;
+}
+
+int fmm_lists_export_exchange(fmm_lists l, int i, int32_t* xoff, int32_t* xidx, int64_t* count, void* stream)
+{
+    if (!l) return fail(FMM_ERR_ARG, "NULL lists");
+    if (!l->built) return fail(FMM_ERR_STATE, "lists not built");
+    if (!(l->mode & FMM_LISTS_EXCHANGE)) return fail(FMM_ERR_STATE, "the lists were built without the role exchange");
+    fmm_tree t = l->tree;
+    if (i < 0 || i >= t->n_inst) return fail(FMM_ERR_ARG, "instance %d outside [0, %d)", i, t->n_inst);
+    GUARD(t->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Inst& S = t->hinst[i];
+    const LInst& T = l->hlinst[i];
+    FMM_CUDA(cudaStreamSynchronize(s));
+    int32_t x = 0;
+    FMM_CUDA(cudaMemcpy(&x, l->xoff + S.o0 + S.nbox, 4, cudaMemcpyDeviceToHost));
+    if (count) *count = x;
+    if (xoff) FMM_CUDA(cudaMemcpyAsync(xoff, l->xoff + S.o0, 4 * (S.nbox + 1), cudaMemcpyDeviceToDevice, s));
+    if (xidx && x > 0)
+        FMM_CUDA(cudaMemcpyAsync(xidx, l->xidx + T.s0, 4 * std::min<int64_t>(x, T.scap), cudaMemcpyDeviceToDevice, s));
+    FMM_CUDA(cudaStreamSynchronize(s));
     return FMM_OK;
 }
 

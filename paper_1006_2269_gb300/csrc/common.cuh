@@ -45,6 +45,8 @@ constexpr int TREE_TILE = TREE_TPB * TREE_ITEMS;
 
 // Weak-list entry naming the parent (level l - 1) of four weak siblings: index | PARENT_FLAG.
 constexpr int32_t PARENT_FLAG = FMM_PARENT_FLAG;
+// Exchange-list entry whose target is the larger leaf (M2P); without it the target takes P2L.
+constexpr int32_t SWAP_M2P = FMM_SWAP_M2P;
 
 // ---- level-order box numbering ----
 __host__ __device__ inline int64_t level_base(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
@@ -267,11 +269,16 @@ struct fmm_lists_s {
     int32_t* status = nullptr;
     double theta = 0.0;
     bool built = false;
-    // parent-level interactions (Section 4's optional optimisation): FMM_LISTS_PARENTS lets
-    // four weak siblings become one entry naming their parent; tiledrop counts the siblings
-    // dropped per candidate tile
+    // Section 4's optional optimisations (mode bits): FMM_LISTS_PARENTS lets four weak siblings
+    // become one entry naming their parent; tiledrop counts the siblings dropped per tile
     int mode = 0;
     uint32_t* tiledrop = nullptr;
+    // finest-level role exchange (FMM_LISTS_EXCHANGE): per-tile counts and the exchange lists
+    // (offsets in the layout of woff, entries in that of the strong lists)
+    uint32_t* tileswap = nullptr;
+    int32_t* xoff = nullptr;
+    int32_t* xidx = nullptr;
+    int32_t* xtgt = nullptr;  // target leaf (global id) of each exchange entry
 };
 
 namespace fmm {

@@ -101,6 +101,11 @@ struct Geo<double> {
     }
     __device__ __forceinline__ double radius(int64_t g) const { return rad[g]; }
     __device__ __forceinline__ Geo shift(int64_t b0) const { return Geo{cen + 2 * b0, rad + b0}; }
+    // z - c_b for a point of leaf a (absolute coordinates)
+    __device__ __forceinline__ cx<double> rel(int64_t a, int64_t b, double x, double y) const
+    {
+        return {x - cen[2 * b], y - cen[2 * b + 1]};
+    }
     // (z - c_g) / rho_g for a point stored with absolute coordinates (0 when rho_g = 0)
     __device__ __forceinline__ cx<double> local(int64_t g, double x, double y) const
     {
@@ -122,6 +127,12 @@ struct Geo<float> {
     }
     __device__ __forceinline__ float radius(int64_t g) const { return rad[g]; }
     __device__ __forceinline__ Geo shift(int64_t b0) const { return Geo{hi + 2 * b0, lo + 2 * b0, rad + b0}; }
+    // z - c_b for a point of leaf a (stored as its offset from c_a)
+    __device__ __forceinline__ cx<float> rel(int64_t a, int64_t b, float x, float y) const
+    {
+        const cx<float> d = diff(a, b);
+        return {d.re + x, d.im + y};
+    }
     // the point is stored as its offset from the centre of leaf g
     __device__ __forceinline__ cx<float> local(int64_t g, float x, float y) const
     {
@@ -594,6 +605,272 @@ __global__ void k_l2l(Sched sc, const Inst* __restrict__ I, int l, int P, int PS
 // ---- L2P: one thread per point (canonical order); initialises the accumulator ----
 // binary64 path: writes the binary64 accumulator.  binary32 path: writes the binary32 far field;
 // the near-field accumulators are combined with it at the end.
+// ---- role exchange at the finest level (Section 4) ----
+// Exchange-list entries of leaf g: xoff / xidx already offset to the instance.
+struct XLists {
+    const int32_t* xoff;
+    const int32_t* xidx;
+    const int32_t* xtgt;
+};
+
+// M2P: the multipole of source leaf sg evaluated at a point, dz = z - c_sg, w = rho_s / dz:
+//   phi += a_0 log|dz| + Re sum_{k>=1} a~_k w^k
+// (field: minus the derivative, -(a_0 - sum_k k a~_k w^k) / dz).
+template <typename T>
+__device__ __forceinline__ cx<T> m2p_w(cx<T> dz, T rho, T& inv_abs2)
+{
+    const T a2 = dz.re * dz.re + dz.im * dz.im;
+    inv_abs2 = (T)1 / a2;
+    return {rho * dz.re * inv_abs2, -rho * dz.im * inv_abs2};
+}
+
+// P2L: one warp per target leaf; the points of all its P2L sources form one stream, 32 at a
+// time (lane = point), each lane's terms q log|dz| and q u^l (u = rho_t / dz) go through shared
+// memory and lane l sums column l.  In scaled form b~_0 += sum q log|dz|,
+// b~_l += -sum q u^l / l.  The leaf is owned by its warp: plain read-modify-write of Le.
+// schedule: the leaves, WPB per block (the P2M schedule)
+template <typename T>
+__global__ void k_p2l(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs, int P, int PS,
+                      const int32_t* __restrict__ lb, const Pk<T>* __restrict__ pk, Geo<T> geo, XLists xl,
+                      cx<T>* __restrict__ Le, float* __restrict__ L0lo)
+{
+    extern __shared__ unsigned char smem[];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const int L = S.L;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    if (L < 1) return;
+    lb += S.lb0;
+    pk += S.p0;
+    geo = geo.shift(S.b0);
+    Le += S.b0 * PS;
+    if constexpr (sizeof(T) == 4) L0lo += S.b0;
+    const int32_t* xoff = xl.xoff + S.o0;
+    const int32_t* xidx = xl.xidx + LIs[z.i].s0;
+    const int64_t base = level_base(L);
+    cx<T>* Sm = (cx<T>*)smem + (size_t)w * 33 * P;
+    for (int64_t b = (int64_t)z.rank * wpb + w; b < level_size(L); b += (int64_t)z.nb * wpb) {
+        const int64_t g = base + b;
+        const int32_t x0 = xoff[g], x1 = xoff[g + 1];
+        if (x0 == x1) continue;
+        const T rho = geo.radius(g);
+        cx<T> acc[2] = {{0, 0}, {0, 0}};
+        T acc0 = 0;
+        for (int32_t e0 = x0; e0 < x1; e0 += 32) {
+            // lane k describes entry e0 + k: its source's first point and count (0 for M2P entries)
+            int32_t cnt = 0, first = 0, src = 0;
+            if (e0 + lane < x1) {
+                const int32_t v = xidx[e0 + lane];
+                if (!(v & SWAP_M2P)) {
+                    first = lb[v];
+                    cnt = lb[v + 1] - first;
+                    src = v;
+                }
+            }
+            int32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int32_t excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int32_t f0 = 0; f0 < total; f0 += 32) {
+                const int32_t fi = f0 + lane;
+                // owner: the last lane k with excl_k <= fi (excl is non-decreasing)
+                int k = 0;
+#pragma unroll
+                for (int st = 16; st; st >>= 1) {
+                    const int cand = k + st;
+                    const int32_t ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+                    if (cand < 32 && ec <= fi) k = cand;
+                }
+                const int32_t fk = __shfl_sync(0xffffffffu, first, k);
+                const int32_t ek = __shfl_sync(0xffffffffu, excl, k);
+                const int32_t sk = __shfl_sync(0xffffffffu, src, k);
+                T qq = 0, lg = 0;
+                cx<T> u = {0, 0};
+                if (fi < total) {
+                    const Pk<T> pt = pk[fk + (fi - ek)];
+                    const cx<T> dz = geo.rel(base + sk, g, pt.x, pt.y);
+                    T inv2;
+                    u = m2p_w(dz, rho, inv2);
+                    qq = pt.q;
+                    lg = qq * (T)0.5 * log_d(dz.re * dz.re + dz.im * dz.im);
+                }
+                cx<T> pw = {qq, 0};
+                Sm[lane] = {lg, 0};
+                for (int l = 1; l < P; l++) {
+                    pw = cmul(pw, u);
+                    Sm[l * 33 + lane] = pw;
+                }
+                __syncwarp();
+                for (int l = lane, s2 = 0; l < P; l += 32, s2++) {
+                    cx<T> sum = {0, 0};
+                    for (int j = 0; j < 32; j++) sum = cadd(sum, Sm[l * 33 + j]);
+                    if (l == 0) acc0 += sum.re;
+                    else acc[s2] = cadd(acc[s2], sum);
+                }
+                __syncwarp();
+            }
+        }
+        cx<T>* B = Le + g * PS;
+        for (int l = lane, s2 = 0; l < P; l += 32, s2++) {
+            if (l == 0) {
+                if constexpr (sizeof(T) == 4) {
+                    float hi = B[0].re, lo = L0lo[g];
+                    two_sum(hi, lo, acc0);
+                    B[0].re = hi;
+                    L0lo[g] = lo;
+                } else {
+                    B[0].re += acc0;
+                }
+            } else {
+                B[l] = cadd(B[l], cscale(acc[s2], (T)-1 / (T)l));
+            }
+        }
+    }
+}
+
+// M2P over the flat exchange lists (entries sorted by target leaf): lane groups of gs lanes
+// (gs >= the largest leaf, up to 32) each walk runs of XCH consecutive entries; a lane takes the
+// target's points gl, gl + gs, ... and accumulates the values of the run's M2P sources in
+// registers (MAXPL points per lane, beyond that directly), flushing them atomically when the
+// target changes.  Potential: adds a_0 log|dz| + Re sum a~_k w^k to acc_re (binary32 path:
+// float-float hi/lo); field (FIELD): adds -(a_0 - sum_k k a~_k w^k) / dz to acc_re/acc_im.
+constexpr int XCH = 8;
+constexpr int MAXPL = 4;
+
+template <typename T>
+struct Acc2 {
+    T hi;
+    float lo;
+};
+
+template <typename T>
+__device__ __forceinline__ void acc_add(Acc2<T>& a, T v)
+{
+    if constexpr (sizeof(T) == 4) two_sum(a.hi, a.lo, v);
+    else a.hi += v;
+}
+
+template <typename T>
+__device__ __forceinline__ void acc_flush(T* hi, float* lo, int64_t i, const Acc2<T>& a)
+{
+    if constexpr (sizeof(T) == 4) atomic_add_ff(hi + i, lo + i, a.hi, a.lo);
+    else atomicAdd(hi + i, a.hi);
+}
+
+// schedule: the near-field schedule (blocks per instance in proportion to its near work)
+template <typename T, bool FIELD>
+__global__ void __launch_bounds__(256) k_m2p(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+                                             int P, int PS, int gs, const int32_t* __restrict__ lb,
+                                             const Pk<T>* __restrict__ pk, Geo<T> geo, XLists xl,
+                                             const cx<T>* __restrict__ Me, T* __restrict__ re_hi,
+                                             float* __restrict__ re_lo, T* __restrict__ im_hi,
+                                             float* __restrict__ im_lo)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst T_ = LIs[z.i];
+    const int L = S.L;
+    if (L < 1) return;
+    lb += S.lb0;
+    pk += S.p0;
+    geo = geo.shift(S.b0);
+    Me += S.b0 * PS;
+    re_hi += S.p0;
+    if constexpr (sizeof(T) == 4) re_lo += S.p0;
+    if (FIELD) {
+        im_hi += S.p0;
+        if constexpr (sizeof(T) == 4) im_lo += S.p0;
+    }
+    const int32_t* xidx = xl.xidx + T_.s0;
+    const int32_t* xtgt = xl.xtgt + T_.s0;
+    const int64_t nx = min((int64_t)xl.xoff[S.o0 + S.nbox], T_.scap);
+    const int64_t base = level_base(L);
+    const int lane = threadIdx.x & 31, G = 32 / gs, grp = lane / gs, gl = lane % gs;
+    const int64_t wg = (int64_t)z.rank * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)z.nb * (blockDim.x >> 5);
+    for (int64_t r = wg * G + grp; r * XCH < nx; r += nw * G) {
+        const int64_t e1 = min(r * XCH + XCH, nx);
+        int64_t cur = -1;
+        int32_t t0 = 0, nt = 0;
+        Acc2<T> ar[MAXPL], ai[MAXPL];
+        auto flush = [&]() {
+#pragma unroll
+            for (int j = 0; j < MAXPL; j++) {
+                const int32_t k = gl + j * gs;
+                if (k < nt) {
+                    acc_flush(re_hi, re_lo, t0 + k, ar[j]);
+                    if (FIELD) acc_flush(im_hi, im_lo, t0 + k, ai[j]);
+                }
+                ar[j] = {0, 0.f};
+                ai[j] = {0, 0.f};
+            }
+        };
+#pragma unroll
+        for (int j = 0; j < MAXPL; j++) {
+            ar[j] = {0, 0.f};
+            ai[j] = {0, 0.f};
+        }
+        for (int64_t e = r * XCH; e < e1; e++) {
+            const int32_t v = xidx[e];
+            if (!(v & SWAP_M2P)) continue;
+            const int64_t g = xtgt[e];
+            if (g != cur) {
+                flush();
+                cur = g;
+                t0 = lb[g - base];
+                nt = lb[g - base + 1] - t0;
+            }
+            const int64_t sg = base + (v & ~SWAP_M2P);
+            cx<T> d = {0, 0};  // c_g - c_sg (the binary32 points are offsets from c_g)
+            if constexpr (sizeof(T) == 4) d = geo.diff(g, sg);
+            const T rho = geo.radius(sg);
+            const cx<T>* A = Me + sg * PS;
+            // the value at target point t0 + k: vr (potential or Re F), vi (Im F)
+            auto eval = [&](int32_t k, T& vr, T& vi) {
+                const Pk<T> p = pk[t0 + k];
+                cx<T> dz;
+                if constexpr (sizeof(T) == 4) dz = {d.re + p.x, d.im + p.y};
+                else dz = geo.rel(g, sg, p.x, p.y);
+                T inv2;
+                const cx<T> w = m2p_w(dz, rho, inv2);
+                cx<T> h = {0, 0};
+                if (FIELD) {
+                    for (int kk = P - 1; kk >= 1; kk--) h = cfma(h, w, cscale(A[kk], (T)kk));
+                    const cx<T> hw = cmul(h, w);
+                    const cx<T> num = {A[0].re - hw.re, -hw.im};
+                    const cx<T> dv = cmul(num, cx<T>{dz.re * inv2, -dz.im * inv2});
+                    vr = -dv.re;
+                    vi = -dv.im;
+                } else {
+                    for (int kk = P - 1; kk >= 1; kk--) h = cfma(h, w, A[kk]);
+                    vr = A[0].re * (T)-0.5 * log_d(inv2) + cmul(h, w).re;
+                    vi = 0;
+                }
+            };
+#pragma unroll
+            for (int j = 0; j < MAXPL; j++) {
+                const int32_t k = gl + j * gs;
+                if (k < nt) {
+                    T vr, vi;
+                    eval(k, vr, vi);
+                    acc_add(ar[j], vr);
+                    if (FIELD) acc_add(ai[j], vi);
+                }
+            }
+            for (int32_t k = gl + MAXPL * gs; k < nt; k += gs) {  // leaves beyond MAXPL points a lane
+                T vr, vi;
+                eval(k, vr, vi);
+                acc_flush(re_hi, re_lo, t0 + k, Acc2<T>{vr, 0.f});
+                if (FIELD) acc_flush(im_hi, im_lo, t0 + k, Acc2<T>{vi, 0.f});
+            }
+        }
+        flush();
+    }
+}
+
 template <typename T>
 __global__ void k_l2p(Sched sc, const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ cleaf,
                       const Pk<T>* __restrict__ pk, Geo<T> geo, const cx<T>* __restrict__ Le,
@@ -1630,8 +1907,21 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             FMM_LAUNCH_CHECK("evaluate: L2L");
         }
     }
+    // role exchange (Section 4): P2L into the leaves' local expansions before they are evaluated
+    const bool swp = (li->mode & FMM_LISTS_EXCHANGE) != 0 && Lmax >= 1;
+    const XLists xl{li->xoff, li->xidx, li->xtgt};
+    int gsx = 1;  // lane group of the M2P kernel: the largest leaf, up to a warp
+    while (gsx < std::min<int64_t>(maxleaf, 32)) gsx <<= 1;
+    StageScope leaf_scope(FMM_STAGE_LEAF, s);  // P2L, L2P, M2P and the near field
+    if (swp) {
+        const size_t sm = (size_t)WPB * 33 * P * sizeof(cx<T>);
+        FMM_CUDA(cudaFuncSetAttribute(k_p2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_p2l<T><<<t->s_p2m.blocks, 32 * WPB, sm, s>>>(t->s_p2m.d, I, LI, P, PS, t->leaf_begin, pk, geo, xl, Le,
+                                                       t->Lf0lo);
+        note_launch();
+        FMM_LAUNCH_CHECK("evaluate: P2L");
+    }
     if (field) {
-        StageScope scope(FMM_STAGE_LEAF, s);
         const unsigned gp2p = (unsigned)t->s_p2p.blocks;
         const Sched sp2p = t->s_p2p.d;
         if constexpr (sizeof(T) == 4) {
@@ -1646,14 +1936,25 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
                                                 t->centers, (float4*)t->pkf, t->qf); note_launch();
             k_l2p_field<float><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, fr, fi, t->status);
             note_launch();
+            if (swp) {
+                k_m2p<float, true><<<gp2p, 256, 0, s>>>(sp2p, I, LI, P, PS, gsx, t->leaf_begin, pk, geo, xl, Me, hr,
+                                                        lr, hi, lo);
+                note_launch();
+            }
             k_p2p_field_f32<<<gp2p, 256, 0, s>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin,
                                                  (const float4*)t->pkf, t->qf, t->cen_hi, t->cen_lo, hr, lr,
                                                  hi, lo); note_launch();
             k_combine_field32<<<gpts, 256, 0, s>>>(spts, I, t->perm, fr, fi, hr, lr, hi, lo, phi, fim);
             note_launch();
         } else {
-            k_l2p_field<double><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->accf,
-                                                     t->accf + n, t->status); note_launch();
+            k_l2p_field<double><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->accf, t->accf + n,
+                                                     t->status);
+            note_launch();
+            if (swp) {
+                k_m2p<double, true><<<gp2p, 256, 0, s>>>(sp2p, I, LI, P, PS, gsx, t->leaf_begin, pk, geo, xl, Me,
+                                                         t->accf, nullptr, t->accf + n, nullptr);
+                note_launch();
+            }
             k_p2p_field64<<<gp2p, 256, 0, s>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin,
                                                (const Pk<double>*)pk, t->accf, t->accf + n); note_launch();
             k_unpermute_field<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->accf, t->accf + n, phi, fim);
@@ -1661,11 +1962,16 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         }
         FMM_LAUNCH_CHECK("evaluate: field");
     } else {
-        StageScope scope(FMM_STAGE_LEAF, s);
         if (!f64) FMM_CUDA(cudaMemsetAsync(nhi, 0, 2 * 4 * (size_t)n, s));
         k_l2p<T><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo,
                                       f64 ? (T*)t->acc : (T*)far32, farlo);
         note_launch();
+        if (swp) {
+            k_m2p<T, false><<<(unsigned)t->s_p2p.blocks, 256, 0, s>>>(t->s_p2p.d, I, LI, P, PS, gsx, t->leaf_begin, pk,
+                                                                     geo, xl, Me, f64 ? (T*)t->acc : (T*)far32,
+                                                                     farlo, nullptr, nullptr);
+            note_launch();
+        }
         const unsigned gp2p = (unsigned)t->s_p2p.blocks;
         const Sched sp2p = t->s_p2p.d;
         // instances whose leaves hold at most SMALL_LEAF points take the leaf-pair kernel, the

@@ -67,6 +67,46 @@ __device__ __forceinline__ bool theta_weak_fast(int64_t a, int64_t b, const floa
     return theta_weak(cen[2 * a], cen[2 * a + 1], rad[a], cen[2 * b], cen[2 * b + 1], rad[b], theta);
 }
 
+// Criterion 2.1 with the roles of the radii exchanged (Section 4's finest-level optimisation):
+// r + theta*R <= theta*d, disjoint spheres; binary64 in the same fixed order as theta_weak.
+__device__ __forceinline__ bool theta_swapped(double ax, double ay, double ra, double bx, double by,
+                                              double rb, double theta)
+{
+    double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by);
+    double d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+    double R = ra > rb ? ra : rb;
+    double r = ra > rb ? rb : ra;
+    return (__dadd_rn(r, __dmul_rn(theta, R)) <= __dmul_rn(theta, d)) && (__dadd_rn(R, r) < d);
+}
+
+// The same two-stage evaluation as theta_weak_fast.
+__device__ __forceinline__ bool theta_swapped_fast(int64_t a, int64_t b, const float* __restrict__ chi,
+                                                   const float* __restrict__ clo,
+                                                   const float* __restrict__ rad32, const double* __restrict__ cen,
+                                                   const double* __restrict__ rad, float th32, double theta)
+{
+    const float2 ha = *(const float2*)(chi + 2 * a), hb = *(const float2*)(chi + 2 * b);
+    const float2 la = *(const float2*)(clo + 2 * a), lb = *(const float2*)(clo + 2 * b);
+    const float dx = (ha.x - hb.x) + (la.x - lb.x), dy = (ha.y - hb.y) + (la.y - lb.y);
+    const float d = sqrtf(dx * dx + dy * dy);
+    const float ra = rad32[a], rb = rad32[b];
+    const float R = fmaxf(ra, rb), r = fminf(ra, rb);
+    const float m1 = th32 * d - (r + th32 * R), s1 = th32 * d + r + th32 * R;
+    const float m2 = d - (R + r), s2 = d + R + r;
+    const float eps = 1.0f / 65536.0f;
+    if (fabsf(m1) > eps * s1 && fabsf(m2) > eps * s2) return m1 >= 0.f && m2 > 0.f;
+    return theta_swapped(cen[2 * a], cen[2 * a + 1], rad[a], cen[2 * b], cen[2 * b + 1], rad[b], theta);
+}
+
+// Optional list variants (Section 4's structural optimisations).
+struct ListOpt {
+    uint32_t* tiledrop;  // per candidate tile: siblings covered by a parent entry
+    uint32_t* tileswap;  // per candidate tile: finest-level pairs moved to the exchange lists
+    int32_t* xoff;       // role-exchange lists: offsets over all boxes (layout of woff)
+    int32_t* xidx;       // entries (layout and capacity of the strong lists)
+    int32_t* xtgt;       // their targets (global leaf ids)
+};
+
 // One instance's view of the list arrays (pointers already offset to the instance).
 struct LView {
     int32_t *woff, *soff, *widx, *wtgt, *sidx, *stgt;
@@ -194,10 +234,12 @@ __device__ __forceinline__ void decode(const TileParents& tp, const int32_t* __r
 // criterion with the target become one entry: 2 on the first (the entry names the parent), 3 on
 // the other three (no entry).  The four children of a source box are candidates 4q .. 4q+3,
 // which sit in lanes 4q' .. 4q'+3 of one warp (tiles, rows and boxes all start at multiples of
-// 4), so one ballot tells each lane about its quad.
+// 4), so one ballot tells each lane about its quad.  With the role exchange (SWP) a strong
+// candidate of an instance's finest level that passes the exchanged criterion is flagged 4 (the
+// target is the smaller leaf: P2L) or 5 (the larger: M2P) and goes to the exchange lists.
 // schedule: candidate tiles of level l
-template <bool PAR>
-__global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, uint32_t* tiledrop, int l,
+template <bool PAR, bool SWP>
+__global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, ListOpt opt, int l,
                                                     const double* __restrict__ cen,
                                                     const double* __restrict__ rad,
                                                     const float* __restrict__ chi,
@@ -208,12 +250,13 @@ __global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, uint32_
     const Inst S = I[z.i];
     if (l > S.L) return;
     const LView v = LIST_VIEW(z.i);
+    const bool fin = SWP && l == S.L;
     cen += 2 * S.b0;
     rad += S.b0;
     chi += 2 * S.b0;
     clo += 2 * S.b0;
     rad32 += S.b0;
-    __shared__ uint32_t wsum[LT / 32], dsum[LT / 32];
+    __shared__ uint32_t wsum[LT / 32], dsum[LT / 32], xsum[LT / 32];
     __shared__ TileParents tp;
     const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
@@ -222,7 +265,7 @@ __global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, uint32_
     const int lane = threadIdx.x & 31;
     for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
-        uint32_t cnt = 0, drop = 0;
+        uint32_t cnt = 0, drop = 0, swp = 0;
         for (int j = 0; j < LI; j++) {
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             int64_t b = 0, c = 0;
@@ -241,6 +284,11 @@ __global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, uint32_
                 if (__ballot_sync(0xffffffffu, m) >> (lane & ~3) & 1u) f = (lane & 3) ? 3 : 2;
                 drop += f == 3;
             }
+            if (SWP && fin && t < nc && f == 0 &&
+                theta_swapped_fast(base + b, base + c, chi, clo, rad32, cen, rad, (float)theta, theta)) {
+                f = rad[base + b] > rad[base + c] ? 5 : 4;
+                swp++;
+            }
             if (t < nc) v.flags[t] = f;
             cnt += f == 1 || f == 2;
         }
@@ -248,20 +296,24 @@ __global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, uint32_
         for (int o = 16; o; o >>= 1) {
             cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
             if (PAR) drop += __shfl_xor_sync(0xffffffffu, drop, o);
+            if (SWP) swp += __shfl_xor_sync(0xffffffffu, swp, o);
         }
         if (lane == 0) {
             wsum[threadIdx.x >> 5] = cnt;
             dsum[threadIdx.x >> 5] = drop;
+            xsum[threadIdx.x >> 5] = swp;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint32_t s = 0, d = 0;
+            uint32_t s = 0, d = 0, x = 0;
             for (int w = 0; w < LT / 32; w++) {
                 s += wsum[w];
                 d += dsum[w];
+                x += xsum[w];
             }
             v.tilecnt[tile] = s;
-            if (PAR) tiledrop[LIs[z.i].c0 + tile] = d;
+            if (PAR) opt.tiledrop[LIs[z.i].c0 + tile] = d;
+            if (SWP) opt.tileswap[LIs[z.i].c0 + tile] = x;
         }
         __syncthreads();
     }
@@ -301,92 +353,114 @@ __device__ int64_t block_exclusive_scan(uint32_t* a, int64_t n)
     return carry;
 }
 
-// Exclusive scan of the weak counts per tile (and of the dropped siblings with PAR); writes the
-// level totals into the offsets.  One block per instance.
-template <bool PAR>
-__global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, uint32_t* tiledrop, int l)
+// Exclusive scan of the weak counts per tile (and of the dropped siblings with PAR, of the
+// exchanged pairs at the finest level with SWP); writes the level totals into the offsets.
+// One block per instance.
+template <bool PAR, bool SWP>
+__global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, ListOpt opt, int l)
 {
     const Inst S = I[blockIdx.x];
     if (l > S.L) return;
     const LView v = LIST_VIEW(blockIdx.x);
+    const bool fin = SWP && l == S.L;
     const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
+    const int64_t c0 = LIs[blockIdx.x].c0;
     const int64_t nweak = block_exclusive_scan(v.tilecnt, ntiles);
-    const int64_t ndrop = PAR ? block_exclusive_scan(tiledrop + LIs[blockIdx.x].c0, ntiles) : 0;
+    const int64_t ndrop = PAR ? block_exclusive_scan(opt.tiledrop + c0, ntiles) : 0;
+    const int64_t nswap = fin ? block_exclusive_scan(opt.tileswap + c0, ntiles) : 0;
     if (threadIdx.x == 0) {
         const int64_t base = level_base(l), nb = level_size(l);
         const int64_t W0 = v.woff[base], S0 = v.soff[base];
         v.woff[base + nb] = (int32_t)min(W0 + nweak, (int64_t)INT32_MAX);
-        v.soff[base + nb] = (int32_t)min(S0 + (nc - nweak - ndrop), (int64_t)INT32_MAX);
+        v.soff[base + nb] = (int32_t)min(S0 + (nc - nweak - ndrop - nswap), (int64_t)INT32_MAX);
+        if (fin) opt.xoff[S.o0 + base + nb] = (int32_t)min(nswap, (int64_t)INT32_MAX);
     }
 }
 
-// Scatter the candidates into the weak and strong lists and write the box offsets.  The tile
-// prefix of weak flags is tilecnt[tile] (of dropped siblings, tiledrop[tile]); the strong prefix
-// is the rest.
+// Scatter the candidates into the weak, strong (and exchange) lists and write the box offsets.
+// The tile prefix of weak flags is tilecnt[tile] (of dropped siblings tiledrop[tile], of
+// exchanged pairs tileswap[tile]); the strong prefix is the rest.
 // schedule: candidate tiles of level l
-template <bool PAR>
-__global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, const uint32_t* tiledrop, int l)
+template <bool PAR, bool SWP>
+__global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, ListOpt opt, int l)
 {
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
     if (l > S.L) return;
     const LView v = LIST_VIEW(z.i);
-    __shared__ uint32_t wsum[LI][LT / 32], dsum[PAR ? LI : 1][LT / 32];
+    const bool fin = SWP && l == S.L;
+    constexpr int NC = 1 + PAR + SWP;  // prefix counters: weak, dropped, exchanged
+    __shared__ uint32_t csum[NC][LI][LT / 32];
     __shared__ TileParents tp;
     const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
     const int64_t base = level_base(l);
     const int64_t W0 = v.woff[base], S0 = v.soff[base];
+    const int64_t c0 = LIs[z.i].c0;
+    int32_t* xoff = SWP ? opt.xoff + S.o0 : nullptr;
+    int32_t* xidx = SWP ? opt.xidx + LIs[z.i].s0 : nullptr;
+    int32_t* xtgt = SWP ? opt.xtgt + LIs[z.i].s0 : nullptr;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint8_t f[LI];
-        uint32_t pre[LI], dpre[LI];
+        uint32_t pre[NC][LI];
 #pragma unroll
         for (int j = 0; j < LI; j++) {
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             f[j] = t < nc ? v.flags[t] : 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, f[j] == 1 || f[j] == 2);
-            pre[j] = __popc(bal & lt);
-            if (lane == 0) wsum[j][w] = __popc(bal);
-            dpre[j] = 0;
-            if (PAR) {
-                const unsigned bd = __ballot_sync(0xffffffffu, f[j] == 3);
-                dpre[j] = __popc(bd & lt);
-                if (lane == 0) dsum[j][w] = __popc(bd);
+#pragma unroll
+            for (int k = 0; k < NC; k++) {
+                // counter k: 0 weak (1, 2), then dropped (3) if PAR, then exchanged (4, 5) if SWP
+                const int kind = k == 0 ? 0 : (PAR && k == 1) ? 1 : 2;
+                const bool in = kind == 0 ? (f[j] == 1 || f[j] == 2) : kind == 1 ? f[j] == 3 : f[j] >= 4;
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                pre[k][j] = __popc(bal & lt);
+                if (lane == 0) csum[k][j][w] = __popc(bal);
             }
         }
         __syncthreads();
         // exclusive prefix in (row j, warp) order = candidate order inside the tile
-        uint32_t run = v.tilecnt[tile], drun = PAR ? tiledrop[LIs[z.i].c0 + tile] : 0;
+        uint32_t run[NC];
+        run[0] = v.tilecnt[tile];
+        if (PAR) run[1] = opt.tiledrop[c0 + tile];
+        if (SWP) run[NC - 1] = fin ? opt.tileswap[c0 + tile] : 0;
 #pragma unroll
         for (int j = 0; j < LI; j++) {
-            uint32_t before = 0, dbefore = 0;
-            for (int ww = 0; ww < LT / 32; ww++) {
-                if (ww == w) {
-                    before = run;
-                    dbefore = drun;
+            uint32_t before[NC];
+#pragma unroll
+            for (int k = 0; k < NC; k++) {
+                before[k] = 0;
+                for (int ww = 0; ww < LT / 32; ww++) {
+                    if (ww == w) before[k] = run[k];
+                    run[k] += csum[k][j][ww];
                 }
-                run += wsum[j][ww];
-                if (PAR) drun += dsum[j][ww];
             }
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             if (t < nc) {
                 int64_t b, c;
                 bool first;
                 decode(tp, v.sidx, lc, t, b, c, first);
-                const int64_t wpre = (int64_t)before + pre[j];              // weak entries before t
-                const int64_t spre = t - wpre - ((int64_t)dbefore + dpre[j]);  // strong entries before t
+                const int64_t wpre = (int64_t)before[0] + pre[0][j];  // weak entries before t
+                const int64_t dpre = PAR ? (int64_t)before[1] + pre[1][j] : 0;
+                const int64_t xpre = SWP ? (int64_t)before[NC - 1] + pre[NC - 1][j] : 0;
+                const int64_t spre = t - wpre - dpre - xpre;  // strong entries before t
                 if (first) {
                     v.woff[base + b] = (int32_t)min(W0 + wpre, (int64_t)INT32_MAX);
                     v.soff[base + b] = (int32_t)min(S0 + spre, (int64_t)INT32_MAX);
+                    if (fin) xoff[base + b] = (int32_t)min(xpre, (int64_t)INT32_MAX);
                 }
                 if (PAR && f[j] == 3) {
                     // a sibling covered by its parent's entry
+                } else if (SWP && f[j] >= 4) {
+                    if (xpre < v.scap) {
+                        xidx[xpre] = f[j] == 5 ? (int32_t)c | SWAP_M2P : (int32_t)c;
+                        xtgt[xpre] = (int32_t)(base + b);
+                    }
                 } else if (f[j]) {
                     const int64_t pos = W0 + wpre;
                     if (pos < v.wcap) {
@@ -406,13 +480,15 @@ __global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, const ui
     }
 }
 
-__global__ void k_lists_check(LIST_ARGS, int n_inst, int32_t* status)
+__global__ void k_lists_check(LIST_ARGS, int n_inst, const int32_t* xoff, int32_t* status)
 {
     for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
         const Inst& S = I[i];
         const LView v = lview(S, LIs[i], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt);
         const int32_t W = v.woff[S.nbox], Sx = v.soff[S.nbox];
-        if ((int64_t)W > v.wcap || (int64_t)Sx > v.scap || W == INT32_MAX || Sx == INT32_MAX)
+        const int32_t X = xoff ? xoff[S.o0 + S.nbox] : 0;
+        if ((int64_t)W > v.wcap || (int64_t)Sx > v.scap || W == INT32_MAX || Sx == INT32_MAX ||
+            (int64_t)X > v.scap || X == INT32_MAX)
             atomicOr(status, ST_CAPACITY);
     }
 }
@@ -467,28 +543,32 @@ int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s)
 {
     const int L = t->Lmax, ni = t->n_inst;
     StageScope scope(FMM_STAGE_LISTS, s);
-    const bool par = li->mode == FMM_LISTS_PARENTS;
+    const bool par = (li->mode & FMM_LISTS_PARENTS) != 0, swp = (li->mode & FMM_LISTS_EXCHANGE) != 0;
+    const ListOpt opt{li->tiledrop, li->tileswap, li->xoff, li->xidx, li->xtgt};
 #define LARGS t->dinst, li->dlinst, li->woff, li->soff, li->widx, li->wtgt, li->sidx, li->stgt, li->flags, li->tilecnt
     k_lists_root<<<1, 256, 0, s>>>(LARGS, ni); note_launch();
+    // exchange offsets below the finest level stay 0
+    if (swp) FMM_CUDA(cudaMemsetAsync(li->xoff, 0, 4 * (size_t)(t->nbox + ni), s));
     for (int l = 1; l <= L; l++) {
         // a single instance keeps the fixed grid of the grid-stride loops (its candidate count
         // is only known on the device); a forest shares blocks in proportion to 4^l
         const SchedH& sh = t->s_lists[l];
         const unsigned g = ni == 1 ? 152 * 8 : (unsigned)sh.blocks;
-        if (par) {
-            k_lists_flags<true><<<g, LT, 0, s>>>(sh.d, LARGS, li->tiledrop, l, t->centers, t->radii, t->cen_hi,
-                                                 t->cen_lo, t->rad32, theta); note_launch();
-            k_lists_scan<true><<<ni, 1024, 0, s>>>(LARGS, li->tiledrop, l); note_launch();
-            k_lists_fill<true><<<g, LT, 0, s>>>(sh.d, LARGS, li->tiledrop, l); note_launch();
-        } else {
-            k_lists_flags<false><<<g, LT, 0, s>>>(sh.d, LARGS, nullptr, l, t->centers, t->radii, t->cen_hi,
-                                                  t->cen_lo, t->rad32, theta); note_launch();
-            k_lists_scan<false><<<ni, 1024, 0, s>>>(LARGS, nullptr, l); note_launch();
-            k_lists_fill<false><<<g, LT, 0, s>>>(sh.d, LARGS, nullptr, l); note_launch();
-        }
+#define LEVEL(PAR, SWP)                                                                                   \
+    do {                                                                                                  \
+        k_lists_flags<PAR, SWP><<<g, LT, 0, s>>>(sh.d, LARGS, opt, l, t->centers, t->radii, t->cen_hi,   \
+                                                 t->cen_lo, t->rad32, theta); note_launch();             \
+        k_lists_scan<PAR, SWP><<<ni, 1024, 0, s>>>(LARGS, opt, l); note_launch();                        \
+        k_lists_fill<PAR, SWP><<<g, LT, 0, s>>>(sh.d, LARGS, opt, l); note_launch();                     \
+    } while (0)
+        if (par && swp) LEVEL(true, true);
+        else if (par) LEVEL(true, false);
+        else if (swp) LEVEL(false, true);
+        else LEVEL(false, false);
+#undef LEVEL
         FMM_LAUNCH_CHECK("lists");
     }
-    k_lists_check<<<1, 256, 0, s>>>(LARGS, ni, li->status); note_launch();
+    k_lists_check<<<1, 256, 0, s>>>(LARGS, ni, swp ? li->xoff : nullptr, li->status); note_launch();
 #undef LARGS
     FMM_LAUNCH_CHECK("lists: check");
     li->theta = theta;

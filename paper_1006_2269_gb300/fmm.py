@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
             "fmm_lists_create": (i32, [vp, i64, i64, ctypes.POINTER(vp)]),
             "fmm_interaction_lists": (i32, [vp, vp, dbl, vp]),
             "fmm_lists_set_mode": (i32, [vp, i32]),
+            "fmm_lists_export_exchange": (i32, [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]),
             "fmm_lists_sync": (i32, [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
             "fmm_lists_export": (i32, [vp, vp, vp, vp, vp, vp]),
             "fmm_lists_destroy": (None, [vp]),
@@ -254,12 +255,29 @@ def fmm_lists_counts(lists, n_inst: int, stream=None, check: bool = True):
     return w, st, rc == FMM_ERR_CAPACITY
 
 
-FMM_LISTS_PLAIN, FMM_LISTS_PARENTS, FMM_PARENT_FLAG = 0, 1, 0x40000000
+FMM_LISTS_PLAIN, FMM_LISTS_PARENTS, FMM_LISTS_EXCHANGE = 0, 1, 2
+FMM_PARENT_FLAG, FMM_SWAP_M2P = 0x40000000, 0x20000000
 
 
 def fmm_lists_set_mode(lists, mode: int):
-    """FMM_LISTS_PARENTS: four weak siblings become their parent where the criterion allows."""
+    """Bits of Section 4's optional optimisations: FMM_LISTS_PARENTS (four weak siblings become
+    their parent where the criterion allows), FMM_LISTS_EXCHANGE (finest-level role exchange:
+    P2L / M2P for strongly coupled leaves of different radii)."""
     _check(load_library().fmm_lists_set_mode(lists, int(mode)))
+
+
+def fmm_lists_export_exchange(lists, i: int, xoff=None, xidx=None, stream=None) -> int:
+    """Instance i's exchange lists into device int32 buffers (either may be None); returns the
+    number of entries."""
+    n = ctypes.c_int64()
+    _check(load_library().fmm_lists_export_exchange(lists, int(i), _dev(xoff, torch.int32, None, "xoff"),
+                                                    _dev(xidx, torch.int32, None, "xidx"), ctypes.byref(n),
+                                                    _stream(stream)))
+    return n.value
+
+
+def _lists_mode(parents: bool, exchange: bool) -> int:
+    return (FMM_LISTS_PARENTS if parents else 0) | (FMM_LISTS_EXCHANGE if exchange else 0)
 
 
 def fmm_interaction_lists(tree, lists, theta: float, stream=None):
@@ -451,6 +469,15 @@ def fmm_launch_count() -> int:
 
 # ---- convenience ---------------------------------------------------------------------------
 
+def _export_exchange(lists, i, nbox, device):
+    xoff = torch.empty(nbox + 1, dtype=torch.int32, device=device)
+    nx = fmm_lists_export_exchange(lists, i, xoff, None)
+    xidx = torch.empty(max(nx, 1), dtype=torch.int32, device=device)
+    fmm_lists_export_exchange(lists, i, None, xidx)
+    torch.cuda.synchronize(device)
+    return xoff, xidx[:nx]
+
+
 class FMM:
     """One point set: its tree, its interaction lists and any number of evaluations.
 
@@ -459,18 +486,19 @@ class FMM:
     """
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, levels: int, theta: float = 0.5,
-                 weak_capacity: int = 0, strong_capacity: int = 0, check: bool = True, parents: bool = False):
+                 weak_capacity: int = 0, strong_capacity: int = 0, check: bool = True, parents: bool = False,
+                 exchange: bool = False):
         self.n = x.numel()
         self.levels = levels
         self.theta = theta
         self.device = x.device
-        self.parents = parents
+        self.mode = _lists_mode(parents, exchange)
         self.tree = fmm_tree_create(self.n, levels)
         self.lists = None
         try:
             self.lists = fmm_lists_create(self.tree, weak_capacity, strong_capacity)
-            if parents:
-                fmm_lists_set_mode(self.lists, FMM_LISTS_PARENTS)
+            if self.mode:
+                fmm_lists_set_mode(self.lists, self.mode)
             self.rebuild(x, y, check=check)
         except Exception:
             self.close()
@@ -490,11 +518,13 @@ class FMM:
                 if e.code != FMM_ERR_CAPACITY:
                     raise
                 w, s = self._needed()
+                if self.mode & FMM_LISTS_EXCHANGE:
+                    s = max(s, fmm_lists_export_exchange(self.lists, 0))  # the exchange lists share it
                 fmm_lists_destroy(self.lists)
                 self.lists = None
                 self.lists = fmm_lists_create(self.tree, 2 * w + 1024, 2 * s + 1024)
-                if self.parents:
-                    fmm_lists_set_mode(self.lists, FMM_LISTS_PARENTS)
+                if self.mode:
+                    fmm_lists_set_mode(self.lists, self.mode)
                 return self.rebuild(x, y, check=check)
             fmm_sync_status(self.tree, self.lists)
 
@@ -544,6 +574,10 @@ class FMM:
         torch.cuda.synchronize(self.device)
         return woff, widx[:w], soff, sidx[:s]
 
+    def export_exchange(self):
+        """The role-exchange lists (xoff over all boxes, xidx) of a build with exchange=True."""
+        return _export_exchange(self.lists, 0, fmm_tree_info(self.tree)[2], self.device)
+
     def close(self):
         if self.lists is not None:
             fmm_lists_destroy(self.lists)
@@ -569,7 +603,8 @@ class FMMBatch:
     """
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, sizes, levels, theta: float = 0.5,
-                 check: bool = True, weak_per_box: int = 48, strong_per_box: int = 24, parents: bool = False):
+                 check: bool = True, weak_per_box: int = 48, strong_per_box: int = 24, parents: bool = False,
+                 exchange: bool = False):
         self.sizes = [int(v) for v in sizes]
         self.levels = [int(v) for v in levels]
         self.n = sum(self.sizes)
@@ -581,11 +616,11 @@ class FMMBatch:
         self.inst = [fmm_tree_instance(self.tree, i) for i in range(self.n_inst)]
         try:
             nb = [d["nbox"] for d in self.inst]
-            self.parents = parents
+            self.mode = _lists_mode(parents, exchange)
             self.lists = fmm_lists_create_batched(self.tree, [weak_per_box * v for v in nb],
                                                   [strong_per_box * v for v in nb])
-            if parents:
-                fmm_lists_set_mode(self.lists, FMM_LISTS_PARENTS)
+            if self.mode:
+                fmm_lists_set_mode(self.lists, self.mode)
             self.rebuild(x, y, check=check)
         except Exception:
             self.close()
@@ -602,13 +637,15 @@ class FMMBatch:
             w, s, over = fmm_lists_counts(self.lists, self.n_inst, check=False)
             if over:
                 nb = [d["nbox"] for d in self.inst]
+                if self.mode & FMM_LISTS_EXCHANGE:  # the exchange lists share the strong capacity
+                    s = [max(int(a), fmm_lists_export_exchange(self.lists, i)) for i, a in enumerate(s)]
                 fmm_lists_destroy(self.lists)
                 self.lists = None
                 # counts of an instance that overflowed are lower bounds: at least double it
                 self.lists = fmm_lists_create_batched(self.tree, [max(2 * int(a) + 64, 16 * b) for a, b in zip(w, nb)],
                                                       [max(2 * int(a) + 64, 8 * b) for a, b in zip(s, nb)])
-                if self.parents:
-                    fmm_lists_set_mode(self.lists, FMM_LISTS_PARENTS)
+                if self.mode:
+                    fmm_lists_set_mode(self.lists, self.mode)
                 return self.rebuild(x, y, check=check)
             self.counts = (w, s)
             fmm_sync_status(self.tree, self.lists)
@@ -635,6 +672,10 @@ class FMMBatch:
         m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
         phi = torch.empty(self.n, dtype=torch.float64, device=self.device)
         return fmm_autotune(self.tree, self.lists, q, p, m, phi, tol)
+
+    def export_exchange(self, i: int):
+        """Instance i's role-exchange lists (xoff over its boxes, xidx)."""
+        return _export_exchange(self.lists, i, self.inst[i]["nbox"], self.device)
 
     def export_instance(self, i: int):
         """perm, rects, leaf_begin and the lists (woff, widx, soff, sidx) of instance i."""

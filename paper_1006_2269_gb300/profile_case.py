@@ -1,7 +1,8 @@
 """A fixed workload run a few times, as a target for a profiler.
 
     python -m paper_1006_2269_gb300.profile_case [--workload clusters-1m] [--evals 3]
-        [--p 20] [--mode mixed|fp64] [--lists plain|parents] [--m2l auto|simt|tensor] [--steps]
+        [--p 20] [--mode mixed|fp64] [--lists plain|parents|exchange|parents+exchange]
+        [--m2l auto|simt|tensor] [--steps]
 
 Builds the tree and the lists of the workload once, then runs `--evals` evaluations (with
 `--steps`, whole steps: tree, lists and evaluation), synchronises and prints one line.  The
@@ -28,7 +29,7 @@ def main(argv=None):
     ap.add_argument("--evals", type=int, default=3)
     ap.add_argument("--p", type=int, default=20)
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--lists", default="plain", choices=["plain", "parents"])
+    ap.add_argument("--lists", default="plain", choices=["plain", "parents", "exchange", "parents+exchange"])
     ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"])
     ap.add_argument("--steps", action="store_true", help="time whole steps, not evaluations only")
     a = ap.parse_args(argv)
@@ -40,7 +41,7 @@ def main(argv=None):
     else:
         c, L, theta = W.uniform(1 << 20, W.SEED_BASE + 7), 8, 0.5
     x, y, q = (torch.as_tensor(np.ascontiguousarray(v), device=dev) for v in (c.x, c.y, c.q))
-    f = fmm.FMM(x, y, L, theta, parents=a.lists == "parents")
+    f = fmm.FMM(x, y, L, theta, parents="parents" in a.lists, exchange="exchange" in a.lists)
     try:
         fmm.fmm_set_m2l_kernel(f.tree, {"auto": fmm.FMM_M2L_AUTO, "simt": fmm.FMM_M2L_SIMT,
                                         "tensor": fmm.FMM_M2L_TENSOR}[a.m2l])
