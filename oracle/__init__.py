@@ -9,6 +9,7 @@ The arithmetic lives in ``fmm_oracle.c`` (compiled with ``-ffp-contract=off`` so
 multiply-add is fused); this module only compiles it and marshals numpy arrays:
 
 * :func:`tree`       -- median-split mesh (Section 4, Fig. 1.1, Fig. 4.1)
+* :func:`tree_uniform` -- the uniform-grid mesh of the comparison in Section 5
 * :func:`lists`      -- strong/weak connectivity with the theta-criterion (Section 4, Crit. 2.1)
 * :func:`fmm`        -- the whole method, P2M .. P2P, unscaled textbook expansions (Section 5)
 * :func:`direct`     -- the O(N^2) definition, Eq. (1.1)
@@ -61,6 +62,8 @@ def _load():
         lib.orc_nbox.argtypes = [i32]
         lib.orc_tree.restype = i32
         lib.orc_tree.argtypes = [i64, vp, vp, i32, vp, vp, vp]
+        lib.orc_tree_uniform.restype = i32
+        lib.orc_tree_uniform.argtypes = [i64, vp, vp, i32, vp, vp, vp]
         lib.orc_geometry.restype = None
         lib.orc_geometry.argtypes = [i64, vp, vp, vp]
         lib.orc_theta_weak.restype = i32
@@ -149,6 +152,20 @@ def tree(x, y, L: int):
     return perm, rects, lb
 
 
+def tree_uniform(x, y, L: int):
+    """The uniform-grid mesh (square root, geometric quadrants) the adaptive one is compared with.
+    Returns (perm, rects, leaf_begin) like :func:`tree`; leaves may be empty."""
+    x, y = _f64(x), _f64(y)
+    n = x.shape[0]
+    perm = np.empty(n, np.int32)
+    rects = np.empty((nbox(L), 4), np.float64)
+    lb = np.empty(4 ** L + 1, np.int64)
+    rc = _load().orc_tree_uniform(n, _ptr(x), _ptr(y), L, _ptr(perm), _ptr(rects), _ptr(lb))
+    if rc:
+        raise OracleError(f"orc_tree_uniform failed ({rc})")
+    return perm, rects, lb
+
+
 def geometry(rects):
     """Centres (midpoints) and radii (half diagonals) of the boxes."""
     rects = _f64(rects)
@@ -202,17 +219,22 @@ def lists(rects, L: int, theta: float, parents: bool = False, swap: bool = False
     return tuple(out)
 
 
+def _flags(parents, swap, uniform):
+    return (1 if parents else 0) | (2 if swap else 0) | (4 if uniform else 0)
+
+
 def fmm(x, y, q, L: int, p: int, theta: float, want_coeffs: bool = False, parents: bool = False,
-        swap: bool = False):
+        swap: bool = False, uniform: bool = False):
     """The whole method in FP64 (Section 4).  Returns phi in input order, plus the unscaled
     multipole and local coefficients (complex, [nbox, p+1]) when ``want_coeffs``.  ``parents``
-    and ``swap`` apply the optional optimisations (see :func:`lists`)."""
+    and ``swap`` apply the optional optimisations (see :func:`lists`); ``uniform`` runs the same
+    method on the uniform-grid mesh (:func:`tree_uniform`)."""
     x, y, q = _f64(x), _f64(y), _f64(q)
     n = x.shape[0]
     phi = np.empty(n, np.float64)
-    if parents or swap:
+    if parents or swap or uniform:
         assert not want_coeffs
-        flags = (1 if parents else 0) | (2 if swap else 0)
+        flags = _flags(parents, swap, uniform)
         rc = _load().orc_fmm_ex(n, _ptr(x), _ptr(y), _ptr(q), L, p, float(theta), flags, _ptr(phi))
         if rc:
             raise OracleError(f"orc_fmm_ex failed ({rc})")
@@ -239,13 +261,14 @@ def direct(x, y, q, targets=None, nthreads: int = 0):
     return phi
 
 
-def fmm_field(x, y, q, L: int, p: int, theta: float, parents: bool = False, swap: bool = False):
+def fmm_field(x, y, q, L: int, p: int, theta: float, parents: bool = False, swap: bool = False,
+              uniform: bool = False):
     """The complex field F_i = sum_{j != i} -q_j / (z_i - z_j) by the method (Section 5's first
-    experiment); returns a complex array in input order.  ``parents`` / ``swap`` as :func:`fmm`."""
+    experiment); returns a complex array in input order.  Options as :func:`fmm`."""
     x, y, q = _f64(x), _f64(y), _f64(q)
     n = x.shape[0]
     fre, fim = np.empty(n), np.empty(n)
-    flags = (1 if parents else 0) | (2 if swap else 0)
+    flags = _flags(parents, swap, uniform)
     rc = _load().orc_fmm_field_ex(n, _ptr(x), _ptr(y), _ptr(q), int(L), int(p), float(theta), flags,
                                   _ptr(fre), _ptr(fim))
     if rc:

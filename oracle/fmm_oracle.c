@@ -44,6 +44,9 @@
  *   R20 role exchange (optional, flags & 2): finest level only; a strong leaf pair passes when
  *       r + theta*R <= theta*d and R + r < d; the smaller target takes P2L, the larger M2P; the
  *       pair leaves the strong list.
+ *   R21 the uniform mesh of the comparison (flags & 4): square root on the bounding box's
+ *       lower-left corner with the longer side, geometric quadrants, the same lists and
+ *       expansions (see orc_tree_uniform).
  */
 #include <complex.h>
 #include <math.h>
@@ -171,6 +174,77 @@ int orc_tree(int64_t n, const double* x, const double* y, int L,
     leaf_begin[nleaf] = n;
     memcpy(perm, work, sizeof(int32_t) * (size_t)n);
     free(work); free(tmp); free(beg); free(nbeg);
+    return 0;
+}
+
+/*
+ * The uniform-grid mesh (the classical non-adaptive FMM mesh that Section 5 compares the adaptive
+ * one with, reading R21): the root is the square [x0, x0 + s] x [y0, y0 + s] with (x0, y0) the
+ * lower-left corner of the points' bounding box and s its longer side; every box splits into
+ * four equal quadrants, children numbered as in orc_tree (x-low/y-low, x-low/y-high, x-high/
+ * y-low, x-high/y-high).  Cell (ix, iy) of level l has x-range
+ * [x0 + s*(ix/2^l), x0 + s*((ix+1)/2^l)], and likewise in y.  A point's leaf has
+ * ix = floor(((x - x0) / s) * 2^L), clamped to [0, 2^L - 1] (iy likewise; all 0 when s = 0).
+ * Leaves may be empty or hold any number of points.  The canonical order is by leaf, then by
+ * input index, and leaf_begin counts the points.
+ * Returns 0, or -1 for bad arguments.
+ */
+int orc_tree_uniform(int64_t n, const double* x, const double* y, int L,
+                     int32_t* perm, double* rects, int64_t* leaf_begin)
+{
+    if (n <= 0 || L < 0 || L > 15 || !x || !y || !perm || !rects || !leaf_begin) return -1;
+    double x0 = x[0], x1 = x[0], y0 = y[0], y1 = y[0];
+    for (int64_t i = 1; i < n; i++) {
+        if (x[i] < x0) x0 = x[i];
+        if (x[i] > x1) x1 = x[i];
+        if (y[i] < y0) y0 = y[i];
+        if (y[i] > y1) y1 = y[i];
+    }
+    const double sx = x1 - x0, sy = y1 - y0;
+    const double side = sx > sy ? sx : sy;
+    const int64_t nleaf = ((int64_t)1) << (2 * L), m = ((int64_t)1) << L;
+    /* every box of every level */
+    for (int l = 0; l <= L; l++) {
+        const int64_t nb = ((int64_t)1) << (2 * l);
+        const double w = (double)(((int64_t)1) << l);
+        for (int64_t b = 0; b < nb; b++) {
+            int64_t ix = 0, iy = 0;
+            for (int j = 0; j < l; j++) { /* digit j (from the top) of b: x bit, y bit */
+                const int64_t d = (b >> (2 * (l - 1 - j))) & 3;
+                ix = 2 * ix + (d >> 1);
+                iy = 2 * iy + (d & 1);
+            }
+            double* r = rects + 4 * (level_base(l) + b);
+            r[0] = x0 + side * ((double)ix / w);
+            r[1] = x0 + side * ((double)(ix + 1) / w);
+            r[2] = y0 + side * ((double)iy / w);
+            r[3] = y0 + side * ((double)(iy + 1) / w);
+        }
+    }
+    /* leaf of every point, then a stable counting sort by leaf */
+    int64_t* leaf = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t b = 0; b <= nleaf; b++) leaf_begin[b] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t ix = 0, iy = 0;
+        if (side > 0.0) {
+            ix = (int64_t)floor(((x[i] - x0) / side) * (double)m);
+            iy = (int64_t)floor(((y[i] - y0) / side) * (double)m);
+            if (ix > m - 1) ix = m - 1;
+            if (iy > m - 1) iy = m - 1;
+            if (ix < 0) ix = 0;
+            if (iy < 0) iy = 0;
+        }
+        int64_t id = 0;
+        for (int j = L - 1; j >= 0; j--) id = 4 * id + 2 * ((ix >> j) & 1) + ((iy >> j) & 1);
+        leaf[i] = id;
+        leaf_begin[id + 1]++;
+    }
+    for (int64_t b = 0; b < nleaf; b++) leaf_begin[b + 1] += leaf_begin[b];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)nleaf);
+    memcpy(fill, leaf_begin, sizeof(int64_t) * (size_t)nleaf);
+    for (int64_t i = 0; i < n; i++) perm[fill[leaf[i]]++] = (int32_t)i;
+    free(fill);
+    free(leaf);
     return 0;
 }
 
@@ -708,7 +782,7 @@ static int fmm_core(int64_t n, const double* x, const double* y, const double* q
     int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     double* rects = (double*)malloc(sizeof(double) * 4 * (size_t)nbox);
     int64_t* lb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nleaf + 1));
-    int rc = orc_tree(n, x, y, L, perm, rects, lb);
+    int rc = (flags & 4) ? orc_tree_uniform(n, x, y, L, perm, rects, lb) : orc_tree(n, x, y, L, perm, rects, lb);
     if (rc) { free(perm); free(rects); free(lb); return rc; }
     double* cen = (double*)malloc(sizeof(double) * 2 * (size_t)nbox);
     double* rad = (double*)malloc(sizeof(double) * (size_t)nbox);
@@ -833,7 +907,8 @@ int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L,
 
 /* The method with the optional structural optimisations of Section 4: flags & 1 parent-level
  * interactions (orc_lists_merge_parents), flags & 2 the finest-level role exchange
- * (orc_lists_swap_leaves). */
+ * (orc_lists_swap_leaves); flags & 4 runs it on the uniform-grid mesh (orc_tree_uniform)
+ * instead of the adaptive one. */
 int orc_fmm_ex(int64_t n, const double* x, const double* y, const double* q, int L, int p,
                double theta, int flags, double* phi)
 {
