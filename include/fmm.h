@@ -112,6 +112,16 @@ int fmm_tree_instance(fmm_tree t, int i, int64_t* p0, int64_t* n, int* levels, i
  * coordinates set FMM_ERR_NONFINITE in the device status. */
 int fmm_build_tree(fmm_tree t, const double* x, const double* y, void* stream);
 
+/* The uniform-grid mesh in place of the median tree (no paper formula: the non-adaptive mesh
+ * that Section 5 compares the adaptive code with).  The root is the square on the points'
+ * bounding-box lower-left corner whose side is the box's longer side; every box splits into four
+ * equal quadrants, children numbered as by fmm_build_tree; a point's leaf cell is
+ * floor(((x - x0) / side) * 2^L), clamped, likewise in y; points are ordered by leaf, then by
+ * input index.  Leaves may be empty or hold any number of points.  Lists, evaluation and export
+ * then work on this mesh unchanged.  Reads the largest leaf of every instance back to the host,
+ * so the call synchronises `stream`; a later fmm_build_tree restores the median tree. */
+int fmm_build_tree_uniform(fmm_tree t, const double* x, const double* y, void* stream);
+
 /* Copy the tree out (device pointers, any may be NULL):
  *   perm[n]            canonical point order: leaves in id order, inside a leaf ascending input
  *                      index; perm[k] is the input index of the k-th point.

@@ -92,7 +92,7 @@ struct DeviceGuard {
 void free_tree(fmm_tree t)
 {
     if (!t) return;
-    void* ptrs[] = {t->rects, t->centers, t->radii, t->rad32, t->cen_hi, t->cen_lo, t->perm, t->leaf_begin,
+    void* ptrs[] = {t->lb_bal, t->rects, t->centers, t->radii, t->rad32, t->cen_hi, t->cen_lo, t->perm, t->leaf_begin,
                     t->leaf_of, t->xs, t->ys, t->dxf, t->dyf, t->keys, t->vals, t->rs_counts,
                     t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->node_off, t->segs, t->status,
                     t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf, t->dinst, t->Lf0lo,
@@ -213,6 +213,13 @@ int fmm_build_tree(fmm_tree t, const double* x, const double* y, void* stream)
     if (!t || !x || !y) return fail(FMM_ERR_ARG, "NULL argument");
     GUARD(t->dev);
     return tree_build(t, x, y, (cudaStream_t)stream);
+}
+
+int fmm_build_tree_uniform(fmm_tree t, const double* x, const double* y, void* stream)
+{
+    if (!t || !x || !y) return fail(FMM_ERR_ARG, "NULL argument");
+    GUARD(t->dev);
+    return tree_build_uniform(t, x, y, (cudaStream_t)stream);
 }
 
 int fmm_tree_export(fmm_tree t, int32_t* perm, double* rects, int32_t* leaf_begin, void* stream)

@@ -125,7 +125,8 @@ struct Inst {
     int64_t ob0;          // ones-before tables: 2^(2L) - 1 entries
     int64_t no0;          // node-offset tables: 2^(2L+1) + 2L entries
     int64_t lb0;          // leaf offsets: 4^L + 1 entries
-    int32_t L, pad;
+    int32_t L;
+    int32_t maxleaf;      // points of the largest leaf (ceil(n / 4^L) on the median tree)
 };
 
 // Launch schedule over the instances of a forest.  A launch is a 1-D grid; block b works for
@@ -251,6 +252,11 @@ struct fmm_tree_s {
     fmm::SchedH* s_l2l = nullptr;    // [Lmax] children of level l, 4 per block (l < L)
     fmm::SchedH* s_lists = nullptr;  // [Lmax + 1] candidate tiles of level l (l <= L)
     bool built = false;
+    // uniform-grid mesh (the non-adaptive comparison of Section 5) in place of the median tree:
+    // leaf offsets and largest leaves then come from the data; the balanced leaf offsets are kept
+    // in lb_bal to restore them for the next median build
+    bool uniform = false;
+    int32_t* lb_bal = nullptr;
 };
 
 struct fmm_lists_s {
@@ -296,6 +302,7 @@ void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls);
 void forest_totals(fmm_tree t);
 int tree_tables_host(int64_t n, int L, int32_t* ones_before, int32_t* node_off, int32_t* leaf_begin);
 int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s);
+int tree_build_uniform(fmm_tree t, const double* x, const double* y, cudaStream_t s);
 
 // lists.cu
 int lists_build(fmm_tree t, fmm_lists l, double theta, cudaStream_t s);

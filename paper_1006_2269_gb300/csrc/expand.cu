@@ -949,7 +949,7 @@ __global__ void __launch_bounds__(256) k_p2p_small(Sched sc, const Inst* __restr
     const Inst S = I[z.i];
     const LInst TL = LIs[z.i];
     const int L = S.L;
-    if ((S.n + level_size(L) - 1) / level_size(L) > gs) return;  // left to k_p2p_large
+    if ((int64_t)S.maxleaf > gs) return;  // left to k_p2p_large
     const int64_t scap = TL.scap;
     soff += S.o0;
     sidx += TL.s0;
@@ -1010,7 +1010,7 @@ __global__ void __launch_bounds__(256) k_p2p_small(Sched sc, const Inst* __restr
                 const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
                 const float xt = tx - ox, yt = ty - oy;
                 const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
-                const float tau2 = (M * (1.f / 256.f)) * (M * (1.f / 256.f));
+                const float tau2 = fmaxf((M * (1.f / 256.f)) * (M * (1.f / 256.f)), 1e-30f);  // > 0: r = 0 is exact
                 float part = 0.f;
 #pragma unroll 4
                 for (int j = 0; j < ns; j++) {
@@ -1115,7 +1115,7 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
     nhi += S.p0;
     nlo += S.p0;
     // groups of gsl lanes, two targets per lane: gsl = pow2ceil(largest leaf of this instance) / 2
-    const int64_t maxleaf = (S.n + level_size(L) - 1) / level_size(L);
+    const int64_t maxleaf = (int64_t)S.maxleaf;
     if (maxleaf > 64) return;  // left to k_p2p_large
     int gsl = 1;
     while (2 * gsl < maxleaf) gsl <<= 1;
@@ -1235,7 +1235,7 @@ __global__ void __launch_bounds__(256) k_p2p_large(Sched sc, const Inst* __restr
     const Inst S = I[z.i];
     const LInst TL = LIs[z.i];
     const int L = S.L;
-    if ((S.n + level_size(L) - 1) / level_size(L) <= small_leaf) return;  // done by the leaf-pair kernel
+    if ((int64_t)S.maxleaf <= small_leaf) return;  // done by the leaf-pair kernel
     const int64_t scap = TL.scap;
     soff += S.o0;
     sidx += TL.s0;
@@ -1265,7 +1265,7 @@ __global__ void __launch_bounds__(256) k_p2p_large(Sched sc, const Inst* __restr
             ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
             oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
             const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
-            tau2 = (M * (1.f / 256.f)) * (M * (1.f / 256.f));
+            tau2 = fmaxf((M * (1.f / 256.f)) * (M * (1.f / 256.f)), 1e-30f);  // > 0: r = 0 is exact
         }
         for (int tc = 0; tc < nt; tc += 32) {
             const int32_t it = t0 + tc + lane;
@@ -1483,7 +1483,7 @@ __global__ void __launch_bounds__(256) k_p2p_field_f32(Sched sc, const Inst* __r
     flr += S.p0;
     fhi += S.p0;
     fli += S.p0;
-    const int64_t maxleaf = (S.n + level_size(L) - 1) / level_size(L);
+    const int64_t maxleaf = (int64_t)S.maxleaf;
     if (maxleaf > 64) return;  // left to the general kernel
     int gsl = 1;
     while (2 * gsl < maxleaf) gsl <<= 1;
@@ -1845,7 +1845,7 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     int64_t maxleaf = 0, minleaf = INT64_MAX;
     for (int i = 0; i < t->n_inst; i++) {
         const Inst& S = t->hinst[i];
-        const int64_t ml = (S.n + level_size(S.L) - 1) / level_size(S.L);
+        const int64_t ml = (int64_t)S.maxleaf;
         maxleaf = std::max(maxleaf, ml);
         minleaf = std::min(minleaf, ml);
     }
@@ -2101,7 +2101,7 @@ int evaluate_field(fmm_tree t, fmm_lists li, const double* q, const fmm_params& 
     int64_t maxleaf = 0;
     for (int i = 0; i < t->n_inst; i++) {
         const Inst& S = t->hinst[i];
-        maxleaf = std::max<int64_t>(maxleaf, (S.n + level_size(S.L) - 1) / level_size(S.L));
+        maxleaf = std::max<int64_t>(maxleaf, (int64_t)S.maxleaf);
     }
     // the binary32 near-field kernel holds up to 64 targets per leaf; larger leaves, tolerances
     // below the binary32 floor and binary64 mode take the binary64 path

@@ -599,6 +599,114 @@ __global__ void k_gather_points(Sched sc, const Inst* __restrict__ I, const int3
     }
 }
 
+// ---- uniform-grid mesh (the non-adaptive comparison of Section 5) -----------------------------
+// Root: the square [x0, x0 + side] x [y0, y0 + side] on the bounding box's lower-left corner with
+// its longer side; every box splits into four equal quadrants (children numbered as in the median
+// tree).  Cell (ix, iy) of level l spans x0 + side * (ix / 2^l) .. x0 + side * ((ix + 1) / 2^l);
+// a point's leaf has ix = floor(((x - x0) / side) * 2^L) clamped to [0, 2^L - 1] (iy likewise, all
+// 0 when side = 0).  Binary64 with explicit rounding, so the mesh is the same bit for bit on any
+// machine that rounds to nearest.
+
+__device__ __forceinline__ double bbox_side(const uint64_t* bb, double& x0, double& y0)
+{
+    x0 = key_value(bb[0]);
+    y0 = key_value(bb[2]);
+    const double sx = __dsub_rn(key_value(bb[1]), x0), sy = __dsub_rn(key_value(bb[3]), y0);
+    return sx > sy ? sx : sy;
+}
+
+// leaf of every point (input order); schedule: points
+__global__ void k_uniform_cells(Sched sc, const Inst* __restrict__ I, const double* __restrict__ x,
+                                const double* __restrict__ y, const uint64_t* __restrict__ bbox,
+                                uint32_t* __restrict__ leaf_of)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    x += S.p0;
+    y += S.p0;
+    leaf_of += S.p0;
+    double x0, y0;
+    const double side = bbox_side(bbox + 4 * z.i, x0, y0);
+    const int L = S.L;
+    const int64_t m = int64_t(1) << L;
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
+        int64_t ix = 0, iy = 0;
+        if (side > 0.0) {
+            ix = (int64_t)floor(__dmul_rn(__ddiv_rn(__dsub_rn(x[i], x0), side), (double)m));
+            iy = (int64_t)floor(__dmul_rn(__ddiv_rn(__dsub_rn(y[i], y0), side), (double)m));
+            ix = min(max(ix, (int64_t)0), m - 1);
+            iy = min(max(iy, (int64_t)0), m - 1);
+        }
+        uint32_t id = 0;
+        for (int j = L - 1; j >= 0; j--) id = 4 * id + 2 * ((ix >> j) & 1) + ((iy >> j) & 1);
+        leaf_of[i] = id;
+    }
+}
+
+// leaf offsets from the leaf ids in canonical (sorted) order: lb[c] = first position whose id is
+// >= c; schedule: points (position j = n closes the table)
+__global__ void k_uniform_lb(Sched sc, const Inst* __restrict__ I, const uint32_t* __restrict__ sorted,
+                             int32_t* __restrict__ lb)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    sorted += S.p0;
+    lb += S.lb0;
+    const int64_t nleaf = level_size(S.L);
+    for (int64_t j = (int64_t)z.rank * blockDim.x + threadIdx.x; j <= S.n; j += (int64_t)z.nb * blockDim.x) {
+        const int64_t prev = j > 0 ? (int64_t)sorted[j - 1] : -1;
+        const int64_t cur = j < S.n ? (int64_t)sorted[j] : nleaf;
+        for (int64_t c = prev + 1; c <= cur; c++) lb[c] = (int32_t)j;
+    }
+}
+
+// largest leaf of each instance into the instance table; schedule: points
+__global__ void k_uniform_maxleaf(Sched sc, Inst* __restrict__ I, const int32_t* __restrict__ lb)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    lb += S.lb0;
+    int32_t mx = 0;
+    for (int64_t c = (int64_t)z.rank * blockDim.x + threadIdx.x; c < level_size(S.L); c += (int64_t)z.nb * blockDim.x)
+        mx = max(mx, lb[c + 1] - lb[c]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(&I[z.i].maxleaf, mx);
+}
+
+__global__ void k_reset_maxleaf(Inst* I, int n_inst)
+{
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) I[i].maxleaf = 0;
+}
+
+// rectangles of every box; schedule: points (boxes of the instance, grid-stride)
+__global__ void k_uniform_rects(Sched sc, const Inst* __restrict__ I, const uint64_t* __restrict__ bbox,
+                                double* __restrict__ rects)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    rects += 4 * S.b0;
+    double x0, y0;
+    const double side = bbox_side(bbox + 4 * z.i, x0, y0);
+    for (int64_t g = (int64_t)z.rank * blockDim.x + threadIdx.x; g < S.nbox; g += (int64_t)z.nb * blockDim.x) {
+        int l = 0;
+        while (level_base(l + 1) <= g) l++;
+        const int64_t b = g - level_base(l);
+        int64_t ix = 0, iy = 0;
+        for (int j = 0; j < l; j++) {
+            const int64_t d = (b >> (2 * (l - 1 - j))) & 3;
+            ix = 2 * ix + (d >> 1);
+            iy = 2 * iy + (d & 1);
+        }
+        const double w = (double)(int64_t(1) << l);
+        double* r = rects + 4 * g;
+        r[0] = __dadd_rn(x0, __dmul_rn(side, __ddiv_rn((double)ix, w)));
+        r[1] = __dadd_rn(x0, __dmul_rn(side, __ddiv_rn((double)(ix + 1), w)));
+        r[2] = __dadd_rn(y0, __dmul_rn(side, __ddiv_rn((double)iy, w)));
+        r[3] = __dadd_rn(y0, __dmul_rn(side, __ddiv_rn((double)(iy + 1), w)));
+    }
+}
+
 }  // namespace
 
 // Host tables of one instance (sizes depend on (n, L) only): ones-before tables for depths
@@ -655,6 +763,7 @@ void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls)
         S.ob0 = ob0;
         S.no0 = no0;
         S.lb0 = lb0;
+        S.maxleaf = (int32_t)((S.n + level_size(S.L) - 1) / level_size(S.L));
         p0 += S.n;
         b0 += S.nbox;
         t0 += S.ntiles;
@@ -753,6 +862,15 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
     int32_t *X, *Xo, *Y, *Yo;
     int32_t* Xfinal_seg = nullptr;
 
+    if (t->uniform) {  // the previous build was the uniform grid: balanced leaves again
+        for (int i = 0; i < ni; i++) {
+            Inst& S = t->hinst[i];
+            S.maxleaf = (int32_t)((S.n + level_size(S.L) - 1) / level_size(S.L));
+        }
+        FMM_CUDA(cudaMemcpy(t->dinst, t->hinst, sizeof(Inst) * ni, cudaMemcpyHostToDevice));
+        FMM_CUDA(cudaMemcpyAsync(t->leaf_begin, t->lb_bal, 4 * (size_t)(t->nleaf + ni), cudaMemcpyDeviceToDevice, s));
+        t->uniform = false;
+    }
     {
         StageScope scope(FMM_STAGE_TREE_SORT, s);
         k_bbox_init<<<1, 256, 0, s>>>(ni, t->bbox_keys); note_launch();
@@ -817,6 +935,58 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
                                            t->xs, t->ys, t->dxf, t->dyf, t->cleaf); note_launch();
         FMM_LAUNCH_CHECK("tree: canonical order");
     }
+    t->built = true;
+    return 0;
+}
+
+// The uniform-grid mesh in place of the median tree (same handle, same downstream stages): cells
+// of every point, a stable sort by cell (ties keep input order), leaf offsets and the largest
+// leaf of every instance (read back, so this call synchronises the stream), the rectangles of
+// every box, the box geometry and the canonical coordinates.
+int tree_build_uniform(fmm_tree t, const double* x, const double* y, cudaStream_t s)
+{
+    const int64_t n = t->n;
+    const int ni = t->n_inst;
+    const int L = t->Lmax;
+    const unsigned gp = (unsigned)t->s_pts.blocks;
+    const Sched sp = t->s_pts.d;
+    if (!t->lb_bal) {  // keep the balanced leaf offsets for a later median build
+        if (cudaMalloc((void**)&t->lb_bal, 4 * (size_t)(t->nleaf + ni)) != cudaSuccess)
+            return fail(FMM_ERR_OOM, "leaf offsets");
+        FMM_CUDA(cudaMemcpyAsync(t->lb_bal, t->leaf_begin, 4 * (size_t)(t->nleaf + ni), cudaMemcpyDeviceToDevice, s));
+    }
+    uint32_t* leaf_of = (uint32_t*)t->leaf_of;
+    {
+        StageScope scope(FMM_STAGE_TREE_SORT, s);
+        k_bbox_init<<<1, 256, 0, s>>>(ni, t->bbox_keys); note_launch();
+        k_make_keys<<<gp, 256, 0, s>>>(sp, t->dinst, x, y, n, t->keys, t->bbox_keys, t->status); note_launch();
+        k_uniform_cells<<<gp, 256, 0, s>>>(sp, t->dinst, x, y, t->bbox_keys, leaf_of); note_launch();
+        FMM_LAUNCH_CHECK("uniform tree: cells");
+        uint32_t* k32 = (uint32_t*)t->keys;
+        int32_t* v32 = t->vals + 2 * n;
+        const int bits = std::max(8, 2 * L);
+        FMM_CUDA(cudaMemcpyAsync(k32, leaf_of, 4 * n, cudaMemcpyDeviceToDevice, s));
+        const int c2 = radix_sort<uint32_t>(t, k32, v32, 0, 1, bits, s);
+        FMM_CUDA(cudaMemcpyAsync(t->perm, v32 + (c2 ? n : 0), 4 * n, cudaMemcpyDeviceToDevice, s));
+        k_uniform_lb<<<gp, 256, 0, s>>>(sp, t->dinst, k32 + (c2 ? n : 0), t->leaf_begin); note_launch();
+        k_reset_maxleaf<<<1, 256, 0, s>>>(t->dinst, ni); note_launch();
+        k_uniform_maxleaf<<<gp, 256, 0, s>>>(sp, t->dinst, t->leaf_begin); note_launch();
+        FMM_LAUNCH_CHECK("uniform tree: order");
+    }
+    {
+        StageScope scope(FMM_STAGE_TREE_FINISH, s);
+        k_uniform_rects<<<gp, 256, 0, s>>>(sp, t->dinst, t->bbox_keys, t->rects); note_launch();
+        const int64_t nb = t->nbox;
+        k_geometry<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(t->rects, nb, t->centers, t->radii,
+                                                                t->rad32, t->cen_hi, t->cen_lo); note_launch();
+        k_gather_points<<<gp, 256, 0, s>>>(sp, t->dinst, t->perm, leaf_of, x, y, t->centers,
+                                           t->xs, t->ys, t->dxf, t->dyf, t->cleaf); note_launch();
+        FMM_LAUNCH_CHECK("uniform tree: geometry");
+    }
+    // the largest leaves decide the near-field kernels on the host
+    FMM_CUDA(cudaStreamSynchronize(s));
+    FMM_CUDA(cudaMemcpy(t->hinst, t->dinst, sizeof(Inst) * ni, cudaMemcpyDeviceToHost));
+    t->uniform = true;
     t->built = true;
     return 0;
 }
