@@ -118,9 +118,12 @@ int fmm_build_tree(fmm_tree t, const double* x, const double* y, void* stream);
  * equal quadrants, children numbered as by fmm_build_tree; a point's leaf cell is
  * floor(((x - x0) / side) * 2^L), clamped, likewise in y; points are ordered by leaf, then by
  * input index.  Leaves may be empty or hold any number of points.  Lists, evaluation and export
- * then work on this mesh unchanged.  Reads the largest leaf of every instance back to the host,
- * so the call synchronises `stream`; a later fmm_build_tree restores the median tree. */
-int fmm_build_tree_uniform(fmm_tree t, const double* x, const double* y, void* stream);
+ * then work on this mesh unchanged.  root_host (may be NULL): a given root square
+ * {x0, y0, side} (host array of 3, side >= 0) used for every instance instead of the bounding
+ * square, e.g. the unit square of Section 5's experiment; points outside it are clamped into its
+ * edge cells.  Reads the largest leaf of every instance back to the host, so the call
+ * synchronises `stream`; a later fmm_build_tree restores the median tree. */
+int fmm_build_tree_uniform(fmm_tree t, const double* x, const double* y, const double* root_host, void* stream);
 
 /* Copy the tree out (device pointers, any may be NULL):
  *   perm[n]            canonical point order: leaves in id order, inside a leaf ascending input

@@ -63,7 +63,9 @@ def _load():
         lib.orc_tree.restype = i32
         lib.orc_tree.argtypes = [i64, vp, vp, i32, vp, vp, vp]
         lib.orc_tree_uniform.restype = i32
-        lib.orc_tree_uniform.argtypes = [i64, vp, vp, i32, vp, vp, vp]
+        lib.orc_tree_uniform.argtypes = [i64, vp, vp, i32, vp, vp, vp, vp]
+        lib.orc_fmm_root.restype = i32
+        lib.orc_fmm_root.argtypes = [i64, vp, vp, vp, i32, i32, dbl, i32, vp, vp]
         lib.orc_geometry.restype = None
         lib.orc_geometry.argtypes = [i64, vp, vp, vp]
         lib.orc_theta_weak.restype = i32
@@ -152,15 +154,22 @@ def tree(x, y, L: int):
     return perm, rects, lb
 
 
-def tree_uniform(x, y, L: int):
+def _root(root):
+    return None if root is None else np.ascontiguousarray(root, np.float64)
+
+
+def tree_uniform(x, y, L: int, root=None):
     """The uniform-grid mesh (square root, geometric quadrants) the adaptive one is compared with.
-    Returns (perm, rects, leaf_begin) like :func:`tree`; leaves may be empty."""
+    ``root`` = (x0, y0, side) fixes the root square (default: the bounding square).  Returns
+    (perm, rects, leaf_begin) like :func:`tree`; leaves may be empty."""
     x, y = _f64(x), _f64(y)
     n = x.shape[0]
     perm = np.empty(n, np.int32)
     rects = np.empty((nbox(L), 4), np.float64)
     lb = np.empty(4 ** L + 1, np.int64)
-    rc = _load().orc_tree_uniform(n, _ptr(x), _ptr(y), L, _ptr(perm), _ptr(rects), _ptr(lb))
+    r = _root(root)
+    rc = _load().orc_tree_uniform(n, _ptr(x), _ptr(y), L, None if r is None else _ptr(r), _ptr(perm), _ptr(rects),
+                                  _ptr(lb))
     if rc:
         raise OracleError(f"orc_tree_uniform failed ({rc})")
     return perm, rects, lb
@@ -224,14 +233,22 @@ def _flags(parents, swap, uniform):
 
 
 def fmm(x, y, q, L: int, p: int, theta: float, want_coeffs: bool = False, parents: bool = False,
-        swap: bool = False, uniform: bool = False):
+        swap: bool = False, uniform: bool = False, root=None):
     """The whole method in FP64 (Section 4).  Returns phi in input order, plus the unscaled
     multipole and local coefficients (complex, [nbox, p+1]) when ``want_coeffs``.  ``parents``
     and ``swap`` apply the optional optimisations (see :func:`lists`); ``uniform`` runs the same
-    method on the uniform-grid mesh (:func:`tree_uniform`)."""
+    method on the uniform-grid mesh (:func:`tree_uniform`), ``root`` = (x0, y0, side) on a given
+    root square."""
     x, y, q = _f64(x), _f64(y), _f64(q)
     n = x.shape[0]
     phi = np.empty(n, np.float64)
+    if root is not None:
+        r = _root(root)
+        rc = _load().orc_fmm_root(n, _ptr(x), _ptr(y), _ptr(q), L, p, float(theta), _flags(parents, swap, True),
+                                  _ptr(r), _ptr(phi))
+        if rc:
+            raise OracleError(f"orc_fmm_root failed ({rc})")
+        return phi
     if parents or swap or uniform:
         assert not want_coeffs
         flags = _flags(parents, swap, uniform)

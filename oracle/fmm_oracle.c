@@ -186,10 +186,11 @@ int orc_tree(int64_t n, const double* x, const double* y, int L,
  * [x0 + s*(ix/2^l), x0 + s*((ix+1)/2^l)], and likewise in y.  A point's leaf has
  * ix = floor(((x - x0) / s) * 2^L), clamped to [0, 2^L - 1] (iy likewise; all 0 when s = 0).
  * Leaves may be empty or hold any number of points.  The canonical order is by leaf, then by
- * input index, and leaf_begin counts the points.
+ * input index, and leaf_begin counts the points.  root (may be NULL): a given root square
+ * (x0, y0, side) instead of the bounding one, e.g. the unit square of Section 5's experiment.
  * Returns 0, or -1 for bad arguments.
  */
-int orc_tree_uniform(int64_t n, const double* x, const double* y, int L,
+int orc_tree_uniform(int64_t n, const double* x, const double* y, int L, const double* root,
                      int32_t* perm, double* rects, int64_t* leaf_begin)
 {
     if (n <= 0 || L < 0 || L > 15 || !x || !y || !perm || !rects || !leaf_begin) return -1;
@@ -201,7 +202,13 @@ int orc_tree_uniform(int64_t n, const double* x, const double* y, int L,
         if (y[i] > y1) y1 = y[i];
     }
     const double sx = x1 - x0, sy = y1 - y0;
-    const double side = sx > sy ? sx : sy;
+    double side = sx > sy ? sx : sy;
+    if (root) { /* a given root square (x0, y0, side); points outside fall into its edge cells */
+        if (!(root[2] >= 0.0)) return -1;
+        x0 = root[0];
+        y0 = root[1];
+        side = root[2];
+    }
     const int64_t nleaf = ((int64_t)1) << (2 * L), m = ((int64_t)1) << L;
     /* every box of every level */
     for (int l = 0; l <= L; l++) {
@@ -774,15 +781,15 @@ void orc_direct_field(int64_t n, const double* x, const double* y, const double*
  * Returns 0 or a negative code as orc_tree.
  * ------------------------------------------------------------------------------------------ */
 static int fmm_core(int64_t n, const double* x, const double* y, const double* q, int L, int p,
-                    double theta, int flags, double* phi, double* fre, double* fim, double* mpole_out,
-                    double* local_out)
+                    double theta, int flags, const double* root, double* phi, double* fre, double* fim,
+                    double* mpole_out, double* local_out)
 {
     if (p < 0 || p > ORC_PMAX || !(theta > 0.0 && theta < 1.0)) return -1;
     int64_t nbox = orc_nbox(L), nleaf = ((int64_t)1) << (2 * L);
     int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     double* rects = (double*)malloc(sizeof(double) * 4 * (size_t)nbox);
     int64_t* lb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nleaf + 1));
-    int rc = (flags & 4) ? orc_tree_uniform(n, x, y, L, perm, rects, lb) : orc_tree(n, x, y, L, perm, rects, lb);
+    int rc = (flags & 4) ? orc_tree_uniform(n, x, y, L, root, perm, rects, lb) : orc_tree(n, x, y, L, perm, rects, lb);
     if (rc) { free(perm); free(rects); free(lb); return rc; }
     double* cen = (double*)malloc(sizeof(double) * 2 * (size_t)nbox);
     double* rad = (double*)malloc(sizeof(double) * (size_t)nbox);
@@ -902,7 +909,7 @@ static int fmm_core(int64_t n, const double* x, const double* y, const double* q
 int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L, int p,
             double theta, double* phi, double* mpole_out, double* local_out)
 {
-    return fmm_core(n, x, y, q, L, p, theta, 0, phi, NULL, NULL, mpole_out, local_out);
+    return fmm_core(n, x, y, q, L, p, theta, 0, NULL, phi, NULL, NULL, mpole_out, local_out);
 }
 
 /* The method with the optional structural optimisations of Section 4: flags & 1 parent-level
@@ -912,7 +919,14 @@ int orc_fmm(int64_t n, const double* x, const double* y, const double* q, int L,
 int orc_fmm_ex(int64_t n, const double* x, const double* y, const double* q, int L, int p,
                double theta, int flags, double* phi)
 {
-    return fmm_core(n, x, y, q, L, p, theta, flags, phi, NULL, NULL, NULL, NULL);
+    return fmm_core(n, x, y, q, L, p, theta, flags, NULL, phi, NULL, NULL, NULL, NULL);
+}
+
+/* The same with the uniform-grid mesh on a given root square (flags & 4; root = x0, y0, side). */
+int orc_fmm_root(int64_t n, const double* x, const double* y, const double* q, int L, int p,
+                 double theta, int flags, const double* root, double* phi)
+{
+    return fmm_core(n, x, y, q, L, p, theta, flags | 4, root, phi, NULL, NULL, NULL, NULL);
 }
 
 /* The method for the complex field G(z_i, z_j) = -q_j / (z_i - z_j) (Section 5): the same tree,
@@ -921,12 +935,12 @@ int orc_fmm_ex(int64_t n, const double* x, const double* y, const double* q, int
 int orc_fmm_field(int64_t n, const double* x, const double* y, const double* q, int L, int p,
                   double theta, double* fre, double* fim)
 {
-    return fmm_core(n, x, y, q, L, p, theta, 0, NULL, fre, fim, NULL, NULL);
+    return fmm_core(n, x, y, q, L, p, theta, 0, NULL, NULL, fre, fim, NULL, NULL);
 }
 
 /* The field with the optional optimisations (flags as orc_fmm_ex). */
 int orc_fmm_field_ex(int64_t n, const double* x, const double* y, const double* q, int L, int p,
                      double theta, int flags, double* fre, double* fim)
 {
-    return fmm_core(n, x, y, q, L, p, theta, flags, NULL, fre, fim, NULL, NULL);
+    return fmm_core(n, x, y, q, L, p, theta, flags, NULL, NULL, fre, fim, NULL, NULL);
 }

@@ -108,7 +108,8 @@ void free_lists(fmm_lists l)
 {
     if (!l) return;
     void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status,
-                    l->dlinst, l->tiledrop, l->tileswap, l->xoff, l->xidx, l->xtgt};
+                    l->dlinst, l->tiledrop, l->tileswap, l->xoff, l->xidx, l->xtgt, l->p2p_items, l->p2p_pos,
+                    l->p2p_tmp, l->p2p_zero};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete[] l->hlinst;
@@ -215,11 +216,14 @@ int fmm_build_tree(fmm_tree t, const double* x, const double* y, void* stream)
     return tree_build(t, x, y, (cudaStream_t)stream);
 }
 
-int fmm_build_tree_uniform(fmm_tree t, const double* x, const double* y, void* stream)
+int fmm_build_tree_uniform(fmm_tree t, const double* x, const double* y, const double* root_host, void* stream)
 {
     if (!t || !x || !y) return fail(FMM_ERR_ARG, "NULL argument");
+    if (root_host && !(root_host[2] >= 0.0 && std::isfinite(root_host[0]) && std::isfinite(root_host[1]) &&
+                       std::isfinite(root_host[2])))
+        return fail(FMM_ERR_ARG, "the root square needs finite x0, y0 and a side >= 0");
     GUARD(t->dev);
-    return tree_build_uniform(t, x, y, (cudaStream_t)stream);
+    return tree_build_uniform(t, x, y, root_host, (cudaStream_t)stream);
 }
 
 int fmm_tree_export(fmm_tree t, int32_t* perm, double* rects, int32_t* leaf_begin, void* stream)

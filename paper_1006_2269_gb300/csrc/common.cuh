@@ -285,6 +285,11 @@ struct fmm_lists_s {
     int32_t* xoff = nullptr;
     int32_t* xidx = nullptr;
     int32_t* xtgt = nullptr;  // target leaf (global id) of each exchange entry
+    // general near-field kernel: work items per strong pair, their exclusive scan
+    int32_t* p2p_items = nullptr;
+    int32_t* p2p_pos = nullptr;
+    uint32_t* p2p_tmp = nullptr;
+    int32_t* p2p_zero = nullptr;
 };
 
 namespace fmm {
@@ -302,7 +307,7 @@ void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls);
 void forest_totals(fmm_tree t);
 int tree_tables_host(int64_t n, int L, int32_t* ones_before, int32_t* node_off, int32_t* leaf_begin);
 int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s);
-int tree_build_uniform(fmm_tree t, const double* x, const double* y, cudaStream_t s);
+int tree_build_uniform(fmm_tree t, const double* x, const double* y, const double* root_host, cudaStream_t s);
 
 // lists.cu
 int lists_build(fmm_tree t, fmm_lists l, double theta, cudaStream_t s);

@@ -1213,14 +1213,69 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
     }
 }
 
-// Leaves of more than 32 points: one lane per target, 32 targets at a time, every source of the
-// pair; one flush per (pair, block of 32 targets).
+// Leaves of more than small_leaf points.  The work of one leaf pair is cut into items (block of
+// 32 targets, block of sources), and the items of all pairs are numbered by a scan, so one large
+// pair spreads over many warps: the uniform-grid mesh can put most points into a few leaves.
+// One lane per target; one flush per item.
+constexpr int P2P_SCH = 1024;         // sources per item (coarser for very large leaves)
+constexpr int64_t P2P_ITEMS_MAX = int64_t(1) << 20;  // items of one pair at most
+
+// Source blocks of a pair: about P2P_SCH sources each, at most P2P_ITEMS_MAX items per pair.
+__device__ __forceinline__ int32_t p2p_src_blocks(int32_t nt, int32_t ns)
+{
+    const int64_t ntc = (nt + 31) / 32;
+    int64_t nsc = (ns + P2P_SCH - 1) / P2P_SCH;
+    if (ntc * nsc > P2P_ITEMS_MAX) nsc = max((int64_t)1, P2P_ITEMS_MAX / ntc);
+    return (int32_t)nsc;
+}
+
+// items[T.s0 + e] for every position e of an instance's strong array (0 outside the finest
+// level's pairs and for instances left to the leaf-pair kernels); schedule: near field
+__global__ void __launch_bounds__(256) k_p2p_items(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+                                                   int small_leaf, const int32_t* __restrict__ soff,
+                                                   const int32_t* __restrict__ sidx,
+                                                   const int32_t* __restrict__ stgt,
+                                                   const int32_t* __restrict__ lb, int32_t* __restrict__ items,
+                                                   unsigned long long* total)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
+    soff += S.o0;
+    sidx += TL.s0;
+    stgt += TL.s0;
+    lb += S.lb0;
+    items += TL.s0;
+    const bool mine = S.maxleaf > small_leaf;
+    const int64_t base = level_base(S.L);
+    const int64_t e_begin = min((int64_t)soff[base], TL.scap);
+    const int64_t e_end = min((int64_t)soff[base + level_size(S.L)], TL.scap);
+    unsigned long long sum = 0;
+    for (int64_t e = (int64_t)z.rank * blockDim.x + threadIdx.x; e < TL.scap; e += (int64_t)z.nb * blockDim.x) {
+        int32_t v = 0;
+        if (mine && e >= e_begin && e < e_end) {
+            const int64_t tl = stgt[e] - base, sl = sidx[e];
+            const int32_t nt = lb[tl + 1] - lb[tl], ns = lb[sl + 1] - lb[sl];
+            v = nt > 0 && ns > 0 ? (int32_t)((nt + 31) / 32) * p2p_src_blocks(nt, ns) : 0;
+        }
+        items[e] = v;
+        sum += (unsigned long long)v;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(total, sum);  // all items: must fit the int32 scan
+}
+
+// schedule: near field; pos = exclusive scan of items over all instances' strong arrays
 template <typename T>
 __global__ void __launch_bounds__(256) k_p2p_large(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                    int small_leaf, const int32_t* __restrict__ soff,
                                                    const int32_t* __restrict__ sidx,
                                                    const int32_t* __restrict__ stgt,
                                                    const int32_t* __restrict__ lb,
+                                                   const int32_t* __restrict__ pos,
+                                                   const unsigned long long* __restrict__ total,
+                                                   int32_t* status,
                                                    const Pk<T>* __restrict__ pk,
                                                    const double* __restrict__ xs,
                                                    const double* __restrict__ ys,
@@ -1236,10 +1291,15 @@ __global__ void __launch_bounds__(256) k_p2p_large(Sched sc, const Inst* __restr
     const LInst TL = LIs[z.i];
     const int L = S.L;
     if ((int64_t)S.maxleaf <= small_leaf) return;  // done by the leaf-pair kernel
+    if (*total > (unsigned long long)INT32_MAX) {  // the item numbering did not fit
+        if (threadIdx.x == 0) atomicOr(status, ST_ARG);
+        return;
+    }
     const int64_t scap = TL.scap;
     soff += S.o0;
     sidx += TL.s0;
     stgt += TL.s0;
+    pos += TL.s0;
     lb += S.lb0;
     pk += S.p0;
     xs += S.p0;
@@ -1254,56 +1314,65 @@ __global__ void __launch_bounds__(256) k_p2p_large(Sched sc, const Inst* __restr
     const int64_t base = level_base(L);
     const int64_t e_begin = min((int64_t)soff[base], scap);
     const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
+    if (e_end <= e_begin) return;
+    const int64_t v0 = pos[e_begin], v1 = pos[e_end];
     const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
-    for (int64_t e = e_begin + warp; e < e_end; e += nwarps) {
+    for (int64_t v = v0 + warp; v < v1; v += nwarps) {
+        // the pair owning item v: the last e with pos[e] <= v (pairs without items share pos)
+        int64_t lo = e_begin, hi = e_end - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (pos[mid] <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t e = lo;
         const int64_t tl = stgt[e] - base, sl = sidx[e];
         const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0, s0 = lb[sl], ns = lb[sl + 1] - s0;
-        float ox = 0.f, oy = 0.f, tau2 = 0.f;
+        const int32_t nsc = p2p_src_blocks(nt, ns), ntc = (nt + 31) / 32;
+        const int32_t local = (int32_t)(v - pos[e]);
+        const int32_t tc = local % ntc, scb = local / ntc;
+        const int32_t slen = (ns + nsc - 1) / nsc;
+        const int32_t jb0 = scb * slen, jb1 = min(ns, jb0 + slen);
+        const int32_t it = t0 + tc * 32 + lane;
+        if (tc * 32 + lane >= nt) continue;
+        const Pk<T> p = pk[it];
         if constexpr (F32) {
             const int64_t sg = base + sl, tg = base + tl;
-            ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
-            oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
+            const float ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
+            const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
             const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
-            tau2 = fmaxf((M * (1.f / 256.f)) * (M * (1.f / 256.f)), 1e-30f);  // > 0: r = 0 is exact
-        }
-        for (int tc = 0; tc < nt; tc += 32) {
-            const int32_t it = t0 + tc + lane;
-            if (tc + lane >= nt) continue;
-            const Pk<T> p = pk[it];
-            if constexpr (F32) {
-                const float xt = p.x - ox, yt = p.y - oy;
-                float hi = 0.f, lo = 0.f;
-                for (int jb = 0; jb < ns; jb += 32) {
-                    float part = 0.f;
-                    const int je = min(ns, jb + 32);
-                    for (int j = jb; j < je; j++) {
-                        const Pk<float> sp = pk[s0 + j];
-                        const float dx = xt - sp.x, dy = yt - sp.y;
-                        const float r2 = dx * dx + dy * dy;
-                        if (r2 >= tau2) {
-                            part += sp.q * __log2f(r2);
-                        } else {
-                            const double ddx = xs[it] - xs[s0 + j], ddy = ys[it] - ys[s0 + j];
-                            const double r2d = ddx * ddx + ddy * ddy;
-                            if (r2d >= 1e-36) part += sp.q * lg2_fast((float)r2d);
-                            else if (r2d > 0.0) part += sp.q * (float)log2(r2d);
-                        }
+            const float tau2 = fmaxf((M * (1.f / 256.f)) * (M * (1.f / 256.f)), 1e-30f);  // > 0: r = 0 is exact
+            const float xt = p.x - ox, yt = p.y - oy;
+            float hi = 0.f, lo2 = 0.f;
+            for (int32_t jb = jb0; jb < jb1; jb += 32) {
+                float part = 0.f;
+                const int32_t je = min(jb1, jb + 32);
+                for (int32_t j = jb; j < je; j++) {
+                    const Pk<float> sp = pk[s0 + j];
+                    const float dx = xt - sp.x, dy = yt - sp.y;
+                    const float r2 = dx * dx + dy * dy;
+                    if (r2 >= tau2) {
+                        part += sp.q * __log2f(r2);
+                    } else {
+                        const double ddx = xs[it] - xs[s0 + j], ddy = ys[it] - ys[s0 + j];
+                        const double r2d = ddx * ddx + ddy * ddy;
+                        if (r2d >= 1e-36) part += sp.q * lg2_fast((float)r2d);
+                        else if (r2d > 0.0) part += sp.q * (float)log2(r2d);
                     }
-                    two_sum(hi, lo, part);
                 }
-                atomicAdd(&nhi[it], hi);
-                atomicAdd(&nlo[it], lo);
-            } else {
-                double part = 0.0;
-                for (int j = 0; j < ns; j++) {
-                    const Pk<double> sp = pk[s0 + j];
-                    const double dx = p.x - sp.x, dy = p.y - sp.y;
-                    const double r2 = dx * dx + dy * dy;
-                    if (r2 > 0.0) part += sp.q * log(r2);
-                }
-                atomicAdd(&acc64[it], 0.5 * part);
+                two_sum(hi, lo2, part);
             }
+            atomic_add_ff(&nhi[it], &nlo[it], hi, lo2);  // many items may add to one target
+        } else {
+            double part = 0.0;
+            for (int32_t j = jb0; j < jb1; j++) {
+                const Pk<double> sp = pk[s0 + j];
+                const double dx = p.x - sp.x, dy = p.y - sp.y;
+                const double r2 = dx * dx + dy * dy;
+                if (r2 > 0.0) part += sp.q * log(r2);
+            }
+            atomicAdd(&acc64[it], 0.5 * part);
         }
     }
 }
@@ -1819,6 +1888,21 @@ int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<double> geo, const
 
 // The whole evaluation: the potential into phi, or (fim != nullptr) the complex field into
 // phi (real part) and fim (imaginary part).
+// Workspace of the general near-field kernel (item counts, their scan), sized by the strong
+// capacity; allocated on first use (synchronous).
+int p2p_items_ws(fmm_lists li)
+{
+    if (li->p2p_items) return 0;
+    const int64_t m = std::max<int64_t>(li->scap, 1);
+    if (cudaMalloc((void**)&li->p2p_items, 4 * (size_t)m) != cudaSuccess ||
+        cudaMalloc((void**)&li->p2p_pos, 4 * (size_t)(m + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&li->p2p_tmp, 4 * (size_t)scan_tmp_words(m)) != cudaSuccess ||
+        cudaMalloc((void**)&li->p2p_zero, 16) != cudaSuccess)  // [0]: 0 (scan base); [2..3]: item total
+        return fail(FMM_ERR_OOM, "near-field workspace");
+    FMM_CUDA(cudaMemset(li->p2p_zero, 0, 16));
+    return 0;
+}
+
 template <typename T>
 int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStream_t s, double* fim = nullptr)
 {
@@ -1991,9 +2075,17 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             note_launch();
         }
         if (maxleaf > small_leaf) {
+            rc = p2p_items_ws(li);
+            if (rc) return rc;
+            unsigned long long* total = (unsigned long long*)(li->p2p_zero + 2);
+            FMM_CUDA(cudaMemsetAsync(total, 0, 8, s));
+            k_p2p_items<<<gp2p, 256, 0, s>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt, t->leaf_begin,
+                                             li->p2p_items, total); note_launch();
+            rc = scan_with_base(li->p2p_items, li->scap, li->p2p_zero, li->p2p_pos, li->p2p_tmp, s);
+            if (rc) return rc;
             k_p2p_large<T><<<gp2p, 256, 0, s>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt,
-                                                t->leaf_begin, pk, t->xs, t->ys, t->cen_hi, t->cen_lo,
-                                                t->rad32, t->acc, nhi, nlo); note_launch();
+                                                t->leaf_begin, li->p2p_pos, total, t->status, pk, t->xs, t->ys,
+                                                t->cen_hi, t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
         }
         if (f64)
             k_unpermute<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->acc, phi);

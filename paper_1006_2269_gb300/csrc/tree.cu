@@ -607,8 +607,14 @@ __global__ void k_gather_points(Sched sc, const Inst* __restrict__ I, const int3
 // 0 when side = 0).  Binary64 with explicit rounding, so the mesh is the same bit for bit on any
 // machine that rounds to nearest.
 
-__device__ __forceinline__ double bbox_side(const uint64_t* bb, double& x0, double& y0)
+// The root square: given (x0, y0, side) when root.z >= 0, else the bounding square.
+__device__ __forceinline__ double root_square(const uint64_t* bb, double3 root, double& x0, double& y0)
 {
+    if (root.z >= 0.0) {
+        x0 = root.x;
+        y0 = root.y;
+        return root.z;
+    }
     x0 = key_value(bb[0]);
     y0 = key_value(bb[2]);
     const double sx = __dsub_rn(key_value(bb[1]), x0), sy = __dsub_rn(key_value(bb[3]), y0);
@@ -617,7 +623,7 @@ __device__ __forceinline__ double bbox_side(const uint64_t* bb, double& x0, doub
 
 // leaf of every point (input order); schedule: points
 __global__ void k_uniform_cells(Sched sc, const Inst* __restrict__ I, const double* __restrict__ x,
-                                const double* __restrict__ y, const uint64_t* __restrict__ bbox,
+                                const double* __restrict__ y, const uint64_t* __restrict__ bbox, double3 root,
                                 uint32_t* __restrict__ leaf_of)
 {
     const Slot z = slot_of(sc);
@@ -626,7 +632,7 @@ __global__ void k_uniform_cells(Sched sc, const Inst* __restrict__ I, const doub
     y += S.p0;
     leaf_of += S.p0;
     double x0, y0;
-    const double side = bbox_side(bbox + 4 * z.i, x0, y0);
+    const double side = root_square(bbox + 4 * z.i, root, x0, y0);
     const int L = S.L;
     const int64_t m = int64_t(1) << L;
     for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
@@ -681,13 +687,13 @@ __global__ void k_reset_maxleaf(Inst* I, int n_inst)
 
 // rectangles of every box; schedule: points (boxes of the instance, grid-stride)
 __global__ void k_uniform_rects(Sched sc, const Inst* __restrict__ I, const uint64_t* __restrict__ bbox,
-                                double* __restrict__ rects)
+                                double3 root, double* __restrict__ rects)
 {
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
     rects += 4 * S.b0;
     double x0, y0;
-    const double side = bbox_side(bbox + 4 * z.i, x0, y0);
+    const double side = root_square(bbox + 4 * z.i, root, x0, y0);
     for (int64_t g = (int64_t)z.rank * blockDim.x + threadIdx.x; g < S.nbox; g += (int64_t)z.nb * blockDim.x) {
         int l = 0;
         while (level_base(l + 1) <= g) l++;
@@ -939,12 +945,15 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
     return 0;
 }
 
-// The uniform-grid mesh in place of the median tree (same handle, same downstream stages): cells
+// The uniform-grid mesh in place of the median tree (same handle, same downstream stages), on the
+// bounding square or on a given root square (x0, y0, side) shared by all instances: cells
 // of every point, a stable sort by cell (ties keep input order), leaf offsets and the largest
 // leaf of every instance (read back, so this call synchronises the stream), the rectangles of
 // every box, the box geometry and the canonical coordinates.
-int tree_build_uniform(fmm_tree t, const double* x, const double* y, cudaStream_t s)
+int tree_build_uniform(fmm_tree t, const double* x, const double* y, const double* root_host, cudaStream_t s)
 {
+    const double3 root = root_host ? make_double3(root_host[0], root_host[1], root_host[2])
+                                   : make_double3(0.0, 0.0, -1.0);
     const int64_t n = t->n;
     const int ni = t->n_inst;
     const int L = t->Lmax;
@@ -960,7 +969,7 @@ int tree_build_uniform(fmm_tree t, const double* x, const double* y, cudaStream_
         StageScope scope(FMM_STAGE_TREE_SORT, s);
         k_bbox_init<<<1, 256, 0, s>>>(ni, t->bbox_keys); note_launch();
         k_make_keys<<<gp, 256, 0, s>>>(sp, t->dinst, x, y, n, t->keys, t->bbox_keys, t->status); note_launch();
-        k_uniform_cells<<<gp, 256, 0, s>>>(sp, t->dinst, x, y, t->bbox_keys, leaf_of); note_launch();
+        k_uniform_cells<<<gp, 256, 0, s>>>(sp, t->dinst, x, y, t->bbox_keys, root, leaf_of); note_launch();
         FMM_LAUNCH_CHECK("uniform tree: cells");
         uint32_t* k32 = (uint32_t*)t->keys;
         int32_t* v32 = t->vals + 2 * n;
@@ -975,7 +984,7 @@ int tree_build_uniform(fmm_tree t, const double* x, const double* y, cudaStream_
     }
     {
         StageScope scope(FMM_STAGE_TREE_FINISH, s);
-        k_uniform_rects<<<gp, 256, 0, s>>>(sp, t->dinst, t->bbox_keys, t->rects); note_launch();
+        k_uniform_rects<<<gp, 256, 0, s>>>(sp, t->dinst, t->bbox_keys, root, t->rects); note_launch();
         const int64_t nb = t->nbox;
         k_geometry<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(t->rects, nb, t->centers, t->radii,
                                                                 t->rad32, t->cen_hi, t->cen_lo); note_launch();

@@ -89,7 +89,7 @@ def load_library(path: str = LIB_PATH):
             "fmm_lists_create": (i32, [vp, i64, i64, ctypes.POINTER(vp)]),
             "fmm_interaction_lists": (i32, [vp, vp, dbl, vp]),
             "fmm_lists_set_mode": (i32, [vp, i32]),
-            "fmm_build_tree_uniform": (i32, [vp, vp, vp, vp]),
+            "fmm_build_tree_uniform": (i32, [vp, vp, vp, vp, vp]),
             "fmm_lists_export_exchange": (i32, [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]),
             "fmm_lists_sync": (i32, [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
             "fmm_lists_export": (i32, [vp, vp, vp, vp, vp, vp]),
@@ -185,12 +185,16 @@ def fmm_build_tree(tree, x: torch.Tensor, y: torch.Tensor, stream=None):
                                          _dev(y, torch.float64, n, "y"), _stream(stream)))
 
 
-def fmm_build_tree_uniform(tree, x: torch.Tensor, y: torch.Tensor, stream=None):
+def fmm_build_tree_uniform(tree, x: torch.Tensor, y: torch.Tensor, root=None, stream=None):
     """The uniform-grid mesh (square root, geometric quadrants) in place of the median tree, for
-    the adaptive-vs-uniform comparison; synchronises the stream."""
+    the adaptive-vs-uniform comparison; ``root`` = (x0, y0, side) fixes the root square (default:
+    the bounding square).  Synchronises the stream."""
     n = fmm_tree_info(tree)[0]
+    r = None if root is None else (ctypes.c_double * 3)(*[float(v) for v in root])
     _check(load_library().fmm_build_tree_uniform(tree, _dev(x, torch.float64, n, "x"),
-                                                 _dev(y, torch.float64, n, "y"), _stream(stream)))
+                                                 _dev(y, torch.float64, n, "y"),
+                                                 None if r is None else ctypes.cast(r, ctypes.c_void_p),
+                                                 _stream(stream)))
 
 
 FMM_NOALLOC_MAX_POINTS = 65536
@@ -496,10 +500,11 @@ class FMM:
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, levels: int, theta: float = 0.5,
                  weak_capacity: int = 0, strong_capacity: int = 0, check: bool = True, parents: bool = False,
-                 exchange: bool = False, mesh: str = "adaptive"):
+                 exchange: bool = False, mesh: str = "adaptive", root=None):
         if mesh not in ("adaptive", "uniform"):
             raise FMMError(FMM_ERR_ARG, f"mesh must be 'adaptive' or 'uniform', not {mesh!r}")
         self.mesh = mesh
+        self.root = root  # uniform mesh: (x0, y0, side) or None for the bounding square
         self.n = x.numel()
         self.levels = levels
         self.theta = theta
@@ -521,7 +526,10 @@ class FMM:
         capacity and retries when the lists overflow."""
         if theta is not None:
             self.theta = theta
-        (fmm_build_tree_uniform if self.mesh == "uniform" else fmm_build_tree)(self.tree, x, y)
+        if self.mesh == "uniform":
+            fmm_build_tree_uniform(self.tree, x, y, self.root)
+        else:
+            fmm_build_tree(self.tree, x, y)
         fmm_interaction_lists(self.tree, self.lists, self.theta)
         if check:
             try:
@@ -616,10 +624,11 @@ class FMMBatch:
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, sizes, levels, theta: float = 0.5,
                  check: bool = True, weak_per_box: int = 48, strong_per_box: int = 24, parents: bool = False,
-                 exchange: bool = False, mesh: str = "adaptive"):
+                 exchange: bool = False, mesh: str = "adaptive", root=None):
         if mesh not in ("adaptive", "uniform"):
             raise FMMError(FMM_ERR_ARG, f"mesh must be 'adaptive' or 'uniform', not {mesh!r}")
         self.mesh = mesh
+        self.root = root
         self.sizes = [int(v) for v in sizes]
         self.levels = [int(v) for v in levels]
         self.n = sum(self.sizes)
@@ -646,7 +655,10 @@ class FMMBatch:
         instance whose lists overflowed and rebuilds."""
         if theta is not None:
             self.theta = theta
-        (fmm_build_tree_uniform if self.mesh == "uniform" else fmm_build_tree)(self.tree, x, y)
+        if self.mesh == "uniform":
+            fmm_build_tree_uniform(self.tree, x, y, self.root)
+        else:
+            fmm_build_tree(self.tree, x, y)
         fmm_interaction_lists(self.tree, self.lists, self.theta)
         if check:
             w, s, over = fmm_lists_counts(self.lists, self.n_inst, check=False)

@@ -155,3 +155,39 @@ def test_collapsed_leaf_pairs(fmmlib, cuda, mesh):
             assert np.max(np.abs(got)) == 0
     finally:
         f.close()
+
+
+@pytest.mark.parametrize("root", [(0.0, 0.0, 1.0), (-0.25, -0.5, 2.0)])
+def test_fixed_root_square(fmmlib, orc, cuda, root):
+    c = W.normal_sq(30000, 53, 0.01)
+    L = 6
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), L, 0.5, mesh="uniform", root=root)
+    try:
+        perm, rects, lb = (a.cpu().numpy() for a in f.export_tree())
+        op, orr, olb = orc.tree_uniform(c.x, c.y, L, root=root)
+        assert np.array_equal(perm, op) and np.array_equal(rects, orr)
+        assert np.array_equal(lb.astype(np.int64), olb)
+        for mode, p, tol in (("fp64", 16, 1e-12), ("mixed", 20, 1e-6)):
+            got = f.evaluate(_t(c.q, cuda), p, mode).cpu().numpy()
+            assert relerr(got, orc.fmm(c.x, c.y, c.q, L, p, 0.5, root=root)) <= tol
+    finally:
+        f.close()
+
+
+def test_one_giant_leaf_mixed(fmmlib, orc, cuda):
+    # a tight cluster in the unit-square mesh: nearly every point in one leaf, which the general
+    # near-field kernel spreads over many warps; the mixed path stays within 1e-6 of the direct sum
+    c = W.normal_sq(60000, 54, 0.002)
+    L = 5
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), L, 0.5, mesh="uniform", root=(0.0, 0.0, 1.0))
+    try:
+        lb = f.export_tree()[2].cpu().numpy()
+        assert np.diff(lb).max() > 50000
+        tg = W.sample_targets(c.x.size, 1000, 55)
+        ref = orc.direct(c.x, c.y, c.q, tg, nthreads=0)
+        got = f.evaluate(_t(c.q, cuda), 20, "mixed").cpu().numpy()[tg]
+        assert relerr(got, ref) <= 1e-6
+        got = f.evaluate(_t(c.q, cuda), 20, "fp64").cpu().numpy()[tg]
+        assert relerr(got, ref) <= 1e-10
+    finally:
+        f.close()

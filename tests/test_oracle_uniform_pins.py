@@ -121,3 +121,20 @@ def test_method_converges(make):
     fe = oracle.fmm_field(c.x, c.y, c.q, 5, 16, 0.5, uniform=True)
     de = oracle.direct_field(c.x, c.y, c.q)
     assert np.max(np.abs(fe - de)) / np.max(np.abs(de)) <= 0.5 ** 17 / 0.25
+
+
+def test_fixed_unit_square_root():
+    # Section 5's experiment puts every point in the unit square; with that square as the root
+    # the leaves are the dyadic squares [i/2^L, (i+1)/2^L] x [j/2^L, (j+1)/2^L] exactly
+    c = W.normal_sq(6000, 19, 0.05)
+    L = 4
+    perm, rects, lb = oracle.tree_uniform(c.x, c.y, L, root=(0.0, 0.0, 1.0))
+    m = 2 ** L
+    leaves = rects[_base(L):]
+    assert np.all(np.isin(leaves[:, 0] * m, np.arange(m))) and np.all(leaves[:, 1] - leaves[:, 0] == 1.0 / m)
+    H, _, _ = np.histogram2d(c.x, c.y, bins=[np.linspace(0, 1, m + 1), np.linspace(0, 1, m + 1)])
+    assert np.diff(lb).max() == H.max() and np.sum(np.diff(lb) > 0) == np.sum(H > 0)
+    d = oracle.direct(c.x, c.y, c.q)
+    errs = [np.max(np.abs(oracle.fmm(c.x, c.y, c.q, L, p, 0.5, root=(0.0, 0.0, 1.0)) - d)) / np.max(np.abs(d))
+            for p in (6, 12)]
+    assert errs[1] <= errs[0] / 8 and errs[1] <= 0.5 ** 13 / 0.25
