@@ -256,6 +256,16 @@ void fmm_lists_destroy(fmm_lists l);
 int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi,
                  void* stream);
 
+/* One whole step on new coordinates and strengths: fmm_build_tree, fmm_interaction_lists and
+ * fmm_evaluate in one call, with the independent parts overlapped on a second stream owned by the
+ * tree.  The lists are built there while `stream` packs the points and runs the upward pass, and
+ * in the mixed mode the near field runs there while `stream` finishes the far field.  Every
+ * dependency goes through events, so the call may be captured into a CUDA graph on `stream`
+ * (the first call creates the stream and its events: make it before capturing).  Same arguments
+ * and errors as the three calls. */
+int fmm_step(fmm_tree t, fmm_lists l, const double* x, const double* y, double theta, const double* q,
+             const fmm_params* prm, double* phi, void* stream);
+
 /* Launch-shape tuning (no paper counterpart).  The M2L and near-field launches of a tree use a
  * total number of blocks that is shared out over its instances in proportion to their work.
  * fmm_autotune runs complete evaluations of (t, l, q, prm) on `stream` for a ladder of such
@@ -379,8 +389,10 @@ typedef enum {
     FMM_STAGE_M2M = 6,
     FMM_STAGE_M2L = 7,
     FMM_STAGE_L2L = 8,
-    FMM_STAGE_LEAF = 9,        /* L2P + near-field direct sum, potentials written in input order */
-    FMM_STAGE_COUNT = 10
+    FMM_STAGE_LEAF = 9,        /* L2P (P2L, M2P), far and near joined in input order (the field:
+                                  also its near sum)                                            */
+    FMM_STAGE_NEAR = 10,       /* near-field direct sum of the potentials                     */
+    FMM_STAGE_COUNT = 11
 } fmm_stage;
 
 /* Enable (on != 0) or disable recording of a CUDA event pair around every stage, on the stream

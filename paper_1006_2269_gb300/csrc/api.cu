@@ -100,6 +100,9 @@ void free_tree(fmm_tree t)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     sched_free_all(t);
+    for (cudaEvent_t e : t->ev)
+        if (e) cudaEventDestroy(e);
+    if (t->side) cudaStreamDestroy(t->side);
     if (t->own_hinst) delete[] t->hinst;
     delete t;
 }
@@ -505,6 +508,32 @@ int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
         return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
     GUARD(t->dev);
     return evaluate(t, l, q, *prm, phi, (cudaStream_t)stream);
+}
+
+int fmm_step(fmm_tree t, fmm_lists l, const double* x, const double* y, double theta, const double* q,
+             const fmm_params* prm, double* phi, void* stream)
+{
+    if (!t || !l || !x || !y || !q || !prm || !phi) return fail(FMM_ERR_ARG, "NULL argument");
+    if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
+    if (!(theta > 0.0 && theta < 1.0)) return fail(FMM_ERR_ARG, "theta = %g outside (0, 1)", theta);
+    if (prm->p < 0 || prm->p > 40) return fail(FMM_ERR_ARG, "p = %d outside [0, 40]", prm->p);
+    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED)
+        return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
+    GUARD(t->dev);
+    if (!t->side) {
+        FMM_CUDA(cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : t->ev) FMM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = tree_build(t, x, y, s);
+    if (rc) return rc;
+    FMM_CUDA(cudaEventRecord(t->ev[0], s));  // tree complete
+    FMM_CUDA(cudaStreamWaitEvent(t->side, t->ev[0], 0));
+    rc = lists_build(t, l, theta, t->side);
+    if (rc) return rc;
+    FMM_CUDA(cudaEventRecord(t->ev[1], t->side));
+    const StepSync sync{t->side, t->ev[1], t->ev[2], t->ev[3]};
+    return evaluate(t, l, q, *prm, phi, s, &sync);
 }
 
 int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm, double* phi, void* stream,

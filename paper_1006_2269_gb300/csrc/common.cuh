@@ -256,6 +256,9 @@ struct fmm_tree_s {
     // leaf offsets and largest leaves then come from the data; the balanced leaf offsets are kept
     // in lb_bal to restore them for the next median build
     bool uniform = false;
+    // fmm_step: a second stream and its events, created on first use
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t* lb_bal = nullptr;
 };
 
@@ -316,8 +319,15 @@ int64_t lists_tile_words(int64_t scap);
 int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int64_t* strong_capacity);
 
 // expand.cu
+// Two-stream step (fmm_step): the lists are built on `side` (lists_done when complete); the
+// evaluation records `gathered` once the points are packed, and its binary32 near field runs on
+// `side`, recording `near_done`.
+struct StepSync {
+    cudaStream_t side;
+    cudaEvent_t lists_done, gathered, near_done;
+};
 int evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,
-             cudaStream_t s);
+             cudaStream_t s, const StepSync* sync = nullptr);
 int evaluate_field(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* fre,
                    double* fim, cudaStream_t s);
 int direct_field(const double* x, const double* y, const double* q, int64_t n, const int64_t* tgt,

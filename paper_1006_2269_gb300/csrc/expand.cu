@@ -905,7 +905,7 @@ __global__ void k_l2p(Sched sc, const Inst* __restrict__ I, int P, int PS, const
         } else {
             cx<T> h = B[P - 1];
             for (int k = P - 2; k >= 0; k--) h = cfma(h, z, B[k]);
-            far[i] = h.re;
+            far[i] += h.re;  // binary64: the near field is already in the accumulator
         }
     }
 }
@@ -1904,8 +1904,18 @@ int p2p_items_ws(fmm_lists li)
 }
 
 template <typename T>
-int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStream_t s, double* fim = nullptr)
+int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStream_t s, double* fim = nullptr,
+        const StepSync* sync = nullptr)
 {
+    // with sync the lists are being built on sync->side: wait for them before their first use
+    bool lists_waited = false;
+    auto wait_lists = [&]() -> int {
+        if (sync && !lists_waited) {
+            FMM_CUDA(cudaStreamWaitEvent(s, sync->lists_done, 0));
+            lists_waited = true;
+        }
+        return 0;
+    };
     const bool f64 = sizeof(T) == 8;
     const bool field = fim != nullptr;
     const int PS = (P + 1) & ~1;
@@ -1952,6 +1962,7 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         FMM_CUDA(cudaMemsetAsync(Le, 0, (size_t)t->nbox * PS * sizeof(cx<T>), s));
         if (!f64) FMM_CUDA(cudaMemsetAsync(t->Lf0lo, 0, 4 * (size_t)t->nbox, s));
         FMM_LAUNCH_CHECK("evaluate: gather");
+        if (sync) FMM_CUDA(cudaEventRecord(sync->gathered, s));
     }
     if (Lmax >= 1) {
         {
@@ -1970,6 +1981,7 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             }
             FMM_LAUNCH_CHECK("evaluate: M2M");
         }
+        if ((rc = wait_lists())) return rc;
         {
             StageScope scope(FMM_STAGE_M2L, s);
             // tensor cores where they measured clearly faster than the SIMT kernel (P >= 29, on
@@ -1996,16 +2008,21 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     const XLists xl{li->xoff, li->xidx, li->xtgt};
     int gsx = 1;  // lane group of the M2P kernel: the largest leaf, up to a warp
     while (gsx < std::min<int64_t>(maxleaf, 32)) gsx <<= 1;
-    StageScope leaf_scope(FMM_STAGE_LEAF, s);  // P2L, L2P, M2P and the near field
-    if (swp) {
+    if ((rc = wait_lists())) return rc;
+    // P2L into the leaves' local expansions (role exchange) before they are evaluated
+    auto p2l = [&]() -> int {
+        if (!swp) return 0;
         const size_t sm = (size_t)WPB * 33 * P * sizeof(cx<T>);
         FMM_CUDA(cudaFuncSetAttribute(k_p2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_p2l<T><<<t->s_p2m.blocks, 32 * WPB, sm, s>>>(t->s_p2m.d, I, LI, P, PS, t->leaf_begin, pk, geo, xl, Le,
                                                        t->Lf0lo);
         note_launch();
         FMM_LAUNCH_CHECK("evaluate: P2L");
-    }
+        return 0;
+    };
     if (field) {
+        StageScope leaf_scope(FMM_STAGE_LEAF, s);  // P2L, L2P, M2P and the near field
+        if ((rc = p2l())) return rc;
         const unsigned gp2p = (unsigned)t->s_p2p.blocks;
         const Sched sp2p = t->s_p2p.d;
         if constexpr (sizeof(T) == 4) {
@@ -2045,8 +2062,56 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             note_launch();
         }
         FMM_LAUNCH_CHECK("evaluate: field");
-    } else {
-        if (!f64) FMM_CUDA(cudaMemsetAsync(nhi, 0, 2 * 4 * (size_t)n, s));
+        return 0;
+    }
+    // potentials.  The near field needs only the packed points and the strong lists, so with sync
+    // (binary32 path) it runs on the lists' stream while this one finishes the far field; its
+    // accumulators (nhi, nlo) are not touched by the far-field kernels.  The binary64 near field
+    // adds into the same accumulator as L2P and stays on this stream, before L2P.
+    const bool overlap = sync != nullptr && !f64;
+    cudaStream_t ns = overlap ? sync->side : s;
+    if (overlap) FMM_CUDA(cudaStreamWaitEvent(ns, sync->gathered, 0));
+    {
+        StageScope near_scope(FMM_STAGE_NEAR, ns);
+        if (f64) FMM_CUDA(cudaMemsetAsync(t->acc, 0, 8 * (size_t)n, ns));
+        else FMM_CUDA(cudaMemsetAsync(nhi, 0, 2 * 4 * (size_t)n, ns));
+        const unsigned gp2p = (unsigned)t->s_p2p.blocks;
+        const Sched sp2p = t->s_p2p.d;
+        // instances whose leaves hold at most SMALL_LEAF points take the leaf-pair kernel, the
+        // others (if any) the general one; each kernel skips the instances of the other
+        const int small_leaf = f64 ? 32 : 64;
+        if (minleaf <= small_leaf) {
+            if constexpr (sizeof(T) == 4) {
+                k_p2p_f32<<<gp2p, 256, 0, ns>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk,
+                                                t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
+            } else {
+                int gs = 1;
+                while (gs < std::min<int64_t>(maxleaf, 32)) gs <<= 1;
+                k_p2p_small<T><<<gp2p, 256, 0, ns>>>(sp2p, I, LI, gs, li->soff, li->sidx, li->stgt,
+                                                     t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
+                                                     t->cen_lo, t->rad32, t->acc, nhi, nlo);
+            }
+            note_launch();
+        }
+        if (maxleaf > small_leaf) {
+            rc = p2p_items_ws(li);
+            if (rc) return rc;
+            unsigned long long* total = (unsigned long long*)(li->p2p_zero + 2);
+            FMM_CUDA(cudaMemsetAsync(total, 0, 8, ns));
+            k_p2p_items<<<gp2p, 256, 0, ns>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt, t->leaf_begin,
+                                              li->p2p_items, total); note_launch();
+            rc = scan_with_base(li->p2p_items, li->scap, li->p2p_zero, li->p2p_pos, li->p2p_tmp, ns);
+            if (rc) return rc;
+            k_p2p_large<T><<<gp2p, 256, 0, ns>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt,
+                                                 t->leaf_begin, li->p2p_pos, total, t->status, pk, t->xs, t->ys,
+                                                 t->cen_hi, t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
+        }
+        FMM_LAUNCH_CHECK("evaluate: near field");
+    }
+    if (overlap) FMM_CUDA(cudaEventRecord(sync->near_done, ns));
+    {
+        StageScope leaf_scope(FMM_STAGE_LEAF, s);  // P2L, L2P, M2P, far and near joined
+        if ((rc = p2l())) return rc;
         k_l2p<T><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo,
                                       f64 ? (T*)t->acc : (T*)far32, farlo);
         note_launch();
@@ -2056,37 +2121,7 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
                                                                      farlo, nullptr, nullptr);
             note_launch();
         }
-        const unsigned gp2p = (unsigned)t->s_p2p.blocks;
-        const Sched sp2p = t->s_p2p.d;
-        // instances whose leaves hold at most SMALL_LEAF points take the leaf-pair kernel, the
-        // others (if any) the general one; each kernel skips the instances of the other
-        const int small_leaf = f64 ? 32 : 64;
-        if (minleaf <= small_leaf) {
-            if constexpr (sizeof(T) == 4) {
-                k_p2p_f32<<<gp2p, 256, 0, s>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk,
-                                               t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
-            } else {
-                int gs = 1;
-                while (gs < std::min<int64_t>(maxleaf, 32)) gs <<= 1;
-                k_p2p_small<T><<<gp2p, 256, 0, s>>>(sp2p, I, LI, gs, li->soff, li->sidx, li->stgt,
-                                                    t->leaf_begin, pk, t->xs, t->ys, t->cen_hi,
-                                                    t->cen_lo, t->rad32, t->acc, nhi, nlo);
-            }
-            note_launch();
-        }
-        if (maxleaf > small_leaf) {
-            rc = p2p_items_ws(li);
-            if (rc) return rc;
-            unsigned long long* total = (unsigned long long*)(li->p2p_zero + 2);
-            FMM_CUDA(cudaMemsetAsync(total, 0, 8, s));
-            k_p2p_items<<<gp2p, 256, 0, s>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt, t->leaf_begin,
-                                             li->p2p_items, total); note_launch();
-            rc = scan_with_base(li->p2p_items, li->scap, li->p2p_zero, li->p2p_pos, li->p2p_tmp, s);
-            if (rc) return rc;
-            k_p2p_large<T><<<gp2p, 256, 0, s>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt,
-                                                t->leaf_begin, li->p2p_pos, total, t->status, pk, t->xs, t->ys,
-                                                t->cen_hi, t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
-        }
+        if (overlap) FMM_CUDA(cudaStreamWaitEvent(s, sync->near_done, 0));
         if (f64)
             k_unpermute<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->acc, phi);
         else
@@ -2100,7 +2135,7 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
 }  // namespace
 
 int evaluate(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, double* phi,
-             cudaStream_t s)
+             cudaStream_t s, const StepSync* sync)
 {
     int rc = ensure_tables();
     if (rc) return rc;
@@ -2108,8 +2143,8 @@ int evaluate(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     // binary32 expansions carry a rounding error of about 1e-7 relative to the potential: a
     // tighter requested tolerance takes the binary64 path
     const bool f64 = prm.mode == FMM_MODE_FP64 || (prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR);
-    if (f64) return run<double>(t, li, q, P, phi, s);
-    return run<float>(t, li, q, P, phi, s);
+    if (f64) return run<double>(t, li, q, P, phi, s, nullptr, sync);
+    return run<float>(t, li, q, P, phi, s, nullptr, sync);
 }
 
 // Launch-shape tuner: times complete evaluations (CUDA events on the caller's stream, best of

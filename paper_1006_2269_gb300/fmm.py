@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
             "fmm_lists_create": (i32, [vp, i64, i64, ctypes.POINTER(vp)]),
             "fmm_interaction_lists": (i32, [vp, vp, dbl, vp]),
             "fmm_lists_set_mode": (i32, [vp, i32]),
+            "fmm_step": (i32, [vp, vp, vp, vp, dbl, vp, ctypes.POINTER(fmm_params), vp, vp]),
             "fmm_build_tree_uniform": (i32, [vp, vp, vp, vp, vp]),
             "fmm_lists_export_exchange": (i32, [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]),
             "fmm_lists_sync": (i32, [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
@@ -422,6 +423,17 @@ def fmm_get_m2l_kernel(tree) -> int:
     return rc
 
 
+def fmm_step(tree, lists, x: torch.Tensor, y: torch.Tensor, theta: float, q: torch.Tensor, p: int, mode: int,
+             phi: torch.Tensor, tol: float = 1e-6, stream=None):
+    """Tree, lists and evaluation in one call, the independent parts overlapped on the tree's
+    second stream (capturable into a CUDA graph after a first call)."""
+    n = fmm_tree_info(tree)[0]
+    prm = fmm_params(int(p), int(mode), float(tol))
+    _check(load_library().fmm_step(tree, lists, _dev(x, torch.float64, n, "x"), _dev(y, torch.float64, n, "y"),
+                                   float(theta), _dev(q, torch.float64, n, "q"), ctypes.byref(prm),
+                                   _dev(phi, torch.float64, n, "phi"), _stream(stream)))
+
+
 def fmm_evaluate_field(tree, lists, q: torch.Tensor, p: int, mode: int, fre: torch.Tensor, fim: torch.Tensor,
                        tol: float = 1e-6, stream=None):
     """The complex field F_i = sum_{j != i} -q_j / (z_i - z_j): real part into fre, imaginary
@@ -457,7 +469,7 @@ def fmm_sync_status(tree, lists=None, stream=None):
 
 
 STAGES = ("tree_sort", "tree_split", "tree_finish", "lists", "gather", "p2m", "m2m", "m2l", "l2l",
-          "leaf")
+          "leaf", "near")
 
 
 def fmm_profile_enable(on: bool = True):
