@@ -35,7 +35,10 @@ constexpr int PMAXC = 41;  // p <= 40
 
 __constant__ double c_md[PMAXC][PMAXC];     // M'[l][k] in binary64
 __constant__ float c_mf[PMAXC][PMAXC];      // M'[l][k] rounded to binary32
-__constant__ double c_binom[PMAXC][PMAXC];  // C(n, k), n < PMAXC
+// binomials C(n, k), n, k < PMAXC, in global memory: blocks copy them to shared memory (a warp
+// reading many different __constant__ addresses at once would be serialised)
+__device__ float g_binom_f[PMAXC * PMAXC];
+__device__ double g_binom_d[PMAXC * PMAXC];
 
 namespace {
 
@@ -273,7 +276,10 @@ __global__ void k_p2m(Sched sc, const Inst* __restrict__ I, int P, int PS, const
 template <typename T>
 __device__ __forceinline__ void load_binom(T* B, int P)
 {
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) B[i] = (T)c_binom[i / P][i % P];
+    const T* src;
+    if constexpr (sizeof(T) == 4) src = g_binom_f;
+    else src = g_binom_d;
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) B[i] = src[(i / P) * PMAXC + i % P];
     __syncthreads();
 }
 
@@ -1814,7 +1820,10 @@ int ensure_tables()
             md[l][k] = v;
             mf[l][k] = (float)v;
         }
-    FMM_CUDA(cudaMemcpyToSymbol(c_binom, bn, sizeof(bn)));
+    static float bnf[PMAXC * PMAXC];
+    for (int i = 0; i < PMAXC * PMAXC; i++) bnf[i] = (float)bn[i / PMAXC][i % PMAXC];
+    FMM_CUDA(cudaMemcpyToSymbol(g_binom_f, bnf, sizeof(bnf)));
+    FMM_CUDA(cudaMemcpyToSymbol(g_binom_d, bn, sizeof(bn)));
     FMM_CUDA(cudaMemcpyToSymbol(c_md, md, sizeof(md)));
     FMM_CUDA(cudaMemcpyToSymbol(c_mf, mf, sizeof(mf)));
     g_tab_ready[dev] = true;

@@ -39,6 +39,20 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// Lanes of the warp holding the same 9-bit value d (digits 0..255, 256 for "no item"): one
+// ballot per bit, each lane keeping the lanes that agree with it on that bit.
+__device__ __forceinline__ unsigned match_digit(uint32_t d)
+{
+    unsigned m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; b++) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bal : ~bal;
+    }
+    return m;
+}
+
 // Order-preserving key of a binary64 value (-0 and +0 share the key of +0).
 __device__ __forceinline__ uint64_t order_key(double v)
 {
@@ -164,7 +178,7 @@ __global__ void __launch_bounds__(TPB) k_rs_hist(Sched sc, const Inst* __restric
         int64_t i = base + (int64_t)j * TPB + threadIdx.x;
         bool v = i < S.n;
         uint32_t d = v ? (uint32_t)((keys[i] >> shift) & (BINS - 1)) : 0xffffffffu;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned peers = match_digit(d);
         if (v && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
@@ -262,7 +276,7 @@ __global__ void __launch_bounds__(TPB) k_rs_scatter(Sched sc, const Inst* __rest
         k[j] = valid ? kin[i] : K(0);
         val[j] = valid ? (FIRST ? (int32_t)i : vin[i]) : 0;
         uint32_t d = valid ? (uint32_t)((k[j] >> shift) & (BINS - 1)) : (uint32_t)BINS;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned peers = match_digit(d);
         uint32_t cur = valid ? wcnt[w][d] : 0;
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) wcnt[w][d] = cur + __popc(peers);
