@@ -25,7 +25,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <array>
 #include <mutex>
+#include <utility>
 
 #include "common.cuh"
 
@@ -66,6 +68,63 @@ template <typename T>
 __device__ __forceinline__ cx<T> cfma(cx<T> a, cx<T> b, cx<T> c)
 {
     return {c.re + a.re * b.re - a.im * b.im, c.im + a.re * b.im + a.im * b.re};
+}
+
+// M'[l][k] as compile-time constants for the binary32 M2L kernel, so that every product takes
+// its coefficient as an immediate operand.  The binomials follow Pascal's rule in binary64, the
+// same additions in the same order as the host table (exact below 2^53, identically rounded
+// above), and the scaling by 2^-(l+k) is exact: the values equal c_mf bit for bit.
+template <int N, int K>
+struct PascalD {
+    static constexpr double v = PascalD<N - 1, K - 1>::v + PascalD<N - 1, K>::v;
+};
+template <int N>
+struct PascalD<N, 0> {
+    static constexpr double v = 1.0;
+};
+template <int K>
+struct PascalD<0, K> {
+    static constexpr double v = 0.0;
+};
+template <>
+struct PascalD<0, 0> {
+    static constexpr double v = 1.0;
+};
+
+constexpr double pow2_neg(int n)
+{
+    double r = 1.0;
+    for (int i = 0; i < n; i++) r *= 0.5;
+    return r;
+}
+
+template <int L, int K>
+struct MCoef {
+    static constexpr float v = (float)(PascalD<L + K - 1, K - 1>::v * pow2_neg(L + K));
+};
+template <int L>
+struct MCoef<L, 0> {
+    static constexpr float v = (float)(-1.0 / ((double)L / pow2_neg(L)));
+};
+template <>
+struct MCoef<0, 0> {
+    static constexpr float v = 0.0f;
+};
+
+// All M' coefficients as compiled, for the host to compare with its table.
+template <int... I>
+constexpr std::array<float, sizeof...(I)> mcoef_table(std::integer_sequence<int, I...>)
+{
+    return {MCoef<I / PMAXC, I % PMAXC>::v...};
+}
+
+// Row O of y = M' x with immediate coefficients (products in the order k = 0, 1, ...).
+template <int O, int... K>
+__device__ __forceinline__ cx<float> m2l_row(const cx<float>* x, std::integer_sequence<int, K...>)
+{
+    float yr = 0.f, yi = 0.f;
+    ((yr += MCoef<O, K>::v * x[K].re, yi += MCoef<O, K>::v * x[K].im), ...);
+    return {yr, yi};
 }
 
 template <typename T>
@@ -332,6 +391,25 @@ __global__ void k_m2m(Sched sc, const Inst* __restrict__ I, int l, int P, int PS
 // binary32, PI = compile-time bound on P (runtime P <= PI; coefficients beyond P are zero): the
 // scaled source coefficients and the partial sums live in registers, the constant matrix is read
 // from the constant bank by the unrolled contraction.
+// The rows of b~ += (v^l) (M' x) for one pair, O = 0 .. PI-1 at compile time: b~_0 (with the log
+// term t0) in float-float, the others scaled by vp = (2v)^O.
+template <int PI, int O>
+__device__ __forceinline__ void m2l_rows(const cx<float>* x, cx<float>* acc, float& lo0, cx<float> vp, cx<float> v2,
+                                         float t0)
+{
+    if constexpr (O < PI) {
+        const cx<float> y = m2l_row<O>(x, std::make_integer_sequence<int, PI>{});
+        if constexpr (O == 0) {
+            two_sum(acc[0].re, lo0, t0);
+            two_sum(acc[0].re, lo0, y.re);
+            acc[0].im += y.im;
+        } else {
+            acc[O] = cfma(vp, y, acc[O]);
+        }
+        m2l_rows<PI, O + 1>(x, acc, lo0, cmul(vp, v2), v2, t0);
+    }
+}
+
 template <typename T, int PI>
 __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pairs(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                    int P, int PS, const int32_t* __restrict__ woff,
@@ -403,25 +481,29 @@ __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pai
                 x[k] = v;
                 up = cmul(up, u2);
             }
-            cx<T> vp = {1, 0};
+            if constexpr (sizeof(T) == 4) {
+                m2l_rows<PI, 0>(x, acc, lo0, cx<float>{1.f, 0.f}, v2, a0 * 0.5f * log_d(r2));
+            } else {
+                cx<T> vp = {1, 0};
 #pragma unroll
-            for (int o = 0; o < PI; o++) {
-                cx<T> y = {0, 0};
+                for (int o = 0; o < PI; o++) {
+                    cx<T> y = {0, 0};
 #pragma unroll
-                for (int k = 0; k < PI; k++) {
-                    const T m = mtab<T>(o, k);
-                    const cx<T> xv = x[k];
-                    y.re += m * xv.re;
-                    y.im += m * xv.im;
+                    for (int k = 0; k < PI; k++) {
+                        const T m = mtab<T>(o, k);
+                        const cx<T> xv = x[k];
+                        y.re += m * xv.re;
+                        y.im += m * xv.im;
+                    }
+                    if (o == 0) {
+                        two_sum(acc[0].re, lo0, a0 * (T)0.5 * log_d(r2));
+                        two_sum(acc[0].re, lo0, y.re);
+                        acc[0].im += y.im;
+                    } else {
+                        acc[o] = cfma(vp, y, acc[o]);
+                    }
+                    vp = cmul(vp, v2);
                 }
-                if (o == 0) {
-                    two_sum(acc[0].re, lo0, a0 * (T)0.5 * log_d(r2));
-                    two_sum(acc[0].re, lo0, y.re);
-                    acc[0].im += y.im;
-                } else {
-                    acc[o] = cfma(vp, y, acc[o]);
-                }
-                vp = cmul(vp, v2);
             }
         }
         // warp-segmented reduction of the last partial sums (targets are non-decreasing across
@@ -1824,6 +1906,12 @@ int ensure_tables()
     for (int i = 0; i < PMAXC * PMAXC; i++) bnf[i] = (float)bn[i / PMAXC][i % PMAXC];
     FMM_CUDA(cudaMemcpyToSymbol(g_binom_f, bnf, sizeof(bnf)));
     FMM_CUDA(cudaMemcpyToSymbol(g_binom_d, bn, sizeof(bn)));
+    // the binary32 M2L kernel compiles these coefficients in as immediates: they must agree
+    static constexpr std::array<float, PMAXC * PMAXC> compiled =
+        mcoef_table(std::make_integer_sequence<int, PMAXC * PMAXC>{});
+    for (int i = 0; i < PMAXC * PMAXC; i++)
+        if (compiled[i] != mf[i / PMAXC][i % PMAXC])
+            return fail(FMM_ERR_STATE, "compiled M2L coefficient (%d, %d) differs from the table", i / PMAXC, i % PMAXC);
     FMM_CUDA(cudaMemcpyToSymbol(c_md, md, sizeof(md)));
     FMM_CUDA(cudaMemcpyToSymbol(c_mf, mf, sizeof(mf)));
     g_tab_ready[dev] = true;
@@ -1895,8 +1983,6 @@ int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<double> geo, const
     return 0;
 }
 
-// The whole evaluation: the potential into phi, or (fim != nullptr) the complex field into
-// phi (real part) and fim (imaginary part).
 // Workspace of the general near-field kernel (item counts, their scan), sized by the strong
 // capacity; allocated on first use (synchronous).
 int p2p_items_ws(fmm_lists li)
@@ -1912,6 +1998,8 @@ int p2p_items_ws(fmm_lists li)
     return 0;
 }
 
+// The whole evaluation: the potential into phi, or (fim != nullptr) the complex field into
+// phi (real part) and fim (imaginary part).
 template <typename T>
 int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStream_t s, double* fim = nullptr,
         const StepSync* sync = nullptr)
