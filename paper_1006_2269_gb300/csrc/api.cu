@@ -102,6 +102,11 @@ void free_tree(fmm_tree t)
     sched_free_all(t);
     for (cudaEvent_t e : t->ev)
         if (e) cudaEventDestroy(e);
+    if (t->ev_level) {
+        for (int i = 0; i <= t->Lmax; i++)
+            if (t->ev_level[i]) cudaEventDestroy(t->ev_level[i]);
+        delete[] t->ev_level;
+    }
     if (t->side) cudaStreamDestroy(t->side);
     if (t->own_hinst) delete[] t->hinst;
     delete t;
@@ -523,13 +528,16 @@ int fmm_step(fmm_tree t, fmm_lists l, const double* x, const double* y, double t
     if (!t->side) {
         FMM_CUDA(cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking));
         for (cudaEvent_t& e : t->ev) FMM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        t->ev_level = new (std::nothrow) cudaEvent_t[t->Lmax + 1]();
+        if (!t->ev_level) return fail(FMM_ERR_OOM, "host allocation");
+        for (int i = 0; i <= t->Lmax; i++) FMM_CUDA(cudaEventCreateWithFlags(&t->ev_level[i], cudaEventDisableTiming));
     }
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = tree_build(t, x, y, s);
+    // the lists of each level are built on the second stream as soon as the tree build has the
+    // geometry of that level
+    int rc = tree_build(t, x, y, s, t->ev_level);
     if (rc) return rc;
-    FMM_CUDA(cudaEventRecord(t->ev[0], s));  // tree complete
-    FMM_CUDA(cudaStreamWaitEvent(t->side, t->ev[0], 0));
-    rc = lists_build(t, l, theta, t->side);
+    rc = lists_build(t, l, theta, t->side, t->ev_level);
     if (rc) return rc;
     FMM_CUDA(cudaEventRecord(t->ev[1], t->side));
     const StepSync sync{t->side, t->ev[1], t->ev[2], t->ev[3]};

@@ -259,6 +259,7 @@ struct fmm_tree_s {
     // fmm_step: a second stream and its events, created on first use
     cudaStream_t side = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t* ev_level = nullptr;  // [Lmax + 1]: geometry of a level complete
     int32_t* lb_bal = nullptr;
 };
 
@@ -309,11 +310,14 @@ int tree_alloc(fmm_tree t, int n_inst, const int64_t* n, const int* levels);
 void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls);
 void forest_totals(fmm_tree t);
 int tree_tables_host(int64_t n, int L, int32_t* ones_before, int32_t* node_off, int32_t* leaf_begin);
-int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s);
+// level_ready (may be null): events [Lmax + 1]; event l is recorded once the geometry (centres,
+// radii) of levels 0 .. l is complete, so that the lists of those levels can be built meanwhile.
+int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cudaEvent_t* level_ready = nullptr);
 int tree_build_uniform(fmm_tree t, const double* x, const double* y, const double* root_host, cudaStream_t s);
 
 // lists.cu
-int lists_build(fmm_tree t, fmm_lists l, double theta, cudaStream_t s);
+// level_ready (may be null): wait for event l before building level l (see tree_build).
+int lists_build(fmm_tree t, fmm_lists l, double theta, cudaStream_t s, const cudaEvent_t* level_ready = nullptr);
 int64_t lists_flag_bytes(int64_t scap);
 int64_t lists_tile_words(int64_t scap);
 int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int64_t* strong_capacity);

@@ -539,13 +539,16 @@ int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int
     return 0;
 }
 
-int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s)
+int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s, const cudaEvent_t* level_ready)
 {
     const int L = t->Lmax, ni = t->n_inst;
     StageScope scope(FMM_STAGE_LISTS, s);
     const bool par = (li->mode & FMM_LISTS_PARENTS) != 0, swp = (li->mode & FMM_LISTS_EXCHANGE) != 0;
     const ListOpt opt{li->tiledrop, li->tileswap, li->xoff, li->xidx, li->xtgt};
 #define LARGS t->dinst, li->dlinst, li->woff, li->soff, li->widx, li->wtgt, li->sidx, li->stgt, li->flags, li->tilecnt
+    // with level_ready this stream runs beside the tree build: event 0 also orders these writes
+    // after the earlier work of the tree's stream (which may still read the previous lists)
+    if (level_ready) FMM_CUDA(cudaStreamWaitEvent(s, level_ready[0], 0));
     k_lists_root<<<1, 256, 0, s>>>(LARGS, ni); note_launch();
     // exchange offsets below the finest level stay 0
     if (swp) FMM_CUDA(cudaMemsetAsync(li->xoff, 0, 4 * (size_t)(t->nbox + ni), s));
@@ -554,6 +557,7 @@ int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s)
         // is only known on the device); a forest shares blocks in proportion to 4^l
         const SchedH& sh = t->s_lists[l];
         const unsigned g = ni == 1 ? 152 * 8 : (unsigned)sh.blocks;
+        if (level_ready) FMM_CUDA(cudaStreamWaitEvent(s, level_ready[l], 0));
 #define LEVEL(PAR, SWP)                                                                                   \
     do {                                                                                                  \
         k_lists_flags<PAR, SWP><<<g, LT, 0, s>>>(sh.d, LARGS, opt, l, t->centers, t->radii, t->cen_hi,   \

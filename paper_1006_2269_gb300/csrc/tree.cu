@@ -559,12 +559,10 @@ __global__ void k_leaf_of(Sched sc, const Inst* __restrict__ I, const int32_t* _
 // Centre (rectangle midpoint) and radius (half diagonal) of every box, with the same sequence of
 // correctly rounded binary64 operations as the criterion's reference; plus a float-float copy
 // of the centre and a binary32 radius for the binary32 path.  One thread per box of the forest.
-__global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, double* __restrict__ cen,
-                           double* __restrict__ rad, float* __restrict__ rad32, float* __restrict__ chi,
-                           float* __restrict__ clo)
+__device__ __forceinline__ void geometry_one(int64_t g, const double* __restrict__ rects, double* __restrict__ cen,
+                                             double* __restrict__ rad, float* __restrict__ rad32,
+                                             float* __restrict__ chi, float* __restrict__ clo)
 {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= nbox) return;
     const double* r = rects + 4 * g;
     double w = __dsub_rn(r[1], r[0]), h = __dsub_rn(r[3], r[2]);
     double cx = midpoint(r[0], r[1]), cy = midpoint(r[2], r[3]);
@@ -578,6 +576,37 @@ __global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, doubl
     chi[2 * g + 1] = hy;
     clo[2 * g] = __double2float_rn(__dsub_rn(cx, (double)hx));
     clo[2 * g + 1] = __double2float_rn(__dsub_rn(cy, (double)hy));
+}
+
+__global__ void k_geometry(const double* __restrict__ rects, int64_t nbox, double* __restrict__ cen,
+                           double* __restrict__ rad, float* __restrict__ rad32, float* __restrict__ chi,
+                           float* __restrict__ clo)
+{
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nbox) return;
+    geometry_one(g, rects, cen, rad, rad32, chi, clo);
+}
+
+// The roots of every instance; one block.
+__global__ void k_geometry_roots(const Inst* __restrict__ I, int n_inst, const double* __restrict__ rects,
+                                 double* __restrict__ cen, double* __restrict__ rad, float* __restrict__ rad32,
+                                 float* __restrict__ chi, float* __restrict__ clo)
+{
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) geometry_one(I[i].b0, rects, cen, rad, rad32, chi, clo);
+}
+
+// The same for the boxes of level l of every instance (as soon as their rectangles exist).
+// schedule: boxes of level l - 1 (128 per block), four children each; level 0: one block
+__global__ void k_geometry_level(Sched sc, const Inst* __restrict__ I, int l, const double* __restrict__ rects,
+                                 double* __restrict__ cen, double* __restrict__ rad, float* __restrict__ rad32,
+                                 float* __restrict__ chi, float* __restrict__ clo)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    if (l > S.L) return;
+    const int64_t nb = level_size(l);
+    for (int64_t b = (int64_t)z.rank * blockDim.x + threadIdx.x; b < nb; b += (int64_t)z.nb * blockDim.x)
+        geometry_one(S.b0 + level_base(l) + b, rects, cen, rad, rad32, chi, clo);
 }
 
 // Coordinates in canonical order, and their binary32 offsets from the leaf centre.
@@ -868,7 +897,7 @@ int tree_alloc(fmm_tree t, int n_inst, const int64_t* ns, const int* Ls)
     return sched_all(t);
 }
 
-int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
+int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cudaEvent_t* level_ready)
 {
     const int64_t n = t->n;  // total points of the forest
     const int ni = t->n_inst;
@@ -896,6 +925,11 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
         k_bbox_init<<<1, 256, 0, s>>>(ni, t->bbox_keys); note_launch();
         k_make_keys<<<gp, 256, 0, s>>>(sp, t->dinst, x, y, n, kx, t->bbox_keys, t->status); note_launch();
         k_root_rect<<<1, 256, 0, s>>>(t->dinst, ni, t->bbox_keys, t->rects); note_launch();
+        if (level_ready) {  // the geometry of each level as soon as its rectangles exist
+            k_geometry_roots<<<1, 256, 0, s>>>(t->dinst, ni, t->rects, t->centers, t->radii, t->rad32, t->cen_hi,
+                                               t->cen_lo); note_launch();
+            FMM_CUDA(cudaEventRecord(level_ready[0], s));
+        }
         FMM_LAUNCH_CHECK("tree: keys");
         // x order and y order of all points, ties by input index (two sorts in one launch sequence)
         int cur = radix_sort<uint64_t>(t, kx, vals, 2 * n, 2, 64, s);
@@ -924,6 +958,12 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
             // split coordinates and child rectangles of level l
             k_split_rects<<<t->s_split[l].blocks, 128, 0, s>>>(t->s_split[l].d, t->dinst, l, X, Y, x, y,
                                                                 t->node_off, t->rects); note_launch();
+            if (level_ready) {
+                k_geometry_level<<<t->s_split[l].blocks, 128, 0, s>>>(t->s_split[l].d, t->dinst, l + 1, t->rects,
+                                                                     t->centers, t->radii, t->rad32, t->cen_hi,
+                                                                     t->cen_lo); note_launch();
+                FMM_CUDA(cudaEventRecord(level_ready[l + 1], s));
+            }
             // X: stable partition of each x-half by the y-half bit; records the next x-half bit
             k_part_count<<<gt, TPB, 0, s>>>(st, t->dinst, l, X, hy, t->tilecnt); note_launch();
             k_scan_tiles<<<ni, 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
@@ -949,8 +989,10 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s)
         FMM_CUDA(cudaMemcpyAsync(t->perm, v32 + (c2 ? n : 0), 4 * n, cudaMemcpyDeviceToDevice, s));
 
         const int64_t nb = t->nbox;
-        k_geometry<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(t->rects, nb, t->centers, t->radii,
-                                                                t->rad32, t->cen_hi, t->cen_lo); note_launch();
+        if (!level_ready)
+            k_geometry<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(t->rects, nb, t->centers, t->radii,
+                                                                    t->rad32, t->cen_hi, t->cen_lo);
+        note_launch();
         k_gather_points<<<gp, 256, 0, s>>>(sp, t->dinst, t->perm, leaf_of, x, y, t->centers,
                                            t->xs, t->ys, t->dxf, t->dyf, t->cleaf); note_launch();
         FMM_LAUNCH_CHECK("tree: canonical order");
