@@ -258,8 +258,10 @@ int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
 
 /* One whole step on new coordinates and strengths: fmm_build_tree, fmm_interaction_lists and
  * fmm_evaluate in one call, with the independent parts overlapped on a second stream owned by the
- * tree.  The lists are built there while `stream` packs the points and runs the upward pass, and
- * in the mixed mode the near field runs there while `stream` finishes the far field.  Every
+ * tree.  The lists of each level are built there as soon as the tree build has that level's box
+ * geometry (beside the remaining partitions of the tree, then beside the packing and upward pass
+ * on `stream`), and in the mixed mode the near field runs there while `stream` finishes the far
+ * field.  Every
  * dependency goes through events, so the call may be captured into a CUDA graph on `stream`
  * (the first call creates the stream and its events: make it before capturing).  Same arguments
  * and errors as the three calls. */

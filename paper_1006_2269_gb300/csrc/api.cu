@@ -539,8 +539,8 @@ int fmm_step(fmm_tree t, fmm_lists l, const double* x, const double* y, double t
     if (rc) return rc;
     rc = lists_build(t, l, theta, t->side, t->ev_level);
     if (rc) return rc;
-    FMM_CUDA(cudaEventRecord(t->ev[1], t->side));
-    const StepSync sync{t->side, t->ev[1], t->ev[2], t->ev[3]};
+    FMM_CUDA(cudaEventRecord(t->ev[0], t->side));
+    const StepSync sync{t->side, t->ev[0], t->ev[1], t->ev[2]};
     return evaluate(t, l, q, *prm, phi, s, &sync);
 }
 

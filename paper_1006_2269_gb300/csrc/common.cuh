@@ -258,7 +258,7 @@ struct fmm_tree_s {
     bool uniform = false;
     // fmm_step: a second stream and its events, created on first use
     cudaStream_t side = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // lists done, points packed, near field done
     cudaEvent_t* ev_level = nullptr;  // [Lmax + 1]: geometry of a level complete
     int32_t* lb_bal = nullptr;
 };

@@ -36,7 +36,6 @@ namespace fmm {
 constexpr int PMAXC = 41;  // p <= 40
 
 __constant__ double c_md[PMAXC][PMAXC];     // M'[l][k] in binary64
-__constant__ float c_mf[PMAXC][PMAXC];      // M'[l][k] rounded to binary32
 // binomials C(n, k), n, k < PMAXC, in global memory: blocks copy them to shared memory (a warp
 // reading many different __constant__ addresses at once would be serialised)
 __device__ float g_binom_f[PMAXC * PMAXC];
@@ -73,7 +72,8 @@ __device__ __forceinline__ cx<T> cfma(cx<T> a, cx<T> b, cx<T> c)
 // M'[l][k] as compile-time constants for the binary32 M2L kernel, so that every product takes
 // its coefficient as an immediate operand.  The binomials follow Pascal's rule in binary64, the
 // same additions in the same order as the host table (exact below 2^53, identically rounded
-// above), and the scaling by 2^-(l+k) is exact: the values equal c_mf bit for bit.
+// above), and the scaling by 2^-(l+k) is exact: the values equal the host table rounded to binary32
+// bit for bit (checked when the tables are made).
 template <int N, int K>
 struct PascalD {
     static constexpr double v = PascalD<N - 1, K - 1>::v + PascalD<N - 1, K>::v;
@@ -127,12 +127,6 @@ __device__ __forceinline__ cx<float> m2l_row(const cx<float>* x, std::integer_se
     return {yr, yi};
 }
 
-template <typename T>
-__device__ __forceinline__ T mtab(int l, int k);
-template <>
-__device__ __forceinline__ double mtab<double>(int l, int k) { return c_md[l][k]; }
-template <>
-__device__ __forceinline__ float mtab<float>(int l, int k) { return c_mf[l][k]; }
 
 template <typename T>
 __device__ __forceinline__ T ipow(T x, int e)
@@ -418,6 +412,7 @@ __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pai
                                                    const cx<T>* __restrict__ Me, cx<T>* __restrict__ Le,
                                                    float* __restrict__ L0lo)
 {
+    static_assert(sizeof(T) == 4, "the binary64 M2L is k_m2l_pairs_f64");
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
     const LInst TL = LIs[z.i];
@@ -481,30 +476,7 @@ __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pai
                 x[k] = v;
                 up = cmul(up, u2);
             }
-            if constexpr (sizeof(T) == 4) {
-                m2l_rows<PI, 0>(x, acc, lo0, cx<float>{1.f, 0.f}, v2, a0 * 0.5f * log_d(r2));
-            } else {
-                cx<T> vp = {1, 0};
-#pragma unroll
-                for (int o = 0; o < PI; o++) {
-                    cx<T> y = {0, 0};
-#pragma unroll
-                    for (int k = 0; k < PI; k++) {
-                        const T m = mtab<T>(o, k);
-                        const cx<T> xv = x[k];
-                        y.re += m * xv.re;
-                        y.im += m * xv.im;
-                    }
-                    if (o == 0) {
-                        two_sum(acc[0].re, lo0, a0 * (T)0.5 * log_d(r2));
-                        two_sum(acc[0].re, lo0, y.re);
-                        acc[0].im += y.im;
-                    } else {
-                        acc[o] = cfma(vp, y, acc[o]);
-                    }
-                    vp = cmul(vp, v2);
-                }
-            }
+            m2l_rows<PI, 0>(x, acc, lo0, cx<float>{1.f, 0.f}, v2, a0 * 0.5f * log_d(r2));
         }
         // warp-segmented reduction of the last partial sums (targets are non-decreasing across
         // lanes; lanes without pairs carry -1 and sit at the end)
@@ -1913,7 +1885,6 @@ int ensure_tables()
         if (compiled[i] != mf[i / PMAXC][i % PMAXC])
             return fail(FMM_ERR_STATE, "compiled M2L coefficient (%d, %d) differs from the table", i / PMAXC, i % PMAXC);
     FMM_CUDA(cudaMemcpyToSymbol(c_md, md, sizeof(md)));
-    FMM_CUDA(cudaMemcpyToSymbol(c_mf, mf, sizeof(mf)));
     g_tab_ready[dev] = true;
     return 0;
 }
