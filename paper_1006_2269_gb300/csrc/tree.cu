@@ -360,24 +360,6 @@ __global__ void __launch_bounds__(TPB) k_part_count(Sched sc, const Inst* __rest
     if (threadIdx.x == 0) tilecnt[S.t0 + z.rank] = tot;
 }
 
-// one block per instance
-__global__ void __launch_bounds__(1024) k_scan_tiles(const Inst* __restrict__ I, int l, uint32_t* a)
-{
-    const Inst S = I[blockIdx.x];
-    if (l >= S.L) return;
-    a += S.t0;
-    __shared__ uint32_t wt[32];
-    uint32_t carry = 0;
-    for (int64_t b = 0; b < S.ntiles; b += blockDim.x) {
-        int64_t i = b + threadIdx.x;
-        uint32_t v = i < S.ntiles ? a[i] : 0;
-        uint32_t tot;
-        uint32_t e = block_excl_scan(v, wt, tot);
-        if (i < S.ntiles) a[i] = carry + e;
-        carry += tot;
-    }
-}
-
 // Stable partition inside segments.  Items carry the index of their level-l box (seg, a node at
 // depth 2l of the floor-left split tree whose offsets are tabulated in node_off).
 //   xmode = 0 (the y-ordered list): segments are the boxes themselves, flag = x-half bit; an item
@@ -387,8 +369,8 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const Inst* __restrict__ I,
 //       the position), flag = y-half bit; out_seg receives the level-(l+1) box, flagout the
 //       x-half bit of the next level.
 // Zeros keep their order and come first.  A segment of size m holds m - floor(m/2) ones, ob[j]
-// counts the ones of all segments before segment j at that depth, tileoff[] is the exclusive scan
-// of the ones per tile.  An instance with fewer than l + 1 levels is finished: its items are
+// counts the ones of all segments before segment j at that depth, tilecnt[] the ones of every
+// tile (each block adds up those before its own).  An instance with fewer than l + 1 levels is finished: its items are
 // copied through unchanged so that the next level finds them in the output buffer.
 // tile schedule
 __global__ void __launch_bounds__(TPB) k_part_scatter(Sched sc, const Inst* __restrict__ I, int l, int xmode,
@@ -400,7 +382,7 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(Sched sc, const Inst* __re
                                                       uint8_t* __restrict__ flagout,
                                                       const int32_t* __restrict__ node_off,
                                                       const int32_t* __restrict__ ones_before,
-                                                      const uint32_t* __restrict__ tileoff,
+                                                      const uint32_t* __restrict__ tilecnt,
                                                       int32_t* status)
 {
     const Slot z = slot_of(sc);
@@ -444,8 +426,18 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(Sched sc, const Inst* __re
         run += __popc(bal);
     }
     if (lane == 0) wtot[w] = run;
+    // ones before this tile: the sum of the earlier tiles' counts (no separate scan launch)
+    __shared__ uint32_t wpart[WARPS];
+    {
+        uint32_t part = 0;
+        for (int32_t k = threadIdx.x; k < tile; k += TPB) part += tilecnt[S.t0 + k];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) wpart[w] = part;
+    }
     __syncthreads();
-    uint32_t woff = tileoff[S.t0 + tile];
+    uint32_t woff = 0;
+    for (int ww = 0; ww < WARPS; ww++) woff += wpart[ww];
     for (int ww = 0; ww < w; ww++) woff += wtot[ww];
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
@@ -950,7 +942,6 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cud
         for (int l = 0; l < L; l++) {
             // Y: stable partition of each box by its x-half bit; records the y-half bit
             k_part_count<<<gt, TPB, 0, s>>>(st, t->dinst, l, Y, hx, t->tilecnt); note_launch();
-            k_scan_tiles<<<ni, 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
             k_part_scatter<<<gt, TPB, 0, s>>>(st, t->dinst, l, 0, Y, YS, Yo, YSo, hx, hy, t->node_off,
                                               t->ones_before, t->tilecnt, t->status); note_launch();
             std::swap(Y, Yo);
@@ -966,7 +957,6 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cud
             }
             // X: stable partition of each x-half by the y-half bit; records the next x-half bit
             k_part_count<<<gt, TPB, 0, s>>>(st, t->dinst, l, X, hy, t->tilecnt); note_launch();
-            k_scan_tiles<<<ni, 1024, 0, s>>>(t->dinst, l, t->tilecnt); note_launch();
             k_part_scatter<<<gt, TPB, 0, s>>>(st, t->dinst, l, 1, X, XS, Xo, XSo, hy, hx, t->node_off,
                                               t->ones_before, t->tilecnt, t->status); note_launch();
             std::swap(X, Xo);
