@@ -139,7 +139,23 @@ __global__ void k_make_keys(Sched sc, const Inst* __restrict__ I, const double* 
         mny = min(mny, __shfl_xor_sync(0xffffffffu, mny, o));
         mxy = max(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
     }
+    // then across the block, so that only one thread per block touches the four shared words
+    __shared__ uint64_t red[4][32];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+        red[0][w] = mnx;
+        red[1][w] = mxx;
+        red[2][w] = mny;
+        red[3][w] = mxy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; k++) {
+            mnx = min(mnx, red[0][k]);
+            mxx = max(mxx, red[1][k]);
+            mny = min(mny, red[2][k]);
+            mxy = max(mxy, red[3][k]);
+        }
         atomicMin((unsigned long long*)&bbox[0], (unsigned long long)mnx);
         atomicMax((unsigned long long*)&bbox[1], (unsigned long long)mxx);
         atomicMin((unsigned long long*)&bbox[2], (unsigned long long)mny);
