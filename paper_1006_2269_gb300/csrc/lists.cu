@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, ListOpt
     for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint32_t cnt = 0, drop = 0, swp = 0;
+#pragma unroll 4
         for (int j = 0; j < LI; j++) {
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             int64_t b = 0, c = 0;
@@ -424,7 +425,26 @@ __global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, ListOpt 
             }
         }
         __syncthreads();
-        // exclusive prefix in (row j, warp) order = candidate order inside the tile
+        // exclusive prefix in (row j, warp) order = candidate order inside the tile: warp 0 scans
+        // the LI x (LT / 32) = 64 counts of each counter (two per lane) in place
+        static_assert(LI * (LT / 32) == 64, "the prefix scan takes two counts per lane");
+        if (w == 0) {
+#pragma unroll
+            for (int k = 0; k < NC; k++) {
+                uint32_t* a = &csum[k][0][0];
+                const uint32_t c0v = a[2 * lane], c1v = a[2 * lane + 1];
+                uint32_t x = c0v + c1v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const uint32_t ex = x - (c0v + c1v);
+                a[2 * lane] = ex;
+                a[2 * lane + 1] = ex + c0v;
+            }
+        }
+        __syncthreads();
         uint32_t run[NC];
         run[0] = v.tilecnt[tile];
         if (PAR) run[1] = opt.tiledrop[c0 + tile];
@@ -433,13 +453,7 @@ __global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, ListOpt 
         for (int j = 0; j < LI; j++) {
             uint32_t before[NC];
 #pragma unroll
-            for (int k = 0; k < NC; k++) {
-                before[k] = 0;
-                for (int ww = 0; ww < LT / 32; ww++) {
-                    if (ww == w) before[k] = run[k];
-                    run[k] += csum[k][j][ww];
-                }
-            }
+            for (int k = 0; k < NC; k++) before[k] = run[k] + csum[k][j][w];
             const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
             if (t < nc) {
                 int64_t b, c;
