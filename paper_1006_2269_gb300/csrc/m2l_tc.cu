@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(TC_ROWS, (KC <= 24 ? 4 : 3)) k_m2l_tc(Sched sc
             }
         }
         // ---- segments of equal target (targets are non-decreasing along the rows) ----
-        const bool head = valid && (t == 0 || tgt_s[t - 1] != (int)g);
+        // a segment also starts at every 32nd row, so that no reduction chain is longer than 32
+        const bool head = valid && (t == 0 || tgt_s[t - 1] != (int)g || (t & 31) == 0);
         const unsigned bal = __ballot_sync(0xffffffffu, head);
         if (lane == 0) wcnt[w] = __popc(bal);
         asm volatile("tcgen05.fence::before_thread_sync;");
