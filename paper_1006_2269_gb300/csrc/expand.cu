@@ -20,8 +20,9 @@
 // few entries to thousands per box, so M2L and the near field run over the flat pair arrays of
 // the lists: every warp takes a fixed chunk of consecutive pairs (sorted by target), each lane a
 // contiguous sub-chunk; partial sums of equal targets are combined by a warp-segmented reduction
-// and added to the target with atomics.  The near-field sums of the binary32 path are flushed in
-// binary64, which keeps the accumulation error at the level of a few hundred binary32 terms.
+// and added to the target with atomics.  The near-field sums of the binary32 path are kept and
+// flushed as float-float pairs, which keeps the accumulation error at the level of a few hundred
+// binary32 terms.
 #include <math.h>
 
 #include <algorithm>
@@ -143,7 +144,7 @@ __device__ __forceinline__ T ipow(T x, int e)
 
 // Box geometry in the working precision.  z0 = c_a - c_b: in binary64 directly, in binary32 from
 // the float-float centres so that the difference of two nearby centres keeps its relative
-// accuracy.  The binary32 path never touches binary64 arithmetic (slow on this GPU): radii come
+// accuracy.  The binary32 path never touches binary64 arithmetic (slow on GB300): radii come
 // from a binary32 copy and point coordinates are binary32 offsets from their leaf centre.
 template <typename T>
 struct Geo;
@@ -662,9 +663,6 @@ __global__ void k_l2l(Sched sc, const Inst* __restrict__ I, int l, int P, int PS
     }
 }
 
-// ---- L2P: one thread per point (canonical order); initialises the accumulator ----
-// binary64 path: writes the binary64 accumulator.  binary32 path: writes the binary32 far field;
-// the near-field accumulators are combined with it at the end.
 // ---- role exchange at the finest level (Section 4) ----
 // Exchange-list entries of leaf g: xoff / xidx already offset to the instance.
 struct XLists {
@@ -931,6 +929,10 @@ __global__ void __launch_bounds__(256) k_m2p(Sched sc, const Inst* __restrict__ 
     }
 }
 
+// ---- L2P: one thread per point (canonical order) ----
+// binary64 path: adds to the binary64 accumulator, which already holds the near field.  binary32
+// path: writes the binary32 far field (float-float); the near-field accumulators are combined
+// with it at the end.
 template <typename T>
 __global__ void k_l2p(Sched sc, const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ cleaf,
                       const Pk<T>* __restrict__ pk, Geo<T> geo, const cx<T>* __restrict__ Le,
