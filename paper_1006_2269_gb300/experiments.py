@@ -73,8 +73,8 @@ def field_errors(n: int, dev, ps=range(2, 31, 2), levels: int | None = None, sam
 
 
 def timing(dev, ns=(200_000, 1_000_000, 5_000_000), p: int = 20, theta: float = 0.5, reps: int = 5):
-    """Milliseconds per complete evaluation (tree, lists, potentials; mixed and binary64 paths)
-    for the distributions of the paper's robustness experiments."""
+    """Milliseconds per complete step (tree, lists, potentials: fmm_step; mixed and binary64
+    paths) for the distributions of the paper's robustness experiments."""
     kinds = {
         "uniform": lambda n, s: W.uniform(n, s),
         "normal sigma 0.1": lambda n, s: W.normal_sq(n, s, 0.1),
@@ -91,10 +91,8 @@ def timing(dev, ns=(200_000, 1_000_000, 5_000_000), p: int = 20, theta: float = 
             try:
                 row = {"distribution": name, "n": n, "levels": L}
                 for mode in (fmm.FMM_MODE_MIXED, fmm.FMM_MODE_FP64):
-                    def step():
-                        fmm.fmm_build_tree(f.tree, x, y)
-                        fmm.fmm_interaction_lists(f.tree, f.lists, theta)
-                        fmm.fmm_evaluate(f.tree, f.lists, q, p, mode, phi)
+                    def step():  # tree, lists and evaluation (two streams, plain launches)
+                        fmm.fmm_step(f.tree, f.lists, x, y, theta, q, p, mode, phi)
                     step()
                     torch.cuda.synchronize()
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
