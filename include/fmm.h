@@ -241,6 +241,23 @@ int fmm_lists_export(fmm_lists l, int32_t* woff, int32_t* widx, int32_t* soff, i
 int fmm_lists_export_instance(fmm_lists l, int i, int32_t* woff, int32_t* widx, int32_t* soff,
                               int32_t* sidx, void* stream);
 
+/* Lists of instance i from device arrays in the layout fmm_lists_export_instance writes (offsets
+ * over the instance's boxes, within-level entries; weak entries may carry FMM_PARENT_FLAG): for
+ * resuming from saved lists without rebuilding them.  Synchronises `stream` (reads the counts);
+ * FMM_ERR_CAPACITY if they exceed the instance's capacities, FMM_ERR_STATE for lists with
+ * exchange lists (FMM_LISTS_EXCHANGE).  Imported lists are not checked: call fmm_validate
+ * before evaluating them. */
+int fmm_lists_import(fmm_lists l, int i, const int32_t* woff, const int32_t* widx, const int32_t* soff,
+                     const int32_t* sidx, void* stream);
+
+/* Structural checks of a built tree and (if l is not NULL) its lists: leaf offsets from 0 to n,
+ * the canonical order a permutation, every point inside its leaf's offsets, finite rectangles
+ * and radii, list offsets non-decreasing within the capacities, every entry listed under its
+ * target and within its level (parent entries within the level above, exchange entries within
+ * the leaves).  Every read is in range, so corrupted structures are reported, not read out of
+ * bounds.  Synchronises `stream`; FMM_OK, or FMM_ERR_STATE naming the first failing check. */
+int fmm_validate(fmm_tree t, fmm_lists l, void* stream);
+
 void fmm_lists_destroy(fmm_lists l);
 
 /* ---------------------------------------------------------------------------------------------

@@ -496,6 +496,31 @@ int fmm_lists_export(fmm_lists l, int32_t* woff, int32_t* widx, int32_t* soff, i
     return fmm_lists_export_instance(l, 0, woff, widx, soff, sidx, stream);
 }
 
+int fmm_lists_import(fmm_lists l, int i, const int32_t* woff, const int32_t* widx, const int32_t* soff,
+                     const int32_t* sidx, void* stream)
+{
+    if (!l || !woff || !soff) return fail(FMM_ERR_ARG, "NULL argument");
+    fmm_tree t = l->tree;
+    if (i < 0 || i >= t->n_inst) return fail(FMM_ERR_ARG, "instance %d outside [0, %d)", i, t->n_inst);
+    if (!t->built) return fail(FMM_ERR_STATE, "tree not built");
+    if (l->mode & FMM_LISTS_EXCHANGE) return fail(FMM_ERR_STATE, "lists with exchange lists cannot be imported");
+    GUARD(t->dev);
+    const int rc = lists_import(l, i, woff, widx, soff, sidx, (cudaStream_t)stream);
+    if (rc) return rc;
+    l->built = true;
+    return FMM_OK;
+}
+
+int fmm_validate(fmm_tree t, fmm_lists l, void* stream)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (!t->built) return fail(FMM_ERR_STATE, "tree not built");
+    if (l && l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
+    if (l && !l->built) return fail(FMM_ERR_STATE, "lists not built");
+    GUARD(t->dev);
+    return validate(t, l, (cudaStream_t)stream);
+}
+
 void fmm_lists_destroy(fmm_lists l)
 {
     if (!l) return;

@@ -323,6 +323,11 @@ int64_t lists_tile_words(int64_t scap);
 int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int64_t* strong_capacity);
 
 // expand.cu
+// Structural checks (fmm_validate) and list import (fmm_lists_import).
+int validate(fmm_tree t, fmm_lists l, cudaStream_t s);
+int lists_import(fmm_lists l, int i, const int32_t* woff, const int32_t* widx, const int32_t* soff,
+                 const int32_t* sidx, cudaStream_t s);
+
 // Two-stream step (fmm_step): the lists are built on `side` (lists_done when complete); the
 // evaluation records `gathered` once the points are packed, and its binary32 near field runs on
 // `side`, recording `near_done`.

@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH):
             "fmm_lists_create": (i32, [vp, i64, i64, ctypes.POINTER(vp)]),
             "fmm_interaction_lists": (i32, [vp, vp, dbl, vp]),
             "fmm_lists_set_mode": (i32, [vp, i32]),
+            "fmm_lists_import": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+            "fmm_validate": (i32, [vp, vp, vp]),
             "fmm_step": (i32, [vp, vp, vp, vp, dbl, vp, ctypes.POINTER(fmm_params), vp, vp]),
             "fmm_build_tree_uniform": (i32, [vp, vp, vp, vp, vp]),
             "fmm_lists_export_exchange": (i32, [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]),
@@ -302,6 +304,18 @@ def fmm_lists_sync(lists, stream=None):
     w, s = ctypes.c_int64(), ctypes.c_int64()
     _check(load_library().fmm_lists_sync(lists, _stream(stream), ctypes.byref(w), ctypes.byref(s)))
     return w.value, s.value
+
+
+def fmm_lists_import(lists, i: int, woff, widx, soff, sidx, stream=None):
+    """Instance i's lists from device int32 arrays in the export layout (then fmm_validate)."""
+    _check(load_library().fmm_lists_import(lists, int(i), _dev(woff, torch.int32, None, "woff"),
+                                           _dev(widx, torch.int32, None, "widx"), _dev(soff, torch.int32, None, "soff"),
+                                           _dev(sidx, torch.int32, None, "sidx"), _stream(stream)))
+
+
+def fmm_validate(tree, lists=None, stream=None):
+    """Structural checks of a built tree and its lists; raises FMMError naming a failed check."""
+    _check(load_library().fmm_validate(tree, lists, _stream(stream)))
 
 
 def fmm_lists_export(lists, woff, widx, soff, sidx, stream=None):
