@@ -258,6 +258,12 @@ int fmm_lists_import(fmm_lists l, int i, const int32_t* woff, const int32_t* wid
  * bounds.  Synchronises `stream`; FMM_OK, or FMM_ERR_STATE naming the first failing check. */
 int fmm_validate(fmm_tree t, fmm_lists l, void* stream);
 
+/* Failure-path self-test of the device's bounded waits (no paper counterpart): one warp runs
+ * the wait the tensor-core M2L uses on an mbarrier that nothing completes; after `tries` tries
+ * (1 .. 2^20) it gives up, records FMM_ERR_TIMEOUT in its status word and returns, leaving the
+ * context usable.  Synchronises `stream`; returns FMM_ERR_TIMEOUT (the expected outcome). */
+int fmm_selftest_bounded_wait(int64_t tries, void* stream);
+
 void fmm_lists_destroy(fmm_lists l);
 
 /* ---------------------------------------------------------------------------------------------

@@ -521,6 +521,12 @@ int fmm_validate(fmm_tree t, fmm_lists l, void* stream)
     return validate(t, l, (cudaStream_t)stream);
 }
 
+int fmm_selftest_bounded_wait(int64_t tries, void* stream)
+{
+    if (tries < 1 || tries > (int64_t(1) << 20)) return fail(FMM_ERR_ARG, "tries = %lld outside [1, 2^20]", (long long)tries);
+    return bounded_wait_selftest(tries, (cudaStream_t)stream);
+}
+
 void fmm_lists_destroy(fmm_lists l)
 {
     if (!l) return;

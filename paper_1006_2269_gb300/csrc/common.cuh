@@ -349,6 +349,7 @@ int autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, do
 // m2l_tc.cu: binary32 M2L on the tensor cores (Me, Le: [nbox][PS] float2)
 bool m2l_tc_supported(int P);
 int m2l_tc(fmm_tree t, fmm_lists l, int P, int PS, const void* Me, void* Le, cudaStream_t s);
+int bounded_wait_selftest(int64_t limit, cudaStream_t s);
 
 // scan.cu: exclusive scan of int32 counts with a base value read from device memory:
 // out[i] = base[0] + sum_{j < i} in[j] for i = 0..m (out has m + 1 entries; out may alias

@@ -38,7 +38,7 @@ constexpr int TC_ROWS = 128;  // weak pairs per tile = MMA M = threads per CTA
 constexpr int TC_N = 32;      // output coefficients l (MMA N), P <= 32
 constexpr int CORE = 128;     // bytes of one core matrix: 8 rows x 16 bytes
 constexpr int TMEM_COLS = 64; // two 32-column binary32 accumulators
-constexpr int64_t WAIT_LIMIT = int64_t(1) << 26;
+constexpr int64_t WAIT_LIMIT = int64_t(1) << 20;  // tries of a bounded wait (each may suspend briefly)
 
 __constant__ float c_tc[2][TC_N][32];  // M' as tf32 high and low parts, zero-padded
 
@@ -421,6 +421,35 @@ __global__ void __launch_bounds__(TC_ROWS, (KC <= 24 ? 4 : 3)) k_m2l_tc(Sched sc
     if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// The bounded wait above on an mbarrier that nothing completes (it expects one arrival that
+// never comes): the wait gives up after `limit` tries, records the timeout and the kernel
+// returns.  One warp, no tensor memory, no MMA: it exercises only the give-up path.
+__global__ void k_wait_selftest(int64_t limit, int32_t* status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        bool ok = false;
+        for (int64_t i = 0; i < limit && !ok; i++) {
+            uint32_t r;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}\n"
+                : "=r"(r)
+                : "r"(b), "r"(0u)
+                : "memory");
+            ok = r != 0;
+        }
+        if (!ok) atomicOr(status, ST_TIMEOUT);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(b));
+    }
+}
+
 std::mutex g_tc_mutex;
 bool g_tc_ready[128] = {};
 
@@ -478,6 +507,27 @@ int launch(fmm_tree t, fmm_lists li, int P, int PS, const void* Me, void* Le, cu
 }  // namespace
 
 bool m2l_tc_supported(int P) { return P <= 32; }
+
+int bounded_wait_selftest(int64_t limit, cudaStream_t s)
+{
+    int32_t* st = nullptr;
+    if (cudaMalloc((void**)&st, 4) != cudaSuccess) return fail(FMM_ERR_OOM, "status word");
+    int rc = FMM_OK;
+    int32_t h = 0;
+    if (cudaMemsetAsync(st, 0, 4, s) != cudaSuccess) rc = fail(FMM_ERR_CUDA, "memset");
+    if (!rc) {
+        k_wait_selftest<<<1, 32, 0, s>>>(limit, st);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess ||
+            cudaMemcpy(&h, st, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = fail(FMM_ERR_CUDA, "bounded-wait self-test");
+    }
+    cudaFree(st);
+    if (rc) return rc;
+    return (h & ST_TIMEOUT) ? fail(FMM_ERR_TIMEOUT, "the bounded wait gave up after %lld tries, as it should",
+                                   (long long)limit)
+                            : FMM_OK;
+}
 
 // Binary32 M2L over all weak pairs with the tensor cores; Me, Le: [nbox][PS] float2.
 int m2l_tc(fmm_tree t, fmm_lists li, int P, int PS, const void* Me, void* Le, cudaStream_t s)

@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
             "fmm_lists_set_mode": (i32, [vp, i32]),
             "fmm_lists_import": (i32, [vp, i32, vp, vp, vp, vp, vp]),
             "fmm_validate": (i32, [vp, vp, vp]),
+            "fmm_selftest_bounded_wait": (i32, [i64, vp]),
             "fmm_step": (i32, [vp, vp, vp, vp, dbl, vp, ctypes.POINTER(fmm_params), vp, vp]),
             "fmm_build_tree_uniform": (i32, [vp, vp, vp, vp, vp]),
             "fmm_lists_export_exchange": (i32, [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]),
@@ -311,6 +312,12 @@ def fmm_lists_import(lists, i: int, woff, widx, soff, sidx, stream=None):
     _check(load_library().fmm_lists_import(lists, int(i), _dev(woff, torch.int32, None, "woff"),
                                            _dev(widx, torch.int32, None, "widx"), _dev(soff, torch.int32, None, "soff"),
                                            _dev(sidx, torch.int32, None, "sidx"), _stream(stream)))
+
+
+def fmm_selftest_bounded_wait(tries: int = 4096, stream=None):
+    """The bounded device wait on an mbarrier nothing completes: raises FMMError(FMM_ERR_TIMEOUT)
+    when it gives up, as designed."""
+    _check(load_library().fmm_selftest_bounded_wait(int(tries), _stream(stream)))
 
 
 def fmm_validate(tree, lists=None, stream=None):

@@ -111,3 +111,19 @@ def test_import_corruption_is_reported(fmmlib, cuda, built, what, message):
         assert ei.value.code == fmmlib.FMM_ERR_STATE and message in str(ei.value)
     finally:
         fmmlib.fmm_lists_destroy(l)
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(fmmlib, orc, cuda):
+    # the tensor-core M2L's bounded wait, on an mbarrier that nothing completes
+    with pytest.raises(fmmlib.FMMError) as ei:
+        fmmlib.fmm_selftest_bounded_wait(4096)
+    assert ei.value.code == fmmlib.FMM_ERR_TIMEOUT
+    # and the device goes on evaluating normally
+    c = W.uniform(5000, 97)
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), 3, 0.5)
+    try:
+        got = f.evaluate(_t(c.q, cuda), 16, "fp64").cpu().numpy()
+        ref = orc.fmm(c.x, c.y, c.q, 3, 16, 0.5)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    finally:
+        f.close()
