@@ -114,10 +114,10 @@ class ClockSampler:
 # ---- the reference arm: the FP64 CPU oracle as it stands ----------------------------------------
 
 def run_reference(args, rank):
-    import oracle
-    from paper_1006_2269_gb300 import workloads as W
     if rank != 0:
         return None
+    import oracle
+    from paper_1006_2269_gb300 import workloads as W
     oracle.build()
     w = W.MIXED_1M
     ns, Ls = 1 << 16, 6  # bounded sample of the workload: same distribution, 16 points per leaf
@@ -140,6 +140,24 @@ def run_reference(args, rank):
                          "sample": f"oracle FMM on N={ns} points of the same distribution, L={Ls}, p={w.p}"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+# ---- replicas: one per GPU, the slowest rank's time, whole-job throughput ---------------------------
+
+def max_over_ranks(ms: float, world: int, device="cpu") -> float:
+    """The slowest rank's time: every rank takes part (world 1: the value itself)."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_replica: int, ms_total: float, steps: int) -> float:
+    """Units of all replicas per second, each step of every replica within the slowest's time."""
+    return world * units_per_replica / (ms_total / steps * 1e-3)
 
 
 # ---- our arm -----------------------------------------------------------------------------------
@@ -432,10 +450,7 @@ def main():
         if world > 1:
             dist.barrier()
         ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-        t = torch.tensor([ms], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item(), launches, prof
+        return max_over_ranks(ms, world, dev), launches, prof
 
     use(fmm.FMM_MODE_MIXED)
     l0 = fmm.fmm_launch_count()
@@ -450,7 +465,7 @@ def main():
 
     K = args.steps
     per_step = ms_mixed_plain / K
-    value = world * n / (per_step * 1e-3)
+    value = job_throughput(world, n, ms_mixed_plain, K)
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]}
     stage_ms64 = {k: v[0] / max(v[1], 1) for k, v in prof64.items() if v[1]}
     top = max(stage_ms, key=stage_ms.get)
@@ -506,11 +521,11 @@ def main():
                    "lists": lists_kind + ("" if lists_kind == "plain" else " (Section 4's optional optimisations)"),
                    "lists_trial_ms_per_step": lists_ms or None},
         "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,
-        "fp64_path": {"value": world * n / (ms_fp64 / args.fp64_steps * 1e-3),
+        "fp64_path": {"value": job_throughput(world, n, ms_fp64, args.fp64_steps),
                       "ms_per_step": ms_fp64 / args.fp64_steps, "stages_ms": stage_ms64},
         "speedup_vs_fp64": (ms_fp64 / args.fp64_steps) / per_step,
         "stages_ms": stage_ms, "weak_pairs": nweak, "near_pair_evals": npairs,
-        "e2e": {"value": world * n / (ms_e2e / K * 1e-3), "unit": UNIT,
+        "e2e": {"value": job_throughput(world, n, ms_e2e, K), "unit": UNIT,
                 "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
         "roofline": roof,
