@@ -127,7 +127,13 @@ struct Inst {
     int64_t lb0;          // leaf offsets: 4^L + 1 entries
     int32_t L;
     int32_t maxleaf;      // points of the largest leaf (ceil(n / 4^L) on the median tree)
+    int32_t lg;           // median tree: levels l < lg split by the global partition passes, the
+                          // rest inside one block per box of level lg (lg == L: none)
 };
+
+// A box of at most TREE_LOCAL_CAP points finishes its median subtree inside one block.
+constexpr int TREE_LOCAL_CAP = 4096;
+constexpr int TREE_LOCAL_TPB = 512;
 
 // Launch schedule over the instances of a forest.  A launch is a 1-D grid; block b works for
 // instance inst[b] as the rank-th of the nb = span[inst].y blocks that instance received
@@ -247,6 +253,7 @@ struct fmm_tree_s {
     fmm::SchedH s_rsscan;  // radix digit-count scans (groups of digits per block)
     fmm::SchedH s_p2m;     // the leaves, 4 per block
     fmm::SchedH s_m2l, s_p2p;
+    fmm::SchedH s_local;   // boxes of level lg (instances with lg < L), one block each
     fmm::SchedH* s_split = nullptr;  // [Lmax] boxes of level l, 128 per block (levels l < L)
     fmm::SchedH* s_m2m = nullptr;    // [Lmax] boxes of level l, 4 per block (l < L)
     fmm::SchedH* s_l2l = nullptr;    // [Lmax] children of level l, 4 per block (l < L)

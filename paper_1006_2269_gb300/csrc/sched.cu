@@ -6,6 +6,7 @@
 // and box counts, levels) and copied to the device once; launches then need no host work.  The
 // per-instance block counts follow the work of each kernel family:
 //   tiles     one block per tree-build tile (exact)
+//   local     one block per box of the level where the median tree finishes inside blocks
 //   points    one block per 1024 points
 //   levels    one block per 4 boxes (warp-per-box kernels) or per 128 boxes (thread-per-box)
 //   lists     one block per tile of about 9 * 4^l candidates of level l
@@ -109,8 +110,10 @@ int sched_all(fmm_tree t)
     t->s_l2l = new (std::nothrow) SchedH[std::max(Lm, 1)];
     t->s_lists = new (std::nothrow) SchedH[Lm + 1];
     if (!t->s_split || !t->s_m2m || !t->s_l2l || !t->s_lists) return fail(FMM_ERR_OOM, "host allocation");
+    each([](const Inst& S) { return S.lg < S.L ? level_size(S.lg) : 0; });
+    if ((rc = make_from(t, b, t->s_local))) return rc;
     for (int l = 0; l < Lm; l++) {
-        each([l](const Inst& S) { return l < S.L ? cdiv(level_size(l), 128) : 0; });
+        each([l](const Inst& S) { return l < S.lg ? cdiv(level_size(l), 128) : 0; });
         if ((rc = make_from(t, b, t->s_split[l]))) return rc;
         each([l](const Inst& S) { return l >= 1 && l < S.L ? cdiv(level_size(l), 4) : 0; });
         if ((rc = make_from(t, b, t->s_m2m[l]))) return rc;
@@ -147,6 +150,7 @@ void sched_free_all(fmm_tree t)
     sched_free(t->s_pts);
     sched_free(t->s_rsscan);
     sched_free(t->s_p2m);
+    sched_free(t->s_local);
     sched_free(t->s_m2l);
     sched_free(t->s_p2p);
     const int Lm = t->Lmax;

@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(TPB) k_part_count(Sched sc, const Inst* __rest
 {
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
-    if (l >= S.L) return;
+    if (l >= S.lg) return;
     in += S.p0;
     flag += S.p0;
     __shared__ uint32_t wt[32];
@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(TPB) k_part_count(Sched sc, const Inst* __rest
 // Zeros keep their order and come first.  A segment of size m holds m - floor(m/2) ones, ob[j]
 // counts the ones of all segments before segment j at that depth, tilecnt[] the ones of every
 // tile (each block adds up those before its own).  An instance with fewer than l + 1 levels is finished: its items are
-// copied through unchanged so that the next level finds them in the output buffer.
+// copied through unchanged so that the next level finds them in the output buffer; so is one
+// whose remaining levels are split inside blocks (l >= lg).
 // tile schedule
 __global__ void __launch_bounds__(TPB) k_part_scatter(Sched sc, const Inst* __restrict__ I, int l, int xmode,
                                                       const int32_t* __restrict__ in,
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(TPB) k_part_scatter(Sched sc, const Inst* __re
     out += S.p0;
     out_seg += S.p0;
     const int32_t n = (int32_t)S.n;
-    if (l >= S.L) {
+    if (l >= S.lg) {
         for (int j = 0; j < ITEMS; j++) {
             const int32_t i = tile * TILE + j * TPB + threadIdx.x;
             if (i < n) {
@@ -505,6 +506,19 @@ __global__ void k_init_hx(Sched sc, const Inst* __restrict__ I, const int32_t* _
 
 __device__ __forceinline__ double midpoint(double a, double b) { return __dmul_rn(0.5, __dadd_rn(a, b)); }
 
+// The four children of box b of level l from its x-split xs and the y-splits of its halves.
+__device__ __forceinline__ void child_rects(double* __restrict__ rects, int l, int64_t b, double xs,
+                                            const double ys[2])
+{
+    const double* pr = rects + 4 * (level_base(l) + b);
+    double px0 = pr[0], px1 = pr[1], py0 = pr[2], py1 = pr[3];
+    double* cr = rects + 4 * (level_base(l + 1) + 4 * b);
+    cr[0] = px0; cr[1] = xs;  cr[2] = py0;   cr[3] = ys[0];
+    cr[4] = px0; cr[5] = xs;  cr[6] = ys[0]; cr[7] = py1;
+    cr[8] = xs;  cr[9] = px1; cr[10] = py0;  cr[11] = ys[1];
+    cr[12] = xs; cr[13] = px1; cr[14] = ys[1]; cr[15] = py1;
+}
+
 __device__ __forceinline__ void split_one(int64_t b, int l, const int32_t* __restrict__ X,
                                           const int32_t* __restrict__ Yn, const double* __restrict__ x,
                                           const double* __restrict__ y, const int32_t* __restrict__ offD,
@@ -520,13 +534,7 @@ __device__ __forceinline__ void split_one(int64_t b, int l, const int32_t* __res
         int64_t my = hm[h] >> 1;
         ys[h] = midpoint(y[Yn[ho[h] + my - 1]], y[Yn[ho[h] + my]]);
     }
-    const double* pr = rects + 4 * (level_base(l) + b);
-    double px0 = pr[0], px1 = pr[1], py0 = pr[2], py1 = pr[3];
-    double* cr = rects + 4 * (level_base(l + 1) + 4 * b);
-    cr[0] = px0; cr[1] = xs;  cr[2] = py0;   cr[3] = ys[0];
-    cr[4] = px0; cr[5] = xs;  cr[6] = ys[0]; cr[7] = py1;
-    cr[8] = xs;  cr[9] = px1; cr[10] = py0;  cr[11] = ys[1];
-    cr[12] = xs; cr[13] = px1; cr[14] = ys[1]; cr[15] = py1;
+    child_rects(rects, l, b, xs, ys);
 }
 
 // Split coordinates of the boxes of level l and the rectangles of their children.  X is the
@@ -539,7 +547,7 @@ __global__ void k_split_rects(Sched sc, const Inst* __restrict__ I, int l, const
 {
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
-    if (l >= S.L) return;
+    if (l >= S.lg) return;
     X += S.p0;
     Yn += S.p0;
     x += S.p0;
@@ -603,18 +611,206 @@ __global__ void k_geometry_roots(const Inst* __restrict__ I, int n_inst, const d
     for (int i = threadIdx.x; i < n_inst; i += blockDim.x) geometry_one(I[i].b0, rects, cen, rad, rad32, chi, clo);
 }
 
-// The same for the boxes of level l of every instance (as soon as their rectangles exist).
-// schedule: boxes of level l - 1 (128 per block), four children each; level 0: one block
+// The same for the boxes of level l of every instance split by the global passes (as soon as
+// their rectangles exist; the block-local split does the levels below lg itself).
+// schedule: boxes of level l - 1 (128 per block), four children each
 __global__ void k_geometry_level(Sched sc, const Inst* __restrict__ I, int l, const double* __restrict__ rects,
                                  double* __restrict__ cen, double* __restrict__ rad, float* __restrict__ rad32,
                                  float* __restrict__ chi, float* __restrict__ clo)
 {
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
-    if (l > S.L) return;
+    if (l > S.lg) return;
     const int64_t nb = level_size(l);
     for (int64_t b = (int64_t)z.rank * blockDim.x + threadIdx.x; b < nb; b += (int64_t)z.nb * blockDim.x)
         geometry_one(S.b0 + level_base(l) + b, rects, cen, rad, rad32, chi, clo);
+}
+
+// ---- the lowest levels inside one block per box -------------------------------------------------
+// A box of level lg with m <= TREE_LOCAL_CAP points finishes its subtree (levels lg .. L-1) in
+// shared memory, with the three steps of every global level: a stable partition of the y-ordered
+// list by the x-half bit, the split coordinates and child rectangles, a stable partition of the
+// x-ordered list by the y-half bit.  Points are renamed by their position in the box's x order at
+// level lg (local ids < m), and segment indices are local to the subtree: node j at relative
+// depth d is node (b << d) + j of the instance, whose offset and ones-before count come from the
+// same tables as in the global passes.  Both therefore build the same tree.  At the end the
+// x-ordered list (segmented by leaves) and each item's leaf go back to X and XS in place.
+struct LocalSmem {
+    int32_t gid[TREE_LOCAL_CAP];                            // local id -> point of the instance
+    uint16_t xl[2][TREE_LOCAL_CAP], yl[2][TREE_LOCAL_CAP];  // x and y orders of local ids
+    uint16_t xs[2][TREE_LOCAL_CAP], ys[2][TREE_LOCAL_CAP];  // their segment indices
+    uint8_t hx[TREE_LOCAL_CAP], hy[TREE_LOCAL_CAP];         // half bits, by local id
+    uint32_t wt[32];
+};
+static_assert(TREE_LOCAL_CAP <= 65536, "local ids and segment indices are 16-bit");
+constexpr int LOC_IPT = TREE_LOCAL_CAP / TREE_LOCAL_TPB;  // consecutive items of one thread
+static_assert(LOC_IPT * TREE_LOCAL_TPB == TREE_LOCAL_CAP && LOC_IPT <= 32, "items per thread");
+
+// One stable partition of the block's lists, as k_part_scatter does it for a whole instance.
+// offA: node offsets of the level-l boxes of the subtree (depth 2l, from its first node); obA:
+// ones-before counts of the segments at depth 2l + XMODE (from the subtree's first node); o: the
+// box's offset in the instance.
+template <int XMODE>
+__device__ __forceinline__ void local_partition(LocalSmem& sm, int cur, int32_t m, int32_t nseg,
+                                                const int32_t* __restrict__ offA, const int32_t* __restrict__ obA,
+                                                int32_t o, int32_t* status)
+{
+    const uint16_t* lst = XMODE ? sm.xl[cur] : sm.yl[cur];
+    const uint16_t* seg = XMODE ? sm.xs[cur] : sm.ys[cur];
+    uint16_t* lo = XMODE ? sm.xl[cur ^ 1] : sm.yl[cur ^ 1];
+    uint16_t* so = XMODE ? sm.xs[cur ^ 1] : sm.ys[cur ^ 1];
+    const uint8_t* fin = XMODE ? sm.hy : sm.hx;
+    uint8_t* fout = XMODE ? sm.hx : sm.hy;
+    const int32_t k0 = (int32_t)threadIdx.x * LOC_IPT;
+    uint32_t fl = 0, c = 0;
+#pragma unroll
+    for (int j = 0; j < LOC_IPT; j++) {
+        const int32_t k = k0 + j;
+        const uint32_t f = k < m ? fin[lst[k]] : 0u;
+        fl |= f << j;
+        c += f;
+    }
+    uint32_t tot;
+    uint32_t G = block_excl_scan(c, sm.wt, tot);  // ones before this thread's first item
+    const int32_t ob0 = obA[0];
+#pragma unroll
+    for (int j = 0; j < LOC_IPT; j++) {
+        const int32_t k = k0 + j;
+        if (k >= m) break;
+        const uint32_t f = (fl >> j) & 1u;
+        const int32_t sg = seg[k];
+        if (sg >= nseg) {  // cannot happen: segment indices of depth 2l are < 4^(l - lg)
+            atomicOr(status, ST_ARG);
+            G += f;
+            continue;
+        }
+        int32_t os = offA[sg] - o, ms = offA[sg + 1] - offA[sg];
+        int32_t s1 = sg;
+        if (XMODE) {  // the x-half of the box
+            const int32_t h = ms >> 1;
+            const int32_t bit = k >= os + h;
+            s1 = 2 * sg + bit;
+            if (bit) {
+                os += h;
+                ms -= h;
+            } else {
+                ms = h;
+            }
+        }
+        const int32_t ones = (int32_t)G - (obA[s1] - ob0);
+        G += f;
+        const int32_t h = ms >> 1;
+        const int32_t np = f ? (os + h + ones) : (k - ones);
+        if (np < os || np >= os + ms || np < 0 || np >= m) {  // cannot happen for consistent tables
+            atomicOr(status, ST_ARG);
+            continue;
+        }
+        const int32_t o2 = f ? os + h : os, m2 = f ? ms - h : h;
+        const int32_t s2 = 2 * s1 + (int32_t)f;
+        const int32_t bit2 = np >= o2 + (m2 >> 1);
+        const uint16_t id = lst[k];
+        lo[np] = id;
+        so[np] = (uint16_t)(XMODE ? s2 : 2 * s2 + bit2);
+        fout[id] = (uint8_t)bit2;
+    }
+    __syncthreads();
+}
+
+// schedule: boxes of level lg of the instances with lg < L, one block each (TREE_LOCAL_TPB
+// threads, sizeof(LocalSmem) bytes of dynamic shared memory).  scratch: n int32 per instance
+// (the local id of every point of the box).  geo != 0: also the geometry of the new boxes.
+__global__ void __launch_bounds__(TREE_LOCAL_TPB, 2)
+k_split_local(Sched sc, const Inst* __restrict__ I, int32_t* __restrict__ X, int32_t* __restrict__ XS,
+              const int32_t* __restrict__ Y, const double* __restrict__ x, const double* __restrict__ y,
+              const int32_t* __restrict__ node_off, const int32_t* __restrict__ ones_before,
+              int32_t* __restrict__ scratch, double* __restrict__ rects, double* __restrict__ cen,
+              double* __restrict__ rad, float* __restrict__ rad32, float* __restrict__ chi,
+              float* __restrict__ clo, int geo, int32_t* status)
+{
+    extern __shared__ __align__(16) unsigned char local_smem[];
+    LocalSmem& sm = *reinterpret_cast<LocalSmem*>(local_smem);
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const int lg = S.lg, L = S.L;
+    if (lg >= L) return;
+    const int64_t b = z.rank;  // the box of level lg
+    X += S.p0;
+    XS += S.p0;
+    Y += S.p0;
+    x += S.p0;
+    y += S.p0;
+    scratch += S.p0;
+    const int32_t* nodes = node_off + S.no0;
+    const int32_t* obt = ones_before + S.ob0;
+    const int32_t o = nodes[node_offset_base(2 * lg) + b];
+    const int32_t m = nodes[node_offset_base(2 * lg) + b + 1] - o;
+    if (m < 0 || m > TREE_LOCAL_CAP || o < 0 || (int64_t)o + m > S.n) {  // block-uniform
+        if (threadIdx.x == 0) atomicOr(status, ST_CAPACITY);
+        return;
+    }
+    const int32_t n = (int32_t)S.n;
+    for (int32_t k = threadIdx.x; k < m; k += blockDim.x) {
+        const int32_t g = X[o + k];
+        const bool ok = g >= 0 && g < n;
+        if (!ok) atomicOr(status, ST_ARG);
+        sm.gid[k] = ok ? g : 0;
+        sm.xl[0][k] = (uint16_t)k;
+        sm.xs[0][k] = 0;
+        sm.ys[0][k] = 0;
+        sm.hx[k] = (uint8_t)(k >= (m >> 1));  // x-half of the box: the upper half of its x order
+        if (ok) scratch[g] = k;
+    }
+    __syncthreads();
+    for (int32_t k = threadIdx.x; k < m; k += blockDim.x) {
+        const int32_t g = Y[o + k];
+        int32_t v = (g >= 0 && g < n) ? scratch[g] : -1;
+        if (v < 0 || v >= m) {
+            atomicOr(status, ST_ARG);
+            v = 0;
+        }
+        sm.yl[0][k] = (uint16_t)v;
+    }
+    __syncthreads();
+    double* R = rects + 4 * S.b0;
+    int cx = 0, cy = 0;
+    for (int l = lg; l < L; l++) {
+        const int r = l - lg;
+        const int32_t* offA = nodes + node_offset_base(2 * l) + (b << (2 * r));
+        // Y: stable partition of every box by its x-half bit; records the y-half bits
+        const int32_t nseg = (int32_t)level_size(r);
+        local_partition<0>(sm, cy, m, nseg, offA, obt + ones_before_offset(2 * l) + (b << (2 * r)), o, status);
+        cy ^= 1;
+        // split coordinates and child rectangles of the subtree's boxes of level l
+        for (int32_t sb = threadIdx.x; sb < nseg; sb += blockDim.x) {
+            const int32_t os = offA[sb] - o, mb = offA[sb + 1] - offA[sb];
+            if (mb < 4 || os < 0 || os + mb > m) {  // every box above the leaves holds >= 4 points
+                atomicOr(status, ST_ARG);
+                continue;
+            }
+            const int32_t mx = mb >> 1;
+            const double xsp = midpoint(x[sm.gid[sm.xl[cx][os + mx - 1]]], x[sm.gid[sm.xl[cx][os + mx]]]);
+            const int32_t ho[2] = {os, os + mx}, hm[2] = {mx, mb - mx};
+            double ysp[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; hh++) {
+                const int32_t my = hm[hh] >> 1;
+                ysp[hh] = midpoint(y[sm.gid[sm.yl[cy][ho[hh] + my - 1]]], y[sm.gid[sm.yl[cy][ho[hh] + my]]]);
+            }
+            const int64_t B = (b << (2 * r)) + sb;
+            child_rects(R, l, B, xsp, ysp);
+            if (geo)
+                for (int c = 0; c < 4; c++)
+                    geometry_one(S.b0 + level_base(l + 1) + 4 * B + c, rects, cen, rad, rad32, chi, clo);
+        }
+        // X: stable partition of each x-half by the y-half bit; records the next x-half bits
+        local_partition<1>(sm, cx, m, nseg, offA, obt + ones_before_offset(2 * l + 1) + (b << (2 * r + 1)), o, status);
+        cx ^= 1;
+    }
+    const int64_t leaf0 = b << (2 * (L - lg));
+    for (int32_t k = threadIdx.x; k < m; k += blockDim.x) {
+        X[o + k] = sm.gid[sm.xl[cx][k]];
+        XS[o + k] = (int32_t)(leaf0 + sm.xs[cx][k]);
+    }
 }
 
 // Coordinates in canonical order, and their binary32 offsets from the leaf centre.
@@ -821,6 +1017,9 @@ void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls)
         S.no0 = no0;
         S.lb0 = lb0;
         S.maxleaf = (int32_t)((S.n + level_size(S.L) - 1) / level_size(S.L));
+        // the first level whose boxes (at most ceil(n / 4^l) points) fit one block
+        S.lg = 0;
+        while (S.lg < S.L && (S.n + level_size(S.lg) - 1) / level_size(S.lg) > TREE_LOCAL_CAP) S.lg++;
         p0 += S.n;
         b0 += S.nbox;
         t0 += S.ntiles;
@@ -902,6 +1101,8 @@ int tree_alloc(fmm_tree t, int n_inst, const int64_t* ns, const int* Ls)
     FMM_CUDA(cudaMemcpy(t->ones_before, ob_all.data(), 4 * ob_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemcpy(t->node_off, off_all.data(), 4 * off_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemset(t->status, 0, 4));
+    FMM_CUDA(cudaFuncSetAttribute(k_split_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(LocalSmem)));
     return sched_all(t);
 }
 
@@ -950,12 +1151,20 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cud
 
     {
         StageScope scope(FMM_STAGE_TREE_SPLIT, s);
+        // global passes for levels l < Lg; the geometry of levels <= Lev is complete after them
+        // (the rest comes from the block-local split)
+        int Lg = 0, Lev = L;
+        for (int i = 0; i < ni; i++) {
+            const Inst& S = t->hinst[i];
+            Lg = std::max(Lg, (int)S.lg);
+            if (S.lg < S.L) Lev = std::min(Lev, (int)S.lg);
+        }
         // box index carried by every item of X and Y (all in the root at level 0)
         int32_t *XS = t->segs, *XSo = t->segs + n, *YS = t->segs + 2 * n, *YSo = t->segs + 3 * n;
         FMM_CUDA(cudaMemsetAsync(XS, 0, 4 * n, s));
         FMM_CUDA(cudaMemsetAsync(YS, 0, 4 * n, s));
         k_init_hx<<<gp, 256, 0, s>>>(sp, t->dinst, X, hx); note_launch();
-        for (int l = 0; l < L; l++) {
+        for (int l = 0; l < Lg; l++) {
             // Y: stable partition of each box by its x-half bit; records the y-half bit
             k_part_count<<<gt, TPB, 0, s>>>(st, t->dinst, l, Y, hx, t->tilecnt); note_launch();
             k_part_scatter<<<gt, TPB, 0, s>>>(st, t->dinst, l, 0, Y, YS, Yo, YSo, hx, hy, t->node_off,
@@ -969,7 +1178,7 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cud
                 k_geometry_level<<<t->s_split[l].blocks, 128, 0, s>>>(t->s_split[l].d, t->dinst, l + 1, t->rects,
                                                                      t->centers, t->radii, t->rad32, t->cen_hi,
                                                                      t->cen_lo); note_launch();
-                FMM_CUDA(cudaEventRecord(level_ready[l + 1], s));
+                if (l + 1 <= Lev) FMM_CUDA(cudaEventRecord(level_ready[l + 1], s));
             }
             // X: stable partition of each x-half by the y-half bit; records the next x-half bit
             k_part_count<<<gt, TPB, 0, s>>>(st, t->dinst, l, X, hy, t->tilecnt); note_launch();
@@ -979,6 +1188,16 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cud
             std::swap(XS, XSo);
             FMM_LAUNCH_CHECK("tree: level split");
         }
+        if (t->s_local.blocks > 0) {  // the levels below lg, one block per box of level lg
+            const int smem = (int)sizeof(LocalSmem);  // opted in when the tree was created
+            k_split_local<<<(unsigned)t->s_local.blocks, TREE_LOCAL_TPB, smem, s>>>(
+                t->s_local.d, t->dinst, X, XS, Y, x, y, t->node_off, t->ones_before, t->leaf_of, t->rects,
+                t->centers, t->radii, t->rad32, t->cen_hi, t->cen_lo, level_ready ? 1 : 0, t->status);
+            note_launch();
+            FMM_LAUNCH_CHECK("tree: block-local split");
+        }
+        if (level_ready)
+            for (int l = Lev + 1; l <= L; l++) FMM_CUDA(cudaEventRecord(level_ready[l], s));
         Xfinal_seg = XS;
     }
 
