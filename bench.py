@@ -288,6 +288,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched workload")
+    ap.add_argument("--blocks", default=None, metavar="M2L,NEAR",
+                    help="grid sizes of the binary32 M2L and near-field kernels instead of the autotuner's "
+                         "(e.g. to profile the plain run's launch configuration under a profiler)")
     ap.add_argument("--lists", default="auto", choices=["auto", "plain", "parents", "exchange", "parents+exchange"],
                     help="interaction lists: the plain rule, with Section 4's parent-level interactions and/or "
                          "finest-level role exchange, or the fastest variant on this workload")
@@ -387,8 +390,11 @@ def main():
     fmm.fmm_lists_set_mode(f.lists, variants[lists_kind])
     step(fmm.FMM_MODE_MIXED)
     fmm.fmm_sync_status(f.tree, f.lists)
-    tuned = {fmm.FMM_MODE_FP64: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_FP64, phi),
-             fmm.FMM_MODE_MIXED: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_MIXED, phi)}
+    tuned = {fmm.FMM_MODE_FP64: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_FP64, phi)}
+    if args.blocks:
+        tuned[fmm.FMM_MODE_MIXED] = tuple(int(v) for v in args.blocks.split(","))
+    else:
+        tuned[fmm.FMM_MODE_MIXED] = fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_MIXED, phi)
 
     def use(mode):
         fmm.fmm_set_launch(f.tree, *tuned[mode])
@@ -514,8 +520,8 @@ def main():
         "config": {"workload": w.name, "n": n, "levels": w.levels, "theta": w.theta, "p": w.p,
                    "mode": "mixed", "l2": "flushed between steps (256 MB write outside the events)",
                    "replicas": world, "cuda_graph": bool(graphs),
-                   "autotuned_blocks": {"m2l": tuned[fmm.FMM_MODE_MIXED][0],
-                                        "near_field": tuned[fmm.FMM_MODE_MIXED][1]},
+                   ("launch_blocks" if args.blocks else "autotuned_blocks"): {
+                       "m2l": tuned[fmm.FMM_MODE_MIXED][0], "near_field": tuned[fmm.FMM_MODE_MIXED][1]},
                    "m2l_kernel": "tensor cores (tcgen05, split tf32)" if m2l_kind == fmm.FMM_M2L_TENSOR
                    else "SIMT binary32",
                    "lists": lists_kind + ("" if lists_kind == "plain" else " (Section 4's optional optimisations)"),
