@@ -27,8 +27,8 @@
  *
  * Readings of points the paper leaves open (each one is also listed in the design notes):
  *   R1  x is split first, then y separately in each x-half; the lower part of a set of n
- *       points gets floor(n/2) of them (Section 4: "at or near their median in each
- *       coordinate direction"; Fig. 1.1: four boxes of very nearly equal counts).
+ *       points gets floor(n/2) of them (Section 4 splits every box close to its median in
+ *       both coordinates; Fig. 1.1 shows four boxes holding almost the same counts).
  *   R2  ties in a coordinate are broken by the original input index.
  *   R3  the split coordinate is 0.5*(a+b) of the two straddling coordinates.
  *   R4  the sphere of a box for Criterion 2.1 is the circumscribed circle of its partition
@@ -365,8 +365,9 @@ void* orc_lists_build(int L, const double* rects, double theta)
     return h;
 }
 
-/* Optional structural optimisation of Section 4: a box weakly coupled to all four children of a
- * box P interacts with P instead, whenever the theta-criterion between P and the box holds.  The
+/* Optional structural optimisation of Section 4: when the four children of a box P all sit on a
+ * target's weak list and Criterion 2.1 also holds between P and the target, one M2L term from P
+ * replaces the four from its children.  The
  * four children appear as four consecutive weak entries 4k, 4k+1, 4k+2, 4k+3 (candidates are
  * taken parent by parent, child by child); they are replaced, in place of the first, by one entry
  * k | ORC_PARENT_FLAG naming the parent at the level above.  Applied once to every level's weak
