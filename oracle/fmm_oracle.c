@@ -14,7 +14,7 @@
  *   Eq. (1.1):  Phi(x_i) = sum_{j != i} G(x_i, x_j) with the 2D harmonic kernel
  *               G(x_i, x_j) = q_j log|x_i - x_j|   (strengths q_j as in Section 5).
  *
- *   - orc_direct : the plain O(N^2) definition of Eq. (1.1) (the error judge).
+ *   - orc_direct : the plain O(N^2) definition of Eq. (1.1) (the reference for every error).
  *   - orc_tree   : the balanced asymmetric mesh of Section 4 / Fig. 1.1 / Fig. 4.1, built by
  *                  recursive median splits along each coordinate direction.
  *   - orc_lists  : the strong/weak connectivity rule of Section 4 with the theta-criterion

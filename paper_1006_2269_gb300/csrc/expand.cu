@@ -1804,7 +1804,7 @@ __global__ void k_combine_field32(Sched sc, const Inst* __restrict__ I, const in
     }
 }
 
-// Direct field at sampled targets (binary64), the judge of the field's error.
+// Direct field at sampled targets (binary64), the reference for the field's error.
 __global__ void k_direct_field(const double* __restrict__ x, const double* __restrict__ y,
                                const double* __restrict__ q, int64_t n, const int64_t* __restrict__ tgt,
                                double* __restrict__ fre, double* __restrict__ fim)

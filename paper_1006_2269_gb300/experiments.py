@@ -22,7 +22,7 @@
     python -m paper_1006_2269_gb300.experiments adaptivity [--n 200000] [--out FILE]
 
 Every number is computed by the library's kernels (the tree, lists, expansions, and the binary64
-direct kernels that judge the error); this module only drives them.
+direct kernels that measure the error); this module only drives them.
 """
 from __future__ import annotations
 
