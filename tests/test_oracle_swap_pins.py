@@ -1,6 +1,9 @@
 """Pins of the oracle's finest-level role exchange (Section 4's second structural optimisation),
 on the CPU.
 
+Criterion: hand values, and the exchanged test as the smaller set expanded by 1/theta about its
+centre staying clear of the larger one (symmetric, Criterion 2.1 for equal radii, implied by it).
+
 Operators: the P2L expansion evaluated inside its disc against the direct sum, within the
 truncation bound of the logarithm's series, |sum_{l>p} u^l / l| <= |u|^(p+1) / ((p+1)(1-|u|)),
 and M2P likewise.  Lists: the exchanged pairs and the remaining strong pairs of a leaf are the
@@ -25,6 +28,39 @@ def _disc_and_annulus(seed, m_src=40, m_tgt=25, r_tgt=0.3, r_in=1.2, r_out=2.0):
     tgt = r_tgt * np.sqrt(g.uniform(0, 1, m_tgt)) * np.exp(1j * g.uniform(0, 2 * np.pi, m_tgt))
     q = g.normal(size=m_src)
     return src, tgt, q
+
+
+def test_swapped_criterion_hand_values():
+    # R = 2, r = 0.5, theta = 1/4: swapped iff 0.5 + 0.5 <= 0.25 d, i.e. d >= 4 (plain: d >= 8.5)
+    assert oracle.theta_swapped((0, 0), 2.0, (4.0, 0), 0.5, 0.25)
+    assert oracle.theta_swapped((0, 0), 0.5, (0, -4.0), 2.0, 0.25)  # argument order does not matter
+    assert not oracle.theta_swapped((0, 0), 2.0, (3.99, 0), 0.5, 0.25)
+    assert not oracle.theta_weak((0, 0), 2.0, (4.0, 0), 0.5, 0.25)
+    # a point-like leaf next to a large one: apart is enough for the exchange, touching is not
+    assert oracle.theta_swapped((0, 0), 1.0, (1.5, 0), 0.0, 0.5)
+    assert not oracle.theta_swapped((0, 0), 1.0, (1.0, 0), 0.0, 0.5)
+
+
+def test_swapped_criterion_is_the_small_set_expanded():
+    # the exchanged test asks that the smaller set, expanded by 1/theta about its centre, stay
+    # clear of the larger one: r/theta + R < d (r <= R); with equal radii it is Criterion 2.1,
+    # and whatever Criterion 2.1 accepts it accepts too
+    g = np.random.default_rng(5)
+    for _ in range(4000):
+        th = g.uniform(0.05, 0.95)
+        r1, r2 = g.uniform(0, 1, 2)
+        c1, c2 = g.uniform(-4, 4, 2), g.uniform(-4, 4, 2)
+        d = np.hypot(*(c1 - c2))
+        R, r = max(r1, r2), min(r1, r2)
+        margin = d - (r / th + R)
+        if abs(margin) < 1e-9:
+            continue
+        sw = oracle.theta_swapped(c1, r1, c2, r2, th)
+        assert sw == (margin > 0)
+        assert sw == oracle.theta_swapped(c2, r2, c1, r1, th)
+        if oracle.theta_weak(c1, r1, c2, r2, th):
+            assert sw
+        assert oracle.theta_swapped(c1, r1, c2, r1, th) == oracle.theta_weak(c1, r1, c2, r1, th)
 
 
 @pytest.mark.parametrize("p", [4, 8, 16, 30])
