@@ -160,7 +160,8 @@ void fmm_tree_destroy(fmm_tree t);
  * n < 4^levels.  It calls no cudaMalloc, cudaFree or other allocating routine.  All calls share
  * the one array, so calls on the same device must not overlap in time (two streams or two host
  * threads running it at once corrupt each other's results).  The first call on a device looks
- * up the array's address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * up the array's address (cudaGetSymbolAddress) and sets the tree kernels' shared-memory limit
+ * (cudaFuncSetAttribute); make that first call before any stream capture.
  * ------------------------------------------------------------------------------------------- */
 #define FMM_NOALLOC_MAX_POINTS 65536
 #define FMM_NOALLOC_MAX_LEVELS 7

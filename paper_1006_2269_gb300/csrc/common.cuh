@@ -317,6 +317,8 @@ int tree_alloc(fmm_tree t, int n_inst, const int64_t* n, const int* levels);
 void fill_instances(Inst* out, int n_inst, const int64_t* ns, const int* Ls);
 void forest_totals(fmm_tree t);
 int tree_tables_host(int64_t n, int L, int32_t* ones_before, int32_t* node_off, int32_t* leaf_begin);
+// Once per device, outside any stream capture: kernel attributes the tree build needs.
+int tree_kernel_setup();
 // level_ready (may be null): events [Lmax + 1]; event l is recorded once the geometry (centres,
 // radii) of levels 0 .. l is complete, so that the lists of those levels can be built meanwhile.
 int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cudaEvent_t* level_ready = nullptr);

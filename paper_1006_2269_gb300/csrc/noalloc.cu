@@ -81,10 +81,12 @@ int scratch_base(unsigned char** out)
     FMM_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 128) return fail(FMM_ERR_ARG, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_base[dev]) {
+    if (!g_na_base[dev]) {  // the first call on this device (documented: before any capture)
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch of fmm_build_tree_noalloc)");
+        const int rc = tree_kernel_setup();  // no tree handle was created on this path
+        if (rc) return rc;
         g_na_base[dev] = (unsigned char*)p;
     }
     *out = g_na_base[dev];

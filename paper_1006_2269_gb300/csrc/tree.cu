@@ -1101,9 +1101,18 @@ int tree_alloc(fmm_tree t, int n_inst, const int64_t* ns, const int* Ls)
     FMM_CUDA(cudaMemcpy(t->ones_before, ob_all.data(), 4 * ob_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemcpy(t->node_off, off_all.data(), 4 * off_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemset(t->status, 0, 4));
+    if ((rc = tree_kernel_setup())) return rc;
+    return sched_all(t);
+}
+
+// The block-local split's dynamic shared memory is above the default limit of a launch; the
+// opt-in holds for the current device from then on.  Called where a tree is created and on the
+// first no-allocation build of a device, so never inside a stream capture of a documented use.
+int tree_kernel_setup()
+{
     FMM_CUDA(cudaFuncSetAttribute(k_split_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sizeof(LocalSmem)));
-    return sched_all(t);
+    return 0;
 }
 
 int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cudaEvent_t* level_ready)

@@ -4,6 +4,10 @@ recorded).  Its output must equal what the allocating entry points produce (fmm_
 fmm_tree_export), bit for bit, on consecutive calls that reuse the library's fixed scratch array.
 
 The file name makes pytest collect it last."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -51,3 +55,38 @@ def test_noalloc_rejects_sizes_beyond_the_scratch(fmmlib, cuda):
         fmmlib.fmm_build_tree_noalloc(x, x, 1, perm, rects, lb)
     assert e.value.code == fmmlib.FMM_ERR_ARG
     assert "65536" in str(e.value)
+
+
+_FRESH = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_1006_2269_gb300 import fmm, workloads as W
+fmm.load_library()
+n, L = 65536, 5  # boxes of level 2 hold 4096 points: levels 2-4 split inside blocks
+c = W.clusters(n, 74)
+dev = torch.device("cuda", 0)
+x, y = (torch.as_tensor(v, device=dev) for v in (c.x, c.y))
+perm = torch.empty(n, dtype=torch.int32, device=dev)
+rects = torch.empty(((4 ** (L + 1) - 1) // 3, 4), dtype=torch.float64, device=dev)
+lb = torch.empty(4 ** L + 1, dtype=torch.int32, device=dev)
+fmm.fmm_build_tree_noalloc(x, y, L, perm, rects, lb)
+torch.cuda.synchronize()
+np.savez(sys.argv[2], perm=perm.cpu().numpy(), rects=rects.cpu().numpy(), lb=lb.cpu().numpy())
+"""
+
+
+def test_noalloc_first_in_a_fresh_process(fmmlib, cuda, orc, tmp_path):
+    # no tree handle exists in that process: the first no-allocation call itself must prepare
+    # the block-local split (its shared memory is above the default launch limit)
+    out = str(tmp_path / "tree.npz")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH, root, out], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = np.load(out)
+    c = W.clusters(65536, 74)
+    operm, orects, olb = orc.tree(c.x, c.y, 5)
+    assert np.array_equal(got["perm"], operm)
+    assert np.array_equal(got["rects"], orects)
+    assert np.array_equal(got["lb"].astype(np.int64), olb)
