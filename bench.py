@@ -160,6 +160,22 @@ def job_throughput(world: int, units_per_replica: int, ms_total: float, steps: i
     return world * units_per_replica / (ms_total / steps * 1e-3)
 
 
+def shard_instances(sizes, world: int, rank: int):
+    """Indices of the independent instances rank `rank` of `world` runs: largest first to the
+    least loaded rank (ties to the lower rank), each rank's indices ascending.  One rank takes
+    every instance in order."""
+    if world == 1:
+        return list(range(len(sizes)))
+    load = [0] * world
+    mine = []
+    for i in sorted(range(len(sizes)), key=lambda j: (-sizes[j], j)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        load[r] += sizes[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
 # ---- our arm -----------------------------------------------------------------------------------
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the SIMT M2L kernel per launch on the 1M
@@ -185,16 +201,20 @@ def pair_counts(f):
     return nweak, pairs
 
 
-def bench_batched(dev, steps, warmup, sequential=True):
+def bench_batched(dev, steps, warmup, sequential=True, world=1, rank=0):
     """The batched workload: 512 independent instances, N log-uniform in [1e3, 2e5] (uniform
     square / 2D normal / jittered unit circle), theta = 1/2, p = 16, leaves of ~32 points.  One
     step = tree, lists and evaluation of every instance, all instances in the same launches,
-    replayed as one CUDA graph with the launch shapes chosen by the library's autotuner.  For
-    comparison the same instances are also run one after another through single-instance
-    handles (one step, plain launches)."""
+    replayed as one CUDA graph with the launch shapes chosen by the library's autotuner.  Under
+    several ranks the instances are shared out (shard_instances; no exchange between ranks) and
+    the value counts the points of all ranks over the slowest rank's time.  For comparison the
+    same instances are also run one after another through single-instance handles (one step,
+    plain launches)."""
     import torch
     from paper_1006_2269_gb300 import fmm, workloads as W
-    inst = W.batched_instances()
+    inst_all = W.batched_instances()
+    n_all = int(sum(c.x.shape[0] for c, _ in inst_all))
+    inst = [inst_all[i] for i in shard_instances([c.x.shape[0] for c, _ in inst_all], world, rank)]
     sizes = [c.x.shape[0] for c, _ in inst]
     levels = [L for _, L in inst]
     x = torch.as_tensor(np.concatenate([c.x for c, _ in inst]), device=dev)
@@ -234,7 +254,7 @@ def bench_batched(dev, steps, warmup, sequential=True):
         g.replay()
         e.record(stream)
     torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(e) for a, e in ev) / steps
+    ms = max_over_ranks(sum(a.elapsed_time(e) for a, e in ev) / steps, world, dev)
     fmm.fmm_sync_status(b.tree, b.lists)
     # accuracy: 16 sampled targets of every instance against the binary64 direct sum
     worst = 0.0
@@ -245,12 +265,17 @@ def bench_batched(dev, steps, warmup, sequential=True):
         fmm.fmm_direct(x[a0:a0 + m], y[a0:a0 + m], q[a0:a0 + m], tg, ref)
         err = ((phi[a0:a0 + m][tg] - ref).abs().max() / ref.abs().max()).item()
         worst = max(worst, err)
+    worst = max_over_ranks(worst, world, dev)
     out = {"workload": "512 instances, N log-uniform in [1e3, 2e5], uniform/normal/circle, "
                        "theta=1/2, p=16, ~32 points per leaf",
-           "instances": len(sizes), "points": n, "value": n / (ms * 1e-3), "unit": UNIT,
+           "instances": len(inst_all), "points": n_all, "value": n_all / (ms * 1e-3), "unit": UNIT,
            "ms_per_step": ms, "gpu_launches_per_step": launches, "cuda_graph": True,
            "autotuned_blocks_per_instance": {"m2l": m2l_blocks, "near_field": p2p_blocks},
            "rel_err_max_sampled": worst, "n_check_per_instance": 16}
+    if world > 1:  # a fixed set of instances shared out: strong scaling for this sub-result
+        out["ranks"] = world
+        out["scaling"] = "strong"
+        out["instances_per_rank"] = "largest first to the least loaded rank"
     b.close()
     if sequential:
         # the same instances one by one through single-instance handles
@@ -271,7 +296,8 @@ def bench_batched(dev, steps, warmup, sequential=True):
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1)
             out["one_by_one"] = {"value": n / (t * 1e-3), "ms_per_step": t,
-                                 "note": "same instances through 512 single-instance handles, plain launches"}
+                                 "note": f"the same {len(inst)} instances through single-instance handles, "
+                                         "plain launches" + ("" if world == 1 else " (this rank's share)")}
         finally:
             for f, _, _ in fs:
                 f.close()
@@ -538,7 +564,8 @@ def main():
         "clocks": clk.summary(),
     }
     if not args.no_batched:
-        out["batched"] = bench_batched(dev, max(3, min(K, 10)), args.warmup, sequential=(rank == 0))
+        out["batched"] = bench_batched(dev, max(3, min(K, 10)), args.warmup, sequential=(rank == 0),
+                                       world=world, rank=rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
