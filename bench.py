@@ -304,6 +304,42 @@ def bench_batched(dev, steps, warmup, sequential=True, world=1, rank=0):
     return out
 
 
+def profile_run(a):
+    """A fixed workload run a few times as a profiler's target (see --profile-run)."""
+    import torch
+    from paper_1006_2269_gb300 import build, fmm, workloads as W
+    build.build()
+    fmm.load_library()
+    dev = torch.device("cuda", 0)
+    p = a.p
+    if a.workload == "clusters-1m":
+        c, L, theta, p = W.mixed_1m_cloud(), W.MIXED_1M.levels, W.MIXED_1M.theta, p or W.MIXED_1M.p
+    elif a.workload == "uniform-1m":
+        c, L, theta, p = W.uniform(1 << 20, W.SEED_BASE + 7), 8, 0.5, p or 20
+    else:
+        c, L, theta, p = W.large_16m_cloud(), W.LARGE_16M.levels, W.LARGE_16M.theta, p or W.LARGE_16M.p
+    lists = a.lists if a.lists != "auto" else "parents"
+    x, y, q = (torch.as_tensor(np.ascontiguousarray(v), device=dev) for v in (c.x, c.y, c.q))
+    f = fmm.FMM(x, y, L, theta, parents="parents" in lists, exchange="exchange" in lists)
+    try:
+        fmm.fmm_set_m2l_kernel(f.tree, {"auto": fmm.FMM_M2L_AUTO, "simt": fmm.FMM_M2L_SIMT,
+                                        "tensor": fmm.FMM_M2L_TENSOR}[a.m2l])
+        mode = fmm.FMM_MODE_MIXED if a.mode == "mixed" else fmm.FMM_MODE_FP64
+        phi = torch.empty(c.x.shape[0], dtype=torch.float64, device=dev)
+        for _ in range(a.profile_run):
+            if a.profile_steps:
+                fmm.fmm_build_tree(f.tree, x, y)
+                fmm.fmm_interaction_lists(f.tree, f.lists, theta)
+            fmm.fmm_evaluate(f.tree, f.lists, q, p, mode, phi)
+        torch.cuda.synchronize()
+        fmm.fmm_sync_status(f.tree, f.lists)
+        nweak, nstrong = fmm.fmm_lists_sync(f.lists)
+        print(f"{a.workload}: {a.profile_run} {'steps' if a.profile_steps else 'evaluations'}, p = {p}, "
+              f"{a.mode}, lists {lists} ({nweak} weak, {nstrong} strong entries), phi[0] = {float(phi[0]):.6e}")
+    finally:
+        f.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,8 +356,21 @@ def main():
     ap.add_argument("--lists", default="auto", choices=["auto", "plain", "parents", "exchange", "parents+exchange"],
                     help="interaction lists: the plain rule, with Section 4's parent-level interactions and/or "
                          "finest-level role exchange, or the fastest variant on this workload")
+    ap.add_argument("--profile-run", type=int, default=0, metavar="K",
+                    help="profiler target: build the tree and lists of --workload once, run K evaluations "
+                         "(whole steps with --profile-steps) on plain launches, print one line and exit; "
+                         "no timing, so a profiler's -s/-c counts select the same kernels on every run")
+    ap.add_argument("--profile-steps", action="store_true")
+    ap.add_argument("--workload", default="clusters-1m", choices=["clusters-1m", "uniform-1m", "rings-16m"],
+                    help="workload of --profile-run")
+    ap.add_argument("--p", type=int, default=None, help="expansion order of --profile-run (workload's default)")
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"], help="precision of --profile-run")
+    ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"], help="M2L kernel of --profile-run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_run:
+        profile_run(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -140,10 +140,10 @@ void fmm_tree_destroy(fmm_tree t);
 
 /* ---------------------------------------------------------------------------------------------
  * Tree construction that allocates nothing.  The paper has no counterpart: this entry point
- * exists for callers that cannot allocate device memory -- code running while its stream is
- * captured into a CUDA graph (an allocation cannot be captured), code inside an application
- * whose own memory manager owns the device, or latency-critical loops that cannot take the
- * synchronisation a cudaMalloc/cudaFree may cause.  It computes exactly what fmm_build_tree
+ * exists for callers that cannot allocate device memory -- code inside an application whose own
+ * memory manager owns the device (an allocation behind its back can fail or fragment what it
+ * manages), or latency-critical loops that cannot take the device-wide synchronisation a
+ * cudaMalloc/cudaFree may cause.  It computes exactly what fmm_build_tree
  * followed by fmm_tree_export computes, but every intermediate buffer lives in one fixed device
  * array compiled into the library (about 7.7 MB, held on every GPU that loads the library until
  * the process exits), so inputs are limited to n <= FMM_NOALLOC_MAX_POINTS points and
@@ -161,7 +161,10 @@ void fmm_tree_destroy(fmm_tree t);
  * the one array, so calls on the same device must not overlap in time (two streams or two host
  * threads running it at once corrupt each other's results).  The first call on a device looks
  * up the array's address (cudaGetSymbolAddress) and sets the tree kernels' shared-memory limit
- * (cudaFuncSetAttribute); make that first call before any stream capture.
+ * (cudaFuncSetAttribute); make that first call before any stream capture.  Both are kept for the
+ * life of the process, so after cudaDeviceReset (a new context) do not call it on that device
+ * again.  Each of rects and leaf_begin must hold the element count above: the library cannot
+ * check the length of a raw pointer.
  * ------------------------------------------------------------------------------------------- */
 #define FMM_NOALLOC_MAX_POINTS 65536
 #define FMM_NOALLOC_MAX_LEVELS 7

@@ -1,10 +1,10 @@
 // Tree construction for callers that cannot allocate device memory.
 //
 // fmm_build_tree needs a tree handle, and creating one calls cudaMalloc.  Some callers cannot do
-// that: code that runs while its stream is being captured into a CUDA graph (an allocation is not
-// an operation a capture can record), code inside a host application whose memory manager owns
-// the device and must not be bypassed, and latency-critical loops that cannot afford the device
-// synchronisation a cudaMalloc/cudaFree may cause.  fmm_build_tree_noalloc serves them: it runs
+// that: code inside a host application whose own memory manager owns the device and must not be
+// bypassed (an allocation outside it can fail or fragment the memory it manages), and
+// latency-critical loops that cannot afford the device-wide synchronisation a cudaMalloc or
+// cudaFree may cause.  fmm_build_tree_noalloc serves them: it runs
 // the same build kernels, but every intermediate buffer lives in one file-scope device array of
 // fixed size that each GPU loading the library keeps until the process exits.  The caller passes
 // only inputs and outputs.
@@ -12,7 +12,9 @@
 // Consequences of the shared array: calls on one device must not overlap in time (two streams,
 // or two host threads, running the build at once would overwrite each other's intermediates),
 // and the first call on a device looks up the array's device address, which should happen before
-// any stream capture begins.
+// any stream capture begins.  That address and the kernels' shared-memory opt-in are kept for the
+// life of the process: after cudaDeviceReset the device's context is a new one, so a process that
+// resets a device must not call this entry point on it again.
 #include <mutex>
 
 #include "common.cuh"
@@ -185,11 +187,13 @@ extern "C" int fmm_build_tree_noalloc(const double* x, const double* y, int64_t 
     t.own_hinst = false;
     forest_totals(&t);
     // a single instance needs no schedule tables (only small host arrays of grid sizes)
+    // the launch schedules hold small host arrays: freed on every way out of this function
+    struct SchedGuard {
+        fmm_tree_s* t;
+        ~SchedGuard() { sched_free_all(t); }
+    } guard{&t};
     rc = sched_all(&t);
-    if (rc) {
-        sched_free_all(&t);
-        return rc;
-    }
+    if (rc) return rc;
     const Layout& Lo = kLayout;
     t.dinst = (Inst*)(base + Lo.inst);
     t.keys = (uint64_t*)(base + Lo.keys);
@@ -225,7 +229,6 @@ extern "C" int fmm_build_tree_noalloc(const double* x, const double* y, int64_t 
     note_launch();
     FMM_LAUNCH_CHECK("fmm_build_tree_noalloc: tables");
     rc = tree_build(&t, x, y, s);
-    sched_free_all(&t);
     if (rc) return rc;
     if (status) FMM_CUDA(cudaMemcpyAsync(status, t.status, 4, cudaMemcpyDeviceToDevice, s));
     return FMM_OK;

@@ -134,17 +134,26 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
+def _need(*specs):
+    """(tensor or None, elements, name) triples: the C entry points write through raw pointers
+    whose length they cannot see, so a buffer shorter than the call's output is refused here,
+    before anything is launched."""
+    for t, n, name in specs:
+        if t is not None and t.numel() < n:
+            raise FMMError(FMM_ERR_ARG, f"{name} has {t.numel()} elements, needs {n}")
+
+
 def _dev(t: torch.Tensor | None, dtype, n=None, name="tensor"):
     if t is None:
         return None
+    if n is not None:
+        _need((t, n, name))
     if not t.is_cuda:
         raise FMMError(FMM_ERR_ARG, f"{name} must be a CUDA tensor")
     if t.dtype != dtype:
         raise FMMError(FMM_ERR_ARG, f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
         raise FMMError(FMM_ERR_ARG, f"{name} must be contiguous")
-    if n is not None and t.numel() < n:
-        raise FMMError(FMM_ERR_ARG, f"{name} has {t.numel()} elements, needs {n}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -209,21 +218,25 @@ def fmm_build_tree_noalloc(x, y, levels: int, perm, rects, leaf_begin, status=No
     """Tree build for callers that cannot allocate device memory: the outputs are the caller's
     tensors, every intermediate lives in the library's fixed device array (n <= 65536,
     levels <= 7).  Calls on one device must not overlap in time."""
-    n = x.numel()
-    _check(load_library().fmm_build_tree_noalloc(_dev(x, torch.float64, n, "x"),
-                                                 _dev(y, torch.float64, n, "y"), n, int(levels),
-                                                 _dev(perm, torch.int32, n, "perm"),
-                                                 _dev(rects, torch.float64, None, "rects"),
-                                                 _dev(leaf_begin, torch.int32, None, "leaf_begin"),
-                                                 _dev(status, torch.int32, 1, "status"),
-                                                 _stream(stream)))
+    n, L = x.numel(), int(levels)
+    nbox = (4 ** (L + 1) - 1) // 3 if 0 <= L <= FMM_NOALLOC_MAX_LEVELS else 0
+    _need((y, n, "y"), (perm, n, "perm"), (rects, 4 * nbox, "rects"),
+          (leaf_begin, 4 ** L + 1 if nbox else 0, "leaf_begin"))
+    args = (_dev(x, torch.float64, n, "x"), _dev(y, torch.float64, n, "y"), n, L,
+            _dev(perm, torch.int32, n, "perm"), _dev(rects, torch.float64, 4 * nbox, "rects"),
+            _dev(leaf_begin, torch.int32, 4 ** L + 1 if nbox else 0, "leaf_begin"),
+            _dev(status, torch.int32, 1, "status"), _stream(stream))
+    _check(load_library().fmm_build_tree_noalloc(*args))
 
 
 def fmm_tree_export(tree, perm=None, rects=None, leaf_begin=None, stream=None):
-    _check(load_library().fmm_tree_export(tree, _dev(perm, torch.int32, None, "perm"),
-                                          _dev(rects, torch.float64, None, "rects"),
-                                          _dev(leaf_begin, torch.int32, None, "leaf_begin"),
-                                          _stream(stream)))
+    n, L, nbox = fmm_tree_info(tree)
+    last = fmm_tree_instance(tree, fmm_tree_num_instances(tree) - 1)
+    nlb = last["lb0"] + 4 ** last["levels"] + 1  # every instance's 4^L_i + 1 offsets
+    _need((perm, n, "perm"), (rects, 4 * nbox, "rects"), (leaf_begin, nlb, "leaf_begin"))
+    args = (tree, _dev(perm, torch.int32, n, "perm"), _dev(rects, torch.float64, 4 * nbox, "rects"),
+            _dev(leaf_begin, torch.int32, 4 ** L + 1, "leaf_begin"), _stream(stream))
+    _check(load_library().fmm_tree_export(*args))
 
 
 def fmm_tree_info(tree):

@@ -220,3 +220,16 @@ def test_bad_arguments(fmmlib, cuda):
     assert e.value.code == fmmlib.FMM_ERR_ARG
     with pytest.raises(fmmlib.FMMError):
         f.evaluate(_t(c.q.astype(np.float32), cuda), 5, "fp64")
+
+
+def test_tree_export_refuses_short_buffers(fmmlib, cuda):
+    import torch
+    c = W.uniform(5000, 76)
+    f = fmmlib.FMM(torch.as_tensor(c.x, device=cuda), torch.as_tensor(c.y, device=cuda), 3, 0.5)
+    try:
+        with pytest.raises(fmmlib.FMMError, match="leaf_begin has 64 elements, needs 65"):
+            fmmlib.fmm_tree_export(f.tree, leaf_begin=torch.empty(64, dtype=torch.int32, device=cuda))
+        with pytest.raises(fmmlib.FMMError, match="rects has"):
+            fmmlib.fmm_tree_export(f.tree, rects=torch.empty((84, 4), dtype=torch.float64, device=cuda))
+    finally:
+        f.close()

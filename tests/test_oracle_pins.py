@@ -193,6 +193,39 @@ def test_tree_rejects_too_few_points(orc):
 
 
 # ---------------------------------------------------------------------------------------------
+# Box geometry (reading R4: the sphere of Criterion 2.1 is the circumscribed circle of the
+# partition rectangle, so centre = midpoint and radius = half the diagonal)
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rect,centre,radius", [
+    ((0.0, 1.0, 0.0, 1.0), (0.5, 0.5), math.sqrt(2.0) / 2),    # unit square
+    ((0.0, 2.0, 0.0, 1.0), (1.0, 0.5), math.sqrt(5.0) / 2),    # 2 x 1 rectangle
+    ((-3.0, 1.0, 2.0, 5.0), (-1.0, 3.5), 2.5),                  # 4 x 3: a 3-4-5 diagonal
+    ((3.0, 3.0, 1.0, 5.0), (3.0, 3.0), 2.0),                    # zero width: a segment
+    ((0.25, 0.25, -0.5, -0.5), (0.25, -0.5), 0.0),              # a point box
+], ids=["unit", "2x1", "3-4-5", "zero-width", "point"])
+def test_geometry_hand_values(orc, rect, centre, radius):
+    cen, rad = orc.geometry(np.array([rect], dtype=np.float64))
+    assert cen[0].tolist() == pytest.approx(list(centre), rel=0, abs=1e-15)
+    assert rad[0] == pytest.approx(radius, rel=1e-15, abs=0)
+
+
+def test_geometry_is_the_smallest_enclosing_circle(orc):
+    # The circle through the four corners about the midpoint is the smallest disc holding the
+    # rectangle: every corner lies on it (a larger radius, e.g. the whole diagonal, fails), and
+    # two opposite corners are a diameter apart (a smaller one cannot hold both).
+    rng = np.random.default_rng(424242)
+    lo = rng.uniform(-5, 5, (200, 2))
+    ext = rng.uniform(0, 3, (200, 2)) * (rng.uniform(size=(200, 2)) > 0.1)
+    rects = np.stack([lo[:, 0], lo[:, 0] + ext[:, 0], lo[:, 1], lo[:, 1] + ext[:, 1]], axis=1)
+    cen, rad = orc.geometry(rects)
+    for (x0, x1, y0, y1), c, r in zip(rects, cen, rad):
+        for cx_, cy_ in ((x0, y0), (x0, y1), (x1, y0), (x1, y1)):
+            assert math.hypot(cx_ - c[0], cy_ - c[1]) == pytest.approx(r, rel=1e-14, abs=1e-300)
+        assert 2 * r == pytest.approx(math.hypot(x1 - x0, y1 - y0), rel=1e-15, abs=1e-300)
+
+
+# ---------------------------------------------------------------------------------------------
 # Connectivity (Section 4)
 # ---------------------------------------------------------------------------------------------
 
@@ -233,6 +266,48 @@ def test_lists_brute_force(orc, name, make, L, theta):
             assert widx[woff[g]:woff[g + 1]].tolist() == ref[l][0][b]
             assert sidx[soff[g]:soff[g + 1]].tolist() == ref[l][1][b]
             assert b in sidx[soff[g]:soff[g + 1]]  # a box is strongly coupled to itself
+
+
+def brute_lists_own_geometry(rects, L, theta):
+    """The same brute force with nothing taken from the oracle: circumscribed circles and
+    Criterion 2.1 written out here, in the arithmetic order of their definitions."""
+    rects = np.asarray(rects, dtype=np.float64)
+    cen = [(0.5 * (r[0] + r[1]), 0.5 * (r[2] + r[3])) for r in rects]
+    rad = [0.5 * math.sqrt((r[1] - r[0]) * (r[1] - r[0]) + (r[3] - r[2]) * (r[3] - r[2])) for r in rects]
+
+    def weak(a, b):
+        dx, dy = cen[a][0] - cen[b][0], cen[a][1] - cen[b][1]
+        d = math.sqrt(dx * dx + dy * dy)
+        R, r = max(rad[a], rad[b]), min(rad[a], rad[b])
+        return R + theta * r <= theta * d and R + r < d
+
+    strong_prev = {(0, 0)}
+    out = {}
+    for l in range(1, L + 1):
+        base = (4 ** l - 1) // 3
+        Wl, Sl = {}, {}
+        for b in range(4 ** l):
+            cand = [c for c in range(4 ** l) if (b // 4, c // 4) in strong_prev]
+            Wl[b] = [c for c in cand if weak(base + b, base + c)]
+            Sl[b] = [c for c in cand if not weak(base + b, base + c)]
+        strong_prev = {(b, c) for b in Sl for c in Sl[b]}
+        out[l] = (Wl, Sl)
+    return out
+
+
+@pytest.mark.parametrize("theta", [0.25, 0.5, math.sqrt(0.5)])
+@pytest.mark.parametrize("name,make,L", [CASES[0], CASES[3]], ids=["uniform", "clusters"])
+def test_lists_brute_force_own_geometry(orc, name, make, L, theta):
+    c = make()
+    perm, rects, lb = orc.tree(c.x, c.y, L)
+    woff, widx, soff, sidx = orc.lists(rects, L, theta)
+    ref = brute_lists_own_geometry(rects, L, theta)
+    for l in range(1, L + 1):
+        base = (4 ** l - 1) // 3
+        for b in range(4 ** l):
+            g = base + b
+            assert widx[woff[g]:woff[g + 1]].tolist() == ref[l][0][b]
+            assert sidx[soff[g]:soff[g + 1]].tolist() == ref[l][1][b]
 
 
 @pytest.mark.parametrize("theta", [0.25, 0.5, math.sqrt(0.5)])

@@ -1,7 +1,9 @@
 """fmm_build_tree_noalloc: the tree build for callers that cannot allocate device memory (for
-example code running while its stream is captured into a CUDA graph, where cudaMalloc cannot be
-recorded).  Its output must equal what the allocating entry points produce (fmm_build_tree +
-fmm_tree_export), bit for bit, on consecutive calls that reuse the library's fixed scratch array.
+example code inside an application whose own memory manager owns the device, or a loop that
+cannot take the synchronisation cudaMalloc may cause).  Its output must equal what the
+allocating entry points produce (fmm_build_tree + fmm_tree_export), bit for bit, on
+consecutive calls that reuse the library's fixed scratch array, and it must leave the free
+device memory unchanged.
 
 The file name makes pytest collect it last."""
 import os
@@ -90,3 +92,23 @@ def test_noalloc_first_in_a_fresh_process(fmmlib, cuda, orc, tmp_path):
     assert np.array_equal(got["perm"], operm)
     assert np.array_equal(got["rects"], orects)
     assert np.array_equal(got["lb"].astype(np.int64), olb)
+
+
+def test_noalloc_allocates_no_device_memory(fmmlib, cuda):
+    # the free device memory is the same before and after a call (after a first call has done
+    # the once-per-device set-up), and the caller's buffers are the only outputs
+    import torch
+    n, L = 20000, 4
+    c = W.clusters(n, 75)
+    x, y = _t(c.x, cuda), _t(c.y, cuda)
+    perm = torch.empty(n, dtype=torch.int32, device=cuda)
+    rects = torch.empty(((4 ** (L + 1) - 1) // 3, 4), dtype=torch.float64, device=cuda)
+    lb = torch.empty(4 ** L + 1, dtype=torch.int32, device=cuda)
+    fmmlib.fmm_build_tree_noalloc(x, y, L, perm, rects, lb)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        fmmlib.fmm_build_tree_noalloc(x, y, L, perm, rects, lb)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
