@@ -111,9 +111,81 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---- the FP64 CPU oracle as it stands, on one core and on every host core ----------------------
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu / /proc/cpuinfo), or the platform's processor string."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+_ORC_SAMPLE = None
+
+
+def _orc_worker_init(ns, Ls, p, theta):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    global _ORC_SAMPLE
+    import oracle
+    from paper_1006_2269_gb300 import workloads as W
+    oracle.build()
+    _ORC_SAMPLE = (oracle, W.mixed_1m_cloud(ns), Ls, p, theta)
+
+
+def _orc_worker_run(_):
+    orc, c, Ls, p, theta = _ORC_SAMPLE
+    t0 = time.perf_counter()
+    orc.fmm(c.x, c.y, c.q, Ls, p, theta)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """One process per host core (spawned, so it is safe beside a CUDA context), each holding the
+    same bounded sample of the workload; a round runs the unmodified oracle FMM once on every core
+    at the same time."""
+
+    def __init__(self, cores, ns, Ls, p, theta):
+        import multiprocessing as mp
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores, initializer=_orc_worker_init, initargs=(ns, Ls, p, theta))
+
+    def round(self, limit_s: float = 600.0) -> float:
+        # a worker that dies is replaced by the pool and its task never returns: the time limit
+        # turns that into an error instead of a wait without end
+        t0 = time.perf_counter()
+        self.pool.map_async(_orc_worker_run, range(self.cores), chunksize=1).get(timeout=limit_s)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
 # ---- the reference arm: the FP64 CPU oracle as it stands ----------------------------------------
 
 def run_reference(args, rank):
+    """The oracle as it stands on the host cores: every step runs the oracle FMM once on each
+    core at the same time, each on the same bounded sample of the benchmark workload."""
     if rank != 0:
         return None
     import oracle
@@ -121,23 +193,27 @@ def run_reference(args, rank):
     oracle.build()
     w = W.MIXED_1M
     ns, Ls = 1 << 16, 6  # bounded sample of the workload: same distribution, 16 points per leaf
-    c = W.mixed_1m_cloud(ns)
-    for _ in range(args.warmup):
-        oracle.fmm(c.x, c.y, c.q, Ls, w.p, w.theta)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.fmm(c.x, c.y, c.q, Ls, w.p, w.theta)
-    dt = (time.perf_counter() - t0) / args.steps
-    v = ns / dt
+    cores = host_cores()
+    pool = OraclePool(cores, ns, Ls, w.p, w.theta)
+    try:
+        for _ in range(args.warmup):
+            pool.round()
+        t = [pool.round() for _ in range(args.steps)]
+    finally:
+        pool.close()
+    dt = sum(t) / args.steps
+    v = cores * ns / dt
+    sample = (f"oracle FMM on N={ns} points of the same distribution, L={Ls}, p={w.p}, one run per core "
+              f"on all {cores} host cores at once ({cpu_model()})")
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"clusters N={ns}, L={Ls}, theta=1/2, p={w.p} (bounded sample of {w.name})",
-                   "sample_of": w.name},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"oracle FMM on N={ns} points of the same distribution, L={Ls}, p={w.p}"},
+                   "sample_of": w.name, "points_per_step": cores * ns},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "nproc": cores, "cpu_model": cpu_model()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -304,6 +380,45 @@ def bench_batched(dev, steps, warmup, sequential=True, world=1, rank=0):
     return out
 
 
+def cpu_baseline(w, W, seconds=8.0):
+    """The oracle FMM as it stands on a bounded sample of the benchmark workload (2^16 points of
+    the same distribution, 16 per leaf): about `seconds` on one core, then about `seconds` with one
+    run per host core at once.  value/cores describe the all-core run."""
+    import oracle
+    oracle.build()
+    ns, Ls = 1 << 16, 6
+    cs = W.mixed_1m_cloud(ns)
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.fmm(cs.x, cs.y, cs.q, Ls, w.p, w.theta)
+        reps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    one = ns * reps / (time.perf_counter() - t0)
+    cores = host_cores()
+    pool = OraclePool(cores, ns, Ls, w.p, w.theta)
+    try:
+        pool.round()  # warm-up: every worker has loaded the oracle and its sample
+        t0 = time.perf_counter()
+        rounds = 0
+        while True:
+            pool.round()
+            rounds += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        allc = cores * ns * rounds / (time.perf_counter() - t0)
+    finally:
+        pool.close()
+    model = cpu_model()
+    return {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle FMM, N={ns} points of the same distribution, L={Ls}, p={w.p}: one run per "
+                      f"core on all {cores} host cores at once, {rounds} rounds",
+            "nproc": cores, "cpu_model": model,
+            "single_core": {"value": one, "unit": UNIT, "cores": 1, "runs": reps}}
+
+
 def profile_run(a):
     """A fixed workload run a few times as a profiler's target (see --profile-run)."""
     import torch
@@ -324,6 +439,9 @@ def profile_run(a):
     try:
         fmm.fmm_set_m2l_kernel(f.tree, {"auto": fmm.FMM_M2L_AUTO, "simt": fmm.FMM_M2L_SIMT,
                                         "tensor": fmm.FMM_M2L_TENSOR}[a.m2l])
+        fmm.fmm_set_m2l_shape(f.tree, *(int(v) for v in a.m2l_shape.split(",")))
+        if a.blocks:
+            fmm.fmm_set_launch(f.tree, *(int(v) for v in a.blocks.split(",")))
         mode = fmm.FMM_MODE_MIXED if a.mode == "mixed" else fmm.FMM_MODE_FP64
         phi = torch.empty(c.x.shape[0], dtype=torch.float64, device=dev)
         for _ in range(a.profile_run):
@@ -366,6 +484,9 @@ def main():
     ap.add_argument("--p", type=int, default=None, help="expansion order of --profile-run (workload's default)")
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"], help="precision of --profile-run")
     ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"], help="M2L kernel of --profile-run")
+    ap.add_argument("--m2l-shape", default="0,0", metavar="CHUNK,STAGES",
+                    help="tensor-core M2L tile shape of --profile-run: consecutive weak entries per row and TMEM "
+                         "accumulator stages (0: defaults)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.profile_run:
@@ -559,7 +680,7 @@ def main():
     t_top = stage_ms[top] * 1e-3
     m2l_kind = fmm.fmm_get_m2l_kernel(f.tree)
     if m2l_kind == fmm.FMM_M2L_AUTO:
-        m2l_kind = fmm.FMM_M2L_TENSOR if 29 <= P <= 32 else fmm.FMM_M2L_SIMT
+        m2l_kind = fmm.FMM_M2L_TENSOR if 24 <= P <= 32 else fmm.FMM_M2L_SIMT
     if top == "near":
         roof = {"bound": "alu", "achieved": npairs / t_top / 1e12, "peak": mufu_peak / 1e12,
                 "unit": "Tlog2/s (MUFU)", "traffic": None}
@@ -616,21 +737,7 @@ def main():
         out["batched"] = bench_batched(dev, max(3, min(K, 10)), args.warmup, sequential=(rank == 0),
                                        world=world, rank=rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        ns, Ls = 1 << 16, 6
-        cs = W.mixed_1m_cloud(ns)
-        t0 = time.perf_counter()
-        reps = 0
-        while True:
-            oracle.fmm(cs.x, cs.y, cs.q, Ls, w.p, w.theta)
-            reps += 1
-            if time.perf_counter() - t0 > 10.0:
-                break
-        dt = (time.perf_counter() - t0) / reps
-        out["cpu_baseline"] = {"value": ns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"oracle FMM, N={ns} points of the same distribution, L={Ls}, "
-                                         f"p={w.p}, {reps} runs"}
+        out["cpu_baseline"] = cpu_baseline(w, W)
     if rank == 0:
         print(json.dumps(out), flush=True)
     f.close()

@@ -313,12 +313,24 @@ int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks);
 /* Which kernel performs the binary32 M2L of tree t: 2 the tensor cores (tcgen05, split-tf32
  * products: each operand as a tf32 high and low part, three products accumulated in binary32;
  * p <= 31 only), 1 the SIMT units in plain binary32, 0 (default) by the order: tensor cores for
- * 28 <= p <= 31, where they measured clearly faster on GB300, SIMT units otherwise.  Changing
+ * 23 <= p <= 31, SIMT units otherwise (on GB300 the tensor cores measured twice as fast at
+ * p = 30 and 20% slower at p = 20).  Changing
  * the kind does not touch the launch tables, but a captured graph keeps the kernel it saw.
  * fmm_autotune sets 1 or 2 by timing both.  The binary64 path always uses the SIMT units. */
 int fmm_set_m2l_kernel(fmm_tree t, int kind);
 /* The current choice (0, 1 or 2), or a negative fmm_status. */
 int fmm_get_m2l_kernel(fmm_tree t);
+
+/* Tile shape of the tensor-core M2L (no paper counterpart).  chunk: every row of its 128-row
+ * tiles takes `chunk` consecutive weak entries, one per tile, and keeps the sums of their common
+ * targets in registers, so a larger chunk means fewer atomic flushes and a coarser split of the
+ * entries over the blocks; 1 .. 256, or 0 for the built-in default (16).  stages: 2 = two TMEM
+ * accumulator buffers, the epilogue of one tile overlapping the MMAs of the next (two blocks per
+ * SM); 1 = one buffer, the epilogue after its own tile's MMAs (three blocks per SM up to p = 20);
+ * 0 = by order (2 from p = 21 on).  fmm_autotune chooses both with the block count.
+ * fmm_get_m2l_shape reports them (host pointers, may be NULL). */
+int fmm_set_m2l_shape(fmm_tree t, int chunk, int stages);
+int fmm_get_m2l_shape(fmm_tree t, int* chunk, int* stages);
 
 /* ---------------------------------------------------------------------------------------------
  * Parameter selector (no paper counterpart).  The paper picks the parameters by rule: p from the

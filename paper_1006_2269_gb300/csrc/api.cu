@@ -115,7 +115,7 @@ void free_tree(fmm_tree t)
 void free_lists(fmm_lists l)
 {
     if (!l) return;
-    void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status,
+    void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->rowtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status,
                     l->dlinst, l->tiledrop, l->tileswap, l->xoff, l->xidx, l->xtgt, l->p2p_items, l->p2p_pos,
                     l->p2p_tmp, l->p2p_zero};
     for (void* p : ptrs)
@@ -600,6 +600,24 @@ int fmm_get_m2l_kernel(fmm_tree t)
 {
     if (!t) return fail(FMM_ERR_ARG, "NULL tree");
     return t->m2l_kind;
+}
+
+int fmm_set_m2l_shape(fmm_tree t, int chunk, int stages)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (chunk < 0 || chunk > 256) return fail(FMM_ERR_ARG, "M2L chunk %d outside [0, 256]", chunk);
+    if (stages < 0 || stages > 2) return fail(FMM_ERR_ARG, "M2L stages %d outside [0, 2]", stages);
+    t->tune_m2l_chunk = chunk;
+    t->tune_m2l_stages = stages;
+    return FMM_OK;
+}
+
+int fmm_get_m2l_shape(fmm_tree t, int* chunk, int* stages)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (chunk) *chunk = t->tune_m2l_chunk;
+    if (stages) *stages = t->tune_m2l_stages;
+    return FMM_OK;
 }
 
 int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks)

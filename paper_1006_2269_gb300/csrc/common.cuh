@@ -245,6 +245,8 @@ struct fmm_tree_s {
     // launch tuning (set by fmm_autotune; 0 = defaults): total blocks of the M2L and near-field
     // launches, shared out over the instances in proportion to their work
     int tune_m2l_blocks = 0, tune_p2p_blocks = 0;
+    int tune_m2l_chunk = 0;   // tensor-core M2L: consecutive weak entries per row (0 = default)
+    int tune_m2l_stages = 0;  // tensor-core M2L: TMEM accumulator stages 1 or 2 (0 = by order)
     int m2l_kind = 0;  // binary32 M2L: 0 = by order (tensor cores for 24 <= P <= 32), 1 = SIMT, 2 = tensor cores
 
     // launch schedules (device tables only for forests of more than one instance)
@@ -279,6 +281,7 @@ struct fmm_lists_s {
     int32_t* soff = nullptr;
     int32_t* widx = nullptr;  // within-level index of the source box
     int32_t* wtgt = nullptr;  // local box id of the target box of each weak entry
+    int32_t* rowtgt = nullptr;  // tensor-core M2L: target box of the first entry of each row chunk
     int32_t* sidx = nullptr;
     int32_t* stgt = nullptr;
     uint8_t* flags = nullptr;     // weak flag per candidate of the level being built

@@ -2054,10 +2054,11 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         if ((rc = wait_lists())) return rc;
         {
             StageScope scope(FMM_STAGE_M2L, s);
-            // tensor cores where they measured clearly faster than the SIMT kernel (P >= 29, on
-            // 2^20 clustered points: 3.3 ms against 3.9-4.6 ms at p = 30; below, the scaling work
-            // around the contraction dominates), unless chosen explicitly
-            const bool tc = m2l_tc_supported(P) && (t->m2l_kind == 2 || (t->m2l_kind == 0 && P >= 29));
+            // tensor cores by default from P = 24 on (on 2^20 clustered points with parent-level
+            // lists they take 1.1 ms against 2.3 ms at p = 30, but 0.8 ms against 0.67 ms at
+            // p = 20, where the O(P) scaling work around the contraction dominates), unless chosen
+            // explicitly or by fmm_autotune
+            const bool tc = m2l_tc_supported(P) && (t->m2l_kind == 2 || (t->m2l_kind == 0 && P >= 24));
             if (sizeof(T) == 4 && tc)
                 rc = m2l_tc(t, li, P, PS, Me, Le, s);
             else
@@ -2243,44 +2244,72 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
         }
         return 0;
     };
+    // Launch shapes: the M2L kernel (SIMT or tensor cores) with its total block count and, for the
+    // tensor-core kernel, the consecutive weak entries per row (its tile-to-pair shape); then the
+    // near field's total block count.  Each candidate is timed on whole evaluations.
     const int ladder[] = {152, 152 * 2, 152 * 4, 152 * 8, 152 * 16, 152 * 32, 152 * 64};
+    const int ladder_tc[] = {152, 152 * 2, 152 * 3, 152 * 4, 152 * 6};
+    const int chunks_tc[] = {8, 16, 32};
     int rc = 0;
+    const int kind0 = t->m2l_kind, chunk0 = t->tune_m2l_chunk, stages0 = t->tune_m2l_stages;
     t->tune_m2l_blocks = t->tune_p2p_blocks = 0;
     if ((rc = sched_tuned(t))) return rc;
-    for (int stage = 0; stage < 2 && !rc; stage++) {
-        int& knob = stage == 0 ? t->tune_m2l_blocks : t->tune_p2p_blocks;
+    const bool try_tc = prm.mode == FMM_MODE_MIXED && !(prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR) &&
+                        m2l_tc_supported(prm.p + 1);
+    {
+        int best_kind = kind0, best_blocks = 0, best_chunk = chunk0, best_stages = stages0;
+        float best_ms = 1e30f;
+        auto consider = [&](int kind, int v, int ch, int st) -> int {
+            t->m2l_kind = kind;
+            t->tune_m2l_blocks = v;
+            t->tune_m2l_chunk = ch;
+            t->tune_m2l_stages = st;
+            int r = sched_tuned(t);
+            float ms = 0.f;
+            if (!r) r = time_one(ms);
+            if (!r && ms < best_ms) {
+                best_ms = ms;
+                best_kind = kind;
+                best_blocks = v;
+                best_chunk = ch;
+                best_stages = st;
+            }
+            return r;
+        };
+        for (int v : ladder)
+            if (!rc) rc = consider(try_tc ? 1 : kind0, v, chunk0, stages0);
+        if (try_tc)
+            for (int v : ladder_tc)
+                for (int ch : chunks_tc)
+                    for (int st = 1; st <= 2 && !rc; st++) rc = consider(2, v, ch, st);
+        t->m2l_kind = best_kind;
+        t->tune_m2l_blocks = best_blocks;
+        t->tune_m2l_chunk = best_chunk;
+        t->tune_m2l_stages = best_stages;
+    }
+    if (!rc) {
         int best_v = 0;
         float best_ms = 1e30f;
         for (int v : ladder) {
-            knob = v;
+            t->tune_p2p_blocks = v;
             if ((rc = sched_tuned(t))) break;
             float ms = 0.f;
-            rc = time_one(ms);
-            if (rc) break;
+            if ((rc = time_one(ms))) break;
             if (ms < best_ms) {
                 best_ms = ms;
                 best_v = v;
             }
         }
-        knob = best_v;
-    }
-    // binary32 M2L: tensor cores or SIMT units, whichever is faster here
-    if (!rc && prm.mode == FMM_MODE_MIXED && !(prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR) &&
-        m2l_tc_supported(prm.p + 1) && (rc = sched_tuned(t)) == 0) {
-        float ms_simt = 0.f, ms_tc = 0.f;
-        t->m2l_kind = 1;
-        rc = time_one(ms_simt);
-        if (!rc) {
-            t->m2l_kind = 2;
-            rc = time_one(ms_tc);
-        }
-        t->m2l_kind = ms_tc < ms_simt ? 2 : 1;
+        t->tune_p2p_blocks = best_v;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!rc) rc = sched_tuned(t);
     if (rc) {
         t->tune_m2l_blocks = t->tune_p2p_blocks = 0;
+        t->tune_m2l_chunk = chunk0;
+        t->tune_m2l_stages = stages0;
+        t->m2l_kind = kind0;
         sched_tuned(t);
         return rc;
     }

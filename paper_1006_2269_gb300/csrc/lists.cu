@@ -542,6 +542,7 @@ int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int
               cudaMalloc((void**)&l->soff, 4 * noff) == cudaSuccess &&
               cudaMalloc((void**)&l->widx, 4 * std::max<int64_t>(w0, 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->wtgt, 4 * std::max<int64_t>(w0, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->rowtgt, 4 * std::max<int64_t>(w0, 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->sidx, 4 * std::max<int64_t>(s0, 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->stgt, 4 * std::max<int64_t>(s0, 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->flags, f0) == cudaSuccess &&

@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH):
             "fmm_set_launch": (i32, [vp, i32, i32]),
             "fmm_set_m2l_kernel": (i32, [vp, i32]),
             "fmm_get_m2l_kernel": (i32, [vp]),
+            "fmm_set_m2l_shape": (i32, [vp, i32, i32]),
+            "fmm_get_m2l_shape": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "fmm_selector_features": (i32, [vp, dbl, vp, vp]),
             "fmm_mlp_create": (i32, [i32, ctypes.POINTER(vp)]),
             "fmm_mlp_destroy": (None, [vp]),
@@ -455,6 +457,18 @@ def fmm_get_m2l_kernel(tree) -> int:
     if rc < 0:
         _check(rc)
     return rc
+
+
+def fmm_set_m2l_shape(tree, chunk: int = 0, stages: int = 0):
+    """Tensor-core M2L tile shape: consecutive weak entries per row (0: default) and TMEM
+    accumulator stages (1, 2; 0: by order)."""
+    _check(load_library().fmm_set_m2l_shape(tree, int(chunk), int(stages)))
+
+
+def fmm_get_m2l_shape(tree):
+    c, st = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().fmm_get_m2l_shape(tree, ctypes.byref(c), ctypes.byref(st)))
+    return c.value, st.value
 
 
 def fmm_step(tree, lists, x: torch.Tensor, y: torch.Tensor, theta: float, q: torch.Tensor, p: int, mode: int,

@@ -70,3 +70,28 @@ def test_tensor_core_m2l_forest(fmmlib, orc, cuda):
             assert relerr(phi[d["p0"]:d["p0"] + d["n"]], ref) <= TOL_MIXED
     finally:
         b.close()
+
+
+@pytest.mark.parametrize("chunk,stages", [(1, 1), (3, 2), (16, 1), (16, 2), (64, 2)])
+@pytest.mark.parametrize("p", [16, 20, 30])
+def test_tensor_core_m2l_tile_shapes(fmmlib, orc, cuda, chunk, stages, p):
+    # every row of a tile takes `chunk` consecutive weak entries: 1 (a target change at almost
+    # every entry), an odd shape whose chunks end inside target runs, the default, and chunks
+    # longer than most target runs; one or two TMEM accumulator stages; p = 16, 20, 30 take the
+    # exact-order kernels; a ragged last chunk in every case
+    c = W.clusters(30011, 402)
+    L = 5
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), L, 0.5, parents=True)
+    try:
+        q = _t(c.q, cuda)
+        fmmlib.fmm_set_m2l_kernel(f.tree, fmmlib.FMM_M2L_TENSOR)
+        fmmlib.fmm_set_m2l_shape(f.tree, chunk, stages)
+        assert fmmlib.fmm_get_m2l_shape(f.tree) == (chunk, stages)
+        tc = f.evaluate(q, p, "mixed").cpu().numpy()
+        fmmlib.fmm_set_m2l_kernel(f.tree, fmmlib.FMM_M2L_SIMT)
+        simt = f.evaluate(q, p, "mixed").cpu().numpy()
+    finally:
+        f.close()
+    ref = orc.fmm(c.x, c.y, c.q, L, p, 0.5, parents=True)
+    assert relerr(tc, ref) <= TOL_MIXED
+    assert relerr(tc, simt) <= TOL_MIXED
