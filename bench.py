@@ -444,12 +444,21 @@ def profile_run(a):
             fmm.fmm_set_launch(f.tree, *(int(v) for v in a.blocks.split(",")))
         mode = fmm.FMM_MODE_MIXED if a.mode == "mixed" else fmm.FMM_MODE_FP64
         phi = torch.empty(c.x.shape[0], dtype=torch.float64, device=dev)
+        if a.stage_times:  # one untimed run first, then the library's per-stage CUDA events
+            fmm.fmm_evaluate(f.tree, f.lists, q, p, mode, phi)
+            torch.cuda.synchronize()
+            fmm.fmm_profile_read()
+            fmm.fmm_profile_enable(True)
         for _ in range(a.profile_run):
             if a.profile_steps:
                 fmm.fmm_build_tree(f.tree, x, y)
                 fmm.fmm_interaction_lists(f.tree, f.lists, theta)
             fmm.fmm_evaluate(f.tree, f.lists, q, p, mode, phi)
         torch.cuda.synchronize()
+        if a.stage_times:
+            fmm.fmm_profile_enable(False)
+            prof = fmm.fmm_profile_read()
+            print(json.dumps({k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]}))
         fmm.fmm_sync_status(f.tree, f.lists)
         nweak, nstrong = fmm.fmm_lists_sync(f.lists)
         print(f"{a.workload}: {a.profile_run} {'steps' if a.profile_steps else 'evaluations'}, p = {p}, "
@@ -479,6 +488,8 @@ def main():
                          "(whole steps with --profile-steps) on plain launches, print one line and exit; "
                          "no timing, so a profiler's -s/-c counts select the same kernels on every run")
     ap.add_argument("--profile-steps", action="store_true")
+    ap.add_argument("--stage-times", action="store_true",
+                    help="with --profile-run: print the mean per-stage device time (ms) of the K runs")
     ap.add_argument("--workload", default="clusters-1m", choices=["clusters-1m", "uniform-1m", "rings-16m"],
                     help="workload of --profile-run")
     ap.add_argument("--p", type=int, default=None, help="expansion order of --profile-run (workload's default)")
