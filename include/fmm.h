@@ -333,6 +333,20 @@ int fmm_set_m2l_shape(fmm_tree t, int chunk, int stages);
 int fmm_get_m2l_shape(fmm_tree t, int* chunk, int* stages);
 
 /* ---------------------------------------------------------------------------------------------
+ * Throughput probes (no paper counterpart): the peaks of the units the ALU-bound kernels use,
+ * measured instead of derived.  fmm_probe_throughput launches one probe on `stream`: kind 0
+ * binary32 FFMA, 1 the approximate base-2 logarithm (lg2.approx, the special-function unit), 2
+ * binary64 DFMA; `iters` (1 .. 2^20) x 128 dependent operations per thread in 8 independent
+ * chains, fmm_probe_blocks() blocks of 256 threads (8 per SM).  *ops (host) receives the
+ * operations it performs (flop for the FMA probes, logarithms for kind 1); the caller times the
+ * launch with events on the same stream.  out: device float buffer of fmm_probe_blocks() * 256
+ * entries, written so that the work is not optimised away.  Asynchronous; FMM_ERR_ARG for a
+ * bad kind or count.
+ * ------------------------------------------------------------------------------------------- */
+int fmm_probe_throughput(int kind, int iters, float* out, double* ops, void* stream);
+int fmm_probe_blocks(void);
+
+/* ---------------------------------------------------------------------------------------------
  * Parameter selector (no paper counterpart).  The paper picks the parameters by rule: p from the
  * tolerance through the error estimate of Section 3 (p ~ log TOL / log theta) and about 20 points
  * per leaf (end of Section 4).  The selector instead predicts the (levels, p) that meets a

@@ -74,6 +74,8 @@ def load_library(path: str = LIB_PATH):
             "fmm_set_m2l_kernel": (i32, [vp, i32]),
             "fmm_get_m2l_kernel": (i32, [vp]),
             "fmm_set_m2l_shape": (i32, [vp, i32, i32]),
+            "fmm_probe_throughput": (i32, [i32, i32, vp, ctypes.POINTER(ctypes.c_double), vp]),
+            "fmm_probe_blocks": (i32, []),
             "fmm_get_m2l_shape": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "fmm_selector_features": (i32, [vp, dbl, vp, vp]),
             "fmm_mlp_create": (i32, [i32, ctypes.POINTER(vp)]),
@@ -457,6 +459,38 @@ def fmm_get_m2l_kernel(tree) -> int:
     if rc < 0:
         _check(rc)
     return rc
+
+
+FMM_PROBE_FFMA, FMM_PROBE_LG2, FMM_PROBE_DFMA = 0, 1, 2
+
+
+def fmm_probe_blocks() -> int:
+    rc = load_library().fmm_probe_blocks()
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def fmm_probe_throughput(kind: int, iters: int = 4096, reps: int = 3) -> float:
+    """Measured throughput of one unit (operations per second; flop for the FMA probes): the
+    best of `reps` timed launches of the library's probe kernel on the current stream."""
+    lib = load_library()
+    nb = fmm_probe_blocks()
+    out = torch.empty(nb * 256, dtype=torch.float32, device="cuda")
+    ops = ctypes.c_double()
+    stream = torch.cuda.current_stream()
+    _check(lib.fmm_probe_throughput(int(kind), int(iters), ctypes.c_void_p(out.data_ptr()), ctypes.byref(ops),
+                                    _stream(None)))  # warm-up
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _check(lib.fmm_probe_throughput(int(kind), int(iters), ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.byref(ops), _stream(None)))
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) * 1e-3)
+    return ops.value / best
 
 
 def fmm_set_m2l_shape(tree, chunk: int = 0, stages: int = 0):

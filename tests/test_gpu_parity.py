@@ -233,3 +233,14 @@ def test_tree_export_refuses_short_buffers(fmmlib, cuda):
             fmmlib.fmm_tree_export(f.tree, rects=torch.empty((84, 4), dtype=torch.float64, device=cuda))
     finally:
         f.close()
+
+
+def test_throughput_probes(fmmlib, cuda):
+    # measured unit peaks: within a factor of the unit-count figures at up to the maximum clock
+    # (152 SMs x 2.07 GHz: 80.5 TFLOP/s FFMA, 5.0e12 lg2/s); binary64 far below binary32
+    ffma = fmmlib.fmm_probe_throughput(fmmlib.FMM_PROBE_FFMA, 1024)
+    lg2 = fmmlib.fmm_probe_throughput(fmmlib.FMM_PROBE_LG2, 256)
+    dfma = fmmlib.fmm_probe_throughput(fmmlib.FMM_PROBE_DFMA, 64)
+    assert 20e12 < ffma < 1.1 * 80.5e12
+    assert 0.5e12 < lg2 < 1.1 * 5.03e12
+    assert 0 < dfma < ffma / 4
