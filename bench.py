@@ -467,6 +467,129 @@ def profile_run(a):
         f.close()
 
 
+def bench_large(dev, steps=3, warmup=2):
+    """The large nonuniform workload: N = 2^24 points on 20 rings plus a Plummer-like core,
+    strengths U[0, 1], 9 levels (64 points per leaf), theta = 1/2, p = 30, tolerance 1e-10, with
+    the parent-level and role-exchange lists.  A step is tree, lists and evaluation (fmm_step) in
+    two precisions: every stage in binary64, and the split mode (binary64 expansions, binary32
+    near-field terms in float-float sums, far and near joined in binary64).  Errors against the
+    binary64 direct sum at 2,048 sampled targets; per-stage device times from one more step run
+    stage by stage."""
+    import torch
+    from paper_1006_2269_gb300 import fmm, workloads as W
+    w = W.LARGE_16M
+    c = W.large_16m_cloud()
+    x, y, q = (torch.as_tensor(a, device=dev) for a in (c.x, c.y, c.q))
+    n, tol = w.n, 1e-10
+    f = fmm.FMM(x, y, w.levels, w.theta, parents=True, exchange=True)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    tg = torch.as_tensor(W.sample_targets(n, w.n_check, W.SEED_BASE + 4 + 100), device=dev)
+    ref = torch.empty(tg.numel(), dtype=torch.float64, device=dev)
+    fmm.fmm_direct(x, y, q, tg, ref)
+    out = {"workload": w.name + ", TOL 1e-10, rings + Plummer core", "points": n, "tol": tol,
+           "n_check": int(tg.numel()), "lists": "parents+exchange (Section 4's optional optimisations)",
+           "steps": steps}
+    try:
+        for name, mode in (("binary64", fmm.FMM_MODE_FP64), ("split", fmm.FMM_MODE_SPLIT)):
+            def step():
+                fmm.fmm_step(f.tree, f.lists, x, y, w.theta, q, w.p, mode, phi, tol)
+
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            fmm.fmm_sync_status(f.tree, f.lists)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / steps
+            err = ((phi[tg] - ref).abs().max() / ref.abs().max()).item()
+            fmm.fmm_profile_read()
+            fmm.fmm_profile_enable(True)
+            fmm.fmm_build_tree(f.tree, x, y)
+            fmm.fmm_interaction_lists(f.tree, f.lists, w.theta)
+            fmm.fmm_evaluate(f.tree, f.lists, q, w.p, mode, phi, tol)
+            torch.cuda.synchronize()
+            fmm.fmm_profile_enable(False)
+            prof = fmm.fmm_profile_read()
+            fmm.fmm_sync_status(f.tree, f.lists)
+            out[name] = {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "rel_err": err,
+                         "met_tol": err <= tol, "stages_ms": {k: v[0] / v[1] for k, v in prof.items() if v[1]}}
+        out["precision"] = {"binary64": "every stage in binary64",
+                            "split": "binary64 P2M, M2M, M2L, L2L, L2P; binary32 near-field terms summed in "
+                                     "float-float; far and near joined in binary64"}
+        return out
+    finally:
+        f.close()
+
+
+def bench_selector(dev, x, y, q, tg, ref, steps, warmup, fixed_ms, tol=1e-6):
+    """The learned-parameter path on the benchmark cloud: every timed step computes the
+    selector's features on a probe tree (the library's feature kernel), runs the network and its
+    masked arg-max (fmm_select_params), reads the chosen (levels, p) back, then builds the lists
+    and evaluates at those parameters (the probe tree is reused when its levels were chosen,
+    otherwise a tree of the chosen levels is built).  Compared with the fixed parameters of the
+    benchmark workload; both errors against the same binary64 direct sums."""
+    import torch
+    from paper_1006_2269_gb300 import fmm
+    from paper_1006_2269_gb300 import selector as S
+    w_theta = 0.5
+    n = x.numel()
+    sel = S.Selector.load(device=dev)
+    L0 = S.probe_levels(n)
+    trees = {L0: fmm.FMM(x, y, L0, w_theta, parents=True)}
+    feats = torch.empty((1, 64), dtype=torch.float32, device=dev)
+    choice = torch.empty((1, 2), dtype=torch.int32, device=dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    chosen = {}
+
+    def sel_step():
+        probe = trees[L0]
+        fmm.fmm_build_tree(probe.tree, x, y)
+        fmm.fmm_selector_features(probe.tree, tol, feats)
+        fmm.fmm_select_params(sel.m, feats, choice)
+        L, p = (int(v) for v in choice[0].tolist())  # the host needs the choice: one sync
+        chosen[(L, p)] = chosen.get((L, p), 0) + 1
+        f = trees.get(L)
+        if f is None:  # first time only (warm-up): a tree of these levels
+            f = trees[L] = fmm.FMM(x, y, L, w_theta, parents=True)
+        if L != L0:
+            fmm.fmm_build_tree(f.tree, x, y)
+        fmm.fmm_interaction_lists(f.tree, f.lists, w_theta)
+        fmm.fmm_evaluate(f.tree, f.lists, q, p, fmm.FMM_MODE_MIXED, phi, tol)
+
+    try:
+        for _ in range(warmup):
+            sel_step()
+        torch.cuda.synchronize()
+        for f in trees.values():
+            fmm.fmm_sync_status(f.tree, f.lists)
+        chosen.clear()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            sel_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        err = ((phi[tg] - ref).abs().max() / ref.abs().max()).item()
+        L, p = max(chosen, key=chosen.get)  # the same choice every step on the same input
+        return {"tol": tol, "value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                "chosen": {"levels": L, "p": p}, "rel_err": err, "met_tol": err <= tol,
+                "fixed_parameters": {"levels": 8, "p": 20, "ms_per_step": fixed_ms, "value": n / (fixed_ms * 1e-3)},
+                "rule_parameters": dict(zip(("levels", "p"), S.fallback_params(n, tol))),
+                "note": "timed step = probe tree + features + network + arg-max + host read of the choice + "
+                        "lists + evaluation (plain launches); the fixed-parameter step is the headline's graph"}
+    finally:
+        for f in trees.values():
+            f.close()
+        sel.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,6 +600,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batched workload")
+    ap.add_argument("--no-selector", action="store_true", help="skip the learned-parameter sub-result")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2^24-point workload at TOL 1e-10")
     ap.add_argument("--blocks", default=None, metavar="M2L,NEAR",
                     help="grid sizes of the binary32 M2L and near-field kernels instead of the autotuner's "
                          "(e.g. to profile the plain run's launch configuration under a profiler)")
@@ -768,6 +893,10 @@ def main():
         "peaks_probed": dict(probed, ffma_tflops_derived=fp32_derived / 1e12, lg2_per_s_derived=mufu_derived),
         "clocks": dict(clk.summary(), window="~1 s of identical untimed steps, then the timed steps"),
     }
+    if not args.no_large:
+        out["large"] = bench_large(dev)
+    if not args.no_selector:
+        out["selector"] = bench_selector(dev, x, y, q, tg, ref, max(3, min(K, 10)), args.warmup, per_step)
     if not args.no_batched:
         out["batched"] = bench_batched(dev, max(3, min(K, 10)), args.warmup, sequential=(rank == 0),
                                        world=world, rank=rank)

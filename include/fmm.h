@@ -51,7 +51,9 @@ typedef enum {
 
 typedef enum {
     FMM_MODE_FP64 = 0,   /* every stage in binary64                                         */
-    FMM_MODE_MIXED = 1   /* binary32 expansions, near field and accumulation (see below)    */
+    FMM_MODE_MIXED = 1,  /* binary32 expansions, near field and accumulation (see below)    */
+    FMM_MODE_SPLIT = 2   /* binary64 expansions (P2M .. L2P); binary32 near-field terms in
+                            float-float sums; far and near joined in binary64 */
 } fmm_mode;
 
 typedef struct fmm_tree_s* fmm_tree;
@@ -61,7 +63,7 @@ typedef struct fmm_lists_s* fmm_lists;
  * Parameters of one evaluation.
  *   p      expansion order: coefficients k = 0..p (a_0 is the logarithmic term), 0 <= p <= 40.
  *          The relative error behaves like theta^(p+1)/(1-theta)^2 (Section 3).
- *   mode   FMM_MODE_FP64 or FMM_MODE_MIXED.
+ *   mode   FMM_MODE_FP64, FMM_MODE_MIXED or FMM_MODE_SPLIT.
  *   tol    requested relative tolerance (0 = none).  In FMM_MODE_MIXED a tol below 1e-7 is
  *          beyond what binary32 expansions can deliver (their rounding alone is about 1e-7 of
  *          the potential), so such a call runs every stage in binary64, exactly as
@@ -267,6 +269,17 @@ int fmm_validate(fmm_tree t, fmm_lists l, void* stream);
  * (1 .. 2^20) it gives up, records FMM_ERR_TIMEOUT in its status word and returns, leaving the
  * context usable.  Synchronises `stream`; returns FMM_ERR_TIMEOUT (the expected outcome). */
 int fmm_selftest_bounded_wait(int64_t tries, void* stream);
+
+/* Failure-path self-test of the work queues (no paper counterpart).  The upward pass (M2M of
+ * every level of every instance) runs as one persistent launch over a queue of items in
+ * dependency order; an item waits, bounded, until the items of the level below are counted done.
+ * This runs that launch with instance 0's item count of its deepest M2M level raised by one, so
+ * the level above waits for an item that is not in the queue: each such wait gives up after
+ * `tries` tries (1 .. 2^20) and records FMM_ERR_TIMEOUT, and the launch completes.  Scratch
+ * coefficients and status; the tree is unchanged and evaluates normally afterwards.  Needs an
+ * instance 0 of at least 3 levels; synchronises `stream`; returns FMM_ERR_TIMEOUT (the expected
+ * outcome). */
+int fmm_selftest_queue_timeout(fmm_tree t, int64_t tries, void* stream);
 
 void fmm_lists_destroy(fmm_lists l);
 

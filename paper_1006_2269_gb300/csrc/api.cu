@@ -96,7 +96,7 @@ void free_tree(fmm_tree t)
                     t->leaf_of, t->xs, t->ys, t->dxf, t->dyf, t->keys, t->vals, t->rs_counts,
                     t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->node_off, t->segs, t->status,
                     t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf, t->dinst, t->Lf0lo,
-                    t->pkf, t->qf, t->accf};
+                    t->pkf, t->qf, t->accf, t->qmem};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     sched_free_all(t);
@@ -115,7 +115,7 @@ void free_tree(fmm_tree t)
 void free_lists(fmm_lists l)
 {
     if (!l) return;
-    void* ptrs[] = {l->woff, l->soff, l->widx, l->wtgt, l->rowtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status,
+    void* ptrs[] = {l->woff, l->soff, l->widx, l->wrow, l->rowtgt, l->sidx, l->stgt, l->flags, l->tilecnt, l->status,
                     l->dlinst, l->tiledrop, l->tileswap, l->xoff, l->xidx, l->xtgt, l->p2p_items, l->p2p_pos,
                     l->p2p_tmp, l->p2p_zero};
     for (void* p : ptrs)
@@ -527,6 +527,14 @@ int fmm_selftest_bounded_wait(int64_t tries, void* stream)
     return bounded_wait_selftest(tries, (cudaStream_t)stream);
 }
 
+int fmm_selftest_queue_timeout(fmm_tree t, int64_t tries, void* stream)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (tries < 1 || tries > (int64_t(1) << 20)) return fail(FMM_ERR_ARG, "tries = %lld outside [1, 2^20]", (long long)tries);
+    GUARD(t->dev);
+    return queue_timeout_selftest(t, tries, (cudaStream_t)stream);
+}
+
 void fmm_lists_destroy(fmm_lists l)
 {
     if (!l) return;
@@ -540,7 +548,7 @@ int fmm_evaluate(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
     if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
     if (!t->built || !l->built) return fail(FMM_ERR_STATE, "tree or lists not built");
     if (prm->p < 0 || prm->p > 40) return fail(FMM_ERR_ARG, "p = %d outside [0, 40]", prm->p);
-    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED)
+    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED && prm->mode != FMM_MODE_SPLIT)
         return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
     GUARD(t->dev);
     return evaluate(t, l, q, *prm, phi, (cudaStream_t)stream);
@@ -553,7 +561,7 @@ int fmm_step(fmm_tree t, fmm_lists l, const double* x, const double* y, double t
     if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
     if (!(theta > 0.0 && theta < 1.0)) return fail(FMM_ERR_ARG, "theta = %g outside (0, 1)", theta);
     if (prm->p < 0 || prm->p > 40) return fail(FMM_ERR_ARG, "p = %d outside [0, 40]", prm->p);
-    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED)
+    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED && prm->mode != FMM_MODE_SPLIT)
         return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
     GUARD(t->dev);
     if (!t->side) {
@@ -582,7 +590,7 @@ int fmm_autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params* prm
     if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
     if (!t->built || !l->built) return fail(FMM_ERR_STATE, "tree or lists not built");
     if (prm->p < 0 || prm->p > 40) return fail(FMM_ERR_ARG, "p = %d outside [0, 40]", prm->p);
-    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED)
+    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED && prm->mode != FMM_MODE_SPLIT)
         return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
     GUARD(t->dev);
     return autotune(t, l, q, *prm, phi, (cudaStream_t)stream, m2l_blocks, p2p_blocks);
@@ -638,7 +646,7 @@ int fmm_evaluate_field(fmm_tree t, fmm_lists l, const double* q, const fmm_param
     if (l->tree != t) return fail(FMM_ERR_STATE, "lists were created for another tree");
     if (!t->built || !l->built) return fail(FMM_ERR_STATE, "tree or lists not built");
     if (prm->p < 0 || prm->p > 40) return fail(FMM_ERR_ARG, "p = %d outside [0, 40]", prm->p);
-    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED)
+    if (prm->mode != FMM_MODE_FP64 && prm->mode != FMM_MODE_MIXED && prm->mode != FMM_MODE_SPLIT)
         return fail(FMM_ERR_ARG, "unknown mode %d", prm->mode);
     GUARD(t->dev);
     return evaluate_field(t, l, q, *prm, fre, fim, (cudaStream_t)stream);

@@ -60,6 +60,18 @@ __device__ __forceinline__ int64_t weak_source(int64_t g, int32_t v)
     return (v & PARENT_FLAG) ? level_base(l - 1) + (v & ~PARENT_FLAG) : level_base(l) + v;
 }
 
+// Target boxes of weak entries.  Entries are sorted by target (CSR over the boxes of an
+// instance, woff[0] = woff[1] = 0); wrow holds the target of every eighth entry.  A reader of
+// consecutive entries takes the target of its first entry from wrow (any entry: from the eighth
+// before it) and steps through the offsets: while e >= woff[g + 1], g = g + 1.
+__device__ __forceinline__ int64_t wtarget_start(const int32_t* __restrict__ wrow,
+                                                 const int32_t* __restrict__ woff, int64_t e)
+{
+    int64_t g = wrow[e >> 3];
+    while (e >= woff[g + 1]) g++;
+    return g;
+}
+
 // The per-depth tables of ones_before are concatenated: depth d starts at 2^d - 1.
 __host__ __device__ inline int64_t ones_before_offset(int depth) { return (int64_t(1) << depth) - 1; }
 
@@ -173,8 +185,15 @@ struct SchedH {
     void* mem = nullptr;
 };
 
+// An item of the upward (M2M) or downward (L2L) work queue: boxes [b0, b0 + nb) of one level of
+// one instance (within-level indices; for the downward pass the parents whose children receive).
+struct QItem {
+    int32_t inst, level, b0, nb;
+};
+constexpr int QLEVELS = 64;  // per-instance stride of the queue counters
+
 struct LInst {            // list storage of one instance
-    int64_t w0, wcap;     // weak entries [w0, w0 + wcap)
+    int64_t w0, wcap;     // weak entries [w0, w0 + wcap) (w0 and wcap multiples of 8)
     int64_t s0, scap;     // strong entries [s0, s0 + scap)
     int64_t f0;           // candidate flags [f0, f0 + 16 scap + tile)
     int64_t c0;           // candidate tile counts
@@ -270,6 +289,10 @@ struct fmm_tree_s {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // lists done, points packed, near field done
     cudaEvent_t* ev_level = nullptr;  // [Lmax + 1]: geometry of a level complete
     int32_t* lb_bal = nullptr;
+    // the upward and downward passes as persistent launches over work queues (expand.cu)
+    void* qmem = nullptr;       // items up, items down, needs up, needs down, done counters, tickets
+    int32_t nq_up = 0, nq_dn = 0;
+    int64_t q_counter_bytes = 0;  // done counters and tickets, cleared before each pass
 };
 
 struct fmm_lists_s {
@@ -280,8 +303,8 @@ struct fmm_lists_s {
     int32_t* woff = nullptr;  // per instance [nbox + 1], local entry positions
     int32_t* soff = nullptr;
     int32_t* widx = nullptr;  // within-level index of the source box
-    int32_t* wtgt = nullptr;  // local box id of the target box of each weak entry
-    int32_t* rowtgt = nullptr;  // tensor-core M2L: target box of the first entry of each row chunk
+    int32_t* wrow = nullptr;    // target box (local id) of weak entries 0, 8, 16, ...: [w0 / 8 + k]
+    int32_t* rowtgt = nullptr;  // tensor-core M2L with rows of T % 8 != 0 entries: target of each row
     int32_t* sidx = nullptr;
     int32_t* stgt = nullptr;
     uint8_t* flags = nullptr;     // weak flag per candidate of the level being built
@@ -357,6 +380,9 @@ int direct(const double* x, const double* y, const double* q, int64_t n, const i
            int64_t m, double* phi, cudaStream_t s);
 int autotune(fmm_tree t, fmm_lists l, const double* q, const fmm_params& prm, double* phi,
              cudaStream_t s, int* m2l_blocks, int* p2p_blocks);
+// Work queues of the upward and downward passes (built once per tree, from its instances).
+int queues_make(fmm_tree t);
+int queue_timeout_selftest(fmm_tree t, int64_t limit, cudaStream_t s);
 
 // m2l_tc.cu: binary32 M2L on the tensor cores (Me, Le: [nbox][PS] float2)
 bool m2l_tc_supported(int P);

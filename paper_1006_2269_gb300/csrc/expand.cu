@@ -29,6 +29,7 @@
 #include <array>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -337,6 +338,55 @@ __device__ __forceinline__ void load_binom(T* B, int P)
     __syncthreads();
 }
 
+// M2M of parent box b of level l (one warp, one lane per output coefficient): the four children's
+// multipoles shifted to the parent.  B: binomial table, D: this warp's scratch of P values.  CG:
+// the children's coefficients are read from L2 (__ldcg), as in the queued upward pass, where other
+// blocks of the same launch wrote them.
+template <typename T, bool CG>
+__device__ __forceinline__ void m2m_box(int l, int64_t b, int P, int PS, const Geo<T>& geo, cx<T>* __restrict__ Me,
+                                        const T* B, cx<T>* D, int lane)
+{
+    const int64_t g = level_base(l) + b;
+    const T rp = geo.radius(g);
+    cx<T> acc[2] = {{0, 0}, {0, 0}};
+    for (int k = 0; k < 4; k++) {
+        const int64_t cg = level_base(l + 1) + 4 * b + k;
+        cx<T> wv = {0, 0};
+        T s = 0;
+        if (rp > 0) {
+            const T ir = (T)1 / rp;
+            wv = cscale(geo.diff(cg, g), ir);
+            s = geo.radius(cg) * ir;
+        }
+        for (int j = lane; j < P; j += 32) {
+            cx<T> m;
+            if constexpr (!CG) {
+                m = Me[cg * PS + j];
+            } else if constexpr (sizeof(T) == 8) {
+                const double2 v = __ldcg((const double2*)(Me + cg * PS + j));
+                m = {v.x, v.y};
+            } else {
+                const float2 v = __ldcg((const float2*)(Me + cg * PS + j));
+                m = {v.x, v.y};
+            }
+            D[j] = cscale(m, ipow(s, j));
+        }
+        __syncwarp();
+        for (int o = lane, si = 0; o < P; o += 32, si++) {
+            cx<T> h;
+            if (o == 0) {
+                h = D[0];
+            } else {
+                h = cscale(D[0], (T)-1 / (T)o);
+                for (int j = 1; j <= o; j++) h = cfma(h, wv, cscale(D[j], B[(o - 1) * P + (j - 1)]));
+            }
+            acc[si] = cadd(acc[si], h);
+        }
+        __syncwarp();
+    }
+    for (int o = lane, si = 0; o < P; o += 32, si++) Me[g * PS + o] = acc[si];
+}
+
 // ---- M2M: one warp per parent, one lane per output coefficient ----
 template <typename T>
 __global__ void k_m2m(Sched sc, const Inst* __restrict__ I, int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Me)
@@ -351,35 +401,128 @@ __global__ void k_m2m(Sched sc, const Inst* __restrict__ I, int l, int P, int PS
     T* B = (T*)smem;
     cx<T>* D = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
     load_binom(B, P);
-    for (int64_t b = (int64_t)z.rank * wpb + w; b < level_size(l); b += (int64_t)z.nb * wpb) {
-        const int64_t g = level_base(l) + b;
-        const T rp = geo.radius(g);
-        cx<T> acc[2] = {{0, 0}, {0, 0}};
-        for (int k = 0; k < 4; k++) {
-            const int64_t cg = level_base(l + 1) + 4 * b + k;
-            cx<T> wv = {0, 0};
-            T s = 0;
-            if (rp > 0) {
-                const T ir = (T)1 / rp;
-                wv = cscale(geo.diff(cg, g), ir);
-                s = geo.radius(cg) * ir;
-            }
-            for (int j = lane; j < P; j += 32) D[j] = cscale(Me[cg * PS + j], ipow(s, j));
-            __syncwarp();
-            for (int o = lane, si = 0; o < P; o += 32, si++) {
-                cx<T> h;
-                if (o == 0) {
-                    h = D[0];
-                } else {
-                    h = cscale(D[0], (T)-1 / (T)o);
-                    for (int j = 1; j <= o; j++) h = cfma(h, wv, cscale(D[j], B[(o - 1) * P + (j - 1)]));
+    for (int64_t b = (int64_t)z.rank * wpb + w; b < level_size(l); b += (int64_t)z.nb * wpb)
+        m2m_box<T, false>(l, b, P, PS, geo, Me, B, D, lane);
+}
+
+// ---- the upward (M2M) and downward (L2L) passes as persistent launches over work queues ----
+//
+// One launch does every level of every instance.  The queue lists items (QBOX boxes of one level
+// of one instance) in dependency order: the upward pass from the deepest M2M level up, the
+// downward pass from level 1 down.  Blocks take items by ticket (an atomic counter), so every item
+// an item waits for has been taken by a running block.  A level's items may start once the
+// instance's level below (upward) or above (downward) is complete: a counter per instance and
+// level counts finished items, and the first thread of the block waits for it to reach the
+// level's item count.  The wait is bounded: if it gives up, the status word gets the timeout bit,
+// the item's work is skipped (its counter still advances, so nothing waits on it forever) and the
+// evaluation reports FMM_ERR_TIMEOUT.
+template <typename T, bool CG>
+__device__ __forceinline__ void l2l_child(int l, int64_t c, int P, int PS, const Geo<T>& geo, cx<T>* __restrict__ Le,
+                                          float* __restrict__ L0lo, const T* Bn, cx<T>* B, int lane);
+
+constexpr int QBOX = 16;                              // boxes per queue item
+constexpr int64_t Q_SPIN_LIMIT = int64_t(1) << 21;    // tries of a dependency wait (about a second)
+constexpr int QBLOCKS_PER_SM = 8;
+
+template <typename T, bool UP>
+__global__ void __launch_bounds__(128) k_pass_queue(const QItem* __restrict__ items, int nitems,
+                                                    const int32_t* __restrict__ need, uint32_t* done,
+                                                    uint32_t* ticket, int64_t spin_limit, int32_t* status,
+                                                    const Inst* __restrict__ I, int P, int PS, Geo<T> geo0,
+                                                    cx<T>* __restrict__ E0, float* __restrict__ L0lo0)
+{
+    extern __shared__ unsigned char smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    T* Bt = (T*)smem;
+    cx<T>* D = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
+    load_binom(Bt, P);
+    __shared__ int it_s, ok_s;
+    for (;;) {
+        if (threadIdx.x == 0) it_s = (int)atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int it = it_s;
+        if (it >= nitems) break;  // block-uniform
+        const QItem q = items[it];
+        const Inst S = I[q.inst];
+        const int dep = UP ? q.level + 1 : q.level - 1;
+        const bool has_dep = UP ? dep < S.L : q.level >= 2;  // the leaves come from P2M, level 1 from M2L
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (has_dep) {
+                const int64_t slot = (int64_t)q.inst * QLEVELS + dep;
+                const uint32_t want = (uint32_t)need[slot];
+                int64_t spins = 0;
+                while (atomicAdd(done + slot, 0u) < want) {
+                    if (++spins > spin_limit) {
+                        atomicOr(status, ST_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
                 }
-                acc[si] = cadd(acc[si], h);
             }
-            __syncwarp();
+            __threadfence();
+            ok_s = ok;
         }
-        for (int o = lane, si = 0; o < P; o += 32, si++) Me[g * PS + o] = acc[si];
+        __syncthreads();
+        if (ok_s) {
+            const Geo<T> geo = geo0.shift(S.b0);
+            cx<T>* E = E0 + S.b0 * PS;
+            if (UP) {
+                for (int b = q.b0 + w; b < q.b0 + q.nb; b += wpb)
+                    m2m_box<T, true>(q.level, b, P, PS, geo, E, Bt, D, lane);
+            } else {
+                float* L0 = sizeof(T) == 4 ? L0lo0 + S.b0 : nullptr;
+                for (int c = 4 * q.b0 + w; c < 4 * (q.b0 + q.nb); c += wpb)
+                    l2l_child<T, true>(q.level, c, P, PS, geo, E, L0, Bt, D, lane);
+            }
+        }
+        __threadfence();  // every thread's coefficients of this item before its count
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(done + (int64_t)q.inst * QLEVELS + q.level, 1u);
     }
+}
+
+// Queue memory: items up, items down, needs up, needs down [n_inst][QLEVELS] (int32), then the
+// counters cleared before each pass: done up, done down [n_inst][QLEVELS], two tickets.
+struct QView {
+    QItem *up, *dn;
+    int32_t *need_up, *need_dn;
+    uint32_t *done_up, *done_dn, *tickets;
+};
+
+QView qview(fmm_tree t)
+{
+    const int64_t ni = t->n_inst;
+    QView v;
+    v.up = (QItem*)t->qmem;
+    v.dn = v.up + t->nq_up;
+    v.need_up = (int32_t*)(v.dn + t->nq_dn);
+    v.need_dn = v.need_up + ni * QLEVELS;
+    v.done_up = (uint32_t*)(v.need_dn + ni * QLEVELS);
+    v.done_dn = v.done_up + ni * QLEVELS;
+    v.tickets = v.done_dn + ni * QLEVELS;
+    return v;
+}
+
+template <typename T, bool UP>
+int launch_pass_queue(fmm_tree t, int P, int PS, const Geo<T>& geo, cx<T>* E, float* L0lo, cudaStream_t s,
+                      const int32_t* need = nullptr, int32_t* status = nullptr, int64_t spin_limit = Q_SPIN_LIMIT)
+{
+    const int nitems = UP ? t->nq_up : t->nq_dn;
+    if (nitems == 0) return 0;
+    const QView v = qview(t);
+    const size_t sm = ((P * P * sizeof(T) + 15) & ~15) + 4 * P * sizeof(cx<T>);
+    int dev = 0, sms = 0;
+    FMM_CUDA(cudaGetDevice(&dev));
+    FMM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::min<int64_t>(nitems, (int64_t)sms * QBLOCKS_PER_SM);
+    k_pass_queue<T, UP><<<grid, 128, sm, s>>>(UP ? v.up : v.dn, nitems, need ? need : (UP ? v.need_up : v.need_dn),
+                                             UP ? v.done_up : v.done_dn, v.tickets + (UP ? 0 : 1), spin_limit,
+                                             status ? status : t->status, t->dinst, P, PS, geo, E, L0lo);
+    note_launch();
+    FMM_LAUNCH_CHECK(UP ? "evaluate: M2M (queued)" : "evaluate: L2L (queued)");
+    return 0;
 }
 
 // ---- M2L over the flat weak-pair array of all levels ----
@@ -409,7 +552,7 @@ template <typename T, int PI>
 __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pairs(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                    int P, int PS, const int32_t* __restrict__ woff,
                                                    const int32_t* __restrict__ widx,
-                                                   const int32_t* __restrict__ wtgt, Geo<T> geo,
+                                                   const int32_t* __restrict__ wrow, Geo<T> geo,
                                                    const cx<T>* __restrict__ Me, cx<T>* __restrict__ Le,
                                                    float* __restrict__ L0lo)
 {
@@ -420,7 +563,7 @@ __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pai
     if (S.L < 1) return;
     woff += S.o0;
     widx += TL.w0;
-    wtgt += TL.w0;
+    wrow += TL.w0 >> 3;
     const int64_t wcap = TL.wcap, nbox = S.nbox;
     geo = geo.shift(S.b0);
     Me += S.b0 * PS;
@@ -441,8 +584,11 @@ __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pai
 #pragma unroll
         for (int j = 0; j < PI; j++) acc[j] = {0, 0};
         int64_t cur = -1;
+        // targets from the row table and the offsets (entries are sorted by target)
+        int64_t g = e0 < e1 ? wtarget_start(wrow, woff, e0) : 0;
+        int64_t gend = woff[g + 1];
         for (int64_t e = e0; e < e1; e++) {
-            const int64_t g = wtgt[e];
+            while (e >= gend) gend = woff[(++g) + 1];
             if (g != cur) {
                 if (cur >= 0) {
                     atomic_add_ff(&Le[cur * PS].re, &L0lo[cur], acc[0].re, lo0);
@@ -521,7 +667,7 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(Sched sc, const Inst* __re
                                                       const LInst* __restrict__ LIs, int P, int PS,
                                                       const int32_t* __restrict__ woff,
                                                       const int32_t* __restrict__ widx,
-                                                      const int32_t* __restrict__ wtgt, Geo<double> geo,
+                                                      const int32_t* __restrict__ wrow, Geo<double> geo,
                                                       const cx<double>* __restrict__ Me,
                                                       cx<double>* __restrict__ Le)
 {
@@ -532,7 +678,7 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(Sched sc, const Inst* __re
     if (S.L < 1) return;
     woff += S.o0;
     widx += TL.w0;
-    wtgt += TL.w0;
+    wrow += TL.w0 >> 3;
     const int64_t wcap = TL.wcap, nbox = S.nbox;
     geo = geo.shift(S.b0);
     Me += S.b0 * PS;
@@ -549,8 +695,10 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(Sched sc, const Inst* __re
         const int64_t e1 = min(e0 + M2L_CH, e_end);
         for (int j = 0; j < P; j++) A[j * nt + tid] = {0, 0};
         int64_t cur = -1;
+        int64_t g = e0 < e1 ? wtarget_start(wrow, woff, e0) : 0;
+        int64_t gend = woff[g + 1];
         for (int64_t e = e0; e < e1; e++) {
-            const int64_t g = wtgt[e];
+            while (e >= gend) gend = woff[(++g) + 1];
             if (g != cur) {
                 if (cur >= 0)
                     for (int j = 0; j < P; j++) {
@@ -609,6 +757,60 @@ __global__ void __launch_bounds__(64) k_m2l_pairs_f64(Sched sc, const Inst* __re
     }
 }
 
+// L2L into child c of level l + 1 (one warp): the parent's local expansion shifted to the child
+// and added to it.  Bn: binomial table, B: this warp's scratch.  CG: the parent's coefficients are
+// read from L2 (__ldcg), as in the queued downward pass, where another block of the launch wrote
+// them.
+template <typename T, bool CG>
+__device__ __forceinline__ void l2l_child(int l, int64_t c, int P, int PS, const Geo<T>& geo, cx<T>* __restrict__ Le,
+                                          float* __restrict__ L0lo, const T* Bn, cx<T>* B, int lane)
+{
+    const int64_t cg = level_base(l + 1) + c, pg = level_base(l) + (c >> 2);
+    const T rp = geo.radius(pg);
+    cx<T> wv = {0, 0};
+    T s = 0;
+    if (rp > 0) {
+        const T ir = (T)1 / rp;
+        wv = cscale(geo.diff(cg, pg), ir);
+        s = geo.radius(cg) * ir;
+    }
+    for (int j = lane; j < P; j += 32) {
+        if constexpr (!CG) {
+            B[j] = Le[pg * PS + j];
+        } else if constexpr (sizeof(T) == 8) {
+            const double2 v = __ldcg((const double2*)(Le + pg * PS + j));
+            B[j] = {v.x, v.y};
+        } else {
+            const float2 v = __ldcg((const float2*)(Le + pg * PS + j));
+            B[j] = {v.x, v.y};
+        }
+    }
+    __syncwarp();
+    for (int o = lane; o < P; o += 32) {
+        if constexpr (sizeof(T) == 4) {
+            if (o == 0) {
+                // child b_0 = parent b_0 + sum_{k >= 1} b_k w^k, added to the child's hi/lo pair
+                cx<T> h = {0, 0};
+                for (int k = P - 1; k >= 1; k--) h = cfma(h, wv, B[k]);
+                const cx<T> r = cmul(h, wv);
+                T hi = Le[cg * PS].re, lo = L0lo[cg] + (CG ? __ldcg(L0lo + pg) : L0lo[pg]);
+                two_sum(hi, lo, B[0].re);
+                two_sum(hi, lo, r.re);
+                const T sum = hi + lo;
+                L0lo[cg] = lo - (sum - hi);
+                Le[cg * PS].re = sum;
+                Le[cg * PS].im += B[0].im + r.im;
+                continue;
+            }
+        }
+        cx<T> h = cscale(B[P - 1], Bn[(P - 1) * P + o]);
+        for (int k = P - 2; k >= o; k--) h = cfma(h, wv, cscale(B[k], Bn[k * P + o]));
+        const cx<T> r = cscale(h, ipow(s, o));
+        Le[cg * PS + o] = cadd(Le[cg * PS + o], r);
+    }
+    __syncwarp();  // B is rewritten by the next box
+}
+
 // ---- L2L: one warp per child box of level l+1 ----
 template <typename T>
 __global__ void k_l2l(Sched sc, const Inst* __restrict__ I, int l, int P, int PS, Geo<T> geo, cx<T>* __restrict__ Le,
@@ -625,42 +827,8 @@ __global__ void k_l2l(Sched sc, const Inst* __restrict__ I, int l, int P, int PS
     T* Bn = (T*)smem;
     cx<T>* B = (cx<T>*)(smem + ((P * P * sizeof(T) + 15) & ~15)) + (size_t)w * P;
     load_binom(Bn, P);
-    for (int64_t c = (int64_t)z.rank * wpb + w; c < level_size(l + 1); c += (int64_t)z.nb * wpb) {
-        const int64_t cg = level_base(l + 1) + c, pg = level_base(l) + (c >> 2);
-        const T rp = geo.radius(pg);
-        cx<T> wv = {0, 0};
-        T s = 0;
-        if (rp > 0) {
-            const T ir = (T)1 / rp;
-            wv = cscale(geo.diff(cg, pg), ir);
-            s = geo.radius(cg) * ir;
-        }
-        for (int j = lane; j < P; j += 32) B[j] = Le[pg * PS + j];
-        __syncwarp();
-        for (int o = lane; o < P; o += 32) {
-            if constexpr (sizeof(T) == 4) {
-                if (o == 0) {
-                    // child b_0 = parent b_0 + sum_{k >= 1} b_k w^k, added to the child's hi/lo pair
-                    cx<T> h = {0, 0};
-                    for (int k = P - 1; k >= 1; k--) h = cfma(h, wv, B[k]);
-                    const cx<T> r = cmul(h, wv);
-                    T hi = Le[cg * PS].re, lo = L0lo[cg] + L0lo[pg];
-                    two_sum(hi, lo, B[0].re);
-                    two_sum(hi, lo, r.re);
-                    const T sum = hi + lo;
-                    L0lo[cg] = lo - (sum - hi);
-                    Le[cg * PS].re = sum;
-                    Le[cg * PS].im += B[0].im + r.im;
-                    continue;
-                }
-            }
-            cx<T> h = cscale(B[P - 1], Bn[(P - 1) * P + o]);
-            for (int k = P - 2; k >= o; k--) h = cfma(h, wv, cscale(B[k], Bn[k * P + o]));
-            const cx<T> r = cscale(h, ipow(s, o));
-            Le[cg * PS + o] = cadd(Le[cg * PS + o], r);
-        }
-        __syncwarp();  // B is rewritten by the next box
-    }
+    for (int64_t c = (int64_t)z.rank * wpb + w; c < level_size(l + 1); c += (int64_t)z.nb * wpb)
+        l2l_child<T, false>(l, c, P, PS, geo, Le, L0lo, Bn, B, lane);
 }
 
 // ---- role exchange at the finest level (Section 4) ----
@@ -1455,6 +1623,24 @@ __global__ void k_unpermute(Sched sc, const Inst* __restrict__ I, const int32_t*
 
 // binary32 path: phi = far + (ln 2 / 2) * near, combined in binary32 (the mixed path targets
 // tolerances >= 1e-7), written in input order.
+// The binary64 far field joined with a binary32 near field (float-float sums in log2 units), in
+// binary64, into input order.
+__global__ void k_combine64(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+                            const double* __restrict__ far, const float* __restrict__ nhi,
+                            const float* __restrict__ nlo, double* __restrict__ phi)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    perm += S.p0;
+    far += S.p0;
+    nhi += S.p0;
+    nlo += S.p0;
+    phi += S.p0;
+    const double scale = 0.34657359027997264;  // ln(2) / 2
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x)
+        phi[perm[i]] = far[i] + scale * ((double)nhi[i] + (double)nlo[i]);
+}
+
 __global__ void k_combine32(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                             const float* __restrict__ far, const float* __restrict__ farlo,
                             const float* __restrict__ nhi, const float* __restrict__ nlo,
@@ -1924,7 +2110,7 @@ int launch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<float> geo, const cx
 {
     if (t->s_m2l.blocks == 0) return 0;
     k_m2l_pairs<float, PI><<<t->s_m2l.blocks, 128, 0, s>>>(t->s_m2l.d, t->dinst, li->dlinst, P, PS, li->woff, li->widx,
-                                                li->wtgt, geo, Me, Le, t->Lf0lo); note_launch();
+                                                li->wrow, geo, Me, Le, t->Lf0lo); note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L");
     return 0;
 }
@@ -1951,7 +2137,7 @@ int dispatch_m2l(fmm_tree t, fmm_lists li, int P, int PS, Geo<double> geo, const
     FMM_CUDA(cudaFuncSetAttribute(k_m2l_pairs_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (t->s_m2l.blocks == 0) return 0;
     k_m2l_pairs_f64<<<t->s_m2l.blocks, NT, sm, s>>>(t->s_m2l.d, t->dinst, li->dlinst, P, PS, li->woff, li->widx,
-                                                    li->wtgt, geo, Me, Le); note_launch();
+                                                    li->wrow, geo, Me, Le); note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L");
     return 0;
 }
@@ -1975,8 +2161,11 @@ int p2p_items_ws(fmm_lists li)
 // phi (real part) and fim (imaginary part).
 template <typename T>
 int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStream_t s, double* fim = nullptr,
-        const StepSync* sync = nullptr)
+        const StepSync* sync = nullptr, bool near32 = false)
 {
+    // near32 (binary64 expansions only): the near field takes the binary32 kernels (float-float
+    // sums of binary32 terms) and is joined to the binary64 far field in binary64
+    near32 = near32 && sizeof(T) == 8 && fim == nullptr;
     // with sync the lists are being built on sync->side: wait for them before their first use
     bool lists_waited = false;
     auto wait_lists = [&]() -> int {
@@ -1991,6 +2180,12 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     const int PS = (P + 1) & ~1;
     int rc = alloc_ws(t, PS, f64);
     if (rc) return rc;
+    if (near32) {
+        if (!t->acc32 && cudaMalloc((void**)&t->acc32, 6 * 4 * (size_t)t->n) != cudaSuccess)
+            return fail(FMM_ERR_OOM, "accumulator");
+        if (!t->pk32 && cudaMalloc(&t->pk32, 16 * (size_t)t->n) != cudaSuccess)
+            return fail(FMM_ERR_OOM, "packed points");
+    }
     if (field) {
         if (f64 && !t->accf && cudaMalloc((void**)&t->accf, 16 * (size_t)t->n) != cudaSuccess)
             return fail(FMM_ERR_OOM, "field accumulator");
@@ -2014,7 +2209,6 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         minleaf = std::min(minleaf, ml);
     }
     const int WPB = 4;
-    const size_t bsm = ((P * P * sizeof(T) + 15) & ~15);
     Geo<T> geo;
     if constexpr (sizeof(T) == 8) geo = Geo<T>{t->centers, t->radii};
     else geo = Geo<T>{t->cen_hi, t->cen_lo, t->rad32};
@@ -2029,6 +2223,11 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         StageScope scope(FMM_STAGE_GATHER, s);
         k_pack<T><<<gpts, 256, 0, s>>>(spts, I, t->perm, q, t->xs, t->ys, t->dxf, t->dyf, pk, t->status);
         note_launch();
+        if (near32) {
+            k_pack<float><<<gpts, 256, 0, s>>>(spts, I, t->perm, q, t->xs, t->ys, t->dxf, t->dyf,
+                                               (Pk<float>*)t->pk32, t->status);
+            note_launch();
+        }
         FMM_CUDA(cudaMemsetAsync(Le, 0, (size_t)t->nbox * PS * sizeof(cx<T>), s));
         if (!f64) FMM_CUDA(cudaMemsetAsync(t->Lf0lo, 0, 4 * (size_t)t->nbox, s));
         FMM_LAUNCH_CHECK("evaluate: gather");
@@ -2043,13 +2242,23 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             note_launch();
             FMM_LAUNCH_CHECK("evaluate: P2M");
         }
+        // forests: every level of every instance in one persistent launch over the work queue;
+        // one instance: a launch per level (measured faster there: 0.11 against 0.20 ms for M2M,
+        // 0.13 against 0.32 ms for L2L on 2^20 points)
+        const bool queued = t->n_inst > 1;
+        const size_t bsm = ((P * P * sizeof(T) + 15) & ~15);
         {
             StageScope scope(FMM_STAGE_M2M, s);
-            for (int l = Lmax - 1; l >= 1; l--) {
-                k_m2m<T><<<t->s_m2m[l].blocks, 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
-                    t->s_m2m[l].d, I, l, P, PS, geo, Me); note_launch();
+            if (queued) {
+                FMM_CUDA(cudaMemsetAsync(qview(t).done_up, 0, (size_t)t->q_counter_bytes, s));
+                if ((rc = launch_pass_queue<T, true>(t, P, PS, geo, Me, nullptr, s))) return rc;
+            } else {
+                for (int l = Lmax - 1; l >= 1; l--) {
+                    k_m2m<T><<<t->s_m2m[l].blocks, 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
+                        t->s_m2m[l].d, I, l, P, PS, geo, Me); note_launch();
+                }
+                FMM_LAUNCH_CHECK("evaluate: M2M");
             }
-            FMM_LAUNCH_CHECK("evaluate: M2M");
         }
         if ((rc = wait_lists())) return rc;
         {
@@ -2067,11 +2276,15 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         }
         {
             StageScope scope(FMM_STAGE_L2L, s);
-            for (int l = 1; l < Lmax; l++) {
-                k_l2l<T><<<t->s_l2l[l].blocks, 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
-                    t->s_l2l[l].d, I, l, P, PS, geo, Le, t->Lf0lo); note_launch();
+            if (queued) {
+                if ((rc = launch_pass_queue<T, false>(t, P, PS, geo, Le, t->Lf0lo, s))) return rc;
+            } else {
+                for (int l = 1; l < Lmax; l++) {
+                    k_l2l<T><<<t->s_l2l[l].blocks, 32 * WPB, bsm + WPB * P * sizeof(cx<T>), s>>>(
+                        t->s_l2l[l].d, I, l, P, PS, geo, Le, t->Lf0lo); note_launch();
+                }
+                FMM_LAUNCH_CHECK("evaluate: L2L");
             }
-            FMM_LAUNCH_CHECK("evaluate: L2L");
         }
     }
     // role exchange (Section 4): P2L into the leaves' local expansions before they are evaluated
@@ -2139,21 +2352,24 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     // (binary32 path) it runs on the lists' stream while this one finishes the far field; its
     // accumulators (nhi, nlo) are not touched by the far-field kernels.  The binary64 near field
     // adds into the same accumulator as L2P and stays on this stream, before L2P.
-    const bool overlap = sync != nullptr && !f64;
+    const bool n32 = !f64 || near32;  // binary32 near field (float-float sums in nhi, nlo)
+    const bool overlap = sync != nullptr && n32;
     cudaStream_t ns = overlap ? sync->side : s;
     if (overlap) FMM_CUDA(cudaStreamWaitEvent(ns, sync->gathered, 0));
+    if (near32) FMM_CUDA(cudaMemsetAsync(t->acc, 0, 8 * (size_t)n, s));  // the far field's accumulator
     {
         StageScope near_scope(FMM_STAGE_NEAR, ns);
-        if (f64) FMM_CUDA(cudaMemsetAsync(t->acc, 0, 8 * (size_t)n, ns));
+        if (!n32) FMM_CUDA(cudaMemsetAsync(t->acc, 0, 8 * (size_t)n, ns));
         else FMM_CUDA(cudaMemsetAsync(nhi, 0, 2 * 4 * (size_t)n, ns));
         const unsigned gp2p = (unsigned)t->s_p2p.blocks;
         const Sched sp2p = t->s_p2p.d;
+        const Pk<float>* pk32 = (const Pk<float>*)t->pk32;
         // instances whose leaves hold at most SMALL_LEAF points take the leaf-pair kernel, the
         // others (if any) the general one; each kernel skips the instances of the other
-        const int small_leaf = f64 ? 32 : 64;
+        const int small_leaf = n32 ? 64 : 32;
         if (minleaf <= small_leaf) {
-            if constexpr (sizeof(T) == 4) {
-                k_p2p_f32<<<gp2p, 256, 0, ns>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk,
+            if (n32) {
+                k_p2p_f32<<<gp2p, 256, 0, ns>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk32,
                                                 t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
             } else {
                 int gs = 1;
@@ -2173,9 +2389,15 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
                                               li->p2p_items, total); note_launch();
             rc = scan_with_base(li->p2p_items, li->scap, li->p2p_zero, li->p2p_pos, li->p2p_tmp, ns);
             if (rc) return rc;
-            k_p2p_large<T><<<gp2p, 256, 0, ns>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt,
-                                                 t->leaf_begin, li->p2p_pos, total, t->status, pk, t->xs, t->ys,
-                                                 t->cen_hi, t->cen_lo, t->rad32, t->acc, nhi, nlo); note_launch();
+            if (n32)
+                k_p2p_large<float><<<gp2p, 256, 0, ns>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt,
+                                                         t->leaf_begin, li->p2p_pos, total, t->status, pk32, t->xs,
+                                                         t->ys, t->cen_hi, t->cen_lo, t->rad32, t->acc, nhi, nlo);
+            else
+                k_p2p_large<T><<<gp2p, 256, 0, ns>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt,
+                                                     t->leaf_begin, li->p2p_pos, total, t->status, pk, t->xs, t->ys,
+                                                     t->cen_hi, t->cen_lo, t->rad32, t->acc, nhi, nlo);
+            note_launch();
         }
         FMM_LAUNCH_CHECK("evaluate: near field");
     }
@@ -2193,7 +2415,9 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             note_launch();
         }
         if (overlap) FMM_CUDA(cudaStreamWaitEvent(s, sync->near_done, 0));
-        if (f64)
+        if (near32)
+            k_combine64<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->acc, nhi, nlo, phi);
+        else if (f64)
             k_unpermute<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->acc, phi);
         else
             k_combine32<<<gpts, 256, 0, s>>>(spts, I, t->perm, far32, farlo, nhi, nlo, phi);
@@ -2213,6 +2437,7 @@ int evaluate(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     const int P = prm.p + 1;
     // binary32 expansions carry a rounding error of about 1e-7 relative to the potential: a
     // tighter requested tolerance takes the binary64 path
+    if (prm.mode == FMM_MODE_SPLIT) return run<double>(t, li, q, P, phi, s, nullptr, sync, true);
     const bool f64 = prm.mode == FMM_MODE_FP64 || (prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR);
     if (f64) return run<double>(t, li, q, P, phi, s, nullptr, sync);
     return run<float>(t, li, q, P, phi, s, nullptr, sync);
@@ -2318,6 +2543,90 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     return 0;
 }
 
+int queues_make(fmm_tree t)
+{
+    const int ni = t->n_inst;
+    std::vector<QItem> up, dn;
+    std::vector<int32_t> nup((size_t)ni * QLEVELS, 0), ndn((size_t)ni * QLEVELS, 0);
+    for (int l = t->Lmax - 1; l >= 1; l--)
+        for (int i = 0; i < ni; i++)
+            if (l < t->hinst[i].L)
+                for (int64_t b0 = 0; b0 < level_size(l); b0 += QBOX) {
+                    up.push_back(QItem{i, l, (int32_t)b0, (int32_t)std::min<int64_t>(QBOX, level_size(l) - b0)});
+                    nup[(size_t)i * QLEVELS + l]++;
+                }
+    for (int l = 1; l < t->Lmax; l++)
+        for (int i = 0; i < ni; i++)
+            if (l < t->hinst[i].L)
+                for (int64_t b0 = 0; b0 < level_size(l); b0 += QBOX) {
+                    dn.push_back(QItem{i, l, (int32_t)b0, (int32_t)std::min<int64_t>(QBOX, level_size(l) - b0)});
+                    ndn[(size_t)i * QLEVELS + l]++;
+                }
+    t->nq_up = (int32_t)up.size();
+    t->nq_dn = (int32_t)dn.size();
+    t->q_counter_bytes = (int64_t)(2 * (size_t)ni * QLEVELS + 2) * sizeof(uint32_t);
+    const size_t bytes = (up.size() + dn.size()) * sizeof(QItem) + 2 * (size_t)ni * QLEVELS * sizeof(int32_t) +
+                         (size_t)t->q_counter_bytes;
+    if (cudaMalloc(&t->qmem, bytes) != cudaSuccess) return fail(FMM_ERR_OOM, "work queues");
+    const QView v = qview(t);
+    if (!up.empty()) FMM_CUDA(cudaMemcpy(v.up, up.data(), up.size() * sizeof(QItem), cudaMemcpyHostToDevice));
+    if (!dn.empty()) FMM_CUDA(cudaMemcpy(v.dn, dn.data(), dn.size() * sizeof(QItem), cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemcpy(v.need_up, nup.data(), nup.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemcpy(v.need_dn, ndn.data(), ndn.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemset(v.done_up, 0, (size_t)t->q_counter_bytes));
+    return 0;
+}
+
+// The queued upward pass with a dependency that never completes: instance 0's item count of its
+// deepest M2M level is raised by one in a copy of the needs, so the items of the level above wait
+// for an item that is not in the queue.  Each wait gives up after `limit` tries; the pass runs on
+// scratch coefficients (p = 3) and a scratch status word, which is read back.
+int queue_timeout_selftest(fmm_tree t, int64_t limit, cudaStream_t s)
+{
+    const Inst& S = t->hinst[0];
+    if (S.L < 3) return fail(FMM_ERR_ARG, "the self-test needs an instance of at least 3 levels");
+    int rc = ensure_tables();
+    if (rc) return rc;
+    const int P = 4, PS = 4;
+    const QView v = qview(t);
+    const size_t nneed = (size_t)t->n_inst * QLEVELS;
+    std::vector<int32_t> need(nneed);
+    cx<double>* E = nullptr;
+    int32_t* dneed = nullptr;
+    int32_t* st = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(E);
+        cudaFree(dneed);
+        cudaFree(st);
+    };
+    if (cudaMalloc((void**)&E, sizeof(cx<double>) * PS * (size_t)t->nbox) != cudaSuccess ||
+        cudaMalloc((void**)&dneed, 4 * nneed) != cudaSuccess || cudaMalloc((void**)&st, 4) != cudaSuccess) {
+        cleanup();
+        return fail(FMM_ERR_OOM, "self-test scratch");
+    }
+    int32_t h = 0;
+    rc = [&]() -> int {
+        FMM_CUDA(cudaStreamSynchronize(s));
+        FMM_CUDA(cudaMemcpy(need.data(), v.need_up, 4 * nneed, cudaMemcpyDeviceToHost));
+        need[(size_t)0 * QLEVELS + (S.L - 1)] += 1;  // a producer that is not in the queue
+        FMM_CUDA(cudaMemcpy(dneed, need.data(), 4 * nneed, cudaMemcpyHostToDevice));
+        FMM_CUDA(cudaMemsetAsync(E, 0, sizeof(cx<double>) * PS * (size_t)t->nbox, s));
+        FMM_CUDA(cudaMemsetAsync(st, 0, 4, s));
+        FMM_CUDA(cudaMemsetAsync(v.done_up, 0, (size_t)t->q_counter_bytes, s));
+        int r = launch_pass_queue<double, true>(t, P, PS, Geo<double>{t->centers, t->radii}, E, nullptr, s, dneed,
+                                                st, limit);
+        if (r) return r;
+        FMM_CUDA(cudaStreamSynchronize(s));
+        FMM_CUDA(cudaMemcpy(&h, st, 4, cudaMemcpyDeviceToHost));
+        return 0;
+    }();
+    cleanup();
+    if (rc) return rc;
+    return (h & ST_TIMEOUT) ? fail(FMM_ERR_TIMEOUT, "a queued item gave up waiting after %lld tries, as it should",
+                                   (long long)limit)
+                            : FMM_OK;
+}
+
 int evaluate_field(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, double* fre,
                    double* fim, cudaStream_t s)
 {
@@ -2331,7 +2640,7 @@ int evaluate_field(fmm_tree t, fmm_lists li, const double* q, const fmm_params& 
     }
     // the binary32 near-field kernel holds up to 64 targets per leaf; larger leaves, tolerances
     // below the binary32 floor and binary64 mode take the binary64 path
-    const bool f64 = prm.mode == FMM_MODE_FP64 || (prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR) || maxleaf > 64;
+    const bool f64 = prm.mode != FMM_MODE_MIXED || (prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR) || maxleaf > 64;
     if (f64) return run<double>(t, li, q, P, fre, s, fim);
     return run<float>(t, li, q, P, fre, s, fim);
 }

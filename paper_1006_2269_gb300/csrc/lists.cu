@@ -109,21 +109,21 @@ struct ListOpt {
 
 // One instance's view of the list arrays (pointers already offset to the instance).
 struct LView {
-    int32_t *woff, *soff, *widx, *wtgt, *sidx, *stgt;
+    int32_t *woff, *soff, *widx, *wrow, *sidx, *stgt;
     uint8_t* flags;
     uint32_t* tilecnt;
     int64_t wcap, scap;
 };
 
 __device__ __forceinline__ LView lview(const Inst& S, const LInst& T, int32_t* woff, int32_t* soff,
-                                       int32_t* widx, int32_t* wtgt, int32_t* sidx, int32_t* stgt,
+                                       int32_t* widx, int32_t* wrow, int32_t* sidx, int32_t* stgt,
                                        uint8_t* flags, uint32_t* tilecnt)
 {
     LView v;
     v.woff = woff + S.o0;
     v.soff = soff + S.o0;
     v.widx = widx + T.w0;
-    v.wtgt = wtgt + T.w0;
+    v.wrow = wrow + (T.w0 >> 3);
     v.sidx = sidx + T.s0;
     v.stgt = stgt + T.s0;
     v.flags = flags + T.f0;
@@ -135,14 +135,14 @@ __device__ __forceinline__ LView lview(const Inst& S, const LInst& T, int32_t* w
 
 #define LIST_ARGS                                                                                 \
     const Inst *__restrict__ I, const LInst *__restrict__ LIs, int32_t *woff, int32_t *soff,     \
-        int32_t *widx, int32_t *wtgt, int32_t *sidx, int32_t *stgt, uint8_t *flags,               \
+        int32_t *widx, int32_t *wrow, int32_t *sidx, int32_t *stgt, uint8_t *flags,               \
         uint32_t *tilecnt
-#define LIST_VIEW(i) lview(I[i], LIs[i], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt)
+#define LIST_VIEW(i) lview(I[i], LIs[i], woff, soff, widx, wrow, sidx, stgt, flags, tilecnt)
 
 __global__ void k_lists_root(LIST_ARGS, int n_inst)
 {
     for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
-        const LView v = lview(I[i], LIs[i], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt);
+        const LView v = lview(I[i], LIs[i], woff, soff, widx, wrow, sidx, stgt, flags, tilecnt);
         v.woff[0] = 0;
         v.woff[1] = 0;
         v.soff[0] = 0;
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, ListOpt 
                     const int64_t pos = W0 + wpre;
                     if (pos < v.wcap) {
                         v.widx[pos] = f[j] == 2 ? (int32_t)(c >> 2) | PARENT_FLAG : (int32_t)c;
-                        v.wtgt[pos] = (int32_t)(base + b);
+                        if ((pos & 7) == 0) v.wrow[pos >> 3] = (int32_t)(base + b);
                     }
                 } else {
                     const int64_t pos = S0 + spre;
@@ -498,7 +498,7 @@ __global__ void k_lists_check(LIST_ARGS, int n_inst, const int32_t* xoff, int32_
 {
     for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
         const Inst& S = I[i];
-        const LView v = lview(S, LIs[i], woff, soff, widx, wtgt, sidx, stgt, flags, tilecnt);
+        const LView v = lview(S, LIs[i], woff, soff, widx, wrow, sidx, stgt, flags, tilecnt);
         const int32_t W = v.woff[S.nbox], Sx = v.soff[S.nbox];
         const int32_t X = xoff ? xoff[S.o0 + S.nbox] : 0;
         if ((int64_t)W > v.wcap || (int64_t)Sx > v.scap || W == INT32_MAX || Sx == INT32_MAX ||
@@ -512,6 +512,7 @@ __global__ void k_lists_check(LIST_ARGS, int n_inst, const int32_t* xoff, int32_
 int64_t lists_flag_bytes(int64_t scap) { return 16 * scap + LTILE; }
 int64_t lists_tile_words(int64_t scap) { return (16 * scap + LTILE - 1) / LTILE + 1; }
 
+
 // Capacities are split over the instances in proportion to their box counts (at least 16 weak and
 // 8 strong entries per box).
 int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int64_t* strong_capacity)
@@ -522,7 +523,7 @@ int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int
     int64_t w0 = 0, s0 = 0, f0 = 0, c0 = 0;
     for (int i = 0; i < ni; i++) {
         LInst& T = l->hlinst[i];
-        T.wcap = weak_capacity[i];
+        T.wcap = (weak_capacity[i] + 7) & ~int64_t(7);  // rows of eight entries (wrow)
         T.scap = strong_capacity[i];
         T.w0 = w0;
         T.s0 = s0;
@@ -541,7 +542,7 @@ int lists_alloc(fmm_tree t, fmm_lists l, const int64_t* weak_capacity, const int
               cudaMalloc((void**)&l->woff, 4 * noff) == cudaSuccess &&
               cudaMalloc((void**)&l->soff, 4 * noff) == cudaSuccess &&
               cudaMalloc((void**)&l->widx, 4 * std::max<int64_t>(w0, 1)) == cudaSuccess &&
-              cudaMalloc((void**)&l->wtgt, 4 * std::max<int64_t>(w0, 1)) == cudaSuccess &&
+              cudaMalloc((void**)&l->wrow, 4 * (w0 / 8 + 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->rowtgt, 4 * std::max<int64_t>(w0, 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->sidx, 4 * std::max<int64_t>(s0, 1)) == cudaSuccess &&
               cudaMalloc((void**)&l->stgt, 4 * std::max<int64_t>(s0, 1)) == cudaSuccess &&
@@ -560,7 +561,7 @@ int lists_build(fmm_tree t, fmm_lists li, double theta, cudaStream_t s, const cu
     StageScope scope(FMM_STAGE_LISTS, s);
     const bool par = (li->mode & FMM_LISTS_PARENTS) != 0, swp = (li->mode & FMM_LISTS_EXCHANGE) != 0;
     const ListOpt opt{li->tiledrop, li->tileswap, li->xoff, li->xidx, li->xtgt};
-#define LARGS t->dinst, li->dlinst, li->woff, li->soff, li->widx, li->wtgt, li->sidx, li->stgt, li->flags, li->tilecnt
+#define LARGS t->dinst, li->dlinst, li->woff, li->soff, li->widx, li->wrow, li->sidx, li->stgt, li->flags, li->tilecnt
     // with level_ready this stream runs beside the tree build: event 0 also orders these writes
     // after the earlier work of the tree's stream (which may still read the previous lists)
     if (level_ready) FMM_CUDA(cudaStreamWaitEvent(s, level_ready[0], 0));

@@ -235,7 +235,7 @@ __device__ __forceinline__ float tf32_hi(float x)
 // registers (four CTAs per SM) measured slower.
 template <int PI, bool EXACT, bool PIPE>
 __global__ void __launch_bounds__(TC_ROWS, (PI <= 21 && !PIPE) ? 3 : 2) k_m2l_tc(Sched sc, const Inst* __restrict__ I,
-                                                    const LInst* __restrict__ LIs, int Prt, int PS, int T,
+                                                    const LInst* __restrict__ LIs, int Prt, int PS, int T, bool rdirect,
                                                     const int32_t* __restrict__ woff,
                                                     const int32_t* __restrict__ widx,
                                                     const int32_t* __restrict__ rowtgt,
@@ -354,7 +354,10 @@ __global__ void __launch_bounds__(TC_ROWS, (PI <= 21 && !PIPE) ? 3 : 2) k_m2l_tc
     auto row_ahead = [&](int c) {
         const int e = row_start(c);
         if (c < nchunk && e < e_end) {
-            rt_next = __ldg(rowtgt + w0 + c * TC_ROWS + t);
+            // row k's first target: the list's every-eighth table when T is a multiple of 8,
+            // else the table made for this launch
+            const int64_t k = (int64_t)c * TC_ROWS + t;
+            rt_next = rdirect ? __ldg(rowtgt + (w0 >> 3) + ((k * T) >> 3)) : __ldg(rowtgt + w0 + k);
             w_next = __ldg(widx + w0 + e);
         }
     };
@@ -672,10 +675,14 @@ int launch3(fmm_tree t, fmm_lists li, int P, int PS, const void* Me, void* Le, c
     using Lay = TcLayout<(PI + 7) / 8 * 8>;
     FMM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PI, EXACT, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
     const int T = t->tune_m2l_chunk > 0 ? t->tune_m2l_chunk : TC_CHUNK_DEFAULT;
-    k_row_targets<<<t->s_m2l.blocks, 256, 0, s>>>(t->s_m2l.d, t->dinst, li->dlinst, T, li->woff, li->rowtgt);
-    note_launch();
+    const bool rdirect = T % 8 == 0;  // rows start at list rows of eight entries
+    if (!rdirect) {
+        k_row_targets<<<t->s_m2l.blocks, 256, 0, s>>>(t->s_m2l.d, t->dinst, li->dlinst, T, li->woff, li->rowtgt);
+        note_launch();
+    }
     k_m2l_tc<PI, EXACT, PIPE><<<t->s_m2l.blocks, TC_ROWS, Lay::SMEM, s>>>(
-        t->s_m2l.d, t->dinst, li->dlinst, P, PS, T, li->woff, li->widx, li->rowtgt, t->cen_hi, t->cen_lo, t->rad32,
+        t->s_m2l.d, t->dinst, li->dlinst, P, PS, T, rdirect, li->woff, li->widx, rdirect ? li->wrow : li->rowtgt,
+        t->cen_hi, t->cen_lo, t->rad32,
         (const float2*)Me, (float*)Le, t->Lf0lo, t->status);
     note_launch();
     FMM_LAUNCH_CHECK("evaluate: M2L (tensor cores)");

@@ -1102,7 +1102,8 @@ int tree_alloc(fmm_tree t, int n_inst, const int64_t* ns, const int* Ls)
     FMM_CUDA(cudaMemcpy(t->node_off, off_all.data(), 4 * off_all.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemset(t->status, 0, 4));
     if ((rc = tree_kernel_setup())) return rc;
-    return sched_all(t);
+    if ((rc = sched_all(t))) return rc;
+    return queues_make(t);
 }
 
 // The block-local split's dynamic shared memory is above the default limit of a launch; the

@@ -115,7 +115,7 @@ __global__ void k_val_offsets(Sched sc, const Inst* __restrict__ I, const LInst*
 // checked by k_val_offsets first; entries beyond the capacity are not read.  schedule: points
 __global__ void k_val_entries(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                               const int32_t* __restrict__ woff, const int32_t* __restrict__ widx,
-                              const int32_t* __restrict__ wtgt, const int32_t* __restrict__ soff,
+                              const int32_t* __restrict__ wrow, const int32_t* __restrict__ soff,
                               const int32_t* __restrict__ sidx, const int32_t* __restrict__ stgt,
                               const int32_t* __restrict__ xoff, const int32_t* __restrict__ xidx,
                               const int32_t* __restrict__ xtgt, const int32_t* word_in, int32_t* word)
@@ -127,15 +127,23 @@ __global__ void k_val_entries(Sched sc, const Inst* __restrict__ I, const LInst*
     woff += S.o0;
     soff += S.o0;
     widx += T.w0;
-    wtgt += T.w0;
+    wrow += T.w0 >> 3;
     sidx += T.s0;
     stgt += T.s0;
     const int64_t i0 = (int64_t)z.rank * blockDim.x + threadIdx.x, di = (int64_t)z.nb * blockDim.x;
     int32_t bad = 0;
     const int64_t nw = min((int64_t)woff[S.nbox], T.wcap), ns = min((int64_t)soff[S.nbox], T.scap);
     for (int64_t e = i0; e < nw; e += di) {
-        const int64_t g = wtgt[e];
-        if (g < 1 || g >= S.nbox || e < woff[g] || e >= woff[g + 1]) {
+        // the target from the offsets (largest g with woff[g] <= e); every eighth entry's target
+        // in the row table must agree, since the M2L kernels start their walks there
+        int64_t lo = 0, hi = S.nbox;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (woff[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        const int64_t g = lo;
+        if (g < 1 || g >= S.nbox || ((e & 7) == 0 && wrow[e >> 3] != g)) {
             bad |= V_WEAK;
             continue;
         }
@@ -174,7 +182,7 @@ __global__ void k_val_entries(Sched sc, const Inst* __restrict__ I, const LInst*
 
 // targets of imported entries from the offsets; schedule: points (boxes)
 __global__ void k_fill_targets(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs, int only,
-                               const int32_t* __restrict__ woff, int32_t* __restrict__ wtgt,
+                               const int32_t* __restrict__ woff, int32_t* __restrict__ wrow,
                                const int32_t* __restrict__ soff, int32_t* __restrict__ stgt)
 {
     const Slot z = slot_of(sc);
@@ -183,12 +191,12 @@ __global__ void k_fill_targets(Sched sc, const Inst* __restrict__ I, const LInst
     const LInst T = LIs[z.i];
     woff += S.o0;
     soff += S.o0;
-    wtgt += T.w0;
+    wrow += T.w0 >> 3;
     stgt += T.s0;
     // imported offsets are not trusted yet: every write stays within [0, capacity)
     for (int64_t g = (int64_t)z.rank * blockDim.x + threadIdx.x; g < S.nbox; g += (int64_t)z.nb * blockDim.x) {
         const int64_t w1 = min((int64_t)woff[g + 1], T.wcap), s1 = min((int64_t)soff[g + 1], T.scap);
-        for (int64_t e = max((int64_t)woff[g], (int64_t)0); e < w1; e++) wtgt[e] = (int32_t)g;
+        for (int64_t e = (max((int64_t)woff[g], (int64_t)0) + 7) & ~int64_t(7); e < w1; e += 8) wrow[e >> 3] = (int32_t)g;
         for (int64_t e = max((int64_t)soff[g], (int64_t)0); e < s1; e++) stgt[e] = (int32_t)g;
     }
 }
@@ -215,7 +223,7 @@ int validate(fmm_tree t, fmm_lists l, cudaStream_t s)
             note_launch();
             // the entry check reads the offsets' verdict from a copy made after k_val_offsets
             FMM_CUDA(cudaMemcpyAsync(word + 1, word, 4, cudaMemcpyDeviceToDevice, s));
-            k_val_entries<<<gp, 256, 0, s>>>(sp, t->dinst, l->dlinst, l->woff, l->widx, l->wtgt, l->soff, l->sidx,
+            k_val_entries<<<gp, 256, 0, s>>>(sp, t->dinst, l->dlinst, l->woff, l->widx, l->wrow, l->soff, l->sidx,
                                              l->stgt, x ? l->xoff : nullptr, l->xidx, l->xtgt, word + 1, word);
             note_launch();
         }
@@ -249,7 +257,7 @@ int lists_import(fmm_lists l, int i, const int32_t* woff, const int32_t* widx, c
     FMM_CUDA(cudaMemcpyAsync(l->soff + S.o0, soff, 4 * (S.nbox + 1), cudaMemcpyDeviceToDevice, s));
     if (nw) FMM_CUDA(cudaMemcpyAsync(l->widx + T.w0, widx, 4 * (size_t)nw, cudaMemcpyDeviceToDevice, s));
     if (ns) FMM_CUDA(cudaMemcpyAsync(l->sidx + T.s0, sidx, 4 * (size_t)ns, cudaMemcpyDeviceToDevice, s));
-    k_fill_targets<<<(unsigned)t->s_pts.blocks, 256, 0, s>>>(t->s_pts.d, t->dinst, l->dlinst, i, l->woff, l->wtgt,
+    k_fill_targets<<<(unsigned)t->s_pts.blocks, 256, 0, s>>>(t->s_pts.d, t->dinst, l->dlinst, i, l->woff, l->wrow,
                                                              l->soff, l->stgt);
     note_launch();
     FMM_LAUNCH_CHECK("lists import");

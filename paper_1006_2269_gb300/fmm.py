@@ -32,6 +32,7 @@ FMM_ERR_DEGENERATE = -9
 
 FMM_MODE_FP64 = 0
 FMM_MODE_MIXED = 1
+FMM_MODE_SPLIT = 2
 
 
 class FMMError(RuntimeError):
@@ -96,6 +97,7 @@ def load_library(path: str = LIB_PATH):
             "fmm_lists_import": (i32, [vp, i32, vp, vp, vp, vp, vp]),
             "fmm_validate": (i32, [vp, vp, vp]),
             "fmm_selftest_bounded_wait": (i32, [i64, vp]),
+            "fmm_selftest_queue_timeout": (i32, [vp, i64, vp]),
             "fmm_step": (i32, [vp, vp, vp, vp, dbl, vp, ctypes.POINTER(fmm_params), vp, vp]),
             "fmm_build_tree_uniform": (i32, [vp, vp, vp, vp, vp]),
             "fmm_lists_export_exchange": (i32, [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]),
@@ -329,6 +331,12 @@ def fmm_lists_import(lists, i: int, woff, widx, soff, sidx, stream=None):
     _check(load_library().fmm_lists_import(lists, int(i), _dev(woff, torch.int32, None, "woff"),
                                            _dev(widx, torch.int32, None, "widx"), _dev(soff, torch.int32, None, "soff"),
                                            _dev(sidx, torch.int32, None, "sidx"), _stream(stream)))
+
+
+def fmm_selftest_queue_timeout(tree, tries: int = 4096, stream=None):
+    """The queued upward pass with a producer missing from the queue: raises
+    FMMError(FMM_ERR_TIMEOUT) when the bounded waits give up, as designed."""
+    _check(load_library().fmm_selftest_queue_timeout(tree, int(tries), _stream(stream)))
 
 
 def fmm_selftest_bounded_wait(tries: int = 4096, stream=None):
@@ -652,7 +660,7 @@ class FMM:
 
     def evaluate(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6, out=None,
                  check: bool = True):
-        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED, "split": FMM_MODE_SPLIT}.get(mode, mode)
         phi = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
         fmm_evaluate(self.tree, self.lists, q, p, m, phi, tol)
         if check:
@@ -661,7 +669,7 @@ class FMM:
 
     def evaluate_field(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6, check: bool = True):
         """The complex field F_i = sum_{j != i} -q_j / (z_i - z_j) (complex128 CUDA tensor)."""
-        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED, "split": FMM_MODE_SPLIT}.get(mode, mode)
         fre = torch.empty(self.n, dtype=torch.float64, device=self.device)
         fim = torch.empty(self.n, dtype=torch.float64, device=self.device)
         fmm_evaluate_field(self.tree, self.lists, q, p, m, fre, fim, tol)
@@ -773,7 +781,7 @@ class FMMBatch:
 
     def evaluate(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6, out=None,
                  check: bool = True):
-        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED, "split": FMM_MODE_SPLIT}.get(mode, mode)
         phi = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
         fmm_evaluate(self.tree, self.lists, q, p, m, phi, tol)
         if check:
@@ -781,7 +789,7 @@ class FMMBatch:
         return phi
 
     def evaluate_field(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6, check: bool = True):
-        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED, "split": FMM_MODE_SPLIT}.get(mode, mode)
         fre = torch.empty(self.n, dtype=torch.float64, device=self.device)
         fim = torch.empty(self.n, dtype=torch.float64, device=self.device)
         fmm_evaluate_field(self.tree, self.lists, q, p, m, fre, fim, tol)
@@ -790,7 +798,7 @@ class FMMBatch:
         return torch.complex(fre, fim)
 
     def autotune(self, q, p: int, mode: str | int = "mixed", tol: float = 1e-6):
-        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED}.get(mode, mode)
+        m = {"fp64": FMM_MODE_FP64, "mixed": FMM_MODE_MIXED, "split": FMM_MODE_SPLIT}.get(mode, mode)
         phi = torch.empty(self.n, dtype=torch.float64, device=self.device)
         return fmm_autotune(self.tree, self.lists, q, p, m, phi, tol)
 

@@ -133,16 +133,23 @@ def run_table(inst: Instance, levels, ps, tol: float, reps: int = 2):
     return out
 
 
-def label(table, tol: float) -> int:
-    """Class of the fastest run that meets tol (the most accurate run if none does)."""
-    ok = [r for r in table if r[3] <= tol]
+LABEL_MARGIN = 0.5  # a label must meet margin * tol: neighbouring point sets then still meet tol
+
+
+def label(table, tol: float, margin: float = 1.0) -> int:
+    """Class of the fastest run whose error is at most margin * tol (the most accurate run if
+    none is)."""
+    ok = [r for r in table if r[3] <= margin * tol]
     best = min(ok, key=lambda r: r[2]) if ok else min(table, key=lambda r: r[3])
     return class_of(best[0], best[1])
 
 
-def candidate_levels(n: int):
+def candidate_levels(n: int, f64: bool = False):
+    """Level counts tried for a label: round(log4(N / 32)) - 2 .. + 1; the binary64 path (tight
+    tolerances) skips the coarsest, whose large leaves make its near field by far the slowest run
+    and never the fastest."""
     Lc = int(round(math.log(n / 32.0) / math.log(4.0)))
-    return [L for L in range(Lc - 2, Lc + 2) if LMIN <= L <= min(LMAX, max_levels(n))]
+    return [L for L in range(Lc - (1 if f64 else 2), Lc + 2) if LMIN <= L <= min(LMAX, max_levels(n))]
 
 
 def candidate_ps(tol: float):
@@ -293,28 +300,37 @@ def make_cloud(i: int, seed: int, nmin: float, nmax: float):
     return W.rings_plummer(n, s)
 
 
-def generate(count: int, seed: int, dev, nmin: float = 1e4, nmax: float = 2e5, tols=TOLS, log=None):
-    """Features X[count * len(tols)][64], labels y and the run tables, from `count` point sets."""
+def generate(count: int, seed: int, dev, nmin: float = 1e4, nmax: float = 1e6, tols=TOLS, log=None,
+             time_budget: float | None = None, save=None):
+    """Features X[count * len(tols)][64], labels y and the run tables, from `count` point sets (or
+    as many as `time_budget` seconds allow); save(X, y) is called after every tenth set."""
     X, y, tables = [], [], []
+    t0 = time.time()
     for i in range(count):
+        if time_budget is not None and time.time() - t0 > time_budget:
+            if log:
+                log(f"time budget reached after {i} point sets")
+            break
         c = make_cloud(i, seed, nmin, nmax)
         inst = Instance(c, dev, seed=seed * 31 + i)
-        levels = candidate_levels(inst.n)
         tab = {}
         for tol in tols:
             key = "f64" if tol < MIXED_FLOOR else "mixed"
             if key not in tab:
-                tab[key] = run_table(inst, levels, candidate_ps(tol), tol)
+                tab[key] = run_table(inst, candidate_levels(inst.n, key == "f64"), candidate_ps(tol), tol,
+                                     reps=1 if key == "f64" else 2)
             f = Selector.features(inst.x, inst.y, tol).cpu().numpy()
             X.append(f)
-            y.append(label(tab[key], tol))
+            y.append(label(tab[key], tol, LABEL_MARGIN))
         tables.append({"n": inst.n, "kind": c.name, "tables": tab})
         if log:
             log(f"instance {i}: n={inst.n} {c.name} labels={[params_of(v) for v in y[-len(tols):]]}")
+        if save is not None and (i + 1) % 10 == 0:
+            save(np.array(X, np.float32), np.array(y, np.int32))
     return np.array(X, np.float32), np.array(y, np.int32), tables
 
 
-def gain(selector: Selector, count: int, seed: int, dev, nmin: float = 1e4, nmax: float = 2e5, tols=TOLS):
+def gain(selector: Selector, count: int, seed: int, dev, nmin: float = 1e4, nmax: float = 1e6, tols=TOLS):
     """Selector against the fallback rule on fresh point sets: per case the chosen parameters,
     their run time and error; totals over all cases."""
     cases = []
@@ -349,18 +365,25 @@ def main(argv=None):
     tr = sub.add_parser("train", help="generate runs, train, report the gain, write the weights")
     tr.add_argument("--instances", type=int, default=300)
     tr.add_argument("--test-instances", type=int, default=30)
-    tr.add_argument("--nmax", type=float, default=2e5)
+    tr.add_argument("--nmax", type=float, default=1e6)
     tr.add_argument("--epochs", type=int, default=400)
     tr.add_argument("--seed", type=int, default=1)
     tr.add_argument("--out", default=WEIGHTS)
     tr.add_argument("--report", default=None)
+    tr.add_argument("--time-budget", type=float, default=None,
+                    help="seconds of data generation at most (the point sets made by then are used)")
+    tr.add_argument("--data", default=None, help="npz file the features and labels are saved to as they grow")
     a = ap.parse_args(argv)
     from . import build
     build.build()
     fmm.load_library()
     dev = torch.device("cuda", 0)
     t0 = time.time()
-    X, y, tables = generate(a.instances, a.seed, dev, nmax=a.nmax, log=print)
+    save = (lambda X_, y_: np.savez(a.data, X=X_, y=y_)) if a.data else None
+    X, y, tables = generate(a.instances, a.seed, dev, nmax=a.nmax, log=lambda m: print(m, flush=True),
+                            time_budget=a.time_budget, save=save)
+    if save is not None:
+        save(X, y)
     t_gen = time.time() - t0
     nval = max(1, len(y) // 10)
     perm = np.random.default_rng(a.seed).permutation(len(y))
@@ -370,7 +393,8 @@ def main(argv=None):
     acc_tr, acc_va = sel.accuracy(X[trn], y[trn]), sel.accuracy(X[va], y[va])
     g = gain(sel, a.test_instances, a.seed + 1000, dev, nmax=a.nmax)
     meta = {
-        "instances": a.instances, "samples": int(len(y)), "tolerances": list(TOLS), "theta": THETA,
+        "instances": int(len(y)) // len(TOLS), "samples": int(len(y)), "tolerances": list(TOLS), "theta": THETA,
+        "label_margin": LABEL_MARGIN,
         "n_range": [1e4, a.nmax], "kinds": list(KINDS), "epochs": a.epochs, "seed": a.seed,
         "loss_first_last": [hist[0], hist[-1]], "accuracy_train": acc_tr, "accuracy_val": acc_va,
         "generation_s": t_gen,

@@ -201,10 +201,14 @@ def test_pipeline_end_to_end(fmmlib, cuda):
 def test_trained_selector_gain(fmmlib, cuda):
     # fresh point sets (seeds unseen in training): the trained selector against the plain rule
     from paper_1006_2269_gb300 import selector as S
+    # N log-uniform in [1e4, 1e6] at tolerances 1e-3, 1e-6, 1e-9: the selector's parameters must
+    # meet the tolerance in every case (the rule's too) and take less time in total
     sel = S.Selector.load(device=cuda)
     try:
         g = S.gain(sel, 10, 4242, cuda)
     finally:
         sel.close()
-    assert g["met_tol_selector"] >= 0.8
+    missed = [c for c in g["cases"] if c["selector"][3] > c["tol"]]
+    assert not missed, missed
+    assert g["met_tol_fallback"] == 1.0
     assert g["ms_selector"] <= g["ms_fallback"]

@@ -127,3 +127,19 @@ def test_bounded_wait_gives_up_and_the_context_survives(fmmlib, orc, cuda):
         assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
     finally:
         f.close()
+
+
+def test_queue_wait_gives_up_and_the_context_survives(fmmlib, orc, cuda):
+    # the persistent upward pass with a dependency that never completes: every waiting item
+    # gives up after its tries, the launch ends, and the tree then evaluates normally
+    c = W.clusters(20000, 98)
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), 4, 0.5)
+    try:
+        with pytest.raises(fmmlib.FMMError) as ei:
+            fmmlib.fmm_selftest_queue_timeout(f.tree, 4096)
+        assert ei.value.code == fmmlib.FMM_ERR_TIMEOUT
+        got = f.evaluate(_t(c.q, cuda), 16, "fp64").cpu().numpy()
+        ref = orc.fmm(c.x, c.y, c.q, 4, 16, 0.5)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    finally:
+        f.close()
