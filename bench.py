@@ -519,8 +519,8 @@ def bench_large(dev, steps=3, warmup=2):
             out[name] = {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "rel_err": err,
                          "met_tol": err <= tol, "stages_ms": {k: v[0] / v[1] for k, v in prof.items() if v[1]}}
         out["precision"] = {"binary64": "every stage in binary64",
-                            "split": "binary64 P2M, M2M, M2L, L2L, L2P; binary32 near-field terms summed in "
-                                     "float-float; far and near joined in binary64"}
+                            "split": "binary64 P2M, M2M, M2L, L2L, L2P; near field in float-float (pairs of "
+                                     "binary32, terms and sums); far and near joined in binary64"}
         return out
     finally:
         f.close()
@@ -722,7 +722,8 @@ def main():
     fmm.fmm_lists_set_mode(f.lists, variants[lists_kind])
     step(fmm.FMM_MODE_MIXED)
     fmm.fmm_sync_status(f.tree, f.lists)
-    tuned = {fmm.FMM_MODE_FP64: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_FP64, phi)}
+    tuned = {fmm.FMM_MODE_FP64: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_FP64, phi),
+             fmm.FMM_MODE_SPLIT: fmm.fmm_autotune(f.tree, f.lists, q, w.p, fmm.FMM_MODE_SPLIT, phi)}
     if args.blocks:
         tuned[fmm.FMM_MODE_MIXED] = tuple(int(v) for v in args.blocks.split(","))
     else:
@@ -743,6 +744,10 @@ def main():
     step(fmm.FMM_MODE_FP64)
     torch.cuda.synchronize()
     err_fp64 = (phi[tg] - ref).abs().max().item() / scale
+    use(fmm.FMM_MODE_SPLIT)
+    step(fmm.FMM_MODE_SPLIT)
+    torch.cuda.synchronize()
+    err_split = (phi[tg] - ref).abs().max().item() / scale
     nweak, npairs = pair_counts(f)
 
     graphs = {}
@@ -812,6 +817,7 @@ def main():
         ms_mixed_plain, launches, _ = timed(fmm.FMM_MODE_MIXED, args.steps)
     ms_e2e, _, _ = timed(fmm.FMM_MODE_MIXED, args.steps, e2e=True)
     ms_fp64, _, prof64 = timed(fmm.FMM_MODE_FP64, args.fp64_steps, profile=True)
+    ms_split, _, prof_split = timed(fmm.FMM_MODE_SPLIT, args.fp64_steps, profile=True)
     fmm.fmm_sync_status(f.tree, f.lists)
 
     K = args.steps
@@ -884,6 +890,10 @@ def main():
         "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,
         "fp64_path": {"value": job_throughput(world, n, ms_fp64, args.fp64_steps),
                       "ms_per_step": ms_fp64 / args.fp64_steps, "stages_ms": stage_ms64},
+        "split_path": {"value": job_throughput(world, n, ms_split, args.fp64_steps),
+                       "ms_per_step": ms_split / args.fp64_steps, "rel_err": err_split,
+                       "precision": "binary64 expansions, float-float near field, binary64 join",
+                       "stages_ms": {k: v[0] / max(v[1], 1) for k, v in prof_split.items() if v[1]}},
         "speedup_vs_fp64": (ms_fp64 / args.fp64_steps) / per_step,
         "stages_ms": stage_ms, "weak_pairs": nweak, "near_pair_evals": npairs,
         "e2e": {"value": job_throughput(world, n, ms_e2e, K), "unit": UNIT,

@@ -52,8 +52,9 @@ typedef enum {
 typedef enum {
     FMM_MODE_FP64 = 0,   /* every stage in binary64                                         */
     FMM_MODE_MIXED = 1,  /* binary32 expansions, near field and accumulation (see below)    */
-    FMM_MODE_SPLIT = 2   /* binary64 expansions (P2M .. L2P); binary32 near-field terms in
-                            float-float sums; far and near joined in binary64 */
+    FMM_MODE_SPLIT = 2   /* binary64 expansions (P2M .. L2P); the near field in float-float
+                            (pairs of binary32: terms and sums, about 2^-46 relative); far and
+                            near joined in binary64 */
 } fmm_mode;
 
 typedef struct fmm_tree_s* fmm_tree;

@@ -38,6 +38,9 @@ namespace fmm {
 constexpr int PMAXC = 41;  // p <= 40
 
 __constant__ double c_md[PMAXC][PMAXC];     // M'[l][k] in binary64
+// log2(j / 128) for j = 128 .. 256 as float-float (high, low): the table of the float-float
+// logarithm of the split mode's near field
+__constant__ float c_lg2t[2][129];
 // binomials C(n, k), n, k < PMAXC, in global memory: blocks copy them to shared memory (a warp
 // reading many different __constant__ addresses at once would be serialised)
 __device__ float g_binom_f[PMAXC * PMAXC];
@@ -1607,6 +1610,182 @@ __global__ void __launch_bounds__(256) k_p2p_large(Sched sc, const Inst* __restr
     }
 }
 
+// ---- float-float near field (split mode) ------------------------------------------------------
+//
+// Pairs of binary32 numbers (hi + lo, |lo| <= half an ulp of hi) carry about 48 bits; the
+// operations are the error-free transformations of Knuth (two-sum) and Dekker (two-product, with
+// the fused multiply-add), as in the double-double literature.  Each near-field term q_j log2 r^2
+// is formed in float-float from float-float coordinate offsets (each point relative to its leaf
+// centre, the leaf-pair offset from the binary64 centres), so its error is about 2^-46 of its
+// size, and the sums are float-float too.
+struct ff {
+    float h, l;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_quick(float a, float b)  // |a| >= |b|
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = ff_two_sum(a.h, b.h);
+    s.l += a.l + b.l;
+    return ff_quick(s.h, s.l);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p) + (a.h * b.l + a.l * b.h);
+    return ff_quick(p, e);
+}
+__device__ __forceinline__ ff ff_sq(ff a)
+{
+    const float p = a.h * a.h;
+    const float e = fmaf(a.h, a.h, -p) + 2.f * a.h * a.l;
+    return ff_quick(p, e);
+}
+__device__ __forceinline__ ff ff_split(double v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+// log2 of a positive float-float a (a.h a normal binary32), table-driven (Tang's method): with
+// a = 2^e m (1 <= m < 2) and F = j / 128 the nearest table point, log2 a = e + log2 F +
+// log2(1 + r), r = (m - F + a.l / 2^e) / F, |r| <= 2^-8; log(1 + r) by its series to r^5 (the
+// first terms in float-float, the rest in binary32), times 1/ln 2 in float-float.
+__device__ __forceinline__ ff ff_log2(ff a)
+{
+    const uint32_t bits = __float_as_uint(a.h);
+    const int e = (int)(bits >> 23) - 127;
+    const float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);  // [1, 2)
+    const int j = __float2int_rn((m - 1.f) * 128.f);                     // 0 .. 128
+    const float F = 1.f + (float)j * (1.f / 128.f);
+    const float invF = 1.f / F;
+    const ff u = ff_two_sum(m - F, ldexpf(a.l, -e));  // m - F is exact
+    const float rh = u.h * invF;
+    const float rl = (fmaf(-rh, F, u.h) + u.l) * invF;
+    const ff r = ff_quick(rh, rl);
+    const ff r2 = ff_sq(r);
+    const float t3 = r2.h * rh * (1.f / 3.f - 0.25f * rh + 0.2f * r2.h);  // r^3/3 - r^4/4 + r^5/5
+    ff L = ff_add(r, ff{-0.5f * r2.h, -0.5f * r2.l});
+    L = ff_add(L, ff{t3, 0.f});
+    const ff inv_ln2 = {1.44269502163f, 1.92596299e-8f};  // 1/ln 2 as float-float
+    L = ff_mul(L, inv_ln2);
+    const ff T = {c_lg2t[0][j], c_lg2t[1][j]};
+    return ff_add(ff_add(ff{(float)e, 0.f}, T), L);
+}
+
+// Points of the float-float near field: offsets from their leaf's centre and strengths, each as
+// float-float (canonical order).  schedule: points
+__global__ void k_pack_ff(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
+                          const double* __restrict__ q, const double* __restrict__ xs, const double* __restrict__ ys,
+                          const int32_t* __restrict__ cleaf, const double* __restrict__ cen, float4* __restrict__ pk)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    perm += S.p0;
+    q += S.p0;
+    xs += S.p0;
+    ys += S.p0;
+    cleaf += S.p0;
+    cen += 2 * S.b0;
+    pk += 2 * S.p0;
+    const int64_t lbase = level_base(S.L);
+    for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
+        const int64_t g = lbase + cleaf[i];
+        const ff x = ff_split(xs[i] - cen[2 * g]), y = ff_split(ys[i] - cen[2 * g + 1]);
+        const ff w = ff_split(q[perm[i]]);
+        pk[2 * i] = make_float4(x.h, x.l, y.h, y.l);
+        pk[2 * i + 1] = make_float4(w.h, w.l, 0.f, 0.f);
+    }
+}
+
+// Near field in float-float: the work items of k_p2p_items (leaf pair, 32 targets, a block of
+// sources), a warp per item and a lane per target; the sum of q_j log2 r^2 over the item's sources
+// goes to the target's float-float accumulator (nhi, nlo) with the exact two-sum atomic.
+// Coincident points (r = 0, among them j = i) are skipped.  schedule: near field
+__global__ void __launch_bounds__(256) k_p2p_ff(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+                                                const int32_t* __restrict__ soff, const int32_t* __restrict__ sidx,
+                                                const int32_t* __restrict__ stgt, const int32_t* __restrict__ lb,
+                                                const int32_t* __restrict__ pos,
+                                                const unsigned long long* __restrict__ total, int32_t* status,
+                                                const float4* __restrict__ pk, const double* __restrict__ cen,
+                                                float* __restrict__ nhi, float* __restrict__ nlo)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst TL = LIs[z.i];
+    const int L = S.L;
+    if (*total > (unsigned long long)INT32_MAX) {  // the item numbering did not fit
+        if (threadIdx.x == 0) atomicOr(status, ST_ARG);
+        return;
+    }
+    const int64_t scap = TL.scap;
+    soff += S.o0;
+    sidx += TL.s0;
+    stgt += TL.s0;
+    pos += TL.s0;
+    lb += S.lb0;
+    pk += 2 * S.p0;
+    cen += 2 * S.b0;
+    nhi += S.p0;
+    nlo += S.p0;
+    const int lane = threadIdx.x & 31;
+    const int64_t base = level_base(L);
+    const int64_t e_begin = min((int64_t)soff[base], scap);
+    const int64_t e_end = min((int64_t)soff[base + level_size(L)], scap);
+    if (e_end <= e_begin) return;
+    const int64_t v0 = pos[e_begin], v1 = pos[e_end];
+    const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
+    for (int64_t v = v0 + warp; v < v1; v += nwarps) {
+        int64_t lo = e_begin, hi = e_end - 1;  // the pair owning item v
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (pos[mid] <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t e = lo;
+        const int64_t tl = stgt[e] - base, sl = sidx[e];
+        const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0, s0 = lb[sl], ns = lb[sl + 1] - s0;
+        const int32_t nsc = p2p_src_blocks(nt, ns), ntc = (nt + 31) / 32;
+        const int32_t local = (int32_t)(v - pos[e]);
+        const int32_t tc = local % ntc, scb = local / ntc;
+        const int32_t slen = (ns + nsc - 1) / nsc;
+        const int32_t jb0 = scb * slen, jb1 = min(ns, jb0 + slen);
+        const int32_t it = t0 + tc * 32 + lane;
+        if (tc * 32 + lane >= nt) continue;
+        // the target relative to the source leaf's centre: its offset plus (c_t - c_s)
+        const int64_t tg = base + tl, sg = base + sl;
+        const float4 tp = pk[2 * it];
+        const ff xt = ff_add(ff{tp.x, tp.y}, ff_split(cen[2 * tg] - cen[2 * sg]));
+        const ff yt = ff_add(ff{tp.z, tp.w}, ff_split(cen[2 * tg + 1] - cen[2 * sg + 1]));
+        ff acc = {0.f, 0.f};
+        for (int32_t jj = jb0; jj < jb1; jj++) {
+            const float4 sp = pk[2 * (s0 + jj)];
+            const float4 sq = pk[2 * (s0 + jj) + 1];
+            const ff dx = ff_add(xt, ff{-sp.x, -sp.y}), dy = ff_add(yt, ff{-sp.z, -sp.w});
+            const ff r2 = ff_add(ff_sq(dx), ff_sq(dy));
+            if (!(r2.h > 0.f)) continue;  // coincident points, j = i among them
+            ff lg;
+            if (r2.h >= 1e-30f) {
+                lg = ff_log2(r2);
+            } else {  // below the binary32 normal range of the table method: binary64
+                lg = ff_split(log2((double)r2.h + (double)r2.l));
+            }
+            acc = ff_add(acc, ff_mul(ff{sq.x, sq.y}, lg));
+        }
+        atomic_add_ff(&nhi[it], &nlo[it], acc.h, acc.l);  // many items may add to one target
+    }
+}
+
 __global__ void k_unpermute(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                             const double* __restrict__ acc, double* __restrict__ phi)
 {
@@ -1623,7 +1802,7 @@ __global__ void k_unpermute(Sched sc, const Inst* __restrict__ I, const int32_t*
 
 // binary32 path: phi = far + (ln 2 / 2) * near, combined in binary32 (the mixed path targets
 // tolerances >= 1e-7), written in input order.
-// The binary64 far field joined with a binary32 near field (float-float sums in log2 units), in
+// The binary64 far field joined with the float-float near field (sums in log2 units), in
 // binary64, into input order.
 __global__ void k_combine64(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                             const double* __restrict__ far, const float* __restrict__ nhi,
@@ -2073,6 +2252,13 @@ int ensure_tables()
         if (compiled[i] != mf[i / PMAXC][i % PMAXC])
             return fail(FMM_ERR_STATE, "compiled M2L coefficient (%d, %d) differs from the table", i / PMAXC, i % PMAXC);
     FMM_CUDA(cudaMemcpyToSymbol(c_md, md, sizeof(md)));
+    static float lg[2][129];
+    for (int j = 0; j <= 128; j++) {
+        const double v = log2((double)(128 + j) / 128.0);
+        lg[0][j] = (float)v;
+        lg[1][j] = (float)(v - (double)lg[0][j]);
+    }
+    FMM_CUDA(cudaMemcpyToSymbol(c_lg2t, lg, sizeof(lg)));
     g_tab_ready[dev] = true;
     return 0;
 }
@@ -2163,8 +2349,8 @@ template <typename T>
 int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStream_t s, double* fim = nullptr,
         const StepSync* sync = nullptr, bool near32 = false)
 {
-    // near32 (binary64 expansions only): the near field takes the binary32 kernels (float-float
-    // sums of binary32 terms) and is joined to the binary64 far field in binary64
+    // near32 (binary64 expansions only, the split mode): the near field in float-float (terms
+    // and sums, k_p2p_ff), joined to the binary64 far field in binary64
     near32 = near32 && sizeof(T) == 8 && fim == nullptr;
     // with sync the lists are being built on sync->side: wait for them before their first use
     bool lists_waited = false;
@@ -2183,7 +2369,7 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     if (near32) {
         if (!t->acc32 && cudaMalloc((void**)&t->acc32, 6 * 4 * (size_t)t->n) != cudaSuccess)
             return fail(FMM_ERR_OOM, "accumulator");
-        if (!t->pk32 && cudaMalloc(&t->pk32, 16 * (size_t)t->n) != cudaSuccess)
+        if (!t->pkff && cudaMalloc(&t->pkff, 32 * (size_t)t->n) != cudaSuccess)
             return fail(FMM_ERR_OOM, "packed points");
     }
     if (field) {
@@ -2224,8 +2410,8 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         k_pack<T><<<gpts, 256, 0, s>>>(spts, I, t->perm, q, t->xs, t->ys, t->dxf, t->dyf, pk, t->status);
         note_launch();
         if (near32) {
-            k_pack<float><<<gpts, 256, 0, s>>>(spts, I, t->perm, q, t->xs, t->ys, t->dxf, t->dyf,
-                                               (Pk<float>*)t->pk32, t->status);
+            k_pack_ff<<<gpts, 256, 0, s>>>(spts, I, t->perm, q, t->xs, t->ys, t->cleaf, t->centers,
+                                           (float4*)t->pkff);
             note_launch();
         }
         FMM_CUDA(cudaMemsetAsync(Le, 0, (size_t)t->nbox * PS * sizeof(cx<T>), s));
@@ -2365,9 +2551,10 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         const Sched sp2p = t->s_p2p.d;
         const Pk<float>* pk32 = (const Pk<float>*)t->pk32;
         // instances whose leaves hold at most SMALL_LEAF points take the leaf-pair kernel, the
-        // others (if any) the general one; each kernel skips the instances of the other
-        const int small_leaf = n32 ? 64 : 32;
-        if (minleaf <= small_leaf) {
+        // others (if any) the general one; each kernel skips the instances of the other (the
+        // float-float near field takes the general kernel's work items for every instance)
+        const int small_leaf = near32 ? 0 : n32 ? 64 : 32;
+        if (!near32 && minleaf <= small_leaf) {
             if (n32) {
                 k_p2p_f32<<<gp2p, 256, 0, ns>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk32,
                                                 t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
@@ -2389,7 +2576,10 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
                                               li->p2p_items, total); note_launch();
             rc = scan_with_base(li->p2p_items, li->scap, li->p2p_zero, li->p2p_pos, li->p2p_tmp, ns);
             if (rc) return rc;
-            if (n32)
+            if (near32)
+                k_p2p_ff<<<gp2p, 256, 0, ns>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, li->p2p_pos,
+                                               total, t->status, (const float4*)t->pkff, t->centers, nhi, nlo);
+            else if (n32)
                 k_p2p_large<float><<<gp2p, 256, 0, ns>>>(sp2p, I, LI, small_leaf, li->soff, li->sidx, li->stgt,
                                                          t->leaf_begin, li->p2p_pos, total, t->status, pk32, t->xs,
                                                          t->ys, t->cen_hi, t->cen_lo, t->rad32, t->acc, nhi, nlo);

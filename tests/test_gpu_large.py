@@ -52,6 +52,9 @@ def test_large_tolerance_1e10_vs_direct(large, orc, cuda):
     ref = orc.direct(c.x, c.y, c.q, tg, nthreads=0)
     phi = f.evaluate(_t(c.q, cuda), w.p, "mixed", tol=1e-10).cpu().numpy()[tg]
     assert relerr(phi, ref) <= 1e-10
+    # the split mode (binary64 expansions, float-float near field) at the same tolerance
+    phi = f.evaluate(_t(c.q, cuda), w.p, "split", tol=1e-10).cpu().numpy()[tg]
+    assert relerr(phi, ref) <= 1e-10
     # the mixed path at its own tolerance on the same input
     phi = f.evaluate(_t(c.q, cuda), 20, "mixed", tol=1e-6).cpu().numpy()[tg]
     assert relerr(phi, ref) <= 1e-6

@@ -244,3 +244,25 @@ def test_throughput_probes(fmmlib, cuda):
     assert 20e12 < ffma < 1.1 * 80.5e12
     assert 0.5e12 < lg2 < 1.1 * 5.03e12
     assert 0 < dfma < ffma / 4
+
+
+SPLIT_CASES = [
+    ("clusters", lambda: W.clusters(30011, 402), 5, 20),
+    ("rings", lambda: W.rings_plummer(40000, 404), 6, 30),
+    ("uniform_ragged", lambda: W.uniform(4 ** 5 * 13 + 7, 405), 5, 24),
+    ("dupes", lambda: _dupes(6000, 406), 3, 18),
+]
+
+
+@pytest.mark.parametrize("name,make,L,p", SPLIT_CASES, ids=[c[0] for c in SPLIT_CASES])
+def test_split_mode_against_oracle(fmmlib, orc, cuda, name, make, L, p):
+    # binary64 expansions with the float-float near field: the near-field terms carry about
+    # 2^-46 of their size, so the result stays within 1e-11 of the binary64 oracle
+    c = make()
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), L, 0.5, parents=True)
+    try:
+        got = f.evaluate(_t(c.q, cuda), p, "split", tol=1e-10).cpu().numpy()
+    finally:
+        f.close()
+    ref = orc.fmm(c.x, c.y, c.q, L, p, 0.5, parents=True)
+    assert relerr(got, ref) <= 1e-11
