@@ -67,8 +67,9 @@ typedef struct fmm_lists_s* fmm_lists;
  *   mode   FMM_MODE_FP64, FMM_MODE_MIXED or FMM_MODE_SPLIT.
  *   tol    requested relative tolerance (0 = none).  In FMM_MODE_MIXED a tol below 1e-7 is
  *          beyond what binary32 expansions can deliver (their rounding alone is about 1e-7 of
- *          the potential), so such a call runs every stage in binary64, exactly as
- *          FMM_MODE_FP64.  Ignored in FMM_MODE_FP64.
+ *          the potential), so such a call runs as FMM_MODE_SPLIT: binary64 expansions and a
+ *          float-float near field, the accuracy of FMM_MODE_FP64 (the binary64 field, which
+ *          has no split form, runs every stage in binary64).  Ignored in the other modes.
  */
 typedef struct {
     int p;

@@ -2625,11 +2625,14 @@ int evaluate(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     int rc = ensure_tables();
     if (rc) return rc;
     const int P = prm.p + 1;
-    // binary32 expansions carry a rounding error of about 1e-7 relative to the potential: a
-    // tighter requested tolerance takes the binary64 path
-    if (prm.mode == FMM_MODE_SPLIT) return run<double>(t, li, q, P, phi, s, nullptr, sync, true);
-    const bool f64 = prm.mode == FMM_MODE_FP64 || (prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR);
-    if (f64) return run<double>(t, li, q, P, phi, s, nullptr, sync);
+    // the mixed mode below the binary32 floor takes the split precision: binary64 expansions (the
+    // far field needs them: binary32 coefficients carry about 1e-7 of the potential) and the
+    // float-float near field, which on GB300 costs a fraction of a binary64 one (slow binary64
+    // units) at binary64 accuracy
+    const bool split = prm.mode == FMM_MODE_SPLIT ||
+                       (prm.mode == FMM_MODE_MIXED && prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR);
+    if (split) return run<double>(t, li, q, P, phi, s, nullptr, sync, true);
+    if (prm.mode == FMM_MODE_FP64) return run<double>(t, li, q, P, phi, s, nullptr, sync);
     return run<float>(t, li, q, P, phi, s, nullptr, sync);
 }
 

@@ -15,8 +15,8 @@ method itself:
    Adam kernels, and selects with the library's masked arg-max.
 
 All arithmetic runs in the CUDA library; this module only orchestrates (which runs to make,
-mini-batch order, bookkeeping).  Mode: tolerances below 1e-7 run the binary64 path, the others
-the mixed path (the library's own policy).
+mini-batch order, bookkeeping).  Mode: the mixed mode throughout; the library runs tolerances
+below 1e-7 in its split precision (binary64 expansions, float-float near field).
 
 Command line (trains on synthetic point sets and writes the weights next to this file):
 
@@ -39,7 +39,7 @@ LMIN, LMAX, PMIN, PMAX, NP = (fmm.FMM_SEL_LMIN, fmm.FMM_SEL_LMAX, fmm.FMM_SEL_PM
                               fmm.FMM_SEL_NP)
 NCLASS = fmm.FMM_MLP_OUT
 THETA = 0.5
-MIXED_FLOOR = 1e-7  # tolerances below it take the binary64 path
+MIXED_FLOOR = 1e-7  # tolerances below it take the split precision (binary64 expansions)
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights")
 
 
@@ -144,12 +144,10 @@ def label(table, tol: float, margin: float = 1.0) -> int:
     return class_of(best[0], best[1])
 
 
-def candidate_levels(n: int, f64: bool = False):
-    """Level counts tried for a label: round(log4(N / 32)) - 2 .. + 1; the binary64 path (tight
-    tolerances) skips the coarsest, whose large leaves make its near field by far the slowest run
-    and never the fastest."""
+def candidate_levels(n: int):
+    """Level counts tried for a label: round(log4(N / 32)) - 2 .. + 1."""
     Lc = int(round(math.log(n / 32.0) / math.log(4.0)))
-    return [L for L in range(Lc - (1 if f64 else 2), Lc + 2) if LMIN <= L <= min(LMAX, max_levels(n))]
+    return [L for L in range(Lc - 2, Lc + 2) if LMIN <= L <= min(LMAX, max_levels(n))]
 
 
 def candidate_ps(tol: float):
@@ -315,10 +313,9 @@ def generate(count: int, seed: int, dev, nmin: float = 1e4, nmax: float = 1e6, t
         inst = Instance(c, dev, seed=seed * 31 + i)
         tab = {}
         for tol in tols:
-            key = "f64" if tol < MIXED_FLOOR else "mixed"
+            key = "split" if tol < MIXED_FLOOR else "mixed"
             if key not in tab:
-                tab[key] = run_table(inst, candidate_levels(inst.n, key == "f64"), candidate_ps(tol), tol,
-                                     reps=1 if key == "f64" else 2)
+                tab[key] = run_table(inst, candidate_levels(inst.n), candidate_ps(tol), tol, reps=2)
             f = Selector.features(inst.x, inst.y, tol).cpu().numpy()
             X.append(f)
             y.append(label(tab[key], tol, LABEL_MARGIN))

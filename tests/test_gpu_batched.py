@@ -113,8 +113,9 @@ def test_forest_potentials(forest, orc, cuda, mode, p, tol):
         assert relerr(phi[a:e], ref) <= tol, (c.name, L)
 
 
-def test_forest_tight_tolerance_takes_binary64(forest, orc, cuda):
-    # a requested tolerance below what binary32 expansions reach runs the binary64 path
+def test_forest_tight_tolerance_takes_split(forest, orc, cuda):
+    # a requested tolerance below what binary32 expansions reach runs the split precision
+    # (binary64 expansions, float-float near field), accurate to the binary64 bound
     clouds, levels, (x, y, q), b = forest
     phi = b.evaluate(_t(q, cuda), 24, "mixed", tol=1e-10).cpu().numpy()
     for (a, e), c, L in zip(_slices(b), clouds, levels):
