@@ -459,10 +459,11 @@ typedef enum {
     FMM_STAGE_M2M = 6,
     FMM_STAGE_M2L = 7,
     FMM_STAGE_L2L = 8,
-    FMM_STAGE_LEAF = 9,        /* L2P (P2L, M2P), far and near joined in input order (the field:
-                                  also its near sum)                                            */
+    FMM_STAGE_LEAF = 9,        /* L2P, far and near joined in input order (the field: also its
+                                  near sum, P2L and M2P)                                        */
     FMM_STAGE_NEAR = 10,       /* near-field direct sum of the potentials                     */
-    FMM_STAGE_COUNT = 11
+    FMM_STAGE_EXCHANGE = 11,   /* P2L and M2P of the role-exchange lists (potentials)         */
+    FMM_STAGE_COUNT = 12
 } fmm_stage;
 
 /* Enable (on != 0) or disable recording of a CUDA event pair around every stage, on the stream

@@ -1800,8 +1800,6 @@ __global__ void k_unpermute(Sched sc, const Inst* __restrict__ I, const int32_t*
         phi[perm[i]] = acc[i];
 }
 
-// binary32 path: phi = far + (ln 2 / 2) * near, combined in binary32 (the mixed path targets
-// tolerances >= 1e-7), written in input order.
 // The binary64 far field joined with the float-float near field (sums in log2 units), in
 // binary64, into input order.
 __global__ void k_combine64(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
@@ -1820,6 +1818,8 @@ __global__ void k_combine64(Sched sc, const Inst* __restrict__ I, const int32_t*
         phi[perm[i]] = far[i] + scale * ((double)nhi[i] + (double)nlo[i]);
 }
 
+// binary32 path: phi = far + (ln 2 / 2) * near, combined in binary32 (the mixed path targets
+// tolerances >= 1e-7), written in input order.
 __global__ void k_combine32(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                             const float* __restrict__ far, const float* __restrict__ farlo,
                             const float* __restrict__ nhi, const float* __restrict__ nlo,
@@ -2593,17 +2593,24 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     }
     if (overlap) FMM_CUDA(cudaEventRecord(sync->near_done, ns));
     {
-        StageScope leaf_scope(FMM_STAGE_LEAF, s);  // P2L, L2P, M2P, far and near joined
-        if ((rc = p2l())) return rc;
-        k_l2p<T><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo,
-                                      f64 ? (T*)t->acc : (T*)far32, farlo);
-        note_launch();
         if (swp) {
+            StageScope x_scope(FMM_STAGE_EXCHANGE, s);
+            if ((rc = p2l())) return rc;
+        }
+        {
+            StageScope leaf_scope(FMM_STAGE_LEAF, s);
+            k_l2p<T><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo,
+                                          f64 ? (T*)t->acc : (T*)far32, farlo);
+            note_launch();
+        }
+        if (swp) {
+            StageScope x_scope(FMM_STAGE_EXCHANGE, s);
             k_m2p<T, false><<<(unsigned)t->s_p2p.blocks, 256, 0, s>>>(t->s_p2p.d, I, LI, P, PS, gsx, t->leaf_begin, pk,
                                                                      geo, xl, Me, f64 ? (T*)t->acc : (T*)far32,
                                                                      farlo, nullptr, nullptr);
             note_launch();
         }
+        StageScope leaf_scope(FMM_STAGE_LEAF, s);  // far and near joined
         if (overlap) FMM_CUDA(cudaStreamWaitEvent(s, sync->near_done, 0));
         if (near32)
             k_combine64<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->acc, nhi, nlo, phi);

@@ -559,7 +559,7 @@ def fmm_sync_status(tree, lists=None, stream=None):
 
 
 STAGES = ("tree_sort", "tree_split", "tree_finish", "lists", "gather", "p2m", "m2m", "m2l", "l2l",
-          "leaf", "near")
+          "leaf", "near", "exchange")
 
 
 def fmm_profile_enable(on: bool = True):
