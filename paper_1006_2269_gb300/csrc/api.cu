@@ -96,7 +96,7 @@ void free_tree(fmm_tree t)
                     t->leaf_of, t->xs, t->ys, t->dxf, t->dyf, t->keys, t->vals, t->rs_counts,
                     t->rs_totals, t->tilecnt, t->hflag, t->bbox_keys, t->ones_before, t->node_off, t->segs, t->status,
                     t->Me, t->Le, t->Mf, t->Lf, t->pk64, t->pk32, t->acc, t->acc32, t->cleaf, t->dinst, t->Lf0lo,
-                    t->pkf, t->qf, t->accf, t->qmem, t->pkff};
+                    t->pkf, t->qf, t->accf, t->qmem, t->pkff, t->mff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     sched_free_all(t);

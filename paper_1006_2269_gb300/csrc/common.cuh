@@ -261,6 +261,8 @@ struct fmm_tree_s {
     double* accf = nullptr; // [2n] binary64 field accumulator (re, im)
     float* Lf0lo = nullptr; // [nbox] low part of Re b_0 of the binary32 locals (float-float)
     void* pkff = nullptr;   // [n][2] float4: float-float offsets from the leaf centre and strength (split mode)
+    void* mff = nullptr;    // [nbox][mff_ps] float4: float-float multipoles (split mode, role exchange)
+    int mff_ps = 0;
 
     // launch tuning (set by fmm_autotune; 0 = defaults): total blocks of the M2L and near-field
     // launches, shared out over the instances in proportion to their work

@@ -1786,6 +1786,314 @@ __global__ void __launch_bounds__(256) k_p2p_ff(Sched sc, const Inst* __restrict
     }
 }
 
+// ---- float-float role exchange (split mode) ---------------------------------------------------
+//
+// P2L and M2P of the exchange lists are point work of the finest level, like the near field, and
+// in binary64 they cost as much as the near field did (binary64 arithmetic runs at 1/73 of the
+// binary32 FMA rate here).  In the split mode they run in float-float: complex products and sums
+// whose low parts are rounded once per operation keep about 2^-44 of each term; the expansions
+// stay binary64 in memory (M2P reads a float-float copy of the multipole coefficients, P2L adds
+// its float-float sums into the binary64 local expansions).
+struct cff {
+    ff re, im;
+};
+
+// a.h b.h = p + e exactly (Dekker's product with the fused multiply-add), the cross terms of the
+// low parts added into e
+__device__ __forceinline__ float ff_prod(ff a, ff b, float& e)
+{
+    const float p = a.h * b.h;
+    e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return p;
+}
+
+// x y - u v + c: the two leading products and c.h summed with exact two-sums, every low-order
+// part added once at the end; the error is about 2^-46 of max(|x y|, |u v|, |c|)
+__device__ __forceinline__ ff ff_dot2(ff x, ff y, ff u, ff v, ff c)
+{
+    float e1, e2;
+    const float p1 = ff_prod(x, y, e1), p2 = ff_prod(u, v, e2);
+    const ff s = ff_two_sum(p1, -p2);
+    const ff s2 = ff_two_sum(s.h, c.h);
+    return ff_quick(s2.h, ((s.l + s2.l) + (e1 - e2)) + c.l);
+}
+
+// x y - u v
+__device__ __forceinline__ ff ff_dot2(ff x, ff y, ff u, ff v)
+{
+    float e1, e2;
+    const float p1 = ff_prod(x, y, e1), p2 = ff_prod(u, v, e2);
+    const ff s = ff_two_sum(p1, -p2);
+    return ff_quick(s.h, s.l + (e1 - e2));
+}
+
+// h w + a and h w (complex)
+__device__ __forceinline__ cff cff_fma(const cff& h, const cff& w, const cff& a)
+{
+    return {ff_dot2(h.re, w.re, h.im, w.im, a.re), ff_dot2(h.re, w.im, ff{-h.im.h, -h.im.l}, w.re, a.im)};
+}
+__device__ __forceinline__ cff cff_mul(const cff& h, const cff& w)
+{
+    return {ff_dot2(h.re, w.re, h.im, w.im), ff_dot2(h.re, w.im, ff{-h.im.h, -h.im.l}, w.re)};
+}
+
+__device__ __forceinline__ cff cff_add(const cff& a, const cff& b) { return {ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+
+// a / b: the quotient of the leading parts, corrected once by the remainder a - q b
+__device__ __forceinline__ ff ff_div(ff a, ff b)
+{
+    const float ib = __frcp_rn(b.h);
+    const float q1 = a.h * ib;
+    float e;
+    const float p = ff_prod(ff{q1, 0.f}, b, e);
+    const float r = ((a.h - p) - e) + a.l;
+    return ff_quick(q1, r * ib);
+}
+
+// log2 of a positive float-float r^2: the table method inside the binary32 normal range (far from
+// its ends), binary64 outside it
+__device__ __forceinline__ ff ff_log2_any(ff a)
+{
+    if (a.h >= 1e-30f && a.h <= 1e30f) return ff_log2(a);
+    return ff_split(log2((double)a.h + (double)a.l));
+}
+
+// rho conj(dz) / |dz|^2 (= rho / dz) and log|dz| of the offset dz = (dx, dy), float-float
+__device__ __forceinline__ void ff_inv_log(ff dx, ff dy, ff rho, ff ln2h, cff& w, ff& lg)
+{
+    const ff r2 = ff_add(ff_sq(dx), ff_sq(dy));
+    const ff s = ff_div(rho, r2);
+    w = {ff_mul(s, dx), ff_mul(s, ff{-dy.h, -dy.l})};
+    lg = ff_mul(ff_log2_any(r2), ln2h);  // log|dz| = (ln 2 / 2) log2 |dz|^2
+}
+
+// The multipole coefficients as float-float (re.h, re.l, im.h, im.l), same layout as the binary64
+// ones.  count = boxes x PS.
+__global__ void k_coeffs_ff(const double2* __restrict__ Me, int64_t count, float4* __restrict__ Mff)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 a = Me[i];
+        const ff re = ff_split(a.x), im = ff_split(a.y);
+        Mff[i] = make_float4(re.h, re.l, im.h, im.l);
+    }
+}
+
+// Split-mode M2P (potentials): the walk of k_m2p over the flat exchange lists (runs of XCH
+// entries per lane group of gs lanes, a lane's points gl, gl + gs, ... of the target leaf), each
+// value in float-float: dz = the point's float-float offset from its leaf centre plus the binary64
+// centre difference c_g - c_s, w = rho_s / dz, Horner over the source's float-float coefficients
+// (the lane's points share each coefficient load), a~_0 log|dz| + Re sum_k a~_k w^k.  A lane sums
+// its points' values over the run's entries of one target in float-float and adds them to the
+// binary64 accumulator when the target changes.  schedule: the near-field schedule
+__global__ void __launch_bounds__(256) k_m2p_ff(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
+                                                int P, int PS, int gs, const int32_t* __restrict__ lb,
+                                                const float4* __restrict__ pk, const double* __restrict__ cen,
+                                                const double* __restrict__ rad, XLists xl,
+                                                const float4* __restrict__ Mff, double* __restrict__ acc)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const LInst T_ = LIs[z.i];
+    const int L = S.L;
+    if (L < 1) return;
+    lb += S.lb0;
+    pk += 2 * S.p0;
+    cen += 2 * S.b0;
+    rad += S.b0;
+    Mff += S.b0 * PS;
+    acc += S.p0;
+    const int32_t* xidx = xl.xidx + T_.s0;
+    const int32_t* xtgt = xl.xtgt + T_.s0;
+    const int64_t nx = min((int64_t)xl.xoff[S.o0 + S.nbox], T_.scap);
+    const int64_t base = level_base(L);
+    const ff ln2h = ff_split(0.34657359027997264);  // ln(2) / 2
+    const int lane = threadIdx.x & 31, G = 32 / gs, grp = lane / gs, gl = lane % gs;
+    const int64_t wg = (int64_t)z.rank * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)z.nb * (blockDim.x >> 5);
+    for (int64_t r = wg * G + grp; r * XCH < nx; r += nw * G) {
+        const int64_t e1 = min(r * XCH + XCH, nx);
+        int64_t cur = -1;
+        int32_t t0 = 0, nt = 0;
+        ff ar[MAXPL];
+#pragma unroll
+        for (int j = 0; j < MAXPL; j++) ar[j] = {0.f, 0.f};
+        auto flush = [&]() {
+#pragma unroll
+            for (int j = 0; j < MAXPL; j++) {
+                const int32_t k = gl + j * gs;
+                if (k < nt) atomicAdd(acc + t0 + k, (double)ar[j].h + (double)ar[j].l);
+                ar[j] = {0.f, 0.f};
+            }
+        };
+        for (int64_t e = r * XCH; e < e1; e++) {
+            const int32_t v = xidx[e];
+            if (!(v & SWAP_M2P)) continue;
+            const int64_t g = xtgt[e];
+            if (g != cur) {
+                flush();
+                cur = g;
+                t0 = lb[g - base];
+                nt = lb[g - base + 1] - t0;
+            }
+            const int64_t sg = base + (v & ~SWAP_M2P);
+            const ff dcx = ff_split(cen[2 * g] - cen[2 * sg]), dcy = ff_split(cen[2 * g + 1] - cen[2 * sg + 1]);
+            const ff rho = ff_split(rad[sg]);
+            const float4* A = Mff + sg * PS;
+            const float4 a0 = A[0];
+            // the lane's first MAXPL points together
+            cff w[MAXPL], h[MAXPL];
+            ff lg[MAXPL];
+#pragma unroll
+            for (int j = 0; j < MAXPL; j++) {
+                h[j] = {{0.f, 0.f}, {0.f, 0.f}};
+                w[j] = h[j];
+                lg[j] = {0.f, 0.f};
+                const int32_t k = gl + j * gs;
+                if (k < nt) {
+                    const float4 p = pk[2 * (t0 + k)];
+                    ff_inv_log(ff_add(ff{p.x, p.y}, dcx), ff_add(ff{p.z, p.w}, dcy), rho, ln2h, w[j], lg[j]);
+                }
+            }
+            for (int kk = P - 1; kk >= 1; kk--) {
+                const float4 a = A[kk];
+                const cff ak = {{a.x, a.y}, {a.z, a.w}};
+#pragma unroll
+                for (int j = 0; j < MAXPL; j++)
+                    if (gl + j * gs < nt) h[j] = cff_fma(h[j], w[j], ak);
+            }
+#pragma unroll
+            for (int j = 0; j < MAXPL; j++)
+                if (gl + j * gs < nt) {
+                    const ff re = ff_dot2(h[j].re, w[j].re, h[j].im, w[j].im, ff_mul(ff{a0.x, a0.y}, lg[j]));
+                    ar[j] = ff_add(ar[j], re);
+                }
+            // leaves of more than MAXPL gs points: the rest one at a time, added directly
+            for (int32_t k = gl + MAXPL * gs; k < nt; k += gs) {
+                const float4 p = pk[2 * (t0 + k)];
+                cff w1, h1 = {{0.f, 0.f}, {0.f, 0.f}};
+                ff lg1;
+                ff_inv_log(ff_add(ff{p.x, p.y}, dcx), ff_add(ff{p.z, p.w}, dcy), rho, ln2h, w1, lg1);
+                for (int kk = P - 1; kk >= 1; kk--) {
+                    const float4 a = A[kk];
+                    h1 = cff_fma(h1, w1, cff{{a.x, a.y}, {a.z, a.w}});
+                }
+                const ff re = ff_dot2(h1.re, w1.re, h1.im, w1.im, ff_mul(ff{a0.x, a0.y}, lg1));
+                atomicAdd(acc + t0 + k, (double)re.h + (double)re.l);
+            }
+        }
+        flush();
+    }
+}
+
+// Split-mode P2L: the walk of k_p2l (a warp per target leaf, the points of its P2L sources 32 at
+// a time, a lane per point) in float-float: u = rho_t / dz from the point's float-float offset
+// plus the binary64 centre difference c_s - c_g, the terms q log|dz| and q u^l through shared
+// memory (a float-float complex value per coefficient), the column sums in float-float; the leaf's
+// sums are added to its binary64 local expansion (b~_0 += sum q log|dz|, b~_l -= sum q u^l / l).
+// schedule: the leaves, WPB per block (the P2M schedule)
+__global__ void k_p2l_ff(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs, int P, int PS,
+                         const int32_t* __restrict__ lb, const float4* __restrict__ pk,
+                         const double* __restrict__ cen, const double* __restrict__ rad, XLists xl,
+                         cx<double>* __restrict__ Le)
+{
+    extern __shared__ unsigned char smem[];
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    const int L = S.L;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    if (L < 1) return;
+    lb += S.lb0;
+    pk += 2 * S.p0;
+    cen += 2 * S.b0;
+    rad += S.b0;
+    Le += S.b0 * PS;
+    const int32_t* xoff = xl.xoff + S.o0;
+    const int32_t* xidx = xl.xidx + LIs[z.i].s0;
+    const int64_t base = level_base(L);
+    const ff ln2h = ff_split(0.34657359027997264);  // ln(2) / 2
+    cff* Sm = (cff*)smem + (size_t)w * 33 * P;
+    for (int64_t b = (int64_t)z.rank * wpb + w; b < level_size(L); b += (int64_t)z.nb * wpb) {
+        const int64_t g = base + b;
+        const int32_t x0 = xoff[g], x1 = xoff[g + 1];
+        if (x0 == x1) continue;
+        const ff rho = ff_split(rad[g]);
+        cff acc[2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};
+        ff acc0 = {0.f, 0.f};
+        for (int32_t e0 = x0; e0 < x1; e0 += 32) {
+            // lane k describes entry e0 + k: its source's first point and count (0 for M2P entries)
+            int32_t cnt = 0, first = 0, src = 0;
+            if (e0 + lane < x1) {
+                const int32_t v = xidx[e0 + lane];
+                if (!(v & SWAP_M2P)) {
+                    first = lb[v];
+                    cnt = lb[v + 1] - first;
+                    src = v;
+                }
+            }
+            int32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int32_t excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int32_t f0 = 0; f0 < total; f0 += 32) {
+                const int32_t fi = f0 + lane;
+                // owner: the last lane k with excl_k <= fi (excl is non-decreasing)
+                int k = 0;
+#pragma unroll
+                for (int st = 16; st; st >>= 1) {
+                    const int cand = k + st;
+                    const int32_t ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+                    if (cand < 32 && ec <= fi) k = cand;
+                }
+                const int32_t fk = __shfl_sync(0xffffffffu, first, k);
+                const int32_t ek = __shfl_sync(0xffffffffu, excl, k);
+                const int32_t sk = __shfl_sync(0xffffffffu, src, k);
+                cff pw = {{0.f, 0.f}, {0.f, 0.f}}, u = pw;
+                ff lg = {0.f, 0.f};
+                if (fi < total) {
+                    const int64_t ip = fk + (fi - ek);
+                    const float4 p = pk[2 * ip], pq = pk[2 * ip + 1];
+                    const int64_t sgb = base + sk;
+                    const ff dx = ff_add(ff{p.x, p.y}, ff_split(cen[2 * sgb] - cen[2 * g]));
+                    const ff dy = ff_add(ff{p.z, p.w}, ff_split(cen[2 * sgb + 1] - cen[2 * g + 1]));
+                    ff_inv_log(dx, dy, rho, ln2h, u, lg);
+                    const ff q = {pq.x, pq.y};
+                    pw.re = q;
+                    lg = ff_mul(q, lg);
+                }
+                Sm[lane] = {lg, {0.f, 0.f}};
+                for (int l = 1; l < P; l++) {
+                    pw = cff_mul(pw, u);
+                    Sm[l * 33 + lane] = pw;
+                }
+                __syncwarp();
+                for (int l = lane, s2 = 0; l < P; l += 32, s2++) {
+                    cff sum = Sm[l * 33];
+                    for (int j = 1; j < 32; j++) sum = cff_add(sum, Sm[l * 33 + j]);
+                    if (l == 0) acc0 = ff_add(acc0, sum.re);
+                    else acc[s2] = cff_add(acc[s2], sum);
+                }
+                __syncwarp();
+            }
+        }
+        cx<double>* B = Le + g * PS;
+        for (int l = lane, s2 = 0; l < P; l += 32, s2++) {
+            if (l == 0) {
+                B[0].re += (double)acc0.h + (double)acc0.l;
+            } else {
+                const double re = (double)acc[s2].re.h + (double)acc[s2].re.l;
+                const double im = (double)acc[s2].im.h + (double)acc[s2].im.l;
+                B[l].re -= re / l;
+                B[l].im -= im / l;
+            }
+        }
+    }
+}
+
 __global__ void k_unpermute(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                             const double* __restrict__ acc, double* __restrict__ phi)
 {
@@ -2371,6 +2679,14 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
             return fail(FMM_ERR_OOM, "accumulator");
         if (!t->pkff && cudaMalloc(&t->pkff, 32 * (size_t)t->n) != cudaSuccess)
             return fail(FMM_ERR_OOM, "packed points");
+        if ((li->mode & FMM_LISTS_EXCHANGE) && t->mff_ps < PS) {  // float-float multipoles for M2P
+            cudaFree(t->mff);
+            t->mff = nullptr;
+            t->mff_ps = 0;
+            if (cudaMalloc(&t->mff, 16 * (size_t)t->nbox * PS) != cudaSuccess)
+                return fail(FMM_ERR_OOM, "float-float multipoles");
+            t->mff_ps = PS;
+        }
     }
     if (field) {
         if (f64 && !t->accf && cudaMalloc((void**)&t->accf, 16 * (size_t)t->n) != cudaSuccess)
@@ -2482,6 +2798,16 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     // P2L into the leaves' local expansions (role exchange) before they are evaluated
     auto p2l = [&]() -> int {
         if (!swp) return 0;
+        if (near32) {  // split mode: float-float
+            const size_t sm = (size_t)WPB * 33 * P * sizeof(cff);
+            FMM_CUDA(cudaFuncSetAttribute(k_p2l_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_p2l_ff<<<t->s_p2m.blocks, 32 * WPB, sm, s>>>(t->s_p2m.d, I, LI, P, PS, t->leaf_begin,
+                                                           (const float4*)t->pkff, t->centers, t->radii, xl,
+                                                           (cx<double>*)Le);
+            note_launch();
+            FMM_LAUNCH_CHECK("evaluate: P2L");
+            return 0;
+        }
         const size_t sm = (size_t)WPB * 33 * P * sizeof(cx<T>);
         FMM_CUDA(cudaFuncSetAttribute(k_p2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_p2l<T><<<t->s_p2m.blocks, 32 * WPB, sm, s>>>(t->s_p2m.d, I, LI, P, PS, t->leaf_begin, pk, geo, xl, Le,
@@ -2603,7 +2929,17 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
                                           f64 ? (T*)t->acc : (T*)far32, farlo);
             note_launch();
         }
-        if (swp) {
+        if (swp && near32) {  // split mode: float-float, from a float-float copy of the multipoles
+            StageScope x_scope(FMM_STAGE_EXCHANGE, s);
+            const int64_t count = t->nbox * PS;
+            k_coeffs_ff<<<(unsigned)std::min<int64_t>((count + 255) / 256, 152 * 16), 256, 0, s>>>(
+                (const double2*)Me, count, (float4*)t->mff);
+            note_launch();
+            k_m2p_ff<<<(unsigned)t->s_p2p.blocks, 256, 0, s>>>(t->s_p2p.d, I, LI, P, PS, gsx, t->leaf_begin,
+                                                               (const float4*)t->pkff, t->centers, t->radii, xl,
+                                                               (const float4*)t->mff, t->acc);
+            note_launch();
+        } else if (swp) {
             StageScope x_scope(FMM_STAGE_EXCHANGE, s);
             k_m2p<T, false><<<(unsigned)t->s_p2p.blocks, 256, 0, s>>>(t->s_p2p.d, I, LI, P, PS, gsx, t->leaf_begin, pk,
                                                                      geo, xl, Me, f64 ? (T*)t->acc : (T*)far32,

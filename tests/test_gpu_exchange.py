@@ -70,7 +70,8 @@ def test_exchange_lists_bit_exact(built, orc, cuda, name, theta):
 
 @pytest.mark.parametrize("name", [c[0] for c in CASES])
 @pytest.mark.parametrize("mode,p,tol,kind", [("fp64", 17, 1e-12, 0), ("mixed", 20, 1e-6, 1), ("mixed", 20, 1e-6, 2),
-                                             ("mixed", 30, 1e-6, 0)])
+                                             ("mixed", 30, 1e-6, 0), ("split", 17, 1e-11, 0),
+                                             ("split", 30, 1e-11, 0)])
 def test_exchange_potentials(built, orc, fmmlib, cuda, name, mode, p, tol, kind):
     c, L, f = built[name]
     fmmlib.fmm_set_m2l_kernel(f.tree, kind)
@@ -91,13 +92,27 @@ def test_exchange_field(built, orc, cuda, name, mode, p, tol):
     assert relerr(got, ref) <= tol
 
 
+@pytest.mark.parametrize("n,L,seed", [(4 ** 3 * 200, 3, 93), (4 ** 2 * 700 + 9, 2, 94)])
+def test_exchange_split_large_leaves(fmmlib, orc, cuda, n, L, seed):
+    # leaves of 200 and about 700 points: the float-float M2P's lanes hold more than their four
+    # points in registers and take the rest one at a time
+    c = W.normal(n, seed)
+    f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), L, 0.5, exchange=True)
+    try:
+        assert _check_lists(f, orc, c, L, 0.5, parents=False) > 0
+        got = f.evaluate(_t(c.q, cuda), 20, "split").cpu().numpy()
+    finally:
+        f.close()
+    assert relerr(got, orc.fmm(c.x, c.y, c.q, L, 20, 0.5, swap=True)) <= 1e-11
+
+
 def test_exchange_with_parent_entries(fmmlib, orc, cuda):
     c = W.clusters(25000, 87)
     L = 5
     f = fmmlib.FMM(_t(c.x, cuda), _t(c.y, cuda), L, 0.5, parents=True, exchange=True)
     try:
         assert _check_lists(f, orc, c, L, 0.5, parents=True) > 0
-        for mode, p, tol in (("fp64", 17, 1e-12), ("mixed", 20, 1e-6)):
+        for mode, p, tol in (("fp64", 17, 1e-12), ("mixed", 20, 1e-6), ("split", 24, 1e-11)):
             got = f.evaluate(_t(c.q, cuda), p, mode).cpu().numpy()
             assert relerr(got, orc.fmm(c.x, c.y, c.q, L, p, 0.5, parents=True, swap=True)) <= tol
     finally:
@@ -120,7 +135,7 @@ def test_exchange_forest(fmmlib, orc, cuda):
             assert np.array_equal(sidx.cpu().numpy().astype(np.int64), osi)
             assert np.array_equal(xoff.cpu().numpy().astype(np.int64), ox)
             assert np.array_equal(xidx.cpu().numpy().astype(np.int64), oxi)
-        for mode, p, tol in (("fp64", 16, 1e-12), ("mixed", 20, 1e-6)):
+        for mode, p, tol in (("fp64", 16, 1e-12), ("mixed", 20, 1e-6), ("split", 20, 1e-11)):
             phi = b.evaluate(_t(q, cuda), p, mode).cpu().numpy()
             for d, c, L in zip(b.inst, clouds, levels):
                 ref = orc.fmm(c.x, c.y, c.q, L, p, 0.5, swap=True)
