@@ -431,6 +431,8 @@ def profile_run(a):
         c, L, theta, p = W.mixed_1m_cloud(), W.MIXED_1M.levels, W.MIXED_1M.theta, p or W.MIXED_1M.p
     elif a.workload == "uniform-1m":
         c, L, theta, p = W.uniform(1 << 20, W.SEED_BASE + 7), 8, 0.5, p or 20
+    elif a.workload == "rings-1m":  # the 2^24-point workload's distribution at 2^20 points, 64 per leaf
+        c, L, theta, p = W.rings_plummer(1 << 20, W.SEED_BASE + 8), 7, 0.5, p or W.LARGE_16M.p
     else:
         c, L, theta, p = W.large_16m_cloud(), W.LARGE_16M.levels, W.LARGE_16M.theta, p or W.LARGE_16M.p
     lists = a.lists if a.lists != "auto" else "parents"
@@ -442,7 +444,7 @@ def profile_run(a):
         fmm.fmm_set_m2l_shape(f.tree, *(int(v) for v in a.m2l_shape.split(",")))
         if a.blocks:
             fmm.fmm_set_launch(f.tree, *(int(v) for v in a.blocks.split(",")))
-        mode = fmm.FMM_MODE_MIXED if a.mode == "mixed" else fmm.FMM_MODE_FP64
+        mode = {"mixed": fmm.FMM_MODE_MIXED, "fp64": fmm.FMM_MODE_FP64, "split": fmm.FMM_MODE_SPLIT}[a.mode]
         phi = torch.empty(c.x.shape[0], dtype=torch.float64, device=dev)
         if a.stage_times:  # one untimed run first, then the library's per-stage CUDA events
             fmm.fmm_evaluate(f.tree, f.lists, q, p, mode, phi)
@@ -615,10 +617,10 @@ def main():
     ap.add_argument("--profile-steps", action="store_true")
     ap.add_argument("--stage-times", action="store_true",
                     help="with --profile-run: print the mean per-stage device time (ms) of the K runs")
-    ap.add_argument("--workload", default="clusters-1m", choices=["clusters-1m", "uniform-1m", "rings-16m"],
+    ap.add_argument("--workload", default="clusters-1m", choices=["clusters-1m", "uniform-1m", "rings-1m", "rings-16m"],
                     help="workload of --profile-run")
     ap.add_argument("--p", type=int, default=None, help="expansion order of --profile-run (workload's default)")
-    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"], help="precision of --profile-run")
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64", "split"], help="precision of --profile-run")
     ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"], help="M2L kernel of --profile-run")
     ap.add_argument("--m2l-shape", default="0,0", metavar="CHUNK,STAGES",
                     help="tensor-core M2L tile shape of --profile-run: consecutive weak entries per row and TMEM "
