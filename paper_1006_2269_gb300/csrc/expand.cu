@@ -1101,13 +1101,14 @@ __global__ void __launch_bounds__(256) k_m2p(Sched sc, const Inst* __restrict__ 
 }
 
 // ---- L2P: one thread per point (canonical order) ----
-// binary64 path: adds to the binary64 accumulator, which already holds the near field.  binary32
-// path: writes the binary32 far field (float-float); the near-field accumulators are combined
+// binary64 path: adds to the binary64 accumulator, which already holds the near field (or, in
+// the split mode, the M2P values).  binary32 path: writes the binary32 far field (float-float),
+// or with `add` adds to the M2P values already there; the near-field accumulators are combined
 // with it at the end.
 template <typename T>
 __global__ void k_l2p(Sched sc, const Inst* __restrict__ I, int P, int PS, const int32_t* __restrict__ cleaf,
                       const Pk<T>* __restrict__ pk, Geo<T> geo, const cx<T>* __restrict__ Le,
-                      const float* __restrict__ L0lo, T* __restrict__ far, float* __restrict__ farlo)
+                      const float* __restrict__ L0lo, T* __restrict__ far, float* __restrict__ farlo, bool add)
 {
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
@@ -1133,6 +1134,13 @@ __global__ void k_l2p(Sched sc, const Inst* __restrict__ I, int P, int PS, const
             for (int k = P - 1; k >= 1; k--) h = cfma(h, z, B[k]);
             T hi = B[0].re, lo = L0lo[g];
             two_sum(hi, lo, cmul(h, z).re);
+            if (add) {  // onto the M2P values already there
+                T fh = far[i];
+                float fl = farlo[i];
+                two_sum(fh, fl, hi);
+                hi = fh;
+                lo += fl;
+            }
             far[i] = hi;
             farlo[i] = lo;
         } else {
@@ -2919,34 +2927,32 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
     }
     if (overlap) FMM_CUDA(cudaEventRecord(sync->near_done, ns));
     {
+        // role exchange: P2L into the leaves' local expansions, M2P into the far accumulator
+        // (the binary32 one is cleared first, and L2P then adds to it)
         if (swp) {
             StageScope x_scope(FMM_STAGE_EXCHANGE, s);
             if ((rc = p2l())) return rc;
-        }
-        {
-            StageScope leaf_scope(FMM_STAGE_LEAF, s);
-            k_l2p<T><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo,
-                                          f64 ? (T*)t->acc : (T*)far32, farlo);
+            if (near32) {  // split mode: float-float, from a float-float copy of the multipoles
+                const int64_t count = t->nbox * PS;
+                k_coeffs_ff<<<(unsigned)std::min<int64_t>((count + 255) / 256, 152 * 16), 256, 0, s>>>(
+                    (const double2*)Me, count, (float4*)t->mff);
+                note_launch();
+                k_m2p_ff<<<(unsigned)t->s_p2p.blocks, 256, 0, s>>>(t->s_p2p.d, I, LI, P, PS, gsx, t->leaf_begin,
+                                                                   (const float4*)t->pkff, t->centers, t->radii,
+                                                                   xl, (const float4*)t->mff, t->acc);
+            } else {
+                if (!f64) FMM_CUDA(cudaMemsetAsync(far32, 0, 2 * 4 * (size_t)n, s));  // far32, farlo
+                k_m2p<T, false><<<(unsigned)t->s_p2p.blocks, 256, 0, s>>>(t->s_p2p.d, I, LI, P, PS, gsx,
+                                                                         t->leaf_begin, pk, geo, xl, Me,
+                                                                         f64 ? (T*)t->acc : (T*)far32, farlo,
+                                                                         nullptr, nullptr);
+            }
             note_launch();
         }
-        if (swp && near32) {  // split mode: float-float, from a float-float copy of the multipoles
-            StageScope x_scope(FMM_STAGE_EXCHANGE, s);
-            const int64_t count = t->nbox * PS;
-            k_coeffs_ff<<<(unsigned)std::min<int64_t>((count + 255) / 256, 152 * 16), 256, 0, s>>>(
-                (const double2*)Me, count, (float4*)t->mff);
-            note_launch();
-            k_m2p_ff<<<(unsigned)t->s_p2p.blocks, 256, 0, s>>>(t->s_p2p.d, I, LI, P, PS, gsx, t->leaf_begin,
-                                                               (const float4*)t->pkff, t->centers, t->radii, xl,
-                                                               (const float4*)t->mff, t->acc);
-            note_launch();
-        } else if (swp) {
-            StageScope x_scope(FMM_STAGE_EXCHANGE, s);
-            k_m2p<T, false><<<(unsigned)t->s_p2p.blocks, 256, 0, s>>>(t->s_p2p.d, I, LI, P, PS, gsx, t->leaf_begin, pk,
-                                                                     geo, xl, Me, f64 ? (T*)t->acc : (T*)far32,
-                                                                     farlo, nullptr, nullptr);
-            note_launch();
-        }
-        StageScope leaf_scope(FMM_STAGE_LEAF, s);  // far and near joined
+        StageScope leaf_scope(FMM_STAGE_LEAF, s);  // L2P, far and near joined
+        k_l2p<T><<<gpts, 256, 0, s>>>(spts, I, P, PS, t->cleaf, pk, geo, Le, t->Lf0lo,
+                                      f64 ? (T*)t->acc : (T*)far32, farlo, swp);
+        note_launch();
         if (overlap) FMM_CUDA(cudaStreamWaitEvent(s, sync->near_done, 0));
         if (near32)
             k_combine64<<<gpts, 256, 0, s>>>(spts, I, t->perm, t->acc, nhi, nlo, phi);

@@ -101,24 +101,27 @@ def test_step_graph_replay(fmmlib, orc, cuda):
         f.close()
 
 
-def test_step_profile_has_every_stage(fmmlib, cuda):
+@pytest.mark.parametrize("exchange,mode", [(False, "mixed"), (True, "mixed"), (True, "split"), (True, "fp64")])
+def test_step_profile_has_every_stage(fmmlib, cuda, exchange, mode):
+    # every stage is timed once per step; the role-exchange stage only with exchange lists
     import torch
     c = W.clusters(30000, 70)
     x, y, q = _t(c.x, cuda), _t(c.y, cuda), _t(c.q, cuda)
-    f = fmmlib.FMM(x, y, 5, 0.5)
+    f = fmmlib.FMM(x, y, 5, 0.5, exchange=exchange)
+    m = {"mixed": fmmlib.FMM_MODE_MIXED, "split": fmmlib.FMM_MODE_SPLIT, "fp64": fmmlib.FMM_MODE_FP64}[mode]
     try:
         phi = torch.empty(c.x.size, dtype=torch.float64, device=cuda)
-        fmmlib.fmm_step(f.tree, f.lists, x, y, 0.5, q, 20, fmmlib.FMM_MODE_MIXED, phi)
+        fmmlib.fmm_step(f.tree, f.lists, x, y, 0.5, q, 20, m, phi)
         torch.cuda.synchronize()
         fmmlib.fmm_profile_read()
         fmmlib.fmm_profile_enable(True)
         for _ in range(3):
-            fmmlib.fmm_step(f.tree, f.lists, x, y, 0.5, q, 20, fmmlib.FMM_MODE_MIXED, phi)
+            fmmlib.fmm_step(f.tree, f.lists, x, y, 0.5, q, 20, m, phi)
         torch.cuda.synchronize()
         fmmlib.fmm_profile_enable(False)
         prof = fmmlib.fmm_profile_read()
         for st in fmmlib.STAGES:
-            if st == "exchange":  # plain lists: no role-exchange entries, no P2L or M2P
+            if st == "exchange" and not exchange:  # plain lists: no P2L or M2P
                 assert prof[st][1] == 0, st
                 continue
             assert prof[st][1] == 3 and prof[st][0] > 0, st
