@@ -68,8 +68,15 @@ def fallback_params(n: int, tol: float, theta: float = THETA, leaf: float = 20.0
     return L, p
 
 
+PROBE_LMAX = 7  # deepest probe tree (N >= 4^8 * 16 = 1,048,576 points would go one level deeper)
+
+
 def probe_levels(n: int) -> int:
-    return max(1, min(LMAX, int(math.floor(math.log(max(n / 16.0, 1.0)) / math.log(4.0)))))
+    """Levels of the tree the features are read from: about 16 points per leaf, at most
+    PROBE_LMAX.  The training sets (N <= 1e6) never reach an eighth level, so a larger set's
+    features stay in the range the network was trained on (an eighth level's occupancy block,
+    zero in every training sample, turned the choice for 2^20 points into nonsense)."""
+    return max(1, min(PROBE_LMAX, int(math.floor(math.log(max(n / 16.0, 1.0)) / math.log(4.0)))))
 
 
 def _t(a, dev, dtype=torch.float64):

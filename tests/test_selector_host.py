@@ -40,3 +40,30 @@ def test_candidates_are_feasible(n):
     assert S.probe_levels(n) <= S.max_levels(n)
     for tol in S.TOLS:
         assert all(S.PMIN <= p <= S.PMAX for p in S.candidate_ps(tol))
+
+
+def test_probe_depth():
+    # about 16 points per leaf inside the training range (N <= 1e6), never deeper than its deepest
+    for n in (10 ** 4, 37000, 2 * 10 ** 5, 10 ** 6):
+        assert S.probe_levels(n) == math.floor(math.log(n / 16) / math.log(4))
+    assert S.probe_levels(10 ** 6) == S.PROBE_LMAX
+    assert S.probe_levels(1 << 20) == S.probe_levels(1 << 24) == S.PROBE_LMAX
+
+
+def test_committed_weights_on_benchmark_cloud():
+    # the committed network on the 2^20-point clustered cloud (features of the oracle's probe
+    # tree): the trees it picks hold 16 to 64 points per leaf, as the labels of the training
+    # sets near 1e6 points do
+    import numpy as np
+    import oracle as orc
+    from oracle import mlp as M
+    from paper_1006_2269_gb300 import workloads as W
+    params = np.fromfile(S.WEIGHTS + ".f32", dtype=np.float32).astype(np.float64)
+    c = W.mixed_1m_cloud()
+    n = c.x.shape[0]
+    L = S.probe_levels(n)
+    _, rects, _ = orc.tree(c.x, c.y, L)
+    for tol in S.TOLS:
+        prob = M.forward(params, M.features(rects, L, n, tol)[None])[0]
+        levels, p = S.params_of(int(np.argmax(prob)))
+        assert levels in (7, 8), (tol, levels, p)
