@@ -887,6 +887,7 @@ def main():
                        "m2l": tuned[fmm.FMM_MODE_MIXED][0], "near_field": tuned[fmm.FMM_MODE_MIXED][1]},
                    "m2l_kernel": "tensor cores (tcgen05, split tf32)" if m2l_kind == fmm.FMM_M2L_TENSOR
                    else "SIMT binary32",
+                   "near_targets_per_lane": fmm.fmm_get_near_shape(f.tree) or 2,
                    "lists": lists_kind + ("" if lists_kind == "plain" else " (Section 4's optional optimisations)"),
                    "lists_trial_ms_per_step": lists_ms or None},
         "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,

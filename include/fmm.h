@@ -317,7 +317,8 @@ int fmm_step(fmm_tree t, fmm_lists l, const double* x, const double* y, double t
  * phi receives the potentials of the last run.  It synchronises with the host (not for use under
  * stream capture).  The chosen totals are reported in m2l_blocks / p2p_blocks (host, may be
  * NULL).  For the mixed path it also times the two binary32 M2L kernels (fmm_set_m2l_kernel)
- * and keeps the faster.  fmm_set_launch sets the totals directly (0 = the built-in default); it
+ * with their tile shapes and the near field's targets per lane (fmm_set_near_shape), and keeps
+ * the fastest.  fmm_set_launch sets the totals directly (0 = the built-in default); it
  * uploads small launch tables and so also synchronises.  Both replace the tree's launch tables
  * and grid sizes: a CUDA graph captured before either call still names the old ones and must
  * not be launched again; capture it anew. */
@@ -346,6 +347,14 @@ int fmm_get_m2l_kernel(fmm_tree t);
  * fmm_get_m2l_shape reports them (host pointers, may be NULL). */
 int fmm_set_m2l_shape(fmm_tree t, int chunk, int stages);
 int fmm_get_m2l_shape(fmm_tree t, int* chunk, int* stages);
+
+/* Work shape of the binary32 near field for leaves of at most 64 points (no paper counterpart):
+ * every lane takes `targets` points of a target leaf (2 or 4) against each source leaf, so each
+ * source point it loads serves that many pair evaluations and the per-leaf-pair set-up is shared
+ * by as many; 0 = the built-in default (2).  fmm_autotune chooses it with the block count.
+ * fmm_get_near_shape reports it (host pointer, may be NULL). */
+int fmm_set_near_shape(fmm_tree t, int targets);
+int fmm_get_near_shape(fmm_tree t, int* targets);
 
 /* ---------------------------------------------------------------------------------------------
  * Throughput probes (no paper counterpart): the peaks of the units the ALU-bound kernels use,
@@ -420,7 +429,11 @@ int fmm_mlp_train_step(fmm_mlp m, const float* X, const int32_t* labels, int B, 
                        void* stream);
 
 /* The selector's choice for B feature vectors (device): levels_p[B][2] = (levels, p) of the most
- * probable class among those with 4^levels <= N (device int32). */
+ * probable class among those whose levels lie in the window the training labels are drawn from,
+ * Lc - 2 <= levels <= Lc + 1 with Lc = round(log4(N / 32)) rounded half up (= floor((b - 4) / 2),
+ * b = floor(log2 N)), and have 4^levels <= N; N is read from the log10 N feature.  Where that
+ * window is empty (very small N) every class with 4^levels <= N, and levels = 4, is allowed
+ * (device int32). */
 int fmm_select_params(fmm_mlp m, const float* features, int B, int32_t* levels_p, void* stream);
 
 /* The complex field of Section 5's first experiment, G(z_i, z_j) = -q_j / (z_i - z_j):

@@ -628,6 +628,22 @@ int fmm_get_m2l_shape(fmm_tree t, int* chunk, int* stages)
     return FMM_OK;
 }
 
+int fmm_set_near_shape(fmm_tree t, int targets)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (targets != 0 && targets != 2 && targets != 4)
+        return fail(FMM_ERR_ARG, "near-field targets per lane %d: 0, 2 or 4", targets);
+    t->tune_p2p_nt = targets;
+    return FMM_OK;
+}
+
+int fmm_get_near_shape(fmm_tree t, int* targets)
+{
+    if (!t) return fail(FMM_ERR_ARG, "NULL tree");
+    if (targets) *targets = t->tune_p2p_nt;
+    return FMM_OK;
+}
+
 int fmm_set_launch(fmm_tree t, int m2l_blocks, int p2p_blocks)
 {
     if (!t) return fail(FMM_ERR_ARG, "NULL tree");

@@ -269,6 +269,7 @@ struct fmm_tree_s {
     int tune_m2l_blocks = 0, tune_p2p_blocks = 0;
     int tune_m2l_chunk = 0;   // tensor-core M2L: consecutive weak entries per row (0 = default)
     int tune_m2l_stages = 0;  // tensor-core M2L: TMEM accumulator stages 1 or 2 (0 = by order)
+    int tune_p2p_nt = 0;      // binary32 near field: targets per lane 2 or 4 (0 = default)
     int m2l_kind = 0;  // binary32 M2L: 0 = by order (tensor cores for 24 <= P <= 32), 1 = SIMT, 2 = tensor cores
 
     // launch schedules (device tables only for forests of more than one instance)

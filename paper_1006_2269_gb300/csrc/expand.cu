@@ -1320,11 +1320,13 @@ __device__ __forceinline__ float p2p_exact(float xt, float yt, int32_t it, const
 }
 
 // binary32 near field for leaves of at most 64 points.  Groups of gsl lanes work on one leaf pair,
-// each lane on two targets (t0 + li and t0 + li + gsl), so a warp holds 32 / gsl leaf pairs at
-// once and every source load serves two pair evaluations; each group walks its own run of
-// consecutive leaf pairs and flushes its sums when the target leaf changes.  The main loop has no
+// each lane on NT targets (t0 + li + k gsl, k < NT), so a warp holds 32 / gsl leaf pairs at once
+// and every source load serves NT pair evaluations; each group walks its own run of consecutive
+// leaf pairs and flushes its sums when the target leaf changes.  More targets per lane spread the
+// per-leaf-pair set-up (geometry loads, scale, flushes) over more pairs.  The main loop has no
 // branch: it keeps the smallest r^2 it met and, for the rare lane whose minimum falls below the
 // exactness threshold, the leaf pair is redone by the exact path.
+template <int NT>
 __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
                                                  const int32_t* __restrict__ soff,
                                                  const int32_t* __restrict__ sidx,
@@ -1355,11 +1357,11 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
     rad32 += S.b0;
     nhi += S.p0;
     nlo += S.p0;
-    // groups of gsl lanes, two targets per lane: gsl = pow2ceil(largest leaf of this instance) / 2
+    // groups of gsl lanes, NT targets per lane: gsl = pow2ceil(largest leaf of this instance) / NT
     const int64_t maxleaf = (int64_t)S.maxleaf;
     if (maxleaf > 64) return;  // left to k_p2p_large
     int gsl = 1;
-    while (2 * gsl < maxleaf) gsl <<= 1;
+    while (NT * gsl < maxleaf) gsl <<= 1;
     const int lane = threadIdx.x & 31, G = 32 / gsl, grp = lane / gsl, li = lane - grp * gsl;
     const int32_t base = (int32_t)level_base(L);
     const int64_t e_begin = min((int64_t)soff[base], scap);
@@ -1372,26 +1374,37 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
     for (int64_t w0 = e_begin + warp * wch; w0 < e_end; w0 += nwarps * wch) {
         const int64_t e0 = w0 + (int64_t)grp * P2P_GROUP_CH;
         const int64_t e1 = min(e0 + P2P_GROUP_CH, e_end);
-        int32_t cur = -1, it0 = 0, it1 = 0;
-        bool v0 = false, v1 = false;
-        float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, tq0 = 0.f, tq1 = 0.f;
-        float hi0 = 0.f, lo0 = 0.f, hi1 = 0.f, lo1 = 0.f;
+        int32_t cur = -1, t0 = 0, nt = 0;
+        float tx[NT], ty[NT], tq[NT], hi[NT], lo[NT];
+#pragma unroll
+        for (int k = 0; k < NT; k++) tx[k] = ty[k] = tq[k] = hi[k] = lo[k] = 0.f;
+        auto flush = [&]() {
+#pragma unroll
+            for (int k = 0; k < NT; k++)
+                if (li + k * gsl < nt) {
+                    atomicAdd(&nhi[t0 + li + k * gsl], hi[k]);
+                    atomicAdd(&nlo[t0 + li + k * gsl], lo[k]);
+                }
+        };
         for (int64_t e = e0; e < e1; e++) {
             const int32_t tl = stgt[e] - base;
             if (tl != cur) {
-                if (v0) { atomicAdd(&nhi[it0], hi0); atomicAdd(&nlo[it0], lo0); }
-                if (v1) { atomicAdd(&nhi[it1], hi1); atomicAdd(&nlo[it1], lo1); }
+                if (cur >= 0) flush();
                 cur = tl;
-                const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0;
-                it0 = t0 + li;
-                it1 = t0 + li + gsl;
-                v0 = li < nt;
-                v1 = li + gsl < nt;
-                hi0 = lo0 = hi1 = lo1 = 0.f;
-                if (v0) { const Pk<float> p = pk[it0]; tx0 = p.x; ty0 = p.y; tq0 = p.q; }
-                if (v1) { const Pk<float> p = pk[it1]; tx1 = p.x; ty1 = p.y; tq1 = p.q; }
+                t0 = lb[tl];
+                nt = lb[tl + 1] - t0;
+#pragma unroll
+                for (int k = 0; k < NT; k++) {
+                    hi[k] = lo[k] = 0.f;
+                    if (li + k * gsl < nt) {
+                        const Pk<float> p = pk[t0 + li + k * gsl];
+                        tx[k] = p.x;
+                        ty[k] = p.y;
+                        tq[k] = p.q;
+                    }
+                }
             }
-            if (!v0) continue;  // v1 implies v0
+            if (li >= nt) continue;  // target k > 0 valid implies target 0 valid
             const int32_t sl = sidx[e];
             const int32_t s0 = lb[sl], ns = lb[sl + 1] - s0;
             const int32_t sg = base + sl, tg = base + tl;
@@ -1399,58 +1412,65 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
             const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
             const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
             const float tau2 = fmaxf((M * (1.f / 256.f)) * (M * (1.f / 256.f)), 1e-30f);
-            // logs are taken of r^2 / M^2, near 1 for most pairs, and log2(M^2) times the sources'
-            // strength is added once per leaf pair: the running sums stay small, and so do their
-            // rounding errors
+            // logs are taken of r^2 / 2^e, 2^e the power of two at or below M^2 (near 1 for most
+            // pairs), and e times the sources' strength is added once per leaf pair: the running
+            // sums stay small, and the scaling and its logarithm are exact
             const float M2 = M * M;
             const bool scaled = M2 > 1e-30f && M2 < 1e30f;
-            const float s2 = scaled ? 1.f / M2 : 1.f;
-            const float c2 = scaled ? lg2_fast(M2) : 0.f;
-            const float xa = tx0 - ox, ya = ty0 - oy, xb = tx1 - ox, yb = ty1 - oy;
-            float pa = 0.f, pb = 0.f, ma = 3.0e38f, mb = 3.0e38f, qs = 0.f;
+            const int ex = scaled ? (int)((__float_as_uint(M2) >> 23) & 0xff) - 127 : 0;
+            const float s2 = __uint_as_float((uint32_t)(127 - ex) << 23);  // 2^-ex
+            const float c2 = (float)ex;
+            float xa[NT], ya[NT], pa[NT], ma[NT];
+#pragma unroll
+            for (int k = 0; k < NT; k++) {
+                xa[k] = tx[k] - ox;
+                ya[k] = ty[k] - oy;
+                pa[k] = 0.f;
+                ma[k] = 3.0e38f;
+            }
+            float qs = 0.f;
             const Pk<float>* src = pk + s0;
             if (sl != tl) {
-#pragma unroll 4
+#pragma unroll 8 / NT
                 for (int32_t j = 0; j < ns; j++) {
                     const Pk<float> sp = src[j];
-                    const float dxa = xa - sp.x, dya = ya - sp.y;
-                    const float dxb = xb - sp.x, dyb = yb - sp.y;
-                    const float ra = dxa * dxa + dya * dya, rb = dxb * dxb + dyb * dyb;
-                    ma = fminf(ma, ra);
-                    mb = fminf(mb, rb);
                     qs += sp.q;
-                    pa += sp.q * lg2_fast(ra * s2);
-                    pb += sp.q * lg2_fast(rb * s2);
+#pragma unroll
+                    for (int k = 0; k < NT; k++) {
+                        const float dx = xa[k] - sp.x, dy = ya[k] - sp.y;
+                        const float r = dx * dx + dy * dy;
+                        ma[k] = fminf(ma[k], r);
+                        pa[k] += sp.q * lg2_fast(r * s2);
+                    }
                 }
-                pa += c2 * qs;
-                pb += c2 * qs;
+#pragma unroll
+                for (int k = 0; k < NT; k++) pa[k] += c2 * qs;
             } else {
                 // the leaf with itself: a point meets itself once; that term is left out
-                const int32_t ia = it0 - s0, ib = it1 - s0;
-#pragma unroll 4
+#pragma unroll 8 / NT
                 for (int32_t j = 0; j < ns; j++) {
                     const Pk<float> sp = src[j];
-                    const float dxa = xa - sp.x, dya = ya - sp.y;
-                    const float dxb = xb - sp.x, dyb = yb - sp.y;
-                    float ra = dxa * dxa + dya * dya, rb = dxb * dxb + dyb * dyb;
-                    ra = j == ia ? 3.0e38f : ra;
-                    rb = j == ib ? 3.0e38f : rb;
-                    ma = fminf(ma, ra);
-                    mb = fminf(mb, rb);
                     qs += sp.q;
-                    pa += j == ia ? 0.f : sp.q * lg2_fast(ra * s2);
-                    pb += j == ib ? 0.f : sp.q * lg2_fast(rb * s2);
+#pragma unroll
+                    for (int k = 0; k < NT; k++) {
+                        const bool self = j == li + k * gsl;
+                        const float dx = xa[k] - sp.x, dy = ya[k] - sp.y;
+                        const float r = self ? 3.0e38f : dx * dx + dy * dy;
+                        ma[k] = fminf(ma[k], r);
+                        pa[k] += self ? 0.f : sp.q * lg2_fast(r * s2);
+                    }
                 }
-                pa += c2 * (qs - tq0);
-                pb += c2 * (qs - tq1);
+#pragma unroll
+                for (int k = 0; k < NT; k++) pa[k] += c2 * (qs - tq[k]);
             }
-            if (ma < tau2) pa = p2p_exact(xa, ya, it0, pk, s0, ns, tau2, xs, ys);
-            if (v1 && mb < tau2) pb = p2p_exact(xb, yb, it1, pk, s0, ns, tau2, xs, ys);
-            two_sum(hi0, lo0, pa);
-            if (v1) two_sum(hi1, lo1, pb);
+#pragma unroll
+            for (int k = 0; k < NT; k++)
+                if (li + k * gsl < nt) {
+                    if (ma[k] < tau2) pa[k] = p2p_exact(xa[k], ya[k], t0 + li + k * gsl, pk, s0, ns, tau2, xs, ys);
+                    two_sum(hi[k], lo[k], pa[k]);
+                }
         }
-        if (v0) { atomicAdd(&nhi[it0], hi0); atomicAdd(&nlo[it0], lo0); }
-        if (v1) { atomicAdd(&nhi[it1], hi1); atomicAdd(&nlo[it1], lo1); }
+        flush();
     }
 }
 
@@ -2890,8 +2910,12 @@ int run(fmm_tree t, fmm_lists li, const double* q, int P, double* phi, cudaStrea
         const int small_leaf = near32 ? 0 : n32 ? 64 : 32;
         if (!near32 && minleaf <= small_leaf) {
             if (n32) {
-                k_p2p_f32<<<gp2p, 256, 0, ns>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin, pk32,
-                                                t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
+                if (t->tune_p2p_nt == 4)
+                    k_p2p_f32<4><<<gp2p, 256, 0, ns>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin,
+                                                       pk32, t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
+                else
+                    k_p2p_f32<2><<<gp2p, 256, 0, ns>>>(sp2p, I, LI, li->soff, li->sidx, li->stgt, t->leaf_begin,
+                                                       pk32, t->xs, t->ys, t->cen_hi, t->cen_lo, t->rad32, nhi, nlo);
             } else {
                 int gs = 1;
                 while (gs < std::min<int64_t>(maxleaf, 32)) gs <<= 1;
@@ -3019,6 +3043,7 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
     const int chunks_tc[] = {8, 16, 32};
     int rc = 0;
     const int kind0 = t->m2l_kind, chunk0 = t->tune_m2l_chunk, stages0 = t->tune_m2l_stages;
+    const int nt0 = t->tune_p2p_nt;
     t->tune_m2l_blocks = t->tune_p2p_blocks = 0;
     if ((rc = sched_tuned(t))) return rc;
     const bool try_tc = prm.mode == FMM_MODE_MIXED && !(prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR) &&
@@ -3055,19 +3080,28 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
         t->tune_m2l_stages = best_stages;
     }
     if (!rc) {
-        int best_v = 0;
+        // near field: block count and, for the binary32 leaf-pair kernel, targets per lane
+        const bool try_nt = prm.mode == FMM_MODE_MIXED && !(prm.tol > 0.0 && prm.tol < MIXED_TOL_FLOOR);
+        int best_v = 0, best_nt = nt0;
         float best_ms = 1e30f;
-        for (int v : ladder) {
-            t->tune_p2p_blocks = v;
-            if ((rc = sched_tuned(t))) break;
-            float ms = 0.f;
-            if ((rc = time_one(ms))) break;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_v = v;
+        for (int nt : {2, 4}) {
+            if (!try_nt && nt != 2) break;
+            t->tune_p2p_nt = try_nt ? nt : nt0;
+            for (int v : ladder) {
+                t->tune_p2p_blocks = v;
+                if ((rc = sched_tuned(t))) break;
+                float ms = 0.f;
+                if ((rc = time_one(ms))) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_v = v;
+                    best_nt = t->tune_p2p_nt;
+                }
             }
+            if (rc) break;
         }
         t->tune_p2p_blocks = best_v;
+        t->tune_p2p_nt = best_nt;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -3076,6 +3110,7 @@ int autotune(fmm_tree t, fmm_lists li, const double* q, const fmm_params& prm, d
         t->tune_m2l_blocks = t->tune_p2p_blocks = 0;
         t->tune_m2l_chunk = chunk0;
         t->tune_m2l_stages = stages0;
+        t->tune_p2p_nt = nt0;
         t->m2l_kind = kind0;
         sched_tuned(t);
         return rc;

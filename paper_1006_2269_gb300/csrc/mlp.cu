@@ -171,15 +171,22 @@ __global__ void k_select(int B, const float* __restrict__ prob, const float* __r
 {
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= B) return;
-    const double n = pow(10.0, (double)feat[(int64_t)row * D0 + FMM_FEAT_LOG10N]);
+    const double n = pow(10.0, (double)feat[(int64_t)row * D0 + FMM_FEAT_LOG10N]) * (1.0 + 1e-6);
     int lmax = FMM_SEL_LMIN;
-    while (lmax + 1 <= FMM_SEL_LMAX && ldexp(1.0, 2 * (lmax + 1)) <= n * (1.0 + 1e-6)) lmax++;
+    while (lmax + 1 <= FMM_SEL_LMAX && ldexp(1.0, 2 * (lmax + 1)) <= n) lmax++;
+    // the window the training labels come from: Lc - 2 .. Lc + 1 around Lc = round(log4(N / 32))
+    // (half up), i.e. Lc = floor((b - 4) / 2) with b = floor(log2 N)
+    int b = 0;
+    while (b < 62 && ldexp(1.0, b + 1) <= n) b++;
+    const int lc = b >= 4 ? (b - 4) / 2 : -((5 - b) / 2);
+    const int wlo = max(FMM_SEL_LMIN, lc - 2), whi = min(lmax, lc + 1);
+    const int lo = wlo <= whi ? wlo : FMM_SEL_LMIN, hi = wlo <= whi ? whi : lmax;
     float best = -1.f;
     int bi = 0;
     for (int c = lane; c < D3; c += 32) {
         const int L = FMM_SEL_LMIN + c / FMM_SEL_NP;
         const float pc = prob[(int64_t)row * D3 + c];
-        if (L <= lmax && pc > best) {
+        if (L >= lo && L <= hi && pc > best) {
             best = pc;
             bi = c;
         }

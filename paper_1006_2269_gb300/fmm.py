@@ -78,6 +78,8 @@ def load_library(path: str = LIB_PATH):
             "fmm_probe_throughput": (i32, [i32, i32, vp, ctypes.POINTER(ctypes.c_double), vp]),
             "fmm_probe_blocks": (i32, []),
             "fmm_get_m2l_shape": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "fmm_set_near_shape": (i32, [vp, i32]),
+            "fmm_get_near_shape": (i32, [vp, ctypes.POINTER(i32)]),
             "fmm_selector_features": (i32, [vp, dbl, vp, vp]),
             "fmm_mlp_create": (i32, [i32, ctypes.POINTER(vp)]),
             "fmm_mlp_destroy": (None, [vp]),
@@ -511,6 +513,17 @@ def fmm_get_m2l_shape(tree):
     c, st = ctypes.c_int(), ctypes.c_int()
     _check(load_library().fmm_get_m2l_shape(tree, ctypes.byref(c), ctypes.byref(st)))
     return c.value, st.value
+
+
+def fmm_set_near_shape(tree, targets: int = 0):
+    """binary32 near field: targets per lane (2, 4; 0: default)."""
+    _check(load_library().fmm_set_near_shape(tree, int(targets)))
+
+
+def fmm_get_near_shape(tree):
+    t = ctypes.c_int()
+    _check(load_library().fmm_get_near_shape(tree, ctypes.byref(t)))
+    return t.value
 
 
 def fmm_step(tree, lists, x: torch.Tensor, y: torch.Tensor, theta: float, q: torch.Tensor, p: int, mode: int,

@@ -151,9 +151,16 @@ def label(table, tol: float, margin: float = 1.0) -> int:
     return class_of(best[0], best[1])
 
 
+def centre_level(n: int) -> int:
+    """round(log4(N / 32)), halves rounded up, from the bit length of N: floor((b - 4) / 2) with
+    b = floor(log2 N) (the rule fmm_select_params applies on the device)."""
+    return (int(n).bit_length() - 1 - 4) // 2
+
+
 def candidate_levels(n: int):
-    """Level counts tried for a label: round(log4(N / 32)) - 2 .. + 1."""
-    Lc = int(round(math.log(n / 32.0) / math.log(4.0)))
+    """Level counts tried for a label, and the only ones the selector may choose:
+    centre_level(N) - 2 .. + 1."""
+    Lc = centre_level(n)
     return [L for L in range(Lc - 2, Lc + 2) if LMIN <= L <= min(LMAX, max_levels(n))]
 
 

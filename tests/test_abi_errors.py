@@ -50,3 +50,9 @@ def test_noalloc_short_outputs_refused_before_launch(lib):
     with pytest.raises(fmm.FMMError, match="perm has 999 elements"):
         fmm.fmm_build_tree_noalloc(x, x, L, torch.empty(n - 1, dtype=torch.int32),
                                    torch.empty((nbox, 4), dtype=torch.float64), lb)
+
+
+def test_shape_setters_check_their_handle(lib):
+    assert lib.fmm_set_near_shape(None, 2) == fmm.FMM_ERR_ARG
+    assert lib.fmm_get_near_shape(None, None) == fmm.FMM_ERR_ARG
+    assert lib.fmm_set_m2l_shape(None, 16, 1) == fmm.FMM_ERR_ARG

@@ -164,8 +164,14 @@ def test_masked_argmax(fmmlib, mlp_ref, cuda):
         fmmlib.fmm_mlp_destroy(m)
     prob = mlp_ref.forward(p.astype(np.float64), X.astype(np.float64))
     for i in range(50):
-        n = 10.0 ** float(X[i, 60])
-        ok = np.array([4 ** (4 + c // 25) <= n * (1 + 1e-6) for c in range(225)])
+        n = 10.0 ** float(X[i, 60]) * (1 + 1e-6)
+        lmax = max([L for L in range(4, 13) if 4 ** L <= n] + [4])
+        b = int(np.floor(np.log2(n)))
+        lc = (b - 4) // 2
+        lo, hi = max(4, lc - 2), min(lmax, lc + 1)
+        if lo > hi:
+            lo, hi = 4, lmax
+        ok = np.array([lo <= 4 + c // 25 <= hi for c in range(225)])
         c = int(np.argmax(np.where(ok, prob[i], -1.0)))
         assert tuple(got[i]) == (4 + c // 25, 8 + c % 25)
 

@@ -67,3 +67,14 @@ def test_committed_weights_on_benchmark_cloud():
         prob = M.forward(params, M.features(rects, L, n, tol)[None])[0]
         levels, p = S.params_of(int(np.argmax(prob)))
         assert levels in (7, 8), (tol, levels, p)
+
+
+def test_centre_level_is_half_up_rounding():
+    # the integer rule equals round(log4(N / 32)) with halves rounded up, away from exact ties
+    # checked against the logarithm; at the ties (N = 2^(2k+6)) it gives the upper level
+    for n in [300, 1000, 12345, 10 ** 4, 37000, 2 * 10 ** 5, 10 ** 6, 3 * 10 ** 6, 2 ** 24 + 3]:
+        v = math.log(n / 32.0) / math.log(4.0)
+        assert S.centre_level(n) == math.floor(v + 0.5), n
+    for k in range(2, 10):
+        assert S.centre_level(2 ** (2 * k + 6)) == k + 1
+    assert S.candidate_levels(1 << 20) == [6, 7, 8, 9]
