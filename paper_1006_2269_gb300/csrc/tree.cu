@@ -190,12 +190,22 @@ __global__ void __launch_bounds__(TPB) k_rs_hist(Sched sc, const Inst* __restric
     __syncthreads();
     const int64_t base = tile * TILE;
     const int lane = threadIdx.x & 31;
+    // one shared-memory atomic per item; a warp whose items all share one digit (the high digits
+    // of clustered or narrow-range coordinates) adds its 32 at once instead of 32 colliding ones
+    uint32_t d[ITEMS];
+#pragma unroll
     for (int j = 0; j < ITEMS; j++) {
-        int64_t i = base + (int64_t)j * TPB + threadIdx.x;
-        bool v = i < S.n;
-        uint32_t d = v ? (uint32_t)((keys[i] >> shift) & (BINS - 1)) : 0xffffffffu;
-        unsigned peers = match_digit(d);
-        if (v && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        const int64_t i = base + (int64_t)j * TPB + threadIdx.x;
+        d[j] = i < S.n ? (uint32_t)((keys[i] >> shift) & (BINS - 1)) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const uint32_t d0 = __shfl_sync(0xffffffffu, d[j], 0);
+        if (__all_sync(0xffffffffu, d[j] == d0)) {
+            if (lane == 0 && d0 != 0xffffffffu) atomicAdd(&h[d0], 32u);
+        } else if (d[j] != 0xffffffffu) {
+            atomicAdd(&h[d[j]], 1u);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < BINS; i += blockDim.x) counts[(int64_t)i * S.ntiles + tile] = h[i];
@@ -271,11 +281,13 @@ __global__ void __launch_bounds__(TPB) k_rs_scatter(Sched sc, const Inst* __rest
     if (!FIRST) vin += so;
     counts += 2 * BINS * S.t0 + (int64_t)blockIdx.y * BINS * S.ntiles;
     totals += (2 * (int64_t)z.i + blockIdx.y) * BINS;
-    const int64_t n = S.n, ntiles = S.ntiles;
+    const int64_t n = S.n;
     {
+        // digit d of this tile starts at (digits below d over all tiles) + (digit d in the tiles
+        // before this one)
         uint32_t tot;
         uint32_t e = block_excl_scan(threadIdx.x < BINS ? totals[threadIdx.x] : 0, wt, tot);
-        if (threadIdx.x < BINS) dbase[threadIdx.x] = e;
+        if (threadIdx.x < BINS) dbase[threadIdx.x] = e + counts[(int64_t)threadIdx.x * S.ntiles + tile];
     }
     for (int i = threadIdx.x; i < WARPS * BINS; i += TPB) (&wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -314,7 +326,7 @@ __global__ void __launch_bounds__(TPB) k_rs_scatter(Sched sc, const Inst* __rest
         int64_t i = base + j * 32 + lane;
         if (i < n) {
             uint32_t d = (uint32_t)((k[j] >> shift) & (BINS - 1));
-            int64_t pos = (int64_t)dbase[d] + counts[(int64_t)d * ntiles + tile] + wcnt[w][d] + r[j];
+            int64_t pos = (int64_t)dbase[d] + wcnt[w][d] + r[j];
             kout[pos] = k[j];
             vout[pos] = val[j];
         }
