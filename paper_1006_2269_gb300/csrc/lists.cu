@@ -25,13 +25,7 @@ namespace {
 constexpr int LT = 256;          // threads per block
 constexpr int LI = 8;            // candidates per thread per tile
 constexpr int LTILE = LT * LI;   // candidates per tile
-
-__device__ __forceinline__ unsigned lanemask_lt()
-{
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
+constexpr int QI = LI / 4;       // quads (four consecutive candidates) per thread per tile
 
 // Criterion 2.1 with correctly rounded binary64 operations in a fixed order (no contraction),
 // plus disjointness of the two spheres.
@@ -43,28 +37,6 @@ __device__ __forceinline__ bool theta_weak(double ax, double ay, double ra, doub
     double R = ra > rb ? ra : rb;
     double r = ra > rb ? rb : ra;
     return (__dadd_rn(R, __dmul_rn(theta, r)) <= __dmul_rn(theta, d)) && (__dadd_rn(R, r) < d);
-}
-
-// The same decision taken in binary32 first (float-float centres, binary32 radii).  Every
-// binary32 quantity below is within 2^-20 (relative to theta*d + R + theta*r, resp. d + R + r) of
-// its binary64 counterpart, so a margin larger than 2^-16 of that scale has the sign the binary64
-// test would find; only candidates closer to the boundary take the binary64 test.
-__device__ __forceinline__ bool theta_weak_fast(int64_t a, int64_t b, const float* __restrict__ chi,
-                                                const float* __restrict__ clo,
-                                                const float* __restrict__ rad32, const double* __restrict__ cen,
-                                                const double* __restrict__ rad, float th32, double theta)
-{
-    const float2 ha = *(const float2*)(chi + 2 * a), hb = *(const float2*)(chi + 2 * b);
-    const float2 la = *(const float2*)(clo + 2 * a), lb = *(const float2*)(clo + 2 * b);
-    const float dx = (ha.x - hb.x) + (la.x - lb.x), dy = (ha.y - hb.y) + (la.y - lb.y);
-    const float d = sqrtf(dx * dx + dy * dy);
-    const float ra = rad32[a], rb = rad32[b];
-    const float R = fmaxf(ra, rb), r = fminf(ra, rb);
-    const float m1 = th32 * d - (R + th32 * r), s1 = th32 * d + R + th32 * r;
-    const float m2 = d - (R + r), s2 = d + R + r;
-    const float eps = 1.0f / 65536.0f;
-    if (fabsf(m1) > eps * s1 && fabsf(m2) > eps * s2) return m1 >= 0.f && m2 > 0.f;
-    return theta_weak(cen[2 * a], cen[2 * a + 1], rad[a], cen[2 * b], cen[2 * b + 1], rad[b], theta);
 }
 
 // Criterion 2.1 with the roles of the radii exchanged (Section 4's finest-level optimisation):
@@ -79,23 +51,42 @@ __device__ __forceinline__ bool theta_swapped(double ax, double ay, double ra, d
     return (__dadd_rn(r, __dmul_rn(theta, R)) <= __dmul_rn(theta, d)) && (__dadd_rn(R, r) < d);
 }
 
-// The same two-stage evaluation as theta_weak_fast.
-__device__ __forceinline__ bool theta_swapped_fast(int64_t a, int64_t b, const float* __restrict__ chi,
-                                                   const float* __restrict__ clo,
-                                                   const float* __restrict__ rad32, const double* __restrict__ cen,
-                                                   const double* __restrict__ rad, float th32, double theta)
+// A box's binary32 view: float-float centre and binary32 radius.
+struct BoxG {
+    float2 h, l;
+    float r;
+};
+
+__device__ __forceinline__ BoxG box_geom(int64_t g, const float* __restrict__ chi, const float* __restrict__ clo,
+                                         const float* __restrict__ rad32)
 {
-    const float2 ha = *(const float2*)(chi + 2 * a), hb = *(const float2*)(chi + 2 * b);
-    const float2 la = *(const float2*)(clo + 2 * a), lb = *(const float2*)(clo + 2 * b);
-    const float dx = (ha.x - hb.x) + (la.x - lb.x), dy = (ha.y - hb.y) + (la.y - lb.y);
+    BoxG B;
+    B.h = *(const float2*)(chi + 2 * g);
+    B.l = *(const float2*)(clo + 2 * g);
+    B.r = rad32[g];
+    return B;
+}
+
+// Criterion 2.1 (SW = false) or its exchanged form (SW = true) decided in binary32 first, from
+// float-float centres and binary32 radii already loaded.  Every binary32 quantity below is within
+// 2^-20 (relative to theta*d + R + theta*r, resp. d + R + r) of its binary64 counterpart, so a
+// margin larger than 2^-16 of that scale has the sign the binary64 test would find; only
+// candidates closer to the boundary take the binary64 test (theta_weak / theta_swapped, by index).
+template <bool SW>
+__device__ __forceinline__ bool crit_fast(const BoxG& A, const BoxG& B, int64_t a, int64_t b,
+                                          const double* __restrict__ cen, const double* __restrict__ rad,
+                                          float th32, double theta)
+{
+    const float dx = (A.h.x - B.h.x) + (A.l.x - B.l.x), dy = (A.h.y - B.h.y) + (A.l.y - B.l.y);
     const float d = sqrtf(dx * dx + dy * dy);
-    const float ra = rad32[a], rb = rad32[b];
-    const float R = fmaxf(ra, rb), r = fminf(ra, rb);
-    const float m1 = th32 * d - (r + th32 * R), s1 = th32 * d + r + th32 * R;
+    const float R = fmaxf(A.r, B.r), r = fminf(A.r, B.r);
+    const float m1 = SW ? th32 * d - (r + th32 * R) : th32 * d - (R + th32 * r);
+    const float s1 = SW ? th32 * d + r + th32 * R : th32 * d + R + th32 * r;
     const float m2 = d - (R + r), s2 = d + R + r;
     const float eps = 1.0f / 65536.0f;
     if (fabsf(m1) > eps * s1 && fabsf(m2) > eps * s2) return m1 >= 0.f && m2 > 0.f;
-    return theta_swapped(cen[2 * a], cen[2 * a + 1], rad[a], cen[2 * b], cen[2 * b + 1], rad[b], theta);
+    return SW ? theta_swapped(cen[2 * a], cen[2 * a + 1], rad[a], cen[2 * b], cen[2 * b + 1], rad[b], theta)
+              : theta_weak(cen[2 * a], cen[2 * a + 1], rad[a], cen[2 * b], cen[2 * b + 1], rad[b], theta);
 }
 
 // Optional list variants (Section 4's structural optimisations).
@@ -179,14 +170,26 @@ struct TileParents {
     int64_t off[TP_MAX + 1];  // clamped soff of parents p0 .. p0 + np
 };
 
-__device__ __forceinline__ int64_t find_parent(const int32_t* __restrict__ soff, int64_t pb0, int64_t np,
-                                               int64_t scap, int64_t S0, int64_t t)
+// The parent owning candidate t: the largest p < np with 16 * (soff[pb0 + p] - S0) <= t (soff
+// clamped to the capacity), found by a whole warp.  Each round the 32 lanes probe 32 evenly
+// spaced parents of the remaining range at once and one ballot narrows it about 32-fold, so a
+// level of 4^l parents takes about l / 2.5 rounds of loads instead of 2l dependent ones.  Every
+// lane returns the result.
+__device__ __forceinline__ int64_t find_parent_warp(const int32_t* __restrict__ soff, int64_t pb0, int64_t np,
+                                                    int64_t scap, int64_t S0, int64_t t)
 {
-    int64_t lo = 0, hi = np - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (16 * (min((int64_t)soff[pb0 + mid], scap) - S0) <= t) lo = mid;
-        else hi = mid - 1;
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = np - 1;  // the answer lies in [lo, hi]; parent 0 always qualifies
+    while (hi > lo) {
+        const int64_t span = hi - lo;
+        // probes lo < m_0 <= m_1 <= ... <= m_31 = hi; the qualifying ones form a prefix of lanes
+        const int64_t m = lo + (span * (lane + 1) + 31) / 32;
+        const bool ok = 16 * (min((int64_t)soff[pb0 + m], scap) - S0) <= t;
+        const int c = __popc(__ballot_sync(0xffffffffu, ok));
+        const int64_t nlo = c ? lo + (span * c + 31) / 32 : lo;              // last qualifying probe
+        const int64_t nhi = c < 32 ? lo + (span * (c + 1) + 31) / 32 - 1 : hi;  // below the first failing one
+        lo = nlo;
+        hi = nhi;
     }
     return lo;
 }
@@ -197,7 +200,10 @@ __device__ __forceinline__ void stage_parents(TileParents& tp, const int32_t* __
 {
     const int64_t pb0 = level_base(l - 1), np = level_size(l - 1);
     __shared__ int64_t ends[2];
-    if (threadIdx.x < 2) ends[threadIdx.x] = find_parent(soff, pb0, np, scap, lc.S0, threadIdx.x ? t1 - 1 : t0);
+    if (threadIdx.x < 64) {  // warps 0 and 1: the parents of the tile's first and last candidates
+        const int64_t e = find_parent_warp(soff, pb0, np, scap, lc.S0, threadIdx.x < 32 ? t0 : t1 - 1);
+        if ((threadIdx.x & 31) == 0) ends[threadIdx.x >> 5] = e;
+    }
     __syncthreads();
     const int64_t p0 = ends[0], p1 = ends[1];
     const int cnt = (int)(p1 - p0 + 1);
@@ -232,9 +238,9 @@ __device__ __forceinline__ void decode(const TileParents& tp, const int32_t* __r
 // Candidate flags: 0 strong, 1 weak.  With parent-level interactions (PAR, Section 4's optional
 // step) four weak siblings c = 4k .. 4k+3 of one target box whose parent k also satisfies the
 // criterion with the target become one entry: 2 on the first (the entry names the parent), 3 on
-// the other three (no entry).  The four children of a source box are candidates 4q .. 4q+3,
-// which sit in lanes 4q' .. 4q'+3 of one warp (tiles, rows and boxes all start at multiples of
-// 4), so one ballot tells each lane about its quad.  With the role exchange (SWP) a strong
+// the other three (no entry).  The four children of a source box are candidates 4q .. 4q+3
+// (tiles and boxes start at multiples of 4), and one thread decides such a quad, so the parent
+// test needs no communication between threads.  With the role exchange (SWP) a strong
 // candidate of an instance's finest level that passes the exchanged criterion is flagged 4 (the
 // target is the smaller leaf: P2L) or 5 (the larger: M2P) and goes to the exchange lists.
 // schedule: candidate tiles of level l
@@ -263,35 +269,47 @@ __global__ void __launch_bounds__(LT) k_lists_flags(Sched sc, LIST_ARGS, ListOpt
     const int64_t ntiles = (nc + LTILE - 1) / LTILE;
     const int64_t base = level_base(l), pbase = level_base(l - 1);
     const int lane = threadIdx.x & 31;
+    const float th32 = (float)theta;
     for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
         uint32_t cnt = 0, drop = 0, swp = 0;
-#pragma unroll 4
-        for (int j = 0; j < LI; j++) {
-            const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
-            int64_t b = 0, c = 0;
-            bool w = false;
-            if (t < nc) {
-                bool first;
-                decode(tp, v.sidx, lc, t, b, c, first);
-                w = theta_weak_fast(base + b, base + c, chi, clo, rad32, cen, rad, (float)theta, theta);
+        // each thread takes whole quads: the four children c .. c + 3 of one source box against
+        // one target box b (candidates 4q .. 4q + 3), so the decode, the target's geometry and
+        // the parent-level test are done once per quad
+#pragma unroll
+        for (int j = 0; j < QI; j++) {
+            const int64_t t = 4 * (tile * (LTILE / 4) + (int64_t)j * LT + threadIdx.x);
+            if (t >= nc) continue;
+            int64_t b, c;
+            bool first;
+            decode(tp, v.sidx, lc, t, b, c, first);
+            const int64_t gb = base + b, gc = base + c;
+            const BoxG T = box_geom(gb, chi, clo, rad32);
+            BoxG C[4];
+            uint32_t f[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                C[i] = box_geom(gc + i, chi, clo, rad32);
+                f[i] = crit_fast<false>(T, C[i], gb, gc + i, cen, rad, th32, theta) ? 1u : 0u;
             }
-            uint8_t f = w ? 1 : 0;
-            if (PAR) {
-                const unsigned q = __ballot_sync(0xffffffffu, w) >> (lane & ~3) & 0xFu;
-                bool m = false;
-                if (q == 0xFu && (lane & 3) == 0)
-                    m = theta_weak_fast(base + b, pbase + (c >> 2), chi, clo, rad32, cen, rad, (float)theta, theta);
-                if (__ballot_sync(0xffffffffu, m) >> (lane & ~3) & 1u) f = (lane & 3) ? 3 : 2;
-                drop += f == 3;
+            if (PAR && (f[0] & f[1] & f[2] & f[3]) &&
+                crit_fast<false>(T, box_geom(pbase + (c >> 2), chi, clo, rad32), gb, pbase + (c >> 2), cen, rad,
+                                 th32, theta)) {
+                f[0] = 2;
+                f[1] = f[2] = f[3] = 3;
+                drop += 3;
             }
-            if (SWP && fin && t < nc && f == 0 &&
-                theta_swapped_fast(base + b, base + c, chi, clo, rad32, cen, rad, (float)theta, theta)) {
-                f = rad[base + b] > rad[base + c] ? 5 : 4;
-                swp++;
+            if (SWP && fin) {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if (f[i] == 0 && crit_fast<true>(T, C[i], gb, gc + i, cen, rad, th32, theta)) {
+                        f[i] = rad[gb] > rad[gc + i] ? 5 : 4;
+                        swp++;
+                    }
             }
-            if (t < nc) v.flags[t] = f;
-            cnt += f == 1 || f == 2;
+            *(uint32_t*)(v.flags + t) = f[0] | f[1] << 8 | f[2] << 16 | f[3] << 24;
+#pragma unroll
+            for (int i = 0; i < 4; i++) cnt += f[i] == 1 || f[i] == 2;
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
@@ -380,6 +398,13 @@ __global__ void __launch_bounds__(1024) k_lists_scan(LIST_ARGS, ListOpt opt, int
     }
 }
 
+// Whether flag f counts for counter kind 0 (weak entry: 1, 2), 1 (sibling covered by its
+// parent's entry: 3) or 2 (exchanged pair: 4, 5).
+__device__ __forceinline__ uint32_t flag_in(uint32_t f, int kind)
+{
+    return kind == 0 ? (f == 1 || f == 2) : kind == 1 ? f == 3 : f >= 4;
+}
+
 // Scatter the candidates into the weak, strong (and exchange) lists and write the box offsets.
 // The tile prefix of weak flags is tilecnt[tile] (of dropped siblings tiledrop[tile], of
 // exchanged pairs tileswap[tile]); the strong prefix is the rest.
@@ -393,7 +418,7 @@ __global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, ListOpt 
     const LView v = LIST_VIEW(z.i);
     const bool fin = SWP && l == S.L;
     constexpr int NC = 1 + PAR + SWP;  // prefix counters: weak, dropped, exchanged
-    __shared__ uint32_t csum[NC][LI][LT / 32];
+    __shared__ uint32_t csum[NC][QI][LT / 32];
     __shared__ TileParents tp;
     const LevelCands lc = level_cands(v.soff, l, v.scap);
     const int64_t nc = lc.count();
@@ -405,43 +430,49 @@ __global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, ListOpt 
     int32_t* xidx = SWP ? opt.xidx + LIs[z.i].s0 : nullptr;
     int32_t* xtgt = SWP ? opt.xtgt + LIs[z.i].s0 : nullptr;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = lanemask_lt();
     for (int64_t tile = z.rank; tile < ntiles; tile += z.nb) {
         stage_parents(tp, v.soff, l, v.scap, lc, tile * LTILE, min(nc, (tile + 1) * LTILE));
-        uint8_t f[LI];
-        uint32_t pre[NC][LI];
+        // per quad (four consecutive candidates, as the flag pass made them): its flags, its count
+        // of each counter and the exclusive prefix of those counts over the warp's lanes
+        uint32_t fw[QI];
+        uint32_t pre[NC][QI];
 #pragma unroll
-        for (int j = 0; j < LI; j++) {
-            const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
-            f[j] = t < nc ? v.flags[t] : 0;
+        for (int j = 0; j < QI; j++) {
+            const int64_t t = 4 * (tile * (LTILE / 4) + (int64_t)j * LT + threadIdx.x);
+            fw[j] = t < nc ? *(const uint32_t*)(v.flags + t) : 0u;
 #pragma unroll
             for (int k = 0; k < NC; k++) {
                 // counter k: 0 weak (1, 2), then dropped (3) if PAR, then exchanged (4, 5) if SWP
                 const int kind = k == 0 ? 0 : (PAR && k == 1) ? 1 : 2;
-                const bool in = kind == 0 ? (f[j] == 1 || f[j] == 2) : kind == 1 ? f[j] == 3 : f[j] >= 4;
-                const unsigned bal = __ballot_sync(0xffffffffu, in);
-                pre[k][j] = __popc(bal & lt);
-                if (lane == 0) csum[k][j][w] = __popc(bal);
-            }
-        }
-        __syncthreads();
-        // exclusive prefix in (row j, warp) order = candidate order inside the tile: warp 0 scans
-        // the LI x (LT / 32) = 64 counts of each counter (two per lane) in place
-        static_assert(LI * (LT / 32) == 64, "the prefix scan takes two counts per lane");
-        if (w == 0) {
+                uint32_t cq = 0;
 #pragma unroll
-            for (int k = 0; k < NC; k++) {
-                uint32_t* a = &csum[k][0][0];
-                const uint32_t c0v = a[2 * lane], c1v = a[2 * lane + 1];
-                uint32_t x = c0v + c1v;
+                for (int i = 0; i < 4; i++) cq += flag_in(fw[j] >> (8 * i) & 0xffu, kind);
+                uint32_t x = cq;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                     if (lane >= o) x += y;
                 }
-                const uint32_t ex = x - (c0v + c1v);
-                a[2 * lane] = ex;
-                a[2 * lane + 1] = ex + c0v;
+                pre[k][j] = x - cq;
+                if (lane == 31) csum[k][j][w] = x;
+            }
+        }
+        __syncthreads();
+        // exclusive prefix of the warp totals in (row j, warp) order = candidate order inside the
+        // tile: warp 0 scans the QI x (LT / 32) = 16 totals of each counter in place
+        static_assert(QI * (LT / 32) <= 32, "one warp total per lane");
+        if (w == 0) {
+#pragma unroll
+            for (int k = 0; k < NC; k++) {
+                uint32_t* a = &csum[k][0][0];
+                const uint32_t cv = lane < QI * (LT / 32) ? a[lane] : 0u;
+                uint32_t x = cv;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane < QI * (LT / 32)) a[lane] = x - cv;
             }
         }
         __syncthreads();
@@ -450,44 +481,51 @@ __global__ void __launch_bounds__(LT) k_lists_fill(Sched sc, LIST_ARGS, ListOpt 
         if (PAR) run[1] = opt.tiledrop[c0 + tile];
         if (SWP) run[NC - 1] = fin ? opt.tileswap[c0 + tile] : 0;
 #pragma unroll
-        for (int j = 0; j < LI; j++) {
-            uint32_t before[NC];
+        for (int j = 0; j < QI; j++) {
+            const int64_t t = 4 * (tile * (LTILE / 4) + (int64_t)j * LT + threadIdx.x);
+            if (t >= nc) continue;
+            int64_t b, c;
+            bool first;
+            decode(tp, v.sidx, lc, t, b, c, first);
+            // entries of each counter before candidate t + i
+            int64_t before[NC];
 #pragma unroll
-            for (int k = 0; k < NC; k++) before[k] = run[k] + csum[k][j][w];
-            const int64_t t = tile * LTILE + (int64_t)j * LT + threadIdx.x;
-            if (t < nc) {
-                int64_t b, c;
-                bool first;
-                decode(tp, v.sidx, lc, t, b, c, first);
-                const int64_t wpre = (int64_t)before[0] + pre[0][j];  // weak entries before t
-                const int64_t dpre = PAR ? (int64_t)before[1] + pre[1][j] : 0;
-                const int64_t xpre = SWP ? (int64_t)before[NC - 1] + pre[NC - 1][j] : 0;
-                const int64_t spre = t - wpre - dpre - xpre;  // strong entries before t
-                if (first) {
+            for (int k = 0; k < NC; k++) before[k] = (int64_t)run[k] + csum[k][j][w] + pre[k][j];
+            const int32_t gb = (int32_t)(base + b);
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint32_t f = fw[j] >> (8 * i) & 0xffu;
+                const int64_t wpre = before[0];
+                const int64_t dpre = PAR ? before[1] : 0;
+                const int64_t xpre = SWP ? before[NC - 1] : 0;
+                const int64_t spre = t + i - wpre - dpre - xpre;  // strong entries before t + i
+                if (i == 0 && first) {
                     v.woff[base + b] = (int32_t)min(W0 + wpre, (int64_t)INT32_MAX);
                     v.soff[base + b] = (int32_t)min(S0 + spre, (int64_t)INT32_MAX);
                     if (fin) xoff[base + b] = (int32_t)min(xpre, (int64_t)INT32_MAX);
                 }
-                if (PAR && f[j] == 3) {
+                if (PAR && f == 3) {
                     // a sibling covered by its parent's entry
-                } else if (SWP && f[j] >= 4) {
+                } else if (SWP && f >= 4) {
                     if (xpre < v.scap) {
-                        xidx[xpre] = f[j] == 5 ? (int32_t)c | SWAP_M2P : (int32_t)c;
-                        xtgt[xpre] = (int32_t)(base + b);
+                        xidx[xpre] = f == 5 ? (int32_t)(c + i) | SWAP_M2P : (int32_t)(c + i);
+                        xtgt[xpre] = gb;
                     }
-                } else if (f[j]) {
+                } else if (f) {
                     const int64_t pos = W0 + wpre;
                     if (pos < v.wcap) {
-                        v.widx[pos] = f[j] == 2 ? (int32_t)(c >> 2) | PARENT_FLAG : (int32_t)c;
-                        if ((pos & 7) == 0) v.wrow[pos >> 3] = (int32_t)(base + b);
+                        v.widx[pos] = f == 2 ? (int32_t)(c >> 2) | PARENT_FLAG : (int32_t)(c + i);
+                        if ((pos & 7) == 0) v.wrow[pos >> 3] = gb;
                     }
                 } else {
                     const int64_t pos = S0 + spre;
                     if (pos < v.scap) {
-                        v.sidx[pos] = (int32_t)c;
-                        v.stgt[pos] = (int32_t)(base + b);
+                        v.sidx[pos] = (int32_t)(c + i);
+                        v.stgt[pos] = gb;
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < NC; k++) before[k] += flag_in(f, k == 0 ? 0 : (PAR && k == 1) ? 1 : 2);
             }
         }
         __syncthreads();
