@@ -1378,6 +1378,8 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
         float tx[NT], ty[NT], tq[NT], hi[NT], lo[NT];
 #pragma unroll
         for (int k = 0; k < NT; k++) tx[k] = ty[k] = tq[k] = hi[k] = lo[k] = 0.f;
+        float2 tch = make_float2(0.f, 0.f), tcl = tch;  // the target leaf's float-float centre
+        float trad = 0.f;                                // and binary32 radius
         auto flush = [&]() {
 #pragma unroll
             for (int k = 0; k < NT; k++)
@@ -1393,6 +1395,9 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
                 cur = tl;
                 t0 = lb[tl];
                 nt = lb[tl + 1] - t0;
+                tch = *(const float2*)(chi + 2 * (base + tl));
+                tcl = *(const float2*)(clo + 2 * (base + tl));
+                trad = rad32[base + tl];
 #pragma unroll
                 for (int k = 0; k < NT; k++) {
                     hi[k] = lo[k] = 0.f;
@@ -1407,10 +1412,11 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
             if (li >= nt) continue;  // target k > 0 valid implies target 0 valid
             const int32_t sl = sidx[e];
             const int32_t s0 = lb[sl], ns = lb[sl + 1] - s0;
-            const int32_t sg = base + sl, tg = base + tl;
-            const float ox = (chi[2 * sg] - chi[2 * tg]) + (clo[2 * sg] - clo[2 * tg]);
-            const float oy = (chi[2 * sg + 1] - chi[2 * tg + 1]) + (clo[2 * sg + 1] - clo[2 * tg + 1]);
-            const float M = rad32[sg] + rad32[tg] + fabsf(ox) + fabsf(oy);
+            const int32_t sg = base + sl;
+            const float2 sch = *(const float2*)(chi + 2 * sg), scl = *(const float2*)(clo + 2 * sg);
+            const float ox = (sch.x - tch.x) + (scl.x - tcl.x);
+            const float oy = (sch.y - tch.y) + (scl.y - tcl.y);
+            const float M = rad32[sg] + trad + fabsf(ox) + fabsf(oy);
             const float tau2 = fmaxf((M * (1.f / 256.f)) * (M * (1.f / 256.f)), 1e-30f);
             // logs are taken of r^2 / 2^e, 2^e the power of two at or below M^2 (near 1 for most
             // pairs), and e times the sources' strength is added once per leaf pair: the running
@@ -1431,33 +1437,33 @@ __global__ void __launch_bounds__(256) k_p2p_f32(Sched sc, const Inst* __restric
             float qs = 0.f;
             const Pk<float>* src = pk + s0;
             if (sl != tl) {
-#pragma unroll 8 / NT
+#pragma unroll 16 / NT
                 for (int32_t j = 0; j < ns; j++) {
-                    const Pk<float> sp = src[j];
-                    qs += sp.q;
+                    const float4 sp = *(const float4*)(src + j);  // x, y, q in one load
+                    qs += sp.z;
 #pragma unroll
                     for (int k = 0; k < NT; k++) {
                         const float dx = xa[k] - sp.x, dy = ya[k] - sp.y;
                         const float r = dx * dx + dy * dy;
                         ma[k] = fminf(ma[k], r);
-                        pa[k] += sp.q * lg2_fast(r * s2);
+                        pa[k] += sp.z * lg2_fast(r * s2);
                     }
                 }
 #pragma unroll
                 for (int k = 0; k < NT; k++) pa[k] += c2 * qs;
             } else {
                 // the leaf with itself: a point meets itself once; that term is left out
-#pragma unroll 8 / NT
+#pragma unroll 16 / NT
                 for (int32_t j = 0; j < ns; j++) {
-                    const Pk<float> sp = src[j];
-                    qs += sp.q;
+                    const float4 sp = *(const float4*)(src + j);
+                    qs += sp.z;
 #pragma unroll
                     for (int k = 0; k < NT; k++) {
                         const bool self = j == li + k * gsl;
                         const float dx = xa[k] - sp.x, dy = ya[k] - sp.y;
                         const float r = self ? 3.0e38f : dx * dx + dy * dy;
                         ma[k] = fminf(ma[k], r);
-                        pa[k] += self ? 0.f : sp.q * lg2_fast(r * s2);
+                        pa[k] += self ? 0.f : sp.z * lg2_fast(r * s2);
                     }
                 }
 #pragma unroll

@@ -825,7 +825,42 @@ k_split_local(Sched sc, const Inst* __restrict__ I, int32_t* __restrict__ X, int
     }
 }
 
-// Coordinates in canonical order, and their binary32 offsets from the leaf centre.
+// Canonical order inside small leaves.  After the last split the x-ordered list X holds every
+// leaf as one contiguous run (XS: its leaf), at the leaf's offsets; the canonical order sorts each
+// run by input index.  With at most LEAF_RANK_MAX points per leaf, each point's place in its run
+// is the number of smaller indices in it (indices are distinct), found by one pass over the run.
+// schedule: points
+constexpr int LEAF_RANK_MAX = 64;
+__global__ void k_leaf_rank(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ X,
+                            const int32_t* __restrict__ XS, const int32_t* __restrict__ leaf_begin,
+                            int32_t* __restrict__ perm, int32_t* __restrict__ cleaf, int32_t* status)
+{
+    const Slot z = slot_of(sc);
+    const Inst S = I[z.i];
+    X += S.p0;
+    XS += S.p0;
+    perm += S.p0;
+    cleaf += S.p0;
+    const int32_t* lb = leaf_begin + S.lb0;
+    const int32_t n = (int32_t)S.n, nleaf = (int32_t)level_size(S.L);
+    for (int32_t i = z.rank * blockDim.x + threadIdx.x; i < n; i += z.nb * blockDim.x) {
+        const int32_t lf = XS[i];
+        const int32_t a = (lf >= 0 && lf < nleaf) ? lb[lf] : 0, e = (lf >= 0 && lf < nleaf) ? lb[lf + 1] : 0;
+        if (i < a || i >= e || e - a > LEAF_RANK_MAX) {  // not a run of this leaf: the tree is broken
+            atomicOr(status, ST_ARG);
+            continue;
+        }
+        const int32_t v = X[i];
+        int32_t r = 0;
+        for (int32_t k = a; k < e; k++) r += X[k] < v;
+        perm[a + r] = v;
+        cleaf[a + r] = lf;
+    }
+}
+
+// Coordinates in canonical order, and their binary32 offsets from the leaf centre.  The leaf of
+// each position comes from leaf_of (by input index) or, when leaf_of is null, from cleaf, which
+// k_leaf_rank has filled already.
 // schedule: points
 __global__ void k_gather_points(Sched sc, const Inst* __restrict__ I, const int32_t* __restrict__ perm,
                                 const uint32_t* __restrict__ leaf_of, const double* __restrict__ x,
@@ -848,8 +883,14 @@ __global__ void k_gather_points(Sched sc, const Inst* __restrict__ I, const int3
     cen += 2 * S.b0;
     for (int64_t i = (int64_t)z.rank * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)z.nb * blockDim.x) {
         int32_t id = perm[i];
-        cleaf[i] = (int32_t)leaf_of[id];
-        int64_t g = level_base(S.L) + leaf_of[id];
+        int32_t lf;
+        if (leaf_of) {
+            lf = (int32_t)leaf_of[id];
+            cleaf[i] = lf;
+        } else {
+            lf = cleaf[i];
+        }
+        int64_t g = level_base(S.L) + lf;
         double a = x[id], b = y[id];
         xs[i] = a;
         ys[i] = b;
@@ -1225,15 +1266,24 @@ int tree_build(fmm_tree t, const double* x, const double* y, cudaStream_t s, cud
 
     {
         StageScope scope(FMM_STAGE_TREE_FINISH, s);
-        // canonical order: stable sort of the input indices by leaf (inside a leaf: input order)
-        uint32_t* leaf_of = (uint32_t*)t->leaf_of;
-        k_leaf_of<<<gp, 256, 0, s>>>(sp, t->dinst, X, Xfinal_seg, leaf_of); note_launch();
-        uint32_t* k32 = (uint32_t*)t->keys;  // reuse the key buffers: [0, n) and [n, 2n)
-        int32_t* v32 = t->vals + 2 * n;      // value buffers [2n, 4n)
-        const int bits = std::max(8, 2 * L);  // with L = 0 all keys are 0: the order stays the input order
-        FMM_CUDA(cudaMemcpyAsync(k32, leaf_of, 4 * n, cudaMemcpyDeviceToDevice, s));
-        int c2 = radix_sort<uint32_t>(t, k32, v32, 0, 1, bits, s);
-        FMM_CUDA(cudaMemcpyAsync(t->perm, v32 + (c2 ? n : 0), 4 * n, cudaMemcpyDeviceToDevice, s));
+        // canonical order: the input indices of every leaf in ascending order.  Small leaves are
+        // ranked in place (k_leaf_rank); otherwise a stable sort of the input indices by leaf.
+        int32_t maxleaf = 0;
+        for (int i = 0; i < ni; i++) maxleaf = std::max(maxleaf, t->hinst[i].maxleaf);
+        uint32_t* leaf_of = nullptr;
+        if (maxleaf <= LEAF_RANK_MAX) {
+            k_leaf_rank<<<gp, 256, 0, s>>>(sp, t->dinst, X, Xfinal_seg, t->leaf_begin, t->perm, t->cleaf,
+                                           t->status); note_launch();
+        } else {
+            leaf_of = (uint32_t*)t->leaf_of;
+            k_leaf_of<<<gp, 256, 0, s>>>(sp, t->dinst, X, Xfinal_seg, leaf_of); note_launch();
+            uint32_t* k32 = (uint32_t*)t->keys;  // reuse the key buffers: [0, n) and [n, 2n)
+            int32_t* v32 = t->vals + 2 * n;      // value buffers [2n, 4n)
+            const int bits = std::max(8, 2 * L);  // with L = 0 all keys are 0: the order stays the input order
+            FMM_CUDA(cudaMemcpyAsync(k32, leaf_of, 4 * n, cudaMemcpyDeviceToDevice, s));
+            int c2 = radix_sort<uint32_t>(t, k32, v32, 0, 1, bits, s);
+            FMM_CUDA(cudaMemcpyAsync(t->perm, v32 + (c2 ? n : 0), 4 * n, cudaMemcpyDeviceToDevice, s));
+        }
 
         const int64_t nb = t->nbox;
         if (!level_ready)
