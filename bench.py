@@ -256,7 +256,7 @@ def shard_instances(sizes, world: int, rank: int):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the SIMT M2L kernel per launch on the 1M
 # clustered workload, from one ncu capture each; valid while that kernel is unchanged
-M2L_TRAFFIC = {(21, 1 << 20, "parents"): 135104768}
+M2L_TRAFFIC = {}  # none yet for the kernel with split row sums
 
 
 def pair_counts(f):
@@ -734,6 +734,42 @@ def main():
     def use(mode):
         fmm.fmm_set_launch(f.tree, *tuned[mode])
 
+    # The autotuner times evaluations; inside a whole step the M2L shares the GPU with the near
+    # field and the tree's tail, so the binary32 M2L kernel (SIMT or tensor cores, with the
+    # tensor-core kernel's tile shapes) is also chosen on whole steps, as the lists are
+    m2l_trial = {}
+    if not args.blocks and w.p + 1 <= 32:
+        def time_steps(k=12):
+            step(fmm.FMM_MODE_MIXED)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                step(fmm.FMM_MODE_MIXED)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / k
+
+        use(fmm.FMM_MODE_MIXED)
+        auto = (fmm.fmm_get_m2l_kernel(f.tree), fmm.fmm_get_m2l_shape(f.tree), tuned[fmm.FMM_MODE_MIXED])
+        best = (time_steps(), auto)
+        m2l_trial["autotuned"] = best[0]
+        near_blocks = tuned[fmm.FMM_MODE_MIXED][1]
+        for blocks in (SM_COUNT * 2, SM_COUNT * 3, SM_COUNT * 4):
+            for chunk in (8, 16, 32):
+                for stages in (1, 2):
+                    fmm.fmm_set_m2l_kernel(f.tree, fmm.FMM_M2L_TENSOR)
+                    fmm.fmm_set_m2l_shape(f.tree, chunk, stages)
+                    fmm.fmm_set_launch(f.tree, blocks, near_blocks)
+                    ms = time_steps()
+                    m2l_trial[f"tensor {blocks}x{chunk}x{stages}"] = ms
+                    if ms < best[0]:
+                        best = (ms, (fmm.FMM_M2L_TENSOR, (chunk, stages), (blocks, near_blocks)))
+        kind, shape, tuned[fmm.FMM_MODE_MIXED] = best[1]
+        fmm.fmm_set_m2l_kernel(f.tree, kind)
+        fmm.fmm_set_m2l_shape(f.tree, *shape)
+        use(fmm.FMM_MODE_MIXED)
+
     use(fmm.FMM_MODE_MIXED)
     tg = torch.as_tensor(W.sample_targets(n, w.n_check, W.SEED_BASE + 101), device=dev)
     ref = torch.empty(tg.numel(), dtype=torch.float64, device=dev)
@@ -889,7 +925,8 @@ def main():
                    else "SIMT binary32",
                    "near_targets_per_lane": fmm.fmm_get_near_shape(f.tree) or 2,
                    "lists": lists_kind + ("" if lists_kind == "plain" else " (Section 4's optional optimisations)"),
-                   "lists_trial_ms_per_step": lists_ms or None},
+                   "lists_trial_ms_per_step": lists_ms or None,
+                   "m2l_trial_ms_per_step": m2l_trial or None},
         "rel_err": err_mixed, "rel_err_fp64": err_fp64, "n_check": w.n_check,
         "fp64_path": {"value": job_throughput(world, n, ms_fp64, args.fp64_steps),
                       "ms_per_step": ms_fp64 / args.fp64_steps, "stages_ms": stage_ms64},

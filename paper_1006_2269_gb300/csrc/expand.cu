@@ -123,13 +123,25 @@ constexpr std::array<float, sizeof...(I)> mcoef_table(std::integer_sequence<int,
     return {MCoef<I / PMAXC, I % PMAXC>::v...};
 }
 
-// Row O of y = M' x with immediate coefficients (products in the order k = 0, 1, ...).
+// One term M'[O][K] x_K of row O into the partial sums of parity K & 1; zero coefficients and the
+// zero imaginary part of x_0 (= a~_0, real) contribute nothing and are left out.
+template <int O, int K>
+__device__ __forceinline__ void m2l_term(const cx<float>* x, float (&yr)[2], float (&yi)[2])
+{
+    if constexpr (MCoef<O, K>::v != 0.0f) {
+        yr[K & 1] = fmaf(MCoef<O, K>::v, x[K].re, yr[K & 1]);
+        if constexpr (K > 0) yi[K & 1] = fmaf(MCoef<O, K>::v, x[K].im, yi[K & 1]);
+    }
+}
+
+// Row O of y = M' x with immediate coefficients: even and odd k in two partial sums (two
+// independent chains of dependent FMAs instead of one), added at the end.
 template <int O, int... K>
 __device__ __forceinline__ cx<float> m2l_row(const cx<float>* x, std::integer_sequence<int, K...>)
 {
-    float yr = 0.f, yi = 0.f;
-    ((yr += MCoef<O, K>::v * x[K].re, yi += MCoef<O, K>::v * x[K].im), ...);
-    return {yr, yi};
+    float yr[2] = {0.f, 0.f}, yi[2] = {0.f, 0.f};
+    (m2l_term<O, K>(x, yr, yi), ...);
+    return {yr[0] + yr[1], yi[0] + yi[1]};
 }
 
 
@@ -611,18 +623,21 @@ __global__ void __launch_bounds__(128, (PI >= 18 && PI <= 21) ? 4 : 1) k_m2l_pai
             const int64_t sg = weak_source(g, widx[e]);
             const cx<T> z0 = geo.diff(sg, g);
             const T r2 = z0.re * z0.re + z0.im * z0.im;
-            const T ir2 = (T)1 / r2;
+            const T ir2 = __frcp_rn(r2);  // correctly rounded, as 1 / r2
             const cx<T> inv = {z0.re * ir2, -z0.im * ir2};
             const cx<T> u2 = cscale(inv, (T)-2 * geo.radius(sg)), v2 = cscale(inv, (T)2 * geo.radius(g));
-            const cx<T>* src = Me + sg * PS;
-            const T a0 = src[0].re;
+            // the source's coefficients two at a time (rows are PS = P rounded up to even long)
+            const float4* src4 = (const float4*)(Me + sg * PS);
+            float4 q4 = src4[0];
+            const T a0 = q4.x;
             cx<T> x[PI];
             x[0] = {a0, 0};
             cx<T> up = u2;
 #pragma unroll
             for (int k = 1; k < PI; k++) {
+                if ((k & 1) == 0) q4 = (k < P) ? src4[k >> 1] : make_float4(0.f, 0.f, 0.f, 0.f);
                 cx<T> v = {0, 0};
-                if (k < P) v = cmul(src[k], up);
+                if (k < P) v = cmul((k & 1) ? cx<T>{q4.z, q4.w} : cx<T>{q4.x, q4.y}, up);
                 x[k] = v;
                 up = cmul(up, u2);
             }
