@@ -256,7 +256,7 @@ def shard_instances(sizes, world: int, rank: int):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the SIMT M2L kernel per launch on the 1M
 # clustered workload, from one ncu capture each; valid while that kernel is unchanged
-M2L_TRAFFIC = {}  # none yet for the kernel with split row sums
+M2L_TRAFFIC = {(21, 1 << 20, "parents"): 85135872 + 3795712}
 
 
 def pair_counts(f):
