@@ -40,7 +40,7 @@ constexpr int PMAXC = 41;  // p <= 40
 __constant__ double c_md[PMAXC][PMAXC];     // M'[l][k] in binary64
 // log2(j / 128) for j = 128 .. 256 as float-float (high, low): the table of the float-float
 // logarithm of the split mode's near field
-__constant__ float c_lg2t[2][129];
+__constant__ float c_lg2t[3][129];  // log2(1 + j/128) as float-float, and 1 / (1 + j/128)
 // binomials C(n, k), n, k < PMAXC, in global memory: blocks copy them to shared memory (a warp
 // reading many different __constant__ addresses at once would be serialised)
 __device__ float g_binom_f[PMAXC * PMAXC];
@@ -1511,6 +1511,30 @@ __device__ __forceinline__ int32_t p2p_src_blocks(int32_t nt, int32_t ns)
     return (int32_t)nsc;
 }
 
+// Work items [v0, v1) of the near field's item numbering, shared out to warps in contiguous
+// ranges: warp w of nwarps takes [va, vb) and the pair e owning va (the last e with pos[e] <= va;
+// pairs without items share pos).  Inside the range the owning pair only moves forward, so one
+// search per warp replaces one per item.
+struct ItemRange {
+    int64_t va, vb, e;
+};
+__device__ __forceinline__ ItemRange item_range(const int32_t* __restrict__ pos, int64_t e_begin, int64_t e_end,
+                                                int64_t v0, int64_t v1, int64_t warp, int64_t nwarps)
+{
+    ItemRange r;
+    const int64_t per = (v1 - v0 + nwarps - 1) / nwarps;
+    r.va = min(v0 + warp * per, v1);
+    r.vb = min(r.va + per, v1);
+    int64_t lo = e_begin, hi = e_end - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (pos[mid] <= r.va) lo = mid;
+        else hi = mid - 1;
+    }
+    r.e = lo;
+    return r;
+}
+
 // items[T.s0 + e] for every position e of an instance's strong array (0 outside the finest
 // level's pairs and for instances left to the leaf-pair kernels); schedule: near field
 __global__ void __launch_bounds__(256) k_p2p_items(Sched sc, const Inst* __restrict__ I, const LInst* __restrict__ LIs,
@@ -1600,15 +1624,10 @@ __global__ void __launch_bounds__(256) k_p2p_large(Sched sc, const Inst* __restr
     const int64_t v0 = pos[e_begin], v1 = pos[e_end];
     const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
-    for (int64_t v = v0 + warp; v < v1; v += nwarps) {
-        // the pair owning item v: the last e with pos[e] <= v (pairs without items share pos)
-        int64_t lo = e_begin, hi = e_end - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (pos[mid] <= v) lo = mid;
-            else hi = mid - 1;
-        }
-        const int64_t e = lo;
+    const ItemRange rg = item_range(pos, e_begin, e_end, v0, v1, warp, nwarps);
+    int64_t e = rg.e;
+    for (int64_t v = rg.va; v < rg.vb; v++) {
+        while (e + 1 < e_end && pos[e + 1] <= v) e++;  // the pair owning item v
         const int64_t tl = stgt[e] - base, sl = sidx[e];
         const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0, s0 = lb[sl], ns = lb[sl + 1] - s0;
         const int32_t nsc = p2p_src_blocks(nt, ns), ntc = (nt + 31) / 32;
@@ -1709,14 +1728,16 @@ __device__ __forceinline__ ff ff_split(double v)
 // a = 2^e m (1 <= m < 2) and F = j / 128 the nearest table point, log2 a = e + log2 F +
 // log2(1 + r), r = (m - F + a.l / 2^e) / F, |r| <= 2^-8; log(1 + r) by its series to r^5 (the
 // first terms in float-float, the rest in binary32), times 1/ln 2 in float-float.
-__device__ __forceinline__ ff ff_log2(ff a)
+// The table is read at 129 different places across a warp: in shared memory (tab, a copy of
+// c_lg2t) those reads take one pass; the constant bank serialises them.
+__device__ __forceinline__ ff ff_log2(ff a, const float (*tab)[129])
 {
     const uint32_t bits = __float_as_uint(a.h);
     const int e = (int)(bits >> 23) - 127;
     const float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);  // [1, 2)
     const int j = __float2int_rn((m - 1.f) * 128.f);                     // 0 .. 128
     const float F = 1.f + (float)j * (1.f / 128.f);
-    const float invF = 1.f / F;
+    const float invF = tab[2][j];  // 1.f / F, correctly rounded
     const ff u = ff_two_sum(m - F, ldexpf(a.l, -e));  // m - F is exact
     const float rh = u.h * invF;
     const float rl = (fmaf(-rh, F, u.h) + u.l) * invF;
@@ -1727,7 +1748,7 @@ __device__ __forceinline__ ff ff_log2(ff a)
     L = ff_add(L, ff{t3, 0.f});
     const ff inv_ln2 = {1.44269502163f, 1.92596299e-8f};  // 1/ln 2 as float-float
     L = ff_mul(L, inv_ln2);
-    const ff T = {c_lg2t[0][j], c_lg2t[1][j]};
+    const ff T = {tab[0][j], tab[1][j]};
     return ff_add(ff_add(ff{(float)e, 0.f}, T), L);
 }
 
@@ -1768,6 +1789,9 @@ __global__ void __launch_bounds__(256) k_p2p_ff(Sched sc, const Inst* __restrict
                                                 const float4* __restrict__ pk, const double* __restrict__ cen,
                                                 float* __restrict__ nhi, float* __restrict__ nlo)
 {
+    __shared__ float tab[3][129];
+    for (int i = threadIdx.x; i < 3 * 129; i += blockDim.x) (&tab[0][0])[i] = (&c_lg2t[0][0])[i];
+    __syncthreads();
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
     const LInst TL = LIs[z.i];
@@ -1794,14 +1818,10 @@ __global__ void __launch_bounds__(256) k_p2p_ff(Sched sc, const Inst* __restrict
     const int64_t v0 = pos[e_begin], v1 = pos[e_end];
     const int64_t warp = ((int64_t)z.rank * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)z.nb * blockDim.x) >> 5;
-    for (int64_t v = v0 + warp; v < v1; v += nwarps) {
-        int64_t lo = e_begin, hi = e_end - 1;  // the pair owning item v
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (pos[mid] <= v) lo = mid;
-            else hi = mid - 1;
-        }
-        const int64_t e = lo;
+    const ItemRange rg = item_range(pos, e_begin, e_end, v0, v1, warp, nwarps);
+    int64_t e = rg.e;
+    for (int64_t v = rg.va; v < rg.vb; v++) {
+        while (e + 1 < e_end && pos[e + 1] <= v) e++;  // the pair owning item v
         const int64_t tl = stgt[e] - base, sl = sidx[e];
         const int32_t t0 = lb[tl], nt = lb[tl + 1] - t0, s0 = lb[sl], ns = lb[sl + 1] - s0;
         const int32_t nsc = p2p_src_blocks(nt, ns), ntc = (nt + 31) / 32;
@@ -1825,7 +1845,7 @@ __global__ void __launch_bounds__(256) k_p2p_ff(Sched sc, const Inst* __restrict
             if (!(r2.h > 0.f)) continue;  // coincident points, j = i among them
             ff lg;
             if (r2.h >= 1e-30f) {
-                lg = ff_log2(r2);
+                lg = ff_log2(r2, tab);
             } else {  // below the binary32 normal range of the table method: binary64
                 lg = ff_split(log2((double)r2.h + (double)r2.l));
             }
@@ -1905,7 +1925,7 @@ __device__ __forceinline__ ff ff_div(ff a, ff b)
 // its ends), binary64 outside it
 __device__ __forceinline__ ff ff_log2_any(ff a)
 {
-    if (a.h >= 1e-30f && a.h <= 1e30f) return ff_log2(a);
+    if (a.h >= 1e-30f && a.h <= 1e30f) return ff_log2(a, c_lg2t);
     return ff_split(log2((double)a.h + (double)a.l));
 }
 
@@ -2609,11 +2629,13 @@ int ensure_tables()
         if (compiled[i] != mf[i / PMAXC][i % PMAXC])
             return fail(FMM_ERR_STATE, "compiled M2L coefficient (%d, %d) differs from the table", i / PMAXC, i % PMAXC);
     FMM_CUDA(cudaMemcpyToSymbol(c_md, md, sizeof(md)));
-    static float lg[2][129];
+    static float lg[3][129];
     for (int j = 0; j <= 128; j++) {
         const double v = log2((double)(128 + j) / 128.0);
         lg[0][j] = (float)v;
         lg[1][j] = (float)(v - (double)lg[0][j]);
+        const float F = 1.f + (float)j * (1.f / 128.f);
+        lg[2][j] = 1.f / F;  // binary32 division, correctly rounded (as on the device)
     }
     FMM_CUDA(cudaMemcpyToSymbol(c_lg2t, lg, sizeof(lg)));
     g_tab_ready[dev] = true;
