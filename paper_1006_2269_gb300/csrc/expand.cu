@@ -1923,19 +1923,19 @@ __device__ __forceinline__ ff ff_div(ff a, ff b)
 
 // log2 of a positive float-float r^2: the table method inside the binary32 normal range (far from
 // its ends), binary64 outside it
-__device__ __forceinline__ ff ff_log2_any(ff a)
+__device__ __forceinline__ ff ff_log2_any(ff a, const float (*tab)[129])
 {
-    if (a.h >= 1e-30f && a.h <= 1e30f) return ff_log2(a, c_lg2t);
+    if (a.h >= 1e-30f && a.h <= 1e30f) return ff_log2(a, tab);
     return ff_split(log2((double)a.h + (double)a.l));
 }
 
 // rho conj(dz) / |dz|^2 (= rho / dz) and log|dz| of the offset dz = (dx, dy), float-float
-__device__ __forceinline__ void ff_inv_log(ff dx, ff dy, ff rho, ff ln2h, cff& w, ff& lg)
+__device__ __forceinline__ void ff_inv_log(ff dx, ff dy, ff rho, ff ln2h, cff& w, ff& lg, const float (*tab)[129])
 {
     const ff r2 = ff_add(ff_sq(dx), ff_sq(dy));
     const ff s = ff_div(rho, r2);
     w = {ff_mul(s, dx), ff_mul(s, ff{-dy.h, -dy.l})};
-    lg = ff_mul(ff_log2_any(r2), ln2h);  // log|dz| = (ln 2 / 2) log2 |dz|^2
+    lg = ff_mul(ff_log2_any(r2, tab), ln2h);  // log|dz| = (ln 2 / 2) log2 |dz|^2
 }
 
 // The multipole coefficients as float-float (re.h, re.l, im.h, im.l), same layout as the binary64
@@ -1962,6 +1962,9 @@ __global__ void __launch_bounds__(256) k_m2p_ff(Sched sc, const Inst* __restrict
                                                 const double* __restrict__ rad, XLists xl,
                                                 const float4* __restrict__ Mff, double* __restrict__ acc)
 {
+    __shared__ float tab[3][129];  // the logarithm's table (see ff_log2)
+    for (int i = threadIdx.x; i < 3 * 129; i += blockDim.x) (&tab[0][0])[i] = (&c_lg2t[0][0])[i];
+    __syncthreads();
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
     const LInst T_ = LIs[z.i];
@@ -2022,7 +2025,7 @@ __global__ void __launch_bounds__(256) k_m2p_ff(Sched sc, const Inst* __restrict
                 const int32_t k = gl + j * gs;
                 if (k < nt) {
                     const float4 p = pk[2 * (t0 + k)];
-                    ff_inv_log(ff_add(ff{p.x, p.y}, dcx), ff_add(ff{p.z, p.w}, dcy), rho, ln2h, w[j], lg[j]);
+                    ff_inv_log(ff_add(ff{p.x, p.y}, dcx), ff_add(ff{p.z, p.w}, dcy), rho, ln2h, w[j], lg[j], tab);
                 }
             }
             for (int kk = P - 1; kk >= 1; kk--) {
@@ -2043,7 +2046,7 @@ __global__ void __launch_bounds__(256) k_m2p_ff(Sched sc, const Inst* __restrict
                 const float4 p = pk[2 * (t0 + k)];
                 cff w1, h1 = {{0.f, 0.f}, {0.f, 0.f}};
                 ff lg1;
-                ff_inv_log(ff_add(ff{p.x, p.y}, dcx), ff_add(ff{p.z, p.w}, dcy), rho, ln2h, w1, lg1);
+                ff_inv_log(ff_add(ff{p.x, p.y}, dcx), ff_add(ff{p.z, p.w}, dcy), rho, ln2h, w1, lg1, tab);
                 for (int kk = P - 1; kk >= 1; kk--) {
                     const float4 a = A[kk];
                     h1 = cff_fma(h1, w1, cff{{a.x, a.y}, {a.z, a.w}});
@@ -2068,6 +2071,9 @@ __global__ void k_p2l_ff(Sched sc, const Inst* __restrict__ I, const LInst* __re
                          cx<double>* __restrict__ Le)
 {
     extern __shared__ unsigned char smem[];
+    __shared__ float tab[3][129];  // the logarithm's table (see ff_log2)
+    for (int i = threadIdx.x; i < 3 * 129; i += blockDim.x) (&tab[0][0])[i] = (&c_lg2t[0][0])[i];
+    __syncthreads();
     const Slot z = slot_of(sc);
     const Inst S = I[z.i];
     const int L = S.L;
@@ -2129,7 +2135,7 @@ __global__ void k_p2l_ff(Sched sc, const Inst* __restrict__ I, const LInst* __re
                     const int64_t sgb = base + sk;
                     const ff dx = ff_add(ff{p.x, p.y}, ff_split(cen[2 * sgb] - cen[2 * g]));
                     const ff dy = ff_add(ff{p.z, p.w}, ff_split(cen[2 * sgb + 1] - cen[2 * g + 1]));
-                    ff_inv_log(dx, dy, rho, ln2h, u, lg);
+                    ff_inv_log(dx, dy, rho, ln2h, u, lg, tab);
                     const ff q = {pq.x, pq.y};
                     pw.re = q;
                     lg = ff_mul(q, lg);
